@@ -1,0 +1,165 @@
+"""Seeded synthetic inputs for the honeycomb QR-CTMRG hot path.
+
+This module is shared by the CUDA path, the CPU oracle, the tests and the
+benchmark.  It holds input generation only -- random site tensors, bond
+Hamiltonians, a classical-Ising site tensor and the workload table -- and none
+of the CTMRG arithmetic (no symmetrisation, no double layer, no contraction).
+
+The paper's workloads are optimised Heisenberg / Kitaev iPEPS tensors (Sec. III)
+which are not available; seeded uniform[-1, 1] tensors of the same shapes stand
+in for them.  The Hamiltonian is the Kitaev-Heisenberg model of Eq. (4),
+H = sum_<ij>_a K S^a_i S^a_j + J sum_<ij> S_i . S_j, with S = sigma / 2 for
+spin-1/2 (Sec. III.A).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+__all__ = [
+    "random_site_tensor",
+    "product_site_tensor",
+    "ising_site_tensor",
+    "spin_matrices",
+    "bond_hamiltonians",
+    "Workload",
+    "WORKLOADS",
+    "batch_workload",
+]
+
+
+def random_site_tensor(d: int, D: int, seed: int) -> np.ndarray:
+    """Raw site tensor A[s, i, j, k] with entries uniform in [-1, 1].
+
+    Layout: float64, shape (d, D, D, D), row-major (s slowest).  The
+    C3v (A1) projection and the Frobenius normalisation are part of the method
+    and are *not* applied here.
+    """
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=(d, D, D, D)).astype(np.float64)
+
+
+def product_site_tensor(v) -> np.ndarray:
+    """D = 1 site tensor A[s, 0, 0, 0] = v[s] (a product state |v> on every site)."""
+    v = np.asarray(v, dtype=np.float64)
+    return v.reshape(-1, 1, 1, 1).copy()
+
+
+def ising_site_tensor(beta: float) -> np.ndarray:
+    """Site tensor whose norm network is the classical Ising model on the honeycomb lattice.
+
+    A[s; i, j, k] = W[s, i] W[s, j] W[s, k] with (W W^T)[s, t] = exp((beta/2) sigma_s sigma_t),
+    sigma = (+1, -1).  Contracting two double-layer tensors over a bond gives
+    (W W^T)[s, t]^2 = exp(beta sigma_s sigma_t), so <Psi|Psi> is the honeycomb
+    Ising partition function and 4 <S^z S^z> on a bond is the nearest-neighbour
+    spin correlation.  d = D = 2, real, symmetric in its three virtual legs.
+    """
+    # (W W^T) = [[e^{b/2}, e^{-b/2}], [e^{-b/2}, e^{b/2}]] has eigenvalues
+    # 2 cosh(b/2) (vector (1,1)/sqrt2) and 2 sinh(b/2) (vector (1,-1)/sqrt2).
+    l0 = 2.0 * math.cosh(beta / 2.0)
+    l1 = 2.0 * math.sinh(beta / 2.0)
+    if l1 <= 0.0:
+        raise ValueError("beta must be positive")
+    r = 1.0 / math.sqrt(2.0)
+    W = np.array([[r * math.sqrt(l0), r * math.sqrt(l1)],
+                  [r * math.sqrt(l0), -r * math.sqrt(l1)]])
+    return np.einsum("si,sj,sk->sijk", W, W, W)
+
+
+def spin_matrices(d: int = 2):
+    """Spin-S operators (S^x, S^y, S^z) for d = 2S + 1 in the S^z basis (m = S, S-1, ...)."""
+    S = (d - 1) / 2.0
+    m = S - np.arange(d)
+    Sz = np.diag(m).astype(np.complex128)
+    Sp = np.zeros((d, d), dtype=np.complex128)
+    for k in range(1, d):
+        # <m+1| S^+ |m> = sqrt(S(S+1) - m(m+1)), with row k-1 holding m+1
+        mm = m[k]
+        Sp[k - 1, k] = math.sqrt(S * (S + 1) - mm * (mm + 1))
+    Sx = (Sp + Sp.conj().T) / 2.0
+    Sy = (Sp - Sp.conj().T) / 2.0j
+    return Sx, Sy, Sz
+
+
+def bond_hamiltonians(K: float, J: float, d: int = 2, rotate_b: bool = False) -> np.ndarray:
+    """Bond operators h_a = K S^a S^a + J S.S for a = x, y, z (Eq. 4), as real d^2 x d^2 matrices.
+
+    Row index (s_A, s_B) = s_A * d + s_B, column index likewise: h[(s t), (s' t')] =
+    <s t| h |s' t'>.  ``rotate_b`` applies the pi-rotation about y on the B site
+    used for the uniform Heisenberg ansatz (Sec. III.B): S^x_B -> -S^x_B,
+    S^z_B -> -S^z_B.
+    """
+    Sx, Sy, Sz = spin_matrices(d)
+    sgn = (-1.0, 1.0, -1.0) if rotate_b else (1.0, 1.0, 1.0)
+    ops = (Sx, Sy, Sz)
+    pair = [sgn[a] * np.kron(ops[a], ops[a]) for a in range(3)]
+    heis = pair[0] + pair[1] + pair[2]
+    hs = []
+    for a in range(3):
+        h = K * pair[a] + J * heis
+        if np.max(np.abs(h.imag)) > 1e-14:
+            raise ValueError("bond operator is not real")
+        hs.append(h.real)
+    return np.ascontiguousarray(np.stack(hs), dtype=np.float64)
+
+
+@dataclass
+class Workload:
+    """One single-instance CTMRG workload (d, D, chi, Hamiltonian, seed)."""
+    name: str
+    d: int
+    D: int
+    chi: int
+    K: float
+    J: float
+    seed: int
+    steps: int
+    tol: float = 1e-10
+    precision: str = "fp64"
+    note: str = ""
+
+    @property
+    def D2(self) -> int:
+        return self.D * self.D
+
+    @property
+    def n(self) -> int:
+        return self.chi * self.D * self.D
+
+    def site_tensor(self) -> np.ndarray:
+        return random_site_tensor(self.d, self.D, self.seed)
+
+    def hamiltonians(self) -> np.ndarray:
+        return bond_hamiltonians(self.K, self.J, self.d)
+
+
+_PHI = 0.3 * math.pi
+
+# The five workloads: Heisenberg D=2/chi=8 (oracle-sized), Kitaev D=4/chi=32,
+# Kitaev-Heisenberg D=6/chi=72 and D=8/chi=128 (phi = 0.3 pi), and a 96-instance
+# ragged batch.  Seeds are 1000 + index (5000 + i for the batch instances).
+WORKLOADS = {
+    "heis_D2_chi8": Workload("heis_D2_chi8", 2, 2, 8, 0.0, 1.0, 1000, 50,
+                             note="Heisenberg J=1, 50 steps or delta<1e-10"),
+    "kitaev_D4_chi32": Workload("kitaev_D4_chi32", 2, 4, 32, 1.0, 0.0, 1001, 200,
+                                note="isotropic Kitaev K=1, 200 steps"),
+    "kh_D6_chi72": Workload("kh_D6_chi72", 2, 6, 72, math.cos(_PHI), math.sin(_PHI), 1002, 200,
+                            note="Kitaev-Heisenberg phi=0.3pi, enlarged corner 2592x2592"),
+    "kh_D8_chi128": Workload("kh_D8_chi128", 2, 8, 128, math.cos(_PHI), math.sin(_PHI), 1003, 30,
+                             note="Kitaev-Heisenberg phi=0.3pi, enlarged corner 8192x8192"),
+}
+
+
+def batch_workload(n_inst: int = 96, seed0: int = 5000):
+    """Ragged batch: D uniform in {3,4,5,6}, chi uniform in {24,32,...,72}, phi_i = 2 pi i / n."""
+    rng = np.random.default_rng(seed0)
+    Ds = rng.integers(3, 7, size=n_inst)
+    chis = 24 + 8 * rng.integers(0, 7, size=n_inst)
+    out = []
+    for i in range(n_inst):
+        phi = 2.0 * math.pi * i / n_inst
+        out.append(Workload(f"batch_{i}", 2, int(Ds[i]), int(chis[i]), math.cos(phi), math.sin(phi),
+                            seed0 + i, 30, precision="split"))
+    return out
