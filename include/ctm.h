@@ -1,0 +1,155 @@
+/*
+ * ctm.h -- C ABI of libctm, a GB300 (sm_103a) implementation of one QR-based,
+ * C3v-symmetric CTMRG renormalisation step for a honeycomb-lattice iPEPS and of
+ * the nearest-neighbour bond energies evaluated from its environment
+ * (Yang & Corboz, "Efficient iPEPS Simulation on the Honeycomb Lattice via
+ * QR-based CTMRG", arXiv 2509.05090).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - All tensors are row-major double (FP64) arrays.  "_dev" pointers are CUDA
+ *    device pointers on the current device; "_host" pointers are host memory.
+ *  - d = physical dimension, D = virtual bond dimension, D2 = D*D (double-layer
+ *    bond), chi = environment bond dimension, n = chi*D2.
+ *  - A[s][i][j][k] (d x D x D x D) is the site tensor of the uniform ansatz
+ *    (Sec. II.A, Fig. 1a).  The three virtual legs are the three bonds of a
+ *    honeycomb site.
+ *  - C[g][h] (chi x chi) is the corner of one 60-degree sector and
+ *    T[a][u][g] (chi x D2 x chi) its edge: a = outer side (the bonds crossing
+ *    the sector boundary), u = the end leg toward the apex, g = the side facing
+ *    the corner (Sec. II.B, Fig. 3a,b).
+ *  - Q[r][j] (n x chi) is the isometric projector of the last step
+ *    (Fig. 3d); its row index r = a*D2 + y fuses the chi index (slow) with a
+ *    double-layer leg.
+ *  - The caller owns all device memory: it allocates one workspace of
+ *    ctm_workspace_bytes() bytes (for example a uint8 torch tensor) and passes
+ *    it to ctm_init.  No call allocates device memory after ctm_init.
+ *  - Work is enqueued on the stream given to ctm_init (a cudaStream_t passed
+ *    as void*; NULL = legacy default stream).  Calls that return "_host"
+ *    results synchronise that stream; the others are asynchronous unless stated.
+ *  - No C++ exception crosses this interface.  Every call returns a status; a
+ *    non-OK status leaves the context valid (it can be destroyed or
+ *    re-initialised) but its environment undefined.  A context is not
+ *    thread-safe.
+ */
+#ifndef CTM_H
+#define CTM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ctm_ctx ctm_ctx;
+
+typedef enum {
+    CTM_OK = 0,
+    CTM_EINVAL = 1,          /* bad argument (null pointer, size out of range) */
+    CTM_ENOMEM = 2,          /* workspace too small */
+    CTM_ECUDA = 3,           /* a CUDA runtime call failed */
+    CTM_ENOTCONVERGED = 4,   /* max_steps reached with delta >= tol (outputs still filled) */
+    CTM_ENONFINITE = 5,      /* NaN or Inf in the environment or the input tensor */
+    CTM_ETIMEOUT = 6,        /* a bounded device-side wait gave up */
+    CTM_EUNSUPPORTED = 7     /* shape or mode not supported by this build */
+} ctm_status;
+
+typedef enum {
+    CTM_FP64 = 0,            /* every contraction in FP64 */
+    CTM_SPLIT_BF16 = 1       /* contractions as split-BF16 tcgen05 products (FP32 accumulate,
+                                FP64 recombination); QR, normalisation and the
+                                convergence test stay FP64 */
+} ctm_precision;
+
+typedef struct {
+    int d, D, chi;           /* physical, virtual and environment bond dimensions */
+    int precision;           /* ctm_precision */
+    int n_split;             /* BF16 slices per operand in CTM_SPLIT_BF16 (2..6); ignored in FP64 */
+    double tol;              /* convergence threshold on delta (Sec. II.B: "desired precision") */
+    int max_steps;           /* step limit of ctm_converge when its argument is <= 0 */
+    int symmetrize;          /* 1: project A onto the C3v A1 subspace and normalise (App. A) */
+} ctm_config;
+
+/* Bytes of device workspace ctm_init needs for this configuration (0 on a bad
+ * config).  Dominated by two n x n FP64 intermediates (enlarged corner and
+ * edge-chain buffers). */
+size_t ctm_workspace_bytes(const ctm_config *cfg);
+
+/* Sec. II.A-B: set up one instance.  A_dev: raw site tensor [s][i][j][k]
+ * (device).  With cfg->symmetrize the tensor is averaged over the six leg
+ * permutations (the C3v group for the A1 irrep, U_g = I; App. A) and
+ * normalised to unit Frobenius norm; then the double layer
+ * a[(ii')][(jj')][(kk')] = sum_s A[s,i,j,k] A[s,i',j',k'] is formed (Fig. 1b),
+ * and the environment starts from C = I, T[a][u][b] = delta_ab t_u with
+ * t_u = sum_{v,w} a[u][(vv)][(ww)], and Q = the first chi columns of I_n.
+ * The workspace must stay valid until ctm_destroy.  On success *out owns a
+ * host-side context. */
+int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t ws_bytes,
+             void *stream, ctm_ctx **out);
+
+/* Sec. II.B, Fig. 3: run nsteps CTMRG steps.  One step builds the enlarged
+ * corner M from (C, T, a), the reduced corner Y = M Q diag(sgn C_ii),
+ * Householder QR Y = Q R with diag(R) >= 0, C' = sym(Q^T M Q)/|.|,
+ * T' = Q^T (T a a) Q/|.|, and delta = |s(C') - s(C)|_2 of the unit-norm
+ * descending singular values.  delta_host (may be NULL) receives the last
+ * delta and makes the call synchronous.  Returns CTM_ENONFINITE if the new
+ * environment holds NaN/Inf (checked only when delta_host is given). */
+int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
+
+/* Sec. II.B: repeat steps until delta < tol (tol <= 0: cfg->tol) or max_steps
+ * (<= 0: cfg->max_steps).  Steps are replayed from a captured CUDA graph;
+ * delta is read back every check_every steps (>= 1).  Synchronous.  Returns
+ * CTM_ENOTCONVERGED (outputs filled) if the limit was hit. */
+int ctm_converge(ctm_ctx *ctx, int max_steps, double tol, int check_every,
+                 int *steps_out, double *delta_out);
+
+/* Eq. (1), Fig. 5b: nearest-neighbour bond energies from the current
+ * environment.  With Q from one more QR step and Ch = sym(Q^T M Q)/|.|, the
+ * reduced density matrix of the apex bond is
+ * rho = tr(Ch^5 Q^T M_oo Q) / tr(Ch^6), where M_oo opens the physical legs of
+ * the apex dimer.  h_dev: 3 bond operators (x, y, z) of size d^2 x d^2,
+ * h[a][(s t)][(s' t')] = <s t| h_a |s' t'> (device).  e_bond_host[a] =
+ * tr(rho h_a); e_site_host = (1/2) sum_a e_bond[a] (Eq. 4 Hamiltonian per
+ * site).  rho_host (may be NULL) receives rho (d^2 x d^2).  Synchronous;
+ * does not change the environment. */
+int ctm_energy(ctm_ctx *ctx, const double *h_dev, double *e_bond_host, double *e_site_host,
+               double *rho_host);
+
+/* Copy the current environment out / in (device pointers; parity checks and
+ * resume).  C: chi x chi, T: chi x D2 x chi, Q: n x chi. */
+int ctm_get_env(const ctm_ctx *ctx, double *C_dev, double *T_dev, double *Q_dev);
+int ctm_set_env(ctm_ctx *ctx, const double *C_dev, const double *T_dev, const double *Q_dev);
+
+/* Intermediates of the most recent step (device copies; parity checks):
+ * which = 0: enlarged corner M (n x n), 1: reduced corner Y (n x chi),
+ * 2: R (chi x chi), 3: the projector Q used (n x chi), 4: corner spectrum s
+ * (chi, descending, unit norm), 5: the prepared site tensor A (d x D^3),
+ * 6: the double layer a (D2^3).  Returns CTM_EINVAL for an unknown id and
+ * CTM_EUNSUPPORTED for an intermediate the current precision does not keep. */
+int ctm_get_intermediate(const ctm_ctx *ctx, int which, double *dst_dev, size_t count);
+
+/* One step (as ctm_step) with CUDA events recorded on the context's stream
+ * between its phases; synchronous.  phase_ms (nphase >= 7) receives the
+ * milliseconds of: [0] enlarged corner, [1] warm start + reduced corner
+ * Y = M Qs, [2] Householder QR, [3] corner renormalisation, [4] edge
+ * renormalisation, [5] corner spectrum and delta, [6] environment hand-over. */
+int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
+
+/* Number of kernel launches the library has enqueued since it was loaded
+ * (host-side count; replays of a captured graph are not counted). */
+unsigned long long ctm_kernel_launches(void);
+
+/* Release the host context (the caller frees the workspace). */
+void ctm_destroy(ctm_ctx *ctx);
+
+/* Human-readable name of a status code. */
+const char *ctm_status_str(int status);
+
+/* Library build identifier, e.g. "libctm sm_103a fp64+bf16split". */
+const char *ctm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CTM_H */

@@ -1,0 +1,223 @@
+"""Thin ctypes binding of libctm (include/ctm.h), same names as the C ABI.
+
+Argument marshalling only: every step of the CTMRG path runs in the CUDA
+kernels of libctm.so.  PyTorch provides device memory (the workspace and the
+input/output tensors) and the CUDA stream.  There is no CPU fallback: if the
+library is missing or no CUDA device is present, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctm.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "ctm.h")
+
+CTM_OK = 0
+CTM_ENOTCONVERGED = 4
+CTM_FP64 = 0
+CTM_SPLIT_BF16 = 1
+PRECISIONS = {"fp64": CTM_FP64, "split_bf16": CTM_SPLIT_BF16}
+
+
+class ctm_config(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("D", ctypes.c_int), ("chi", ctypes.c_int),
+                ("precision", ctypes.c_int), ("n_split", ctypes.c_int), ("tol", ctypes.c_double),
+                ("max_steps", ctypes.c_int), ("symmetrize", ctypes.c_int)]
+
+
+class CtmError(RuntimeError):
+    def __init__(self, status, what):
+        self.status = status
+        super().__init__(f"{what}: {status_str(status)}")
+
+
+_lib = None
+
+
+def header_functions(path: str = HEADER):
+    """Names of the functions include/ctm.h declares."""
+    txt = open(path).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(ctm_[a-z_0-9]+)\s*\(", txt)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libctm.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libctm.so not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    dp = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.c_int
+    cfgp = ctypes.POINTER(ctm_config)
+    sigs = {
+        "ctm_workspace_bytes": (ctypes.c_size_t, [cfgp]),
+        "ctm_init": (I, [cfgp, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+        "ctm_step": (I, [P, I, dp]),
+        "ctm_converge": (I, [P, I, ctypes.c_double, I, ctypes.POINTER(I), dp]),
+        "ctm_energy": (I, [P, P, dp, dp, dp]),
+        "ctm_get_env": (I, [P, P, P, P]),
+        "ctm_set_env": (I, [P, P, P, P]),
+        "ctm_get_intermediate": (I, [P, I, P, ctypes.c_size_t]),
+        "ctm_destroy": (None, [P]),
+        "ctm_status_str": (ctypes.c_char_p, [I]),
+        "ctm_version": (ctypes.c_char_p, []),
+        "ctm_step_profiled": (I, [P, dp, I]),
+        "ctm_kernel_launches": (ctypes.c_ulonglong, []),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = lib
+    return lib
+
+
+def ctm_kernel_launches() -> int:
+    return int(load().ctm_kernel_launches())
+
+
+def status_str(status: int) -> str:
+    return load().ctm_status_str(int(status)).decode()
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("libctm needs a CUDA device; there is no CPU fallback")
+    return torch
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_config(d, D, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True):
+    return ctm_config(int(d), int(D), int(chi), PRECISIONS[precision] if isinstance(precision, str) else
+                      int(precision), int(n_split), float(tol), int(max_steps), 1 if symmetrize else 0)
+
+
+def ctm_workspace_bytes(cfg: ctm_config) -> int:
+    return int(load().ctm_workspace_bytes(ctypes.byref(cfg)))
+
+
+class CTM:
+    """One CTMRG instance on the current CUDA device (ctm_init ... ctm_destroy)."""
+
+    def __init__(self, A, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True,
+                 stream=None):
+        torch = _torch()
+        lib = load()
+        if isinstance(A, np.ndarray):
+            A = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float64)).cuda()
+        A = A.to(device="cuda", dtype=torch.float64).contiguous()
+        d, D = int(A.shape[0]), int(A.shape[1])
+        self.d, self.D, self.chi = d, D, int(chi)
+        self.D2 = D * D
+        self.n = self.chi * self.D2
+        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize)
+        nbytes = ctm_workspace_bytes(self.cfg)
+        if nbytes == 0:
+            raise CtmError(1, "ctm_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self._A = A
+        h = ctypes.c_void_p()
+        st = lib.ctm_init(ctypes.byref(self.cfg), _ptr(A), _ptr(self.workspace), nbytes,
+                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_init")
+        self._h = h
+
+    # --- calls ---------------------------------------------------------
+    def ctm_step(self, nsteps=1, want_delta=True):
+        d = ctypes.c_double(float("nan"))
+        st = load().ctm_step(self._h, int(nsteps), ctypes.byref(d) if want_delta else None)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_step")
+        return d.value if want_delta else None
+
+    def ctm_converge(self, max_steps=0, tol=0.0, check_every=1, raise_not_converged=False):
+        steps = ctypes.c_int(0)
+        delta = ctypes.c_double(float("nan"))
+        st = load().ctm_converge(self._h, int(max_steps), float(tol), int(check_every), ctypes.byref(steps),
+                                 ctypes.byref(delta))
+        if st not in (CTM_OK, CTM_ENOTCONVERGED) or (st != CTM_OK and raise_not_converged):
+            raise CtmError(st, "ctm_converge")
+        return steps.value, delta.value, st == CTM_OK
+
+    def ctm_energy(self, h):
+        torch = _torch()
+        if isinstance(h, np.ndarray):
+            h = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64))
+        h = h.to(device="cuda", dtype=torch.float64).contiguous()
+        dd = self.d * self.d
+        e = (ctypes.c_double * 3)()
+        es = ctypes.c_double()
+        rho = (ctypes.c_double * (dd * dd))()
+        st = load().ctm_energy(self._h, _ptr(h), e, ctypes.byref(es), rho)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_energy")
+        return np.array(e[:]), es.value, np.array(rho[:]).reshape(dd, dd)
+
+    def ctm_get_env(self):
+        torch = _torch()
+        C = torch.empty((self.chi, self.chi), dtype=torch.float64, device="cuda")
+        T = torch.empty((self.chi, self.D2, self.chi), dtype=torch.float64, device="cuda")
+        Q = torch.empty((self.n, self.chi), dtype=torch.float64, device="cuda")
+        st = load().ctm_get_env(self._h, _ptr(C), _ptr(T), _ptr(Q))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_get_env")
+        return C, T, Q
+
+    def ctm_set_env(self, C, T, Q):
+        torch = _torch()
+        conv = [(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)) if isinstance(x, np.ndarray) else x)
+                .to(device="cuda", dtype=torch.float64).contiguous() for x in (C, T, Q)]
+        st = load().ctm_set_env(self._h, *[_ptr(x) for x in conv])
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_set_env")
+
+    _SHAPES = {0: "M", 1: "Y", 2: "R", 3: "Q", 4: "s", 5: "A", 6: "a"}
+
+    def ctm_get_intermediate(self, which):
+        torch = _torch()
+        if isinstance(which, str):
+            which = {v: k for k, v in self._SHAPES.items()}[which]
+        n, chi, D2 = self.n, self.chi, self.D2
+        shape = {0: (n, n), 1: (n, chi), 2: (chi, chi), 3: (n, chi), 4: (chi,),
+                 5: (self.d, self.D, self.D, self.D), 6: (D2, D2, D2)}[which]
+        out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        st = load().ctm_get_intermediate(self._h, int(which), _ptr(out), out.numel())
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_get_intermediate")
+        return out
+
+    PHASES = ("enlarged_corner", "reduced_corner", "qr", "corner", "edge", "spectrum", "handover")
+
+    def ctm_step_profiled(self):
+        ms = (ctypes.c_double * 8)()
+        st = load().ctm_step_profiled(self._h, ms, 8)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_step_profiled")
+        return dict(zip(self.PHASES, ms[:7]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            load().ctm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

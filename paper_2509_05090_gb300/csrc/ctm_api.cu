@@ -1,0 +1,683 @@
+// C ABI of libctm: context, workspace layout and the launch sequence of one
+// QR-based C3v CTMRG step (Sec. II.B, Fig. 3) and of the bond-energy
+// evaluation (Sec. II.C, Eq. 1).  See include/ctm.h for the contract.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "ctm_internal.h"
+
+namespace {
+
+// ---------------------------------------------------------------- rho reduction
+// raw[pB][pA] = sum_{ab, z} Y1o[ab][pB][z] * G2[ab][pA][z]  (dd = d^2 <= 9)
+constexpr int RHO_MAX_DD = 9;
+
+__global__ void rho_partial_kernel(long long nab, int dd, int D2, const double *Y1o, const double *G2,
+                                   double *partials)
+{
+    __shared__ double red[RHO_MAX_DD * RHO_MAX_DD][8];
+    double acc[RHO_MAX_DD * RHO_MAX_DD];
+    for (int i = 0; i < dd * dd; ++i) acc[i] = 0.0;
+    const long long row = (long long)dd * D2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nab * D2;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long ab = t / D2;
+        int z = (int)(t - ab * D2);
+        const double *y = Y1o + ab * row + z;
+        const double *g = G2 + ab * row + z;
+        for (int pb = 0; pb < dd; ++pb) {
+            double yv = y[(size_t)pb * D2];
+            for (int pa = 0; pa < dd; ++pa) acc[pb * dd + pa] = fma(yv, g[(size_t)pa * D2], acc[pb * dd + pa]);
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < dd * dd; ++i) {
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < dd * dd) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * dd * dd + threadIdx.x] = s;
+    }
+}
+
+__global__ void rho_final_kernel(int nblocks, int dd, const double *partials, double *raw)
+{
+    int i = threadIdx.x;
+    if (i >= dd * dd) return;
+    double s = 0.0;
+    for (int b = 0; b < nblocks; ++b) s += partials[(size_t)b * dd * dd + i];
+    raw[i] = s;
+}
+
+constexpr int RHO_BLOCKS = 256;
+constexpr int NORM_BLOCKS = 256;
+
+size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+
+struct ctm_ctx {
+    ctm_config cfg;
+    int d, D, D2, chi;
+    long long n;
+    cudaStream_t stream;      // the caller's stream
+    cudaStream_t own;         // private stream used for graph capture and replay
+    cudaEvent_t ev_in, ev_out;
+    // FP64 buffers (device, inside the caller's workspace)
+    double *A, *a;
+    double *C, *Cn, *Cr;
+    double *T, *Tn;
+    double *Q, *Qn, *Qs, *Y, *W, *MQ;
+    double *R;
+    double *M, *X, *H;
+    double *Y1;
+    double *s, *s_new, *delta;
+    double *splitk;
+    size_t splitk_elems;
+    double *qr_sbuf, *qr_rowbuf;
+    unsigned *qr_bar;
+    int *err, *flag;
+    double *norm_part;
+    // energy
+    double *b, *Y1o, *G2, *P5a, *P5b, *rho_part, *rho_raw, *eout, *h;
+    // graph of `graph_steps` steps
+    cudaGraphExec_t graph;
+    int graph_steps;
+    int graph_failed;
+    int steps_done;
+};
+
+namespace {
+
+// Carve the workspace.  With base == nullptr only the size is computed.
+size_t layout(ctm_ctx *c, char *base)
+{
+    const long long chi = c->chi, D2 = c->D2, n = c->n, d = c->d;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += align_up(bytes);
+        return p;
+    };
+    auto td = [&](long long count) -> double * { return (double *)take(sizeof(double) * (size_t)count); };
+    c->A = td(d * c->D * c->D * c->D);
+    c->a = td(D2 * D2 * D2);
+    c->C = td(chi * chi);
+    c->Cn = td(chi * chi);
+    c->Cr = td(chi * chi);
+    c->T = td(chi * D2 * chi);
+    c->Tn = td(chi * D2 * chi);
+    c->Q = td(n * chi);
+    c->Qn = td(n * chi);
+    c->Qs = td(n * chi);
+    c->Y = td(n * chi);
+    c->W = td(n * chi);
+    c->MQ = td(n * chi);
+    c->R = td(chi * chi);
+    c->M = td(n * n);
+    c->X = td(n * n);
+    c->H = td(n * n);
+    c->Y1 = td(chi * chi * D2);
+    c->s = td(chi);
+    c->s_new = td(chi);
+    c->delta = td(8);
+    // split-K scratch: the largest ksplit * M * N over the step's GEMMs
+    size_t sk = 0;
+    auto need = [&](long long M, long long N, long long K) {
+        int s = gemm_f64_pick_split((int)M, (int)N, (int)K);
+        if (s > 1 && (size_t)(s * M * N) > sk) sk = (size_t)(s * M * N);
+    };
+    need(n, chi, chi);
+    need(n, n, chi);
+    need(chi * chi, D2, D2 * D2);
+    need(chi * chi, D2 * D2, D2);
+    need(n, chi, n);
+    need(chi, chi, n);
+    need(n, D2 * chi, chi);
+    need(chi, D2 * chi, n);
+    need(chi, chi, chi);
+    need(chi * chi, d * d * D2, D2 * D2);
+    c->splitk_elems = sk;
+    c->splitk = td((long long)sk + 1);
+    c->qr_sbuf = td((long long)qr_scratch_doubles((int)chi));
+    c->qr_rowbuf = td(2 * chi);
+    c->qr_bar = (unsigned *)take(64);
+    c->err = (int *)take(64);
+    c->flag = (int *)take(64);
+    c->norm_part = td(NORM_BLOCKS);
+    c->b = td(d * d * D2 * D2 * D2);
+    c->Y1o = td(chi * chi * d * d * D2);
+    c->G2 = td(chi * chi * d * d * D2);
+    c->P5a = td(chi * chi);
+    c->P5b = td(chi * chi);
+    c->rho_part = td((long long)RHO_BLOCKS * d * d * d * d);
+    c->rho_raw = td(d * d * d * d);
+    c->eout = td(4 + d * d * d * d);
+    c->h = td(3 * d * d * d * d);
+    return off;
+}
+
+bool config_ok(const ctm_config *cfg)
+{
+    if (!cfg) return false;
+    if (cfg->d < 1 || cfg->d > 3) return false;
+    if (cfg->D < 1 || cfg->D > 12) return false;
+    if (cfg->chi < 1 || cfg->chi > 160) return false;
+    if (cfg->precision != CTM_FP64) return false;
+    long long n = (long long)cfg->chi * cfg->D * cfg->D;
+    if (n > 20000) return false;
+    return true;
+}
+
+#define CK(expr)                                          \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return CTM_ECUDA;          \
+    } while (0)
+
+// ---------------------------------------------------------------- enlarged corner
+// Fig. 3(c): X'[a][b][u][l] = sum_{g,h} T[a,u,g] C[g,h] T[b,l,h];
+// Y1[(a,b)][z] = sum_{u,l} X' aB[u,l,z]; M[(a,y)][(b,x)] = sum_z Y1 aA[z,x,y].
+int enqueue_enlarged_corner(ctm_ctx *c)
+{
+    const int chi = c->chi, D2 = c->D2;
+    const long long n = c->n;
+    cudaStream_t st = c->stream;
+    GemmF64 g;
+    // W = T C
+    g = GemmF64{(int)n, chi, chi, c->T, idx_lin(chi), idx_lin(1), c->C, idx_lin(chi), idx_lin(1),
+                c->W, idx_lin(chi), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // X'[a][b][u][l] = W[(a,u),h] T[(b,l),h]
+    g = GemmF64{(int)n, (int)n, chi, c->W, idx_lin(chi), idx_lin(1), c->T, idx_lin(1), idx_lin(chi),
+                c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // Y1 = X' a   (chi^2 x D2^2) (D2^2 x D2)
+    g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
+                idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // M[(a,y)][(b,x)] = Y1[(a,b), z] a[z, (x,y)]
+    g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
+                idx_lin(1), c->M, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    return CTM_OK;
+}
+
+// Fig. 3(d): Y = M Qs, Qs = Q diag(sgn C_jj); Householder QR -> Qout, R.
+int enqueue_projector(ctm_ctx *c, double *Qout)
+{
+    const int chi = c->chi;
+    const long long n = c->n;
+    cudaStream_t st = c->stream;
+    CK(launch_warm_start((int)n, chi, c->Q, c->C, c->Qs, st));
+    GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
+              c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err};
+    CK(qr_householder((int)n, chi, c->Y, Qout, c->R, qs, st));
+    return CTM_OK;
+}
+
+// Fig. 3(a): Cout = sym(Qp^T M Qp) / |.|_F.
+int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout)
+{
+    const int chi = c->chi;
+    const long long n = c->n;
+    cudaStream_t st = c->stream;
+    GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), Qp, idx_lin(chi), idx_lin(1),
+              c->MQ, idx_lin(chi), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
+                c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(launch_corner_sym_normalize(chi, c->Cr, Cout, st));
+    return CTM_OK;
+}
+
+// Fig. 3(b): T'[i,x,j] = sum Q[(a,y),i] T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j], normalised.
+int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
+{
+    const int chi = c->chi, D2 = c->D2;
+    const long long n = c->n;
+    cudaStream_t st = c->stream;
+    GemmF64 g;
+    // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]
+    g = GemmF64{(int)n, (int)n, chi, c->T, idx_lin(chi), idx_lin(1), Qp, idx_lin(n), idx_lin(1),
+                c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(chi, 1, (long long)D2 * D2), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
+    g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
+                idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // H3'[a][y][x][j] = H2[(a,j),z] a[z,(x,y)]
+    g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
+                idx_lin(1), c->H, idx_split(chi, (long long)D2 * D2 * chi, 1), idx_split(D2, chi, (long long)D2 * chi),
+                1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // T'[i][(x,j)] = sum_{(a,y)} Q[(a,y),i] H3'[(a,y),(x,j)]
+    g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),
+                Tout, idx_lin(n), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(launch_normalize((long long)chi * D2 * chi, Tout, c->norm_part, NORM_BLOCKS, st));
+    return CTM_OK;
+}
+
+int enqueue_step(ctm_ctx *c)
+{
+    int rc;
+    cudaStream_t st = c->stream;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
+    if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
+    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
+    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, nullptr, st));
+    CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
+    return CTM_OK;
+}
+
+// One step with CUDA events between its phases (same launches as enqueue_step).
+int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
+{
+    int rc;
+    cudaStream_t st = c->stream;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    CK(cudaEventRecord(ev[0], st));
+    if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
+    CK(cudaEventRecord(ev[1], st));
+    CK(launch_warm_start((int)n, (int)chi, c->Q, c->C, c->Qs, st));
+    {
+        GemmF64 g{(int)n, (int)chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
+                  c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
+        CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    }
+    CK(cudaEventRecord(ev[2], st));
+    {
+        QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err};
+        CK(qr_householder((int)n, (int)chi, c->Y, c->Qn, c->R, qs, st));
+    }
+    CK(cudaEventRecord(ev[3], st));
+    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    CK(cudaEventRecord(ev[4], st));
+    if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
+    CK(cudaEventRecord(ev[5], st));
+    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, nullptr, st));
+    CK(cudaEventRecord(ev[6], st));
+    CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(ev[7], st));
+    return CTM_OK;
+}
+
+int read_status(ctm_ctx *c)
+{
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (err) return CTM_ETIMEOUT;
+    return CTM_OK;
+}
+
+int check_env_finite(ctm_ctx *c)
+{
+    cudaStream_t st = c->stream;
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+    CK(launch_check_finite((long long)c->chi * c->chi, c->C, c->flag, st));
+    CK(launch_check_finite((long long)c->chi * c->D2 * c->chi, c->T, c->flag, st));
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return f ? CTM_ENONFINITE : CTM_OK;
+}
+
+int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int *steps_out, double *delta_out)
+{
+    if (c->graph && c->graph_steps != check_every) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (!c->graph && !c->graph_failed) {
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = CTM_OK;
+        for (int i = 0; i < check_every && rc == CTM_OK; ++i) rc = enqueue_step(c);
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (rc != CTM_OK || e != cudaSuccess || !c->graph) {
+            // capture unsupported for some launch: replay eagerly instead
+            cudaGetLastError();
+            c->graph = nullptr;
+            c->graph_failed = 1;
+        } else {
+            c->graph_steps = check_every;
+        }
+    }
+    int done = 0;
+    double delta = INFINITY;
+    while (done < max_steps) {
+        int chunk = check_every;
+        if (done + chunk > max_steps) chunk = max_steps - done;
+        if (c->graph && chunk == c->graph_steps) {
+            CK(cudaGraphLaunch(c->graph, c->stream));
+        } else {
+            for (int i = 0; i < chunk; ++i) {
+                int rc = enqueue_step(c);
+                if (rc != CTM_OK) return rc;
+            }
+        }
+        done += chunk;
+        c->steps_done += chunk;
+        CK(cudaMemcpyAsync(&delta, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        int rc = read_status(c);
+        if (rc != CTM_OK) return rc;
+        if (!isfinite(delta)) return CTM_ENONFINITE;
+        if (delta < tol) break;
+    }
+    if (steps_out) *steps_out = done;
+    if (delta_out) *delta_out = delta;
+    int rc = check_env_finite(c);
+    if (rc != CTM_OK) return rc;
+    return (delta < tol) ? CTM_OK : CTM_ENOTCONVERGED;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ctm_workspace_bytes(const ctm_config *cfg)
+{
+    if (!config_ok(cfg)) return 0;
+    ctm_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.cfg = *cfg;
+    c.d = cfg->d;
+    c.D = cfg->D;
+    c.D2 = cfg->D * cfg->D;
+    c.chi = cfg->chi;
+    c.n = (long long)c.chi * c.D2;
+    return layout(&c, nullptr);
+}
+
+int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t ws_bytes, void *stream,
+             ctm_ctx **out)
+{
+    if (!out) return CTM_EINVAL;
+    *out = nullptr;
+    if (!cfg || !A_dev || !workspace) return CTM_EINVAL;
+    if (cfg->precision != CTM_FP64) return CTM_EUNSUPPORTED;
+    if (!config_ok(cfg)) return CTM_EINVAL;
+    if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
+    ctm_ctx *c = new (std::nothrow) ctm_ctx;
+    if (!c) return CTM_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->cfg = *cfg;
+    c->d = cfg->d;
+    c->D = cfg->D;
+    c->D2 = cfg->D * cfg->D;
+    c->chi = cfg->chi;
+    c->n = (long long)c->chi * c->D2;
+    c->stream = (cudaStream_t)stream;
+    if (!qr_supported((int)c->n, c->chi)) {
+        delete c;
+        return CTM_EUNSUPPORTED;
+    }
+    size_t need = layout(c, nullptr);
+    if (ws_bytes < need) {
+        delete c;
+        return CTM_ENOMEM;
+    }
+    layout(c, (char *)workspace);
+    cudaStream_t st = c->stream;
+    int rc = CTM_OK;
+    do {
+        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
+        if (cudaMemsetAsync(c->err, 0, sizeof(int), st) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (launch_c3v_project_normalize(c->d, c->D, A_dev, c->A, cfg->symmetrize ? 1 : 0, st) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
+        if (launch_double_layer(c->d, c->D, c->A, c->A, c->a, st) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (launch_init_env(c->chi, c->D, c->a, c->C, c->T, c->Q, st) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (launch_spectrum_init(c->chi, c->s, st) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (cudaMemsetAsync(c->flag, 0, sizeof(int), st) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (launch_check_finite((long long)c->d * c->D * c->D * c->D, c->A, c->flag, st) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
+        int f = 0;
+        if (cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
+        if (f) rc = CTM_ENONFINITE;
+    } while (0);
+    if (rc != CTM_OK) {
+        ctm_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return CTM_OK;
+}
+
+int ctm_step(ctm_ctx *c, int nsteps, double *delta_host)
+{
+    if (!c || nsteps < 0) return CTM_EINVAL;
+    for (int i = 0; i < nsteps; ++i) {
+        int rc = enqueue_step(c);
+        if (rc != CTM_OK) return rc;
+        c->steps_done++;
+    }
+    if (delta_host) {
+        CK(cudaMemcpyAsync(delta_host, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        int rc = read_status(c);
+        if (rc != CTM_OK) return rc;
+        if (!isfinite(*delta_host)) return CTM_ENONFINITE;
+        return check_env_finite(c);
+    }
+    return CTM_OK;
+}
+
+int ctm_converge(ctm_ctx *c, int max_steps, double tol, int check_every, int *steps_out, double *delta_out)
+{
+    if (!c) return CTM_EINVAL;
+    if (max_steps <= 0) max_steps = c->cfg.max_steps;
+    if (tol <= 0.0) tol = c->cfg.tol;
+    if (check_every < 1) check_every = 1;
+    if (max_steps <= 0) return CTM_EINVAL;
+    // work is replayed on the private stream, ordered after the caller's stream
+    cudaStream_t user = c->stream;
+    CK(cudaEventRecord(c->ev_in, user));
+    CK(cudaStreamWaitEvent(c->own, c->ev_in, 0));
+    c->stream = c->own;
+    int rc = converge_on_own(c, max_steps, tol, check_every, steps_out, delta_out);
+    c->stream = user;
+    if (cudaEventRecord(c->ev_out, c->own) != cudaSuccess) return CTM_ECUDA;
+    if (cudaStreamWaitEvent(user, c->ev_out, 0) != cudaSuccess) return CTM_ECUDA;
+    return rc;
+}
+
+int ctm_energy(ctm_ctx *c, const double *h_dev, double *e_bond_host, double *e_site_host, double *rho_host)
+{
+    if (!c || !h_dev) return CTM_EINVAL;
+    const int chi = c->chi, D2 = c->D2, d = c->d, dd = d * d;
+    const long long n = c->n;
+    cudaStream_t st = c->stream;
+    int rc;
+    if (dd > RHO_MAX_DD) return CTM_EUNSUPPORTED;
+    // projector of one more step and Ch = sym(Q^T M Q)/|.|
+    if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
+    if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
+    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    // P5 = Ch^5
+    GemmF64 g;
+    const double *src = c->Cn;
+    double *bufs[2] = {c->P5a, c->P5b};
+    for (int p = 0; p < 4; ++p) {
+        double *dst = bufs[p & 1];
+        g = GemmF64{chi, chi, chi, src, idx_lin(chi), idx_lin(1), c->Cn, idx_lin(chi), idx_lin(1), dst,
+                    idx_lin(chi), idx_lin(1), 1.0, 0.0};
+        CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+        src = dst;
+    }
+    // E = Q P5 Q^T  (n x n, symmetric) into H
+    g = GemmF64{(int)n, chi, chi, c->Qn, idx_lin(chi), idx_lin(1), src, idx_lin(chi), idx_lin(1), c->W,
+                idx_lin(chi), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    g = GemmF64{(int)n, (int)n, chi, c->W, idx_lin(chi), idx_lin(1), c->Qn, idx_lin(1), idx_lin(chi), c->H,
+                idx_lin(n), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // open layers b[p][..] = A[s] (x) A[t], p = s*d + t
+    CK(launch_open_layers(d, c->D, c->A, c->b, st));
+    const long long D3 = (long long)D2 * D2 * D2;
+    // Y1o[(a,b)][(pB,z)] = sum_{u,l} X'[(a,b),(u,l)] b[pB][u][l][z]
+    g = GemmF64{chi * chi, dd * D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->b, idx_lin(D2),
+                idx_split(D2, D3, 1), c->Y1o, idx_lin((long long)dd * D2), idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    // G2[(a,b)][(pA,z)] = sum_{x,y} E[(a,y),(b,x)] b[pA][z][x][y]
+    g = GemmF64{chi * chi, dd * D2, D2 * D2, c->H, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n),
+                c->b, idx_lin(1), idx_split(D2, D3, (long long)D2 * D2), c->G2, idx_lin((long long)dd * D2),
+                idx_lin(1), 1.0, 0.0};
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CTM_COUNT_LAUNCH(1);
+    rho_partial_kernel<<<RHO_BLOCKS, 256, 0, st>>>((long long)chi * chi, dd, D2, c->Y1o, c->G2, c->rho_part);
+    CK(cudaGetLastError());
+    CTM_COUNT_LAUNCH(1);
+    rho_final_kernel<<<1, 128, 0, st>>>(RHO_BLOCKS, dd, c->rho_part, c->rho_raw);
+    CK(cudaGetLastError());
+    CK(launch_bond_energy(d, c->rho_raw, h_dev, c->eout, st));
+    double host[4 + RHO_MAX_DD * RHO_MAX_DD];
+    CK(cudaMemcpyAsync(host, c->eout, sizeof(double) * (4 + dd * dd), cudaMemcpyDeviceToHost, st));
+    if ((rc = read_status(c)) != CTM_OK) return rc;
+    for (int i = 0; i < 4 + dd * dd; ++i)
+        if (!isfinite(host[i])) return CTM_ENONFINITE;
+    if (e_bond_host)
+        for (int i = 0; i < 3; ++i) e_bond_host[i] = host[i];
+    if (e_site_host) *e_site_host = host[3];
+    if (rho_host)
+        for (int i = 0; i < dd * dd; ++i) rho_host[i] = host[4 + i];
+    return CTM_OK;
+}
+
+int ctm_get_env(const ctm_ctx *c, double *C_dev, double *T_dev, double *Q_dev)
+{
+    if (!c) return CTM_EINVAL;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    if (C_dev) CK(cudaMemcpyAsync(C_dev, c->C, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, c->stream));
+    if (T_dev)
+        CK(cudaMemcpyAsync(T_dev, c->T, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, c->stream));
+    if (Q_dev) CK(cudaMemcpyAsync(Q_dev, c->Q, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CTM_OK;
+}
+
+int ctm_set_env(ctm_ctx *c, const double *C_dev, const double *T_dev, const double *Q_dev)
+{
+    if (!c || !C_dev || !T_dev || !Q_dev) return CTM_EINVAL;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    cudaStream_t st = c->stream;
+    CK(cudaMemcpyAsync(c->C, C_dev, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->T, T_dev, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(c->Q, Q_dev, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
+    // the spectrum of the new corner becomes the reference for the next delta
+    CK(launch_spectrum((int)chi, c->C, c->s, c->s, c->delta, nullptr, st));
+    CK(cudaStreamSynchronize(st));
+    return CTM_OK;
+}
+
+int ctm_get_intermediate(const ctm_ctx *c, int which, double *dst, size_t count)
+{
+    if (!c || !dst) return CTM_EINVAL;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    const double *src = nullptr;
+    size_t cnt = 0;
+    switch (which) {
+    case 0: src = c->M; cnt = (size_t)(n * n); break;
+    case 1: src = c->Y; cnt = (size_t)(n * chi); break;
+    case 2: src = c->R; cnt = (size_t)(chi * chi); break;
+    case 3: src = c->Q; cnt = (size_t)(n * chi); break;
+    case 4: src = c->s; cnt = (size_t)chi; break;
+    case 5: src = c->A; cnt = (size_t)c->d * c->D * c->D * c->D; break;
+    case 6: src = c->a; cnt = (size_t)(D2 * D2 * D2); break;
+    default: return CTM_EINVAL;
+    }
+    if (count < cnt) return CTM_EINVAL;
+    CK(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return CTM_OK;
+}
+
+void ctm_destroy(ctm_ctx *c)
+{
+    if (!c) return;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->own) {
+        cudaStreamSynchronize(c->own);
+        cudaStreamDestroy(c->own);
+    }
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    delete c;
+}
+
+const char *ctm_status_str(int s)
+{
+    switch (s) {
+    case CTM_OK: return "CTM_OK";
+    case CTM_EINVAL: return "CTM_EINVAL: invalid argument";
+    case CTM_ENOMEM: return "CTM_ENOMEM: workspace too small";
+    case CTM_ECUDA: return "CTM_ECUDA: CUDA runtime error";
+    case CTM_ENOTCONVERGED: return "CTM_ENOTCONVERGED: step limit reached";
+    case CTM_ENONFINITE: return "CTM_ENONFINITE: NaN or Inf";
+    case CTM_ETIMEOUT: return "CTM_ETIMEOUT: bounded device wait expired";
+    case CTM_EUNSUPPORTED: return "CTM_EUNSUPPORTED: unsupported shape or mode";
+    default: return "unknown status";
+    }
+}
+
+int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
+{
+    if (!c || !phase_ms || nphase < 7) return CTM_EINVAL;
+    cudaEvent_t ev[8];
+    for (int i = 0; i < 8; ++i)
+        if (cudaEventCreate(&ev[i]) != cudaSuccess) return CTM_ECUDA;
+    int rc = enqueue_step_profiled(c, ev);
+    if (rc == CTM_OK) {
+        c->steps_done++;
+        if (cudaEventSynchronize(ev[7]) != cudaSuccess) rc = CTM_ECUDA;
+    }
+    if (rc == CTM_OK) rc = read_status(c);
+    if (rc == CTM_OK)
+        for (int i = 0; i < 7; ++i) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess) rc = CTM_ECUDA;
+            phase_ms[i] = ms;
+        }
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+    return rc;
+}
+
+unsigned long long ctm_kernel_launches(void) { return g_ctm_launches; }
+
+const char *ctm_version(void) { return "libctm sm_103a fp64"; }
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Internal declarations shared by the libctm translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "../../include/ctm.h"
+
+// Two-level index map: off(i) = (i / div) * s1 + (i % div) * s2.  A plain
+// strided dimension is {div = 1 << 30, s1 = 0, s2 = stride}.  All tensor
+// contractions of the step are GEMMs whose operands and outputs are 4-index
+// tensors; splitting each GEMM dimension into two indices lets one kernel read
+// and write every permuted layout directly.
+struct Idx2 {
+    int div;
+    long long s1, s2;
+};
+
+static inline Idx2 idx_lin(long long stride) { return Idx2{1 << 30, 0, stride}; }
+static inline Idx2 idx_split(int div, long long s_hi, long long s_lo) { return Idx2{div, s_hi, s_lo}; }
+
+// C(m,n) = alpha * sum_k A(m,k) B(k,n) + beta * C(m,n), FP64.
+struct GemmF64 {
+    int M, N, K;
+    const double *A;
+    Idx2 Am, Ak;
+    const double *B;
+    Idx2 Bk, Bn;
+    double *C;
+    Idx2 Cm, Cn;
+    double alpha, beta;
+};
+
+// Launch a FP64 GEMM; split-K (ksplit > 1) uses `scratch` (>= ksplit*M*N doubles).
+cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st);
+// Number of K-splits gemm_f64 picks for this shape (1 = none) and the scratch it needs.
+int gemm_f64_pick_split(int M, int N, int K);
+
+// ---------------------------------------------------------------- QR
+// Householder QR of Y (n x k row-major, n >= k) with diag(R) >= 0.  Q (n x k)
+// and R (k x k) row-major.  One cooperative launch: factorisation, backward
+// accumulation of Q = H_0 ... H_{k-1} [I;0] and the sign gauge.
+struct QrScratch {
+    double *sbuf;      // 3 * k
+    double *rowbuf;    // 2 * k
+    unsigned *bar;     // 2 (count, generation)
+    int *err;          // 1
+};
+size_t qr_scratch_doubles(int k);
+cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,
+                           cudaStream_t st);
+int qr_supported(int n, int k);
+
+// ---------------------------------------------------------------- small kernels
+cudaError_t launch_c3v_project_normalize(int d, int D, const double *Ain, double *Aout, int symmetrize,
+                                         cudaStream_t st);
+cudaError_t launch_double_layer(int d, int D, const double *K, const double *B, double *a, cudaStream_t st);
+cudaError_t launch_init_env(int chi, int D, const double *a, double *C, double *T, double *Q, cudaStream_t st);
+cudaError_t launch_warm_start(int n, int chi, const double *Q, const double *C, double *Qs, cudaStream_t st);
+cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, cudaStream_t st);
+cudaError_t launch_normalize(long long count, double *x, double *partials, int nblocks, cudaStream_t st);
+cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
+                            double *work, cudaStream_t st);
+cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st);
+cudaError_t launch_bond_energy(int d, const double *rho_raw, const double *h, double *out, cudaStream_t st);
+cudaError_t launch_open_layers(int d, int D, const double *A, double *b, cudaStream_t st);
+cudaError_t launch_check_finite(long long count, const double *x, int *flag, cudaStream_t st);
+size_t spectrum_work_doubles(int chi);
+
+int device_sm_count();
+// Host-side count of kernel launches the library has enqueued (graph replays excluded).
+extern unsigned long long g_ctm_launches;
+#define CTM_COUNT_LAUNCH(nl) (g_ctm_launches += (unsigned long long)(nl))
+cudaError_t qr_prepare();
+cudaError_t spectrum_prepare();

@@ -1,0 +1,187 @@
+// FP64 tensor-contraction GEMM for the plain-precision CTMRG step.
+//
+// Every contraction of the step (enlarged corner, Sec. II.B Fig. 3c; reduced
+// corner and corner renormalisation, Fig. 3a,d; edge renormalisation,
+// Fig. 3b) is a GEMM over fused tensor indices.  Operands and outputs are
+// addressed through two-level index maps (Idx2) so that the permuted 4-index
+// layouts are read and written in place, with no transpose kernels.
+//
+// Tile: 64 x 64 outputs per 256-thread CTA, 4 x 4 per thread (strided by 16
+// so a warp's shared-memory reads are conflict-free), K staged 16 at a time
+// through shared memory with a register prefetch of the next K tile.
+#include "ctm_internal.h"
+
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
+
+__device__ __forceinline__ long long off2(const Idx2 &x, int i)
+{
+    int hi = i / x.div;
+    int lo = i - hi * x.div;
+    return (long long)hi * x.s1 + (long long)lo * x.s2;
+}
+
+// When the K map has unit stride the A tile is fetched K-fastest, otherwise
+// M-fastest (and N-fastest / K-fastest for B), so consecutive threads touch
+// consecutive addresses whenever the layout allows it.
+__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int a_kfast, int b_nfast, int kchunk,
+                                                      double *partial)
+{
+    __shared__ double As[BK][BM + 1];
+    __shared__ double Bs[BK][BN + 1];
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(g.K, kbeg + kchunk);
+
+    double acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+
+    double ra[4], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int lin = tid + e * NT;   // 0..1023 over the 64 x 16 tile
+            int mm, kk;
+            if (a_kfast) { kk = lin & 15; mm = lin >> 4; }
+            else { mm = lin & 63; kk = lin >> 6; }
+            int m = m0 + mm, k = k0 + kk;
+            ra[e] = (m < g.M && k < kend) ? g.A[off2(g.Am, m) + off2(g.Ak, k)] : 0.0;
+            int nn, kb;
+            if (b_nfast) { nn = lin & 63; kb = lin >> 6; }
+            else { kb = lin & 15; nn = lin >> 4; }
+            int n = n0 + nn, k2 = k0 + kb;
+            rb[e] = (n < g.N && k2 < kend) ? g.B[off2(g.Bk, k2) + off2(g.Bn, n)] : 0.0;
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            int lin = tid + e * NT;
+            int mm, kk;
+            if (a_kfast) { kk = lin & 15; mm = lin >> 4; }
+            else { mm = lin & 63; kk = lin >> 6; }
+            As[kk][mm] = ra[e];
+            int nn, kb;
+            if (b_nfast) { nn = lin & 63; kb = lin >> 6; }
+            else { kb = lin & 15; nn = lin >> 4; }
+            Bs[kb][nn] = rb[e];
+        }
+    };
+
+    if (kbeg < kend) fetch(kbeg);
+    for (int k0 = kbeg; k0 < kend; k0 += BK) {
+        __syncthreads();
+        stash();
+        __syncthreads();
+        if (k0 + BK < kend) fetch(k0 + BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+    }
+
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        int m = m0 + ty + 16 * i;
+        if (m >= g.M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int n = n0 + tx + 16 * j;
+            if (n >= g.N) continue;
+            if (partial) {
+                partial[((size_t)blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
+            } else {
+                long long o = off2(g.Cm, m) + off2(g.Cn, n);
+                double v = g.alpha * acc[i][j];
+                if (g.beta != 0.0) v += g.beta * g.C[o];
+                g.C[o] = v;
+            }
+        }
+    }
+}
+
+// Deterministic split-K reduction: fixed summation order over the splits.
+__global__ void splitk_reduce_kernel(GemmF64 g, int ksplit, const double *partial)
+{
+    long long total = (long long)g.M * g.N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int z = 0; z < ksplit; ++z) s += partial[(size_t)z * total + t];
+        int m = (int)(t / g.N), n = (int)(t - (long long)m * g.N);
+        long long o = off2(g.Cm, m) + off2(g.Cn, n);
+        double v = g.alpha * s;
+        if (g.beta != 0.0) v += g.beta * g.C[o];
+        g.C[o] = v;
+    }
+}
+
+}  // namespace
+
+unsigned long long g_ctm_launches = 0;
+
+int device_sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+int gemm_f64_pick_split(int M, int N, int K)
+{
+    long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    long long want = 2LL * device_sm_count();
+    if (tiles >= want || K < 4 * BK) return 1;
+    long long s = (want + tiles - 1) / tiles;
+    long long maxs = K / (2 * BK);
+    if (s > maxs) s = maxs;
+    if (s > 64) s = 64;
+    return s < 1 ? 1 : (int)s;
+}
+
+cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)
+{
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    int a_kfast = (g.Ak.s2 == 1 && g.Ak.div >= g.K) ? 1 : 0;
+    int b_nfast = (g.Bn.s2 == 1 && g.Bn.div >= g.N) ? 1 : 0;
+    if (ksplit < 1 || !scratch) ksplit = 1;
+    int kchunk = (g.K + ksplit - 1) / ksplit;
+    kchunk = ((kchunk + BK - 1) / BK) * BK;
+    if (kchunk <= 0) kchunk = BK;
+    ksplit = (g.K + kchunk - 1) / kchunk;
+    if (ksplit < 1) ksplit = 1;
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ksplit);
+    if (ksplit == 1) {
+        CTM_COUNT_LAUNCH(1);
+        gemm_f64_kernel<<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, nullptr);
+        return cudaGetLastError();
+    }
+    CTM_COUNT_LAUNCH(2);
+    gemm_f64_kernel<<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, scratch);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    long long total = (long long)g.M * g.N;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 4 * device_sm_count()) blocks = 4 * device_sm_count();
+    splitk_reduce_kernel<<<blocks, 256, 0, st>>>(g, ksplit, scratch);
+    return cudaGetLastError();
+}

@@ -1,0 +1,443 @@
+// Bandwidth- and latency-bound kernels of the CTMRG step: C3v projection and
+// double layer (Sec. II.A, App. A, Fig. 1b), environment initialisation,
+// warm start of the reduced corner, corner re-symmetrisation and
+// normalisation (Fig. 3a), edge normalisation, the corner-spectrum
+// convergence test, and the final bond-energy contraction (Eq. 1, Eq. 4).
+// All FP64.
+#include <math.h>
+
+#include "ctm_internal.h"
+
+namespace {
+
+__device__ __forceinline__ double block_sum(double v, double *red)
+{
+    // 256-thread reduction through shared memory (red: >= 32 doubles)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    int nw = (blockDim.x + 31) >> 5;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    __syncthreads();
+    return s;
+}
+
+// a0: A_sym = (1/6) sum over the six permutations of the virtual legs, then
+// unit Frobenius norm.  One CTA; the tensor is at most a few thousand entries.
+__global__ void c3v_project_kernel(int d, int D, const double *Ain, double *Aout, int symmetrize)
+{
+    extern __shared__ double sA[];
+    __shared__ double red[32];
+    const int D3 = D * D * D, tot = d * D3;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) {
+        int s = t / D3, r = t % D3;
+        int i = r / (D * D), j = (r / D) % D, k = r % D;
+        const double *As = Ain + (size_t)s * D3;
+        double v;
+        if (symmetrize)
+            v = (As[(i * D + j) * D + k] + As[(i * D + k) * D + j] + As[(j * D + i) * D + k] +
+                 As[(j * D + k) * D + i] + As[(k * D + i) * D + j] + As[(k * D + j) * D + i]) / 6.0;
+        else
+            v = As[r];
+        sA[t] = v;
+    }
+    __syncthreads();
+    double ss = 0.0;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) ss += sA[t] * sA[t];
+    ss = block_sum(ss, red);
+    double f = (symmetrize && ss > 0.0) ? 1.0 / sqrt(ss) : 1.0;
+    for (int t = threadIdx.x; t < tot; t += blockDim.x) Aout[t] = sA[t] * f;
+}
+
+// a1: a[(ii')][(jj')][(kk')] = sum_s K[s,i,j,k] B[s,i',j',k'].
+__global__ void double_layer_kernel(int d, int D, const double *K, const double *B, double *a)
+{
+    const int D2 = D * D, D3 = D * D * D;
+    const long long tot = (long long)D2 * D2 * D2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int u = (int)(t / (D2 * D2)), v = (int)((t / D2) % D2), w = (int)(t % D2);
+        int i = u / D, i2 = u % D, j = v / D, j2 = v % D, k = w / D, k2 = w % D;
+        double s = 0.0;
+        for (int p = 0; p < d; ++p)
+            s = fma(K[(size_t)p * D3 + (i * D + j) * D + k], B[(size_t)p * D3 + (i2 * D + j2) * D + k2], s);
+        a[t] = s;
+    }
+}
+
+// Open layers for the bond-energy contraction: b[(s,t)][u][v][w] = A[s]... (x) A[t]...
+__global__ void open_layers_kernel(int d, int D, const double *A, double *b)
+{
+    const int D2 = D * D, D3 = D * D * D;
+    const long long per = (long long)D2 * D2 * D2;
+    const long long tot = per * d * d;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        int p = (int)(t / per);
+        long long r = t - p * per;
+        int s = p / d, q = p % d;
+        int u = (int)(r / (D2 * D2)), v = (int)((r / D2) % D2), w = (int)(r % D2);
+        int i = u / D, i2 = u % D, j = v / D, j2 = v % D, k = w / D, k2 = w % D;
+        b[t] = A[(size_t)s * D3 + (i * D + j) * D + k] * A[(size_t)q * D3 + (i2 * D + j2) * D + k2];
+    }
+}
+
+// Initial environment: C = I, T[a][u][b] = delta_ab t_u, t_u = sum_{v,w} a[u][(vv)][(ww)],
+// Q = first chi columns of I_n.
+__global__ void init_env_kernel(int chi, int D, const double *a, double *C, double *T, double *Q)
+{
+    const int D2 = D * D;
+    const long long n = (long long)chi * D2;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long t = tid; t < (long long)chi * chi; t += stride) C[t] = ((t / chi) == (t % chi)) ? 1.0 : 0.0;
+    for (long long t = tid; t < n * chi; t += stride) Q[t] = ((t / chi) == (t % chi)) ? 1.0 : 0.0;
+    for (long long t = tid; t < (long long)chi * D2 * chi; t += stride) {
+        int al = (int)(t / ((long long)D2 * chi));
+        int u = (int)((t / chi) % D2);
+        int be = (int)(t % chi);
+        double v = 0.0;
+        if (al == be)
+            for (int p = 0; p < D; ++p)
+                for (int q = 0; q < D; ++q) v += a[((size_t)u * D2 + p * D + p) * D2 + q * D + q];
+        T[t] = v;
+    }
+}
+
+// Reduced-corner warm start: Qs = Q diag(sgn C_jj), sgn(0) = +1.
+__global__ void warm_start_kernel(long long n, int chi, const double *Q, const double *C, double *Qs)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * chi;
+         t += (long long)gridDim.x * blockDim.x) {
+        int j = (int)(t % chi);
+        double v = Q[t];
+        Qs[t] = (C[(size_t)j * chi + j] < 0.0) ? -v : v;
+    }
+}
+
+// a5 tail: C' = (Cr + Cr^T)/2, then unit Frobenius norm.  One CTA.
+__global__ void corner_sym_norm_kernel(int chi, const double *Cr, double *Cn)
+{
+    __shared__ double red[32];
+    double ss = 0.0;
+    for (int t = threadIdx.x; t < chi * chi; t += blockDim.x) {
+        int i = t / chi, j = t % chi;
+        double v = 0.5 * (Cr[t] + Cr[(size_t)j * chi + i]);
+        ss += v * v;
+    }
+    ss = block_sum(ss, red);
+    double f = ss > 0.0 ? 1.0 / sqrt(ss) : 1.0;
+    for (int t = threadIdx.x; t < chi * chi; t += blockDim.x) {
+        int i = t / chi, j = t % chi;
+        Cn[t] = 0.5 * (Cr[t] + Cr[(size_t)j * chi + i]) * f;
+    }
+}
+
+// Frobenius normalisation of a large array: per-block partial sums of squares...
+__global__ void sumsq_partial_kernel(long long count, const double *x, double *partials)
+{
+    __shared__ double red[32];
+    double s = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        s = fma(x[t], x[t], s);
+    s = block_sum(s, red);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// ... then every block re-sums the partials in the same order and scales its share.
+__global__ void scale_by_partials_kernel(long long count, double *x, const double *partials, int np)
+{
+    __shared__ double f;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += partials[i];
+        f = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    }
+    __syncthreads();
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        x[t] *= f;
+}
+
+// a7: corner spectrum and delta.  One CTA: Householder tridiagonalisation of the
+// symmetric corner in shared memory, Sturm-count bisection for every
+// eigenvalue (one thread each), |lambda| sorted descending by rank, unit
+// 2-norm, delta = |s_new - s_old|_2.
+__global__ void spectrum_kernel(int chi, const double *C, double *s_new, const double *s_old, double *delta)
+{
+    extern __shared__ double sm[];
+    __shared__ double red[32];
+    __shared__ double sh_beta, sh_alpha, sh_K;
+    __shared__ int sh_skip;
+    double *A = sm;                      // chi x chi
+    double *v = A + chi * chi;           // chi
+    double *p = v + chi;                 // chi
+    double *dg = p + chi;                // chi
+    double *e2 = dg + chi;               // chi
+    double *lam = e2 + chi;              // chi
+    const int tid = threadIdx.x;
+    for (int t = tid; t < chi * chi; t += blockDim.x) {
+        int i = t / chi, j = t % chi;
+        A[t] = 0.5 * (C[t] + C[(size_t)j * chi + i]);
+    }
+    __syncthreads();
+    for (int kc = 0; kc + 2 < chi; ++kc) {
+        const int b0 = kc + 1, m = chi - b0;
+        double part = 0.0;
+        for (int i = 1 + tid; i < m; i += blockDim.x) part += A[(b0 + i) * chi + kc] * A[(b0 + i) * chi + kc];
+        double tail = block_sum(part, red);
+        if (tid == 0) {
+            double x0 = A[b0 * chi + kc];
+            sh_skip = (tail == 0.0);
+            double nrm = sqrt(tail + x0 * x0);
+            double alpha = (x0 >= 0.0) ? -nrm : nrm;
+            sh_alpha = alpha;
+            sh_beta = (tail == 0.0) ? 0.0 : 1.0 / (nrm * (nrm + fabs(x0)));
+            v[0] = x0 - alpha;
+        }
+        __syncthreads();
+        if (sh_skip) continue;
+        for (int i = 1 + tid; i < m; i += blockDim.x) v[i] = A[(b0 + i) * chi + kc];
+        __syncthreads();
+        const double beta = sh_beta;
+        for (int i = tid; i < m; i += blockDim.x) {
+            double s = 0.0;
+            for (int j = 0; j < m; ++j) s = fma(A[(b0 + i) * chi + b0 + j], v[j], s);
+            p[i] = beta * s;
+        }
+        __syncthreads();
+        double pv = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) pv += p[i] * v[i];
+        pv = block_sum(pv, red);
+        const double Kf = 0.5 * beta * pv;
+        for (int i = tid; i < m; i += blockDim.x) p[i] -= Kf * v[i];   // p <- w
+        __syncthreads();
+        for (int t = tid; t < m * m; t += blockDim.x) {
+            int i = t / m, j = t % m;
+            A[(b0 + i) * chi + b0 + j] -= v[i] * p[j] + p[i] * v[j];
+        }
+        if (tid == 0) {
+            A[b0 * chi + kc] = sh_alpha;
+            A[kc * chi + b0] = sh_alpha;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < chi; i += blockDim.x) {
+        dg[i] = A[i * chi + i];
+        double e = (i + 1 < chi) ? A[(i + 1) * chi + i] : 0.0;
+        e2[i] = e * e;
+    }
+    __syncthreads();
+    // Gershgorin bounds
+    double lo_l = 1e300, hi_l = -1e300;
+    for (int i = tid; i < chi; i += blockDim.x) {
+        double r = sqrt(e2[i]) + (i > 0 ? sqrt(e2[i - 1]) : 0.0);
+        lo_l = fmin(lo_l, dg[i] - r);
+        hi_l = fmax(hi_l, dg[i] + r);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo_l = fmin(lo_l, __shfl_down_sync(0xffffffffu, lo_l, o));
+        hi_l = fmax(hi_l, __shfl_down_sync(0xffffffffu, hi_l, o));
+    }
+    __shared__ double slo[32], shi[32];
+    if ((tid & 31) == 0) { slo[tid >> 5] = lo_l; shi[tid >> 5] = hi_l; }
+    __syncthreads();
+    double glo = slo[0], ghi = shi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { glo = fmin(glo, slo[w]); ghi = fmax(ghi, shi[w]); }
+    const double scale = fmax(fabs(glo), fabs(ghi));
+    const double pivmin = 1e-300 + scale * 1e-30;
+    for (int ei = tid; ei < chi; ei += blockDim.x) {
+        double lo = glo - 1e-12 * scale - 1e-300, hi = ghi + 1e-12 * scale + 1e-300;
+        for (int it = 0; it < 200; ++it) {
+            double mid = 0.5 * (lo + hi);
+            if (mid <= lo || mid >= hi || hi - lo <= 2e-16 * scale) break;
+            int cnt = 0;
+            double q = dg[0] - mid;
+            if (fabs(q) < pivmin) q = -pivmin;
+            cnt += (q < 0.0);
+            for (int j = 1; j < chi; ++j) {
+                q = dg[j] - mid - e2[j - 1] / q;
+                if (fabs(q) < pivmin) q = -pivmin;
+                cnt += (q < 0.0);
+            }
+            if (cnt <= ei) lo = mid;
+            else hi = mid;
+        }
+        lam[ei] = fabs(0.5 * (lo + hi));
+    }
+    __syncthreads();
+    double ss = 0.0;
+    for (int i = tid; i < chi; i += blockDim.x) ss += lam[i] * lam[i];
+    ss = block_sum(ss, red);
+    const double f = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+    for (int i = tid; i < chi; i += blockDim.x) {
+        double ai = lam[i];
+        int rank = 0;
+        for (int j = 0; j < chi; ++j) {
+            double aj = lam[j];
+            rank += (aj > ai) || (aj == ai && j < i);
+        }
+        p[rank] = ai * f;
+    }
+    __syncthreads();
+    double dd = 0.0;
+    for (int i = tid; i < chi; i += blockDim.x) {
+        double x = p[i] - s_old[i];
+        dd += x * x;
+        s_new[i] = p[i];
+    }
+    dd = block_sum(dd, red);
+    if (tid == 0) *delta = sqrt(dd);
+}
+
+__global__ void spectrum_init_kernel(int chi, double *s)
+{
+    for (int i = threadIdx.x; i < chi; i += blockDim.x) s[i] = 1.0 / sqrt((double)chi);
+}
+
+// Eq. (1): rho[(sA sB)][(tA tB)] = raw[(sB tB)][(sA tA)] / trace; e_a = tr(rho h_a);
+// E_site = (1/2) sum_a e_a.  out: e_x, e_y, e_z, E_site, then rho (d^4).
+__global__ void bond_energy_kernel(int d, const double *raw, const double *h, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int dd = d * d;
+    double z = 0.0;
+    for (int sA = 0; sA < d; ++sA)
+        for (int sB = 0; sB < d; ++sB) z += raw[(sB * d + sB) * dd + (sA * d + sA)];
+    double *rho = out + 4;
+    for (int sA = 0; sA < d; ++sA)
+        for (int sB = 0; sB < d; ++sB)
+            for (int tA = 0; tA < d; ++tA)
+                for (int tB = 0; tB < d; ++tB)
+                    rho[(sA * d + sB) * dd + tA * d + tB] = raw[(sB * d + tB) * dd + (sA * d + tA)] / z;
+    double es = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = 0.0;
+        for (int r = 0; r < dd; ++r)
+            for (int c = 0; c < dd; ++c) e += rho[r * dd + c] * h[(size_t)a * dd * dd + c * dd + r];
+        out[a] = e;
+        es += e;
+    }
+    out[3] = 0.5 * es;
+}
+
+__global__ void check_finite_kernel(long long count, const double *x, int *flag)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[t])) *flag = 1;
+}
+
+int grid_for(long long count, int per_sm = 8)
+{
+    long long b = (count + 255) / 256;
+    long long cap = (long long)per_sm * device_sm_count();
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_c3v_project_normalize(int d, int D, const double *Ain, double *Aout, int symmetrize,
+                                         cudaStream_t st)
+{
+    size_t smem = sizeof(double) * (size_t)d * D * D * D;
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(c3v_project_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    CTM_COUNT_LAUNCH(1);
+    c3v_project_kernel<<<1, 256, smem, st>>>(d, D, Ain, Aout, symmetrize);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_double_layer(int d, int D, const double *K, const double *B, double *a, cudaStream_t st)
+{
+    long long tot = (long long)D * D * D * D * D * D;
+    CTM_COUNT_LAUNCH(1);
+    double_layer_kernel<<<grid_for(tot), 256, 0, st>>>(d, D, K, B, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_open_layers(int d, int D, const double *A, double *b, cudaStream_t st)
+{
+    long long tot = (long long)D * D * D * D * D * D * d * d;
+    CTM_COUNT_LAUNCH(1);
+    open_layers_kernel<<<grid_for(tot), 256, 0, st>>>(d, D, A, b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_env(int chi, int D, const double *a, double *C, double *T, double *Q, cudaStream_t st)
+{
+    long long tot = (long long)chi * D * D * chi;
+    CTM_COUNT_LAUNCH(1);
+    init_env_kernel<<<grid_for(tot), 256, 0, st>>>(chi, D, a, C, T, Q);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warm_start(int n, int chi, const double *Q, const double *C, double *Qs, cudaStream_t st)
+{
+    CTM_COUNT_LAUNCH(1);
+    warm_start_kernel<<<grid_for((long long)n * chi), 256, 0, st>>>(n, chi, Q, C, Qs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, cudaStream_t st)
+{
+    CTM_COUNT_LAUNCH(1);
+    corner_sym_norm_kernel<<<1, 256, 0, st>>>(chi, Cr, Cn);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_normalize(long long count, double *x, double *partials, int nblocks, cudaStream_t st)
+{
+    CTM_COUNT_LAUNCH(1);
+    sumsq_partial_kernel<<<nblocks, 256, 0, st>>>(count, x, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    CTM_COUNT_LAUNCH(1);
+    scale_by_partials_kernel<<<nblocks, 256, 0, st>>>(count, x, partials, nblocks);
+    return cudaGetLastError();
+}
+
+size_t spectrum_work_doubles(int chi) { return (size_t)chi * chi + 5 * (size_t)chi; }
+
+cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
+                            double *work, cudaStream_t st)
+{
+    (void)work;
+    size_t smem = sizeof(double) * spectrum_work_doubles(chi);
+    if (smem > 200 * 1024) return cudaErrorInvalidValue;
+    CTM_COUNT_LAUNCH(1);
+    spectrum_kernel<<<1, 256, smem, st>>>(chi, C, s_new, s_old, delta);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st)
+{
+    CTM_COUNT_LAUNCH(1);
+    spectrum_init_kernel<<<1, 256, 0, st>>>(chi, s);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bond_energy(int d, const double *rho_raw, const double *h, double *out, cudaStream_t st)
+{
+    CTM_COUNT_LAUNCH(1);
+    bond_energy_kernel<<<1, 32, 0, st>>>(d, rho_raw, h, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_check_finite(long long count, const double *x, int *flag, cudaStream_t st)
+{
+    CTM_COUNT_LAUNCH(1);
+    check_finite_kernel<<<grid_for(count), 256, 0, st>>>(count, x, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t spectrum_prepare()
+{
+    return cudaFuncSetAttribute(spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}

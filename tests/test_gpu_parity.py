@@ -1,0 +1,221 @@
+"""GPU (libctm, FP64 path) against the FP64 CPU oracle, element by element.
+
+Every call goes through the C ABI (paper_2509_05090_gb300.binding).  Step
+parity feeds the oracle's own environment into one GPU step so rounding does
+not compound; trajectory parity runs whole converging iterations.
+
+Tolerances (FP64 throughout; both sides sum the same products in different
+orders, so differences are a few ulps times the contraction length):
+  * M, Y, A, a: max|diff| <= 1e-12 max|ref|
+  * Q, C', T': max|diff| <= 1e-10 max|ref| on the leading block of columns with
+    R_ii / R_00 >= 1e-8 (beyond it Q is fixed only up to rounding); C', T'
+    compared whole when no column falls below that ratio
+  * spectra 1e-10, energies 1e-12 absolute.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_05090_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _ctm(A, chi, **kw):
+    from paper_2509_05090_gb300 import binding
+    return binding.CTM(A, chi, **kw)
+
+
+CASES = [
+    ("heis_D2_chi8", 2, 2, 8, 1000),
+    ("kitaev_D4_chi32", 2, 4, 32, 1001),
+    ("ragged_D3_chi13", 2, 3, 13, 77),
+    ("ragged_D2_chi70", 2, 2, 70, 78),
+    ("spin1_D2_chi9", 3, 2, 9, 79),
+]
+
+
+@pytest.mark.parametrize("name,d,D,chi,seed", CASES)
+def test_prepared_tensors_match_oracle(ctm_lib, name, d, D, chi, seed):
+    A = I.random_site_tensor(d, D, seed)
+    g = _ctm(A, chi)
+    ref = O.OracleCTM(A, chi)
+    assert _rel(_np(g.ctm_get_intermediate("A")), ref.A) <= 1e-14
+    assert _rel(_np(g.ctm_get_intermediate("a")), ref.a) <= 1e-13
+    C, T, Q = g.ctm_get_env()
+    assert np.array_equal(_np(C), ref.C)
+    assert _rel(_np(T), ref.T) <= 1e-13
+    assert np.array_equal(_np(Q), ref.Q)
+    g.close()
+
+
+def _step_parity(A, chi, pre_steps, tol_q=1e-10):
+    ref = O.OracleCTM(A, chi)
+    for _ in range(pre_steps):
+        ref.step()
+    g = _ctm(A, chi)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    ref.step()
+    g.ctm_step(1)
+    last = ref.last
+    assert _rel(_np(g.ctm_get_intermediate("M")), last["M"]) <= 1e-12
+    assert _rel(_np(g.ctm_get_intermediate("Y")), last["Y"]) <= 1e-12
+    R_ref = last["R"]
+    dR = np.abs(np.diag(R_ref))
+    lead = int(np.sum(dR / dR[0] >= 1e-8))
+    R = _np(g.ctm_get_intermediate("R"))
+    assert np.all(np.diag(R) >= 0.0)
+    assert np.all(np.tril(R, -1) == 0.0)
+    assert _rel(R[:lead], R_ref[:lead]) <= 1e-10
+    C, T, Q = (_np(x) for x in g.ctm_get_env())
+    assert _rel(Q[:, :lead], last["Q"][:, :lead]) <= tol_q
+    assert np.max(np.abs(Q.T @ Q - np.eye(chi))) <= 1e-12
+    if lead == chi:
+        assert _rel(C, last["C"]) <= 1e-10
+        assert _rel(T, last["T"]) <= 1e-10
+    assert np.max(np.abs(_np(g.ctm_get_intermediate("s")) - ref.s)) <= 1e-10
+    g.close()
+    return lead
+
+
+@pytest.mark.parametrize("name,d,D,chi,seed", CASES)
+@pytest.mark.parametrize("pre", [0, 3])
+def test_single_step_matches_oracle(ctm_lib, name, d, D, chi, seed, pre):
+    A = I.random_site_tensor(d, D, seed)
+    _step_parity(A, chi, pre)
+
+
+def test_single_step_matches_oracle_d6_chi72(ctm_lib):
+    """The benchmark workload (D = 6, chi = 72, enlarged corner 2592 x 2592), full size."""
+    w = I.WORKLOADS["kh_D6_chi72"]
+    _step_parity(w.site_tensor(), w.chi, 1)
+
+
+def test_trajectory_and_energy_match_oracle(ctm_lib):
+    w = I.WORKLOADS["heis_D2_chi8"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    ref = O.OracleCTM(A, w.chi)
+    g = _ctm(A, w.chi)
+    for k in range(w.steps):
+        dr = ref.step()
+        dg = g.ctm_step(1)
+        assert abs(dg - dr) <= 1e-10 + 1e-8 * abs(dr)
+    e_ref, E_ref = ref.energy(h)
+    e, E, rho = g.ctm_energy(h)
+    assert abs(E - E_ref) <= 1e-12
+    assert np.max(np.abs(e - e_ref)) <= 1e-12
+    assert np.max(np.abs(rho - ref.rho())) <= 1e-12
+    g.close()
+
+
+def test_energy_from_oracle_environment(ctm_lib):
+    w = I.WORKLOADS["kitaev_D4_chi32"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    ref = O.OracleCTM(A, w.chi)
+    for _ in range(5):
+        ref.step()
+    g = _ctm(A, w.chi)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    e, E, rho = g.ctm_energy(h)
+    e_ref, E_ref = ref.energy(h)
+    assert abs(E - E_ref) <= 1e-12
+    assert np.max(np.abs(e - e_ref)) <= 1e-12
+    g.close()
+
+
+def test_product_state_exact_on_gpu(ctm_lib):
+    v = np.array([0.6, -0.8])
+    g = _ctm(I.product_site_tensor(v), 5, symmetrize=False)
+    g.ctm_converge(max_steps=10, tol=1e-14)
+    h = I.bond_hamiltonians(0.3, 0.9)
+    e, E, rho = g.ctm_energy(h)
+    p = np.outer(v, v)
+    assert np.max(np.abs(rho - np.kron(p, p))) <= 1e-14
+    st = np.kron(v, v)
+    assert np.allclose(e, [st @ h[a] @ st for a in range(3)], atol=1e-14)
+    g.close()
+
+
+def test_ising_bond_correlation_on_gpu(ctm_lib):
+    from test_oracle_pins import _ising_exact_bond_correlation
+    beta = 0.3
+    g = _ctm(I.ising_site_tensor(beta), 8)
+    steps, delta, ok = g.ctm_converge(max_steps=300, tol=1e-12)
+    assert ok
+    Sz = np.diag([0.5, -0.5])
+    hz = np.kron(Sz, Sz)
+    e, _, _ = g.ctm_energy(np.stack([hz, hz, hz]))
+    assert abs(4 * e[2] - _ising_exact_bond_correlation(beta)) < 1e-9
+    g.close()
+
+
+def test_converge_graph_equals_eager_steps(ctm_lib):
+    w = I.WORKLOADS["heis_D2_chi8"]
+    A = w.site_tensor()
+    g1 = _ctm(A, w.chi)
+    g2 = _ctm(A, w.chi)
+    steps, delta, ok = g1.ctm_converge(max_steps=20, tol=1e-300, check_every=5)
+    assert steps == 20 and not ok
+    g2.ctm_step(20)
+    for x, y in zip(g1.ctm_get_env(), g2.ctm_get_env()):
+        assert np.array_equal(_np(x), _np(y))
+    g1.close()
+    g2.close()
+
+
+def test_full_size_d8_chi128_first_step(ctm_lib):
+    """D = 8, chi = 128 (enlarged corner 8192 x 8192): the first step from the
+    initial environment, sampled M entries against the oracle's definition and
+    the QR invariants on the full 8192 x 128 reduced corner."""
+    w = I.WORKLOADS["kh_D8_chi128"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)          # oracle's own initial environment (cheap)
+    g = _ctm(A, w.chi)
+    g.ctm_step(1)
+    M = _np(g.ctm_get_intermediate("M"))
+    n, chi, D2 = w.n, w.chi, w.D2
+    rng = np.random.default_rng(5)
+    rows = rng.integers(0, n, 48)
+    cols = rng.integers(0, n, 48)
+    # block-diagonal start: M[(a,y),(b,x)] = delta_ab sum t_u t_l a[u,l,z] a[z,x,y]
+    t = ref.T[0, :, 0]
+    m = np.einsum("u,l,ulz,zxy->yx", t, t, ref.a, ref.a)
+    for r, c in zip(rows, cols):
+        exp = m[r % D2, c % D2] if (r // D2) == (c // D2) else 0.0
+        assert abs(M[r, c] - exp) <= 1e-12 * np.max(np.abs(m))
+    for b in range(0, chi, 37):   # whole diagonal blocks
+        blk = M[b * D2:(b + 1) * D2, b * D2:(b + 1) * D2]
+        assert _rel(blk, m) <= 1e-12
+    Y = _np(g.ctm_get_intermediate("Y"))
+    assert np.array_equal(Y, M[:, :chi])
+    R = _np(g.ctm_get_intermediate("R"))
+    C, T, Q = (_np(x) for x in g.ctm_get_env())
+    assert np.max(np.abs(Q.T @ Q - np.eye(chi))) <= 1e-12
+    assert np.all(np.diag(R) >= 0) and np.all(np.tril(R, -1) == 0)
+    assert np.linalg.norm(Y - Q @ R) <= 1e-13 * np.linalg.norm(Y)
+    assert abs(np.linalg.norm(T) - 1) < 1e-13 and abs(np.linalg.norm(C) - 1) < 1e-13
+    assert np.max(np.abs(C - C.T)) == 0.0
+    g.close()
+
+
+def test_nonfinite_input_rejected(ctm_lib):
+    from paper_2509_05090_gb300 import binding
+    A = I.random_site_tensor(2, 2, 3)
+    A[1, 0, 1, 1] = np.nan
+    with pytest.raises(binding.CtmError) as ei:
+        _ctm(A, 8)
+    assert ei.value.status == 5
+
+
+def test_chi_one_and_d1(ctm_lib):
+    A = I.random_site_tensor(2, 3, 12)
+    _step_parity(A, 1, 2)
+    _step_parity(I.random_site_tensor(2, 1, 4), 3, 1)
