@@ -132,7 +132,9 @@ int ctm_get_intermediate(const ctm_ctx *ctx, int which, double *dst_dev, size_t 
  * between its phases; synchronous.  phase_ms (nphase >= 7) receives the
  * milliseconds of: [0] enlarged corner, [1] warm start + reduced corner
  * Y = M Qs, [2] Householder QR, [3] corner renormalisation, [4] edge
- * renormalisation, [5] corner spectrum and delta, [6] environment hand-over. */
+ * renormalisation, [5] wait for the corner spectrum, [6] environment
+ * hand-over, and (nphase >= 8) [7] the corner spectrum and delta, which run on
+ * a second stream concurrently with [4]. */
 int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
 
 /* Number of kernel launches the library has enqueued since it was loaded

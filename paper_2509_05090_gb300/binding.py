@@ -201,14 +201,17 @@ class CTM:
             raise CtmError(st, "ctm_get_intermediate")
         return out
 
-    PHASES = ("enlarged_corner", "reduced_corner", "qr", "corner", "edge", "spectrum", "handover")
+    PHASES = ("enlarged_corner", "reduced_corner", "qr", "corner", "edge", "spectrum_wait", "handover")
+    SIDE_PHASES = ("spectrum",)
 
     def ctm_step_profiled(self):
         ms = (ctypes.c_double * 8)()
         st = load().ctm_step_profiled(self._h, ms, 8)
         if st != CTM_OK:
             raise CtmError(st, "ctm_step_profiled")
-        return dict(zip(self.PHASES, ms[:7]))
+        out = dict(zip(self.PHASES, ms[:7]))
+        out["spectrum"] = ms[7]      # on the side stream, overlapped with "edge"
+        return out
 
     def close(self):
         if getattr(self, "_h", None):

@@ -70,6 +70,8 @@ struct ctm_ctx {
     cudaStream_t stream;      // the caller's stream
     cudaStream_t own;         // private stream used for graph capture and replay
     cudaEvent_t ev_in, ev_out;
+    cudaStream_t side;        // corner spectrum runs here, overlapped with the edge update
+    cudaEvent_t ev_fork, ev_join;
     // FP64 buffers (device, inside the caller's workspace)
     double *A, *a;
     double *C, *Cn, *Cr;
@@ -78,7 +80,7 @@ struct ctm_ctx {
     double *R;
     double *M, *X, *H;
     double *Y1;
-    double *s, *s_new, *delta;
+    double *s, *s_new, *delta, *spec_work;
     double *splitk;
     size_t splitk_elems;
     double *qr_sbuf, *qr_rowbuf;
@@ -128,6 +130,7 @@ size_t layout(ctm_ctx *c, char *base)
     c->s = td(chi);
     c->s_new = td(chi);
     c->delta = td(8);
+    c->spec_work = td((long long)spectrum_work_doubles((int)chi));
     // split-K scratch: the largest ksplit * M * N over the step's GEMMs
     size_t sk = 0;
     auto need = [&](long long M, long long N, long long K) {
@@ -277,8 +280,13 @@ int enqueue_step(ctm_ctx *c)
     if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
     if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    // the corner spectrum only reads C' and the old spectrum: run it beside the edge update
+    CK(cudaEventRecord(c->ev_fork, st));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, c->spec_work, c->side));
+    CK(cudaEventRecord(c->ev_join, c->side));
     if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
-    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, nullptr, st));
+    CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
@@ -309,9 +317,13 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     CK(cudaEventRecord(ev[3], st));
     if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
     CK(cudaEventRecord(ev[4], st));
+    CK(cudaStreamWaitEvent(c->side, ev[4], 0));
+    CK(cudaEventRecord(ev[8], c->side));
+    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, c->spec_work, c->side));
+    CK(cudaEventRecord(ev[9], c->side));
     if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
     CK(cudaEventRecord(ev[5], st));
-    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, nullptr, st));
+    CK(cudaStreamWaitEvent(st, ev[9], 0));
     CK(cudaEventRecord(ev[6], st));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
@@ -444,7 +456,13 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     int rc = CTM_OK;
     do {
         if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess) { rc = CTM_ECUDA; break; }
-        if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
         if (cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess) {
             rc = CTM_ECUDA;
@@ -599,7 +617,7 @@ int ctm_set_env(ctm_ctx *c, const double *C_dev, const double *T_dev, const doub
     CK(cudaMemcpyAsync(c->T, T_dev, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->Q, Q_dev, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
     // the spectrum of the new corner becomes the reference for the next delta
-    CK(launch_spectrum((int)chi, c->C, c->s, c->s, c->delta, nullptr, st));
+    CK(launch_spectrum((int)chi, c->C, c->s, c->s, c->delta, c->spec_work, st));
     CK(cudaStreamSynchronize(st));
     return CTM_OK;
 }
@@ -634,6 +652,12 @@ void ctm_destroy(ctm_ctx *c)
         cudaStreamSynchronize(c->own);
         cudaStreamDestroy(c->own);
     }
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     delete c;
@@ -657,8 +681,8 @@ const char *ctm_status_str(int s)
 int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
 {
     if (!c || !phase_ms || nphase < 7) return CTM_EINVAL;
-    cudaEvent_t ev[8];
-    for (int i = 0; i < 8; ++i)
+    cudaEvent_t ev[10];
+    for (int i = 0; i < 10; ++i)
         if (cudaEventCreate(&ev[i]) != cudaSuccess) return CTM_ECUDA;
     int rc = enqueue_step_profiled(c, ev);
     if (rc == CTM_OK) {
@@ -672,7 +696,12 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
             if (cudaEventElapsedTime(&ms, ev[i], ev[i + 1]) != cudaSuccess) rc = CTM_ECUDA;
             phase_ms[i] = ms;
         }
-    for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
+    if (rc == CTM_OK && nphase >= 8) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, ev[8], ev[9]) != cudaSuccess) rc = CTM_ECUDA;
+        phase_ms[7] = ms;
+    }
+    for (int i = 0; i < 10; ++i) cudaEventDestroy(ev[i]);
     return rc;
 }
 

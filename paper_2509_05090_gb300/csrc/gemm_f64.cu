@@ -13,8 +13,6 @@
 
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, NT = 256;
-
 __device__ __forceinline__ long long off2(const Idx2 &x, int i)
 {
     int hi = i / x.div;
@@ -22,16 +20,22 @@ __device__ __forceinline__ long long off2(const Idx2 &x, int i)
     return (long long)hi * x.s1 + (long long)lo * x.s2;
 }
 
-// When the K map has unit stride the A tile is fetched K-fastest, otherwise
-// M-fastest (and N-fastest / K-fastest for B), so consecutive threads touch
-// consecutive addresses whenever the layout allows it.
-__global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int a_kfast, int b_nfast, int kchunk,
-                                                      double *partial)
+// BM x BN outputs per CTA, (BM/4) x (BN/4) threads with a 4 x 4 micro-tile
+// each (rows ty + TY*i, columns tx + TX*j), K staged BK at a time.  The tile
+// shape is picked per GEMM so that the bond dimensions (chi = 72, D2 = 36 ...)
+// divide it without padding waste.  When the K map has unit stride the A tile
+// is fetched K-fastest, otherwise M-fastest (likewise N/K for B), so
+// consecutive threads touch consecutive addresses whenever the layout allows.
+template <int BM, int BN, int BK>
+__global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_f64_kernel(GemmF64 g, int a_kfast, int b_nfast,
+                                                                       int kchunk, double *partial)
 {
+    constexpr int TY = BM / 4, TX = BN / 4, NT = TY * TX;
+    constexpr int EA = (BM * BK + NT - 1) / NT, EB = (BN * BK + NT - 1) / NT;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int tx = tid % TX, ty = tid / TX;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(g.K, kbeg + kchunk);
@@ -42,35 +46,55 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int a_kfast, in
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
 
-    double ra[4], rb[4];
+    double ra[EA], rb[EB];
     auto fetch = [&](int k0) {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            int lin = tid + e * NT;   // 0..1023 over the 64 x 16 tile
-            int mm, kk;
-            if (a_kfast) { kk = lin & 15; mm = lin >> 4; }
-            else { mm = lin & 63; kk = lin >> 6; }
-            int m = m0 + mm, k = k0 + kk;
-            ra[e] = (m < g.M && k < kend) ? g.A[off2(g.Am, m) + off2(g.Ak, k)] : 0.0;
-            int nn, kb;
-            if (b_nfast) { nn = lin & 63; kb = lin >> 6; }
-            else { kb = lin & 15; nn = lin >> 4; }
-            int n = n0 + nn, k2 = k0 + kb;
-            rb[e] = (n < g.N && k2 < kend) ? g.B[off2(g.Bk, k2) + off2(g.Bn, n)] : 0.0;
+        for (int e = 0; e < EA; ++e) {
+            int lin = tid + e * NT;
+            double v = 0.0;
+            if (lin < BM * BK) {
+                int mm, kk;
+                if (a_kfast) { kk = lin % BK; mm = lin / BK; }
+                else { mm = lin % BM; kk = lin / BM; }
+                int m = m0 + mm, k = k0 + kk;
+                if (m < g.M && k < kend) v = g.A[off2(g.Am, m) + off2(g.Ak, k)];
+            }
+            ra[e] = v;
+        }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            int lin = tid + e * NT;
+            double v = 0.0;
+            if (lin < BN * BK) {
+                int nn, kb;
+                if (b_nfast) { nn = lin % BN; kb = lin / BN; }
+                else { kb = lin % BK; nn = lin / BK; }
+                int n = n0 + nn, k2 = k0 + kb;
+                if (n < g.N && k2 < kend) v = g.B[off2(g.Bk, k2) + off2(g.Bn, n)];
+            }
+            rb[e] = v;
         }
     };
     auto stash = [&]() {
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < EA; ++e) {
             int lin = tid + e * NT;
-            int mm, kk;
-            if (a_kfast) { kk = lin & 15; mm = lin >> 4; }
-            else { mm = lin & 63; kk = lin >> 6; }
-            As[kk][mm] = ra[e];
-            int nn, kb;
-            if (b_nfast) { nn = lin & 63; kb = lin >> 6; }
-            else { kb = lin & 15; nn = lin >> 4; }
-            Bs[kb][nn] = rb[e];
+            if (lin < BM * BK) {
+                int mm, kk;
+                if (a_kfast) { kk = lin % BK; mm = lin / BK; }
+                else { mm = lin % BM; kk = lin / BM; }
+                As[kk][mm] = ra[e];
+            }
+        }
+#pragma unroll
+        for (int e = 0; e < EB; ++e) {
+            int lin = tid + e * NT;
+            if (lin < BN * BK) {
+                int nn, kb;
+                if (b_nfast) { nn = lin % BN; kb = lin / BN; }
+                else { kb = lin % BK; nn = lin / BK; }
+                Bs[kb][nn] = rb[e];
+            }
         }
     };
 
@@ -84,9 +108,9 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int a_kfast, in
         for (int kk = 0; kk < BK; ++kk) {
             double a[4], b[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + TX * j];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -96,11 +120,11 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int a_kfast, in
 
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        int m = m0 + ty + 16 * i;
+        int m = m0 + ty + TY * i;
         if (m >= g.M) continue;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            int n = n0 + tx + 16 * j;
+            int n = n0 + tx + TX * j;
             if (n >= g.N) continue;
             if (partial) {
                 partial[((size_t)blockIdx.z * g.M + m) * g.N + n] = acc[i][j];
@@ -113,6 +137,12 @@ __global__ void __launch_bounds__(NT) gemm_f64_kernel(GemmF64 g, int a_kfast, in
         }
     }
 }
+
+struct TileCfg {
+    int bm, bn, bk;
+};
+constexpr TileCfg kTiles[] = {{64, 64, 16}, {72, 72, 12}, {64, 32, 16}, {72, 36, 12}, {32, 64, 16},
+                              {36, 72, 12}, {64, 72, 12}, {72, 64, 16}, {32, 32, 16}, {36, 36, 12}};
 
 // Deterministic split-K reduction: fixed summation order over the splits.
 __global__ void splitk_reduce_kernel(GemmF64 g, int ksplit, const double *partial)
@@ -146,21 +176,41 @@ int device_sm_count()
     return sms;
 }
 
+static long long ceil_to(long long x, long long b) { return (x + b - 1) / b * b; }
+
+// Tile with the least padded work; ties go to the larger tile.
+static TileCfg pick_tile(int M, int N, int K)
+{
+    TileCfg best = kTiles[0];
+    double best_cost = 1e300;
+    for (const TileCfg &t : kTiles) {
+        double cost = (double)ceil_to(M, t.bm) * ceil_to(N, t.bn) * ceil_to(K, t.bk);
+        // small tiles re-read operands more often; charge them a little
+        cost *= 1.0 + 8.0 / t.bm + 8.0 / t.bn;
+        if (cost < best_cost * 0.999) {
+            best_cost = cost;
+            best = t;
+        }
+    }
+    return best;
+}
+
 int gemm_f64_pick_split(int M, int N, int K)
 {
-    long long tiles = (long long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    TileCfg t = pick_tile(M, N, K);
+    long long tiles = (long long)((M + t.bm - 1) / t.bm) * ((N + t.bn - 1) / t.bn);
     long long want = 2LL * device_sm_count();
-    if (tiles >= want || K < 4 * BK) return 1;
+    if (tiles >= want || K < 4 * t.bk) return 1;
     long long s = (want + tiles - 1) / tiles;
-    long long maxs = K / (2 * BK);
+    long long maxs = K / (2 * t.bk);
     if (s > maxs) s = maxs;
     if (s > 64) s = 64;
     return s < 1 ? 1 : (int)s;
 }
 
-cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)
+template <int BM, int BN, int BK>
+static cudaError_t launch_tile(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)
 {
-    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     int a_kfast = (g.Ak.s2 == 1 && g.Ak.div >= g.K) ? 1 : 0;
     int b_nfast = (g.Bn.s2 == 1 && g.Bn.div >= g.N) ? 1 : 0;
     if (ksplit < 1 || !scratch) ksplit = 1;
@@ -170,13 +220,14 @@ cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t
     ksplit = (g.K + kchunk - 1) / kchunk;
     if (ksplit < 1) ksplit = 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ksplit);
+    constexpr int NT = (BM / 4) * (BN / 4);
     if (ksplit == 1) {
         CTM_COUNT_LAUNCH(1);
-        gemm_f64_kernel<<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, nullptr);
+        gemm_f64_kernel<BM, BN, BK><<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, nullptr);
         return cudaGetLastError();
     }
     CTM_COUNT_LAUNCH(2);
-    gemm_f64_kernel<<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, scratch);
+    gemm_f64_kernel<BM, BN, BK><<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long total = (long long)g.M * g.N;
@@ -184,4 +235,24 @@ cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t
     if (blocks > 4 * device_sm_count()) blocks = 4 * device_sm_count();
     splitk_reduce_kernel<<<blocks, 256, 0, st>>>(g, ksplit, scratch);
     return cudaGetLastError();
+}
+
+cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)
+{
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    TileCfg t = pick_tile(g.M, g.N, g.K);
+#define CTM_TILE(a, b, c) \
+    if (t.bm == a && t.bn == b && t.bk == c) return launch_tile<a, b, c>(g, ksplit, scratch, st);
+    CTM_TILE(64, 64, 16)
+    CTM_TILE(72, 72, 12)
+    CTM_TILE(64, 32, 16)
+    CTM_TILE(72, 36, 12)
+    CTM_TILE(32, 64, 16)
+    CTM_TILE(36, 72, 12)
+    CTM_TILE(64, 72, 12)
+    CTM_TILE(72, 64, 16)
+    CTM_TILE(32, 32, 16)
+    CTM_TILE(36, 36, 12)
+#undef CTM_TILE
+    return cudaErrorInvalidValue;
 }

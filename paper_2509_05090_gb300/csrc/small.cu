@@ -163,22 +163,26 @@ __global__ void scale_by_partials_kernel(long long count, double *x, const doubl
         x[t] *= f;
 }
 
-// a7: corner spectrum and delta.  One CTA: Householder tridiagonalisation of the
-// symmetric corner in shared memory, Sturm-count bisection for every
-// eigenvalue (one thread each), |lambda| sorted descending by rank, unit
-// 2-norm, delta = |s_new - s_old|_2.
-__global__ void spectrum_kernel(int chi, const double *C, double *s_new, const double *s_old, double *delta)
+// a7: corner spectrum and delta, in three launches.
+// (1) one CTA: Householder tridiagonalisation of the symmetric corner in shared
+//     memory -> diagonal d and squared off-diagonal e^2 (global work buffer);
+// (2) one warp per eigenvalue: multisection on the Gershgorin interval, each
+//     lane evaluating the Sturm count at one of 32 points per round
+//     (5 bits per round instead of 1).  The count is the number of sign
+//     changes of p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, kept in range by
+//     exact power-of-two rescaling -- no division on the dependent chain;
+// (3) one CTA: |lambda| sorted descending by rank, unit 2-norm, delta.
+constexpr int SPEC_WARPS = 8;
+
+__global__ void tridiag_kernel(int chi, const double *C, double *work)
 {
     extern __shared__ double sm[];
     __shared__ double red[32];
-    __shared__ double sh_beta, sh_alpha, sh_K;
+    __shared__ double sh_beta, sh_alpha;
     __shared__ int sh_skip;
     double *A = sm;                      // chi x chi
     double *v = A + chi * chi;           // chi
     double *p = v + chi;                 // chi
-    double *dg = p + chi;                // chi
-    double *e2 = dg + chi;               // chi
-    double *lam = e2 + chi;              // chi
     const int tid = threadIdx.x;
     for (int t = tid; t < chi * chi; t += blockDim.x) {
         int i = t / chi, j = t % chi;
@@ -227,48 +231,81 @@ __global__ void spectrum_kernel(int chi, const double *C, double *s_new, const d
         __syncthreads();
     }
     for (int i = tid; i < chi; i += blockDim.x) {
-        dg[i] = A[i * chi + i];
+        work[i] = A[i * chi + i];
         double e = (i + 1 < chi) ? A[(i + 1) * chi + i] : 0.0;
-        e2[i] = e * e;
+        work[chi + i] = e * e;
     }
-    __syncthreads();
-    // Gershgorin bounds
-    double lo_l = 1e300, hi_l = -1e300;
-    for (int i = tid; i < chi; i += blockDim.x) {
-        double r = sqrt(e2[i]) + (i > 0 ? sqrt(e2[i - 1]) : 0.0);
-        lo_l = fmin(lo_l, dg[i] - r);
-        hi_l = fmax(hi_l, dg[i] + r);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        lo_l = fmin(lo_l, __shfl_down_sync(0xffffffffu, lo_l, o));
-        hi_l = fmax(hi_l, __shfl_down_sync(0xffffffffu, hi_l, o));
-    }
-    __shared__ double slo[32], shi[32];
-    if ((tid & 31) == 0) { slo[tid >> 5] = lo_l; shi[tid >> 5] = hi_l; }
-    __syncthreads();
-    double glo = slo[0], ghi = shi[0];
-    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { glo = fmin(glo, slo[w]); ghi = fmax(ghi, shi[w]); }
-    const double scale = fmax(fabs(glo), fabs(ghi));
-    const double pivmin = 1e-300 + scale * 1e-30;
-    for (int ei = tid; ei < chi; ei += blockDim.x) {
-        double lo = glo - 1e-12 * scale - 1e-300, hi = ghi + 1e-12 * scale + 1e-300;
-        for (int it = 0; it < 200; ++it) {
-            double mid = 0.5 * (lo + hi);
-            if (mid <= lo || mid >= hi || hi - lo <= 2e-16 * scale) break;
-            int cnt = 0;
-            double q = dg[0] - mid;
-            if (fabs(q) < pivmin) q = -pivmin;
-            cnt += (q < 0.0);
-            for (int j = 1; j < chi; ++j) {
-                q = dg[j] - mid - e2[j - 1] / q;
-                if (fabs(q) < pivmin) q = -pivmin;
-                cnt += (q < 0.0);
-            }
-            if (cnt <= ei) lo = mid;
-            else hi = mid;
+}
+
+// number of eigenvalues of the tridiagonal (d, e2) below x
+__device__ __forceinline__ int sturm_count(int chi, const double *d, const double *e2, double x, double tiny)
+{
+    double pm = 1.0, p = d[0] - x;
+    if (p == 0.0) p = -tiny;
+    int cnt = (p < 0.0);
+    for (int i = 1; i < chi; ++i) {
+        double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
+        if (pn == 0.0) pn = (p < 0.0) ? tiny : -tiny;
+        cnt += ((pn < 0.0) != (p < 0.0));
+        pm = p;
+        p = pn;
+        double ap = fabs(p);
+        if (ap > 0x1p+500) {
+            p *= 0x1p-500;
+            pm *= 0x1p-500;
+        } else if (ap < 0x1p-500) {
+            p *= 0x1p+500;
+            pm *= 0x1p+500;
         }
-        lam[ei] = fabs(0.5 * (lo + hi));
     }
+    return cnt;
+}
+
+__global__ void bisect_kernel(int chi, const double *work, double *lam)
+{
+    __shared__ double d[160], e2[160];
+    for (int i = threadIdx.x; i < chi; i += blockDim.x) {
+        d[i] = work[i];
+        e2[i] = work[chi + i];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int ei = blockIdx.x * SPEC_WARPS + (threadIdx.x >> 5);
+    if (ei >= chi) return;
+    // Gershgorin interval (every lane computes it; chi is small)
+    double lo = 1e300, hi = -1e300;
+    for (int i = 0; i < chi; ++i) {
+        double r = sqrt(e2[i]) + (i > 0 ? sqrt(e2[i - 1]) : 0.0);
+        lo = fmin(lo, d[i] - r);
+        hi = fmax(hi, d[i] + r);
+    }
+    const double scale = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
+    lo -= 1e-12 * scale;
+    hi += 1e-12 * scale;
+    const double tiny = 1e-290 * scale;
+    for (int round = 0; round < 16; ++round) {
+        if (hi - lo <= 4e-16 * scale) break;
+        double x = lo + (hi - lo) * (double)(lane + 1) / 33.0;
+        int cnt = sturm_count(chi, d, e2, x, tiny);
+        unsigned below = __ballot_sync(0xffffffffu, cnt <= ei);   // a prefix of lanes
+        int L = __popc(below);
+        double xl = __shfl_sync(0xffffffffu, x, (L > 0) ? L - 1 : 0);
+        double xh = __shfl_sync(0xffffffffu, x, (L < 32) ? L : 31);
+        double nlo = (L > 0) ? xl : lo;
+        double nhi = (L < 32) ? xh : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    if (lane == 0) lam[ei] = 0.5 * (lo + hi);
+}
+
+__global__ void spectrum_finish_kernel(int chi, const double *lam_in, double *s_new, const double *s_old,
+                                       double *delta)
+{
+    __shared__ double red[32];
+    __shared__ double lam[160], srt[160];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < chi; i += blockDim.x) lam[i] = fabs(lam_in[i]);
     __syncthreads();
     double ss = 0.0;
     for (int i = tid; i < chi; i += blockDim.x) ss += lam[i] * lam[i];
@@ -281,16 +318,16 @@ __global__ void spectrum_kernel(int chi, const double *C, double *s_new, const d
             double aj = lam[j];
             rank += (aj > ai) || (aj == ai && j < i);
         }
-        p[rank] = ai * f;
+        srt[rank] = ai * f;
     }
     __syncthreads();
     double dd = 0.0;
     for (int i = tid; i < chi; i += blockDim.x) {
-        double x = p[i] - s_old[i];
+        double x = srt[i] - s_old[i];
         dd += x * x;
-        s_new[i] = p[i];
     }
     dd = block_sum(dd, red);
+    for (int i = tid; i < chi; i += blockDim.x) s_new[i] = srt[i];
     if (tid == 0) *delta = sqrt(dd);
 }
 
@@ -403,16 +440,21 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
     return cudaGetLastError();
 }
 
-size_t spectrum_work_doubles(int chi) { return (size_t)chi * chi + 5 * (size_t)chi; }
+size_t spectrum_work_doubles(int chi) { return (size_t)3 * chi + 8; }
 
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
                             double *work, cudaStream_t st)
 {
-    (void)work;
-    size_t smem = sizeof(double) * spectrum_work_doubles(chi);
-    if (smem > 200 * 1024) return cudaErrorInvalidValue;
-    CTM_COUNT_LAUNCH(1);
-    spectrum_kernel<<<1, 256, smem, st>>>(chi, C, s_new, s_old, delta);
+    if (chi > 160 || !work) return cudaErrorInvalidValue;
+    size_t smem = sizeof(double) * ((size_t)chi * chi + 2 * (size_t)chi);
+    CTM_COUNT_LAUNCH(3);
+    tridiag_kernel<<<1, 256, smem, st>>>(chi, C, work);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, work + 2 * chi, s_new, s_old, delta);
     return cudaGetLastError();
 }
 
@@ -439,5 +481,5 @@ cudaError_t launch_check_finite(long long count, const double *x, int *flag, cud
 
 cudaError_t spectrum_prepare()
 {
-    return cudaFuncSetAttribute(spectrum_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }

@@ -165,8 +165,10 @@ def test_converge_graph_equals_eager_steps(ctm_lib):
     steps, delta, ok = g1.ctm_converge(max_steps=20, tol=1e-300, check_every=5)
     assert steps == 20 and not ok
     g2.ctm_step(20)
+    # the QR sums its partial dot products with FP64 atomics, so replays agree
+    # to rounding, not bit for bit
     for x, y in zip(g1.ctm_get_env(), g2.ctm_get_env()):
-        assert np.array_equal(_np(x), _np(y))
+        assert _rel(_np(x), _np(y)) <= 1e-12
     g1.close()
     g2.close()
 
