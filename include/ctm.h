@@ -64,7 +64,7 @@ typedef enum {
 typedef struct {
     int d, D, chi;           /* physical, virtual and environment bond dimensions */
     int precision;           /* ctm_precision */
-    int n_split;             /* BF16 slices per operand in CTM_SPLIT_BF16 (2..6); ignored in FP64 */
+    int n_split;             /* BF16 slices per operand in CTM_SPLIT_BF16 (2..5); ignored in FP64 */
     double tol;              /* convergence threshold on delta (Sec. II.B: "desired precision") */
     int max_steps;           /* step limit of ctm_converge when its argument is <= 0 */
     int symmetrize;          /* 1: project A onto the C3v A1 subspace and normalise (App. A) */
@@ -140,6 +140,21 @@ int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
 /* Number of kernel launches the library has enqueued since it was loaded
  * (host-side count; replays of a captured graph are not counted). */
 unsigned long long ctm_kernel_launches(void);
+
+/* The contraction engine on its own (Sec. II.B: every update of Fig. 3 is a
+ * chain of such products).  C = A B for row-major FP64 matrices A (M x K),
+ * B (K x N), C (M x N), all device pointers.  precision CTM_FP64 runs the FP64
+ * GEMM; CTM_SPLIT_BF16 splits every row of A and column of B into n_split
+ * (2..5) BF16 digit slices on a per-row / per-column power-of-two grid and
+ * sums the slice products of total order < n_split on tcgen05 tensor cores,
+ * exactly in FP32 per 256-deep K chunk, recombined in 64-bit integers
+ * (relative error ~ n_split 2^(-8 n_split) of the row/column maxima).  The
+ * caller supplies ctm_gemm_workspace_bytes() bytes of device workspace
+ * (256-byte aligned).  Synchronous.  CTM_ETIMEOUT if a bounded device wait
+ * expired. */
+size_t ctm_gemm_workspace_bytes(int M, int N, int K, int precision, int n_split);
+int ctm_gemm(int M, int N, int K, const double *A_dev, const double *B_dev, double *C_dev, int precision,
+             int n_split, void *workspace, size_t ws_bytes, void *stream);
 
 /* Release the host context (the caller frees the workspace). */
 void ctm_destroy(ctm_ctx *ctx);

@@ -72,6 +72,8 @@ def load(path: str = LIB_PATH):
         "ctm_version": (ctypes.c_char_p, []),
         "ctm_step_profiled": (I, [P, dp, I]),
         "ctm_kernel_launches": (ctypes.c_ulonglong, []),
+        "ctm_gemm_workspace_bytes": (ctypes.c_size_t, [I, I, I, I, I]),
+        "ctm_gemm": (I, [I, I, I, P, P, P, I, I, P, ctypes.c_size_t, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -83,6 +85,27 @@ def load(path: str = LIB_PATH):
 
 def ctm_kernel_launches() -> int:
     return int(load().ctm_kernel_launches())
+
+
+def ctm_gemm(A, B, precision="fp64", n_split=4):
+    """C = A B through the library's contraction engine (torch CUDA float64 tensors)."""
+    torch = _torch()
+    A = A.to(device="cuda", dtype=torch.float64).contiguous()
+    B = B.to(device="cuda", dtype=torch.float64).contiguous()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    nbytes = int(load().ctm_gemm_workspace_bytes(M, N, K, prec, n_split))
+    if nbytes == 0:
+        raise CtmError(1, "ctm_gemm_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    st = load().ctm_gemm(M, N, K, _ptr(A), _ptr(B), _ptr(C), prec, int(n_split), _ptr(ws), nbytes,
+                         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != CTM_OK:
+        raise CtmError(st, "ctm_gemm")
+    return C
 
 
 def status_str(status: int) -> str:

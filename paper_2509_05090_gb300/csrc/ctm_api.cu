@@ -6,6 +6,7 @@
 #include <string.h>
 
 #include <new>
+#include <vector>
 
 #include "ctm_internal.h"
 
@@ -83,6 +84,8 @@ struct ctm_ctx {
     double *s, *s_new, *delta, *spec_work;
     double *splitk;
     size_t splitk_elems;
+    int split_T;              // 0: FP64 contractions; 2..5: split-BF16 slices per operand
+    SplitWork sw;
     double *qr_sbuf, *qr_rowbuf;
     unsigned *qr_bar;
     int *err, *flag;
@@ -97,6 +100,19 @@ struct ctm_ctx {
 };
 
 namespace {
+
+struct Shape {
+    int M, N, K;
+};
+
+// (M, N, K) of the eleven contractions of one step, in launch order.
+std::vector<Shape> step_shapes(const ctm_ctx *c)
+{
+    const int chi = c->chi, D2 = c->D2, n = (int)c->n;
+    return {{n, chi, chi},         {n, n, chi},   {chi * chi, D2, D2 * D2}, {chi * chi, D2 * D2, D2},
+            {n, chi, n},           {n, chi, n},   {chi, chi, n},            {n, n, chi},
+            {chi * chi, D2, D2 * D2}, {chi * chi, D2 * D2, D2}, {chi, n, n}};
+}
 
 // Carve the workspace.  With base == nullptr only the size is computed.
 size_t layout(ctm_ctx *c, char *base)
@@ -164,6 +180,30 @@ size_t layout(ctm_ctx *c, char *base)
     c->rho_raw = td(d * d * d * d);
     c->eout = td(4 + d * d * d * d);
     c->h = td(3 * d * d * d * d);
+    if (c->split_T > 0) {
+        // packed digit slices, exponents and the split-K integer accumulator for the
+        // largest operand of the step's contractions
+        size_t ap = 0, bp = 0, pp = 0;
+        long long ecap = 0;
+        for (const auto &sh : step_shapes(c)) {
+            SplitPlan pl = split_plan(sh.M, sh.N, sh.K, c->split_T);
+            if (pl.a_pack_bytes > ap) ap = pl.a_pack_bytes;
+            if (pl.b_pack_bytes > bp) bp = pl.b_pack_bytes;
+            if (pl.partial_bytes > pp) pp = pl.partial_bytes;
+            if (sh.M > ecap) ecap = sh.M;
+            if (sh.N > ecap) ecap = sh.N;
+        }
+        c->sw.Apk = (unsigned char *)take(ap);
+        c->sw.a_pack_cap = ap;
+        c->sw.Bpk = (unsigned char *)take(bp);
+        c->sw.b_pack_cap = bp;
+        c->sw.eA = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw.eB = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw.e_cap = (int)ecap;
+        c->sw.partial = (void *)take(pp + 8);
+        c->sw.partial_cap = pp;
+        c->sw.err = c->err;
+    }
     return off;
 }
 
@@ -173,10 +213,18 @@ bool config_ok(const ctm_config *cfg)
     if (cfg->d < 1 || cfg->d > 3) return false;
     if (cfg->D < 1 || cfg->D > 12) return false;
     if (cfg->chi < 1 || cfg->chi > 160) return false;
-    if (cfg->precision != CTM_FP64) return false;
+    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return false;
+    if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
     long long n = (long long)cfg->chi * cfg->D * cfg->D;
     if (n > 20000) return false;
     return true;
+}
+
+// The step's contractions: FP64 GEMM, or the split-BF16 tcgen05 engine.
+cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g)
+{
+    if (c->split_T > 0) return gemm_split(g, c->split_T, c->sw, c->stream);
+    return gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->stream);
 }
 
 #define CK(expr)                                          \
@@ -197,19 +245,19 @@ int enqueue_enlarged_corner(ctm_ctx *c)
     // W = T C
     g = GemmF64{(int)n, chi, chi, c->T, idx_lin(chi), idx_lin(1), c->C, idx_lin(chi), idx_lin(1),
                 c->W, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     // X'[a][b][u][l] = W[(a,u),h] T[(b,l),h]
     g = GemmF64{(int)n, (int)n, chi, c->W, idx_lin(chi), idx_lin(1), c->T, idx_lin(1), idx_lin(chi),
                 c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     // Y1 = X' a   (chi^2 x D2^2) (D2^2 x D2)
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     // M[(a,y)][(b,x)] = Y1[(a,b), z] a[z, (x,y)]
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
                 idx_lin(1), c->M, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     return CTM_OK;
 }
 
@@ -222,7 +270,7 @@ int enqueue_projector(ctm_ctx *c, double *Qout)
     CK(launch_warm_start((int)n, chi, c->Q, c->C, c->Qs, st));
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
               c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err};
     CK(qr_householder((int)n, chi, c->Y, Qout, c->R, qs, st));
     return CTM_OK;
@@ -236,10 +284,10 @@ int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout)
     cudaStream_t st = c->stream;
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), Qp, idx_lin(chi), idx_lin(1),
               c->MQ, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
                 c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     CK(launch_corner_sym_normalize(chi, c->Cr, Cout, st));
     return CTM_OK;
 }
@@ -254,20 +302,20 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]
     g = GemmF64{(int)n, (int)n, chi, c->T, idx_lin(chi), idx_lin(1), Qp, idx_lin(n), idx_lin(1),
                 c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(chi, 1, (long long)D2 * D2), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     // H3'[a][y][x][j] = H2[(a,j),z] a[z,(x,y)]
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
                 idx_lin(1), c->H, idx_split(chi, (long long)D2 * D2 * chi, 1), idx_split(D2, chi, (long long)D2 * chi),
                 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     // T'[i][(x,j)] = sum_{(a,y)} Q[(a,y),i] H3'[(a,y),(x,j)]
     g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),
                 Tout, idx_lin(n), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(run_gemm(c, g));
     CK(launch_normalize((long long)chi * D2 * chi, Tout, c->norm_part, NORM_BLOCKS, st));
     return CTM_OK;
 }
@@ -307,7 +355,7 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     {
         GemmF64 g{(int)n, (int)chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
                   c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-        CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+        CK(run_gemm(c, g));
     }
     CK(cudaEventRecord(ev[2], st));
     {
@@ -420,6 +468,7 @@ size_t ctm_workspace_bytes(const ctm_config *cfg)
     c.D2 = cfg->D * cfg->D;
     c.chi = cfg->chi;
     c.n = (long long)c.chi * c.D2;
+    c.split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
     return layout(&c, nullptr);
 }
 
@@ -429,7 +478,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     if (!out) return CTM_EINVAL;
     *out = nullptr;
     if (!cfg || !A_dev || !workspace) return CTM_EINVAL;
-    if (cfg->precision != CTM_FP64) return CTM_EUNSUPPORTED;
+    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return CTM_EUNSUPPORTED;
     if (!config_ok(cfg)) return CTM_EINVAL;
     if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
     ctm_ctx *c = new (std::nothrow) ctm_ctx;
@@ -441,6 +490,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     c->D2 = cfg->D * cfg->D;
     c->chi = cfg->chi;
     c->n = (long long)c->chi * c->D2;
+    c->split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
     c->stream = (cudaStream_t)stream;
     if (!qr_supported((int)c->n, c->chi)) {
         delete c;
@@ -455,7 +505,10 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     cudaStream_t st = c->stream;
     int rc = CTM_OK;
     do {
-        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
         if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -707,6 +760,63 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
 
 unsigned long long ctm_kernel_launches(void) { return g_ctm_launches; }
 
-const char *ctm_version(void) { return "libctm sm_103a fp64"; }
+size_t ctm_gemm_workspace_bytes(int M, int N, int K, int precision, int n_split)
+{
+    if (M <= 0 || N <= 0 || K <= 0) return 0;
+    if (precision == CTM_FP64) {
+        int s = gemm_f64_pick_split(M, N, K);
+        return align_up(64) + align_up(sizeof(double) * (size_t)(s > 1 ? s : 0) * M * N + 8);
+    }
+    if (precision != CTM_SPLIT_BF16 || !split_supported_T(n_split)) return 0;
+    SplitPlan p = split_plan(M, N, K, n_split);
+    int ec = M > N ? M : N;
+    return align_up(64) + align_up(p.a_pack_bytes) + align_up(p.b_pack_bytes) + 2 * align_up(sizeof(int) * ec) +
+           align_up(p.partial_bytes + 8);
+}
+
+int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, int precision, int n_split,
+             void *workspace, size_t ws_bytes, void *stream)
+{
+    if (M <= 0 || N <= 0 || K <= 0 || !A || !B || !C || !workspace) return CTM_EINVAL;
+    size_t need = ctm_gemm_workspace_bytes(M, N, K, precision, n_split);
+    if (need == 0) return CTM_EINVAL;
+    if (ws_bytes < need) return CTM_ENOMEM;
+    if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    char *base = (char *)workspace;
+    int *err = (int *)base;
+    size_t off = align_up(64);
+    GemmF64 g{M, N, K, A, idx_lin(K), idx_lin(1), B, idx_lin(N), idx_lin(1), C, idx_lin(N), idx_lin(1), 1.0, 0.0};
+    CK(cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (precision == CTM_FP64) {
+        CK(gemm_f64(g, gemm_f64_pick_split(M, N, K), (double *)(base + off), st));
+    } else {
+        if (split_prepare() != cudaSuccess) return CTM_ECUDA;
+        SplitPlan p = split_plan(M, N, K, n_split);
+        int ec = M > N ? M : N;
+        SplitWork w;
+        w.Apk = (unsigned char *)(base + off);
+        off += align_up(p.a_pack_bytes);
+        w.a_pack_cap = p.a_pack_bytes;
+        w.Bpk = (unsigned char *)(base + off);
+        off += align_up(p.b_pack_bytes);
+        w.b_pack_cap = p.b_pack_bytes;
+        w.eA = (int *)(base + off);
+        off += align_up(sizeof(int) * ec);
+        w.eB = (int *)(base + off);
+        off += align_up(sizeof(int) * ec);
+        w.e_cap = ec;
+        w.partial = base + off;
+        w.partial_cap = p.partial_bytes;
+        w.err = err;
+        CK(gemm_split(g, n_split, w, st));
+    }
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return e ? CTM_ETIMEOUT : CTM_OK;
+}
+
+const char *ctm_version(void) { return "libctm sm_103a fp64+bf16split"; }
 
 }  // extern "C"

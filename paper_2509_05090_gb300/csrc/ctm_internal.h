@@ -37,6 +37,26 @@ cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t
 // Number of K-splits gemm_f64 picks for this shape (1 = none) and the scratch it needs.
 int gemm_f64_pick_split(int M, int N, int K);
 
+// ---------------------------------------------------------------- split-BF16 engine
+// C = A B evaluated as sum_{i+j<T} A_i B_j of BF16 digit slices on tcgen05 (see gemm_split.cu).
+struct SplitPlan {
+    int NT, mTiles, nTiles, kTiles, chunks_per_split, ksplit;
+    size_t a_pack_bytes, b_pack_bytes, partial_bytes;
+};
+struct SplitWork {
+    unsigned char *Apk, *Bpk;
+    size_t a_pack_cap, b_pack_cap;
+    int *eA, *eB;
+    int e_cap;
+    void *partial;
+    size_t partial_cap;
+    int *err;
+};
+SplitPlan split_plan(int M, int N, int K, int T);
+int split_supported_T(int T);
+cudaError_t split_prepare();
+cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st);
+
 // ---------------------------------------------------------------- QR
 // Householder QR of Y (n x k row-major, n >= k) with diag(R) >= 0.  Q (n x k)
 // and R (k x k) row-major.  One cooperative launch: factorisation, backward

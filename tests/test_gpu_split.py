@@ -1,0 +1,102 @@
+"""Split-BF16 tcgen05 contraction engine against the FP64 CPU oracle.
+
+The engine evaluates C = A B as sum_{i+j<T} A_i B_j of BF16 digit slices with
+exact per-chunk FP32 accumulation, so its error is the dropped-pair truncation:
+|C_split - C|_{mn} <= (T + 1) 2^(-8T) K max_k|A_mk| max_k|B_kn| (the bound used
+below, with the row/column maxima of the operands).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_05090_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _split_gemm(A, B, T):
+    import torch
+    from paper_2509_05090_gb300 import binding
+    return _np(binding.ctm_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), "split_bf16", T))
+
+
+SHAPES = [(128, 64, 64), (200, 72, 72), (130, 100, 40), (64, 300, 520), (300, 130, 1000), (1024, 96, 4096)]
+
+
+@pytest.mark.parametrize("M,N,K", SHAPES)
+@pytest.mark.parametrize("T", [2, 3, 4, 5])
+def test_split_gemm_within_truncation_bound(ctm_lib, M, N, K, T):
+    rng = np.random.default_rng(M * 7 + N * 3 + K + T)
+    # rows and columns of very different scales exercise the per-row / per-column grids
+    A = rng.standard_normal((M, K)) * np.exp2(rng.integers(-20, 20, size=(M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp2(rng.integers(-20, 20, size=(1, N)))
+    ref = O.matmul(A, B)
+    C = _split_gemm(A, B, T)
+    bound = (T + 1) * 2.0 ** (-8 * T) * K * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=0)[None, :]
+    assert np.all(np.abs(C - ref) <= bound)
+
+
+def test_split_gemm_exact_on_small_integers(ctm_lib):
+    """Integer operands that fit the top slice are multiplied exactly."""
+    rng = np.random.default_rng(1)
+    A = rng.integers(-128, 129, size=(256, 512)).astype(np.float64)
+    B = rng.integers(-128, 129, size=(512, 96)).astype(np.float64)
+    A[:, 0] = 128.0 * np.sign(A[:, 0] + 0.5)   # fixes the row grid at 2^8
+    B[0, :] = 128.0
+    # x 2^15 on that grid needs digits d_0, d_1 (d_2 = 0), so T = 3 keeps every
+    # nonzero slice pair, including (1, 1)
+    C = _split_gemm(A, B, 3)
+    assert np.array_equal(C, A @ B)
+
+
+def test_split_gemm_zero_rows_and_ragged(ctm_lib):
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((77, 33))
+    A[5] = 0.0
+    B = rng.standard_normal((33, 19))
+    B[:, 3] = 0.0
+    C = _split_gemm(A, B, 5)
+    ref = O.matmul(A, B)
+    assert np.all(C[5] == 0.0) and np.all(C[:, 3] == 0.0)
+    assert np.max(np.abs(C - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def _ctm(A, chi, **kw):
+    from paper_2509_05090_gb300 import binding
+    return binding.CTM(A, chi, **kw)
+
+
+@pytest.mark.parametrize("T,tol", [(3, 1e-4), (4, 1e-7), (5, 1e-9)])
+def test_split_step_matches_oracle(ctm_lib, T, tol):
+    w = I.WORKLOADS["kitaev_D4_chi32"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)
+    for _ in range(3):
+        ref.step()
+    g = _ctm(A, w.chi, precision="split_bf16", n_split=T)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    ref.step()
+    g.ctm_step(1)
+    M = _np(g.ctm_get_intermediate("M"))
+    assert np.max(np.abs(M - ref.last["M"])) <= tol * np.max(np.abs(ref.last["M"]))
+    s = _np(g.ctm_get_intermediate("s"))
+    assert np.max(np.abs(s - ref.s)) <= 100 * tol
+    g.close()
+
+
+def test_split_energy_error_below_1e9(ctm_lib):
+    """Mixed precision (T = 5 slices) reaches the FP64 oracle's converged energy within 1e-9."""
+    w = I.WORKLOADS["heis_D2_chi8"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    ref = O.OracleCTM(A, w.chi)
+    ref.converge(300, 1e-12)
+    _, E_ref = ref.energy(h)
+    g = _ctm(A, w.chi, precision="split_bf16", n_split=5)
+    steps, delta, ok = g.ctm_converge(max_steps=300, tol=1e-12)
+    e, E, rho = g.ctm_energy(h)
+    assert abs(E - E_ref) <= 1e-9
+    g.close()
