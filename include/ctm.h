@@ -156,6 +156,23 @@ size_t ctm_gemm_workspace_bytes(int M, int N, int K, int precision, int n_split)
 int ctm_gemm(int M, int N, int K, const double *A_dev, const double *B_dev, double *C_dev, int precision,
              int n_split, void *workspace, size_t ws_bytes, void *stream);
 
+/* Allocation-free ctm_gemm, for callers that cannot allocate device memory
+ * (a plugin whose host framework owns every device allocation, a
+ * latency-critical loop that cannot afford an allocation or its failure
+ * mid-run, a service with a device-memory budget fixed at start-up).  The
+ * paper has no counterpart; this is a library convenience.  Same operands,
+ * precisions and result as ctm_gemm, but the scratch lives in a file-scope
+ * device array of CTM_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library holds until exit.  A shape whose scratch (ctm_gemm_workspace_bytes)
+ * exceeds that size returns CTM_ENOMEM.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress, with that device current)
+ * and caches it, so make that first call before any stream capture.  All
+ * calls share the array: each call clears what must start at zero, and calls
+ * that overlap on the GPU race, so serialise them.  Synchronous. */
+#define CTM_NOALLOC_SCRATCH_BYTES (32u << 20)
+int ctm_gemm_noalloc(int M, int N, int K, const double *A_dev, const double *B_dev, double *C_dev, int precision,
+                     int n_split, void *stream);
+
 /* Release the host context (the caller frees the workspace). */
 void ctm_destroy(ctm_ctx *ctx);
 

@@ -74,6 +74,7 @@ def load(path: str = LIB_PATH):
         "ctm_kernel_launches": (ctypes.c_ulonglong, []),
         "ctm_gemm_workspace_bytes": (ctypes.c_size_t, [I, I, I, I, I]),
         "ctm_gemm": (I, [I, I, I, P, P, P, I, I, P, ctypes.c_size_t, P]),
+        "ctm_gemm_noalloc": (I, [I, I, I, P, P, P, I, I, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -105,6 +106,23 @@ def ctm_gemm(A, B, precision="fp64", n_split=4):
                          ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     if st != CTM_OK:
         raise CtmError(st, "ctm_gemm")
+    return C
+
+
+def ctm_gemm_noalloc(A, B, precision="fp64", n_split=4):
+    """C = A B through ctm_gemm_noalloc: no workspace, the library's fixed device scratch."""
+    torch = _torch()
+    A = A.to(device="cuda", dtype=torch.float64).contiguous()
+    B = B.to(device="cuda", dtype=torch.float64).contiguous()
+    M, K = A.shape
+    K2, N = B.shape
+    assert K == K2
+    prec = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    C = torch.empty((M, N), dtype=torch.float64, device="cuda")
+    st = load().ctm_gemm_noalloc(M, N, K, _ptr(A), _ptr(B), _ptr(C), prec, int(n_split),
+                                 ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if st != CTM_OK:
+        raise CtmError(st, "ctm_gemm_noalloc")
     return C
 
 
