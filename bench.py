@@ -170,8 +170,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kh_D6_chi72")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split_bf16"])
-    ap.add_argument("--n-split", type=int, default=3)
+    ap.add_argument("--precision", default="split_bf16", choices=["fp64", "split_bf16"])
+    ap.add_argument("--n-split", type=int, default=5)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--converge-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -196,32 +198,33 @@ def main():
     A = w.site_tensor()
     h = w.hamiltonians()
     ctm = binding.CTM(A, w.chi, precision=args.precision, n_split=args.n_split)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         ctm.ctm_step(1, want_delta=False)
     torch.cuda.synchronize()
 
-    phases = {p: 0.0 for p in binding.CTM.PHASES + binding.CTM.SIDE_PHASES}
-    step_ms = []
+    # ---- timed region: K back-to-back steps (the corner spectrum of step t overlaps
+    # step t+1 as in real use).  The working set of one step (three n x n FP64
+    # intermediates plus packed operands, >= 0.2 GB at D=6, chi=72) exceeds the
+    # 129 MB L2, so no flush is inserted between steps.
+    stream = ctm.stream
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
     launches0 = binding.ctm_kernel_launches()
     wall0 = time.perf_counter()
     with ClockSampler(dev_index) as clk:
-        for _ in range(args.steps):
-            flush.fill_(1)                     # evict L2 between timed steps
-            ph = ctm.ctm_step_profiled()       # events on the context's stream around each phase
-            for k, v in ph.items():
-                phases[k] += v
-            step_ms.append(sum(v for k, v in ph.items() if k in binding.CTM.PHASES))
+        e0.record(stream)
+        ctm.ctm_step(args.steps, want_delta=False)
+        e1.record(stream)
         torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     launches = binding.ctm_kernel_launches() - launches0
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = sum(step_ms)
+    total_ms = e0.elapsed_time(e1)
     t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
     if ws > 1:
         dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
@@ -229,31 +232,88 @@ def main():
     ms_per_step = total_ms / args.steps
     value = ws * args.steps / (total_ms / 1e3)
 
-    # dominant kernel: the FP64 contraction GEMM (the four GEMM phases of the step)
+    # ---- profiled steps (same kernels, events between phases and around every
+    # contraction launch; L2 flushed before each) for the roofline of the
+    # dominant kernel, the contraction engine
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    phases = {p: 0.0 for p in binding.CTM.PHASES + binding.CTM.SIDE_PHASES}
+    nprof = max(3, min(args.steps, 10))
+    for _ in range(nprof):
+        flush.fill_(1)
+        ph = ctm.ctm_step_profiled()
+        for k, v in ph.items():
+            phases[k] += v
     peaks, src = _peaks()
-    gemm_ms = (phases["enlarged_corner"] + phases["reduced_corner"] + phases["corner"] + phases["edge"]) / args.steps
+    kern_ms = phases["gemm_kernels"] / nprof
     flops = step_gemm_flops(w.chi, w.D2)
-    achieved = flops / (gemm_ms / 1e3) / 1e12
-    peak = fp64_peak_tflops(peaks)
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": "gemm_f64_kernel (+ split-K reduce) over the step's 11 contractions",
-                "peak_source": f"{src} bf16 burst x nominal FP64/BF16 (1.25/2250)",
-                "phase_ms": {k: v / args.steps for k, v in phases.items()}}
+    if args.precision == "fp64":
+        achieved = flops / (kern_ms / 1e3) / 1e12
+        peak = fp64_peak_tflops(peaks)
+        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "kernel": "gemm_f64_kernel (+ split-K reduce): the step's 11 FP64 contractions",
+                    "peak_source": f"{src}: bf16 burst x nominal FP64/BF16 (1.25/2250); FP64 DFMA pipe, not tcgen05"}
+    else:
+        T = args.n_split
+        pairs = T * (T + 1) // 2
+        achieved = pairs * flops / (kern_ms / 1e3) / 1e12
+        peak = peaks["bf16_tflops"]
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "kernel": f"gemm_split_kernel: {pairs} BF16 slice products (T={T}) per contraction, tcgen05 "
+                              "kind::f16 into TMEM",
+                    "peak_source": f"{src} bf16 burst",
+                    "fp64_equivalent_tflops": flops / (kern_ms / 1e3) / 1e12}
+    roofline["kernel_ms_per_step"] = kern_ms
+    roofline["algorithmic_flops_per_step"] = flops
+    roofline["phase_ms"] = {k: v / nprof for k, v in phases.items()}
 
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "bf16-split",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.n_split}-split+f64",
         "data": "synthetic (seeded uniform[-1,1] site tensor, C3v-projected)",
         "config": {"workload": w.name, "d": w.d, "D": w.D, "chi": w.chi, "n": w.n,
-                   "precision": args.precision, "parallelism": "replicas" if ws > 1 else "single",
-                   "l2": "flushed (256 MB write) before every timed step"},
+                   "precision": args.precision, "n_split": args.n_split if args.precision != "fp64" else None,
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "l2": "timed steps back to back; per-step working set > L2 (no flush); profiled steps flush "
+                         "256 MB before each"},
         "roofline": roofline,
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "wall_s_timed_region": wall,
     }
+
+    # ---- mixed vs FP64 on the same GPU: same K steps from the same start, and the
+    # time to a converged environment (delta < tol) or to the step limit
+    if not args.no_compare and rank == 0:
+        ref = binding.CTM(A, w.chi, precision="fp64")
+        ref.ctm_step(args.warmup + args.steps, want_delta=False)
+        ctm2 = binding.CTM(A, w.chi, precision=args.precision, n_split=args.n_split)
+        ctm2.ctm_step(args.warmup + args.steps, want_delta=False)
+        _, E_ref, _ = ref.ctm_energy(h)
+        _, E_mix, _ = ctm2.ctm_energy(h)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(ref.stream)
+        ref.ctm_step(args.steps, want_delta=False)
+        f1.record(ref.stream)
+        torch.cuda.synchronize()
+        fp64_rate = args.steps / (f0.elapsed_time(f1) / 1e3)
+        conv = {}
+        for name, prec in (("mixed", args.precision), ("fp64", "fp64")):
+            cc = binding.CTM(A, w.chi, precision=prec, n_split=args.n_split)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            nst, dl, ok = cc.ctm_converge(max_steps=args.converge_steps, tol=w.tol, check_every=10)
+            conv[name] = {"steps": nst, "delta": dl, "converged": ok, "seconds": time.perf_counter() - t0}
+            cc.close()
+        line["mixed_vs_fp64"] = {"fp64_steps_per_s": fp64_rate, "E_site_fp64": E_ref, "E_site_mixed": E_mix,
+                                 "abs_energy_error": abs(E_mix - E_ref),
+                                 "after_steps": args.warmup + args.steps,
+                                 "time_to_converged": conv, "tol": w.tol}
+        ref.close()
+        ctm2.close()
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:

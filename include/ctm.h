@@ -132,9 +132,13 @@ int ctm_get_intermediate(const ctm_ctx *ctx, int which, double *dst_dev, size_t 
  * between its phases; synchronous.  phase_ms (nphase >= 7) receives the
  * milliseconds of: [0] enlarged corner, [1] warm start + reduced corner
  * Y = M Qs, [2] Householder QR, [3] corner renormalisation, [4] edge
- * renormalisation, [5] wait for the corner spectrum, [6] environment
- * hand-over, and (nphase >= 8) [7] the corner spectrum and delta, which run on
- * a second stream concurrently with [4]. */
+ * renormalisation, [5] wait for the previous step's corner spectrum,
+ * [6] environment hand-over, and (nphase >= 8) [7] this step's corner
+ * spectrum and delta, which run on a second stream and overlap the next step
+ * (here they are waited for before returning), and (nphase >= 9) [8] the
+ * summed time of the contraction-engine kernels alone (events around each
+ * launch: the FP64 GEMM with its split-K reduction, or the tcgen05 kernel
+ * without its operand pre-pass). */
 int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
 
 /* Number of kernel launches the library has enqueued since it was loaded

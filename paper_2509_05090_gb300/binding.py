@@ -243,15 +243,16 @@ class CTM:
         return out
 
     PHASES = ("enlarged_corner", "reduced_corner", "qr", "corner", "edge", "spectrum_wait", "handover")
-    SIDE_PHASES = ("spectrum",)
+    SIDE_PHASES = ("spectrum", "gemm_kernels")
 
     def ctm_step_profiled(self):
-        ms = (ctypes.c_double * 8)()
-        st = load().ctm_step_profiled(self._h, ms, 8)
+        ms = (ctypes.c_double * 9)()
+        st = load().ctm_step_profiled(self._h, ms, 9)
         if st != CTM_OK:
             raise CtmError(st, "ctm_step_profiled")
         out = dict(zip(self.PHASES, ms[:7]))
-        out["spectrum"] = ms[7]      # on the side stream, overlapped with "edge"
+        out["spectrum"] = ms[7]       # side stream, overlaps the next step in ctm_step
+        out["gemm_kernels"] = ms[8]   # the contraction-engine kernels alone (subset of the phases)
         return out
 
     def close(self):

@@ -96,6 +96,10 @@ struct ctm_ctx {
     cudaGraphExec_t graph;
     int graph_steps;
     int graph_failed;
+    int side_pending;
+    // kernel timing (ctm_step_profiled): events around each contraction launch
+    int prof_on, prof_n;
+    cudaEvent_t prof_ev[64];
     int steps_done;
 };
 
@@ -223,8 +227,16 @@ bool config_ok(const ctm_config *cfg)
 // The step's contractions: FP64 GEMM, or the split-BF16 tcgen05 engine.
 cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g)
 {
-    if (c->split_T > 0) return gemm_split(g, c->split_T, c->sw, c->stream);
-    return gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->stream);
+    cudaEvent_t *ev = nullptr;
+    if (c->prof_on && c->prof_n + 2 <= 64) {
+        ev = c->prof_ev + c->prof_n;
+        c->prof_n += 2;
+    }
+    if (c->split_T > 0) return gemm_split(g, c->split_T, c->sw, c->stream, ev);
+    if (ev) cudaEventRecord(ev[0], c->stream);
+    cudaError_t e = gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->stream);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    return e;
 }
 
 #define CK(expr)                                          \
@@ -320,6 +332,10 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     return CTM_OK;
 }
 
+// The corner spectrum of step t runs on the side stream while step t+1 computes;
+// it reads C (handed over at the end of step t) and must finish before step
+// t+1 overwrites C.  `side_pending` marks spectrum work not yet joined into
+// the caller's stream; every public call joins it before returning.
 int enqueue_step(ctm_ctx *c)
 {
     int rc;
@@ -328,17 +344,26 @@ int enqueue_step(ctm_ctx *c)
     if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
     if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
-    // the corner spectrum only reads C' and the old spectrum: run it beside the edge update
-    CK(cudaEventRecord(c->ev_fork, st));
-    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, c->spec_work, c->side));
-    CK(cudaEventRecord(c->ev_join, c->side));
     if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
-    CK(cudaStreamWaitEvent(st, c->ev_join, 0));
+    if (c->side_pending) CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
+    CK(cudaEventRecord(c->ev_fork, st));
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
+    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
+    CK(cudaEventRecord(c->ev_join, c->side));
+    c->side_pending = 1;
+    return CTM_OK;
+}
+
+int join_side(ctm_ctx *c)
+{
+    if (c->side_pending) {
+        CK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        c->side_pending = 0;
+    }
     return CTM_OK;
 }
 
@@ -365,19 +390,21 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     CK(cudaEventRecord(ev[3], st));
     if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
     CK(cudaEventRecord(ev[4], st));
-    CK(cudaStreamWaitEvent(c->side, ev[4], 0));
-    CK(cudaEventRecord(ev[8], c->side));
-    CK(launch_spectrum((int)chi, c->Cn, c->s_new, c->s, c->delta, c->spec_work, c->side));
-    CK(cudaEventRecord(ev[9], c->side));
     if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
     CK(cudaEventRecord(ev[5], st));
-    CK(cudaStreamWaitEvent(st, ev[9], 0));
+    if (c->side_pending) CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     CK(cudaEventRecord(ev[6], st));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
-    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaEventRecord(ev[7], st));
+    CK(cudaStreamWaitEvent(c->side, ev[7], 0));
+    CK(cudaEventRecord(ev[8], c->side));
+    CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
+    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
+    CK(cudaEventRecord(ev[9], c->side));
+    CK(cudaEventRecord(c->ev_join, c->side));
+    c->side_pending = 1;
     return CTM_OK;
 }
 
@@ -413,6 +440,7 @@ int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int 
         CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
         int rc = CTM_OK;
         for (int i = 0; i < check_every && rc == CTM_OK; ++i) rc = enqueue_step(c);
+        if (rc == CTM_OK) rc = join_side(c);
         cudaError_t e = cudaStreamEndCapture(c->stream, &g);
         if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph, g, 0);
         if (g) cudaGraphDestroy(g);
@@ -437,6 +465,7 @@ int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int 
                 int rc = enqueue_step(c);
                 if (rc != CTM_OK) return rc;
             }
+            if (join_side(c) != CTM_OK) return CTM_ECUDA;
         }
         done += chunk;
         c->steps_done += chunk;
@@ -558,6 +587,7 @@ int ctm_step(ctm_ctx *c, int nsteps, double *delta_host)
         if (rc != CTM_OK) return rc;
         c->steps_done++;
     }
+    if (join_side(c) != CTM_OK) return CTM_ECUDA;
     if (delta_host) {
         CK(cudaMemcpyAsync(delta_host, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
         int rc = read_status(c);
@@ -590,6 +620,7 @@ int ctm_converge(ctm_ctx *c, int max_steps, double tol, int check_every, int *st
 int ctm_energy(ctm_ctx *c, const double *h_dev, double *e_bond_host, double *e_site_host, double *rho_host)
 {
     if (!c || !h_dev) return CTM_EINVAL;
+    if (join_side(c) != CTM_OK) return CTM_ECUDA;
     const int chi = c->chi, D2 = c->D2, d = c->d, dd = d * d;
     const long long n = c->n;
     cudaStream_t st = c->stream;
@@ -664,6 +695,7 @@ int ctm_get_env(const ctm_ctx *c, double *C_dev, double *T_dev, double *Q_dev)
 int ctm_set_env(ctm_ctx *c, const double *C_dev, const double *T_dev, const double *Q_dev)
 {
     if (!c || !C_dev || !T_dev || !Q_dev) return CTM_EINVAL;
+    if (join_side(c) != CTM_OK) return CTM_ECUDA;
     const long long chi = c->chi, D2 = c->D2, n = c->n;
     cudaStream_t st = c->stream;
     CK(cudaMemcpyAsync(c->C, C_dev, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
@@ -711,6 +743,8 @@ void ctm_destroy(ctm_ctx *c)
     }
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->prof_ev[0])
+        for (int i = 0; i < 64; ++i) cudaEventDestroy(c->prof_ev[i]);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     delete c;
@@ -737,11 +771,18 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
     cudaEvent_t ev[10];
     for (int i = 0; i < 10; ++i)
         if (cudaEventCreate(&ev[i]) != cudaSuccess) return CTM_ECUDA;
+    if (!c->prof_ev[0])
+        for (int i = 0; i < 64; ++i)
+            if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) return CTM_ECUDA;
+    c->prof_on = 1;
+    c->prof_n = 0;
     int rc = enqueue_step_profiled(c, ev);
+    c->prof_on = 0;
     if (rc == CTM_OK) {
         c->steps_done++;
-        if (cudaEventSynchronize(ev[7]) != cudaSuccess) rc = CTM_ECUDA;
+        if (cudaEventSynchronize(ev[7]) != cudaSuccess || cudaEventSynchronize(ev[9]) != cudaSuccess) rc = CTM_ECUDA;
     }
+    if (rc == CTM_OK && join_side(c) != CTM_OK) rc = CTM_ECUDA;
     if (rc == CTM_OK) rc = read_status(c);
     if (rc == CTM_OK)
         for (int i = 0; i < 7; ++i) {
@@ -753,6 +794,15 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
         float ms = 0.f;
         if (cudaEventElapsedTime(&ms, ev[8], ev[9]) != cudaSuccess) rc = CTM_ECUDA;
         phase_ms[7] = ms;
+    }
+    if (rc == CTM_OK && nphase >= 9) {
+        double tot = 0.0;
+        for (int i = 0; i + 1 < c->prof_n; i += 2) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]) != cudaSuccess) rc = CTM_ECUDA;
+            tot += ms;
+        }
+        phase_ms[8] = tot;
     }
     for (int i = 0; i < 10; ++i) cudaEventDestroy(ev[i]);
     return rc;
@@ -809,7 +859,7 @@ int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, i
         w.partial = base + off;
         w.partial_cap = p.partial_bytes;
         w.err = err;
-        CK(gemm_split(g, n_split, w, st));
+        CK(gemm_split(g, n_split, w, st, nullptr));
     }
     int e = 0;
     CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -55,7 +55,7 @@ struct SplitWork {
 SplitPlan split_plan(int M, int N, int K, int T);
 int split_supported_T(int T);
 cudaError_t split_prepare();
-cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st);
+cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev);
 
 // ---------------------------------------------------------------- QR
 // Householder QR of Y (n x k row-major, n >= k) with diag(R) >= 0.  Q (n x k)

@@ -15,6 +15,7 @@ namespace {
 
 __device__ __forceinline__ long long off2(const Idx2 &x, int i)
 {
+    if (x.s1 == 0) return (long long)i * x.s2;   // plain strided dimension: no division
     int hi = i / x.div;
     int lo = i - hi * x.div;
     return (long long)hi * x.s1 + (long long)lo * x.s2;

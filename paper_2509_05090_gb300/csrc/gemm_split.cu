@@ -43,6 +43,7 @@ constexpr long long SP_SPIN = 4000000LL;   // x ~200 ns sleep: ~1 s
 
 __device__ __forceinline__ long long off2(const Idx2 &x, int i)
 {
+    if (x.s1 == 0) return (long long)i * x.s2;   // plain strided dimension: no division
     int hi = i / x.div;
     int lo = i - hi * x.div;
     return (long long)hi * x.s1 + (long long)lo * x.s2;
@@ -528,7 +529,7 @@ cudaError_t split_prepare()
                                 (int)split_smem_bytes<96>(5));
 }
 
-cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st)
+cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev)
 {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     if (!split_supported_T(T) || g.alpha != 1.0 || g.beta != 0.0) return cudaErrorInvalidValue;
@@ -581,11 +582,13 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st)
                 w.err};
     dim3 grid(p.nTiles, p.mTiles, p.ksplit);
     CTM_COUNT_LAUNCH(1);
+    if (ev) cudaEventRecord(ev[0], st);
     if (p.NT == 96)
         gemm_split_kernel<96><<<grid, SP_THREADS, split_smem_bytes<96>(T), st>>>(a);
     else
         gemm_split_kernel<64><<<grid, SP_THREADS, split_smem_bytes<64>(T), st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
     if (p.ksplit > 1) {
         long long total = (long long)g.M * g.N;
         CTM_COUNT_LAUNCH(1);

@@ -172,7 +172,7 @@ __global__ void scale_by_partials_kernel(long long count, double *x, const doubl
 //     changes of p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, kept in range by
 //     exact power-of-two rescaling -- no division on the dependent chain;
 // (3) one CTA: |lambda| sorted descending by rank, unit 2-norm, delta.
-constexpr int SPEC_WARPS = 8;
+constexpr int SPEC_WARPS = 1;   // one eigenvalue per CTA: the chi Sturm chains spread over chi SMs
 
 __global__ void tridiag_kernel(int chi, const double *C, double *work)
 {
