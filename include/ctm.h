@@ -115,6 +115,26 @@ int ctm_converge(ctm_ctx *ctx, int max_steps, double tol, int check_every,
 int ctm_energy(ctm_ctx *ctx, const double *h_dev, double *e_bond_host, double *e_site_host,
                double *rho_host);
 
+/* Sec. II.D: energy gradient by a hand-written adjoint.  From the current
+ * environment, run `warmup` steps (treated as constants, in the context's
+ * precision), then k_tracked steps in FP64 whose inputs are checkpointed, then
+ * the energy of ctm_energy.  The adjoint recomputes each tracked step from its
+ * checkpoint and back-propagates through every contraction, the Householder
+ * QR (Y-bar = (Q-bar + Q copyltu(-Q-bar^T Q)) R^{-T}, the triangular solve
+ * regularised as R_ii / (R_ii^2 + (1e-13 R_00)^2)), the corner and edge
+ * normalisations, the double and open layers, and the C3v projection and
+ * normalisation of ctm_init.  The environment entering the tracked steps is
+ * held fixed (its dependence on A is not differentiated); the warm-start sign
+ * diag(sgn C_ii) is piecewise constant.  h_dev as in ctm_energy.  dA_dev
+ * (device, layout of A) receives dE_site/dA for the raw tensor passed to
+ * ctm_init; energy_host (may be NULL) the energy.  gws: device workspace of
+ * ctm_grad_workspace_bytes(ctx, k_tracked) bytes (256-byte aligned).  On
+ * return the context holds the environment after the tracked steps.
+ * Synchronous. */
+size_t ctm_grad_workspace_bytes(const ctm_ctx *ctx, int k_tracked);
+int ctm_grad(ctm_ctx *ctx, int warmup, int k_tracked, const double *h_dev, void *gws, size_t gws_bytes,
+             double *energy_host, double *dA_dev);
+
 /* Copy the current environment out / in (device pointers; parity checks and
  * resume).  C: chi x chi, T: chi x D2 x chi, Q: n x chi. */
 int ctm_get_env(const ctm_ctx *ctx, double *C_dev, double *T_dev, double *Q_dev);

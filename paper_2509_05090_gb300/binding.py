@@ -75,6 +75,8 @@ def load(path: str = LIB_PATH):
         "ctm_gemm_workspace_bytes": (ctypes.c_size_t, [I, I, I, I, I]),
         "ctm_gemm": (I, [I, I, I, P, P, P, I, I, P, ctypes.c_size_t, P]),
         "ctm_gemm_noalloc": (I, [I, I, I, P, P, P, I, I, P]),
+        "ctm_grad_workspace_bytes": (ctypes.c_size_t, [P, I]),
+        "ctm_grad": (I, [P, I, I, P, P, ctypes.c_size_t, dp, P]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -208,6 +210,24 @@ class CTM:
         if st != CTM_OK:
             raise CtmError(st, "ctm_energy")
         return np.array(e[:]), es.value, np.array(rho[:]).reshape(dd, dd)
+
+    def ctm_grad(self, h, warmup=10, k_tracked=24):
+        """(E_site, dE/dA) by the hand-written adjoint; dA has the layout of the raw A given to ctm_init."""
+        torch = _torch()
+        if isinstance(h, np.ndarray):
+            h = torch.from_numpy(np.ascontiguousarray(h, dtype=np.float64))
+        h = h.to(device="cuda", dtype=torch.float64).contiguous()
+        nbytes = int(load().ctm_grad_workspace_bytes(self._h, int(k_tracked)))
+        if nbytes == 0:
+            raise CtmError(1, "ctm_grad_workspace_bytes")
+        gws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        dA = torch.empty_like(self._A)
+        E = ctypes.c_double()
+        st = load().ctm_grad(self._h, int(warmup), int(k_tracked), _ptr(h), _ptr(gws), nbytes, ctypes.byref(E),
+                             _ptr(dA))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_grad")
+        return E.value, dA
 
     def ctm_get_env(self):
         torch = _torch()

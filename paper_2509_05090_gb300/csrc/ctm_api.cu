@@ -8,7 +8,7 @@
 #include <new>
 #include <vector>
 
-#include "ctm_internal.h"
+#include "ctm_ctx.h"
 
 namespace {
 
@@ -60,50 +60,11 @@ __global__ void rho_final_kernel(int nblocks, int dd, const double *partials, do
 constexpr int RHO_BLOCKS = 256;
 constexpr int NORM_BLOCKS = 256;
 
-size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 
-struct ctm_ctx {
-    ctm_config cfg;
-    int d, D, D2, chi;
-    long long n;
-    cudaStream_t stream;      // the caller's stream
-    cudaStream_t own;         // private stream used for graph capture and replay
-    cudaEvent_t ev_in, ev_out;
-    cudaStream_t side;        // corner spectrum runs here, overlapped with the edge update
-    cudaEvent_t ev_fork, ev_join;
-    // FP64 buffers (device, inside the caller's workspace)
-    double *A, *a;
-    double *C, *Cn, *Cr;
-    double *T, *Tn;
-    double *Q, *Qn, *Qs, *Y, *W, *MQ;
-    double *R;
-    double *M, *X, *H;
-    double *Y1;
-    double *s, *s_new, *delta, *spec_work;
-    double *splitk;
-    size_t splitk_elems;
-    int split_T;              // 0: FP64 contractions; 2..5: split-BF16 slices per operand
-    SplitWork sw;
-    double *qr_sbuf, *qr_rowbuf;
-    unsigned *qr_bar;
-    int *err, *flag;
-    double *norm_part;
-    // energy
-    double *b, *Y1o, *G2, *P5a, *P5b, *rho_part, *rho_raw, *eout, *h;
-    // graph of `graph_steps` steps
-    cudaGraphExec_t graph;
-    int graph_steps;
-    int graph_failed;
-    int side_pending;
-    // kernel timing (ctm_step_profiled): events around each contraction launch
-    int prof_on, prof_n;
-    cudaEvent_t prof_ev[64];
-    int steps_done;
-};
 
-namespace {
+namespace ctmi {
 
 struct Shape {
     int M, N, K;
@@ -129,6 +90,7 @@ size_t layout(ctm_ctx *c, char *base)
         return p;
     };
     auto td = [&](long long count) -> double * { return (double *)take(sizeof(double) * (size_t)count); };
+    c->Araw = td(d * c->D * c->D * c->D);
     c->A = td(d * c->D * c->D * c->D);
     c->a = td(D2 * D2 * D2);
     c->C = td(chi * chi);
@@ -234,7 +196,7 @@ cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g)
     }
     if (c->split_T > 0) return gemm_split(g, c->split_T, c->sw, c->stream, ev);
     if (ev) cudaEventRecord(ev[0], c->stream);
-    cudaError_t e = gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->stream);
+    cudaError_t e = gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, c->stream);
     if (ev) cudaEventRecord(ev[1], c->stream);
     return e;
 }
@@ -482,7 +444,21 @@ int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int 
     return (delta < tol) ? CTM_OK : CTM_ENOTCONVERGED;
 }
 
-}  // namespace
+cudaError_t rho_reduce(ctm_ctx *c)
+{
+    const int dd = c->d * c->d;
+    CTM_COUNT_LAUNCH(2);
+    rho_partial_kernel<<<RHO_BLOCKS, 256, 0, c->stream>>>((long long)c->chi * c->chi, dd, c->D2, c->Y1o, c->G2,
+                                                         c->rho_part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    rho_final_kernel<<<1, 128, 0, c->stream>>>(RHO_BLOCKS, dd, c->rho_part, c->rho_raw);
+    return cudaGetLastError();
+}
+
+}  // namespace ctmi
+
+using namespace ctmi;
 
 extern "C" {
 
@@ -551,6 +527,11 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
             break;
         }
         if (cudaMemsetAsync(c->err, 0, sizeof(int), st) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (cudaMemcpyAsync(c->Araw, A_dev, sizeof(double) * c->d * c->D * c->D * c->D, cudaMemcpyDeviceToDevice,
+                            st) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
         if (launch_c3v_project_normalize(c->d, c->D, A_dev, c->A, cfg->symmetrize ? 1 : 0, st) != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
@@ -638,34 +619,31 @@ int ctm_energy(ctm_ctx *c, const double *h_dev, double *e_bond_host, double *e_s
         double *dst = bufs[p & 1];
         g = GemmF64{chi, chi, chi, src, idx_lin(chi), idx_lin(1), c->Cn, idx_lin(chi), idx_lin(1), dst,
                     idx_lin(chi), idx_lin(1), 1.0, 0.0};
-        CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+        CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
         src = dst;
     }
     // E = Q P5 Q^T  (n x n, symmetric) into H
     g = GemmF64{(int)n, chi, chi, c->Qn, idx_lin(chi), idx_lin(1), src, idx_lin(chi), idx_lin(1), c->W,
                 idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
     g = GemmF64{(int)n, (int)n, chi, c->W, idx_lin(chi), idx_lin(1), c->Qn, idx_lin(1), idx_lin(chi), c->H,
                 idx_lin(n), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
     // open layers b[p][..] = A[s] (x) A[t], p = s*d + t
     CK(launch_open_layers(d, c->D, c->A, c->b, st));
     const long long D3 = (long long)D2 * D2 * D2;
     // Y1o[(a,b)][(pB,z)] = sum_{u,l} X'[(a,b),(u,l)] b[pB][u][l][z]
     g = GemmF64{chi * chi, dd * D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->b, idx_lin(D2),
                 idx_split(D2, D3, 1), c->Y1o, idx_lin((long long)dd * D2), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
     // G2[(a,b)][(pA,z)] = sum_{x,y} E[(a,y),(b,x)] b[pA][z][x][y]
     g = GemmF64{chi * chi, dd * D2, D2 * D2, c->H, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n),
                 c->b, idx_lin(1), idx_split(D2, D3, (long long)D2 * D2), c->G2, idx_lin((long long)dd * D2),
                 idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, st));
+    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
     CTM_COUNT_LAUNCH(1);
-    rho_partial_kernel<<<RHO_BLOCKS, 256, 0, st>>>((long long)chi * chi, dd, D2, c->Y1o, c->G2, c->rho_part);
-    CK(cudaGetLastError());
-    CTM_COUNT_LAUNCH(1);
-    rho_final_kernel<<<1, 128, 0, st>>>(RHO_BLOCKS, dd, c->rho_part, c->rho_raw);
-    CK(cudaGetLastError());
+    CK(rho_reduce(c));
+
     CK(launch_bond_energy(d, c->rho_raw, h_dev, c->eout, st));
     double host[4 + RHO_MAX_DD * RHO_MAX_DD];
     CK(cudaMemcpyAsync(host, c->eout, sizeof(double) * (4 + dd * dd), cudaMemcpyDeviceToHost, st));
@@ -839,7 +817,7 @@ int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, i
     GemmF64 g{M, N, K, A, idx_lin(K), idx_lin(1), B, idx_lin(N), idx_lin(1), C, idx_lin(N), idx_lin(1), 1.0, 0.0};
     CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     if (precision == CTM_FP64) {
-        CK(gemm_f64(g, gemm_f64_pick_split(M, N, K), (double *)(base + off), st));
+        CK(gemm_f64(g, gemm_f64_pick_split(M, N, K), (double *)(base + off), (ws_bytes - off) / sizeof(double), st));
     } else {
         if (split_prepare() != cudaSuccess) return CTM_ECUDA;
         SplitPlan p = split_plan(M, N, K, n_split);

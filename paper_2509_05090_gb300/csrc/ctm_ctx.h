@@ -1,0 +1,55 @@
+// The context behind the C ABI's opaque ctm_ctx, shared by the translation
+// units that enqueue work for it (ctm_api.cu: the step and the energy;
+// ctm_grad.cu: the adjoint).
+#pragma once
+
+#include "ctm_internal.h"
+
+inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct ctm_ctx {
+    ctm_config cfg;
+    int d, D, D2, chi;
+    long long n;
+    cudaStream_t stream;      // the caller's stream
+    cudaStream_t own;         // private stream used for graph capture and replay
+    cudaEvent_t ev_in, ev_out;
+    cudaStream_t side;        // corner spectrum runs here, overlapped with the edge update
+    cudaEvent_t ev_fork, ev_join;
+    // FP64 buffers (device, inside the caller's workspace)
+    double *Araw, *A, *a;
+    double *C, *Cn, *Cr;
+    double *T, *Tn;
+    double *Q, *Qn, *Qs, *Y, *W, *MQ;
+    double *R;
+    double *M, *X, *H;
+    double *Y1;
+    double *s, *s_new, *delta, *spec_work;
+    double *splitk;
+    size_t splitk_elems;
+    int split_T;              // 0: FP64 contractions; 2..5: split-BF16 slices per operand
+    SplitWork sw;
+    double *qr_sbuf, *qr_rowbuf;
+    unsigned *qr_bar;
+    int *err, *flag;
+    double *norm_part;
+    // energy
+    double *b, *Y1o, *G2, *P5a, *P5b, *rho_part, *rho_raw, *eout, *h;
+    // graph of `graph_steps` steps
+    cudaGraphExec_t graph;
+    int graph_steps;
+    int graph_failed;
+    int side_pending;
+    // kernel timing (ctm_step_profiled): events around each contraction launch
+    int prof_on, prof_n;
+    cudaEvent_t prof_ev[64];
+    int steps_done;
+};
+
+namespace ctmi {
+cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g);
+int enqueue_enlarged_corner(ctm_ctx *c);
+int join_side(ctm_ctx *c);
+int read_status(ctm_ctx *c);
+cudaError_t rho_reduce(ctm_ctx *c);   // raw[pB][pA] = sum Y1o G2 (energy contraction)
+}  // namespace ctmi

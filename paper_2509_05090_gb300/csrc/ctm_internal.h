@@ -32,8 +32,9 @@ struct GemmF64 {
     double alpha, beta;
 };
 
-// Launch a FP64 GEMM; split-K (ksplit > 1) uses `scratch` (>= ksplit*M*N doubles).
-cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st);
+// Launch a FP64 GEMM; split-K (ksplit > 1) uses `scratch` of scratch_elems doubles
+// (the split is reduced so that ksplit*M*N fits).
+cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, size_t scratch_elems, cudaStream_t st);
 // Number of K-splits gemm_f64 picks for this shape (1 = none) and the scratch it needs.
 int gemm_f64_pick_split(int M, int N, int K);
 

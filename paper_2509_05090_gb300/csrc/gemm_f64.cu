@@ -238,9 +238,14 @@ static cudaError_t launch_tile(const GemmF64 &g, int ksplit, double *scratch, cu
     return cudaGetLastError();
 }
 
-cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)
+cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, size_t scratch_elems, cudaStream_t st)
 {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    // never let the split-K partials outgrow the scratch the caller owns
+    const size_t per_split = (size_t)g.M * (size_t)g.N;
+    if (ksplit > 1 && (!scratch || (size_t)ksplit * per_split > scratch_elems))
+        ksplit = scratch ? (int)(scratch_elems / per_split) : 1;
+    if (ksplit < 1) ksplit = 1;
     TileCfg t = pick_tile(g.M, g.N, g.K);
 #define CTM_TILE(a, b, c) \
     if (t.bm == a && t.bn == b && t.bk == c) return launch_tile<a, b, c>(g, ksplit, scratch, st);
