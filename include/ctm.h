@@ -197,6 +197,27 @@ int ctm_gemm(int M, int N, int K, const double *A_dev, const double *B_dev, doub
 int ctm_gemm_noalloc(int M, int N, int K, const double *A_dev, const double *B_dev, double *C_dev, int precision,
                      int n_split, void *stream);
 
+/* Ragged batch of independent instances (Sec. III.B's slicing and a
+ * parameter sweep run side by side): count configurations (D, chi may
+ * differ) with site tensors A_dev[i].  Each instance owns a context, a slice
+ * of the caller's workspace (ctm_batch_workspace_bytes) and a stream.
+ * ctm_batch_step advances every instance by nsteps steps: the first call runs
+ * one step eagerly, timing the split engine's candidate tile shapes for every
+ * contraction shape of the batch (autotuner, cached per shape), then captures
+ * one batched step -- all instances' kernels, concurrent across their
+ * streams -- as a CUDA graph, so each further batched step is one graph
+ * launch.  max_delta_host (may be NULL) receives the largest delta and makes
+ * the call synchronous.  ctm_batch_ctx exposes instance i's context (after
+ * synchronising the batch) for ctm_energy, ctm_get_env and the like; it stays
+ * owned by the batch. */
+typedef struct ctm_batch ctm_batch;
+size_t ctm_batch_workspace_bytes(const ctm_config *cfgs, int count);
+int ctm_batch_init(const ctm_config *cfgs, int count, const double *const *A_dev, void *workspace, size_t ws_bytes,
+                   void *stream, ctm_batch **out);
+int ctm_batch_step(ctm_batch *batch, int nsteps, double *max_delta_host);
+int ctm_batch_ctx(ctm_batch *batch, int i, ctm_ctx **ctx);
+void ctm_batch_destroy(ctm_batch *batch);
+
 /* Release the host context (the caller frees the workspace). */
 void ctm_destroy(ctm_ctx *ctx);
 

@@ -76,6 +76,11 @@ def load(path: str = LIB_PATH):
         "ctm_gemm": (I, [I, I, I, P, P, P, I, I, P, ctypes.c_size_t, P]),
         "ctm_gemm_noalloc": (I, [I, I, I, P, P, P, I, I, P]),
         "ctm_grad_workspace_bytes": (ctypes.c_size_t, [P, I]),
+        "ctm_batch_workspace_bytes": (ctypes.c_size_t, [P, I]),
+        "ctm_batch_init": (I, [P, I, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+        "ctm_batch_step": (I, [P, I, dp]),
+        "ctm_batch_ctx": (I, [P, I, ctypes.POINTER(P)]),
+        "ctm_batch_destroy": (None, [P]),
         "ctm_grad": (I, [P, I, I, P, P, ctypes.c_size_t, dp, P]),
     }
     for name, (res, args) in sigs.items():
@@ -279,6 +284,79 @@ class CTM:
         if getattr(self, "_h", None):
             self.stream.synchronize()
             load().ctm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class _CtxView(CTM):
+    """A context owned by a batch (no workspace of its own; not destroyed here)."""
+
+    def __init__(self, handle, d, D, chi, A, stream):
+        self._h = handle
+        self.d, self.D, self.chi = d, D, chi
+        self.D2 = D * D
+        self.n = chi * self.D2
+        self._A = A
+        self.stream = stream
+
+    def close(self):
+        self._h = None
+
+
+class CTMBatch:
+    """Ragged batch of instances advanced together (ctm_batch_* of include/ctm.h)."""
+
+    def __init__(self, tensors, chis, precision="split_bf16", n_split=5, tol=1e-10, max_steps=200, stream=None):
+        torch = _torch()
+        lib = load()
+        As = []
+        for A in tensors:
+            if isinstance(A, np.ndarray):
+                A = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float64))
+            As.append(A.to(device="cuda", dtype=torch.float64).contiguous())
+        self._A = As
+        cfgs = (ctm_config * len(As))(*[make_config(A.shape[0], A.shape[1], chi, precision, n_split, tol, max_steps)
+                                        for A, chi in zip(As, chis)])
+        self._cfgs = cfgs
+        self.chis = [int(c) for c in chis]
+        nbytes = int(lib.ctm_batch_workspace_bytes(ctypes.cast(cfgs, ctypes.c_void_p), len(As)))
+        if nbytes == 0:
+            raise CtmError(1, "ctm_batch_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        ptrs = (ctypes.c_void_p * len(As))(*[A.data_ptr() for A in As])
+        h = ctypes.c_void_p()
+        st = lib.ctm_batch_init(ctypes.cast(cfgs, ctypes.c_void_p), len(As), ctypes.cast(ptrs, ctypes.c_void_p),
+                                _ptr(self.workspace), nbytes, ctypes.c_void_p(self.stream.cuda_stream),
+                                ctypes.byref(h))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_batch_init")
+        self._h = h
+
+    def ctm_batch_step(self, nsteps=1, want_delta=False):
+        d = ctypes.c_double(float("nan"))
+        st = load().ctm_batch_step(self._h, int(nsteps), ctypes.byref(d) if want_delta else None)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_batch_step")
+        return d.value if want_delta else None
+
+    def instance(self, i):
+        h = ctypes.c_void_p()
+        st = load().ctm_batch_ctx(self._h, int(i), ctypes.byref(h))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_batch_ctx")
+        A = self._A[i]
+        return _CtxView(h, int(A.shape[0]), int(A.shape[1]), self.chis[i], A, self.stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            load().ctm_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -152,7 +152,7 @@ size_t layout(ctm_ctx *c, char *base)
         size_t ap = 0, bp = 0, pp = 0;
         long long ecap = 0;
         for (const auto &sh : step_shapes(c)) {
-            SplitPlan pl = split_plan(sh.M, sh.N, sh.K, c->split_T);
+            SplitPlan pl = split_plan_caps(sh.M, sh.N, sh.K, c->split_T);
             if (pl.a_pack_bytes > ap) ap = pl.a_pack_bytes;
             if (pl.b_pack_bytes > bp) bp = pl.b_pack_bytes;
             if (pl.partial_bytes > pp) pp = pl.partial_bytes;
@@ -169,6 +169,7 @@ size_t layout(ctm_ctx *c, char *base)
         c->sw.partial = (void *)take(pp + 8);
         c->sw.partial_cap = pp;
         c->sw.err = c->err;
+        c->sw.autotune = 0;
     }
     return off;
 }
@@ -245,7 +246,7 @@ int enqueue_projector(ctm_ctx *c, double *Qout)
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
               c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
     CK(run_gemm(c, g));
-    QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err};
+    QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err, c->qr_rows_min};
     CK(qr_householder((int)n, chi, c->Y, Qout, c->R, qs, st));
     return CTM_OK;
 }
@@ -346,7 +347,7 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     }
     CK(cudaEventRecord(ev[2], st));
     {
-        QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err};
+        QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err, c->qr_rows_min};
         CK(qr_householder((int)n, (int)chi, c->Y, c->Qn, c->R, qs, st));
     }
     CK(cudaEventRecord(ev[3], st));
@@ -496,6 +497,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     c->chi = cfg->chi;
     c->n = (long long)c->chi * c->D2;
     c->split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
+    c->qr_rows_min = 1;
     c->stream = (cudaStream_t)stream;
     if (!qr_supported((int)c->n, c->chi)) {
         delete c;
@@ -837,6 +839,7 @@ int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, i
         w.partial = base + off;
         w.partial_cap = p.partial_bytes;
         w.err = err;
+        w.autotune = 0;
         CK(gemm_split(g, n_split, w, st, nullptr));
     }
     int e = 0;

@@ -42,6 +42,7 @@ struct ctm_ctx {
     int side_pending;
     // kernel timing (ctm_step_profiled): events around each contraction launch
     int prof_on, prof_n;
+    int qr_rows_min;          // 1 for a lone instance; larger inside a batch
     cudaEvent_t prof_ev[64];
     int steps_done;
 };
@@ -49,6 +50,7 @@ struct ctm_ctx {
 namespace ctmi {
 cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g);
 int enqueue_enlarged_corner(ctm_ctx *c);
+int enqueue_step(ctm_ctx *c);
 int join_side(ctm_ctx *c);
 int read_status(ctm_ctx *c);
 cudaError_t rho_reduce(ctm_ctx *c);   // raw[pB][pA] = sum Y1o G2 (energy contraction)

@@ -52,8 +52,11 @@ struct SplitWork {
     void *partial;
     size_t partial_cap;
     int *err;
+    int autotune;      // time the candidate tile shapes / K-splits of a new shape once (eager only)
 };
-SplitPlan split_plan(int M, int N, int K, int T);
+SplitPlan split_plan(int M, int N, int K, int T, int nt_override = 0, int ks_override = 0);
+// Largest pack / accumulator sizes over every plan the autotuner may pick.
+SplitPlan split_plan_caps(int M, int N, int K, int T);
 int split_supported_T(int T);
 cudaError_t split_prepare();
 cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev);
@@ -67,6 +70,7 @@ struct QrScratch {
     double *rowbuf;    // 2 * k
     unsigned *bar;     // 2 (count, generation)
     int *err;          // 1
+    int rows_min;      // fewest rows per CTA (batched instances use small grids so they overlap)
 };
 size_t qr_scratch_doubles(int k);
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,

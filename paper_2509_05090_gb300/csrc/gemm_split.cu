@@ -29,6 +29,8 @@
 // kernel raises an error flag, stops issuing work, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
+#include <vector>
+
 #include "ctm_internal.h"
 
 namespace {
@@ -497,10 +499,10 @@ size_t split_smem_bytes(int T)
 
 int split_supported_T(int T) { return T >= 2 && T <= 5; }
 
-SplitPlan split_plan(int M, int N, int K, int T)
+SplitPlan split_plan(int M, int N, int K, int T, int nt_override, int ks_override)
 {
     SplitPlan p{};
-    p.NT = pick_nt(N, T);
+    p.NT = (nt_override == 64 || (nt_override == 96 && T * 96 <= 512)) ? nt_override : pick_nt(N, T);
     p.mTiles = (M + SP_BM - 1) / SP_BM;
     p.nTiles = (N + p.NT - 1) / p.NT;
     p.kTiles = (K + SP_BK - 1) / SP_BK;
@@ -508,16 +510,31 @@ SplitPlan split_plan(int M, int N, int K, int T)
     const long long tiles = (long long)p.mTiles * p.nTiles;
     int ks = 1;
     const int sms = device_sm_count();
-    if (tiles < sms && chunks > 1) {
+    if (ks_override > 0) {
+        ks = ks_override;
+    } else if (tiles < sms && chunks > 1) {
         ks = (int)((sms + tiles - 1) / tiles);
-        if (ks > chunks) ks = chunks;
     }
+    if (ks > chunks) ks = chunks;
+    if (ks < 1) ks = 1;
     p.chunks_per_split = (chunks + ks - 1) / ks;
     p.ksplit = (chunks + p.chunks_per_split - 1) / p.chunks_per_split;
     p.a_pack_bytes = (size_t)T * p.mTiles * p.kTiles * SP_BM * SP_BK * 2;
     p.b_pack_bytes = (size_t)T * p.nTiles * p.kTiles * p.NT * SP_BK * 2;
     p.partial_bytes = p.ksplit > 1 ? (size_t)M * N * 8 : 0;
     return p;
+}
+
+SplitPlan split_plan_caps(int M, int N, int K, int T)
+{
+    SplitPlan c = split_plan(M, N, K, T);
+    for (int nt : {64, 96}) {
+        SplitPlan p = split_plan(M, N, K, T, nt, 0);
+        if (p.b_pack_bytes > c.b_pack_bytes) c.b_pack_bytes = p.b_pack_bytes;
+    }
+    const int kTiles = (K + SP_BK - 1) / SP_BK;
+    if (kTiles > SP_KT_PER_CHUNK) c.partial_bytes = (size_t)M * N * 8;   // any split-K candidate
+    return c;
 }
 
 cudaError_t split_prepare()
@@ -529,11 +546,9 @@ cudaError_t split_prepare()
                                 (int)split_smem_bytes<96>(5));
 }
 
-cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev)
+static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
+                                  SplitPlan p)
 {
-    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
-    if (!split_supported_T(T) || g.alpha != 1.0 || g.beta != 0.0) return cudaErrorInvalidValue;
-    SplitPlan p = split_plan(g.M, g.N, g.K, T);
     if (p.a_pack_bytes > w.a_pack_cap || p.b_pack_bytes > w.b_pack_cap || p.partial_bytes > w.partial_cap ||
         g.M > w.e_cap || g.N > w.e_cap)
         return cudaErrorInvalidValue;
@@ -598,3 +613,82 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
     }
     return e;
 }
+
+// ---------------------------------------------------------------- autotuner
+// For each new (M, N, K, T) the first eager call times every candidate plan
+// (N tile 64 / 96, K-split auto, 1, 2x, 1/2x) end to end on the real operands
+// with CUDA events, keeps the fastest, and re-runs it so the output is valid.
+// The choice is cached for the process; captured calls use the cache or the
+// default plan.
+#include <map>
+#include <mutex>
+#include <tuple>
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
+}  // namespace
+
+cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev)
+{
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    if (!split_supported_T(T) || g.alpha != 1.0 || g.beta != 0.0) return cudaErrorInvalidValue;
+    const auto key = std::make_tuple(g.M, g.N, g.K, T);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end())
+            return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, it->second.first, it->second.second));
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (!w.autotune || cs != cudaStreamCaptureStatusNone)
+        return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T));
+    SplitPlan base = split_plan(g.M, g.N, g.K, T);
+    const int chunks = (base.kTiles + SP_KT_PER_CHUNK - 1) / SP_KT_PER_CHUNK;
+    std::vector<std::pair<int, int>> cands;
+    for (int nt : {64, 96}) {
+        if (nt == 96 && T * 96 > 512) continue;
+        for (int ks : {base.ksplit, 1, 2 * base.ksplit, base.ksplit / 2}) {
+            if (ks < 1 || ks > chunks) continue;
+            std::pair<int, int> c{nt, ks};
+            bool dup = false;
+            for (auto &o : cands) dup |= (o == c);
+            if (!dup) cands.push_back(c);
+        }
+    }
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return cudaErrorUnknown;
+    float best = 1e30f;
+    std::pair<int, int> best_c{base.NT, base.ksplit};
+    for (auto &cnd : cands) {
+        SplitPlan p = split_plan(g.M, g.N, g.K, T, cnd.first, cnd.second);
+        if (p.a_pack_bytes > w.a_pack_cap || p.b_pack_bytes > w.b_pack_cap || p.partial_bytes > w.partial_cap) continue;
+        float ms = 0.f, tot = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {   // first run warms caches and the instruction stream
+            cudaEventRecord(e0, st);
+            cudaError_t e = gemm_split_run(g, T, w, st, nullptr, p);
+            cudaEventRecord(e1, st);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return e != cudaSuccess ? e : cudaErrorUnknown;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) tot = ms;
+        }
+        if (tot < best) {
+            best = tot;
+            best_c = cnd;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = best_c;
+    }
+    return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, best_c.first, best_c.second));
+}
+
+int split_autotuned_shapes() { return (int)g_tune.size(); }

@@ -199,10 +199,11 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
 
 size_t qr_smem_bytes(int rows_per, int k) { return sizeof(double) * ((size_t)2 * rows_per * k + 6 * (size_t)k); }
 
-int qr_layout(int n, int k, int *G_out, int *rows_out)
+int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
 {
     int sms = device_sm_count();
     int rows_per = (n + sms - 1) / sms;
+    if (rows_per < rows_min) rows_per = rows_min;
     if (rows_per < 1) rows_per = 1;
     int G = (n + rows_per - 1) / rows_per;
     *G_out = G;
@@ -217,13 +218,15 @@ size_t qr_scratch_doubles(int k) { return (size_t)5 * k + 8; }
 int qr_supported(int n, int k)
 {
     int G, rp;
-    return n >= k && k >= 1 && qr_layout(n, k, &G, &rp);
+    return n >= k && k >= 1 && qr_layout(n, k, 1, &G, &rp);
 }
 
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s, cudaStream_t st)
 {
     int G, rows_per;
-    if (!qr_layout(n, k, &G, &rows_per)) return cudaErrorInvalidValue;
+    if (!qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rows_per)) {
+        if (!qr_layout(n, k, 1, &G, &rows_per)) return cudaErrorInvalidValue;
+    }
     size_t smem = qr_smem_bytes(rows_per, k);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel, QR_THREADS, smem);
