@@ -133,6 +133,7 @@ size_t layout(ctm_ctx *c, char *base)
     c->splitk = td((long long)sk + 1);
     c->qr_sbuf = td((long long)qr_scratch_doubles((int)chi));
     c->qr_rowbuf = td(2 * chi);
+    c->qr_wy = td((long long)qr_wy_doubles((int)n, (int)chi));
     c->qr_bar = (unsigned *)take(64);
     c->err = (int *)take(64);
     c->flag = (int *)take(64);
@@ -170,6 +171,14 @@ size_t layout(ctm_ctx *c, char *base)
         c->sw.partial_cap = pp;
         c->sw.err = c->err;
         c->sw.autotune = 0;
+        const Shape ash[2] = {{(int)(chi * chi), (int)D2, (int)(D2 * D2)}, {(int)(chi * chi), (int)(D2 * D2), (int)D2}};
+        for (int sl = 0; sl < 2; ++sl) {
+            SplitPlan pl = split_plan_caps(ash[sl].M, ash[sl].N, ash[sl].K, c->split_T);
+            c->apk[sl] = (unsigned char *)take(pl.b_pack_bytes);
+            c->apk_cap[sl] = pl.b_pack_bytes;
+            c->ape[sl] = (int *)take(sizeof(int) * (size_t)ash[sl].N);
+            c->apk_state[sl] = 0;
+        }
     }
     return off;
 }
@@ -188,14 +197,25 @@ bool config_ok(const ctm_config *cfg)
 }
 
 // The step's contractions: FP64 GEMM, or the split-BF16 tcgen05 engine.
-cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g)
+cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint)
 {
     cudaEvent_t *ev = nullptr;
     if (c->prof_on && c->prof_n + 2 <= 64) {
         ev = c->prof_ev + c->prof_n;
         c->prof_n += 2;
     }
-    if (c->split_T > 0) return gemm_split(g, c->split_T, c->sw, c->stream, ev);
+    if (c->split_T > 0) {
+        SplitOpts o{};
+        if (hint == GEMM_REUSE_A) o.reuse_a = 1;
+        if (hint == GEMM_B_IS_A_LZ || hint == GEMM_B_IS_A_ZX) {
+            const int slot = hint == GEMM_B_IS_A_LZ ? 0 : 1;
+            o.b_pk = c->apk[slot];
+            o.b_e = c->ape[slot];
+            o.b_cap = c->apk_cap[slot];
+            o.b_state = &c->apk_state[slot];
+        }
+        return gemm_split(g, c->split_T, c->sw, c->stream, ev, &o);
+    }
     if (ev) cudaEventRecord(ev[0], c->stream);
     cudaError_t e = gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, c->stream);
     if (ev) cudaEventRecord(ev[1], c->stream);
@@ -228,11 +248,11 @@ int enqueue_enlarged_corner(ctm_ctx *c)
     // Y1 = X' a   (chi^2 x D2^2) (D2^2 x D2)
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, GEMM_B_IS_A_LZ));
     // M[(a,y)][(b,x)] = Y1[(a,b), z] a[z, (x,y)]
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
                 idx_lin(1), c->M, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, GEMM_B_IS_A_ZX));
     return CTM_OK;
 }
 
@@ -246,7 +266,7 @@ int enqueue_projector(ctm_ctx *c, double *Qout)
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
               c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
     CK(run_gemm(c, g));
-    QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err, c->qr_rows_min};
+    QrScratch qs = qr_scratch(c);
     CK(qr_householder((int)n, chi, c->Y, Qout, c->R, qs, st));
     return CTM_OK;
 }
@@ -257,9 +277,10 @@ int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout)
     const int chi = c->chi;
     const long long n = c->n;
     cudaStream_t st = c->stream;
+    // the previous split contraction was Y = M Qs (only the QR in between): M is already packed
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), Qp, idx_lin(chi), idx_lin(1),
               c->MQ, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, GEMM_REUSE_A));
     g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
                 c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
     CK(run_gemm(c, g));
@@ -281,12 +302,12 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, GEMM_B_IS_A_LZ));
     // H3'[a][y][x][j] = H2[(a,j),z] a[z,(x,y)]
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
                 idx_lin(1), c->H, idx_split(chi, (long long)D2 * D2 * chi, 1), idx_split(D2, chi, (long long)D2 * chi),
                 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, GEMM_B_IS_A_ZX));
     // T'[i][(x,j)] = sum_{(a,y)} Q[(a,y),i] H3'[(a,y),(x,j)]
     g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),
                 Tout, idx_lin(n), idx_lin(1), 1.0, 0.0};
@@ -347,7 +368,7 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     }
     CK(cudaEventRecord(ev[2], st));
     {
-        QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err, c->qr_rows_min};
+        QrScratch qs = qr_scratch(c);
         CK(qr_householder((int)n, (int)chi, c->Y, c->Qn, c->R, qs, st));
     }
     CK(cudaEventRecord(ev[3], st));

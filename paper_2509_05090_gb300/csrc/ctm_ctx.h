@@ -29,7 +29,13 @@ struct ctm_ctx {
     size_t splitk_elems;
     int split_T;              // 0: FP64 contractions; 2..5: split-BF16 slices per operand
     SplitWork sw;
-    double *qr_sbuf, *qr_rowbuf;
+    // the double layer a is a constant B operand of four contractions per step:
+    // its packed digit slices are kept (slot 0: a as [(u,l)][z], slot 1: a as [z][(x,y)])
+    unsigned char *apk[2];
+    int *ape[2];
+    size_t apk_cap[2];
+    int apk_state[2];
+    double *qr_sbuf, *qr_rowbuf, *qr_wy;
     unsigned *qr_bar;
     int *err, *flag;
     double *norm_part;
@@ -48,7 +54,26 @@ struct ctm_ctx {
 };
 
 namespace ctmi {
-cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g);
+// QR scratch views of the context's workspace
+inline QrScratch qr_scratch(ctm_ctx *c)
+{
+    const long long n = c->n, k = c->chi;
+    QrScratch q;
+    q.sbuf = c->qr_sbuf;
+    q.rowbuf = c->qr_rowbuf;
+    q.bar = c->qr_bar;
+    q.err = c->err;
+    q.rows_min = c->qr_rows_min;
+    q.V = c->qr_wy;
+    q.S = q.V + n * k;
+    q.W = q.S + k * k;
+    q.ta = q.W + k * k;
+    q.sk = q.ta + 2 * k + k * k;   // (k*k of slack after ta keeps the scratch 8-byte aligned)
+    q.sk_elems = (size_t)(64 * k * k) - (size_t)(k * k);
+    return q;
+}
+enum { GEMM_PLAIN = 0, GEMM_REUSE_A = 1, GEMM_B_IS_A_LZ = 2, GEMM_B_IS_A_ZX = 3 };
+cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint = GEMM_PLAIN);
 int enqueue_enlarged_corner(ctm_ctx *c);
 int enqueue_step(ctm_ctx *c);
 int join_side(ctm_ctx *c);

@@ -375,7 +375,7 @@ int step_forward_keep(ctm_ctx *c, GradBufs &b, const double *C, const double *T,
          S2(chi, (long long)D2 * n, D2), S2(D2, 1, n)));
     CK(launch_warm_start((int)n, chi, Qp, C, c->Qs, st));
     CK(G((int)n, chi, (int)n, c->M, L(n), L(1), c->Qs, L(chi), L(1), c->Y, L(chi), L(1)));
-    QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err, c->qr_rows_min};
+    QrScratch qs = ctmi::qr_scratch(c);
     CK(qr_householder((int)n, chi, c->Y, c->Qn, c->R, qs, st));
     CK(G((int)n, chi, (int)n, c->M, L(n), L(1), c->Qn, L(chi), L(1), c->MQ, L(chi), L(1)));
     CK(G(chi, chi, (int)n, c->Qn, L(1), L(chi), c->MQ, L(chi), L(1), c->Cr, L(chi), L(1)));
@@ -548,7 +548,7 @@ extern "C" int ctm_grad(ctm_ctx *c, int warmup, int k_tracked, const double *h_d
     CK(launch_warm_start((int)n, chi, Qk, Ck, c->Qs, st));
     CK(G((int)n, chi, (int)n, c->M, L(n), L(1), c->Qs, L(chi), L(1), c->Y, L(chi), L(1)));
     {
-        QrScratch qs{c->qr_sbuf, c->qr_rowbuf, c->qr_bar, c->err, c->qr_rows_min};
+        QrScratch qs = ctmi::qr_scratch(c);
         CK(qr_householder((int)n, chi, c->Y, c->Qn, c->R, qs, st));
     }
     CK(G((int)n, chi, (int)n, c->M, L(n), L(1), c->Qn, L(chi), L(1), c->MQ, L(chi), L(1)));

@@ -55,23 +55,40 @@ struct SplitWork {
     int autotune;      // time the candidate tile shapes / K-splits of a new shape once (eager only)
 };
 SplitPlan split_plan(int M, int N, int K, int T, int nt_override = 0, int ks_override = 0);
+// Operand reuse: reuse_a = the A operand (same pointer and maps) was packed by the
+// previous split call and is unchanged; b_cache = a constant B operand packed once
+// into caller-owned buffers (re-packed if the plan's N tile changes).
+struct SplitOpts {
+    int reuse_a;
+    unsigned char *b_pk;
+    int *b_e;
+    size_t b_cap;
+    int *b_state;     // host: N tile of the cached pack, 0 = empty
+};
 // Largest pack / accumulator sizes over every plan the autotuner may pick.
 SplitPlan split_plan_caps(int M, int N, int K, int T);
 int split_supported_T(int T);
 cudaError_t split_prepare();
-cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev);
+cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
+                       const SplitOpts *opt = nullptr);
 
 // ---------------------------------------------------------------- QR
 // Householder QR of Y (n x k row-major, n >= k) with diag(R) >= 0.  Q (n x k)
-// and R (k x k) row-major.  One cooperative launch: factorisation, backward
-// accumulation of Q = H_0 ... H_{k-1} [I;0] and the sign gauge.
+// and R (k x k) row-major.  A cooperative factorisation (one grid barrier per
+// column), then Q in compact-WY form by GEMMs and the sign gauge.
 struct QrScratch {
     double *sbuf;      // 3 * k
     double *rowbuf;    // 2 * k
     unsigned *bar;     // 2 (count, generation)
     int *err;          // 1
     int rows_min;      // fewest rows per CTA (batched instances use small grids so they overlap)
+    double *V;         // n x k reflectors
+    double *S, *W;     // k x k each
+    double *ta;        // 2 x k (tau, alpha)
+    double *sk;        // split-K scratch of the V^T V product
+    size_t sk_elems;
 };
+size_t qr_wy_doubles(int n, int k);   // V + S + W + ta + split-K scratch
 size_t qr_scratch_doubles(int k);
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,
                            cudaStream_t st);

@@ -547,30 +547,51 @@ cudaError_t split_prepare()
 }
 
 static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
-                                  SplitPlan p)
+                                  SplitPlan p, const SplitOpts *opt = nullptr)
 {
+    const bool reuse_a = opt && opt->reuse_a;
+    bool pack_b = true;
+    if (opt && opt->b_pk) {
+        if (p.b_pack_bytes > opt->b_cap) return cudaErrorInvalidValue;
+        pack_b = (*opt->b_state != p.NT);
+        w.Bpk = opt->b_pk;
+        w.b_pack_cap = opt->b_cap;
+        w.eB = opt->b_e;
+    }
     if (p.a_pack_bytes > w.a_pack_cap || p.b_pack_bytes > w.b_pack_cap || p.partial_bytes > w.partial_cap ||
         g.M > w.e_cap || g.N > w.e_cap)
         return cudaErrorInvalidValue;
     cudaError_t e;
     // exponents: rows of A, columns of B
-    CTM_COUNT_LAUNCH(4);
-    split_rowexp_kernel<<<(g.M * 32 + 255) / 256, 256, 0, st>>>(g.M, g.K, g.A, g.Am, g.Ak, w.eA);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    split_rowexp_kernel<<<(g.N * 32 + 255) / 256, 256, 0, st>>>(g.N, g.K, g.B, g.Bn, g.Bk, w.eB);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!reuse_a) {
+        CTM_COUNT_LAUNCH(1);
+        split_rowexp_kernel<<<(g.M * 32 + 255) / 256, 256, 0, st>>>(g.M, g.K, g.A, g.Am, g.Ak, w.eA);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (pack_b) {
+        CTM_COUNT_LAUNCH(1);
+        split_rowexp_kernel<<<(g.N * 32 + 255) / 256, 256, 0, st>>>(g.N, g.K, g.B, g.Bn, g.Bk, w.eB);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     auto grid_of = [](long long units) {
         long long b = (units + 255) / 256;
         long long cap = 16LL * device_sm_count();
         return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
     };
     long long ua = (long long)p.mTiles * SP_BM * p.kTiles * 8, ub = (long long)p.nTiles * p.NT * p.kTiles * 8;
-    split_pack_kernel<<<grid_of(ua), 256, 0, st>>>(g.M, g.K, SP_BM, p.mTiles, p.kTiles, T, g.A, g.Am, g.Ak, w.eA,
-                                                   w.Apk);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    split_pack_kernel<<<grid_of(ub), 256, 0, st>>>(g.N, g.K, p.NT, p.nTiles, p.kTiles, T, g.B, g.Bn, g.Bk, w.eB,
-                                                   w.Bpk);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (!reuse_a) {
+        CTM_COUNT_LAUNCH(1);
+        split_pack_kernel<<<grid_of(ua), 256, 0, st>>>(g.M, g.K, SP_BM, p.mTiles, p.kTiles, T, g.A, g.Am, g.Ak,
+                                                       w.eA, w.Apk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    if (pack_b) {
+        CTM_COUNT_LAUNCH(1);
+        split_pack_kernel<<<grid_of(ub), 256, 0, st>>>(g.N, g.K, p.NT, p.nTiles, p.kTiles, T, g.B, g.Bn, g.Bk,
+                                                       w.eB, w.Bpk);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (opt && opt->b_pk) *opt->b_state = p.NT;
+    }
     if (p.ksplit > 1) {
         e = cudaMemsetAsync(w.partial, 0, p.partial_bytes, st);
         if (e != cudaSuccess) return e;
@@ -629,7 +650,8 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_tune;
 }  // namespace
 
-cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev)
+cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
+                       const SplitOpts *opt)
 {
     if (g.M <= 0 || g.N <= 0) return cudaSuccess;
     if (!split_supported_T(T) || g.alpha != 1.0 || g.beta != 0.0) return cudaErrorInvalidValue;
@@ -638,12 +660,13 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune.find(key);
         if (it != g_tune.end())
-            return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, it->second.first, it->second.second));
+            return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, it->second.first, it->second.second),
+                                  opt);
     }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
     if (!w.autotune || cs != cudaStreamCaptureStatusNone)
-        return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T));
+        return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T), opt);
     SplitPlan base = split_plan(g.M, g.N, g.K, T);
     const int chunks = (base.kTiles + SP_KT_PER_CHUNK - 1) / SP_KT_PER_CHUNK;
     std::vector<std::pair<int, int>> cands;
@@ -688,7 +711,16 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = best_c;
     }
-    return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, best_c.first, best_c.second));
+    // the candidates re-packed both operands into the work buffers: a cached B is
+    // re-packed by this final run, a reused A is freshly packed already
+    SplitOpts fin{};
+    if (opt) {
+        fin = *opt;
+        fin.reuse_a = 0;
+        if (fin.b_state) *fin.b_state = 0;
+    }
+    return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, best_c.first, best_c.second),
+                          opt ? &fin : nullptr);
 }
 
 int split_autotuned_shapes() { return (int)g_tune.size(); }

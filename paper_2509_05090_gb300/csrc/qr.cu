@@ -9,8 +9,14 @@
 // atomics; after one grid barrier every CTA reads the k sums and row j, derives
 // the reflector (alpha = -sign(x_0)|x|, v = x - alpha e_0, tau = 2/v^T v)
 // redundantly, and applies it to its own rows:  v^T a_kk = x^T a_kk - alpha a_jk.
-// So a column costs one grid barrier.  Q = H_0 H_1 ... H_{k-1} [I; 0] is then
-// accumulated backwards the same way, and columns with R_jj < 0 are negated.
+// So a column costs one grid barrier.  The reflectors v_j (unnormalised,
+// tau_j = 2 / v_j^T v_j) are written out and Q = H_0 ... H_{k-1} [I; 0] is formed
+// in compact-WY form without further barriers: with S = V^T V, the triangular
+// factor satisfies T^{-1} = striu(S) + diag(S)/2 (the "UT" form of the
+// product of reflectors), so Q = E - V W with W = T V_top^T (one small
+// triangular solve) -- two GEMMs and two small kernels.  Columns with
+// R_jj < 0 are negated (gauge diag(R) >= 0).  The grid size of the
+// factorisation is tuned once per shape by timing a few rows-per-CTA choices.
 //
 // The grid barrier is a counter/generation pair in global memory; its spin is
 // bounded (about a second) and on expiry sets an error flag that the host
@@ -24,29 +30,31 @@ namespace {
 constexpr int QR_THREADS = 256;
 constexpr long long QR_SPIN_LIMIT = 20000000LL;   // x ~64 ns sleep: ~1.3 s
 
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *gen, unsigned G, int *err)
+// Grid barrier number `epoch` (1, 2, ...): one release-add per CTA on a
+// monotonic counter; the CTA that completes G*epoch arrivals publishes the epoch
+// with a release store, the others poll it with acquire loads.  No reset, no
+// extra fences; the poll is bounded.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *flag, unsigned G, unsigned epoch, int *err)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *vgen = gen;
-        unsigned my = *vgen;
-        __threadfence();
-        unsigned arrived = atomicAdd(count, 1u);
-        if (arrived == G - 1) {
-            atomicExch(count, 0u);
-            __threadfence();
-            atomicAdd(gen, 1u);
+        unsigned old;
+        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
+        if (old == G * epoch - 1) {
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(epoch) : "memory");
         } else {
             long long it = 0;
-            while (*vgen == my) {
+            unsigned f;
+            for (;;) {
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flag) : "memory");
+                if ((int)(f - epoch) >= 0) break;
                 if (++it > QR_SPIN_LIMIT) {
                     atomicExch(err, 1);
                     break;
                 }
-                __nanosleep(64);
+                if (it > 64) __nanosleep(32);
             }
         }
-        __threadfence();
     }
     __syncthreads();
     return *((volatile int *)err) == 0;
@@ -56,6 +64,8 @@ struct QrArgs {
     int n, k, G, rows_per;
     const double *Y;
     double *Q, *R;
+    double *V;        // n x k reflectors (written)
+    double *ta;       // 2 x k: tau, alpha (written by CTA 0)
     double *sbuf;     // 3 x k, rotating accumulators
     double *rowbuf;   // 2 x k
     unsigned *bar;
@@ -71,8 +81,8 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     const int r1 = min(a.n, r0 + a.rows_per);
     const int nr = max(0, r1 - r0);
     double *Ys = sm;                          // rows_per x k
-    double *Qs = Ys + (size_t)a.rows_per * k; // rows_per x k
-    double *sv = Qs + (size_t)a.rows_per * k; // k
+    double *Qs = nullptr;
+    double *sv = Ys + (size_t)a.rows_per * k; // k
     double *rj = sv + k;                      // k
     double *cf = rj + k;                      // k
     double *taus = cf + k;                    // k
@@ -83,19 +93,28 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     for (int t = tid; t < nr * k; t += blockDim.x) Ys[t] = a.Y[(size_t)r0 * k + t];
     __syncthreads();
 
-    int step = 0;   // rotating-buffer counter shared by both phases
+    int step = 0;   // rotating-buffer counter
     // ---------------------------------------------------------- factorisation
     for (int j = 0; j < k; ++j, ++step) {
         double *acc = a.sbuf + (step % 3) * k;
         const int rs = max(r0, j) - r0;   // first local row taking part
-        for (int kk = j + tid; kk < k; kk += blockDim.x) {
+        // x^T a_kk over this CTA's rows: P lanes per column split the rows so the
+        // dependent FP64 chain is short, then combine with shuffles
+        const int ncols = k - j;
+        int P = 1;
+        while (P < 32 && P * 2 * ncols <= (int)blockDim.x) P *= 2;
+        for (int base = 0; base < ncols * P; base += blockDim.x) {
+            const int t = base + tid;
+            const int kk = j + t / P, part = t % P;
             double s = 0.0;
-            for (int r = rs; r < nr; ++r) s = fma(Ys[r * k + j], Ys[r * k + kk], s);
-            if (rs < nr) atomicAdd(&acc[kk], s);
+            if (t < ncols * P)
+                for (int r = rs + part; r < nr; r += P) s = fma(Ys[r * k + j], Ys[r * k + kk], s);
+            for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, P);
+            if (t < ncols * P && part == 0 && rs < nr) atomicAdd(&acc[kk], s);
         }
         if (j >= r0 && j < r1)
             for (int kk = j + tid; kk < k; kk += blockDim.x) a.rowbuf[(j & 1) * k + kk] = Ys[(j - r0) * k + kk];
-        if (!grid_barrier(a.bar, a.bar + 1, a.G, a.err)) return;
+        if (!grid_barrier(a.bar, a.bar + 1, a.G, (unsigned)(step + 1), a.err)) return;
         for (int kk = j + tid; kk < k; kk += blockDim.x) {
             sv[kk] = ((volatile double *)acc)[kk];
             rj[kk] = ((volatile double *)a.rowbuf)[(j & 1) * k + kk];
@@ -143,61 +162,74 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
         __syncthreads();
     }
 
-    // ---------------------------------------------------------- Q = H_0..H_{k-1} [I;0]
+    // ---------------------------------------------------------- reflectors out
     for (int t = tid; t < nr * k; t += blockDim.x) {
-        int r = t / k, cc = t % k;
-        Qs[t] = (r0 + r == cc) ? 1.0 : 0.0;
-    }
-    __syncthreads();
-    for (int j = k - 1; j >= 0; --j) {
-        const double tau = taus[j];
-        if (tau == 0.0) continue;       // uniform across CTAs
-        const double v0 = v0s[j];
-        double *acc = a.sbuf + (step % 3) * k;
-        const int rs = max(r0, j) - r0;
-        for (int kk = j + tid; kk < k; kk += blockDim.x) {
-            double s = 0.0;
-            for (int r = rs; r < nr; ++r) {
-                double vr = (r0 + r == j) ? v0 : Ys[r * k + j];
-                s = fma(vr, Qs[r * k + kk], s);
-            }
-            if (rs < nr) atomicAdd(&acc[kk], s);
-        }
-        if (!grid_barrier(a.bar, a.bar + 1, a.G, a.err)) return;
-        for (int kk = j + tid; kk < k; kk += blockDim.x) sv[kk] = tau * ((volatile double *)acc)[kk];
-        if (c == 0) {
-            double *z = a.sbuf + ((step + 2) % 3) * k;
-            for (int kk = tid; kk < k; kk += blockDim.x) z[kk] = 0.0;
-        }
-        __syncthreads();
-        const int ncol = k - j;
-        const int rows = nr - rs;
-        for (int t = tid; t < rows * ncol; t += blockDim.x) {
-            int r = rs + t / ncol;
-            int kk = j + t % ncol;
-            double vr = (r0 + r == j) ? v0 : Ys[r * k + j];
-            Qs[r * k + kk] -= vr * sv[kk];
-        }
-        __syncthreads();
-        ++step;
-    }
-
-    // ---------------------------------------------------------- gauge diag(R) >= 0
-    for (int t = tid; t < nr * k; t += blockDim.x) {
-        int cc = t % k;
-        double v = Qs[t];
-        a.Q[(size_t)r0 * k + t] = (alps[cc] < 0.0) ? -v : v;
+        const int r = r0 + t / k, j = t % k;
+        double v = 0.0;
+        if (r == j) v = v0s[j];
+        else if (r > j) v = Ys[t];
+        if (taus[j] == 0.0) v = 0.0;
+        a.V[(size_t)r0 * k + t] = v;
     }
     if (c == 0) {
+        for (int j = tid; j < k; j += blockDim.x) {
+            a.ta[j] = taus[j];
+            a.ta[k + j] = alps[j];
+        }
         __syncthreads();
         for (int t = tid; t < k * k; t += blockDim.x) {
             int rr = t / k;
             if (alps[rr] < 0.0) a.R[t] = -a.R[t];
         }
     }
+    (void)Qs;
+    (void)step;
 }
 
-size_t qr_smem_bytes(int rows_per, int k) { return sizeof(double) * ((size_t)2 * rows_per * k + 6 * (size_t)k); }
+// W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
+// One CTA.  The strict upper triangle of S (packed by rows), the reciprocal
+// diagonal and W live in shared memory; rows are solved from the bottom, the
+// P lanes of a column splitting each row's sum (short FP64 chains), and the
+// only divisions are the k reciprocals, taken in parallel up front.
+__global__ void qr_wy_solve_kernel(int k, int P, const double *S, const double *V, const double *ta, double *W)
+{
+    extern __shared__ double sm[];
+    double *Ws = sm;                              // k x k
+    double *Up = Ws + (size_t)k * k;              // k(k-1)/2, row i at i*k - i(i+1)/2
+    double *rd = Up + (size_t)k * (k - 1) / 2;    // k
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+        const int i = t / k, j = t % k;
+        if (j > i) Up[i * k - i * (i + 1) / 2 + (j - i - 1)] = S[t];
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) rd[i] = (ta[i] == 0.0) ? 1.0 : 2.0 / S[(size_t)i * k + i];
+    __syncthreads();
+    const int col = threadIdx.x / P, part = threadIdx.x % P;
+    const bool active = col < k;
+    for (int i = k - 1; i >= 0; --i) {
+        const double *u = Up + (i * k - i * (i + 1) / 2) - (i + 1);   // u[j] = U[i][j], j > i
+        double s = 0.0;
+        if (active)
+            for (int j = i + 1 + part; j < k; j += P) s = fma(-u[j], Ws[j * k + col], s);
+        for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, P);
+        if (active && part == 0) Ws[i * k + col] = (V[(size_t)col * k + i] + s) * rd[i];   // V_top^T[i][col]
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < k * k; t += blockDim.x) W[t] = Ws[t];
+}
+
+// Q <- diag-sign gauge of (E - V W): Q holds -V W on entry.
+__global__ void qr_form_q_kernel(long long n, int k, const double *ta, double *Q)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * k;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / k;
+        const int c = (int)(t % k);
+        double q = Q[t] + (r == c ? 1.0 : 0.0);
+        Q[t] = (ta[k + c] < 0.0) ? -q : q;
+    }
+}
+
+size_t qr_smem_bytes(int rows_per, int k) { return sizeof(double) * ((size_t)rows_per * k + 6 * (size_t)k); }
 
 int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
 {
@@ -218,16 +250,15 @@ size_t qr_scratch_doubles(int k) { return (size_t)5 * k + 8; }
 int qr_supported(int n, int k)
 {
     int G, rp;
-    return n >= k && k >= 1 && qr_layout(n, k, 1, &G, &rp);
+    return n >= k && k >= 1 && k <= 128 && qr_layout(n, k, 1, &G, &rp);
 }
 
-cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s, cudaStream_t st)
+size_t qr_wy_doubles(int n, int k) { return (size_t)n * k + 4 * (size_t)k * k + 2 * (size_t)k + 64 * (size_t)k * k; }
+
+static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y, double *R, QrScratch s, cudaStream_t st)
 {
-    int G, rows_per;
-    if (!qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rows_per)) {
-        if (!qr_layout(n, k, 1, &G, &rows_per)) return cudaErrorInvalidValue;
-    }
-    size_t smem = qr_smem_bytes(rows_per, k);
+    const int G = (n + rows_per - 1) / rows_per;
+    const size_t smem = qr_smem_bytes(rows_per, k);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel, QR_THREADS, smem);
     if (per_sm * device_sm_count() < G) return cudaErrorCooperativeLaunchTooLarge;
@@ -235,13 +266,99 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return e;
-    QrArgs a{n, k, G, rows_per, Y, Q, R, s.sbuf, s.rowbuf, s.bar, s.err};
+    QrArgs a{n, k, G, rows_per, Y, nullptr, R, s.V, s.ta, s.sbuf, s.rowbuf, s.bar, s.err};
     void *args[] = {&a};
     CTM_COUNT_LAUNCH(1);
     return cudaLaunchCooperativeKernel((void *)qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st);
 }
 
+#include <map>
+#include <mutex>
+#include <utility>
+static std::mutex g_qr_mu;
+static std::map<std::pair<int, int>, int> g_qr_rows;   // (n, k) -> rows per CTA, for rows_min == 1
+
+// rows per CTA: tuned once per (n, k) by timing the factorisation (eager calls only)
+static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, cudaStream_t st)
+{
+    int G, rp0;
+    qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp0);
+    if (s.rows_min > 1) return rp0;
+    {
+        std::lock_guard<std::mutex> lk(g_qr_mu);
+        auto it = g_qr_rows.find({n, k});
+        if (it != g_qr_rows.end()) return it->second;
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    if (cs != cudaStreamCaptureStatusNone) return rp0;
+    int best = rp0;
+    float best_ms = 1e30f;
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return rp0;
+    for (int rp : {rp0, 24, 32, 48, 64, 96, 128}) {
+        if (rp < rp0 || qr_smem_bytes(rp, k) > 200 * 1024) continue;
+        float ms = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            cudaError_t e = qr_factor_launch(n, k, rp, Y, R, s, st);
+            cudaEventRecord(e1, st);
+            if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                ms = 1e30f;
+                cudaGetLastError();
+                break;
+            }
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        int herr = 0;
+        cudaMemcpy(&herr, s.err, sizeof(int), cudaMemcpyDeviceToHost);
+        if (herr) break;   // a bounded wait expired: keep the default, the caller will report it
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = rp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> lk(g_qr_mu);
+    g_qr_rows[{n, k}] = best;
+    return best;
+}
+
+cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s, cudaStream_t st)
+{
+    int G, rp;
+    if (!qr_supported(n, k) || !s.V) return cudaErrorInvalidValue;
+    if (!qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp) && !qr_layout(n, k, 1, &G, &rp))
+        return cudaErrorInvalidValue;
+    const int rows_per = qr_pick_rows(n, k, Y, R, s, st);
+    cudaError_t e = qr_factor_launch(n, k, rows_per, Y, R, s, st);
+    if (e != cudaSuccess) return e;
+    // S = V^T V
+    GemmF64 gs{k, k, n, s.V, idx_lin(1), idx_lin(k), s.V, idx_lin(k), idx_lin(1), s.S, idx_lin(k), idx_lin(1), 1.0,
+               0.0};
+    if ((e = gemm_f64(gs, gemm_f64_pick_split(k, k, n), s.sk, s.sk_elems, st)) != cudaSuccess) return e;
+    CTM_COUNT_LAUNCH(2);
+    int P = 1;
+    while (P * 2 * k <= 1024 && P < 32) P *= 2;       // threads per column
+    const int threads = ((P * k + 31) / 32) * 32;
+    qr_wy_solve_kernel<<<1, threads, sizeof(double) * ((size_t)k * k + (size_t)k * (k - 1) / 2 + k), st>>>(
+        k, P, s.S, s.V, s.ta, s.W);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // Q = -V W, then + E and the sign gauge
+    GemmF64 gq{n, k, k, s.V, idx_lin(k), idx_lin(1), s.W, idx_lin(k), idx_lin(1), Q, idx_lin(k), idx_lin(1), -1.0,
+               0.0};
+    if ((e = gemm_f64(gq, 1, nullptr, 0, st)) != cudaSuccess) return e;
+    long long tot = (long long)n * k;
+    int blocks = (int)((tot + 255) / 256);
+    if (blocks > 8 * device_sm_count()) blocks = 8 * device_sm_count();
+    qr_form_q_kernel<<<blocks, 256, 0, st>>>(n, k, s.ta, Q);
+    return cudaGetLastError();
+}
+
 cudaError_t qr_prepare()
 {
-    return cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(qr_wy_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }
