@@ -179,14 +179,25 @@ int device_sm_count()
 
 static long long ceil_to(long long x, long long b) { return (x + b - 1) / b * b; }
 
-// Tile with the least padded work; ties go to the larger tile.
+// Tile choice.  The FP64 pipe of one SM is the bottleneck, so the cost of a tile
+// shape is the number of waves of CTAs times the padded work of one CTA (small
+// tiles also re-read operands more often, charged lightly).  When split-K will
+// apply (few tiles, long K) the padded total work decides instead.
 static TileCfg pick_tile(int M, int N, int K)
 {
+    const long long sms = device_sm_count();
     TileCfg best = kTiles[0];
     double best_cost = 1e300;
     for (const TileCfg &t : kTiles) {
-        double cost = (double)ceil_to(M, t.bm) * ceil_to(N, t.bn) * ceil_to(K, t.bk);
-        // small tiles re-read operands more often; charge them a little
+        const long long tiles = ((M + t.bm - 1) / t.bm) * (long long)((N + t.bn - 1) / t.bn);
+        const bool splitk = tiles < 2 * sms && K >= 4 * t.bk;
+        double cost;
+        if (splitk) {
+            cost = (double)ceil_to(M, t.bm) * ceil_to(N, t.bn) * ceil_to(K, t.bk) / (double)sms;
+        } else {
+            const long long waves = (tiles + sms - 1) / sms;
+            cost = (double)waves * t.bm * t.bn * ceil_to(K, t.bk);
+        }
         cost *= 1.0 + 8.0 / t.bm + 8.0 / t.bn;
         if (cost < best_cost * 0.999) {
             best_cost = cost;

@@ -187,32 +187,54 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
 }
 
 // W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
-// One CTA.  The strict upper triangle of S (packed by rows), the reciprocal
-// diagonal and W live in shared memory; rows are solved from the bottom, the
-// P lanes of a column splitting each row's sum (short FP64 chains), and the
-// only divisions are the k reciprocals, taken in parallel up front.
-__global__ void qr_wy_solve_kernel(int k, int P, const double *S, const double *V, const double *ta, double *W)
+// One CTA, blocked from the bottom in row blocks of QR_WB: for a block, every
+// (row, column) pair first sums the already solved rows below the block -- all
+// independent, one pass -- and then the QR_WB x QR_WB diagonal block is solved
+// row by row (short chains).  U (full, shared), the reciprocal diagonal and W
+// live in shared memory; the only divisions are the k reciprocals.
+constexpr int QR_WB = 8;
+
+__device__ __forceinline__ int up_off(int k, int i, int j) { return i * k - (i * (i - 1)) / 2 + (j - i); }
+
+__global__ void qr_wy_solve_kernel(int k, const double *S, const double *V, const double *ta, double *W)
 {
     extern __shared__ double sm[];
     double *Ws = sm;                              // k x k
-    double *Up = Ws + (size_t)k * k;              // k(k-1)/2, row i at i*k - i(i+1)/2
-    double *rd = Up + (size_t)k * (k - 1) / 2;    // k
+    double *Us = Ws + (size_t)k * k;              // upper triangle of S, packed by rows (k (k+1) / 2)
+    double *rd = Us + (size_t)k * (k + 1) / 2;    // k
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
         const int i = t / k, j = t % k;
-        if (j > i) Up[i * k - i * (i + 1) / 2 + (j - i - 1)] = S[t];
+        if (j >= i) Us[up_off(k, i, j)] = S[t];
     }
     for (int i = threadIdx.x; i < k; i += blockDim.x) rd[i] = (ta[i] == 0.0) ? 1.0 : 2.0 / S[(size_t)i * k + i];
     __syncthreads();
-    const int col = threadIdx.x / P, part = threadIdx.x % P;
-    const bool active = col < k;
-    for (int i = k - 1; i >= 0; --i) {
-        const double *u = Up + (i * k - i * (i + 1) / 2) - (i + 1);   // u[j] = U[i][j], j > i
-        double s = 0.0;
-        if (active)
-            for (int j = i + 1 + part; j < k; j += P) s = fma(-u[j], Ws[j * k + col], s);
-        for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, P);
-        if (active && part == 0) Ws[i * k + col] = (V[(size_t)col * k + i] + s) * rd[i];   // V_top^T[i][col]
+    for (int i1 = k; i1 > 0; i1 -= QR_WB) {
+        const int i0 = i1 - QR_WB > 0 ? i1 - QR_WB : 0;
+        const int rows = i1 - i0;
+        // rhs for the block: V_top^T[i][col] - sum_{j >= i1} U[i][j] W[j][col]
+        for (int t = threadIdx.x; t < rows * k; t += blockDim.x) {
+            const int i = i0 + t / k, col = t % k;
+            const double *u = Us + up_off(k, i, i) - i;   // u[j] = U[i][j] for j >= i
+            double s0 = 0.0, s1 = 0.0;
+            int j = i1;
+            for (; j + 1 < k; j += 2) {
+                s0 = fma(u[j], Ws[j * k + col], s0);
+                s1 = fma(u[j + 1], Ws[(j + 1) * k + col], s1);
+            }
+            if (j < k) s0 = fma(u[j], Ws[j * k + col], s0);
+            Ws[i * k + col] = V[(size_t)col * k + i] - (s0 + s1);
+        }
         __syncthreads();
+        // the diagonal block, bottom row first
+        for (int i = i1 - 1; i >= i0; --i) {
+            const double *u = Us + up_off(k, i, i) - i;
+            for (int col = threadIdx.x; col < k; col += blockDim.x) {
+                double s = Ws[i * k + col];
+                for (int j = i + 1; j < i1; ++j) s = fma(-u[j], Ws[j * k + col], s);
+                Ws[i * k + col] = s * rd[i];
+            }
+            __syncthreads();
+        }
     }
     for (int t = threadIdx.x; t < k * k; t += blockDim.x) W[t] = Ws[t];
 }
@@ -339,11 +361,8 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
                0.0};
     if ((e = gemm_f64(gs, gemm_f64_pick_split(k, k, n), s.sk, s.sk_elems, st)) != cudaSuccess) return e;
     CTM_COUNT_LAUNCH(2);
-    int P = 1;
-    while (P * 2 * k <= 1024 && P < 32) P *= 2;       // threads per column
-    const int threads = ((P * k + 31) / 32) * 32;
-    qr_wy_solve_kernel<<<1, threads, sizeof(double) * ((size_t)k * k + (size_t)k * (k - 1) / 2 + k), st>>>(
-        k, P, s.S, s.V, s.ta, s.W);
+    qr_wy_solve_kernel<<<1, 512, sizeof(double) * ((size_t)k * k + (size_t)k * (k + 1) / 2 + k), st>>>(
+        k, s.S, s.V, s.ta, s.W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Q = -V W, then + E and the sign gauge
     GemmF64 gq{n, k, k, s.V, idx_lin(k), idx_lin(1), s.W, idx_lin(k), idx_lin(1), Q, idx_lin(k), idx_lin(1), -1.0,
