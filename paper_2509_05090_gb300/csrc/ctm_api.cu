@@ -235,7 +235,6 @@ int enqueue_enlarged_corner(ctm_ctx *c)
 {
     const int chi = c->chi, D2 = c->D2;
     const long long n = c->n;
-    cudaStream_t st = c->stream;
     GemmF64 g;
     // W = T C
     g = GemmF64{(int)n, chi, chi, c->T, idx_lin(chi), idx_lin(1), c->C, idx_lin(chi), idx_lin(1),
@@ -249,9 +248,10 @@ int enqueue_enlarged_corner(ctm_ctx *c)
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
     CK(run_gemm(c, g, GEMM_B_IS_A_LZ));
-    // M[(a,y)][(b,x)] = Y1[(a,b), z] a[z, (x,y)]
+    // M[(a,y)][(b,x)] = Y1[(a,b), z] a[z, x, y]; the GEMM column index runs over (y, x)
+    // with x fastest, so an output tile covers whole contiguous (b, x) runs of M
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
-                idx_lin(1), c->M, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n), 1.0, 0.0};
+                idx_split(D2, 1, D2), c->M, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, n, 1), 1.0, 0.0};
     CK(run_gemm(c, g, GEMM_B_IS_A_ZX));
     return CTM_OK;
 }
@@ -295,18 +295,18 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     const long long n = c->n;
     cudaStream_t st = c->stream;
     GemmF64 g;
-    // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]
-    g = GemmF64{(int)n, (int)n, chi, c->T, idx_lin(chi), idx_lin(1), Qp, idx_lin(n), idx_lin(1),
-                c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(chi, 1, (long long)D2 * D2), 1.0, 0.0};
+    // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]; column index (j, w), w fastest
+    g = GemmF64{(int)n, (int)n, chi, c->T, idx_lin(chi), idx_lin(1), Qp, idx_lin(n), idx_split(D2, 1, chi),
+                c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1), 1.0, 0.0};
     CK(run_gemm(c, g));
     // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
     CK(run_gemm(c, g, GEMM_B_IS_A_LZ));
-    // H3'[a][y][x][j] = H2[(a,j),z] a[z,(x,y)]
+    // H3'[a][y][x][j] = H2[(a,j),z] a[z, x, y]; column index (y, x), x fastest
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
-                idx_lin(1), c->H, idx_split(chi, (long long)D2 * D2 * chi, 1), idx_split(D2, chi, (long long)D2 * chi),
-                1.0, 0.0};
+                idx_split(D2, 1, D2), c->H, idx_split(chi, (long long)D2 * D2 * chi, 1),
+                idx_split(D2, (long long)D2 * chi, chi), 1.0, 0.0};
     CK(run_gemm(c, g, GEMM_B_IS_A_ZX));
     // T'[i][(x,j)] = sum_{(a,y)} Q[(a,y),i] H3'[(a,y),(x,j)]
     g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),

@@ -182,15 +182,16 @@ static long long ceil_to(long long x, long long b) { return (x + b - 1) / b * b;
 // Tile choice.  The FP64 pipe of one SM is the bottleneck, so the cost of a tile
 // shape is the number of waves of CTAs times the padded work of one CTA (small
 // tiles also re-read operands more often, charged lightly).  When split-K will
-// apply (few tiles, long K) the padded total work decides instead.
-static TileCfg pick_tile(int M, int N, int K)
+// apply (few tiles, long K, and the caller gave split-K scratch) the padded total
+// work decides instead.
+static TileCfg pick_tile(int M, int N, int K, bool splitk_ok)
 {
     const long long sms = device_sm_count();
     TileCfg best = kTiles[0];
     double best_cost = 1e300;
     for (const TileCfg &t : kTiles) {
         const long long tiles = ((M + t.bm - 1) / t.bm) * (long long)((N + t.bn - 1) / t.bn);
-        const bool splitk = tiles < 2 * sms && K >= 4 * t.bk;
+        const bool splitk = splitk_ok && tiles < 2 * sms && K >= 4 * t.bk;
         double cost;
         if (splitk) {
             cost = (double)ceil_to(M, t.bm) * ceil_to(N, t.bn) * ceil_to(K, t.bk) / (double)sms;
@@ -209,7 +210,7 @@ static TileCfg pick_tile(int M, int N, int K)
 
 int gemm_f64_pick_split(int M, int N, int K)
 {
-    TileCfg t = pick_tile(M, N, K);
+    TileCfg t = pick_tile(M, N, K, true);
     long long tiles = (long long)((M + t.bm - 1) / t.bm) * ((N + t.bn - 1) / t.bn);
     long long want = 2LL * device_sm_count();
     if (tiles >= want || K < 4 * t.bk) return 1;
@@ -257,7 +258,7 @@ cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, size_t scrat
     if (ksplit > 1 && (!scratch || (size_t)ksplit * per_split > scratch_elems))
         ksplit = scratch ? (int)(scratch_elems / per_split) : 1;
     if (ksplit < 1) ksplit = 1;
-    TileCfg t = pick_tile(g.M, g.N, g.K);
+    TileCfg t = pick_tile(g.M, g.N, g.K, ksplit > 1);
 #define CTM_TILE(a, b, c) \
     if (t.bm == a && t.bn == b && t.bk == c) return launch_tile<a, b, c>(g, ksplit, scratch, st);
     CTM_TILE(64, 64, 16)

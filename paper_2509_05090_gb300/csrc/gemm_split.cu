@@ -38,7 +38,13 @@ namespace {
 constexpr int SP_BM = 128;       // tile rows = TMEM lanes
 constexpr int SP_BK = 64;        // K per packed tile (128-byte rows)
 constexpr int SP_KT_PER_CHUNK = 4;   // 4 x 64 = 256 K per exact chunk
-constexpr int SP_ASLOTS = 4;
+// A-slice ring depth: deep enough that the next K tile's slices are in flight
+// while the current one is multiplied (within 227 KB with T = 5 B slices x 2).
+template <int NT>
+constexpr int sp_aslots()
+{
+    return NT == 96 ? 6 : 8;
+}
 constexpr int SP_BSLOTS = 2;
 constexpr int SP_THREADS = 320;  // 10 warps
 constexpr long long SP_SPIN = 4000000LL;   // x ~200 ns sleep: ~1 s
@@ -58,21 +64,43 @@ __device__ __forceinline__ int sw128_off(int r, int k)
 }
 
 // ---------------------------------------------------------------- pre-pass
-// e[r] = exponent E with max_k |X(r,k)| < 2^E (0 for an all-zero row); one warp per row.
+// Row grids.  e[r] holds the largest high word of |X(r, k)| over k: for
+// non-negative doubles the integer order of the high words is the numeric order
+// of their exponents, which is all the grid needs, so no FP64 instruction is
+// used.  E = exp_of_word(e[r]) satisfies max_k |X(r,k)| < 2^E (frexp's
+// convention); zero, subnormal-only and inf/NaN rows get E = 0.
+__device__ __forceinline__ unsigned abs_hi_word(double x) { return (unsigned)__double2hiint(x) & 0x7FFFFFFFu; }
+__device__ __forceinline__ int exp_of_word(int w)
+{
+    const int ex = w >> 20;
+    return (ex == 0 || ex == 0x7FF) ? 0 : ex - 1022;
+}
+
+// one warp per row (rows whose K index is contiguous or irregular)
 __global__ void split_rowexp_kernel(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int *e)
 {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= R) return;
     const long long ro = off2(rmap, warp);
-    double m = 0.0;
-    for (int k = lane; k < K; k += 32) m = fmax(m, fabs(X[ro + off2(kmap, k)]));
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane == 0) {
-        int E = 0;
-        if (m > 0.0 && isfinite(m)) frexp(m, &E);
-        e[warp] = E;
-    }
+    unsigned m = 0;
+    for (int k = lane; k < K; k += 32) m = max(m, abs_hi_word(X[ro + off2(kmap, k)]));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) e[warp] = (int)m;
+}
+
+// Transposed operands (row index unit-stride, K index strided): one thread per
+// row over a K range, lanes along the contiguous rows; the K ranges combine with
+// atomicMax into e[], which the caller has zeroed.
+constexpr int SP_COLEXP_K = 32;
+__global__ void split_colexp_kernel(int R, int K, const double *X, long long kstride, int *e)
+{
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= R) return;
+    const int k0 = blockIdx.y * SP_COLEXP_K, k1 = min(K, k0 + SP_COLEXP_K);
+    unsigned m = 0;
+    for (int k = k0; k < k1; ++k) m = max(m, abs_hi_word(X[(long long)k * kstride + r]));
+    if (m) atomicMax(e + r, (int)m);
 }
 
 // Digits of one value: F = round(x 2^(P - E)) from the IEEE fields, integer ops only.
@@ -88,6 +116,40 @@ __device__ __forceinline__ long long fixed_point(double x, int E, int P)
     else if (s <= -64) F = 0;
     else F = (mant + (1LL << (-s - 1))) >> (-s);   // round half up on the magnitude
     return (b >> 63) ? -F : F;
+}
+
+// BF16 bits of a digit |d| <= 256: 2^23 + 256 + d is exact in FP32 (integer
+// below 2^24), subtracting 2^23 + 256 leaves d exactly, and an integer of at most
+// 8 significant bits has zero low 16 bits in FP32, so the BF16 pattern is the high
+// half.  One integer add and one FP32 add (no 64-bit conversion, which GB300 runs
+// on its narrow FP64 unit).
+__device__ __forceinline__ uint32_t bf16_of_digit(int d)
+{
+    const float f = __int_as_float(0x4B000000 + 256 + d) - 8388864.0f;
+    return __float_as_uint(f) >> 16;
+}
+
+// Balanced base-256 digits of 8 fixed-point values, least significant slice
+// first; slice t's 16-byte chunk goes to base + t * slice_bytes.
+__device__ __forceinline__ void write_digit_chunks(long long *F, int T, unsigned char *base, long long slice_bytes)
+{
+    for (int t = T - 1; t >= 0; --t) {
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            long long d;
+            if (t > 0) {
+                d = F[q] & 255;
+                if (d >= 128) d -= 256;
+                F[q] = (F[q] - d) >> 8;
+            } else {
+                d = F[q];
+            }
+            const uint32_t h = bf16_of_digit((int)d);
+            w[q >> 1] = (q & 1) ? (w[q >> 1] | (h << 16)) : h;
+        }
+        *reinterpret_cast<uint4 *>(base + (long long)t * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
+    }
 }
 
 // Pack T digit slices of X (R x K via maps) into [T][rowTiles][kTiles][rowsT x 64] swizzled tiles.
@@ -106,7 +168,7 @@ __global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTi
         const int k0 = c8 * 8;
         long long F[8];
         if (r < R) {
-            const int E = e[r];
+            const int E = exp_of_word(e[r]);
             const long long ro = off2(rmap, r);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
@@ -118,25 +180,38 @@ __global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTi
             for (int q = 0; q < 8; ++q) F[q] = 0;
         }
         const long long tile = (long long)(r / rowsT) * kTiles + (k0 / SP_BK);
-        unsigned char *base = out + tile * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK);
-        // balanced base-256 digits, least significant slice first
-        for (int t = T - 1; t >= 0; --t) {
-            __align__(16) __nv_bfloat16 v[8];
+        write_digit_chunks(F, T, out + tile * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK), slice_bytes);
+    }
+}
+
+// The same packing for a transposed operand, X(r, k) = X[k * kstride + r]: a
+// block stages 32 rows x one 64-wide K tile through shared memory, reading with
+// the lanes along the contiguous rows and writing the swizzled chunks as above.
+__global__ void __launch_bounds__(256) split_pack_t_kernel(int R, int K, int rowsT, int kTiles, int T, const double *X,
+                                                           long long kstride, const int *e, unsigned char *out,
+                                                           long long slice_bytes)
+{
+    __shared__ long long Fs[32][SP_BK + 1];
+    const int r0 = blockIdx.x * 32, kt = blockIdx.y;
+    const int P = 7 + 8 * (T - 1);
+    {
+        const int r = threadIdx.x & 31, kg = threadIdx.x >> 5;
+        const int gr = r0 + r;
+        const int E = gr < R ? exp_of_word(e[gr]) : 0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                long long d;
-                if (t > 0) {
-                    d = F[q] & 255;
-                    if (d >= 128) d -= 256;
-                    F[q] = (F[q] - d) >> 8;
-                } else {
-                    d = F[q];
-                }
-                v[q] = __float2bfloat16_rn((float)d);
-            }
-            *reinterpret_cast<uint4 *>(base + (long long)t * slice_bytes) = *reinterpret_cast<uint4 *>(v);
+        for (int q = 0; q < 8; ++q) {
+            const int kl = kg * 8 + q, k = kt * SP_BK + kl;
+            Fs[r][kl] = (gr < R && k < K) ? fixed_point(X[(long long)k * kstride + gr], E, P) : 0;
         }
     }
+    __syncthreads();
+    const int r = threadIdx.x >> 3, c8 = threadIdx.x & 7;
+    const int gr = r0 + r;
+    long long F[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) F[q] = Fs[r][c8 * 8 + q];
+    const long long tile = (long long)(gr / rowsT) * kTiles + kt;
+    write_digit_chunks(F, T, out + tile * ((long long)rowsT * SP_BK * 2) + sw128_off(gr % rowsT, c8 * 8), slice_bytes);
 }
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -210,18 +285,16 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v)
+// 16 consecutive TMEM columns of this warp's 32 lanes; completes at tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r)
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // int64 -> nearest double times 2^scale, integer instructions only (|S| < 2^63).
 __device__ __forceinline__ double scaled_int_to_double(long long S, int scale)
@@ -276,6 +349,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
     constexpr int A_TILE = SP_BM * SP_BK * 2;   // 16 KB
     constexpr int B_TILE = NT * SP_BK * 2;
     constexpr int HALF = NT / 2;
+    constexpr int SP_ASLOTS = sp_aslots<NT>();
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t bars[SP_ASLOTS * 2 + SP_BSLOTS * 2 + 3];
     __shared__ uint32_t tmem_base_sh;
@@ -423,34 +497,69 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
             tc_fence_after();
+            // one level at a time: all its column groups in flight, then one wait.
+            // A level holds an integer below 2^31 in magnitude (exact for t <= 3),
+            // so a 32-bit conversion suffices.
             for (int t = 0; t < T; ++t) {
                 const int sh = 8 * (T - 1 - t);
+                uint32_t r[HALF];
 #pragma unroll
-                for (int g = 0; g < HALF / 16; ++g) {
-                    float v[16];
-                    tmem_ld16(tmem + lane_base + (uint32_t)(t * NT + half * HALF + 16 * g), v);
+                for (int g = 0; g < HALF / 16; ++g)
+                    tmem_ld16(tmem + lane_base + (uint32_t)(t * NT + half * HALF + 16 * g), r + 16 * g);
+                tmem_wait_ld();
 #pragma unroll
-                    for (int q = 0; q < 16; ++q) acc[16 * g + q] += (long long)__float2ll_rn(v[q]) << sh;
-                }
+                for (int q = 0; q < HALF; ++q) acc[q] += (long long)__float2int_rn(__uint_as_float(r[q])) << sh;
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(ACC_EMPTY);
         }
+        // Output through shared memory.  Once the last accumulator is drained every
+        // copy has landed and every MMA has completed, so the operand ring is free:
+        // the 8 epilogue warps stage the tile there (FP64 bits, or the int64 sum for
+        // split-K) with the row and column offsets of the output maps, then write it
+        // out with the lanes running along whichever output index is contiguous.
+        constexpr int PITCH = NT + 1;
+        long long *stage = reinterpret_cast<long long *>(sm);
+        long long *row_off = stage + SP_BM * PITCH;
+        long long *col_off = row_off + SP_BM;
+        const int ew = warp - 2, et = threadIdx.x - 64;   // epilogue warp / thread index
+        const int m0 = mt * SP_BM, n0 = nt * NT;
+        const int rows = min(SP_BM, a.M - m0), cols = min(NT, a.N - n0);
         if (!*abort_flag) {
-            const int m = mt * SP_BM + 32 * sub + lane;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int r = 32 * sub + lane;
+            const int m = m0 + r;
             if (m < a.M) {
-                const int sc_m = a.eA[m] - 14 - 8 * (T - 1);
-                const long long om = off2(a.Cm, m);
+                const int sc_m = exp_of_word(a.eA[m]) - 14 - 8 * (T - 1);
+                if (half == 0) row_off[r] = a.ksplit == 1 ? off2(a.Cm, m) : (long long)m * a.N;
 #pragma unroll
                 for (int q = 0; q < HALF; ++q) {
-                    const int n = nt * NT + half * HALF + q;
-                    if (n < a.N) {
-                        if (a.ksplit == 1)
-                            a.C[om + off2(a.Cn, n)] = scaled_int_to_double(acc[q], sc_m + a.eB[n]);
-                        else
-                            atomicAdd(&a.partial[(size_t)m * a.N + n], (unsigned long long)acc[q]);
+                    const int c = half * HALF + q;
+                    if (n0 + c < a.N)
+                        stage[r * PITCH + c] = a.ksplit == 1
+                                                   ? __double_as_longlong(scaled_int_to_double(acc[q], sc_m + exp_of_word(a.eB[n0 + c])))
+                                                   : acc[q];
+                }
+            }
+            for (int c = et; c < cols; c += 256) col_off[c] = a.ksplit == 1 ? off2(a.Cn, n0 + c) : (long long)(n0 + c);
+        }
+        asm volatile("bar.sync 1, 256;" ::: "memory");
+        if (!*abort_flag) {
+            const bool along_n = (a.ksplit > 1) || a.Cn.s2 == 1 || a.Cm.s2 != 1;
+            if (along_n) {
+                for (int r = ew; r < rows; r += 8) {
+                    const long long ro = row_off[r];
+                    for (int c = lane; c < cols; c += 32) {
+                        const long long v = stage[r * PITCH + c];
+                        if (a.ksplit == 1) a.C[ro + col_off[c]] = __longlong_as_double(v);
+                        else atomicAdd(&a.partial[ro + col_off[c]], (unsigned long long)v);
                     }
+                }
+            } else {
+                for (int c = ew; c < cols; c += 8) {
+                    const long long co = col_off[c];
+                    for (int r = lane; r < rows; r += 32) a.C[row_off[r] + co] = __longlong_as_double(stage[r * PITCH + c]);
                 }
             }
         }
@@ -476,7 +585,7 @@ __global__ void split_finalize_kernel(int M, int N, int T, const unsigned long l
          t += (long long)gridDim.x * blockDim.x) {
         const int m = (int)(t / N), n = (int)(t - (long long)m * N);
         C[off2(Cm, m) + off2(Cn, n)] =
-            scaled_int_to_double((long long)partial[t], eA[m] + eB[n] - 14 - 8 * (T - 1));
+            scaled_int_to_double((long long)partial[t], exp_of_word(eA[m]) + exp_of_word(eB[n]) - 14 - 8 * (T - 1));
     }
 }
 
@@ -491,7 +600,9 @@ int pick_nt(int N, int T)
 template <int NT>
 size_t split_smem_bytes(int T)
 {
-    size_t b = 1024 + (size_t)SP_ASLOTS * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
+    size_t b = 1024 + (size_t)sp_aslots<NT>() * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
+    const size_t out_stage = 1024 + (size_t)SP_BM * (NT + 1) * 8 + (size_t)(SP_BM + NT) * 8;   // epilogue reuse
+    if (b < out_stage) b = out_stage;
     return b < 120 * 1024 ? 120 * 1024 : b;
 }
 
@@ -546,6 +657,33 @@ cudaError_t split_prepare()
                                 (int)split_smem_bytes<96>(5));
 }
 
+// Exponents and digit slices of one operand X(r, k) (rows of A, columns of B).
+// A transposed operand -- unit-stride rows, strided K -- is read with the lanes
+// along its rows; everything else one row per warp / thread chunk along K.
+static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int rowsT, int rowTiles,
+                                 int kTiles, int T, int *e, unsigned char *pk, cudaStream_t st)
+{
+    const long long slice_bytes = (long long)rowTiles * kTiles * rowsT * SP_BK * 2;
+    if (rmap.s1 == 0 && rmap.s2 == 1 && kmap.s1 == 0 && kmap.s2 != 1) {
+        cudaError_t e0 = cudaMemsetAsync(e, 0, sizeof(int) * (size_t)R, st);
+        if (e0 != cudaSuccess) return e0;
+        CTM_COUNT_LAUNCH(2);
+        split_colexp_kernel<<<dim3((R + 127) / 128, (K + SP_COLEXP_K - 1) / SP_COLEXP_K), 128, 0, st>>>(R, K, X,
+                                                                                                       kmap.s2, e);
+        split_pack_t_kernel<<<dim3(rowTiles * rowsT / 32, kTiles), 256, 0, st>>>(R, K, rowsT, kTiles, T, X, kmap.s2,
+                                                                                e, pk, slice_bytes);
+        return cudaGetLastError();
+    }
+    CTM_COUNT_LAUNCH(2);
+    split_rowexp_kernel<<<(R * 32 + 255) / 256, 256, 0, st>>>(R, K, X, rmap, kmap, e);
+    const long long units = (long long)rowTiles * rowsT * kTiles * 8;
+    long long blocks = (units + 255) / 256, cap = 16LL * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    if (blocks < 1) blocks = 1;
+    split_pack_kernel<<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowTiles, kTiles, T, X, rmap, kmap, e, pk);
+    return cudaGetLastError();
+}
+
 static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
                                   SplitPlan p, const SplitOpts *opt = nullptr)
 {
@@ -562,34 +700,13 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
         g.M > w.e_cap || g.N > w.e_cap)
         return cudaErrorInvalidValue;
     cudaError_t e;
-    // exponents: rows of A, columns of B
     if (!reuse_a) {
-        CTM_COUNT_LAUNCH(1);
-        split_rowexp_kernel<<<(g.M * 32 + 255) / 256, 256, 0, st>>>(g.M, g.K, g.A, g.Am, g.Ak, w.eA);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = split_prepass(g.M, g.K, g.A, g.Am, g.Ak, SP_BM, p.mTiles, p.kTiles, T, w.eA, w.Apk, st);
+        if (e != cudaSuccess) return e;
     }
     if (pack_b) {
-        CTM_COUNT_LAUNCH(1);
-        split_rowexp_kernel<<<(g.N * 32 + 255) / 256, 256, 0, st>>>(g.N, g.K, g.B, g.Bn, g.Bk, w.eB);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    auto grid_of = [](long long units) {
-        long long b = (units + 255) / 256;
-        long long cap = 16LL * device_sm_count();
-        return (int)(b < cap ? (b < 1 ? 1 : b) : cap);
-    };
-    long long ua = (long long)p.mTiles * SP_BM * p.kTiles * 8, ub = (long long)p.nTiles * p.NT * p.kTiles * 8;
-    if (!reuse_a) {
-        CTM_COUNT_LAUNCH(1);
-        split_pack_kernel<<<grid_of(ua), 256, 0, st>>>(g.M, g.K, SP_BM, p.mTiles, p.kTiles, T, g.A, g.Am, g.Ak,
-                                                       w.eA, w.Apk);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    if (pack_b) {
-        CTM_COUNT_LAUNCH(1);
-        split_pack_kernel<<<grid_of(ub), 256, 0, st>>>(g.N, g.K, p.NT, p.nTiles, p.kTiles, T, g.B, g.Bn, g.Bk,
-                                                       w.eB, w.Bpk);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        e = split_prepass(g.N, g.K, g.B, g.Bn, g.Bk, p.NT, p.nTiles, p.kTiles, T, w.eB, w.Bpk, st);
+        if (e != cudaSuccess) return e;
         if (opt && opt->b_pk) *opt->b_state = p.NT;
     }
     if (p.ksplit > 1) {
@@ -626,9 +743,11 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     if (p.ksplit > 1) {
-        long long total = (long long)g.M * g.N;
+        const long long total = (long long)g.M * g.N;
+        long long blocks = (total + 255) / 256, cap = 16LL * device_sm_count();
+        if (blocks > cap) blocks = cap;
         CTM_COUNT_LAUNCH(1);
-        split_finalize_kernel<<<grid_of(total), 256, 0, st>>>(g.M, g.N, T, (const unsigned long long *)w.partial,
+        split_finalize_kernel<<<(int)blocks, 256, 0, st>>>(g.M, g.N, T, (const unsigned long long *)w.partial,
                                                               w.eA, w.eB, g.C, g.Cm, g.Cn);
         e = cudaGetLastError();
     }
@@ -637,7 +756,7 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
 
 // ---------------------------------------------------------------- autotuner
 // For each new (M, N, K, T) the first eager call times every candidate plan
-// (N tile 64 / 96, K-split auto, 1, 2x, 1/2x) end to end on the real operands
+// (N tile 64 / 96, K-split auto, 1, 2x, 1/2x, one wave) end to end on the real operands
 // with CUDA events, keeps the fastest, and re-runs it so the output is valid.
 // The choice is cached for the process; captured calls use the cache or the
 // default plan.
@@ -672,7 +791,9 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
     std::vector<std::pair<int, int>> cands;
     for (int nt : {64, 96}) {
         if (nt == 96 && T * 96 > 512) continue;
-        for (int ks : {base.ksplit, 1, 2 * base.ksplit, base.ksplit / 2}) {
+        // auto, none, 2x, 1/2x, and the most splits that still fit one wave of CTAs
+        const int one_wave = (int)(device_sm_count() / ((long long)base.mTiles * ((g.N + nt - 1) / nt)));
+        for (int ks : {base.ksplit, 1, 2 * base.ksplit, base.ksplit / 2, one_wave}) {
             if (ks < 1 || ks > chunks) continue;
             std::pair<int, int> c{nt, ks};
             bool dup = false;

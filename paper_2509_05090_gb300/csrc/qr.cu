@@ -81,7 +81,6 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     const int r1 = min(a.n, r0 + a.rows_per);
     const int nr = max(0, r1 - r0);
     double *Ys = sm;                          // rows_per x k
-    double *Qs = nullptr;
     double *sv = Ys + (size_t)a.rows_per * k; // k
     double *rj = sv + k;                      // k
     double *cf = rj + k;                      // k
@@ -182,7 +181,6 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             if (alps[rr] < 0.0) a.R[t] = -a.R[t];
         }
     }
-    (void)Qs;
     (void)step;
 }
 
