@@ -69,7 +69,7 @@ inline QrScratch qr_scratch(ctm_ctx *c)
     q.W = q.S + k * k;
     q.ta = q.W + k * k;
     q.sk = q.ta + 2 * k + k * k;   // (k*k of slack after ta keeps the scratch 8-byte aligned)
-    q.sk_elems = (size_t)(64 * k * k) - (size_t)(k * k);
+    q.sk_elems = qr_sk_doubles((int)n, (int)k);
     return q;
 }
 enum { GEMM_PLAIN = 0, GEMM_REUSE_A = 1, GEMM_B_IS_A_LZ = 2, GEMM_B_IS_A_ZX = 3 };

@@ -89,6 +89,7 @@ struct QrScratch {
     size_t sk_elems;
 };
 size_t qr_wy_doubles(int n, int k);   // V + S + W + ta + split-K scratch
+size_t qr_sk_doubles(int n, int k);   // the split-K scratch part
 size_t qr_scratch_doubles(int k);
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,
                            cudaStream_t st);

@@ -179,47 +179,52 @@ int device_sm_count()
 
 static long long ceil_to(long long x, long long b) { return (x + b - 1) / b * b; }
 
-// Tile choice.  The FP64 pipe of one SM is the bottleneck, so the cost of a tile
-// shape is the number of waves of CTAs times the padded work of one CTA (small
-// tiles also re-read operands more often, charged lightly).  When split-K will
-// apply (few tiles, long K, and the caller gave split-K scratch) the padded total
-// work decides instead.
-static TileCfg pick_tile(int M, int N, int K, bool splitk_ok)
+// Tile and K-split choice.  The FP64 pipe of one SM is the bottleneck, so the
+// cost of a (tile, split) pair is the number of waves of CTAs times the padded
+// work of one CTA (small tiles also re-read operands more often, charged
+// lightly).  Split-K candidates (only when the caller gave scratch): enough
+// splits for two CTAs per SM, and the most splits that still fit one wave.
+struct TilePick {
+    TileCfg t;
+    int ksplit;
+};
+
+static TilePick pick_tile_split(int M, int N, int K, bool splitk_ok)
 {
     const long long sms = device_sm_count();
-    TileCfg best = kTiles[0];
+    TilePick best{kTiles[0], 1};
     double best_cost = 1e300;
     for (const TileCfg &t : kTiles) {
         const long long tiles = ((M + t.bm - 1) / t.bm) * (long long)((N + t.bn - 1) / t.bn);
-        const bool splitk = splitk_ok && tiles < 2 * sms && K >= 4 * t.bk;
-        double cost;
-        if (splitk) {
-            cost = (double)ceil_to(M, t.bm) * ceil_to(N, t.bn) * ceil_to(K, t.bk) / (double)sms;
-        } else {
-            const long long waves = (tiles + sms - 1) / sms;
-            cost = (double)waves * t.bm * t.bn * ceil_to(K, t.bk);
+        long long cand[3] = {1, 1, 1};
+        int nc = 1;
+        if (splitk_ok && tiles < 2 * sms && K >= 4 * t.bk) {
+            long long maxs = K / (2 * t.bk);
+            if (maxs > 64) maxs = 64;
+            long long s2 = (2 * sms + tiles - 1) / tiles, s1 = sms / tiles;
+            cand[nc++] = s2 < maxs ? s2 : maxs;
+            cand[nc++] = s1 < maxs ? s1 : maxs;
         }
-        cost *= 1.0 + 8.0 / t.bm + 8.0 / t.bn;
-        if (cost < best_cost * 0.999) {
-            best_cost = cost;
-            best = t;
+        for (int ci = 0; ci < nc; ++ci) {
+            const long long s = cand[ci] < 1 ? 1 : cand[ci];
+            const long long kchunk = ceil_to((K + s - 1) / s, t.bk);
+            const long long s_eff = (K + kchunk - 1) / kchunk;
+            const long long ctas = tiles * s_eff;
+            const long long waves = (ctas + sms - 1) / sms;
+            double cost = (double)waves * t.bm * t.bn * kchunk * (1.0 + 8.0 / t.bm + 8.0 / t.bn);
+            if (s_eff > 1) cost += (double)M * N * s_eff / (double)sms;   // the split-K reduction
+            if (cost < best_cost * 0.999) {
+                best_cost = cost;
+                best = TilePick{t, (int)s_eff};
+            }
         }
     }
     return best;
 }
 
-int gemm_f64_pick_split(int M, int N, int K)
-{
-    TileCfg t = pick_tile(M, N, K, true);
-    long long tiles = (long long)((M + t.bm - 1) / t.bm) * ((N + t.bn - 1) / t.bn);
-    long long want = 2LL * device_sm_count();
-    if (tiles >= want || K < 4 * t.bk) return 1;
-    long long s = (want + tiles - 1) / tiles;
-    long long maxs = K / (2 * t.bk);
-    if (s > maxs) s = maxs;
-    if (s > 64) s = 64;
-    return s < 1 ? 1 : (int)s;
-}
+static TileCfg pick_tile(int M, int N, int K, bool splitk_ok) { return pick_tile_split(M, N, K, splitk_ok).t; }
+
+int gemm_f64_pick_split(int M, int N, int K) { return pick_tile_split(M, N, K, true).ksplit; }
 
 template <int BM, int BN, int BK>
 static cudaError_t launch_tile(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)

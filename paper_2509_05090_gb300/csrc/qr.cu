@@ -97,24 +97,46 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     for (int j = 0; j < k; ++j, ++step) {
         double *acc = a.sbuf + (step % 3) * k;
         const int rs = max(r0, j) - r0;   // first local row taking part
-        // x^T a_kk over this CTA's rows: P lanes per column split the rows so the
-        // dependent FP64 chain is short, then combine with shuffles
+        // x^T a_kk over this CTA's rows: P lanes per column split the rows, two
+        // accumulators each, so the dependent FP64 chain is short; then shuffles
         const int ncols = k - j;
         int P = 1;
         while (P < 32 && P * 2 * ncols <= (int)blockDim.x) P *= 2;
         for (int base = 0; base < ncols * P; base += blockDim.x) {
             const int t = base + tid;
             const int kk = j + t / P, part = t % P;
-            double s = 0.0;
-            if (t < ncols * P)
-                for (int r = rs + part; r < nr; r += P) s = fma(Ys[r * k + j], Ys[r * k + kk], s);
+            double s0 = 0.0, s1 = 0.0;
+            if (t < ncols * P) {
+                int r = rs + part;
+                for (; r + P < nr; r += 2 * P) {
+                    s0 = fma(Ys[r * k + j], Ys[r * k + kk], s0);
+                    s1 = fma(Ys[(r + P) * k + j], Ys[(r + P) * k + kk], s1);
+                }
+                if (r < nr) s0 = fma(Ys[r * k + j], Ys[r * k + kk], s0);
+            }
+            double s = s0 + s1;
             for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, P);
             if (t < ncols * P && part == 0 && rs < nr) atomicAdd(&acc[kk], s);
         }
         if (j >= r0 && j < r1)
             for (int kk = j + tid; kk < k; kk += blockDim.x) a.rowbuf[(j & 1) * k + kk] = Ys[(j - r0) * k + kk];
         if (!grid_barrier(a.bar, a.bar + 1, a.G, (unsigned)(step + 1), a.err)) return;
-        for (int kk = j + tid; kk < k; kk += blockDim.x) {
+        // thread 0 derives the reflector (alpha = -sign(x_0)|x|, v_0 = x_0 - alpha,
+        // tau = 2 / v^T v = 1 / (|x| (|x| + |x_0|))) while the others fetch the sums
+        if (tid == 0) {
+            const double nrm2 = ((volatile double *)acc)[j], x0 = ((volatile double *)a.rowbuf)[(j & 1) * k + j];
+            const double nrm = sqrt(nrm2);
+            double tau = 0.0, alpha = x0, v0 = 0.0;
+            if (nrm > 0.0) {
+                alpha = (x0 >= 0.0) ? -nrm : nrm;
+                v0 = x0 - alpha;
+                tau = 1.0 / (nrm * (nrm + fabs(x0)));
+            }
+            taus[j] = tau;
+            v0s[j] = v0;
+            alps[j] = (nrm > 0.0) ? alpha : 0.0;
+        }
+        for (int kk = j + 1 + tid; kk < k; kk += blockDim.x) {
             sv[kk] = ((volatile double *)acc)[kk];
             rj[kk] = ((volatile double *)a.rowbuf)[(j & 1) * k + kk];
         }
@@ -123,31 +145,17 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             for (int kk = tid; kk < k; kk += blockDim.x) z[kk] = 0.0;
         }
         __syncthreads();
-        if (tid == 0) {
-            double nrm2 = sv[j], x0 = rj[j];
-            double nrm = sqrt(nrm2);
-            double tau = 0.0, alpha = x0, v0 = 0.0;
-            if (nrm > 0.0) {
-                alpha = (x0 >= 0.0) ? -nrm : nrm;
-                v0 = x0 - alpha;
-                tau = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / v^T v, v^T v = 2|x|(|x| + |x_0|)
-            }
-            taus[j] = tau;
-            v0s[j] = v0;
-            alps[j] = (nrm > 0.0) ? alpha : 0.0;
-        }
-        __syncthreads();
         const double tau = taus[j], v0 = v0s[j], alpha = alps[j];
         for (int kk = j + 1 + tid; kk < k; kk += blockDim.x) cf[kk] = tau * (sv[kk] - alpha * rj[kk]);
-        __syncthreads();
         if (c == 0) {
             for (int kk = tid; kk < k; kk += blockDim.x) {
                 double v = 0.0;
                 if (kk == j) v = alpha;
-                else if (kk > j) v = rj[kk] - v0 * cf[kk];
+                else if (kk > j) v = rj[kk] - v0 * (tau * (sv[kk] - alpha * rj[kk]));
                 a.R[(size_t)j * k + kk] = v;
             }
         }
+        __syncthreads();
         if (tau != 0.0) {
             const int ncol = k - j - 1;
             const int rows = nr - rs;
@@ -273,7 +281,13 @@ int qr_supported(int n, int k)
     return n >= k && k >= 1 && k <= 128 && qr_layout(n, k, 1, &G, &rp);
 }
 
-size_t qr_wy_doubles(int n, int k) { return (size_t)n * k + 4 * (size_t)k * k + 2 * (size_t)k + 64 * (size_t)k * k; }
+size_t qr_sk_doubles(int n, int k)
+{
+    const size_t a = 64 * (size_t)k * k, b = 4 * (size_t)n * k;   // split-K partials of V^T V and of V W
+    return a > b ? a : b;
+}
+
+size_t qr_wy_doubles(int n, int k) { return (size_t)n * k + 3 * (size_t)k * k + 2 * (size_t)k + qr_sk_doubles(n, k); }
 
 static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y, double *R, QrScratch s, cudaStream_t st)
 {
@@ -316,8 +330,9 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
     float best_ms = 1e30f;
     cudaEvent_t e0, e1;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return rp0;
-    for (int rp : {rp0, 24, 32, 48, 64, 96, 128}) {
-        if (rp < rp0 || qr_smem_bytes(rp, k) > 200 * 1024) continue;
+    // fewer rows than rp0 puts several CTAs on an SM (the launch checks they all fit)
+    for (int rp : {rp0, 8, 12, 16, 24, 32, 48, 64, 96, 128}) {
+        if ((rp < rp0 && rp * 2 < rp0) || (rp != rp0 && rp < 8) || qr_smem_bytes(rp, k) > 200 * 1024) continue;
         float ms = 0.f;
         for (int rep = 0; rep < 2; ++rep) {
             cudaEventRecord(e0, st);
@@ -365,7 +380,7 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
     // Q = -V W, then + E and the sign gauge
     GemmF64 gq{n, k, k, s.V, idx_lin(k), idx_lin(1), s.W, idx_lin(k), idx_lin(1), Q, idx_lin(k), idx_lin(1), -1.0,
                0.0};
-    if ((e = gemm_f64(gq, 1, nullptr, 0, st)) != cudaSuccess) return e;
+    if ((e = gemm_f64(gq, gemm_f64_pick_split(n, k, k), s.sk, s.sk_elems, st)) != cudaSuccess) return e;
     long long tot = (long long)n * k;
     int blocks = (int)((tot + 255) / 256);
     if (blocks > 8 * device_sm_count()) blocks = 8 * device_sm_count();
