@@ -6,9 +6,10 @@
 // addressed through two-level index maps (Idx2) so that the permuted 4-index
 // layouts are read and written in place, with no transpose kernels.
 //
-// Tile: 64 x 64 outputs per 256-thread CTA, 4 x 4 per thread (strided by 16
-// so a warp's shared-memory reads are conflict-free), K staged 16 at a time
-// through shared memory with a register prefetch of the next K tile.
+// Tiles from 32 x 32 to 72 x 72 outputs per CTA (the bond dimensions divide
+// them), a strided micro-tile per thread so a warp's shared-memory reads are
+// conflict-free, K staged through shared memory with a register prefetch of the
+// next K tile; the tile and the K split are chosen per shape from a wave model.
 #include "ctm_internal.h"
 
 namespace {
@@ -21,17 +22,19 @@ __device__ __forceinline__ long long off2(const Idx2 &x, int i)
     return (long long)hi * x.s1 + (long long)lo * x.s2;
 }
 
-// BM x BN outputs per CTA, (BM/4) x (BN/4) threads with a 4 x 4 micro-tile
-// each (rows ty + TY*i, columns tx + TX*j), K staged BK at a time.  The tile
+// BM x BN outputs per CTA, (BM/MT) x (BN/MT) threads with an MT x MT micro-tile
+// each (rows ty + TY*i, columns tx + TX*j), K staged BK at a time.  GB300's FP64
+// pipe is narrow enough that shared-memory bandwidth never binds, so the small
+// tiles use 2 x 2 micro-tiles: more threads per CTA to hide the FP64 latency.  The tile
 // shape is picked per GEMM so that the bond dimensions (chi = 72, D2 = 36 ...)
 // divide it without padding waste.  When the K map has unit stride the A tile
 // is fetched K-fastest, otherwise M-fastest (likewise N/K for B), so
 // consecutive threads touch consecutive addresses whenever the layout allows.
-template <int BM, int BN, int BK>
-__global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_f64_kernel(GemmF64 g, int a_kfast, int b_nfast,
-                                                                       int kchunk, double *partial)
+template <int BM, int BN, int BK, int MT>
+__global__ void __launch_bounds__((BM / MT) * (BN / MT)) gemm_f64_kernel(GemmF64 g, int a_kfast, int b_nfast,
+                                                                         int kchunk, double *partial)
 {
-    constexpr int TY = BM / 4, TX = BN / 4, NT = TY * TX;
+    constexpr int TY = BM / MT, TX = BN / MT, NT = TY * TX;
     constexpr int EA = (BM * BK + NT - 1) / NT, EB = (BN * BK + NT - 1) / NT;
     __shared__ double As[BK][BM + 1];
     __shared__ double Bs[BK][BN + 1];
@@ -41,11 +44,11 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_f64_kernel(GemmF64 g
     const int kbeg = blockIdx.z * kchunk;
     const int kend = min(g.K, kbeg + kchunk);
 
-    double acc[4][4];
+    double acc[MT][MT];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+        for (int j = 0; j < MT; ++j) acc[i][j] = 0.0;
 
     double ra[EA], rb[EB];
     auto fetch = [&](int k0) {
@@ -107,24 +110,24 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_f64_kernel(GemmF64 g
         if (k0 + BK < kend) fetch(k0 + BK);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
-            double a[4], b[4];
+            double a[MT], b[MT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + TY * i];
+            for (int i = 0; i < MT; ++i) a[i] = As[kk][ty + TY * i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + TX * j];
+            for (int j = 0; j < MT; ++j) b[j] = Bs[kk][tx + TX * j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < MT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < MT; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
         }
     }
 
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < MT; ++i) {
         int m = m0 + ty + TY * i;
         if (m >= g.M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < MT; ++j) {
             int n = n0 + tx + TX * j;
             if (n >= g.N) continue;
             if (partial) {
@@ -140,10 +143,11 @@ __global__ void __launch_bounds__((BM / 4) * (BN / 4)) gemm_f64_kernel(GemmF64 g
 }
 
 struct TileCfg {
-    int bm, bn, bk;
+    int bm, bn, bk, mt;
 };
-constexpr TileCfg kTiles[] = {{64, 64, 16}, {72, 72, 12}, {64, 32, 16}, {72, 36, 12}, {32, 64, 16},
-                              {36, 72, 12}, {64, 72, 12}, {72, 64, 16}, {32, 32, 16}, {36, 36, 12}};
+constexpr TileCfg kTiles[] = {{64, 64, 16, 4}, {72, 72, 12, 4}, {64, 32, 16, 4}, {72, 36, 12, 4},
+                              {32, 64, 16, 4}, {36, 72, 12, 4}, {64, 72, 12, 4}, {72, 64, 16, 4},
+                              {32, 32, 16, 2}, {36, 36, 12, 2}};
 
 // Deterministic split-K reduction: fixed summation order over the splits.
 __global__ void splitk_reduce_kernel(GemmF64 g, int ksplit, const double *partial)
@@ -226,7 +230,7 @@ static TileCfg pick_tile(int M, int N, int K, bool splitk_ok) { return pick_tile
 
 int gemm_f64_pick_split(int M, int N, int K) { return pick_tile_split(M, N, K, true).ksplit; }
 
-template <int BM, int BN, int BK>
+template <int BM, int BN, int BK, int MT>
 static cudaError_t launch_tile(const GemmF64 &g, int ksplit, double *scratch, cudaStream_t st)
 {
     int a_kfast = (g.Ak.s2 == 1 && g.Ak.div >= g.K) ? 1 : 0;
@@ -238,14 +242,14 @@ static cudaError_t launch_tile(const GemmF64 &g, int ksplit, double *scratch, cu
     ksplit = (g.K + kchunk - 1) / kchunk;
     if (ksplit < 1) ksplit = 1;
     dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM, ksplit);
-    constexpr int NT = (BM / 4) * (BN / 4);
+    constexpr int NT = (BM / MT) * (BN / MT);
     if (ksplit == 1) {
         CTM_COUNT_LAUNCH(1);
-        gemm_f64_kernel<BM, BN, BK><<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, nullptr);
+        gemm_f64_kernel<BM, BN, BK, MT><<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, nullptr);
         return cudaGetLastError();
     }
     CTM_COUNT_LAUNCH(2);
-    gemm_f64_kernel<BM, BN, BK><<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, scratch);
+    gemm_f64_kernel<BM, BN, BK, MT><<<grid, NT, 0, st>>>(g, a_kfast, b_nfast, kchunk, scratch);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     long long total = (long long)g.M * g.N;
@@ -264,18 +268,18 @@ cudaError_t gemm_f64(const GemmF64 &g, int ksplit, double *scratch, size_t scrat
         ksplit = scratch ? (int)(scratch_elems / per_split) : 1;
     if (ksplit < 1) ksplit = 1;
     TileCfg t = pick_tile(g.M, g.N, g.K, ksplit > 1);
-#define CTM_TILE(a, b, c) \
-    if (t.bm == a && t.bn == b && t.bk == c) return launch_tile<a, b, c>(g, ksplit, scratch, st);
-    CTM_TILE(64, 64, 16)
-    CTM_TILE(72, 72, 12)
-    CTM_TILE(64, 32, 16)
-    CTM_TILE(72, 36, 12)
-    CTM_TILE(32, 64, 16)
-    CTM_TILE(36, 72, 12)
-    CTM_TILE(64, 72, 12)
-    CTM_TILE(72, 64, 16)
-    CTM_TILE(32, 32, 16)
-    CTM_TILE(36, 36, 12)
+#define CTM_TILE(a, b, c, d) \
+    if (t.bm == a && t.bn == b && t.bk == c && t.mt == d) return launch_tile<a, b, c, d>(g, ksplit, scratch, st);
+    CTM_TILE(64, 64, 16, 4)
+    CTM_TILE(72, 72, 12, 4)
+    CTM_TILE(64, 32, 16, 4)
+    CTM_TILE(72, 36, 12, 4)
+    CTM_TILE(32, 64, 16, 4)
+    CTM_TILE(36, 72, 12, 4)
+    CTM_TILE(64, 72, 12, 4)
+    CTM_TILE(72, 64, 16, 4)
+    CTM_TILE(32, 32, 16, 2)
+    CTM_TILE(36, 36, 12, 2)
 #undef CTM_TILE
     return cudaErrorInvalidValue;
 }

@@ -17,7 +17,8 @@
 // S = sum_t S_t 2^(8 (T-1-t)) in int64; the chunks of one CTA are summed in
 // registers, split-K CTAs with 64-bit integer atomics (exact, so the result
 // does not depend on the order).  The FP64 output is S 2^(E_A + E_B - 14 -
-// 8 (T-1)), built from the integer with integer instructions.
+// 8 (T-1)): the int64 -> FP64 conversion instruction and an exact shift of the
+// exponent field.
 //
 // Kernel.  Tile 128 x NT (NT = 64 or 96), K staged 64 at a time.  The slicing
 // pre-pass writes each operand tile in the exact shared-memory image the MMA
@@ -25,7 +26,9 @@
 // (r/8)*1024 + (r%8)*128, 16-byte chunk c at (c ^ (r%8))*16), so one bulk
 // asynchronous copy (cp.async.bulk, the TMA engine) moves a whole tile.
 // Warp 0 issues the copies, warp 1 the tcgen05.mma instructions (one thread),
-// warps 2..9 drain TMEM with tcgen05.ld.  All waits are bounded; on expiry the
+// warps 2..17 drain TMEM with tcgen05.ld (four per TMEM sub-partition, a
+// quarter of the tile's columns each) and write the tile out through shared
+// memory.  All waits are bounded; on expiry the
 // kernel raises an error flag, stops issuing work, frees its TMEM and returns.
 #include <cuda_bf16.h>
 
@@ -46,7 +49,9 @@ constexpr int sp_aslots()
     return NT == 96 ? 6 : 8;
 }
 constexpr int SP_BSLOTS = 2;
-constexpr int SP_THREADS = 320;  // 10 warps
+constexpr int SP_EPI_WARPS = 16;                 // 4 per TMEM sub-partition
+constexpr int SP_EPI_THREADS = 32 * SP_EPI_WARPS;
+constexpr int SP_THREADS = 64 + SP_EPI_THREADS;  // producer, MMA issuer, epilogue
 constexpr long long SP_SPIN = 4000000LL;   // x ~200 ns sleep: ~1 s
 
 __device__ __forceinline__ long long off2(const Idx2 &x, int i)
@@ -294,40 +299,25 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t *r)
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t *r)
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+}
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// int64 -> nearest double times 2^scale, integer instructions only (|S| < 2^63).
+// int64 -> nearest double (round half to even, the conversion instruction) times
+// 2^scale, the scaling done exactly on the exponent field; results below the
+// normal range flush to zero and above it go to infinity.
 __device__ __forceinline__ double scaled_int_to_double(long long S, int scale)
 {
-    if (S == 0) return 0.0;
-    unsigned long long sign = 0, m = (unsigned long long)S;
-    if (S < 0) {
-        sign = 1ULL << 63;
-        m = (unsigned long long)(-S);
-    }
-    int lz = __clzll(m);
-    int top = 63 - lz;                 // index of the leading bit
-    unsigned long long mant;
-    int e2 = top;
-    if (top > 52) {
-        int sh = top - 52;
-        unsigned long long half = 1ULL << (sh - 1);
-        unsigned long long rem = m & ((1ULL << sh) - 1);
-        mant = m >> sh;
-        if (rem > half || (rem == half && (mant & 1))) {   // round half to even
-            ++mant;
-            if (mant >> 53) {
-                mant >>= 1;
-                ++e2;
-            }
-        }
-    } else {
-        mant = m << (52 - top);
-    }
-    int be = e2 + scale + 1023;
-    if (be <= 0) return 0.0;            // underflow: far below FP64 resolution of any result here
-    if (be >= 2047) return __longlong_as_double((long long)(sign | (0x7FFULL << 52)));
-    return __longlong_as_double((long long)(sign | ((unsigned long long)be << 52) | (mant & 0xFFFFFFFFFFFFFULL)));
+    const double d = __ll2double_rn(S);
+    const int hi = __double2hiint(d), lo = __double2loint(d);
+    const int be = ((hi >> 20) & 0x7FF) + scale;
+    if (S == 0 || be <= 0) return 0.0;   // far below FP64 resolution of any result here
+    if (be >= 2047) return __hiloint2double((hi & (int)0x80000000) | 0x7FF00000, 0);
+    return __hiloint2double((hi & ~0x7FF00000) | (be << 20), lo);
 }
 
 struct SplitArgs {
@@ -348,7 +338,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
 {
     constexpr int A_TILE = SP_BM * SP_BK * 2;   // 16 KB
     constexpr int B_TILE = NT * SP_BK * 2;
-    constexpr int HALF = NT / 2;
+    constexpr int QW = NT / 4;   // columns per epilogue warp
     constexpr int SP_ASLOTS = sp_aslots<NT>();
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t bars[SP_ASLOTS * 2 + SP_BSLOTS * 2 + 3];
@@ -386,7 +376,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             mbar_init(B_empty(s), 1);
         }
         mbar_init(ACC_FULL, 1);
-        mbar_init(ACC_EMPTY, 8);
+        mbar_init(ACC_EMPTY, SP_EPI_WARPS);
         mbar_init(DRAIN, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -482,13 +472,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             }
         }
     } else {
-        // ------------------------------------------------ epilogue warps 2..9
+        // ------------------------------------------------ epilogue warps 2..17
         const int sub = warp & 3;              // TMEM sub-partition this warp may read
-        const int half = (warp - 2) >> 2;      // which half of the NT columns
+        const int part = (warp - 2) >> 2;      // which quarter of the NT columns
         const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
-        long long acc[HALF];
+        long long acc[QW];
 #pragma unroll
-        for (int q = 0; q < HALF; ++q) acc[q] = 0;
+        for (int q = 0; q < QW; ++q) acc[q] = 0;
         int chunk = 0;
         for (int c = c_beg; c < c_end; ++c, ++chunk) {
             // one lane polls, the warp follows it, so tcgen05.ld below runs converged
@@ -502,13 +492,13 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             // so a 32-bit conversion suffices.
             for (int t = 0; t < T; ++t) {
                 const int sh = 8 * (T - 1 - t);
-                uint32_t r[HALF];
+                uint32_t r[QW];
 #pragma unroll
-                for (int g = 0; g < HALF / 16; ++g)
-                    tmem_ld16(tmem + lane_base + (uint32_t)(t * NT + half * HALF + 16 * g), r + 16 * g);
+                for (int g = 0; g < QW / 8; ++g)
+                    tmem_ld8(tmem + lane_base + (uint32_t)(t * NT + part * QW + 8 * g), r + 8 * g);
                 tmem_wait_ld();
 #pragma unroll
-                for (int q = 0; q < HALF; ++q) acc[q] += (long long)__float2int_rn(__uint_as_float(r[q])) << sh;
+                for (int q = 0; q < QW; ++q) acc[q] += (long long)__float2int_rn(__uint_as_float(r[q])) << sh;
             }
             tc_fence_before();
             __syncwarp();
@@ -516,7 +506,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
         }
         // Output through shared memory.  Once the last accumulator is drained every
         // copy has landed and every MMA has completed, so the operand ring is free:
-        // the 8 epilogue warps stage the tile there (FP64 bits, or the int64 sum for
+        // the epilogue warps stage the tile there (FP64 bits, or the int64 sum for
         // split-K) with the row and column offsets of the output maps, then write it
         // out with the lanes running along whichever output index is contiguous.
         constexpr int PITCH = NT + 1;
@@ -532,23 +522,23 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             const int m = m0 + r;
             if (m < a.M) {
                 const int sc_m = exp_of_word(a.eA[m]) - 14 - 8 * (T - 1);
-                if (half == 0) row_off[r] = a.ksplit == 1 ? off2(a.Cm, m) : (long long)m * a.N;
+                if (part == 0) row_off[r] = a.ksplit == 1 ? off2(a.Cm, m) : (long long)m * a.N;
 #pragma unroll
-                for (int q = 0; q < HALF; ++q) {
-                    const int c = half * HALF + q;
+                for (int q = 0; q < QW; ++q) {
+                    const int c = part * QW + q;
                     if (n0 + c < a.N)
                         stage[r * PITCH + c] = a.ksplit == 1
                                                    ? __double_as_longlong(scaled_int_to_double(acc[q], sc_m + exp_of_word(a.eB[n0 + c])))
                                                    : acc[q];
                 }
             }
-            for (int c = et; c < cols; c += 256) col_off[c] = a.ksplit == 1 ? off2(a.Cn, n0 + c) : (long long)(n0 + c);
+            for (int c = et; c < cols; c += SP_EPI_THREADS) col_off[c] = a.ksplit == 1 ? off2(a.Cn, n0 + c) : (long long)(n0 + c);
         }
-        asm volatile("bar.sync 1, 256;" ::: "memory");
+        asm volatile("bar.sync 1, %0;" ::"n"(SP_EPI_THREADS) : "memory");
         if (!*abort_flag) {
             const bool along_n = (a.ksplit > 1) || a.Cn.s2 == 1 || a.Cm.s2 != 1;
             if (along_n) {
-                for (int r = ew; r < rows; r += 8) {
+                for (int r = ew; r < rows; r += SP_EPI_WARPS) {
                     const long long ro = row_off[r];
                     for (int c = lane; c < cols; c += 32) {
                         const long long v = stage[r * PITCH + c];
@@ -557,7 +547,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
                     }
                 }
             } else {
-                for (int c = ew; c < cols; c += 8) {
+                for (int c = ew; c < cols; c += SP_EPI_WARPS) {
                     const long long co = col_off[c];
                     for (int r = lane; r < rows; r += 32) a.C[row_off[r] + co] = __longlong_as_double(stage[r * PITCH + c]);
                 }

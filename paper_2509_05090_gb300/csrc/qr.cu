@@ -9,7 +9,9 @@
 // atomics; after one grid barrier every CTA reads the k sums and row j, derives
 // the reflector (alpha = -sign(x_0)|x|, v = x - alpha e_0, tau = 2/v^T v)
 // redundantly, and applies it to its own rows:  v^T a_kk = x^T a_kk - alpha a_jk.
-// So a column costs one grid barrier.  The reflectors v_j (unnormalised,
+// Applying reflector j to the trailing columns and forming the partial sums of
+// column j+1 is one pass over the CTA's rows, so a column costs one grid barrier
+// and one sweep of the shared-memory block.  The reflectors v_j (unnormalised,
 // tau_j = 2 / v_j^T v_j) are written out and Q = H_0 ... H_{k-1} [I; 0] is formed
 // in compact-WY form without further barriers: with S = V^T V, the triangular
 // factor satisfies T^{-1} = striu(S) + diag(S)/2 (the "UT" form of the
@@ -18,7 +20,7 @@
 // R_jj < 0 are negated (gauge diag(R) >= 0).  The grid size of the
 // factorisation is tuned once per shape by timing a few rows-per-CTA choices.
 //
-// The grid barrier is a counter/generation pair in global memory; its spin is
+// The grid barrier is one monotonic counter in global memory; its spin is
 // bounded (about a second) and on expiry sets an error flag that the host
 // reports as CTM_ETIMEOUT instead of hanging.
 #include <cooperative_groups.h>
@@ -27,33 +29,29 @@
 
 namespace {
 
-constexpr int QR_THREADS = 256;
+constexpr int QR_THREADS = 512;
 constexpr long long QR_SPIN_LIMIT = 20000000LL;   // x ~64 ns sleep: ~1.3 s
 
-// Grid barrier number `epoch` (1, 2, ...): one release-add per CTA on a
-// monotonic counter; the CTA that completes G*epoch arrivals publishes the epoch
-// with a release store, the others poll it with acquire loads.  No reset, no
-// extra fences; the poll is bounded.
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned *flag, unsigned G, unsigned epoch, int *err)
+// Grid barrier number `epoch` (1, 2, ...): every CTA adds 1 to a monotonic
+// counter with a release reduction (no value returned) and polls the counter
+// with acquire loads until it reaches G * epoch.  No reset, no separate flag;
+// the poll is bounded.
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned G, unsigned epoch, int *err)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
-        unsigned old;
-        asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(count) : "memory");
-        if (old == G * epoch - 1) {
-            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(flag), "r"(epoch) : "memory");
-        } else {
-            long long it = 0;
-            unsigned f;
-            for (;;) {
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(flag) : "memory");
-                if ((int)(f - epoch) >= 0) break;
-                if (++it > QR_SPIN_LIMIT) {
-                    atomicExch(err, 1);
-                    break;
-                }
-                if (it > 64) __nanosleep(32);
+        asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
+        const unsigned target = G * epoch;
+        long long it = 0;
+        unsigned f;
+        for (;;) {
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(count) : "memory");
+            if ((int)(f - target) >= 0) break;
+            if (++it > QR_SPIN_LIMIT) {
+                atomicExch(err, 1);
+                break;
             }
+            if (it > 64) __nanosleep(32);
         }
     }
     __syncthreads();
@@ -92,13 +90,14 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     for (int t = tid; t < nr * k; t += blockDim.x) Ys[t] = a.Y[(size_t)r0 * k + t];
     __syncthreads();
 
-    int step = 0;   // rotating-buffer counter
-    // ---------------------------------------------------------- factorisation
-    for (int j = 0; j < k; ++j, ++step) {
-        double *acc = a.sbuf + (step % 3) * k;
-        const int rs = max(r0, j) - r0;   // first local row taking part
-        // x^T a_kk over this CTA's rows: P lanes per column split the rows, two
-        // accumulators each, so the dependent FP64 chain is short; then shuffles
+    // Column sums x_j^T a_kk (rows >= j of the current trailing block) over this
+    // CTA's rows, kk = j .. k-1, into acc: P lanes per column split the rows, two
+    // accumulators each, so the dependent FP64 chains stay short; then shuffles.
+    // With upd != 0 the trailing columns kk > j are first updated by the previous
+    // reflector (a_kk -= v cf_kk, v = column j-1) in the same pass, and the
+    // owner of row j publishes it for the next pivot.
+    auto col_pass = [&](int j, double *acc, int upd) {
+        const int rs = max(r0, j) - r0;
         const int ncols = k - j;
         int P = 1;
         while (P < 32 && P * 2 * ncols <= (int)blockDim.x) P *= 2;
@@ -107,20 +106,44 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             const int kk = j + t / P, part = t % P;
             double s0 = 0.0, s1 = 0.0;
             if (t < ncols * P) {
+                const double cfk = (upd && kk > j) ? cf[kk] : 0.0;
                 int r = rs + part;
                 for (; r + P < nr; r += 2 * P) {
-                    s0 = fma(Ys[r * k + j], Ys[r * k + kk], s0);
-                    s1 = fma(Ys[(r + P) * k + j], Ys[(r + P) * k + kk], s1);
+                    const int r2 = r + P;
+                    double x0 = Ys[r * k + kk], x1 = Ys[r2 * k + kk];
+                    if (upd && kk > j) {
+                        x0 = fma(-Ys[r * k + j - 1], cfk, x0);
+                        x1 = fma(-Ys[r2 * k + j - 1], cfk, x1);
+                        Ys[r * k + kk] = x0;
+                        Ys[r2 * k + kk] = x1;
+                    }
+                    s0 = fma(Ys[r * k + j], x0, s0);
+                    s1 = fma(Ys[r2 * k + j], x1, s1);
+                    if (r0 + r == j) a.rowbuf[(j & 1) * k + kk] = x0;
+                    if (r0 + r2 == j) a.rowbuf[(j & 1) * k + kk] = x1;
                 }
-                if (r < nr) s0 = fma(Ys[r * k + j], Ys[r * k + kk], s0);
+                if (r < nr) {
+                    double x0 = Ys[r * k + kk];
+                    if (upd && kk > j) {
+                        x0 = fma(-Ys[r * k + j - 1], cfk, x0);
+                        Ys[r * k + kk] = x0;
+                    }
+                    s0 = fma(Ys[r * k + j], x0, s0);
+                    if (r0 + r == j) a.rowbuf[(j & 1) * k + kk] = x0;
+                }
             }
-            double s = s0 + s1;
-            for (int o = P >> 1; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o, P);
-            if (t < ncols * P && part == 0 && rs < nr) atomicAdd(&acc[kk], s);
+            double sum = s0 + s1;
+            for (int o = P >> 1; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, P);
+            if (t < ncols * P && part == 0 && rs < nr) atomicAdd(&acc[kk], sum);
         }
-        if (j >= r0 && j < r1)
-            for (int kk = j + tid; kk < k; kk += blockDim.x) a.rowbuf[(j & 1) * k + kk] = Ys[(j - r0) * k + kk];
-        if (!grid_barrier(a.bar, a.bar + 1, a.G, (unsigned)(step + 1), a.err)) return;
+    };
+
+    int step = 0;   // rotating-buffer counter
+    // ---------------------------------------------------------- factorisation
+    col_pass(0, a.sbuf, 0);
+    for (int j = 0; j < k; ++j, ++step) {
+        double *acc = a.sbuf + (step % 3) * k;
+        if (!grid_barrier(a.bar, a.G, (unsigned)(step + 1), a.err)) return;
         // thread 0 derives the reflector (alpha = -sign(x_0)|x|, v_0 = x_0 - alpha,
         // tau = 2 / v^T v = 1 / (|x| (|x| + |x_0|))) while the others fetch the sums
         if (tid == 0) {
@@ -156,17 +179,19 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             }
         }
         __syncthreads();
-        if (tau != 0.0) {
-            const int ncol = k - j - 1;
-            const int rows = nr - rs;
-            for (int t = tid; t < rows * ncol; t += blockDim.x) {
-                int r = rs + t / ncol;
-                int kk = j + 1 + t % ncol;
-                double vr = (r0 + r == j) ? v0 : Ys[r * k + j];
-                Ys[r * k + kk] -= vr * cf[kk];
+        if (j + 1 < k) {
+            // H_j on column j+1 (rows below the pivot: row j itself is R's and
+            // never read again), then the fused update + column sums for j+1
+            const int rs1 = max(r0, j + 1) - r0;
+            const double cf1 = cf[j + 1];
+            for (int r = rs1 + tid; r < nr; r += blockDim.x) {
+                const double x = fma(-Ys[r * k + j], cf1, Ys[r * k + j + 1]);
+                Ys[r * k + j + 1] = x;
+                if (r0 + r == j + 1) a.rowbuf[((j + 1) & 1) * k + j + 1] = x;
             }
+            __syncthreads();
+            col_pass(j + 1, a.sbuf + ((step + 1) % 3) * k, 1);
         }
-        __syncthreads();
     }
 
     // ---------------------------------------------------------- reflectors out
@@ -193,56 +218,117 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
 }
 
 // W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
-// One CTA, blocked from the bottom in row blocks of QR_WB: for a block, every
-// (row, column) pair first sums the already solved rows below the block -- all
-// independent, one pass -- and then the QR_WB x QR_WB diagonal block is solved
-// row by row (short chains).  U (full, shared), the reciprocal diagonal and W
-// live in shared memory; the only divisions are the k reciprocals.
-constexpr int QR_WB = 8;
+// The k right-hand sides are independent: CTA b solves columns [8b, 8b + 8).
+// Rows are blocked by QR_WB = 8 from the bottom; every CTA first inverts the
+// diagonal 8 x 8 blocks of U (all blocks at once, one thread per block column),
+// then per row block sums the already solved rows below it (independent dot
+// products split over QR_WL lanes) and applies the block inverse (8-term dots).
+// So the dependent FP64 chains per block are short and the CTA syncs twice per
+// block.  U (packed upper triangle), the block inverses and the CTA's W columns
+// live in shared memory.
+constexpr int QR_WB = 8;      // row block (and diagonal inverse) size
+constexpr int QR_WC = 8;      // right-hand-side columns per CTA
+constexpr int QR_WL = 4;      // lanes per dot product in the block update
+constexpr int QR_WY_THREADS = 256;
 
 __device__ __forceinline__ int up_off(int k, int i, int j) { return i * k - (i * (i - 1)) / 2 + (j - i); }
 
-__global__ void qr_wy_solve_kernel(int k, const double *S, const double *V, const double *ta, double *W)
+size_t qr_wy_smem_bytes(int k)
+{
+    const int nb = (k + QR_WB - 1) / QR_WB;
+    return sizeof(double) * ((size_t)k * (k + 1) / 2 + (size_t)nb * QR_WB * QR_WB + (size_t)k * QR_WC + k);
+}
+
+__global__ void __launch_bounds__(QR_WY_THREADS) qr_wy_solve_kernel(int k, const double *S, const double *V,
+                                                                    const double *ta, double *W)
 {
     extern __shared__ double sm[];
-    double *Ws = sm;                              // k x k
-    double *Us = Ws + (size_t)k * k;              // upper triangle of S, packed by rows (k (k+1) / 2)
-    double *rd = Us + (size_t)k * (k + 1) / 2;    // k
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    const int nb = (k + QR_WB - 1) / QR_WB;
+    double *Us = sm;                                   // k (k+1) / 2
+    double *Di = Us + (size_t)k * (k + 1) / 2;         // nb x 8 x 8 block inverses
+    double *Wc = Di + (size_t)nb * QR_WB * QR_WB;      // k x QR_WC
+    double *rd = Wc + (size_t)k * QR_WC;               // k reciprocal diagonal
+    const int c0 = blockIdx.x * QR_WC;
+    const int ncol = min(QR_WC, k - c0);
+    const int tid = threadIdx.x;
+    for (int t = tid; t < k * k; t += blockDim.x) {
         const int i = t / k, j = t % k;
-        if (j >= i) Us[up_off(k, i, j)] = S[t];
+        if (j > i) Us[up_off(k, i, j)] = S[t];
+        else if (j == i) Us[up_off(k, i, i)] = (ta[i] == 0.0) ? 1.0 : 0.5 * S[t];
     }
-    for (int i = threadIdx.x; i < k; i += blockDim.x) rd[i] = (ta[i] == 0.0) ? 1.0 : 2.0 / S[(size_t)i * k + i];
+    for (int t = tid; t < k * QR_WC; t += blockDim.x) {
+        const int i = t / QR_WC, cc = t % QR_WC;
+        Wc[t] = (cc < ncol) ? V[(size_t)(c0 + cc) * k + i] : 0.0;
+    }
     __syncthreads();
-    for (int i1 = k; i1 > 0; i1 -= QR_WB) {
-        const int i0 = i1 - QR_WB > 0 ? i1 - QR_WB : 0;
-        const int rows = i1 - i0;
-        // rhs for the block: V_top^T[i][col] - sum_{j >= i1} U[i][j] W[j][col]
-        for (int t = threadIdx.x; t < rows * k; t += blockDim.x) {
-            const int i = i0 + t / k, col = t % k;
-            const double *u = Us + up_off(k, i, i) - i;   // u[j] = U[i][j] for j >= i
-            double s0 = 0.0, s1 = 0.0;
-            int j = i1;
-            for (; j + 1 < k; j += 2) {
-                s0 = fma(u[j], Ws[j * k + col], s0);
-                s1 = fma(u[j + 1], Ws[(j + 1) * k + col], s1);
+    for (int i = tid; i < k; i += blockDim.x) rd[i] = 1.0 / Us[up_off(k, i, i)];
+    __syncthreads();
+    // block inverses: thread (b, c) back-substitutes D_b x = e_c
+    for (int t = tid; t < nb * QR_WB; t += blockDim.x) {
+        const int bb = t / QR_WB, cl = t % QR_WB;
+        const int i0 = bb * QR_WB, bs = min(QR_WB, k - i0);
+        double *D = Di + bb * QR_WB * QR_WB;
+        if (cl < bs) {
+            double x[QR_WB];
+#pragma unroll
+            for (int r = QR_WB - 1; r >= 0; --r) {
+                double v = 0.0;
+                if (r <= cl) {
+                    v = (r == cl) ? 1.0 : 0.0;
+#pragma unroll
+                    for (int j = r + 1; j < QR_WB; ++j)
+                        if (j <= cl) v = fma(-Us[up_off(k, i0 + r, i0 + j)], x[j], v);
+                    v *= rd[i0 + r];
+                }
+                x[r] = v;
             }
-            if (j < k) s0 = fma(u[j], Ws[j * k + col], s0);
-            Ws[i * k + col] = V[(size_t)col * k + i] - (s0 + s1);
+#pragma unroll
+            for (int r = 0; r < QR_WB; ++r) D[r * QR_WB + cl] = x[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < QR_WB; ++r) D[r * QR_WB + cl] = 0.0;
+        }
+    }
+    __syncthreads();
+    for (int bb = nb - 1; bb >= 0; --bb) {
+        const int i0 = bb * QR_WB, i1 = min(k, i0 + QR_WB);
+        // rhs of the block: Wc[i][cc] -= sum_{j >= i1} U[i][j] Wc[j][cc]
+        for (int t = tid; t < QR_WB * QR_WC * QR_WL; t += blockDim.x) {
+            const int lane = t % QR_WL, pc = t / QR_WL;
+            const int i = i0 + pc / QR_WC, cc = pc % QR_WC;
+            double s0 = 0.0, s1 = 0.0;
+            if (i < i1) {
+                const double *u = Us + up_off(k, i, i) - i;   // u[j] = U[i][j] for j >= i
+                int j = i1 + lane;
+                for (; j + QR_WL < k; j += 2 * QR_WL) {
+                    s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
+                    s1 = fma(u[j + QR_WL], Wc[(j + QR_WL) * QR_WC + cc], s1);
+                }
+                if (j < k) s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
+            }
+            double sum = s0 + s1;
+#pragma unroll
+            for (int o = QR_WL / 2; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, QR_WL);
+            if (lane == 0 && i < i1) Wc[i * QR_WC + cc] -= sum;
         }
         __syncthreads();
-        // the diagonal block, bottom row first
-        for (int i = i1 - 1; i >= i0; --i) {
-            const double *u = Us + up_off(k, i, i) - i;
-            for (int col = threadIdx.x; col < k; col += blockDim.x) {
-                double s = Ws[i * k + col];
-                for (int j = i + 1; j < i1; ++j) s = fma(-u[j], Ws[j * k + col], s);
-                Ws[i * k + col] = s * rd[i];
-            }
-            __syncthreads();
+        // apply the block inverse
+        double wv = 0.0;
+        const int r = tid / QR_WC, cc = tid % QR_WC;
+        if (tid < QR_WB * QR_WC && i0 + r < i1) {
+            const double *D = Di + bb * QR_WB * QR_WB + r * QR_WB;
+#pragma unroll
+            for (int j = 0; j < QR_WB; ++j)
+                if (i0 + j < i1) wv = fma(D[j], Wc[(i0 + j) * QR_WC + cc], wv);
         }
+        __syncthreads();
+        if (tid < QR_WB * QR_WC && i0 + r < i1) Wc[(i0 + r) * QR_WC + cc] = wv;
+        __syncthreads();
     }
-    for (int t = threadIdx.x; t < k * k; t += blockDim.x) W[t] = Ws[t];
+    for (int t = tid; t < k * QR_WC; t += blockDim.x) {
+        const int i = t / QR_WC, cc = t % QR_WC;
+        if (cc < ncol) W[(size_t)i * k + c0 + cc] = Wc[t];
+    }
 }
 
 // Q <- diag-sign gauge of (E - V W): Q holds -V W on entry.
@@ -374,8 +460,7 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
                0.0};
     if ((e = gemm_f64(gs, gemm_f64_pick_split(k, k, n), s.sk, s.sk_elems, st)) != cudaSuccess) return e;
     CTM_COUNT_LAUNCH(2);
-    qr_wy_solve_kernel<<<1, 512, sizeof(double) * ((size_t)k * k + (size_t)k * (k + 1) / 2 + k), st>>>(
-        k, s.S, s.V, s.ta, s.W);
+    qr_wy_solve_kernel<<<(k + QR_WC - 1) / QR_WC, QR_WY_THREADS, qr_wy_smem_bytes(k), st>>>(k, s.S, s.V, s.ta, s.W);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     // Q = -V W, then + E and the sign gauge
     GemmF64 gq{n, k, k, s.V, idx_lin(k), idx_lin(1), s.W, idx_lin(k), idx_lin(1), Q, idx_lin(k), idx_lin(1), -1.0,
