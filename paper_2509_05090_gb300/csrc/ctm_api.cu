@@ -132,7 +132,7 @@ size_t layout(ctm_ctx *c, char *base)
     c->splitk_elems = sk;
     c->splitk = td((long long)sk + 1);
     c->qr_sbuf = td((long long)qr_scratch_doubles((int)chi));
-    c->qr_rowbuf = td(2 * chi);
+    c->qr_rowbuf = td((long long)qr_rowbuf_doubles((int)chi));
     c->qr_wy = td((long long)qr_wy_doubles((int)n, (int)chi));
     c->qr_bar = (unsigned *)take(64);
     c->err = (int *)take(64);

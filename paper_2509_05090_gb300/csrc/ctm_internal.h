@@ -77,8 +77,8 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
 // and R (k x k) row-major.  A cooperative factorisation (one grid barrier per
 // column), then Q in compact-WY form by GEMMs and the sign gauge.
 struct QrScratch {
-    double *sbuf;      // 3 * k
-    double *rowbuf;    // 2 * k
+    double *sbuf;      // qr_scratch_doubles(k): rotating column-sum accumulators
+    double *rowbuf;    // qr_rowbuf_doubles(k): published panel rows
     unsigned *bar;     // 2 (count, generation)
     int *err;          // 1
     int rows_min;      // fewest rows per CTA (batched instances use small grids so they overlap)
@@ -91,6 +91,7 @@ struct QrScratch {
 size_t qr_wy_doubles(int n, int k);   // V + S + W + ta + split-K scratch
 size_t qr_sk_doubles(int n, int k);   // the split-K scratch part
 size_t qr_scratch_doubles(int k);
+size_t qr_rowbuf_doubles(int k);
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,
                            cudaStream_t st);
 int qr_supported(int n, int k);

@@ -3,15 +3,25 @@
 // fixed so that diag(R) >= 0.  Always FP64.
 //
 // One cooperative launch over G <= #SM CTAs.  CTA c keeps its block of rows of
-// Y (and later of Q) in shared memory for the whole factorisation.  Per column
-// j every CTA forms the partial dot products x^T a_kk over its rows (x = the
-// column below the diagonal) and adds them into one k-vector with FP64
-// atomics; after one grid barrier every CTA reads the k sums and row j, derives
-// the reflector (alpha = -sign(x_0)|x|, v = x - alpha e_0, tau = 2/v^T v)
-// redundantly, and applies it to its own rows:  v^T a_kk = x^T a_kk - alpha a_jk.
-// Applying reflector j to the trailing columns and forming the partial sums of
-// column j+1 is one pass over the CTA's rows, so a column costs one grid barrier
-// and one sweep of the shared-memory block.  The reflectors v_j (unnormalised,
+// Y (and later of the reflectors) in shared memory for the whole factorisation.
+// Columns are taken in panels of up to QB.  For a panel starting at column j0
+// every CTA forms, over its rows >= j0, the partial Gram rows
+// G[i][kk] = a_{j0+i}^T a_kk (i < QB, kk >= j0+i) and the owners publish the
+// panel's rows j0 .. j0+QB-1; the partial sums meet in global memory through
+// FP64 atomics and one grid barrier.  Then every CTA derives the panel's
+// reflectors redundantly, column by column, from those numbers alone: for
+// column j = j0+i with x = the column below the diagonal, alpha = -sign(x_0)|x|,
+// v = x - alpha e_0, tau = 2/v^T v and v^T a_kk = G[i][kk] - alpha a_jk.
+// Because the reflector H_j is orthogonal, the Gram rows of the later panel
+// columns after applying it are the same inner products minus the row-j
+// contribution, G[i'][kk] -= R[j][j0+i'] R[j][kk], and the published rows are
+// updated like the data.  A downdated squared norm that falls below 1/16 of its
+// value at the panel start ends the panel there (so rounding errors are
+// amplified at most 4x); the next panel then starts from freshly reduced sums,
+// which makes the worst case the one-column-per-barrier algorithm.  Finally the
+// CTA applies the panel's reflectors to its own rows and, in the same pass over
+// its shared-memory block, forms the next panel's partial Gram rows.  So a
+// panel of QB columns costs one grid barrier.  The reflectors v_j (unnormalised,
 // tau_j = 2 / v_j^T v_j) are written out and Q = H_0 ... H_{k-1} [I; 0] is formed
 // in compact-WY form without further barriers: with S = V^T V, the triangular
 // factor satisfies T^{-1} = striu(S) + diag(S)/2 (the "UT" form of the
@@ -30,6 +40,8 @@
 namespace {
 
 constexpr int QR_THREADS = 512;
+constexpr int QB = 8;                     // panel width (columns per grid barrier)
+constexpr double QR_DOWNDATE_MIN = 1.0 / 16.0;   // smallest kept ratio of downdated / fresh norm^2
 constexpr long long QR_SPIN_LIMIT = 20000000LL;   // x ~64 ns sleep: ~1.3 s
 
 // Grid barrier number `epoch` (1, 2, ...): every CTA adds 1 to a monotonic
@@ -61,11 +73,11 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned G, unsign
 struct QrArgs {
     int n, k, G, rows_per;
     const double *Y;
-    double *Q, *R;
+    double *R;
     double *V;        // n x k reflectors (written)
     double *ta;       // 2 x k: tau, alpha (written by CTA 0)
-    double *sbuf;     // 3 x k, rotating accumulators
-    double *rowbuf;   // 2 x k
+    double *sbuf;     // 3 x QB x k rotating Gram-row accumulators
+    double *rowbuf;   // 2 x QB x k published panel rows
     unsigned *bar;
     int *err;
 };
@@ -73,125 +85,178 @@ struct QrArgs {
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
 {
     extern __shared__ double sm[];
+    __shared__ int stop_sh;
     const int k = a.k;
     const int c = blockIdx.x;
     const int r0 = c * a.rows_per;
     const int r1 = min(a.n, r0 + a.rows_per);
     const int nr = max(0, r1 - r0);
-    double *Ys = sm;                          // rows_per x k
-    double *sv = Ys + (size_t)a.rows_per * k; // k
-    double *rj = sv + k;                      // k
-    double *cf = rj + k;                      // k
-    double *taus = cf + k;                    // k
-    double *v0s = taus + k;                   // k
-    double *alps = v0s + k;                   // k
     const int tid = threadIdx.x;
+    double *Ys = sm;                                // rows_per x k
+    double *Gs = Ys + (size_t)a.rows_per * k;       // QB x k: panel Gram rows, downdated
+    double *Ps = Gs + QB * k;                       // QB x k: panel rows, updated
+    double *cfs = Ps + QB * k;                      // QB x k: tau_j v_j^T a_kk
+    double *Rj = cfs + QB * k;                      // k: current row of R
+    double *taus = Rj + k;                          // k
+    double *v0s = taus + k;                         // k
+    double *alps = v0s + k;                         // k
+    double *g0 = alps + k;                          // QB: squared norms at the panel start
+    auto acc_buf = [&](int blk) { return a.sbuf + (size_t)(blk % 3) * QB * k; };
+    auto pub_buf = [&](int blk) { return a.rowbuf + (size_t)(blk & 1) * QB * k; };
 
     for (int t = tid; t < nr * k; t += blockDim.x) Ys[t] = a.Y[(size_t)r0 * k + t];
     __syncthreads();
 
-    // Column sums x_j^T a_kk (rows >= j of the current trailing block) over this
-    // CTA's rows, kk = j .. k-1, into acc: P lanes per column split the rows, two
-    // accumulators each, so the dependent FP64 chains stay short; then shuffles.
-    // With upd != 0 the trailing columns kk > j are first updated by the previous
-    // reflector (a_kk -= v cf_kk, v = column j-1) in the same pass, and the
-    // owner of row j publishes it for the next pivot.
-    auto col_pass = [&](int j, double *acc, int upd) {
-        const int rs = max(r0, j) - r0;
-        const int ncols = k - j;
+    // Apply the reflectors of the panel at j0 (width nb, coefficients cfs, vectors
+    // in the panel columns) to this CTA's rows >= j1 and form the partial Gram
+    // rows of the panel at j1 (width nn) over those rows; the owners of rows
+    // j1 .. j1+nn-1 publish them.  Panel columns j1 .. j1+nn-1 are updated first
+    // (one thread per element), then every column kk >= j1 is swept once: P lanes
+    // split its rows, the update is a sum of nb independent terms and the nn Gram
+    // sums are independent chains; partial sums meet through FP64 atomics.
+    auto gram_pass = [&](int j0, int nb, int j1, int nn, double *acc, double *pub) {
+        const int rs = max(r0, j1) - r0;   // first local row >= j1
+        const int nrow = max(0, nr - rs);
+        if (nb > 0) {
+            for (int t = tid; t < nrow * nn; t += blockDim.x) {
+                const int r = rs + t / nn, col = j1 + t % nn;
+                double s0 = 0.0, s1 = 0.0;
+                for (int i = 0; i < nb; i += 2) {
+                    s0 = fma(Ys[r * k + j0 + i], cfs[i * k + col], s0);
+                    if (i + 1 < nb) s1 = fma(Ys[r * k + j0 + i + 1], cfs[(i + 1) * k + col], s1);
+                }
+                Ys[r * k + col] -= s0 + s1;
+            }
+            __syncthreads();
+        }
+        const int ncols = k - j1;
         int P = 1;
         while (P < 32 && P * 2 * ncols <= (int)blockDim.x) P *= 2;
         for (int base = 0; base < ncols * P; base += blockDim.x) {
             const int t = base + tid;
-            const int kk = j + t / P, part = t % P;
-            double s0 = 0.0, s1 = 0.0;
+            const int kk = j1 + t / P, part = t % P;
+            double g[QB];
+#pragma unroll
+            for (int i = 0; i < QB; ++i) g[i] = 0.0;
             if (t < ncols * P) {
-                const double cfk = (upd && kk > j) ? cf[kk] : 0.0;
-                int r = rs + part;
-                for (; r + P < nr; r += 2 * P) {
-                    const int r2 = r + P;
-                    double x0 = Ys[r * k + kk], x1 = Ys[r2 * k + kk];
-                    if (upd && kk > j) {
-                        x0 = fma(-Ys[r * k + j - 1], cfk, x0);
-                        x1 = fma(-Ys[r2 * k + j - 1], cfk, x1);
-                        Ys[r * k + kk] = x0;
-                        Ys[r2 * k + kk] = x1;
+                const bool upd = nb > 0 && kk >= j1 + nn;
+                for (int r = rs + part; r < nr; r += P) {
+                    double x = Ys[r * k + kk];
+                    if (upd) {
+                        double s0 = 0.0, s1 = 0.0;
+                        for (int i = 0; i < nb; i += 2) {
+                            s0 = fma(Ys[r * k + j0 + i], cfs[i * k + kk], s0);
+                            if (i + 1 < nb) s1 = fma(Ys[r * k + j0 + i + 1], cfs[(i + 1) * k + kk], s1);
+                        }
+                        x -= s0 + s1;
+                        Ys[r * k + kk] = x;
                     }
-                    s0 = fma(Ys[r * k + j], x0, s0);
-                    s1 = fma(Ys[r2 * k + j], x1, s1);
-                    if (r0 + r == j) a.rowbuf[(j & 1) * k + kk] = x0;
-                    if (r0 + r2 == j) a.rowbuf[(j & 1) * k + kk] = x1;
-                }
-                if (r < nr) {
-                    double x0 = Ys[r * k + kk];
-                    if (upd && kk > j) {
-                        x0 = fma(-Ys[r * k + j - 1], cfk, x0);
-                        Ys[r * k + kk] = x0;
-                    }
-                    s0 = fma(Ys[r * k + j], x0, s0);
-                    if (r0 + r == j) a.rowbuf[(j & 1) * k + kk] = x0;
+#pragma unroll
+                    for (int i = 0; i < QB; ++i)
+                        if (i < nn && j1 + i <= kk) g[i] = fma(Ys[r * k + j1 + i], x, g[i]);
+                    const int rg = r0 + r;
+                    if (rg < j1 + nn) pub[(rg - j1) * k + kk] = x;
                 }
             }
-            double sum = s0 + s1;
-            for (int o = P >> 1; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, P);
-            if (t < ncols * P && part == 0 && rs < nr) atomicAdd(&acc[kk], sum);
+#pragma unroll
+            for (int i = 0; i < QB; ++i) {
+                double v = g[i];
+                for (int o = P >> 1; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, P);
+                if (t < ncols * P && part == 0 && nrow > 0 && i < nn && j1 + i <= kk) atomicAdd(&acc[i * k + kk], v);
+            }
         }
     };
 
-    int step = 0;   // rotating-buffer counter
-    // ---------------------------------------------------------- factorisation
-    col_pass(0, a.sbuf, 0);
-    for (int j = 0; j < k; ++j, ++step) {
-        double *acc = a.sbuf + (step % 3) * k;
-        if (!grid_barrier(a.bar, a.G, (unsigned)(step + 1), a.err)) return;
-        // thread 0 derives the reflector (alpha = -sign(x_0)|x|, v_0 = x_0 - alpha,
-        // tau = 2 / v^T v = 1 / (|x| (|x| + |x_0|))) while the others fetch the sums
-        if (tid == 0) {
-            const double nrm2 = ((volatile double *)acc)[j], x0 = ((volatile double *)a.rowbuf)[(j & 1) * k + j];
-            const double nrm = sqrt(nrm2);
-            double tau = 0.0, alpha = x0, v0 = 0.0;
-            if (nrm > 0.0) {
-                alpha = (x0 >= 0.0) ? -nrm : nrm;
-                v0 = x0 - alpha;
-                tau = 1.0 / (nrm * (nrm + fabs(x0)));
-            }
-            taus[j] = tau;
-            v0s[j] = v0;
-            alps[j] = (nrm > 0.0) ? alpha : 0.0;
-        }
-        for (int kk = j + 1 + tid; kk < k; kk += blockDim.x) {
-            sv[kk] = ((volatile double *)acc)[kk];
-            rj[kk] = ((volatile double *)a.rowbuf)[(j & 1) * k + kk];
+    int j0 = 0, nn0 = min(QB, k), blk = 0;
+    gram_pass(0, 0, 0, nn0, acc_buf(0), pub_buf(0));
+    while (j0 < k) {
+        const double *acc = acc_buf(blk);
+        const double *pub = pub_buf(blk);
+        if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 1), a.err)) return;
+        for (int t = tid; t < nn0 * (k - j0); t += blockDim.x) {
+            const int i = t / (k - j0), kk = j0 + t % (k - j0);
+            Gs[i * k + kk] = (kk >= j0 + i) ? ((volatile const double *)acc)[i * k + kk] : 0.0;
+            Ps[i * k + kk] = ((volatile const double *)pub)[i * k + kk];
         }
         if (c == 0) {
-            double *z = a.sbuf + ((step + 2) % 3) * k;
-            for (int kk = tid; kk < k; kk += blockDim.x) z[kk] = 0.0;
+            double *z = a.sbuf + (size_t)((blk + 2) % 3) * QB * k;
+            for (int t = tid; t < QB * k; t += blockDim.x) z[t] = 0.0;
         }
         __syncthreads();
-        const double tau = taus[j], v0 = v0s[j], alpha = alps[j];
-        for (int kk = j + 1 + tid; kk < k; kk += blockDim.x) cf[kk] = tau * (sv[kk] - alpha * rj[kk]);
-        if (c == 0) {
-            for (int kk = tid; kk < k; kk += blockDim.x) {
-                double v = 0.0;
-                if (kk == j) v = alpha;
-                else if (kk > j) v = rj[kk] - v0 * (tau * (sv[kk] - alpha * rj[kk]));
-                a.R[(size_t)j * k + kk] = v;
-            }
-        }
-        __syncthreads();
-        if (j + 1 < k) {
-            // H_j on column j+1 (rows below the pivot: row j itself is R's and
-            // never read again), then the fused update + column sums for j+1
-            const int rs1 = max(r0, j + 1) - r0;
-            const double cf1 = cf[j + 1];
-            for (int r = rs1 + tid; r < nr; r += blockDim.x) {
-                const double x = fma(-Ys[r * k + j], cf1, Ys[r * k + j + 1]);
-                Ys[r * k + j + 1] = x;
-                if (r0 + r == j + 1) a.rowbuf[((j + 1) & 1) * k + j + 1] = x;
+        if (tid < nn0) g0[tid] = Gs[tid * k + j0 + tid];
+        // ------------------------------------------------ the panel's reflectors
+        int nb = nn0;
+        for (int i = 0; i < nn0; ++i) {
+            const int j = j0 + i;
+            if (tid == 0) {
+                const double nrm2 = Gs[i * k + j], x0 = Ps[i * k + j];
+                int stop = -1;
+                if (i > 0 && !(nrm2 >= QR_DOWNDATE_MIN * g0[i])) {
+                    stop = i;   // cancellation: column j starts the next panel from fresh sums
+                } else {
+                    const double nrm = sqrt(nrm2);
+                    double tau = 0.0, alpha = x0, v0 = 0.0;
+                    if (nrm > 0.0) {
+                        alpha = (x0 >= 0.0) ? -nrm : nrm;
+                        v0 = x0 - alpha;
+                        tau = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / v^T v
+                    }
+                    taus[j] = tau;
+                    v0s[j] = v0;
+                    alps[j] = (nrm > 0.0) ? alpha : 0.0;
+                }
+                stop_sh = stop;
             }
             __syncthreads();
-            col_pass(j + 1, a.sbuf + ((step + 1) % 3) * k, 1);
+            if (stop_sh >= 0) {
+                nb = stop_sh;
+                break;
+            }
+            const double tau = taus[j], v0 = v0s[j], alpha = alps[j];
+            for (int kk = tid; kk < k; kk += blockDim.x) {
+                double rv = 0.0;
+                if (kk == j) {
+                    rv = alpha;
+                } else if (kk > j) {
+                    const double cf = tau * (Gs[i * k + kk] - alpha * Ps[i * k + kk]);
+                    cfs[i * k + kk] = cf;
+                    rv = Ps[i * k + kk] - v0 * cf;
+                    Rj[kk] = rv;
+                }
+                if (c == 0) a.R[(size_t)j * k + kk] = rv;
+            }
+            __syncthreads();
+            // H_j on the later panel rows and Gram rows (rows >= j+1 from here on)
+            const int rest = nn0 - 1 - i;
+            for (int t = tid; t < rest * (k - j - 1); t += blockDim.x) {
+                const int ip = i + 1 + t / (k - j - 1), kk = j + 1 + t % (k - j - 1);
+                Ps[ip * k + kk] = fma(-Ps[ip * k + j], cfs[i * k + kk], Ps[ip * k + kk]);
+                if (kk >= j0 + ip) Gs[ip * k + kk] = fma(-Rj[j0 + ip], Rj[kk], Gs[ip * k + kk]);
+            }
+            __syncthreads();
         }
+        const int j1 = j0 + nb;
+        // reflector entries of the panel's own rows (below the diagonal) come from
+        // the updated panel rows; rows >= j1 get the in-panel updates here
+        for (int t = tid; t < nb * nb; t += blockDim.x) {
+            const int ip = t / nb, i = t % nb;
+            const int rg = j0 + ip;
+            if (i < ip && rg >= r0 && rg < r1) Ys[(rg - r0) * k + j0 + i] = Ps[ip * k + j0 + i];
+        }
+        {
+            const int rs = max(r0, j1) - r0;
+            for (int r = rs + tid; r < nr; r += blockDim.x)
+                for (int i = 0; i < nb; ++i) {
+                    const double v = Ys[r * k + j0 + i];
+                    for (int ip = i + 1; ip < nb; ++ip) Ys[r * k + j0 + ip] = fma(-v, cfs[i * k + j0 + ip], Ys[r * k + j0 + ip]);
+                }
+        }
+        __syncthreads();
+        const int nn1 = min(QB, k - j1);
+        if (j1 < k) gram_pass(j0, nb, j1, nn1, acc_buf(blk + 1), pub_buf(blk + 1));
+        j0 = j1;
+        nn0 = nn1;
+        ++blk;
     }
 
     // ---------------------------------------------------------- reflectors out
@@ -214,7 +279,6 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             if (alps[rr] < 0.0) a.R[t] = -a.R[t];
         }
     }
-    (void)step;
 }
 
 // W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
@@ -343,7 +407,10 @@ __global__ void qr_form_q_kernel(long long n, int k, const double *ta, double *Q
     }
 }
 
-size_t qr_smem_bytes(int rows_per, int k) { return sizeof(double) * ((size_t)rows_per * k + 6 * (size_t)k); }
+size_t qr_smem_bytes(int rows_per, int k)
+{
+    return sizeof(double) * ((size_t)rows_per * k + 3 * (size_t)QB * k + 4 * (size_t)k + QB);
+}
 
 int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
 {
@@ -359,7 +426,8 @@ int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
 
 }  // namespace
 
-size_t qr_scratch_doubles(int k) { return (size_t)5 * k + 8; }
+size_t qr_scratch_doubles(int k) { return (size_t)3 * QB * k + 8; }
+size_t qr_rowbuf_doubles(int k) { return (size_t)2 * QB * k; }
 
 int qr_supported(int n, int k)
 {
@@ -382,11 +450,11 @@ static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y,
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel, QR_THREADS, smem);
     if (per_sm * device_sm_count() < G) return cudaErrorCooperativeLaunchTooLarge;
-    cudaError_t e = cudaMemsetAsync(s.sbuf, 0, sizeof(double) * 3 * k, st);
+    cudaError_t e = cudaMemsetAsync(s.sbuf, 0, sizeof(double) * 3 * QB * k, st);
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return e;
-    QrArgs a{n, k, G, rows_per, Y, nullptr, R, s.V, s.ta, s.sbuf, s.rowbuf, s.bar, s.err};
+    QrArgs a{n, k, G, rows_per, Y, R, s.V, s.ta, s.sbuf, s.rowbuf, s.bar, s.err};
     void *args[] = {&a};
     CTM_COUNT_LAUNCH(1);
     return cudaLaunchCooperativeKernel((void *)qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st);
