@@ -85,15 +85,16 @@ struct QrArgs {
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
 {
     extern __shared__ double sm[];
-    __shared__ int stop_sh;
+    __shared__ int stop_sh[2];
     const int k = a.k;
+    const int ld = k | 1;   // odd row pitch: a warp reading one column of 16 rows hits 16 distinct bank pairs
     const int c = blockIdx.x;
     const int r0 = c * a.rows_per;
     const int r1 = min(a.n, r0 + a.rows_per);
     const int nr = max(0, r1 - r0);
     const int tid = threadIdx.x;
-    double *Ys = sm;                                // rows_per x k
-    double *Gs = Ys + (size_t)a.rows_per * k;       // QB x k: panel Gram rows, downdated
+    double *Ys = sm;                                // rows_per x ld
+    double *Gs = Ys + (size_t)a.rows_per * ld;      // QB x k: panel Gram rows, downdated
     double *Ps = Gs + QB * k;                       // QB x k: panel rows, updated
     double *cfs = Ps + QB * k;                      // QB x k: tau_j v_j^T a_kk
     double *Rj = cfs + QB * k;                      // k: current row of R
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     auto acc_buf = [&](int blk) { return a.sbuf + (size_t)(blk % 3) * QB * k; };
     auto pub_buf = [&](int blk) { return a.rowbuf + (size_t)(blk & 1) * QB * k; };
 
-    for (int t = tid; t < nr * k; t += blockDim.x) Ys[t] = a.Y[(size_t)r0 * k + t];
+    for (int t = tid; t < nr * k; t += blockDim.x) Ys[(t / k) * ld + t % k] = a.Y[(size_t)r0 * k + t];
     __syncthreads();
 
     // Apply the reflectors of the panel at j0 (width nb, coefficients cfs, vectors
@@ -122,10 +123,10 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
                 const int r = rs + t / nn, col = j1 + t % nn;
                 double s0 = 0.0, s1 = 0.0;
                 for (int i = 0; i < nb; i += 2) {
-                    s0 = fma(Ys[r * k + j0 + i], cfs[i * k + col], s0);
-                    if (i + 1 < nb) s1 = fma(Ys[r * k + j0 + i + 1], cfs[(i + 1) * k + col], s1);
+                    s0 = fma(Ys[r * ld + j0 + i], cfs[i * k + col], s0);
+                    if (i + 1 < nb) s1 = fma(Ys[r * ld + j0 + i + 1], cfs[(i + 1) * k + col], s1);
                 }
-                Ys[r * k + col] -= s0 + s1;
+                Ys[r * ld + col] -= s0 + s1;
             }
             __syncthreads();
         }
@@ -141,19 +142,19 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             if (t < ncols * P) {
                 const bool upd = nb > 0 && kk >= j1 + nn;
                 for (int r = rs + part; r < nr; r += P) {
-                    double x = Ys[r * k + kk];
+                    double x = Ys[r * ld + kk];
                     if (upd) {
                         double s0 = 0.0, s1 = 0.0;
                         for (int i = 0; i < nb; i += 2) {
-                            s0 = fma(Ys[r * k + j0 + i], cfs[i * k + kk], s0);
-                            if (i + 1 < nb) s1 = fma(Ys[r * k + j0 + i + 1], cfs[(i + 1) * k + kk], s1);
+                            s0 = fma(Ys[r * ld + j0 + i], cfs[i * k + kk], s0);
+                            if (i + 1 < nb) s1 = fma(Ys[r * ld + j0 + i + 1], cfs[(i + 1) * k + kk], s1);
                         }
                         x -= s0 + s1;
-                        Ys[r * k + kk] = x;
+                        Ys[r * ld + kk] = x;
                     }
 #pragma unroll
                     for (int i = 0; i < QB; ++i)
-                        if (i < nn && j1 + i <= kk) g[i] = fma(Ys[r * k + j1 + i], x, g[i]);
+                        if (i < nn && j1 + i <= kk) g[i] = fma(Ys[r * ld + j1 + i], x, g[i]);
                     const int rg = r0 + r;
                     if (rg < j1 + nn) pub[(rg - j1) * k + kk] = x;
                 }
@@ -165,6 +166,22 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
                 if (t < ncols * P && part == 0 && nrow > 0 && i < nn && j1 + i <= kk) atomicAdd(&acc[i * k + kk], v);
             }
         }
+    };
+
+    // Reflector of column j from its (downdated) squared norm below the diagonal
+    // and its pivot entry: alpha = -sign(x_0)|x|, v_0 = x_0 - alpha,
+    // tau = 2 / v^T v = 1 / (|x| (|x| + |x_0|)).
+    auto reflector = [&](int j, double nrm2, double x0) {
+        const double nrm = sqrt(nrm2);
+        double tau = 0.0, alpha = x0, v0 = 0.0;
+        if (nrm > 0.0) {
+            alpha = (x0 >= 0.0) ? -nrm : nrm;
+            v0 = x0 - alpha;
+            tau = 1.0 / (nrm * (nrm + fabs(x0)));
+        }
+        taus[j] = tau;
+        v0s[j] = v0;
+        alps[j] = (nrm > 0.0) ? alpha : 0.0;
     };
 
     int j0 = 0, nn0 = min(QB, k), blk = 0;
@@ -184,72 +201,75 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
         }
         __syncthreads();
         if (tid < nn0) g0[tid] = Gs[tid * k + j0 + tid];
+        if (tid == 0) {
+            reflector(j0, Gs[j0], Ps[j0]);
+            stop_sh[0] = -1;
+        }
         // ------------------------------------------------ the panel's reflectors
+        // Per column j two passes.  A: thread kk forms cf = tau v^T a_kk and
+        // R[j][kk] from row i (already downdated), and the thread owning column
+        // j+1 derives reflector j+1 right away from its own entries.  B: the later
+        // panel rows and Gram rows are downdated by H_j.
         int nb = nn0;
         for (int i = 0; i < nn0; ++i) {
-            const int j = j0 + i;
-            if (tid == 0) {
-                const double nrm2 = Gs[i * k + j], x0 = Ps[i * k + j];
-                int stop = -1;
-                if (i > 0 && !(nrm2 >= QR_DOWNDATE_MIN * g0[i])) {
-                    stop = i;   // cancellation: column j starts the next panel from fresh sums
-                } else {
-                    const double nrm = sqrt(nrm2);
-                    double tau = 0.0, alpha = x0, v0 = 0.0;
-                    if (nrm > 0.0) {
-                        alpha = (x0 >= 0.0) ? -nrm : nrm;
-                        v0 = x0 - alpha;
-                        tau = 1.0 / (nrm * (nrm + fabs(x0)));   // 2 / v^T v
-                    }
-                    taus[j] = tau;
-                    v0s[j] = v0;
-                    alps[j] = (nrm > 0.0) ? alpha : 0.0;
-                }
-                stop_sh = stop;
-            }
             __syncthreads();
-            if (stop_sh >= 0) {
-                nb = stop_sh;
+            if (stop_sh[i & 1] >= 0) {
+                nb = i;
                 break;
             }
+            const int j = j0 + i;
             const double tau = taus[j], v0 = v0s[j], alpha = alps[j];
             for (int kk = tid; kk < k; kk += blockDim.x) {
-                double rv = 0.0;
-                if (kk == j) {
-                    rv = alpha;
-                } else if (kk > j) {
-                    const double cf = tau * (Gs[i * k + kk] - alpha * Ps[i * k + kk]);
+                double rv = (kk == j) ? alpha : 0.0;
+                if (kk > j) {
+                    const double pik = Ps[i * k + kk];
+                    const double cf = tau * (Gs[i * k + kk] - alpha * pik);
+                    rv = pik - v0 * cf;
                     cfs[i * k + kk] = cf;
-                    rv = Ps[i * k + kk] - v0 * cf;
                     Rj[kk] = rv;
+                    if (kk == j + 1 && i + 1 < nn0) {
+                        const double nrm2 = fma(-rv, rv, Gs[(i + 1) * k + kk]);
+                        const double x0 = fma(-Ps[(i + 1) * k + j], cf, Ps[(i + 1) * k + kk]);
+                        int stop = -1;
+                        if (!(nrm2 >= QR_DOWNDATE_MIN * g0[i + 1])) stop = i + 1;   // cancellation
+                        else reflector(kk, nrm2, x0);
+                        stop_sh[(i + 1) & 1] = stop;
+                    }
                 }
                 if (c == 0) a.R[(size_t)j * k + kk] = rv;
             }
             __syncthreads();
-            // H_j on the later panel rows and Gram rows (rows >= j+1 from here on)
             const int rest = nn0 - 1 - i;
             for (int t = tid; t < rest * (k - j - 1); t += blockDim.x) {
                 const int ip = i + 1 + t / (k - j - 1), kk = j + 1 + t % (k - j - 1);
                 Ps[ip * k + kk] = fma(-Ps[ip * k + j], cfs[i * k + kk], Ps[ip * k + kk]);
                 if (kk >= j0 + ip) Gs[ip * k + kk] = fma(-Rj[j0 + ip], Rj[kk], Gs[ip * k + kk]);
             }
-            __syncthreads();
         }
         const int j1 = j0 + nb;
         // reflector entries of the panel's own rows (below the diagonal) come from
-        // the updated panel rows; rows >= j1 get the in-panel updates here
+        // the updated panel rows; rows >= j1 get the in-panel updates, one thread
+        // per row, in registers
         for (int t = tid; t < nb * nb; t += blockDim.x) {
             const int ip = t / nb, i = t % nb;
             const int rg = j0 + ip;
-            if (i < ip && rg >= r0 && rg < r1) Ys[(rg - r0) * k + j0 + i] = Ps[ip * k + j0 + i];
+            if (i < ip && rg >= r0 && rg < r1) Ys[(rg - r0) * ld + j0 + i] = Ps[ip * k + j0 + i];
         }
         {
             const int rs = max(r0, j1) - r0;
-            for (int r = rs + tid; r < nr; r += blockDim.x)
-                for (int i = 0; i < nb; ++i) {
-                    const double v = Ys[r * k + j0 + i];
-                    for (int ip = i + 1; ip < nb; ++ip) Ys[r * k + j0 + ip] = fma(-v, cfs[i * k + j0 + ip], Ys[r * k + j0 + ip]);
-                }
+            for (int r = rs + tid; r < nr; r += blockDim.x) {
+                double v[QB];
+#pragma unroll
+                for (int i = 0; i < QB; ++i) v[i] = (i < nb) ? Ys[r * ld + j0 + i] : 0.0;
+#pragma unroll
+                for (int i = 0; i < QB; ++i)
+#pragma unroll
+                    for (int ip = i + 1; ip < QB; ++ip)
+                        if (ip < nb) v[ip] = fma(-v[i], cfs[i * k + j0 + ip], v[ip]);
+#pragma unroll
+                for (int i = 1; i < QB; ++i)
+                    if (i < nb) Ys[r * ld + j0 + i] = v[i];
+            }
         }
         __syncthreads();
         const int nn1 = min(QB, k - j1);
@@ -264,7 +284,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
         const int r = r0 + t / k, j = t % k;
         double v = 0.0;
         if (r == j) v = v0s[j];
-        else if (r > j) v = Ys[t];
+        else if (r > j) v = Ys[(t / k) * ld + j];
         if (taus[j] == 0.0) v = 0.0;
         a.V[(size_t)r0 * k + t] = v;
     }
@@ -409,7 +429,7 @@ __global__ void qr_form_q_kernel(long long n, int k, const double *ta, double *Q
 
 size_t qr_smem_bytes(int rows_per, int k)
 {
-    return sizeof(double) * ((size_t)rows_per * k + 3 * (size_t)QB * k + 4 * (size_t)k + QB);
+    return sizeof(double) * ((size_t)rows_per * (k | 1) + 3 * (size_t)QB * k + 4 * (size_t)k + QB);
 }
 
 int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
