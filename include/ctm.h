@@ -93,7 +93,10 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
  * T' = Q^T (T a a) Q/|.|, and delta = |s(C') - s(C)|_2 of the unit-norm
  * descending singular values.  delta_host (may be NULL) receives the last
  * delta and makes the call synchronous.  Returns CTM_ENONFINITE if the new
- * environment holds NaN/Inf (checked only when delta_host is given). */
+ * environment holds NaN/Inf (checked only when delta_host is given).
+ * Once the context has run a step, a call with nsteps >= 2 replays the nsteps
+ * steps as one CUDA graph (captured on the first such call with that nsteps,
+ * and kept until another nsteps is requested); the work is the same. */
 int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
 
 /* Sec. II.B: repeat steps until delta < tol (tol <= 0: cfg->tol) or max_steps

@@ -413,37 +413,59 @@ int check_env_finite(ctm_ctx *c)
     return f ? CTM_ENONFINITE : CTM_OK;
 }
 
-int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int *steps_out, double *delta_out)
+// Capture `nsteps` steps (spectrum fork/join included) into c->graph on the
+// private stream c->own; the caller has switched c->stream to c->own.  Kernel
+// launches counted during the capture are what one replay launches.  A launch
+// that cannot be captured leaves graph_failed set and the caller runs eagerly.
+int capture_steps(ctm_ctx *c, int nsteps)
 {
-    if (c->graph && c->graph_steps != check_every) {
+    if (c->graph && c->graph_steps == nsteps) return CTM_OK;
+    if (c->graph) {
         cudaGraphExecDestroy(c->graph);
         c->graph = nullptr;
     }
-    if (!c->graph && !c->graph_failed) {
-        cudaGraph_t g = nullptr;
-        CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = CTM_OK;
-        for (int i = 0; i < check_every && rc == CTM_OK; ++i) rc = enqueue_step(c);
-        if (rc == CTM_OK) rc = join_side(c);
-        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-        if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph, g, 0);
-        if (g) cudaGraphDestroy(g);
-        if (rc != CTM_OK || e != cudaSuccess || !c->graph) {
-            // capture unsupported for some launch: replay eagerly instead
-            cudaGetLastError();
-            c->graph = nullptr;
-            c->graph_failed = 1;
-        } else {
-            c->graph_steps = check_every;
-        }
+    if (c->graph_failed) return CTM_OK;
+    cudaGraph_t g = nullptr;
+    const unsigned long long l0 = g_ctm_launches;
+    CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    int rc = CTM_OK;
+    for (int i = 0; i < nsteps && rc == CTM_OK; ++i) rc = enqueue_step(c);
+    if (rc == CTM_OK) rc = join_side(c);
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    c->side_pending = 0;
+    if (rc != CTM_OK || e != cudaSuccess || !c->graph) {
+        cudaGetLastError();
+        c->graph = nullptr;
+        c->graph_failed = 1;
+    } else {
+        c->graph_steps = nsteps;
+        c->graph_kernels = g_ctm_launches - l0;
     }
+    g_ctm_launches = l0;   // nothing ran yet: replays add graph_kernels
+    return CTM_OK;
+}
+
+int graph_launch(ctm_ctx *c)
+{
+    CK(cudaGraphLaunch(c->graph, c->stream));
+    CTM_COUNT_LAUNCH(c->graph_kernels);
+    return CTM_OK;
+}
+
+int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int *steps_out, double *delta_out)
+{
+    int rc0 = capture_steps(c, check_every);
+    if (rc0 != CTM_OK) return rc0;
     int done = 0;
     double delta = INFINITY;
     while (done < max_steps) {
         int chunk = check_every;
         if (done + chunk > max_steps) chunk = max_steps - done;
         if (c->graph && chunk == c->graph_steps) {
-            CK(cudaGraphLaunch(c->graph, c->stream));
+            int rc = graph_launch(c);
+            if (rc != CTM_OK) return rc;
         } else {
             for (int i = 0; i < chunk; ++i) {
                 int rc = enqueue_step(c);
@@ -586,7 +608,27 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
 int ctm_step(ctm_ctx *c, int nsteps, double *delta_host)
 {
     if (!c || nsteps < 0) return CTM_EINVAL;
-    for (int i = 0; i < nsteps; ++i) {
+    bool done = false;
+    if (nsteps >= 2 && c->steps_done > 0) {
+        // several steps after the first eager one (whose launches ran the
+        // autotuners): replay them as one captured graph, ordered after the
+        // caller's stream
+        cudaStream_t user = c->stream;
+        CK(cudaEventRecord(c->ev_in, user));
+        CK(cudaStreamWaitEvent(c->own, c->ev_in, 0));
+        c->stream = c->own;
+        int rc = capture_steps(c, nsteps);
+        if (rc == CTM_OK && c->graph) {
+            rc = graph_launch(c);
+            done = (rc == CTM_OK);
+        }
+        c->stream = user;
+        if (cudaEventRecord(c->ev_out, c->own) != cudaSuccess) return CTM_ECUDA;
+        if (cudaStreamWaitEvent(user, c->ev_out, 0) != cudaSuccess) return CTM_ECUDA;
+        if (rc != CTM_OK) return rc;
+        if (done) c->steps_done += nsteps;
+    }
+    for (int i = 0; i < nsteps && !done; ++i) {
         int rc = enqueue_step(c);
         if (rc != CTM_OK) return rc;
         c->steps_done++;

@@ -41,10 +41,12 @@ struct ctm_ctx {
     double *norm_part;
     // energy
     double *b, *Y1o, *G2, *P5a, *P5b, *rho_part, *rho_raw, *eout, *h;
-    // graph of `graph_steps` steps
+    // graph of `graph_steps` steps (captured on the private stream), and how many
+    // kernels one replay launches
     cudaGraphExec_t graph;
     int graph_steps;
     int graph_failed;
+    unsigned long long graph_kernels;
     int side_pending;
     // kernel timing (ctm_step_profiled): events around each contraction launch
     int prof_on, prof_n;

@@ -4,7 +4,7 @@
 //
 // One cooperative launch over G <= #SM CTAs.  CTA c keeps its block of rows of
 // Y (and later of the reflectors) in shared memory for the whole factorisation.
-// Columns are taken in panels of up to QB.  For a panel starting at column j0
+// Columns are taken in panels of up to QB (8).  For a panel starting at column j0
 // every CTA forms, over its rows >= j0, the partial Gram rows
 // G[i][kk] = a_{j0+i}^T a_kk (i < QB, kk >= j0+i) and the owners publish the
 // panel's rows j0 .. j0+QB-1; the partial sums meet in global memory through
