@@ -52,7 +52,8 @@ constexpr int SP_BSLOTS = 2;
 constexpr int SP_EPI_WARPS = 16;                 // 4 per TMEM sub-partition
 constexpr int SP_EPI_THREADS = 32 * SP_EPI_WARPS;
 constexpr int SP_THREADS = 64 + SP_EPI_THREADS;  // producer, MMA issuer, epilogue
-constexpr long long SP_SPIN = 4000000LL;   // x ~200 ns sleep: ~1 s
+constexpr unsigned SP_SUSPEND_NS = 2000;        // try_wait suspend-time hint: woken at phase completion
+constexpr unsigned long long SP_WAIT_NS = 1000000000ULL;   // give up a wait after ~1 s
 
 __device__ __forceinline__ long long off2(const Idx2 &x, int i)
 {
@@ -238,25 +239,33 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 {
     uint32_t ok;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(ok)
-        : "r"(bar), "r"(parity)
+        : "r"(bar), "r"(parity), "r"(SP_SUSPEND_NS)
         : "memory");
     return ok != 0;
 }
-// bounded wait: false (and the abort flag raised) after ~1 s
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Bounded wait.  try_wait suspends the thread until the phase completes (or the
+// hint expires), so a waiting producer / MMA thread resumes without a sleep
+// quantum; after ~1 s of global time it gives up: false, abort flag raised.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort_flag)
 {
-    long long it = 0;
-    while (!mbar_try(bar, parity)) {
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    for (unsigned it = 1;; ++it) {
+        if (mbar_try(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (++it > SP_SPIN) {
+        if ((it & 15) == 0 && global_ns() - t0 > SP_WAIT_NS) {
             *abort_flag = 1;
             return false;
         }
-        __nanosleep(128);
     }
-    return true;
 }
 __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t bar)
 {
@@ -333,7 +342,7 @@ struct SplitArgs {
     int *err;
 };
 
-template <int NT>
+template <int NT, int T>
 __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
 {
     constexpr int A_TILE = SP_BM * SP_BK * 2;   // 16 KB
@@ -348,7 +357,6 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
     unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *Asm = sm;                                   // SP_ASLOTS x A_TILE
     unsigned char *Bsm = sm + SP_ASLOTS * A_TILE;              // SP_BSLOTS x (T x B_TILE)
-    const int T = a.T;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const uint32_t bar0 = smem_u32(bars);
     auto A_full = [&](int s) { return bar0 + 8u * s; };
@@ -427,11 +435,12 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
             const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
                                    ((uint32_t)(SP_BM >> 4) << 24);
+            // descriptors of ring slot 0; slot s is (s * tile bytes) >> 4 further on
+            const uint64_t ad0 = sdesc_sw128(smem_u32(Asm)), bd0 = sdesc_sw128(smem_u32(Bsm));
             int u = 0, b = 0, chunk = 0;
             for (int c = c_beg; c < c_end && !*abort_flag; ++c, ++chunk) {
                 if (!mbar_wait(ACC_EMPTY, (chunk & 1) ^ 1, abort_flag)) break;
                 tc_fence_after();
-                uint32_t started = 0;   // bit t: level t already written in this chunk
                 const int kt0 = c * SP_KT_PER_CHUNK, kt1 = min(a.kTiles, kt0 + SP_KT_PER_CHUNK);
                 for (int kt = kt0; kt < kt1; ++kt) {
                     const int sb = b % SP_BSLOTS;
@@ -439,18 +448,26 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
                     tc_fence_after();
                     const int kvalid = min(SP_BK, a.K - kt * SP_BK);
                     const int ksteps = (kvalid + 15) / 16;
+                    // level t = i + j is first written by (i = 0, kk = 0) of the chunk's first K tile
+                    const uint32_t acc0 = (kt == kt0) ? 0u : 1u;
+                    const uint64_t bdb = bd0 + (uint64_t)((sb * T * B_TILE) >> 4);
+#pragma unroll
                     for (int i = 0; i < T; ++i) {
                         const int sa = u % SP_ASLOTS;
                         if (!mbar_wait(A_full(sa), (u / SP_ASLOTS) & 1, abort_flag)) break;
                         tc_fence_after();
-                        const uint64_t ad = sdesc_sw128(smem_u32(Asm + sa * A_TILE));
+                        const uint64_t ad = ad0 + (uint64_t)((sa * A_TILE) >> 4);
+#pragma unroll
                         for (int j = 0; j < T - i; ++j) {
-                            const int t = i + j;
-                            const uint64_t bd = sdesc_sw128(smem_u32(Bsm + (sb * T + j) * B_TILE));
-                            for (int kk = 0; kk < ksteps; ++kk) {
-                                const uint32_t acc = (started >> t) & 1u;
-                                mma_bf16(tmem + (uint32_t)(t * NT), ad + 2ull * kk, bd + 2ull * kk, idesc, acc);
-                                started |= 1u << t;
+                            const uint32_t d = tmem + (uint32_t)((i + j) * NT);
+                            const uint64_t bd = bdb + (uint64_t)((j * B_TILE) >> 4);
+                            if (ksteps == SP_BK / 16) {
+#pragma unroll
+                                for (int kk = 0; kk < SP_BK / 16; ++kk)
+                                    mma_bf16(d, ad + 2ull * kk, bd + 2ull * kk, idesc, (i == 0 && kk == 0) ? acc0 : 1u);
+                            } else {
+                                for (int kk = 0; kk < ksteps; ++kk)
+                                    mma_bf16(d, ad + 2ull * kk, bd + 2ull * kk, idesc, (i == 0 && kk == 0) ? acc0 : 1u);
                             }
                         }
                         mma_commit(A_empty(sa));
@@ -465,10 +482,9 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
             // every MMA this thread issued has completed once DRAIN flips (bounded wait)
             mma_commit(DRAIN);
             {
-                volatile int never = 0;
-                long long it = 0;
-                while (!mbar_try(DRAIN, 0) && ++it < SP_SPIN) __nanosleep(128);
-                (void)never;
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(DRAIN, 0) && global_ns() - t0 < SP_WAIT_NS) {
+                }
             }
         }
     } else {
@@ -638,13 +654,25 @@ SplitPlan split_plan_caps(int M, int N, int K, int T)
     return c;
 }
 
+template <int NT, int T>
+static cudaError_t split_attr()
+{
+    return cudaFuncSetAttribute(gemm_split_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)split_smem_bytes<NT>(T));
+}
+
 cudaError_t split_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(gemm_split_kernel<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)split_smem_bytes<64>(5));
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(gemm_split_kernel<96>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)split_smem_bytes<96>(5));
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = split_attr<64, 2>();
+    if (e == cudaSuccess) e = split_attr<64, 3>();
+    if (e == cudaSuccess) e = split_attr<64, 4>();
+    if (e == cudaSuccess) e = split_attr<64, 5>();
+    if (e == cudaSuccess) e = split_attr<96, 2>();
+    if (e == cudaSuccess) e = split_attr<96, 3>();
+    if (e == cudaSuccess) e = split_attr<96, 4>();
+    if (e == cudaSuccess) e = split_attr<96, 5>();
+    return e;
 }
 
 // Exponents and digit slices of one operand X(r, k) (rows of A, columns of B).
@@ -726,10 +754,17 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
     dim3 grid(p.nTiles, p.mTiles, p.ksplit);
     CTM_COUNT_LAUNCH(1);
     if (ev) cudaEventRecord(ev[0], st);
-    if (p.NT == 96)
-        gemm_split_kernel<96><<<grid, SP_THREADS, split_smem_bytes<96>(T), st>>>(a);
-    else
-        gemm_split_kernel<64><<<grid, SP_THREADS, split_smem_bytes<64>(T), st>>>(a);
+#define CTM_SPLIT_LAUNCH(nt, t) \
+    if (p.NT == nt && T == t) gemm_split_kernel<nt, t><<<grid, SP_THREADS, split_smem_bytes<nt>(t), st>>>(a);
+    CTM_SPLIT_LAUNCH(64, 2)
+    CTM_SPLIT_LAUNCH(64, 3)
+    CTM_SPLIT_LAUNCH(64, 4)
+    CTM_SPLIT_LAUNCH(64, 5)
+    CTM_SPLIT_LAUNCH(96, 2)
+    CTM_SPLIT_LAUNCH(96, 3)
+    CTM_SPLIT_LAUNCH(96, 4)
+    CTM_SPLIT_LAUNCH(96, 5)
+#undef CTM_SPLIT_LAUNCH
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
     if (p.ksplit > 1) {
