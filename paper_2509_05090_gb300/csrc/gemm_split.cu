@@ -20,7 +20,8 @@
 // 8 (T-1)): the int64 -> FP64 conversion instruction and an exact shift of the
 // exponent field.
 //
-// Kernel.  Tile 128 x NT (NT = 64 or 96), K staged 64 at a time.  The slicing
+// Kernel.  Tile 128 x NT (NT = 64 or 96), K staged 64 at a time; one MMA covers up to
+// 256 / NT slice pairs (N = up to 256), since narrow MMAs run far below the tensor peak.  The slicing
 // pre-pass writes each operand tile in the exact shared-memory image the MMA
 // expects (K-major, 128-byte swizzle: row r of a 128-byte-wide tile at
 // (r/8)*1024 + (r%8)*128, 16-byte chunk c at (c ^ (r%8))*16), so one bulk
@@ -400,12 +401,15 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
     const uint32_t tmem = tmem_base_sh;
 
     if (warp == 0) {
-        // ------------------------------------------------ producer: bulk copies
+        // ------------------------------------------------ producers: bulk copies
+        // lane 0 streams the B tiles (all T slices of a K tile per slot), lane 1 the
+        // A slices; each blocks only on its own ring, so the A stream runs ahead of a
+        // full B ring instead of queueing behind it
         if (lane == 0) {
-            int u = 0, b = 0;
+            int b = 0;
             for (int c = c_beg; c < c_end && !*abort_flag; ++c) {
                 const int kt0 = c * SP_KT_PER_CHUNK, kt1 = min(a.kTiles, kt0 + SP_KT_PER_CHUNK);
-                for (int kt = kt0; kt < kt1; ++kt) {
+                for (int kt = kt0; kt < kt1; ++kt, ++b) {
                     const int sb = b % SP_BSLOTS;
                     if (!mbar_wait(B_empty(sb), ((b / SP_BSLOTS) & 1) ^ 1, abort_flag)) break;
                     mbar_expect_tx(B_full(sb), (uint32_t)(T * B_TILE));
@@ -414,17 +418,21 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
                             a.Bpk + j * a.b_slice_bytes + ((long long)nt * a.kTiles + kt) * B_TILE;
                         bulk_g2s(smem_u32(Bsm + (sb * T + j) * B_TILE), src, B_TILE, B_full(sb));
                     }
-                    ++b;
-                    for (int i = 0; i < T; ++i) {
+                }
+            }
+        } else if (lane == 1) {
+            int u = 0;
+            for (int c = c_beg; c < c_end && !*abort_flag; ++c) {
+                const int kt0 = c * SP_KT_PER_CHUNK, kt1 = min(a.kTiles, kt0 + SP_KT_PER_CHUNK);
+                for (int kt = kt0; kt < kt1 && !*abort_flag; ++kt) {
+                    for (int i = 0; i < T; ++i, ++u) {
                         const int sa = u % SP_ASLOTS;
                         if (!mbar_wait(A_empty(sa), ((u / SP_ASLOTS) & 1) ^ 1, abort_flag)) break;
                         mbar_expect_tx(A_full(sa), (uint32_t)A_TILE);
                         const unsigned char *src =
                             a.Apk + i * a.a_slice_bytes + ((long long)mt * a.kTiles + kt) * A_TILE;
                         bulk_g2s(smem_u32(Asm + sa * A_TILE), src, A_TILE, A_full(sa));
-                        ++u;
                     }
-                    if (*abort_flag) break;
                 }
             }
         }
@@ -433,8 +441,11 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
         if (lane == 0) {
             // kind::f16: D = F32 (bits 4-5 = 1), A = B = BF16 (bits 7-9, 10-12 = 1),
             // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
-            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NT >> 3) << 17) |
-                                   ((uint32_t)(SP_BM >> 4) << 24);
+            const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SP_BM >> 4) << 24);
+            // The T B slices of a K tile are consecutive NT-row tiles of one 128-byte-swizzled
+            // operand and the level accumulators consecutive NT-column blocks of TMEM, so
+            // A_i times slices j0 .. j0+G-1 is one MMA of N = G NT (<= 256) into levels i+j0 ..
+            constexpr int G = 256 / NT;
             // descriptors of ring slot 0; slot s is (s * tile bytes) >> 4 further on
             const uint64_t ad0 = sdesc_sw128(smem_u32(Asm)), bd0 = sdesc_sw128(smem_u32(Bsm));
             int u = 0, b = 0, chunk = 0;
@@ -458,9 +469,11 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
                         tc_fence_after();
                         const uint64_t ad = ad0 + (uint64_t)((sa * A_TILE) >> 4);
 #pragma unroll
-                        for (int j = 0; j < T - i; ++j) {
-                            const uint32_t d = tmem + (uint32_t)((i + j) * NT);
-                            const uint64_t bd = bdb + (uint64_t)((j * B_TILE) >> 4);
+                        for (int j0 = 0; j0 < T - i; j0 += G) {
+                            const int nj = (T - i - j0 < G) ? T - i - j0 : G;
+                            const uint32_t idesc = idesc0 | ((uint32_t)((nj * NT) >> 3) << 17);
+                            const uint32_t d = tmem + (uint32_t)((i + j0) * NT);
+                            const uint64_t bd = bdb + (uint64_t)((j0 * B_TILE) >> 4);
                             if (ksteps == SP_BK / 16) {
 #pragma unroll
                                 for (int kk = 0; kk < SP_BK / 16; ++kk)
