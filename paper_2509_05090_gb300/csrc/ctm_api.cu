@@ -170,7 +170,7 @@ size_t layout(ctm_ctx *c, char *base)
         c->sw.partial = (void *)take(pp + 8);
         c->sw.partial_cap = pp;
         c->sw.err = c->err;
-        c->sw.autotune = 0;
+        c->sw.autotune = 1;   // the first eager call of each contraction shape times its plans
         const Shape ash[2] = {{(int)(chi * chi), (int)D2, (int)(D2 * D2)}, {(int)(chi * chi), (int)(D2 * D2), (int)D2}};
         for (int sl = 0; sl < 2; ++sl) {
             SplitPlan pl = split_plan_caps(ash[sl].M, ash[sl].N, ash[sl].K, c->split_T);

@@ -42,17 +42,21 @@ namespace {
 constexpr int SP_BM = 128;       // tile rows = TMEM lanes
 constexpr int SP_BK = 64;        // K per packed tile (128-byte rows)
 constexpr int SP_KT_PER_CHUNK = 4;   // 4 x 64 = 256 K per exact chunk
-// A-slice ring depth: deep enough that the next K tile's slices are in flight
-// while the current one is multiplied (within 227 KB with T = 5 B slices x 2).
+constexpr int SP_BSLOTS = 2;     // B ring: all T slices of a K tile per slot
+// Per tile width: A-slice ring depth (the next K tile's slices in flight while the
+// current one is multiplied, within 227 KB with T = 5 B slices x 2), epilogue warps
+// (four or two per TMEM sub-partition), TMEM columns (T NT <= the allocation) and
+// CTAs per SM.  NT = 48 is the two-CTAs-per-SM shape: 256 TMEM columns and ~109 KB
+// of shared memory each, so one CTA's epilogue overlaps the other's loads and MMAs.
 template <int NT>
-constexpr int sp_aslots()
-{
-    return NT == 96 ? 6 : 8;
-}
-constexpr int SP_BSLOTS = 2;
-constexpr int SP_EPI_WARPS = 16;                 // 4 per TMEM sub-partition
-constexpr int SP_EPI_THREADS = 32 * SP_EPI_WARPS;
-constexpr int SP_THREADS = 64 + SP_EPI_THREADS;  // producer, MMA issuer, epilogue
+struct SpCfg {
+    static constexpr int ASLOTS = NT == 96 ? 6 : (NT == 64 ? 8 : 3);
+    static constexpr int EPI_WARPS = NT == 48 ? 8 : 16;
+    static constexpr int EPI_THREADS = 32 * EPI_WARPS;
+    static constexpr int THREADS = 64 + EPI_THREADS;   // producers, MMA issuer, epilogue
+    static constexpr int TMEM_COLS = NT == 48 ? 256 : 512;
+    static constexpr int MIN_BLOCKS = NT == 48 ? 2 : 1;
+};
 constexpr unsigned SP_SUSPEND_NS = 2000;        // try_wait suspend-time hint: woken at phase completion
 constexpr unsigned long long SP_WAIT_NS = 1000000000ULL;   // give up a wait after ~1 s
 
@@ -194,9 +198,9 @@ __global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTi
 // The same packing for a transposed operand, X(r, k) = X[k * kstride + r]: a
 // block stages 32 rows x one 64-wide K tile through shared memory, reading with
 // the lanes along the contiguous rows and writing the swizzled chunks as above.
-__global__ void __launch_bounds__(256) split_pack_t_kernel(int R, int K, int rowsT, int kTiles, int T, const double *X,
-                                                           long long kstride, const int *e, unsigned char *out,
-                                                           long long slice_bytes)
+__global__ void __launch_bounds__(256) split_pack_t_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles, int T,
+                                                           const double *X, long long kstride, const int *e,
+                                                           unsigned char *out, long long slice_bytes)
 {
     __shared__ long long Fs[32][SP_BK + 1];
     const int r0 = blockIdx.x * 32, kt = blockIdx.y;
@@ -214,6 +218,7 @@ __global__ void __launch_bounds__(256) split_pack_t_kernel(int R, int K, int row
     __syncthreads();
     const int r = threadIdx.x >> 3, c8 = threadIdx.x & 7;
     const int gr = r0 + r;
+    if (gr >= rowsTotal) return;   // past the last padded tile (rowsT need not divide by 32)
     long long F[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) F[q] = Fs[r][c8 * 8 + q];
@@ -344,12 +349,15 @@ struct SplitArgs {
 };
 
 template <int NT, int T>
-__global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
+__global__ void __launch_bounds__(SpCfg<NT>::THREADS, SpCfg<NT>::MIN_BLOCKS) gemm_split_kernel(SplitArgs a)
 {
     constexpr int A_TILE = SP_BM * SP_BK * 2;   // 16 KB
     constexpr int B_TILE = NT * SP_BK * 2;
-    constexpr int QW = NT / 4;   // columns per epilogue warp
-    constexpr int SP_ASLOTS = sp_aslots<NT>();
+    constexpr int QW = NT / (SpCfg<NT>::EPI_WARPS / 4);   // columns per epilogue warp
+    constexpr int SP_ASLOTS = SpCfg<NT>::ASLOTS;
+    constexpr int SP_EPI_WARPS = SpCfg<NT>::EPI_WARPS;
+    constexpr int SP_EPI_THREADS = SpCfg<NT>::EPI_THREADS;
+    constexpr int TMEM_COLS = SpCfg<NT>::TMEM_COLS;
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t bars[SP_ASLOTS * 2 + SP_BSLOTS * 2 + 3];
     __shared__ uint32_t tmem_base_sh;
@@ -391,7 +399,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
     }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(512)
+                     "r"(TMEM_COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -503,7 +511,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
     } else {
         // ------------------------------------------------ epilogue warps 2..17
         const int sub = warp & 3;              // TMEM sub-partition this warp may read
-        const int part = (warp - 2) >> 2;      // which quarter of the NT columns
+        const int part = (warp - 2) >> 2;      // which slice of the NT columns
         const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
         long long acc[QW];
 #pragma unroll
@@ -591,7 +599,7 @@ __global__ void __launch_bounds__(SP_THREADS, 1) gemm_split_kernel(SplitArgs a)
     if (warp == 0) {
         __syncwarp();
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
     }
     if (threadIdx.x == 0 && abort_sh) atomicExch(a.err, 2);
 }
@@ -615,14 +623,16 @@ int pick_nt(int N, int T)
     return (w96 <= w64) ? 96 : 64;
 }
 
-// At least 120 KB, so a second CTA never shares the SM (each CTA holds all 512 TMEM columns).
+// A one-CTA-per-SM shape asks for at least 120 KB, so a second CTA never shares the SM
+// (it holds all 512 TMEM columns); the NT = 48 shape fits two per SM.
 template <int NT>
 size_t split_smem_bytes(int T)
 {
-    size_t b = 1024 + (size_t)sp_aslots<NT>() * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
+    size_t b = 1024 + (size_t)SpCfg<NT>::ASLOTS * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
     const size_t out_stage = 1024 + (size_t)SP_BM * (NT + 1) * 8 + (size_t)(SP_BM + NT) * 8;   // epilogue reuse
     if (b < out_stage) b = out_stage;
-    return b < 120 * 1024 ? 120 * 1024 : b;
+    if (SpCfg<NT>::MIN_BLOCKS == 1 && b < 120 * 1024) b = 120 * 1024;
+    return b;
 }
 
 }  // namespace
@@ -632,7 +642,9 @@ int split_supported_T(int T) { return T >= 2 && T <= 5; }
 SplitPlan split_plan(int M, int N, int K, int T, int nt_override, int ks_override)
 {
     SplitPlan p{};
-    p.NT = (nt_override == 64 || (nt_override == 96 && T * 96 <= 512)) ? nt_override : pick_nt(N, T);
+    p.NT = (nt_override == 64 || (nt_override == 96 && T * 96 <= 512) || (nt_override == 48 && T * 48 <= 256))
+               ? nt_override
+               : pick_nt(N, T);
     p.mTiles = (M + SP_BM - 1) / SP_BM;
     p.nTiles = (N + p.NT - 1) / p.NT;
     p.kTiles = (K + SP_BK - 1) / SP_BK;
@@ -658,7 +670,7 @@ SplitPlan split_plan(int M, int N, int K, int T, int nt_override, int ks_overrid
 SplitPlan split_plan_caps(int M, int N, int K, int T)
 {
     SplitPlan c = split_plan(M, N, K, T);
-    for (int nt : {64, 96}) {
+    for (int nt : {48, 64, 96}) {
         SplitPlan p = split_plan(M, N, K, T, nt, 0);
         if (p.b_pack_bytes > c.b_pack_bytes) c.b_pack_bytes = p.b_pack_bytes;
     }
@@ -685,6 +697,10 @@ cudaError_t split_prepare()
     if (e == cudaSuccess) e = split_attr<96, 3>();
     if (e == cudaSuccess) e = split_attr<96, 4>();
     if (e == cudaSuccess) e = split_attr<96, 5>();
+    if (e == cudaSuccess) e = split_attr<48, 2>();
+    if (e == cudaSuccess) e = split_attr<48, 3>();
+    if (e == cudaSuccess) e = split_attr<48, 4>();
+    if (e == cudaSuccess) e = split_attr<48, 5>();
     return e;
 }
 
@@ -701,8 +717,8 @@ static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 
         CTM_COUNT_LAUNCH(2);
         split_colexp_kernel<<<dim3((R + 127) / 128, (K + SP_COLEXP_K - 1) / SP_COLEXP_K), 128, 0, st>>>(R, K, X,
                                                                                                        kmap.s2, e);
-        split_pack_t_kernel<<<dim3(rowTiles * rowsT / 32, kTiles), 256, 0, st>>>(R, K, rowsT, kTiles, T, X, kmap.s2,
-                                                                                e, pk, slice_bytes);
+        split_pack_t_kernel<<<dim3((rowTiles * rowsT + 31) / 32, kTiles), 256, 0, st>>>(
+            R, K, rowsT, rowTiles * rowsT, kTiles, T, X, kmap.s2, e, pk, slice_bytes);
         return cudaGetLastError();
     }
     CTM_COUNT_LAUNCH(2);
@@ -768,7 +784,8 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
     CTM_COUNT_LAUNCH(1);
     if (ev) cudaEventRecord(ev[0], st);
 #define CTM_SPLIT_LAUNCH(nt, t) \
-    if (p.NT == nt && T == t) gemm_split_kernel<nt, t><<<grid, SP_THREADS, split_smem_bytes<nt>(t), st>>>(a);
+    if (p.NT == nt && T == t)                                                                               \
+        gemm_split_kernel<nt, t><<<grid, SpCfg<nt>::THREADS, split_smem_bytes<nt>(t), st>>>(a);
     CTM_SPLIT_LAUNCH(64, 2)
     CTM_SPLIT_LAUNCH(64, 3)
     CTM_SPLIT_LAUNCH(64, 4)
@@ -777,6 +794,10 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
     CTM_SPLIT_LAUNCH(96, 3)
     CTM_SPLIT_LAUNCH(96, 4)
     CTM_SPLIT_LAUNCH(96, 5)
+    CTM_SPLIT_LAUNCH(48, 2)
+    CTM_SPLIT_LAUNCH(48, 3)
+    CTM_SPLIT_LAUNCH(48, 4)
+    CTM_SPLIT_LAUNCH(48, 5)
 #undef CTM_SPLIT_LAUNCH
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (ev) cudaEventRecord(ev[1], st);
@@ -827,8 +848,8 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
     SplitPlan base = split_plan(g.M, g.N, g.K, T);
     const int chunks = (base.kTiles + SP_KT_PER_CHUNK - 1) / SP_KT_PER_CHUNK;
     std::vector<std::pair<int, int>> cands;
-    for (int nt : {64, 96}) {
-        if (nt == 96 && T * 96 > 512) continue;
+    for (int nt : {48, 64, 96}) {
+        if ((nt == 96 && T * 96 > 512) || (nt == 48 && T * 48 > 256)) continue;
         // auto, none, 2x, 1/2x, and the most splits that still fit one wave of CTAs
         const int one_wave = (int)(device_sm_count() / ((long long)base.mTiles * ((g.N + nt - 1) / nt)));
         for (int ks : {base.ksplit, 1, 2 * base.ksplit, base.ksplit / 2, one_wave}) {
