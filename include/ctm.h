@@ -87,6 +87,12 @@ size_t ctm_workspace_bytes(const ctm_config *cfg);
 int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t ws_bytes,
              void *stream, ctm_ctx **out);
 
+/* Autotuning (no counterpart in the paper).  The first eager call of each
+ * contraction shape in split mode times its candidate tile plans, and the first
+ * QR of each shape its grid size; the choices are kept for the process.  With
+ * the environment variable CTM_AUTOTUNE_CACHE=<file> they are also read from and
+ * appended to that text file, so another process runs the same plans. */
+
 /* Sec. II.B, Fig. 3: run nsteps CTMRG steps.  One step builds the enlarged
  * corner M from (C, T, a), the reduced corner Y = M Q diag(sgn C_ii),
  * Householder QR Y = Q R with diag(R) >= 0, C' = sym(Q^T M Q)/|.|,

@@ -113,6 +113,9 @@ cudaError_t launch_check_finite(long long count, const double *x, int *flag, cud
 size_t spectrum_work_doubles(int chi);
 
 int device_sm_count();
+// Optional persistent autotuning decisions (CTM_AUTOTUNE_CACHE=<file>, see tune_cache.cu).
+bool tune_cache_lookup(const char *tag, const int *key, int nkey, int *val, int nval);
+void tune_cache_store(const char *tag, const int *key, int nkey, const int *val, int nval);
 // Host-side count of kernel launches the library has enqueued (graph replays excluded).
 extern unsigned long long g_ctm_launches;
 #define CTM_COUNT_LAUNCH(nl) (g_ctm_launches += (unsigned long long)(nl))

@@ -841,6 +841,15 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
             return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, it->second.first, it->second.second),
                                   opt);
     }
+    const int tkey[4] = {g.M, g.N, g.K, T};
+    int tval[2];
+    if (w.autotune && tune_cache_lookup("split", tkey, 4, tval, 2)) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune[key] = {tval[0], tval[1]};
+        }
+        return gemm_split_run(g, T, w, st, ev, split_plan(g.M, g.N, g.K, T, tval[0], tval[1]), opt);
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
     if (!w.autotune || cs != cudaStreamCaptureStatusNone)
@@ -891,6 +900,9 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
         std::lock_guard<std::mutex> lk(g_tune_mu);
         g_tune[key] = best_c;
     }
+    tval[0] = best_c.first;
+    tval[1] = best_c.second;
+    tune_cache_store("split", tkey, 4, tval, 2);
     // the candidates re-packed both operands into the work buffers: a cached B is
     // re-packed by this final run, a reused A is freshly packed already
     SplitOpts fin{};

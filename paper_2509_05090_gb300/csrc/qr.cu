@@ -497,6 +497,17 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
         auto it = g_qr_rows.find({n, k});
         if (it != g_qr_rows.end()) return it->second;
     }
+    const int tkey[2] = {n, k};
+    int tval = 0;
+    int per_sm = 0;
+    if (tune_cache_lookup("qr", tkey, 2, &tval, 1) && tval >= 1 && qr_smem_bytes(tval, k) <= 200 * 1024 &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel, QR_THREADS, qr_smem_bytes(tval, k)) ==
+            cudaSuccess &&
+        (long long)per_sm * device_sm_count() >= (n + tval - 1) / tval) {
+        std::lock_guard<std::mutex> lk(g_qr_mu);
+        g_qr_rows[{n, k}] = tval;
+        return tval;
+    }
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     cudaStreamIsCapturing(st, &cs);
     if (cs != cudaStreamCaptureStatusNone) return rp0;
@@ -529,8 +540,11 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    std::lock_guard<std::mutex> lk(g_qr_mu);
-    g_qr_rows[{n, k}] = best;
+    {
+        std::lock_guard<std::mutex> lk(g_qr_mu);
+        g_qr_rows[{n, k}] = best;
+    }
+    tune_cache_store("qr", tkey, 2, &best, 1);
     return best;
 }
 
