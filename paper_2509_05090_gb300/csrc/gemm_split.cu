@@ -195,6 +195,53 @@ __global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTi
     }
 }
 
+// Exponent and digits in one kernel for a small operand whose K index is contiguous
+// (X(r, k) = X[off(r) + k]): one warp per row scans the row for its exponent
+// word, then packs it in 8-wide chunks (the second read of the row hits L1/L2);
+// rows past R up to the padded tile count are written as zero digits.
+__global__ void __launch_bounds__(256) split_rowpack_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles, int T,
+                                                            const double *X, Idx2 rmap, int *e, unsigned char *out,
+                                                            long long slice_bytes)
+{
+    const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (r >= rowsTotal) return;
+    const int P = 7 + 8 * (T - 1);
+    const long long tile_bytes = (long long)rowsT * SP_BK * 2;
+    unsigned char *row_base = out + (long long)(r / rowsT) * kTiles * tile_bytes;
+    if (r < R) {
+        const double *x = X + off2(rmap, r);
+        unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+        int k = lane;
+        for (; k + 96 < K; k += 128) {
+            m0 = max(m0, abs_hi_word(x[k]));
+            m1 = max(m1, abs_hi_word(x[k + 32]));
+            m2 = max(m2, abs_hi_word(x[k + 64]));
+            m3 = max(m3, abs_hi_word(x[k + 96]));
+        }
+        for (; k < K; k += 32) m0 = max(m0, abs_hi_word(x[k]));
+        unsigned m = max(max(m0, m1), max(m2, m3));
+        for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (lane == 0) e[r] = (int)m;
+        const int E = exp_of_word((int)m);
+        for (int c8 = lane; c8 < kTiles * 8; c8 += 32) {
+            const int k0 = c8 * 8;
+            long long F[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) F[q] = (k0 + q < K) ? fixed_point(x[k0 + q], E, P) : 0;
+            write_digit_chunks(F, T, row_base + (long long)(k0 / SP_BK) * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK),
+                               slice_bytes);
+        }
+    } else {
+        for (int c8 = lane; c8 < kTiles * 8; c8 += 32) {
+            const int k0 = c8 * 8;
+            long long F[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+            write_digit_chunks(F, T, row_base + (long long)(k0 / SP_BK) * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK),
+                               slice_bytes);
+        }
+    }
+}
+
 // The same packing for a transposed operand, X(r, k) = X[k * kstride + r]: a
 // block stages 32 rows x one 64-wide K tile through shared memory, reading with
 // the lanes along the contiguous rows and writing the swizzled chunks as above.
@@ -721,10 +768,18 @@ static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 
             R, K, rowsT, rowTiles * rowsT, kTiles, T, X, kmap.s2, e, pk, slice_bytes);
         return cudaGetLastError();
     }
+    if (kmap.s1 == 0 && kmap.s2 == 1 && (long long)R * K <= (1LL << 20)) {
+        // small operands: one launch; large ones scan faster in the two-kernel form
+        const int rows = rowTiles * rowsT;
+        CTM_COUNT_LAUNCH(1);
+        split_rowpack_kernel<<<(rows + 7) / 8, 256, 0, st>>>(R, K, rowsT, rows, kTiles, T, X, rmap, e, pk,
+                                                             slice_bytes);
+        return cudaGetLastError();
+    }
     CTM_COUNT_LAUNCH(2);
     split_rowexp_kernel<<<(R * 32 + 255) / 256, 256, 0, st>>>(R, K, X, rmap, kmap, e);
     const long long units = (long long)rowTiles * rowsT * kTiles * 8;
-    long long blocks = (units + 255) / 256, cap = 16LL * device_sm_count();
+    long long blocks = (units + 255) / 256, cap = 64LL * device_sm_count();
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     split_pack_kernel<<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowTiles, kTiles, T, X, rmap, kmap, e, pk);
