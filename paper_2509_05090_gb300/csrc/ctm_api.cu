@@ -179,6 +179,15 @@ size_t layout(ctm_ctx *c, char *base)
             c->ape[sl] = (int *)take(sizeof(int) * (size_t)ash[sl].N);
             c->apk_state[sl] = 0;
         }
+        // A packs kept for a second contraction: T (n x chi) and Q^T (chi x n)
+        const Shape csh[2] = {{(int)n, (int)chi, (int)chi}, {(int)chi, (int)chi, (int)n}};
+        for (int sl = 0; sl < 2; ++sl) {
+            SplitPlan pl = split_plan_caps(csh[sl].M, csh[sl].N, csh[sl].K, c->split_T);
+            c->ack[sl] = (unsigned char *)take(pl.a_pack_bytes);
+            c->ack_cap[sl] = pl.a_pack_bytes;
+            c->ace[sl] = (int *)take(sizeof(int) * (size_t)csh[sl].M);
+            c->ack_valid[sl] = 0;
+        }
     }
     return off;
 }
@@ -214,7 +223,19 @@ cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint)
             o.b_cap = c->apk_cap[slot];
             o.b_state = &c->apk_state[slot];
         }
-        return gemm_split(g, c->split_T, c->sw, c->stream, ev, &o);
+        int fill_slot = -1;
+        if (hint >= GEMM_A_FILL_T && hint <= GEMM_A_USE_Q) {
+            const int slot = (hint == GEMM_A_FILL_T || hint == GEMM_A_USE_T) ? 0 : 1;
+            const bool use = (hint == GEMM_A_USE_T || hint == GEMM_A_USE_Q) && c->ack_valid[slot];
+            o.a_pk = c->ack[slot];
+            o.a_e = c->ace[slot];
+            o.a_cap = c->ack_cap[slot];
+            o.a_fill = use ? 0 : 1;
+            if (!use) fill_slot = slot;
+        }
+        cudaError_t e = gemm_split(g, c->split_T, c->sw, c->stream, ev, &o);
+        if (fill_slot >= 0) c->ack_valid[fill_slot] = (e == cudaSuccess);
+        return e;
     }
     if (ev) cudaEventRecord(ev[0], c->stream);
     cudaError_t e = gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, c->stream);
@@ -236,10 +257,11 @@ int enqueue_enlarged_corner(ctm_ctx *c)
     const int chi = c->chi, D2 = c->D2;
     const long long n = c->n;
     GemmF64 g;
-    // W = T C
+    // W = T C (T's packed digits are kept for H1' = T Q of the edge update)
     g = GemmF64{(int)n, chi, chi, c->T, idx_lin(chi), idx_lin(1), c->C, idx_lin(chi), idx_lin(1),
                 c->W, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    c->ack_valid[0] = 0;
+    CK(run_gemm(c, g, GEMM_A_FILL_T));
     // X'[a][b][u][l] = W[(a,u),h] T[(b,l),h]
     g = GemmF64{(int)n, (int)n, chi, c->W, idx_lin(chi), idx_lin(1), c->T, idx_lin(1), idx_lin(chi),
                 c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1), 1.0, 0.0};
@@ -262,6 +284,7 @@ int enqueue_projector(ctm_ctx *c, double *Qout)
     const int chi = c->chi;
     const long long n = c->n;
     cudaStream_t st = c->stream;
+    c->ack_valid[1] = 0;   // the QR below writes a new Q
     CK(launch_warm_start((int)n, chi, c->Q, c->C, c->Qs, st));
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),
               c->Y, idx_lin(chi), idx_lin(1), 1.0, 0.0};
@@ -283,7 +306,7 @@ int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout)
     CK(run_gemm(c, g, GEMM_REUSE_A));
     g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
                 c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_FILL_Q : GEMM_PLAIN));
     CK(launch_corner_sym_normalize(chi, c->Cr, Cout, st));
     return CTM_OK;
 }
@@ -298,7 +321,7 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]; column index (j, w), w fastest
     g = GemmF64{(int)n, (int)n, chi, c->T, idx_lin(chi), idx_lin(1), Qp, idx_lin(n), idx_split(D2, 1, chi),
                 c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, GEMM_A_USE_T));
     // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
@@ -311,7 +334,7 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     // T'[i][(x,j)] = sum_{(a,y)} Q[(a,y),i] H3'[(a,y),(x,j)]
     g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),
                 Tout, idx_lin(n), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g));
+    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_USE_Q : GEMM_PLAIN));
     CK(launch_normalize((long long)chi * D2 * chi, Tout, c->norm_part, NORM_BLOCKS, st));
     return CTM_OK;
 }
@@ -360,6 +383,7 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     CK(cudaEventRecord(ev[0], st));
     if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
     CK(cudaEventRecord(ev[1], st));
+    c->ack_valid[1] = 0;   // the QR below writes a new Q
     CK(launch_warm_start((int)n, (int)chi, c->Q, c->C, c->Qs, st));
     {
         GemmF64 g{(int)n, (int)chi, (int)n, c->M, idx_lin(n), idx_lin(1), c->Qs, idx_lin(chi), idx_lin(1),

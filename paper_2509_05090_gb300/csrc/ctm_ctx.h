@@ -35,6 +35,13 @@ struct ctm_ctx {
     int *ape[2];
     size_t apk_cap[2];
     int apk_state[2];
+    // split mode: A packs used twice per step (slot 0: T as the A operand of W = T C
+    // and H1' = T Q; slot 1: Q^T for C_r = Q^T (M Q) and T' = Q^T H3'), and whether
+    // the pack matches the current T / Q
+    unsigned char *ack[2];
+    int *ace[2];
+    size_t ack_cap[2];
+    int ack_valid[2];
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
     unsigned *qr_bar;
     int *err, *flag;
@@ -74,7 +81,16 @@ inline QrScratch qr_scratch(ctm_ctx *c)
     q.sk_elems = qr_sk_doubles((int)n, (int)k);
     return q;
 }
-enum { GEMM_PLAIN = 0, GEMM_REUSE_A = 1, GEMM_B_IS_A_LZ = 2, GEMM_B_IS_A_ZX = 3 };
+enum {
+    GEMM_PLAIN = 0,
+    GEMM_REUSE_A = 1,
+    GEMM_B_IS_A_LZ = 2,
+    GEMM_B_IS_A_ZX = 3,
+    GEMM_A_FILL_T = 4,
+    GEMM_A_USE_T = 5,
+    GEMM_A_FILL_Q = 6,
+    GEMM_A_USE_Q = 7
+};
 cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint = GEMM_PLAIN);
 int enqueue_enlarged_corner(ctm_ctx *c);
 int enqueue_step(ctm_ctx *c);

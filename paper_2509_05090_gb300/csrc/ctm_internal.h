@@ -64,6 +64,12 @@ struct SplitOpts {
     int *b_e;
     size_t b_cap;
     int *b_state;     // host: N tile of the cached pack, 0 = empty
+    // A operand held in caller-owned buffers (a matrix packed once, used by two
+    // contractions): a_fill = 1 packs it there, 0 uses the pack as it is
+    unsigned char *a_pk;
+    int *a_e;
+    size_t a_cap;
+    int a_fill;
 };
 // Largest pack / accumulator sizes over every plan the autotuner may pick.
 SplitPlan split_plan_caps(int M, int N, int K, int T);

@@ -789,7 +789,14 @@ static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 
 static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
                                   SplitPlan p, const SplitOpts *opt = nullptr)
 {
-    const bool reuse_a = opt && opt->reuse_a;
+    bool pack_a = !(opt && opt->reuse_a);
+    if (opt && opt->a_pk) {
+        if (p.a_pack_bytes > opt->a_cap) return cudaErrorInvalidValue;
+        w.Apk = opt->a_pk;
+        w.a_pack_cap = opt->a_cap;
+        w.eA = opt->a_e;
+        pack_a = opt->a_fill != 0;
+    }
     bool pack_b = true;
     if (opt && opt->b_pk) {
         if (p.b_pack_bytes > opt->b_cap) return cudaErrorInvalidValue;
@@ -802,7 +809,7 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
         g.M > w.e_cap || g.N > w.e_cap)
         return cudaErrorInvalidValue;
     cudaError_t e;
-    if (!reuse_a) {
+    if (pack_a) {
         e = split_prepass(g.M, g.K, g.A, g.Am, g.Ak, SP_BM, p.mTiles, p.kTiles, T, w.eA, w.Apk, st);
         if (e != cudaSuccess) return e;
     }
