@@ -939,7 +939,8 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
         SplitPlan p = split_plan(g.M, g.N, g.K, T, cnd.first, cnd.second);
         if (p.a_pack_bytes > w.a_pack_cap || p.b_pack_bytes > w.b_pack_cap || p.partial_bytes > w.partial_cap) continue;
         float ms = 0.f, tot = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {   // first run warms caches and the instruction stream
+        tot = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {   // first run warms caches; the fastest of three counts
             cudaEventRecord(e0, st);
             cudaError_t e = gemm_split_run(g, T, w, st, nullptr, p);
             cudaEventRecord(e1, st);
@@ -949,7 +950,7 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
                 return e != cudaSuccess ? e : cudaErrorUnknown;
             }
             cudaEventElapsedTime(&ms, e0, e1);
-            if (rep) tot = ms;
+            if (rep && ms < tot) tot = ms;
         }
         if (tot < best) {
             best = tot;

@@ -518,8 +518,9 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
     // fewer rows than rp0 puts several CTAs on an SM (the launch checks they all fit)
     for (int rp : {rp0, 8, 12, 16, 24, 32, 48, 64, 96, 128}) {
         if ((rp < rp0 && rp * 2 < rp0) || (rp != rp0 && rp < 8) || qr_smem_bytes(rp, k) > 200 * 1024) continue;
-        float ms = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {
+        float ms = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {   // first run warms up; the fastest of three counts
+            float t = 0.f;
             cudaEventRecord(e0, st);
             cudaError_t e = qr_factor_launch(n, k, rp, Y, R, s, st);
             cudaEventRecord(e1, st);
@@ -528,7 +529,8 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
                 cudaGetLastError();
                 break;
             }
-            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep && t < ms) ms = t;
         }
         int herr = 0;
         cudaMemcpy(&herr, s.err, sizeof(int), cudaMemcpyDeviceToHost);
