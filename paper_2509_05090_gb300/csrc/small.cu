@@ -12,7 +12,7 @@ namespace {
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
-    // 256-thread reduction through shared memory (red: >= 32 doubles)
+    // block-wide reduction through shared memory (red: >= 32 doubles, any block size up to 1024)
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
     int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __syncthreads();
@@ -166,15 +166,16 @@ __global__ void scale_by_partials_kernel(long long count, double *x, const doubl
 // a7: corner spectrum and delta, in three launches.
 // (1) one CTA: Householder tridiagonalisation of the symmetric corner in shared
 //     memory -> diagonal d and squared off-diagonal e^2 (global work buffer);
-// (2) one warp per eigenvalue: multisection on the Gershgorin interval, each
+// (2) one warp per eigenvalue: multisection on [-|C|_F, |C|_F], each
 //     lane evaluating the Sturm count at one of 32 points per round
 //     (5 bits per round instead of 1).  The count is the number of sign
 //     changes of p_i = (d_i - x) p_{i-1} - e_{i-1}^2 p_{i-2}, kept in range by
 //     exact power-of-two rescaling -- no division on the dependent chain;
 // (3) one CTA: |lambda| sorted descending by rank, unit 2-norm, delta.
 constexpr int SPEC_WARPS = 1;   // one eigenvalue per CTA: the chi Sturm chains spread over chi SMs
+constexpr int TRI_THREADS = 256;
 
-__global__ void tridiag_kernel(int chi, const double *C, double *work)
+__global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const double *C, double *work)
 {
     extern __shared__ double sm[];
     __shared__ double red[32];
@@ -272,16 +273,13 @@ __global__ void bisect_kernel(int chi, const double *work, double *lam)
     const int lane = threadIdx.x & 31;
     const int ei = blockIdx.x * SPEC_WARPS + (threadIdx.x >> 5);
     if (ei >= chi) return;
-    // Gershgorin interval (every lane computes it; chi is small)
-    double lo = 1e300, hi = -1e300;
-    for (int i = 0; i < chi; ++i) {
-        double r = sqrt(e2[i]) + (i > 0 ? sqrt(e2[i - 1]) : 0.0);
-        lo = fmin(lo, d[i] - r);
-        hi = fmax(hi, d[i] + r);
-    }
-    const double scale = fmax(fmax(fabs(lo), fabs(hi)), 1e-300);
-    lo -= 1e-12 * scale;
-    hi += 1e-12 * scale;
+    // every eigenvalue lies in [-|T|_F, |T|_F] (the Frobenius norm bounds the
+    // spectral radius; it is the corner's, unchanged by the orthogonal reduction):
+    // one square root instead of per-row Gershgorin radii
+    double f2 = 0.0;
+    for (int i = 0; i < chi; ++i) f2 = fma(d[i], d[i], f2) + 2.0 * e2[i];
+    const double scale = fmax(sqrt(f2), 1e-300);
+    double lo = -scale * (1.0 + 1e-12), hi = scale * (1.0 + 1e-12);
     const double tiny = 1e-290 * scale;
     for (int round = 0; round < 16; ++round) {
         if (hi - lo <= 4e-16 * scale) break;
@@ -448,7 +446,7 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
     if (chi > 160 || !work) return cudaErrorInvalidValue;
     size_t smem = sizeof(double) * ((size_t)chi * chi + 2 * (size_t)chi);
     CTM_COUNT_LAUNCH(3);
-    tridiag_kernel<<<1, 256, smem, st>>>(chi, C, work);
+    tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
