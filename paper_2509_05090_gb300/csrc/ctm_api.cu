@@ -583,8 +583,12 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
             rc = CTM_ECUDA;
             break;
         }
+        // the corner spectrum overlaps the next step on the side stream; lowest priority,
+        // so the step's own pending CTAs are scheduled first
+        int prio_least = 0, prio_greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
         if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
             rc = CTM_ECUDA;
