@@ -140,23 +140,31 @@ __device__ __forceinline__ uint32_t bf16_of_digit(int d)
     return __float_as_uint(f) >> 16;
 }
 
-// Balanced base-256 digits of 8 fixed-point values, least significant slice
-// first; slice t's 16-byte chunk goes to base + t * slice_bytes.
-__device__ __forceinline__ void write_digit_chunks(long long *F, int T, unsigned char *base, long long slice_bytes)
+// Balanced base-256 digits of 8 fixed-point values; slice t (t = 0 most
+// significant) gets weight 256^(T-1-t) and its 16-byte chunk goes to
+// base + t * slice_bytes.  With B = 128 (256^(T-1) + ... + 256 + 1) and
+// |F| <= 2^(7 + 8 (T-1)) < B, G = F + B >= 0 and byte j of G minus 128 is the
+// balanced digit of weight 256^j for j < T-1 (each in [-128, 127]); the top
+// digit is G >> 8 (T-1) minus 128.  Same digits as repeated "take the balanced
+// low byte and shift", with one 64-bit add and byte extracts.
+__device__ __forceinline__ void write_digit_chunks(const long long *F, int T, unsigned char *base,
+                                                   long long slice_bytes)
 {
+    const long long B = 128LL * (((1LL << (8 * T)) - 1) / 255);
+    uint32_t lo[8], top[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const long long G = F[q] + B;
+        lo[q] = (uint32_t)G;
+        top[q] = (uint32_t)(G >> (8 * (T - 1)));
+    }
     for (int t = T - 1; t >= 0; --t) {
+        const int sh = 8 * (T - 1 - t);
         uint32_t w[4];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            long long d;
-            if (t > 0) {
-                d = F[q] & 255;
-                if (d >= 128) d -= 256;
-                F[q] = (F[q] - d) >> 8;
-            } else {
-                d = F[q];
-            }
-            const uint32_t h = bf16_of_digit((int)d);
+            const int u = (t > 0) ? (int)((lo[q] >> sh) & 255u) : (int)top[q];
+            const uint32_t h = bf16_of_digit(u - 128);
             w[q >> 1] = (q & 1) ? (w[q >> 1] | (h << 16)) : h;
         }
         *reinterpret_cast<uint4 *>(base + (long long)t * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);

@@ -238,26 +238,38 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const dou
     }
 }
 
-// number of eigenvalues of the tridiagonal (d, e2) below x
+// Number of eigenvalues of the tridiagonal (d, e2) below x: the sign changes of
+// p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}.  Only the recurrence itself is FP64
+// arithmetic (three operations per step -- GB300's FP64 pipe is narrow); the zero
+// test, the sign comparison and the range check read the bit pattern with integer
+// instructions, and the rare rescaling is by exact powers of two.
 __device__ __forceinline__ int sturm_count(int chi, const double *d, const double *e2, double x, double tiny)
 {
     double pm = 1.0, p = d[0] - x;
     if (p == 0.0) p = -tiny;
     int cnt = (p < 0.0);
+    int hp = __double2hiint(p);
     for (int i = 1; i < chi; ++i) {
         double pn = fma(d[i] - x, p, -e2[i - 1] * pm);
-        if (pn == 0.0) pn = (p < 0.0) ? tiny : -tiny;
-        cnt += ((pn < 0.0) != (p < 0.0));
+        int hn = __double2hiint(pn);
+        if (((hn & 0x7FFFFFFF) | __double2loint(pn)) == 0) {   // +-0
+            pn = (hp < 0) ? tiny : -tiny;
+            hn = __double2hiint(pn);
+        }
+        cnt += ((hn ^ hp) < 0);   // sign bits differ
         pm = p;
         p = pn;
-        double ap = fabs(p);
-        if (ap > 0x1p+500) {
+        const int ex = (hn >> 20) & 0x7FF;
+        if (ex > 1023 + 500) {
             p *= 0x1p-500;
             pm *= 0x1p-500;
-        } else if (ap < 0x1p-500) {
+            hn = __double2hiint(p);
+        } else if (ex < 1023 - 500) {
             p *= 0x1p+500;
             pm *= 0x1p+500;
+            hn = __double2hiint(p);
         }
+        hp = hn;
     }
     return cnt;
 }
