@@ -203,7 +203,7 @@ __global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTi
     }
 }
 
-// Exponent and digits in one kernel for a small operand whose K index is contiguous
+// Exponent and digits in one kernel for an operand whose K index is contiguous
 // (X(r, k) = X[off(r) + k]): one warp per row scans the row for its exponent
 // word, then packs it in 8-wide chunks (the second read of the row hits L1/L2);
 // rows past R up to the padded tile count are written as zero digits.
@@ -776,8 +776,7 @@ static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 
             R, K, rowsT, rowTiles * rowsT, kTiles, T, X, kmap.s2, e, pk, slice_bytes);
         return cudaGetLastError();
     }
-    if (kmap.s1 == 0 && kmap.s2 == 1 && (long long)R * K <= (1LL << 20)) {
-        // small operands: one launch; large ones scan faster in the two-kernel form
+    if (kmap.s1 == 0 && kmap.s2 == 1) {
         const int rows = rowTiles * rowsT;
         CTM_COUNT_LAUNCH(1);
         split_rowpack_kernel<<<(rows + 7) / 8, 256, 0, st>>>(R, K, rowsT, rows, kTiles, T, X, rmap, e, pk,
