@@ -1,0 +1,107 @@
+"""GPU paths that the workload-driven tests reach only by chance.
+
+* Every contraction tile width of the split engine (48: two CTAs per SM, 64, 96),
+  forced through the plan cache (CTM_AUTOTUNE_CACHE) in a fresh process per width,
+  for a whole CTMRG step against the FP64 oracle.
+* The blocked QR's early panel end: a previous projector with nearly parallel
+  column pairs makes the reduced corner's columns nearly dependent, so downdated
+  panel norms collapse and the factorisation restarts panels from fresh sums.
+"""
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2509_05090_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _step_shapes(chi, D2):
+    n = chi * D2
+    return sorted({(n, chi, chi), (n, n, chi), (chi * chi, D2, D2 * D2), (chi * chi, D2 * D2, D2), (n, chi, n),
+                   (chi, chi, n), (chi, n, n)})
+
+
+_CHILD = textwrap.dedent("""
+    import sys, numpy as np
+    sys.path.insert(0, sys.argv[1])
+    from paper_2509_05090_gb300 import binding
+    env = np.load(sys.argv[2])
+    g = binding.CTM(env["A"], int(env["chi"]), precision="split_bf16", n_split=5)
+    g.ctm_set_env(env["C"], env["T"], env["Q"])
+    g.ctm_step(1)
+    np.savez(sys.argv[3], M=g.ctm_get_intermediate("M").cpu().numpy(), s=g.ctm_get_intermediate("s").cpu().numpy())
+    g.close()
+""")
+
+
+@pytest.mark.parametrize("nt", [48, 64, 96])
+def test_split_step_each_tile_width(ctm_lib, tmp_path, nt):
+    w = I.WORKLOADS["kitaev_D4_chi32"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)
+    for _ in range(3):
+        ref.step()
+    env = tmp_path / "env.npz"
+    np.savez(env, A=A, chi=w.chi, C=ref.C, T=ref.T, Q=ref.Q)
+    ref.step()
+    cache = tmp_path / "plans.txt"
+    cache.write_text("".join(f"split {M} {N} {K} 5 : {nt} 1\n" for M, N, K in _step_shapes(w.chi, w.D2)))
+    out = tmp_path / "out.npz"
+    script = tmp_path / "child.py"
+    script.write_text(_CHILD)
+    r = subprocess.run([sys.executable, str(script), ROOT, str(env), str(out)], capture_output=True, text=True,
+                       timeout=600, env=dict(os.environ, CTM_AUTOTUNE_CACHE=str(cache)))
+    assert r.returncode == 0, r.stderr[-2000:]
+    got = np.load(out)
+    # T = 5 slices: the contraction error bound (see test_gpu_split) is far below 1e-9 of max|M|
+    assert _rel(got["M"], ref.last["M"]) <= 1e-9
+    assert np.max(np.abs(got["s"] - ref.s)) <= 1e-7
+
+
+def test_qr_panel_restart_on_nearly_parallel_columns(ctm_lib):
+    from paper_2509_05090_gb300 import binding
+    w = I.WORKLOADS["kitaev_D4_chi32"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)
+    for _ in range(3):
+        ref.step()
+    Q = ref.Q.copy()
+    for c in (1, 9, 17, 26):   # inside panels and at a panel start
+        Q[:, c] = Q[:, c - 1] + 1e-3 * Q[:, c]
+    ref.set_env(ref.C, ref.T, Q)
+    g = binding.CTM(A, w.chi)
+    g.ctm_set_env(ref.C, ref.T, Q)
+    ref.step()
+    g.ctm_step(1)
+    last = ref.last
+    Y = last["Y"]
+    # the reduced corner really has nearly dependent column pairs
+    cosang = abs(Y[:, 1] @ Y[:, 0]) / (np.linalg.norm(Y[:, 1]) * np.linalg.norm(Y[:, 0]))
+    assert cosang > 0.99
+    R_ref = last["R"]
+    dR = np.abs(np.diag(R_ref))
+    lead = int(np.sum(dR / dR[0] >= 1e-8))
+    R = _np(g.ctm_get_intermediate("R"))
+    assert np.all(np.diag(R) >= 0.0)
+    assert _rel(R[:lead], R_ref[:lead]) <= 1e-10
+    C, T, Qn = (_np(x) for x in g.ctm_get_env())
+    assert _rel(Qn[:, :lead], last["Q"][:, :lead]) <= 1e-10
+    assert np.max(np.abs(Qn.T @ Qn - np.eye(w.chi))) <= 1e-12
+    assert np.max(np.abs(Qn @ R - _np(g.ctm_get_intermediate("Y")))) <= 1e-12 * np.max(np.abs(Y))
+    g.close()
