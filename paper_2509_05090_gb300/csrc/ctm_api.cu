@@ -307,7 +307,7 @@ int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout)
     g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
                 c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
     CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_FILL_Q : GEMM_PLAIN));
-    CK(launch_corner_sym_normalize(chi, c->Cr, Cout, st));
+    CK(launch_corner_sym_normalize(chi, c->Cr, Cout, c->norm_part, st));
     return CTM_OK;
 }
 

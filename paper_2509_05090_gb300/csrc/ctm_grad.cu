@@ -553,7 +553,7 @@ extern "C" int ctm_grad(ctm_ctx *c, int warmup, int k_tracked, const double *h_d
     }
     CK(G((int)n, chi, (int)n, c->M, L(n), L(1), c->Qn, L(chi), L(1), c->MQ, L(chi), L(1)));
     CK(G(chi, chi, (int)n, c->Qn, L(1), L(chi), c->MQ, L(chi), L(1), c->Cr, L(chi), L(1)));
-    CK(launch_corner_sym_normalize(chi, c->Cr, b.P[0], st));     // P1 = Ch
+    CK(launch_corner_sym_normalize(chi, c->Cr, b.P[0], c->norm_part, st));   // P1 = Ch
     for (int p = 1; p < 5; ++p)
         CK(G(chi, chi, chi, b.P[p - 1], L(chi), L(1), b.P[0], L(chi), L(1), b.P[p], L(chi), L(1)));
     CK(G((int)n, chi, chi, c->Qn, L(chi), L(1), b.P[4], L(chi), L(1), b.G, L(chi), L(1)));

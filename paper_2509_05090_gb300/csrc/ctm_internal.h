@@ -108,7 +108,9 @@ cudaError_t launch_c3v_project_normalize(int d, int D, const double *Ain, double
 cudaError_t launch_double_layer(int d, int D, const double *K, const double *B, double *a, cudaStream_t st);
 cudaError_t launch_init_env(int chi, int D, const double *a, double *C, double *T, double *Q, cudaStream_t st);
 cudaError_t launch_warm_start(int n, int chi, const double *Q, const double *C, double *Qs, cudaStream_t st);
-cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, cudaStream_t st);
+// partials: CORNER_NORM_BLOCKS doubles of scratch
+constexpr int CORNER_NORM_BLOCKS = 64;
+cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, double *partials, cudaStream_t st);
 cudaError_t launch_normalize(long long count, double *x, double *partials, int nblocks, cudaStream_t st);
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
                             double *work, cudaStream_t st);

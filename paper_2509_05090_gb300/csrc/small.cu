@@ -12,17 +12,20 @@ namespace {
 
 __device__ __forceinline__ double block_sum(double v, double *red)
 {
-    // block-wide reduction through shared memory (red: >= 32 doubles, any block size up to 1024)
+    // block-wide reduction (any block size up to 1024; red: >= 32 doubles): warp
+    // sums, then warp 0 reduces the per-warp sums with shuffles -- short FP64 chains
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
     __syncthreads();
     if (lane == 0) red[warp] = v;
     __syncthreads();
-    double s = 0.0;
-    int nw = (blockDim.x + 31) >> 5;
-    for (int w = 0; w < nw; ++w) s += red[w];
+    if (warp == 0) {
+        double s = (lane < nw) ? red[lane] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[32] = s;
+    }
     __syncthreads();
-    return s;
+    return red[32];
 }
 
 // a0: A_sym = (1/6) sum over the six permutations of the virtual legs, then
@@ -30,7 +33,7 @@ __device__ __forceinline__ double block_sum(double v, double *red)
 __global__ void c3v_project_kernel(int d, int D, const double *Ain, double *Aout, int symmetrize)
 {
     extern __shared__ double sA[];
-    __shared__ double red[32];
+    __shared__ double red[33];
     const int D3 = D * D * D, tot = d * D3;
     for (int t = threadIdx.x; t < tot; t += blockDim.x) {
         int s = t / D3, r = t % D3;
@@ -118,28 +121,42 @@ __global__ void warm_start_kernel(long long n, int chi, const double *Q, const d
     }
 }
 
-// a5 tail: C' = (Cr + Cr^T)/2, then unit Frobenius norm.  One CTA.
-__global__ void corner_sym_norm_kernel(int chi, const double *Cr, double *Cn)
+// a5 tail: C' = (Cr + Cr^T)/2, then unit Frobenius norm, over several blocks (the FP64 work of one SM would
+// bind): partial sums of squares, then every block derives the factor from the
+// partials with one warp and scales its share.
+__global__ void corner_sym_sumsq_kernel(int chi, const double *Cr, double *partials)
 {
-    __shared__ double red[32];
+    __shared__ double red[33];
     double ss = 0.0;
-    for (int t = threadIdx.x; t < chi * chi; t += blockDim.x) {
-        int i = t / chi, j = t % chi;
-        double v = 0.5 * (Cr[t] + Cr[(size_t)j * chi + i]);
-        ss += v * v;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < chi * chi; t += gridDim.x * blockDim.x) {
+        const int i = t / chi, j = t - i * chi;
+        const double v = 0.5 * (Cr[t] + Cr[(size_t)j * chi + i]);
+        ss = fma(v, v, ss);
     }
     ss = block_sum(ss, red);
-    double f = ss > 0.0 ? 1.0 / sqrt(ss) : 1.0;
-    for (int t = threadIdx.x; t < chi * chi; t += blockDim.x) {
-        int i = t / chi, j = t % chi;
-        Cn[t] = 0.5 * (Cr[t] + Cr[(size_t)j * chi + i]) * f;
+    if (threadIdx.x == 0) partials[blockIdx.x] = ss;
+}
+__global__ void corner_sym_scale_kernel(int chi, const double *Cr, const double *partials, int np, double *Cn)
+{
+    __shared__ double f;
+    if (threadIdx.x < 32) {
+        double s = 0.0;
+        for (int i = threadIdx.x; i < np; i += 32) s += partials[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) f = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    }
+    __syncthreads();
+    const double h = 0.5 * f;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < chi * chi; t += gridDim.x * blockDim.x) {
+        const int i = t / chi, j = t - i * chi;
+        Cn[t] = (Cr[t] + Cr[(size_t)j * chi + i]) * h;
     }
 }
 
 // Frobenius normalisation of a large array: per-block partial sums of squares...
 __global__ void sumsq_partial_kernel(long long count, const double *x, double *partials)
 {
-    __shared__ double red[32];
+    __shared__ double red[33];
     double s = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
          t += (long long)gridDim.x * blockDim.x)
@@ -152,10 +169,11 @@ __global__ void sumsq_partial_kernel(long long count, const double *x, double *p
 __global__ void scale_by_partials_kernel(long long count, double *x, const double *partials, int np)
 {
     __shared__ double f;
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {   // one warp sums the partials: short chains, then shuffles
         double s = 0.0;
-        for (int i = 0; i < np; ++i) s += partials[i];
-        f = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+        for (int i = threadIdx.x; i < np; i += 32) s += partials[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) f = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
     }
     __syncthreads();
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
@@ -178,7 +196,7 @@ constexpr int TRI_THREADS = 256;
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const double *C, double *work)
 {
     extern __shared__ double sm[];
-    __shared__ double red[32];
+    __shared__ double red[33];
     __shared__ double sh_beta, sh_alpha;
     __shared__ int sh_skip;
     double *A = sm;                      // chi x chi
@@ -312,7 +330,7 @@ __global__ void bisect_kernel(int chi, const double *work, double *lam)
 __global__ void spectrum_finish_kernel(int chi, const double *lam_in, double *s_new, const double *s_old,
                                        double *delta)
 {
-    __shared__ double red[32];
+    __shared__ double red[33];
     __shared__ double lam[160], srt[160];
     const int tid = threadIdx.x;
     for (int i = tid; i < chi; i += blockDim.x) lam[i] = fabs(lam_in[i]);
@@ -432,10 +450,15 @@ cudaError_t launch_warm_start(int n, int chi, const double *Q, const double *C, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, cudaStream_t st)
+cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, double *partials, cudaStream_t st)
 {
-    CTM_COUNT_LAUNCH(1);
-    corner_sym_norm_kernel<<<1, 256, 0, st>>>(chi, Cr, Cn);
+    int nb = (chi * chi + 255) / 256;
+    if (nb > CORNER_NORM_BLOCKS) nb = CORNER_NORM_BLOCKS;
+    CTM_COUNT_LAUNCH(2);
+    corner_sym_sumsq_kernel<<<nb, 256, 0, st>>>(chi, Cr, partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    corner_sym_scale_kernel<<<nb, 256, 0, st>>>(chi, Cr, partials, nb, Cn);
     return cudaGetLastError();
 }
 
