@@ -138,6 +138,7 @@ size_t layout(ctm_ctx *c, char *base)
     c->err = (int *)take(64);
     c->flag = (int *)take(64);
     c->norm_part = td(NORM_BLOCKS);
+    c->norm_part2 = td(NORM_BLOCKS);
     c->b = td(d * d * D2 * D2 * D2);
     c->Y1o = td(chi * chi * d * d * D2);
     c->G2 = td(chi * chi * d * d * D2);
@@ -171,6 +172,14 @@ size_t layout(ctm_ctx *c, char *base)
         c->sw.partial_cap = pp;
         c->sw.err = c->err;
         c->sw.autotune = 1;   // the first eager call of each contraction shape times its plans
+        // the two lanes of the corner / edge updates (see enqueue_step)
+        c->sw_c = c->sw;
+        c->sw_c.Bpk = (unsigned char *)take(bp);
+        c->sw_c.eB = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw_c.partial = (void *)take(pp + 8);
+        c->sw_e = c->sw;
+        c->sw_e.Apk = (unsigned char *)take(ap);
+        c->sw_e.eA = (int *)take(sizeof(int) * (size_t)ecap);
         const Shape ash[2] = {{(int)(chi * chi), (int)D2, (int)(D2 * D2)}, {(int)(chi * chi), (int)(D2 * D2), (int)D2}};
         for (int sl = 0; sl < 2; ++sl) {
             SplitPlan pl = split_plan_caps(ash[sl].M, ash[sl].N, ash[sl].K, c->split_T);
@@ -206,7 +215,7 @@ bool config_ok(const ctm_config *cfg)
 }
 
 // The step's contractions: FP64 GEMM, or the split-BF16 tcgen05 engine.
-cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint)
+cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint, int lane)
 {
     cudaEvent_t *ev = nullptr;
     if (c->prof_on && c->prof_n + 2 <= 64) {
@@ -233,7 +242,8 @@ cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint)
             o.a_fill = use ? 0 : 1;
             if (!use) fill_slot = slot;
         }
-        cudaError_t e = gemm_split(g, c->split_T, c->sw, c->stream, ev, &o);
+        const SplitWork &w = lane == 1 ? c->sw_c : (lane == 2 ? c->sw_e : c->sw);
+        cudaError_t e = gemm_split(g, c->split_T, w, lane == 1 ? c->lane2 : c->stream, ev, &o);
         if (fill_slot >= 0) c->ack_valid[fill_slot] = (e == cudaSuccess);
         return e;
     }
@@ -295,24 +305,27 @@ int enqueue_projector(ctm_ctx *c, double *Qout)
 }
 
 // Fig. 3(a): Cout = sym(Qp^T M Qp) / |.|_F.
-int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout)
+// lane 1 (split mode): on lane2, with the corner lane's work buffers.
+int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout, int lane = 0)
 {
     const int chi = c->chi;
     const long long n = c->n;
-    cudaStream_t st = c->stream;
+    cudaStream_t st = lane == 1 ? c->lane2 : c->stream;
     // the previous split contraction was Y = M Qs (only the QR in between): M is already packed
     GemmF64 g{(int)n, chi, (int)n, c->M, idx_lin(n), idx_lin(1), Qp, idx_lin(chi), idx_lin(1),
               c->MQ, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g, GEMM_REUSE_A));
+    CK(run_gemm(c, g, GEMM_REUSE_A, lane));
     g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
                 c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_FILL_Q : GEMM_PLAIN));
-    CK(launch_corner_sym_normalize(chi, c->Cr, Cout, c->norm_part, st));
+    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_FILL_Q : GEMM_PLAIN, lane));
+    CK(launch_corner_sym_normalize(chi, c->Cr, Cout, lane == 1 ? c->norm_part2 : c->norm_part, st));
     return CTM_OK;
 }
 
 // Fig. 3(b): T'[i,x,j] = sum Q[(a,y),i] T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j], normalised.
-int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
+// lane 2 (split mode): with the edge lane's work buffers, concurrent with a corner
+// update on lane2; the last contraction waits for it (it uses the corner's pack of Q^T).
+int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout, int lane = 0)
 {
     const int chi = c->chi, D2 = c->D2;
     const long long n = c->n;
@@ -321,20 +334,21 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout)
     // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]; column index (j, w), w fastest
     g = GemmF64{(int)n, (int)n, chi, c->T, idx_lin(chi), idx_lin(1), Qp, idx_lin(n), idx_split(D2, 1, chi),
                 c->X, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1), 1.0, 0.0};
-    CK(run_gemm(c, g, GEMM_A_USE_T));
+    CK(run_gemm(c, g, GEMM_A_USE_T, lane));
     // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
     g = GemmF64{chi * chi, D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->a, idx_lin(D2),
                 idx_lin(1), c->Y1, idx_lin(D2), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g, GEMM_B_IS_A_LZ));
+    CK(run_gemm(c, g, GEMM_B_IS_A_LZ, lane));
     // H3'[a][y][x][j] = H2[(a,j),z] a[z, x, y]; column index (y, x), x fastest
     g = GemmF64{chi * chi, D2 * D2, D2, c->Y1, idx_lin(D2), idx_lin(1), c->a, idx_lin((long long)D2 * D2),
                 idx_split(D2, 1, D2), c->H, idx_split(chi, (long long)D2 * D2 * chi, 1),
                 idx_split(D2, (long long)D2 * chi, chi), 1.0, 0.0};
-    CK(run_gemm(c, g, GEMM_B_IS_A_ZX));
+    CK(run_gemm(c, g, GEMM_B_IS_A_ZX, lane));
     // T'[i][(x,j)] = sum_{(a,y)} Q[(a,y),i] H3'[(a,y),(x,j)]
     g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),
                 Tout, idx_lin(n), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_USE_Q : GEMM_PLAIN));
+    if (lane == 2) CK(cudaStreamWaitEvent(st, c->ev_corner, 0));
+    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_USE_Q : GEMM_PLAIN, lane));
     CK(launch_normalize((long long)chi * D2 * chi, Tout, c->norm_part, NORM_BLOCKS, st));
     return CTM_OK;
 }
@@ -350,8 +364,19 @@ int enqueue_step(ctm_ctx *c)
     const long long chi = c->chi, D2 = c->D2, n = c->n;
     if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
-    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
-    if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
+    // Split mode after the first step (whose eager contractions time their plans
+    // one at a time): the corner and edge updates both need only Q, so the corner
+    // update runs on lane2 beside the edge update.
+    if (c->split_T > 0 && c->steps_done > 0) {
+        CK(cudaEventRecord(c->ev_q, st));
+        CK(cudaStreamWaitEvent(c->lane2, c->ev_q, 0));
+        if ((rc = enqueue_corner(c, c->Qn, c->Cn, 1)) != CTM_OK) return rc;
+        CK(cudaEventRecord(c->ev_corner, c->lane2));
+        if ((rc = enqueue_edge(c, c->Qn, c->Tn, 2)) != CTM_OK) return rc;
+    } else {
+        if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+        if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
+    }
     if (c->side_pending) CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
@@ -590,7 +615,10 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
         if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->lane2, cudaStreamNonBlocking, prio_greatest) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_q, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_corner, cudaEventDisableTiming) != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
         }
@@ -812,6 +840,12 @@ void ctm_destroy(ctm_ctx *c)
         cudaStreamSynchronize(c->side);
         cudaStreamDestroy(c->side);
     }
+    if (c->lane2) {
+        cudaStreamSynchronize(c->lane2);
+        cudaStreamDestroy(c->lane2);
+    }
+    if (c->ev_q) cudaEventDestroy(c->ev_q);
+    if (c->ev_corner) cudaEventDestroy(c->ev_corner);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->prof_ev[0])

@@ -16,6 +16,11 @@ struct ctm_ctx {
     cudaEvent_t ev_in, ev_out;
     cudaStream_t side;        // corner spectrum runs here, overlapped with the edge update
     cudaEvent_t ev_fork, ev_join;
+    // split mode: the corner update (M Q, Q^T (M Q), normalisation) runs on lane2
+    // while the edge update runs on the step's stream; ev_q = Q is ready,
+    // ev_corner = the corner update (and its pack of Q^T) is done
+    cudaStream_t lane2;
+    cudaEvent_t ev_q, ev_corner;
     // FP64 buffers (device, inside the caller's workspace)
     double *Araw, *A, *a;
     double *C, *Cn, *Cr;
@@ -29,6 +34,8 @@ struct ctm_ctx {
     size_t splitk_elems;
     int split_T;              // 0: FP64 contractions; 2..5: split-BF16 slices per operand
     SplitWork sw;
+    SplitWork sw_c;           // corner lane: M's pack read from sw; own B pack, exponents, split-K buffer
+    SplitWork sw_e;           // edge lane: own A pack and exponents; B pack and split-K buffer of sw
     // the double layer a is a constant B operand of four contractions per step:
     // its packed digit slices are kept (slot 0: a as [(u,l)][z], slot 1: a as [z][(x,y)])
     unsigned char *apk[2];
@@ -45,7 +52,7 @@ struct ctm_ctx {
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
     unsigned *qr_bar;
     int *err, *flag;
-    double *norm_part;
+    double *norm_part, *norm_part2;
     // energy
     double *b, *Y1o, *G2, *P5a, *P5b, *rho_part, *rho_raw, *eout, *h;
     // graph of `graph_steps` steps (captured on the private stream), and how many
@@ -91,7 +98,8 @@ enum {
     GEMM_A_FILL_Q = 6,
     GEMM_A_USE_Q = 7
 };
-cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint = GEMM_PLAIN);
+// lane 0: the step's stream and work buffers; 1: the corner lane; 2: the edge lane
+cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint = GEMM_PLAIN, int lane = 0);
 int enqueue_enlarged_corner(ctm_ctx *c);
 int enqueue_step(ctm_ctx *c);
 int join_side(ctm_ctx *c);

@@ -114,109 +114,123 @@ __global__ void split_colexp_kernel(int R, int K, const double *X, long long kst
     if (m) atomicMax(e + r, (int)m);
 }
 
-// Digits of one value: F = round(x 2^(P - E)) from the IEEE fields, integer ops only.
-__device__ __forceinline__ long long fixed_point(double x, int E, int P)
+// Digit slicing with T fixed at compile time.  P = 7 + 8 (T-1) fraction bits
+// on the row grid; B = 128 (256^(T-1) + ... + 256 + 1) biases the fixed-point
+// value F (|F| <= 2^P < B) to G = F + B >= 0, and then byte j of G minus 128 is
+// the balanced digit of weight 256^j for j < T-1 (each in [-128, 127]) and
+// G >> 8 (T-1) minus 128 the top digit (in [-128, 128]): the same digits as
+// repeatedly taking the balanced low byte and shifting.
+template <int T>
+struct SplitDigits {
+    static constexpr int P = 7 + 8 * (T - 1);
+    static constexpr unsigned long long B = 128ULL * (((1ULL << (8 * T)) - 1) / 255);
+};
+
+// Right shift, less one guard bit, that puts a value of biased exponent field ex
+// on the grid of a row with exponent E: x = mant 2^(ex - 1075), so
+// F = round(x 2^(P - E)) = ((mant >> sh) + 1) >> 1 with sh = rs - ex,
+// rs = E + 1074 - P (rounding half up on the magnitude).
+__device__ __forceinline__ int grid_shift(int E, int P) { return E + 1074 - P; }
+
+// G = F + B of one value from its IEEE fields, integer operations only.  Zero
+// and subnormal values (far below any row grid) give F = 0, as do values more
+// than 63 bits below it; sh < 0 happens only on rows whose grid is undefined
+// (E = 0 for an inf/NaN row) and gives F = 0 too.
+template <int T>
+__device__ __forceinline__ unsigned long long biased_fixed(double x, int rs)
 {
-    unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    int ex = (int)((b >> 52) & 0x7FF);
-    if (ex == 0) return 0;                         // zero or subnormal (far below the row grid)
-    long long mant = (long long)((b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52));
-    int s = ex - 1075 - E + P;                     // x = mant 2^(ex - 1075)
-    long long F;
-    if (s >= 0) F = mant << s;                     // |x 2^(P-E)| < 2^P, no overflow
-    else if (s <= -64) F = 0;
-    else F = (mant + (1LL << (-s - 1))) >> (-s);   // round half up on the magnitude
-    return (b >> 63) ? -F : F;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)(b >> 52) & 0x7FF;
+    const int sh = rs - ex;
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFULL) | (1ULL << 52);
+    unsigned long long F = ((mant >> (sh & 63)) + 1) >> 1;
+    if (ex == 0 || (unsigned)sh > 63u) F = 0;
+    const unsigned long long m = (unsigned long long)((long long)b >> 63);   // all ones if negative
+    return (F ^ m) - m + SplitDigits<T>::B;
 }
 
-// BF16 bits of a digit |d| <= 256: 2^23 + 256 + d is exact in FP32 (integer
-// below 2^24), subtracting 2^23 + 256 leaves d exactly, and an integer of at most
-// 8 significant bits has zero low 16 bits in FP32, so the BF16 pattern is the high
-// half.  One integer add and one FP32 add (no 64-bit conversion, which GB300 runs
-// on its narrow FP64 unit).
-__device__ __forceinline__ uint32_t bf16_of_digit(int d)
+// BF16 pair {lo, hi} in one word (lo in the low half).  The inputs are integers of
+// at most 8 significant bits, so the conversion is exact.
+__device__ __forceinline__ uint32_t bf16x2_of(float lo, float hi)
 {
-    const float f = __int_as_float(0x4B000000 + 256 + d) - 8388864.0f;
-    return __float_as_uint(f) >> 16;
+    uint32_t w;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(w) : "f"(hi), "f"(lo));
+    return w;
 }
 
-// Balanced base-256 digits of 8 fixed-point values; slice t (t = 0 most
-// significant) gets weight 256^(T-1-t) and its 16-byte chunk goes to
-// base + t * slice_bytes.  With B = 128 (256^(T-1) + ... + 256 + 1) and
-// |F| <= 2^(7 + 8 (T-1)) < B, G = F + B >= 0 and byte j of G minus 128 is the
-// balanced digit of weight 256^j for j < T-1 (each in [-128, 127]); the top
-// digit is G >> 8 (T-1) minus 128.  Same digits as repeated "take the balanced
-// low byte and shift", with one 64-bit add and byte extracts.
-__device__ __forceinline__ void write_digit_chunks(const long long *F, int T, unsigned char *base,
+// The digit of slice t (t = 0 most significant, weight 256^(T-1-t)) of a biased
+// word, as an exact FP32 integer: the digit byte u placed under the exponent of
+// 2^23 reads as 2^23 + u, and subtracting 2^23 + 128 leaves u - 128 (one byte
+// permute and one FP32 add; the top digit, up to 9 bits, is added instead).
+template <int T>
+__device__ __forceinline__ float slice_digit(unsigned long long G, int t)
+{
+    if (t == 0) return __uint_as_float(0x4B000000u + (uint32_t)(G >> (8 * (T - 1)))) - 8388736.0f;
+    return __uint_as_float(__byte_perm((uint32_t)G, 0x4B000000u, 0x7650u | (unsigned)(T - 1 - t))) - 8388736.0f;
+}
+
+// Slices of 8 consecutive-K values: slice t's 16-byte chunk goes to base + t * slice_bytes.
+template <int T>
+__device__ __forceinline__ void write_digit_chunks(const unsigned long long *G, unsigned char *base,
                                                    long long slice_bytes)
 {
-    const long long B = 128LL * (((1LL << (8 * T)) - 1) / 255);
-    uint32_t lo[8], top[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const long long G = F[q] + B;
-        lo[q] = (uint32_t)G;
-        top[q] = (uint32_t)(G >> (8 * (T - 1)));
-    }
-    for (int t = T - 1; t >= 0; --t) {
-        const int sh = 8 * (T - 1 - t);
+    for (int t = 0; t < T; ++t) {
         uint32_t w[4];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int u = (t > 0) ? (int)((lo[q] >> sh) & 255u) : (int)top[q];
-            const uint32_t h = bf16_of_digit(u - 128);
-            w[q >> 1] = (q & 1) ? (w[q >> 1] | (h << 16)) : h;
-        }
+        for (int q = 0; q < 4; ++q) w[q] = bf16x2_of(slice_digit<T>(G[2 * q], t), slice_digit<T>(G[2 * q + 1], t));
         *reinterpret_cast<uint4 *>(base + (long long)t * slice_bytes) = make_uint4(w[0], w[1], w[2], w[3]);
     }
 }
 
 // Pack T digit slices of X (R x K via maps) into [T][rowTiles][kTiles][rowsT x 64] swizzled tiles.
 // One thread per (row, 8-wide K chunk): it writes one 16-byte chunk per slice.
-__global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTiles, int T, const double *X,
-                                  Idx2 rmap, Idx2 kmap, const int *e, unsigned char *out)
+template <int T>
+__global__ void split_pack_kernel(int R, int K, int rowsT, int rowTiles, int kTiles, const double *X, Idx2 rmap,
+                                  Idx2 kmap, const int *e, unsigned char *out)
 {
     const long long units = (long long)rowTiles * rowsT * kTiles * 8;
     const long long tile_bytes = (long long)rowsT * SP_BK * 2;
     const long long slice_bytes = tile_bytes * rowTiles * kTiles;
-    const int P = 7 + 8 * (T - 1);
     for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
          u += (long long)gridDim.x * blockDim.x) {
         const int c8 = (int)(u % (kTiles * 8));
         const int r = (int)(u / (kTiles * 8));
         const int k0 = c8 * 8;
-        long long F[8];
+        unsigned long long G[8];
         if (r < R) {
-            const int E = exp_of_word(e[r]);
+            const int rs = grid_shift(exp_of_word(e[r]), SplitDigits<T>::P);
             const long long ro = off2(rmap, r);
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
                 int k = k0 + q;
-                F[q] = (k < K) ? fixed_point(X[ro + off2(kmap, k)], E, P) : 0;
+                G[q] = (k < K) ? biased_fixed<T>(X[ro + off2(kmap, k)], rs) : SplitDigits<T>::B;
             }
         } else {
 #pragma unroll
-            for (int q = 0; q < 8; ++q) F[q] = 0;
+            for (int q = 0; q < 8; ++q) G[q] = SplitDigits<T>::B;
         }
         const long long tile = (long long)(r / rowsT) * kTiles + (k0 / SP_BK);
-        write_digit_chunks(F, T, out + tile * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK), slice_bytes);
+        write_digit_chunks<T>(G, out + tile * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK), slice_bytes);
     }
 }
 
 // Exponent and digits in one kernel for an operand whose K index is contiguous
-// (X(r, k) = X[off(r) + k]): one warp per row scans the row for its exponent
-// word, then packs it in 8-wide chunks (the second read of the row hits L1/L2);
-// rows past R up to the padded tile count are written as zero digits.
-__global__ void __launch_bounds__(256) split_rowpack_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles, int T,
+// (X(r, k) = X[off(r) + k]) but whose rows are not 16-byte aligned pairs: one
+// warp per row scans the row for its exponent word, then packs it in 8-wide
+// chunks (the second read of the row hits L1/L2); rows past R up to the padded
+// tile count are written as zero digits.
+template <int T>
+__global__ void __launch_bounds__(256) split_rowpack_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles,
                                                             const double *X, Idx2 rmap, int *e, unsigned char *out,
                                                             long long slice_bytes)
 {
     const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (r >= rowsTotal) return;
-    const int P = 7 + 8 * (T - 1);
     const long long tile_bytes = (long long)rowsT * SP_BK * 2;
     unsigned char *row_base = out + (long long)(r / rowsT) * kTiles * tile_bytes;
+    unsigned long long G[8];
     if (r < R) {
         const double *x = X + off2(rmap, r);
         unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
@@ -231,21 +245,74 @@ __global__ void __launch_bounds__(256) split_rowpack_kernel(int R, int K, int ro
         unsigned m = max(max(m0, m1), max(m2, m3));
         for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
         if (lane == 0) e[r] = (int)m;
-        const int E = exp_of_word((int)m);
+        const int rs = grid_shift(exp_of_word((int)m), SplitDigits<T>::P);
         for (int c8 = lane; c8 < kTiles * 8; c8 += 32) {
             const int k0 = c8 * 8;
-            long long F[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) F[q] = (k0 + q < K) ? fixed_point(x[k0 + q], E, P) : 0;
-            write_digit_chunks(F, T, row_base + (long long)(k0 / SP_BK) * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK),
-                               slice_bytes);
+            for (int q = 0; q < 8; ++q) G[q] = (k0 + q < K) ? biased_fixed<T>(x[k0 + q], rs) : SplitDigits<T>::B;
+            write_digit_chunks<T>(G, row_base + (long long)(k0 / SP_BK) * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK),
+                                  slice_bytes);
         }
     } else {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) G[q] = SplitDigits<T>::B;
         for (int c8 = lane; c8 < kTiles * 8; c8 += 32) {
             const int k0 = c8 * 8;
-            long long F[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-            write_digit_chunks(F, T, row_base + (long long)(k0 / SP_BK) * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK),
-                               slice_bytes);
+            write_digit_chunks<T>(G, row_base + (long long)(k0 / SP_BK) * tile_bytes + sw128_off(r % rowsT, k0 % SP_BK),
+                                  slice_bytes);
+        }
+    }
+}
+
+// Packing of a contiguous-K operand read once, held in registers: a group of
+// WPR warps owns one row; at step j warp w of the group loads the 64-wide K
+// tile kt = j WPR + w as one double2 per lane (512 contiguous bytes per warp
+// instruction), the group reduces the exponent word through shared memory, and
+// each lane writes its two digits of every slice as one 32-bit word, so one
+// store instruction fills the tile's whole 128-byte swizzled row of that
+// slice.  Needs K even, 16-byte aligned rows and NV WPR >= kTiles; rows from R
+// up to rowsTotal and columns from K up to the tile edge get zero digits.
+template <int NV, int T>
+__global__ void __launch_bounds__(512, 1) split_rowpack_reg_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles,
+                                                                int WPR, const double *X, Idx2 rmap, int *e,
+                                                                unsigned char *out, long long slice_bytes)
+{
+    __shared__ unsigned s_m[16];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int g = warp / WPR, w = warp - g * WPR;
+    const int r = blockIdx.x * (blockDim.x / (32 * WPR)) + g;
+    const bool live = r < R;
+    const double *x = live ? X + off2(rmap, r) : X;
+    double2 v[NV];
+    unsigned m = 0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int k = ((j * WPR + w) << 6) + 2 * lane;
+        v[j] = make_double2(0.0, 0.0);
+        if (live && k < K) v[j] = *reinterpret_cast<const double2 *>(x + k);
+    }
+#pragma unroll
+    for (int j = 0; j < NV; ++j) m = max(m, max(abs_hi_word(v[j].x), abs_hi_word(v[j].y)));
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) s_m[warp] = m;
+    __syncthreads();
+    if (r >= rowsTotal) return;
+    m = 0;
+    for (int i = 0; i < WPR; ++i) m = max(m, s_m[g * WPR + i]);
+    if (live && w == 0 && lane == 0) e[r] = (int)m;
+    const int rs = grid_shift(exp_of_word((int)m), SplitDigits<T>::P);
+    const long long tile_bytes = (long long)rowsT * SP_BK * 2;
+    unsigned char *row_base = out + (long long)(r / rowsT) * kTiles * tile_bytes + sw128_off(r % rowsT, 2 * lane);
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        const int kt = j * WPR + w;
+        if (kt < kTiles) {
+            const unsigned long long G0 = biased_fixed<T>(v[j].x, rs), G1 = biased_fixed<T>(v[j].y, rs);
+            unsigned char *dst = row_base + (long long)kt * tile_bytes;
+#pragma unroll
+            for (int t = 0; t < T; ++t)
+                *reinterpret_cast<uint32_t *>(dst + (long long)t * slice_bytes) =
+                    bf16x2_of(slice_digit<T>(G0, t), slice_digit<T>(G1, t));
         }
     }
 }
@@ -253,32 +320,32 @@ __global__ void __launch_bounds__(256) split_rowpack_kernel(int R, int K, int ro
 // The same packing for a transposed operand, X(r, k) = X[k * kstride + r]: a
 // block stages 32 rows x one 64-wide K tile through shared memory, reading with
 // the lanes along the contiguous rows and writing the swizzled chunks as above.
-__global__ void __launch_bounds__(256) split_pack_t_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles, int T,
+template <int T>
+__global__ void __launch_bounds__(256) split_pack_t_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles,
                                                            const double *X, long long kstride, const int *e,
                                                            unsigned char *out, long long slice_bytes)
 {
-    __shared__ long long Fs[32][SP_BK + 1];
+    __shared__ unsigned long long Gs[32][SP_BK + 1];
     const int r0 = blockIdx.x * 32, kt = blockIdx.y;
-    const int P = 7 + 8 * (T - 1);
     {
         const int r = threadIdx.x & 31, kg = threadIdx.x >> 5;
         const int gr = r0 + r;
-        const int E = gr < R ? exp_of_word(e[gr]) : 0;
+        const int rs = grid_shift(gr < R ? exp_of_word(e[gr]) : 0, SplitDigits<T>::P);
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             const int kl = kg * 8 + q, k = kt * SP_BK + kl;
-            Fs[r][kl] = (gr < R && k < K) ? fixed_point(X[(long long)k * kstride + gr], E, P) : 0;
+            Gs[r][kl] = (gr < R && k < K) ? biased_fixed<T>(X[(long long)k * kstride + gr], rs) : SplitDigits<T>::B;
         }
     }
     __syncthreads();
     const int r = threadIdx.x >> 3, c8 = threadIdx.x & 7;
     const int gr = r0 + r;
     if (gr >= rowsTotal) return;   // past the last padded tile (rowsT need not divide by 32)
-    long long F[8];
+    unsigned long long G[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) F[q] = Fs[r][c8 * 8 + q];
+    for (int q = 0; q < 8; ++q) G[q] = Gs[r][c8 * 8 + q];
     const long long tile = (long long)(gr / rowsT) * kTiles + kt;
-    write_digit_chunks(F, T, out + tile * ((long long)rowsT * SP_BK * 2) + sw128_off(gr % rowsT, c8 * 8), slice_bytes);
+    write_digit_chunks<T>(G, out + tile * ((long long)rowsT * SP_BK * 2) + sw128_off(gr % rowsT, c8 * 8), slice_bytes);
 }
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -762,25 +829,161 @@ cudaError_t split_prepare()
 // Exponents and digit slices of one operand X(r, k) (rows of A, columns of B).
 // A transposed operand -- unit-stride rows, strided K -- is read with the lanes
 // along its rows; everything else one row per warp / thread chunk along K.
-static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int rowsT, int rowTiles,
-                                 int kTiles, int T, int *e, unsigned char *pk, cudaStream_t st)
+// ---------------------------------------------------------------- transposed operands, one launch
+// Exponents and digits of a transposed operand X(r, k) = X[k * kstride + r] in
+// one launch: a cluster of CS CTAs spans K for one group of 32 rows (lanes along
+// the contiguous rows, warp kg on the 8-wide chunk kg of each 64-wide K tile).
+// CTA c holds the K tiles kt = c + CS i, i < KC, in registers; the row maxima of
+// the cluster's CTAs are combined through distributed shared memory between
+// cluster barriers (hardware barriers: every thread of every CTA reaches both),
+// then each held tile is converted and written through shared memory so that
+// eight consecutive threads store one row's 128 bytes.  Rows from R up to
+// rowsTotal get zero digits.  Needs CS KC >= kTiles, KC <= KCMAX, CS <= 8.
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ unsigned ld_cluster_u32(const void *local, unsigned rank)
+{
+    uint32_t ra, v;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(smem_u32(local)), "r"(rank));
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+template <int T, int KCMAX>
+__global__ void __launch_bounds__(256, 1) split_pack_tc_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles,
+                                                               int KC, const double *X, long long kstride, int *e,
+                                                               unsigned char *out, long long slice_bytes)
+{
+    __shared__ unsigned long long Gs[32][SP_BK + 1];
+    __shared__ unsigned s_part[8][32];
+    __shared__ unsigned s_cta[32];
+    __shared__ unsigned s_row[32];
+    const int lane = threadIdx.x & 31, kg = threadIdx.x >> 5;
+    const int CS = gridDim.x, c = blockIdx.x;   // the cluster spans the grid's x extent
+    const int r0 = blockIdx.y * 32, gr = r0 + lane;
+    double v[KCMAX][8];
+    unsigned m = 0;
+#pragma unroll
+    for (int i = 0; i < KCMAX; ++i) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = (c + CS * i) * SP_BK + kg * 8 + q;
+            v[i][q] = (i < KC && gr < R && k < K) ? X[(long long)k * kstride + gr] : 0.0;
+            m = max(m, abs_hi_word(v[i][q]));
+        }
+    }
+    s_part[kg][lane] = m;
+    __syncthreads();
+    if (kg == 0) {
+        unsigned mm = 0;
+        for (int w = 0; w < 8; ++w) mm = max(mm, s_part[w][lane]);
+        s_cta[lane] = mm;
+    }
+    cluster_arrive();
+    cluster_wait();   // every CTA's s_cta is written
+    if (kg == 0) {
+        unsigned mm = 0;
+        for (int p = 0; p < CS; ++p) mm = max(mm, ld_cluster_u32(&s_cta[lane], (unsigned)p));
+        s_row[lane] = mm;
+        if (c == 0 && gr < R) e[gr] = (int)mm;
+    }
+    cluster_arrive();   // this CTA's remote reads are done; waited for before exit
+    __syncthreads();
+    const int rs = grid_shift(exp_of_word((int)s_row[lane]), SplitDigits<T>::P);
+    const int rw = threadIdx.x >> 3, c8 = threadIdx.x & 7;
+    const int grw = r0 + rw;
+#pragma unroll
+    for (int i = 0; i < KCMAX; ++i) {
+        const int kt = c + CS * i;
+        if (i < KC && kt < kTiles) {   // uniform over the CTA
+#pragma unroll
+            for (int q = 0; q < 8; ++q) Gs[lane][kg * 8 + q] = biased_fixed<T>(v[i][q], rs);
+            __syncthreads();
+            if (grw < rowsTotal) {
+                unsigned long long G[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) G[q] = Gs[rw][c8 * 8 + q];
+                const long long tile = (long long)(grw / rowsT) * kTiles + kt;
+                write_digit_chunks<T>(G, out + tile * ((long long)rowsT * SP_BK * 2) + sw128_off(grw % rowsT, c8 * 8),
+                                      slice_bytes);
+            }
+            __syncthreads();
+        }
+    }
+    cluster_wait();
+}
+
+template <int T, int KCMAX>
+static cudaError_t launch_pack_tc(int R, int K, int rowsT, int rowsTotal, int kTiles, int CS, int KC, const double *X,
+                                  long long kstride, int *e, unsigned char *pk, long long slice_bytes, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CS, (rowsTotal + 31) / 32, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, split_pack_tc_kernel<T, KCMAX>, R, K, rowsT, rowsTotal, kTiles, KC, X, kstride, e,
+                              pk, slice_bytes);
+}
+
+template <int T>
+static cudaError_t split_prepass_t(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int rowsT, int rowTiles,
+                                   int kTiles, int *e, unsigned char *pk, cudaStream_t st)
 {
     const long long slice_bytes = (long long)rowTiles * kTiles * rowsT * SP_BK * 2;
+    const int KC = (kTiles + 7) / 8;
+    int CS = 1;
+    while (CS * KC < kTiles) CS *= 2;   // <= 8 for kTiles <= 64
+    // one launch for transposed operands whose clusters fit in one wave (one CTA
+    // per SM at this register count); wider ones convert faster at full occupancy
+    if (rmap.s1 == 0 && rmap.s2 == 1 && kmap.s1 == 0 && kmap.s2 != 1 && kTiles <= 64 &&
+        (long long)(rowTiles * rowsT + 31) / 32 * CS <= device_sm_count()) {
+        CTM_COUNT_LAUNCH(1);
+        cudaError_t e1 = KC <= 2 ? launch_pack_tc<T, 2>(R, K, rowsT, rowTiles * rowsT, kTiles, CS, KC, X, kmap.s2, e, pk,
+                                                        slice_bytes, st)
+                                 : launch_pack_tc<T, 8>(R, K, rowsT, rowTiles * rowsT, kTiles, CS, KC, X, kmap.s2, e, pk,
+                                                        slice_bytes, st);
+        return e1 != cudaSuccess ? e1 : cudaGetLastError();
+    }
     if (rmap.s1 == 0 && rmap.s2 == 1 && kmap.s1 == 0 && kmap.s2 != 1) {
         cudaError_t e0 = cudaMemsetAsync(e, 0, sizeof(int) * (size_t)R, st);
         if (e0 != cudaSuccess) return e0;
         CTM_COUNT_LAUNCH(2);
         split_colexp_kernel<<<dim3((R + 127) / 128, (K + SP_COLEXP_K - 1) / SP_COLEXP_K), 128, 0, st>>>(R, K, X,
                                                                                                        kmap.s2, e);
-        split_pack_t_kernel<<<dim3((rowTiles * rowsT + 31) / 32, kTiles), 256, 0, st>>>(
-            R, K, rowsT, rowTiles * rowsT, kTiles, T, X, kmap.s2, e, pk, slice_bytes);
+        split_pack_t_kernel<T><<<dim3((rowTiles * rowsT + 31) / 32, kTiles), 256, 0, st>>>(
+            R, K, rowsT, rowTiles * rowsT, kTiles, X, kmap.s2, e, pk, slice_bytes);
         return cudaGetLastError();
     }
     if (kmap.s1 == 0 && kmap.s2 == 1) {
         const int rows = rowTiles * rowsT;
         CTM_COUNT_LAUNCH(1);
-        split_rowpack_kernel<<<(rows + 7) / 8, 256, 0, st>>>(R, K, rowsT, rows, kTiles, T, X, rmap, e, pk,
-                                                             slice_bytes);
+        const bool pairs = ((uintptr_t)X & 15) == 0 && (K & 1) == 0 && (rmap.s1 & 1) == 0 && (rmap.s2 & 1) == 0;
+        if (pairs && kTiles <= 128) {
+            int nv = 1;
+            while (nv < 8 && (kTiles + nv - 1) / nv > 8) nv *= 2;
+            const int wpr = (kTiles + nv - 1) / nv;        // <= 16 warps per row
+            const int rpb = wpr >= 8 ? 1 : 8 / wpr;         // rows per block
+            const int blocks = (rows + rpb - 1) / rpb, threads = 32 * wpr * rpb;
+#define CTM_ROWPACK(NVV)                                                                                              \
+    split_rowpack_reg_kernel<NVV, T><<<blocks, threads, 0, st>>>(R, K, rowsT, rows, kTiles, wpr, X, rmap, e, pk,       \
+                                                                 slice_bytes)
+            if (nv == 1) CTM_ROWPACK(1);
+            else if (nv == 2) CTM_ROWPACK(2);
+            else if (nv == 4) CTM_ROWPACK(4);
+            else CTM_ROWPACK(8);
+#undef CTM_ROWPACK
+            return cudaGetLastError();
+        }
+        split_rowpack_kernel<T><<<(rows + 7) / 8, 256, 0, st>>>(R, K, rowsT, rows, kTiles, X, rmap, e, pk,
+                                                                slice_bytes);
         return cudaGetLastError();
     }
     CTM_COUNT_LAUNCH(2);
@@ -789,8 +992,20 @@ static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 
     long long blocks = (units + 255) / 256, cap = 64LL * device_sm_count();
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    split_pack_kernel<<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowTiles, kTiles, T, X, rmap, kmap, e, pk);
+    split_pack_kernel<T><<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowTiles, kTiles, X, rmap, kmap, e, pk);
     return cudaGetLastError();
+}
+
+static cudaError_t split_prepass(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int rowsT, int rowTiles,
+                                 int kTiles, int T, int *e, unsigned char *pk, cudaStream_t st)
+{
+    switch (T) {
+    case 2: return split_prepass_t<2>(R, K, X, rmap, kmap, rowsT, rowTiles, kTiles, e, pk, st);
+    case 3: return split_prepass_t<3>(R, K, X, rmap, kmap, rowsT, rowTiles, kTiles, e, pk, st);
+    case 4: return split_prepass_t<4>(R, K, X, rmap, kmap, rowsT, rowTiles, kTiles, e, pk, st);
+    case 5: return split_prepass_t<5>(R, K, X, rmap, kmap, rowsT, rowTiles, kTiles, e, pk, st);
+    default: return cudaErrorInvalidValue;
+    }
 }
 
 static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,

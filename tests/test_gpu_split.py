@@ -24,7 +24,9 @@ def _split_gemm(A, B, T):
     return _np(binding.ctm_gemm(torch.from_numpy(A).cuda(), torch.from_numpy(B).cuda(), "split_bf16", T))
 
 
-SHAPES = [(128, 64, 64), (200, 72, 72), (130, 100, 40), (64, 300, 520), (300, 130, 1000), (1024, 96, 4096)]
+SHAPES = [(128, 64, 64), (200, 72, 72), (130, 100, 40), (64, 300, 520), (300, 130, 1000), (1024, 96, 4096),
+          (96, 40, 5000),    # K > 4096: the two-launch transposed-operand pre-pass
+          (64, 5000, 520)]   # 5000 transposed rows: clusters beyond one wave, the two-launch pre-pass
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
@@ -85,6 +87,31 @@ def test_split_step_matches_oracle(ctm_lib, T, tol):
     assert np.max(np.abs(M - ref.last["M"])) <= tol * np.max(np.abs(ref.last["M"]))
     s = _np(g.ctm_get_intermediate("s"))
     assert np.max(np.abs(s - ref.s)) <= 100 * tol
+    g.close()
+
+
+def test_split_step_matches_oracle_d6_chi72(ctm_lib):
+    """The benchmark workload (D = 6, chi = 72, n = 2592) in the benchmark's precision (T = 5),
+    one step from the oracle's environment after one oracle step."""
+    w = I.WORKLOADS["kh_D6_chi72"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)
+    ref.step()
+    g = _ctm(A, w.chi, precision="split_bf16", n_split=5)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    ref_Qs = ref.warm_start()
+    ref.step()
+    g.ctm_step(1)
+    M = _np(g.ctm_get_intermediate("M"))
+    assert np.max(np.abs(M - ref.last["M"])) <= 1e-9 * np.max(np.abs(ref.last["M"]))
+    # Y = M Qs: the error of M carried through Qs plus this contraction's own truncation bound
+    Qs = ref_Qs
+    Mmax = np.max(np.abs(ref.last["M"]))
+    bound = Mmax * (1e-9 * np.max(np.sum(np.abs(Qs), axis=0)) + 6 * 2.0 ** -40 * w.n * np.max(np.abs(Qs)))
+    assert np.max(np.abs(_np(g.ctm_get_intermediate("Y")) - ref.last["Y"])) <= bound
+    C, T, Q = (_np(x) for x in g.ctm_get_env())
+    assert np.max(np.abs(Q.T @ Q - np.eye(w.chi))) <= 1e-12
+    assert np.max(np.abs(_np(g.ctm_get_intermediate("s")) - ref.s)) <= 1e-7
     g.close()
 
 
