@@ -28,6 +28,11 @@ if ROOT not in sys.path:
 
 METRIC = "CTMRG steps/s & time-to-converged env at D=6,χ=72; mixed vs FP64 at ≤1e-9 dE"
 L2_FLUSH_BYTES = 256 << 20
+# DRAM bytes of the step's 11 contraction launches, from one ncu capture per
+# workload (--metrics dram__bytes_read.sum,dram__bytes_write.sum on the launches
+# of one step, plans replayed from the plain run's autotune cache).  Set back to
+# absent whenever the contraction kernel changes.
+NCU_TRAFFIC = {}
 
 
 def _peaks():
@@ -356,6 +361,11 @@ def main():
                               "kind::f16 into TMEM",
                     "peak_source": f"{src} bf16 burst",
                     "fp64_equivalent_tflops": flops / (kern_ms / 1e3) / 1e12}
+    key = (w.name, args.precision, args.n_split if args.precision != "fp64" else 0)
+    if key in NCU_TRAFFIC:
+        roofline["traffic"] = NCU_TRAFFIC[key]
+        roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of the step's 11 contraction "
+                                    "launches (bytes per step, like achieved), one ncu capture, cold cache")
     roofline["kernel_ms_per_step"] = kern_ms
     roofline["algorithmic_flops_per_step"] = flops
     roofline["phase_ms"] = {k: v / nprof for k, v in phases.items()}

@@ -672,43 +672,103 @@ __global__ void __launch_bounds__(SpCfg<NT>::THREADS, SpCfg<NT>::MIN_BLOCKS) gem
         long long *stage = reinterpret_cast<long long *>(sm);
         long long *row_off = stage + SP_BM * PITCH;
         long long *col_off = row_off + SP_BM;
+        int *row_sc = reinterpret_cast<int *>(col_off + NT);   // exponent scales of the output
+        int *col_sc = row_sc + SP_BM;
         const int ew = warp - 2, et = threadIdx.x - 64;   // epilogue warp / thread index
         const int m0 = mt * SP_BM, n0 = nt * NT;
         const int rows = min(SP_BM, a.M - m0), cols = min(NT, a.N - n0);
+        const bool fin = a.ksplit == 1;   // FP64 output here, else int64 sums to the split-K buffer
         if (!*abort_flag) {
+            // the raw sums go to shared memory; they are converted in the write-out,
+            // where the accumulator registers are free and a batch of values converts
+            // at once instead of one long dependent chain per value
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             const int r = 32 * sub + lane;
             const int m = m0 + r;
             if (m < a.M) {
-                const int sc_m = exp_of_word(a.eA[m]) - 14 - 8 * (T - 1);
-                if (part == 0) row_off[r] = a.ksplit == 1 ? off2(a.Cm, m) : (long long)m * a.N;
+                if (part == 0) {
+                    row_off[r] = fin ? off2(a.Cm, m) : (long long)m * a.N;
+                    row_sc[r] = fin ? exp_of_word(__ldg(a.eA + m)) - 14 - 8 * (T - 1) : 0;
+                }
 #pragma unroll
                 for (int q = 0; q < QW; ++q) {
                     const int c = part * QW + q;
-                    if (n0 + c < a.N)
-                        stage[r * PITCH + c] = a.ksplit == 1
-                                                   ? __double_as_longlong(scaled_int_to_double(acc[q], sc_m + exp_of_word(a.eB[n0 + c])))
-                                                   : acc[q];
+                    if (n0 + c < a.N) stage[r * PITCH + c] = acc[q];
                 }
             }
-            for (int c = et; c < cols; c += SP_EPI_THREADS) col_off[c] = a.ksplit == 1 ? off2(a.Cn, n0 + c) : (long long)(n0 + c);
+            for (int c = et; c < cols; c += SP_EPI_THREADS) {
+                col_off[c] = fin ? off2(a.Cn, n0 + c) : (long long)(n0 + c);
+                col_sc[c] = fin ? exp_of_word(__ldg(a.eB + n0 + c)) : 0;
+            }
         }
         asm volatile("bar.sync 1, %0;" ::"n"(SP_EPI_THREADS) : "memory");
         if (!*abort_flag) {
+            // Write-out in groups of WU rows (columns): the staged values, offsets and
+            // scales of a group are read from shared memory before its stores.
+            constexpr int WU = 4;
             const bool along_n = (a.ksplit > 1) || a.Cn.s2 == 1 || a.Cm.s2 != 1;
             if (along_n) {
-                for (int r = ew; r < rows; r += SP_EPI_WARPS) {
-                    const long long ro = row_off[r];
-                    for (int c = lane; c < cols; c += 32) {
-                        const long long v = stage[r * PITCH + c];
-                        if (a.ksplit == 1) a.C[ro + col_off[c]] = __longlong_as_double(v);
-                        else atomicAdd(&a.partial[ro + col_off[c]], (unsigned long long)v);
+                constexpr int NCH = (NT + 31) / 32;   // 32-column chunks of a row
+                long long co[NCH];
+                int cs[NCH];
+#pragma unroll
+                for (int j = 0; j < NCH; ++j) {
+                    const bool in = lane + 32 * j < cols;
+                    co[j] = in ? col_off[lane + 32 * j] : 0;
+                    cs[j] = in ? col_sc[lane + 32 * j] : 0;
+                }
+                for (int rb = ew; rb < rows; rb += WU * SP_EPI_WARPS) {
+                    long long ro[WU], v[WU][NCH];
+                    int rsc[WU];
+#pragma unroll
+                    for (int w = 0; w < WU; ++w) {
+                        const int r = rb + w * SP_EPI_WARPS;
+                        ro[w] = r < rows ? row_off[r] : 0;
+                        rsc[w] = r < rows ? row_sc[r] : 0;
+#pragma unroll
+                        for (int j = 0; j < NCH; ++j)
+                            v[w][j] = (r < rows && lane + 32 * j < cols) ? stage[r * PITCH + lane + 32 * j] : 0;
+                    }
+#pragma unroll
+                    for (int w = 0; w < WU; ++w) {
+                        if (rb + w * SP_EPI_WARPS >= rows) break;
+#pragma unroll
+                        for (int j = 0; j < NCH; ++j) {
+                            if (lane + 32 * j >= cols) continue;
+                            if (fin) a.C[ro[w] + co[j]] = scaled_int_to_double(v[w][j], rsc[w] + cs[j]);
+                            else atomicAdd(&a.partial[ro[w] + co[j]], (unsigned long long)v[w][j]);
+                        }
                     }
                 }
             } else {
-                for (int c = ew; c < cols; c += SP_EPI_WARPS) {
-                    const long long co = col_off[c];
-                    for (int r = lane; r < rows; r += 32) a.C[row_off[r] + co] = __longlong_as_double(stage[r * PITCH + c]);
+                constexpr int NRC = SP_BM / 32;   // 32-row chunks of a column
+                long long ro[NRC];
+                int rsc[NRC];
+#pragma unroll
+                for (int j = 0; j < NRC; ++j) {
+                    const bool in = lane + 32 * j < rows;
+                    ro[j] = in ? row_off[lane + 32 * j] : 0;
+                    rsc[j] = in ? row_sc[lane + 32 * j] : 0;
+                }
+                for (int cb = ew; cb < cols; cb += WU * SP_EPI_WARPS) {
+                    long long co[WU], v[WU][NRC];
+                    int cs[WU];
+#pragma unroll
+                    for (int w = 0; w < WU; ++w) {
+                        const int c = cb + w * SP_EPI_WARPS;
+                        co[w] = c < cols ? col_off[c] : 0;
+                        cs[w] = c < cols ? col_sc[c] : 0;
+#pragma unroll
+                        for (int j = 0; j < NRC; ++j)
+                            v[w][j] = (c < cols && lane + 32 * j < rows) ? stage[(lane + 32 * j) * PITCH + c] : 0;
+                    }
+#pragma unroll
+                    for (int w = 0; w < WU; ++w) {
+                        if (cb + w * SP_EPI_WARPS >= cols) break;
+#pragma unroll
+                        for (int j = 0; j < NRC; ++j)
+                            if (lane + 32 * j < rows) a.C[ro[j] + co[w]] = scaled_int_to_double(v[w][j], rsc[j] + cs[w]);
+                    }
                 }
             }
         }
@@ -751,7 +811,7 @@ template <int NT>
 size_t split_smem_bytes(int T)
 {
     size_t b = 1024 + (size_t)SpCfg<NT>::ASLOTS * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
-    const size_t out_stage = 1024 + (size_t)SP_BM * (NT + 1) * 8 + (size_t)(SP_BM + NT) * 8;   // epilogue reuse
+    const size_t out_stage = 1024 + (size_t)SP_BM * (NT + 1) * 8 + (size_t)(SP_BM + NT) * 12;   // epilogue reuse
     if (b < out_stage) b = out_stage;
     if (SpCfg<NT>::MIN_BLOCKS == 1 && b < 120 * 1024) b = 120 * 1024;
     return b;
