@@ -100,9 +100,10 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
  * descending singular values.  delta_host (may be NULL) receives the last
  * delta and makes the call synchronous.  Returns CTM_ENONFINITE if the new
  * environment holds NaN/Inf (checked only when delta_host is given).
- * Once the context has run a step, a call with nsteps >= 2 replays the nsteps
- * steps as one CUDA graph (captured on the first such call with that nsteps,
- * and kept until another nsteps is requested); the work is the same. */
+ * Once the context has run a step, a call replays its nsteps steps as one
+ * CUDA graph: a one-step graph for nsteps = 1 (captured on the first such call
+ * and kept), and one for the last nsteps >= 2 requested (re-captured when that
+ * count changes); the work is the same. */
 int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
 
 /* Sec. II.B: repeat steps until delta < tol (tol <= 0: cfg->tol) or max_steps
@@ -171,7 +172,7 @@ int ctm_get_intermediate(const ctm_ctx *ctx, int which, double *dst_dev, size_t 
 int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
 
 /* Number of kernel launches the library has enqueued since it was loaded
- * (host-side count; replays of a captured graph are not counted). */
+ * (host-side count; a replay of a captured graph adds the kernels it holds). */
 unsigned long long ctm_kernel_launches(void);
 
 /* The contraction engine on its own (Sec. II.B: every update of Fig. 3 is a

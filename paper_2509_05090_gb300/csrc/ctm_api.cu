@@ -466,12 +466,13 @@ int check_env_finite(ctm_ctx *c)
 // private stream c->own; the caller has switched c->stream to c->own.  Kernel
 // launches counted during the capture are what one replay launches.  A launch
 // that cannot be captured leaves graph_failed set and the caller runs eagerly.
-int capture_steps(ctm_ctx *c, int nsteps)
+// Capture nsteps steps into *exec (replacing what it held); on failure the
+// context stays eager (graph_failed).
+static int capture_into(ctm_ctx *c, int nsteps, cudaGraphExec_t *exec, unsigned long long *kernels)
 {
-    if (c->graph && c->graph_steps == nsteps) return CTM_OK;
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
+    if (*exec) {
+        cudaGraphExecDestroy(*exec);
+        *exec = nullptr;
     }
     if (c->graph_failed) return CTM_OK;
     cudaGraph_t g = nullptr;
@@ -481,25 +482,35 @@ int capture_steps(ctm_ctx *c, int nsteps)
     for (int i = 0; i < nsteps && rc == CTM_OK; ++i) rc = enqueue_step(c);
     if (rc == CTM_OK) rc = join_side(c);
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph, g, 0);
+    if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);
     c->side_pending = 0;
-    if (rc != CTM_OK || e != cudaSuccess || !c->graph) {
+    if (rc != CTM_OK || e != cudaSuccess || !*exec) {
         cudaGetLastError();
-        c->graph = nullptr;
+        *exec = nullptr;
         c->graph_failed = 1;
     } else {
-        c->graph_steps = nsteps;
-        c->graph_kernels = g_ctm_launches - l0;
+        *kernels = g_ctm_launches - l0;
     }
-    g_ctm_launches = l0;   // nothing ran yet: replays add graph_kernels
+    g_ctm_launches = l0;   // nothing ran yet: replays add the captured kernel count
     return CTM_OK;
 }
 
-int graph_launch(ctm_ctx *c)
+int capture_steps(ctm_ctx *c, int nsteps)
 {
-    CK(cudaGraphLaunch(c->graph, c->stream));
-    CTM_COUNT_LAUNCH(c->graph_kernels);
+    if (nsteps == 1) return c->graph1 ? CTM_OK : capture_into(c, 1, &c->graph1, &c->graph1_kernels);
+    if (c->graph && c->graph_steps == nsteps) return CTM_OK;
+    int rc = capture_into(c, nsteps, &c->graph, &c->graph_kernels);
+    if (c->graph) c->graph_steps = nsteps;
+    return rc;
+}
+
+// Replay the captured graph of nsteps steps (capture_steps first).
+int graph_launch(ctm_ctx *c, int nsteps)
+{
+    cudaGraphExec_t ge = nsteps == 1 ? c->graph1 : c->graph;
+    CK(cudaGraphLaunch(ge, c->stream));
+    CTM_COUNT_LAUNCH(nsteps == 1 ? c->graph1_kernels : c->graph_kernels);
     return CTM_OK;
 }
 
@@ -512,8 +523,8 @@ int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int 
     while (done < max_steps) {
         int chunk = check_every;
         if (done + chunk > max_steps) chunk = max_steps - done;
-        if (c->graph && chunk == c->graph_steps) {
-            int rc = graph_launch(c);
+        if (chunk == 1 ? c->graph1 != nullptr : (c->graph && chunk == c->graph_steps)) {
+            int rc = graph_launch(c, chunk);
             if (rc != CTM_OK) return rc;
         } else {
             for (int i = 0; i < chunk; ++i) {
@@ -665,17 +676,17 @@ int ctm_step(ctm_ctx *c, int nsteps, double *delta_host)
 {
     if (!c || nsteps < 0) return CTM_EINVAL;
     bool done = false;
-    if (nsteps >= 2 && c->steps_done > 0) {
-        // several steps after the first eager one (whose launches ran the
-        // autotuners): replay them as one captured graph, ordered after the
-        // caller's stream
+    if (nsteps >= 1 && c->steps_done > 0) {
+        // steps after the first eager one (whose launches ran the autotuners):
+        // replay them as one captured graph (one for a single step, one for the
+        // last multi-step count), ordered after the caller's stream
         cudaStream_t user = c->stream;
         CK(cudaEventRecord(c->ev_in, user));
         CK(cudaStreamWaitEvent(c->own, c->ev_in, 0));
         c->stream = c->own;
         int rc = capture_steps(c, nsteps);
-        if (rc == CTM_OK && c->graph) {
-            rc = graph_launch(c);
+        if (rc == CTM_OK && (nsteps == 1 ? c->graph1 : c->graph)) {
+            rc = graph_launch(c, nsteps);
             done = (rc == CTM_OK);
         }
         c->stream = user;
@@ -832,6 +843,7 @@ void ctm_destroy(ctm_ctx *c)
 {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
     if (c->own) {
         cudaStreamSynchronize(c->own);
         cudaStreamDestroy(c->own);

@@ -61,6 +61,9 @@ struct ctm_ctx {
     int graph_steps;
     int graph_failed;
     unsigned long long graph_kernels;
+    // one step, for ctm_step(1) after the first step (a user's step-by-step loop)
+    cudaGraphExec_t graph1;
+    unsigned long long graph1_kernels;
     int side_pending;
     // kernel timing (ctm_step_profiled): events around each contraction launch
     int prof_on, prof_n;
