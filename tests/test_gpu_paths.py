@@ -50,18 +50,28 @@ _CHILD = textwrap.dedent("""
 """)
 
 
-@pytest.mark.parametrize("nt", [48, 64, 96])
-def test_split_step_each_tile_width(ctm_lib, tmp_path, nt):
-    w = I.WORKLOADS["kitaev_D4_chi32"]
+def _plan_line(M, N, K, nt):
+    # "pt": the persistent variant (N tile 48, K split -1) wherever K fits one 256-wide chunk
+    if nt == "pt":
+        return f"split {M} {N} {K} 5 : 48 {-1 if K <= 256 else 1}\n"
+    return f"split {M} {N} {K} 5 : {nt} 1\n"
+
+
+@pytest.mark.parametrize("wl,nt", [("kitaev_D4_chi32", 48), ("kitaev_D4_chi32", 64), ("kitaev_D4_chi32", 96),
+                                   ("kitaev_D4_chi32", "pt"), ("kh_D6_chi72", "pt")])
+def test_split_step_each_tile_width(ctm_lib, tmp_path, wl, nt):
+    """One split step with every contraction forced onto one plan family.  At D = 6, chi = 72 the
+    persistent variant walks more output tiles than there are SMs (double-buffered accumulators)."""
+    w = I.WORKLOADS[wl]
     A = w.site_tensor()
     ref = O.OracleCTM(A, w.chi)
-    for _ in range(3):
+    for _ in range(3 if w.chi <= 32 else 1):
         ref.step()
     env = tmp_path / "env.npz"
     np.savez(env, A=A, chi=w.chi, C=ref.C, T=ref.T, Q=ref.Q)
     ref.step()
     cache = tmp_path / "plans.txt"
-    cache.write_text("".join(f"split {M} {N} {K} 5 : {nt} 1\n" for M, N, K in _step_shapes(w.chi, w.D2)))
+    cache.write_text("".join(_plan_line(M, N, K, nt) for M, N, K in _step_shapes(w.chi, w.D2)))
     out = tmp_path / "out.npz"
     script = tmp_path / "child.py"
     script.write_text(_CHILD)
