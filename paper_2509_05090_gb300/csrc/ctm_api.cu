@@ -153,7 +153,11 @@ size_t layout(ctm_ctx *c, char *base)
         // largest operand of the step's contractions
         size_t ap = 0, bp = 0, pp = 0;
         long long ecap = 0;
-        for (const auto &sh : step_shapes(c)) {
+        std::vector<Shape> shapes = step_shapes(c);
+        // the energy's large contractions (E = W Q^T and the two open-layer contractions)
+        shapes.push_back({(int)n, (int)n, (int)chi});
+        shapes.push_back({(int)(chi * chi), (int)(d * d * D2), (int)(D2 * D2)});
+        for (const auto &sh : shapes) {
             SplitPlan pl = split_plan_caps(sh.M, sh.N, sh.K, c->split_T);
             if (pl.a_pack_bytes > ap) ap = pl.a_pack_bytes;
             if (pl.b_pack_bytes > bp) bp = pl.b_pack_bytes;
@@ -758,21 +762,23 @@ int ctm_energy(ctm_ctx *c, const double *h_dev, double *e_bond_host, double *e_s
     g = GemmF64{(int)n, chi, chi, c->Qn, idx_lin(chi), idx_lin(1), src, idx_lin(chi), idx_lin(1), c->W,
                 idx_lin(chi), idx_lin(1), 1.0, 0.0};
     CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
+    // (this and the two open-layer contractions below go through run_gemm: the split-BF16
+    // engine in split mode, whose error at T = 5 is far below the energy's tolerance)
     g = GemmF64{(int)n, (int)n, chi, c->W, idx_lin(chi), idx_lin(1), c->Qn, idx_lin(1), idx_lin(chi), c->H,
                 idx_lin(n), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
+    CK(run_gemm(c, g));
     // open layers b[p][..] = A[s] (x) A[t], p = s*d + t
     CK(launch_open_layers(d, c->D, c->A, c->b, st));
     const long long D3 = (long long)D2 * D2 * D2;
     // Y1o[(a,b)][(pB,z)] = sum_{u,l} X'[(a,b),(u,l)] b[pB][u][l][z]
     g = GemmF64{chi * chi, dd * D2, D2 * D2, c->X, idx_lin((long long)D2 * D2), idx_lin(1), c->b, idx_lin(D2),
                 idx_split(D2, D3, 1), c->Y1o, idx_lin((long long)dd * D2), idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
+    CK(run_gemm(c, g));
     // G2[(a,b)][(pA,z)] = sum_{x,y} E[(a,y),(b,x)] b[pA][z][x][y]
     g = GemmF64{chi * chi, dd * D2, D2 * D2, c->H, idx_split(chi, (long long)D2 * n, D2), idx_split(D2, 1, n),
                 c->b, idx_lin(1), idx_split(D2, D3, (long long)D2 * D2), c->G2, idx_lin((long long)dd * D2),
                 idx_lin(1), 1.0, 0.0};
-    CK(gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, st));
+    CK(run_gemm(c, g));
     CTM_COUNT_LAUNCH(1);
     CK(rho_reduce(c));
 
