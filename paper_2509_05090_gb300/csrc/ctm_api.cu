@@ -96,6 +96,7 @@ size_t layout(ctm_ctx *c, char *base)
     c->C = td(chi * chi);
     c->Cn = td(chi * chi);
     c->Cr = td(chi * chi);
+    c->Cspec = td(chi * chi);
     c->T = td(chi * D2 * chi);
     c->Tn = td(chi * D2 * chi);
     c->Q = td(n * chi);
@@ -357,10 +358,11 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout, int lane = 0)
     return CTM_OK;
 }
 
-// The corner spectrum of step t runs on the side stream while step t+1 computes;
-// it reads C (handed over at the end of step t) and must finish before step
-// t+1 overwrites C.  `side_pending` marks spectrum work not yet joined into
-// the caller's stream; every public call joins it before returning.
+// The corner spectrum of step t runs on the side stream while the step (in split
+// mode from the corner update on) and step t+1 compute; it reads C' (its copy
+// Cspec in split mode, else C once handed over at the end of step t) and must
+// finish before that buffer is rewritten.  `side_pending` marks spectrum work not
+// yet joined into the caller's stream; every public call joins it before returning.
 int enqueue_step(ctm_ctx *c)
 {
     int rc;
@@ -374,13 +376,30 @@ int enqueue_step(ctm_ctx *c)
     if (c->split_T > 0 && c->steps_done > 0) {
         CK(cudaEventRecord(c->ev_q, st));
         CK(cudaStreamWaitEvent(c->lane2, c->ev_q, 0));
+        // the previous step's spectrum (reading C or Cspec) is done before Cspec is rewritten
+        if (c->side_pending) CK(cudaStreamWaitEvent(c->lane2, c->ev_join, 0));
         if ((rc = enqueue_corner(c, c->Qn, c->Cn, 1)) != CTM_OK) return rc;
+        CK(cudaMemcpyAsync(c->Cspec, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, c->lane2));
         CK(cudaEventRecord(c->ev_corner, c->lane2));
+        // this step's corner spectrum starts from its private copy of C' as soon as the
+        // corner update is done, beside the edge update and the next step's first
+        // phases; only the next such step rewrites the copy, after waiting for it
+        CK(cudaStreamWaitEvent(c->side, c->ev_corner, 0));
+        CK(launch_spectrum((int)chi, c->Cspec, c->s_new, c->s, c->delta, c->spec_work, c->side));
+        CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
+        CK(cudaEventRecord(c->ev_join, c->side));
+        c->side_pending = 1;
         if ((rc = enqueue_edge(c, c->Qn, c->Tn, 2)) != CTM_OK) return rc;
-    } else {
-        if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
-        if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
+        // no wait for the spectrum before the hand-over: it reads Cspec, and the last
+        // edge contraction waited for the corner update, which waited for the previous
+        // spectrum (the one that may read C)
+        CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
+        return CTM_OK;
     }
+    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
     if (c->side_pending) CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));

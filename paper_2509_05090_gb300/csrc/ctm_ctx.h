@@ -24,6 +24,7 @@ struct ctm_ctx {
     // FP64 buffers (device, inside the caller's workspace)
     double *Araw, *A, *a;
     double *C, *Cn, *Cr;
+    double *Cspec;            // split mode: the copy of C' the side-stream spectrum reads
     double *T, *Tn;
     double *Q, *Qn, *Qs, *Y, *W, *MQ;
     double *R;
