@@ -198,40 +198,54 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const dou
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ double sh_beta, sh_alpha;
-    __shared__ int sh_skip;
-    double *A = sm;                      // chi x chi
-    double *v = A + chi * chi;           // chi
+    // odd row pitch: the mat-vec's lanes read down a column, conflict-free
+    const int ld = chi | 1;
+    double *A = sm;                      // chi x ld
+    double *v = A + chi * ld;            // chi
     double *p = v + chi;                 // chi
     const int tid = threadIdx.x;
     for (int t = tid; t < chi * chi; t += blockDim.x) {
         int i = t / chi, j = t % chi;
-        A[t] = 0.5 * (C[t] + C[(size_t)j * chi + i]);
+        A[i * ld + j] = 0.5 * (C[t] + C[(size_t)j * chi + i]);
     }
     __syncthreads();
     for (int kc = 0; kc + 2 < chi; ++kc) {
         const int b0 = kc + 1, m = chi - b0;
+        // x = the column below the diagonal, kept in v (v_0 = x_0 until alpha is known)
         double part = 0.0;
-        for (int i = 1 + tid; i < m; i += blockDim.x) part += A[(b0 + i) * chi + kc] * A[(b0 + i) * chi + kc];
-        double tail = block_sum(part, red);
-        if (tid == 0) {
-            double x0 = A[b0 * chi + kc];
-            sh_skip = (tail == 0.0);
-            double nrm = sqrt(tail + x0 * x0);
-            double alpha = (x0 >= 0.0) ? -nrm : nrm;
-            sh_alpha = alpha;
-            sh_beta = (tail == 0.0) ? 0.0 : 1.0 / (nrm * (nrm + fabs(x0)));
-            v[0] = x0 - alpha;
-        }
-        __syncthreads();
-        if (sh_skip) continue;
-        for (int i = 1 + tid; i < m; i += blockDim.x) v[i] = A[(b0 + i) * chi + kc];
-        __syncthreads();
-        const double beta = sh_beta;
         for (int i = tid; i < m; i += blockDim.x) {
-            double s = 0.0;
-            for (int j = 0; j < m; ++j) s = fma(A[(b0 + i) * chi + b0 + j], v[j], s);
-            p[i] = beta * s;
+            const double x = A[(b0 + i) * ld + kc];
+            v[i] = x;
+            if (i > 0) part += x * x;
         }
+        const double tail = block_sum(part, red);   // its barriers also publish v
+        if (tail == 0.0) continue;                  // already tridiagonal in this column
+        const double x0 = v[0];
+        // the last thread (outside the mat-vec rows) derives the reflector while the
+        // others form y = A x; then A v = y - alpha A e_0 with v = x - alpha e_0
+        if (tid == (int)blockDim.x - 1) {
+            const double nrm = sqrt(tail + x0 * x0);
+            const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+            sh_alpha = alpha;
+            sh_beta = 1.0 / (nrm * (nrm + fabs(x0)));
+        }
+        for (int i = tid; i < m; i += blockDim.x) {
+            const double *row = A + (b0 + i) * ld + b0;
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+            int j = 0;
+            for (; j + 3 < m; j += 4) {
+                s0 = fma(row[j], v[j], s0);
+                s1 = fma(row[j + 1], v[j + 1], s1);
+                s2 = fma(row[j + 2], v[j + 2], s2);
+                s3 = fma(row[j + 3], v[j + 3], s3);
+            }
+            for (; j < m; ++j) s0 = fma(row[j], v[j], s0);
+            p[i] = (s0 + s1) + (s2 + s3);
+        }
+        __syncthreads();
+        const double beta = sh_beta, alpha = sh_alpha;
+        for (int i = tid; i < m; i += blockDim.x) p[i] = beta * fma(-alpha, A[(b0 + i) * ld + b0], p[i]);
+        if (tid == 0) v[0] = x0 - alpha;
         __syncthreads();
         double pv = 0.0;
         for (int i = tid; i < m; i += blockDim.x) pv += p[i] * v[i];
@@ -241,17 +255,17 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const dou
         __syncthreads();
         for (int t = tid; t < m * m; t += blockDim.x) {
             int i = t / m, j = t % m;
-            A[(b0 + i) * chi + b0 + j] -= v[i] * p[j] + p[i] * v[j];
+            A[(b0 + i) * ld + b0 + j] -= v[i] * p[j] + p[i] * v[j];
         }
         if (tid == 0) {
-            A[b0 * chi + kc] = sh_alpha;
-            A[kc * chi + b0] = sh_alpha;
+            A[b0 * ld + kc] = alpha;
+            A[kc * ld + b0] = alpha;
         }
         __syncthreads();
     }
     for (int i = tid; i < chi; i += blockDim.x) {
-        work[i] = A[i * chi + i];
-        double e = (i + 1 < chi) ? A[(i + 1) * chi + i] : 0.0;
+        work[i] = A[i * ld + i];
+        double e = (i + 1 < chi) ? A[(i + 1) * ld + i] : 0.0;
         work[chi + i] = e * e;
     }
 }
@@ -479,7 +493,7 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
                             double *work, cudaStream_t st)
 {
     if (chi > 160 || !work) return cudaErrorInvalidValue;
-    size_t smem = sizeof(double) * ((size_t)chi * chi + 2 * (size_t)chi);
+    size_t smem = sizeof(double) * ((size_t)chi * (chi | 1) + 2 * (size_t)chi);
     CTM_COUNT_LAUNCH(3);
     tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     cudaError_t e = cudaGetLastError();
@@ -514,5 +528,5 @@ cudaError_t launch_check_finite(long long count, const double *x, int *flag, cud
 
 cudaError_t spectrum_prepare()
 {
-    return cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
 }
