@@ -103,7 +103,9 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
  * Once the context has run a step, a call replays its nsteps steps as one
  * CUDA graph: a one-step graph for nsteps = 1 (captured on the first such call
  * and kept), and one for the last nsteps >= 2 requested (re-captured when that
- * count changes); the work is the same. */
+ * count changes); the work is the same.  Only the context's configured
+ * contraction precision is replayed this way (the adjoint's tracked FP64 steps
+ * on a split-BF16 context run eagerly). */
 int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
 
 /* Sec. II.B: repeat steps until delta < tol (tol <= 0: cfg->tol) or max_steps

@@ -699,7 +699,10 @@ int ctm_step(ctm_ctx *c, int nsteps, double *delta_host)
 {
     if (!c || nsteps < 0) return CTM_EINVAL;
     bool done = false;
-    if (nsteps >= 1 && c->steps_done > 0) {
+    // the captured graphs hold the context's configured contractions; a caller that
+    // switches the mode for a while (the adjoint's tracked FP64 steps) runs eagerly
+    const int cfg_T = (c->cfg.precision == CTM_SPLIT_BF16) ? c->cfg.n_split : 0;
+    if (nsteps >= 1 && c->steps_done > 0 && c->split_T == cfg_T) {
         // steps after the first eager one (whose launches ran the autotuners):
         // replay them as one captured graph (one for a single step, one for the
         // last multi-step count), ordered after the caller's stream
