@@ -8,6 +8,11 @@
  * no blocking, fusion or reordering beyond pairwise contraction of a tensor
  * network.
  *
+ * Threads.  Where a loop nest writes disjoint outputs, its outermost output
+ * loop is shared among OpenMP threads (when built with -fopenmp).  Every output
+ * element is still accumulated by one thread in the loop order written here, so
+ * the results do not depend on the thread count (bit for bit).
+ *
  * Index conventions (all arrays row-major double):
  *   A[s][i][j][k]            site tensor, d x D x D x D                (Fig. 1a)
  *   a[u][v][w], u = i*D + i'  double-layer tensor, D2 = D*D per leg    (Fig. 1b)
@@ -28,6 +33,9 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define IDX3(a, b, c, nb, nc) (((size_t)(a) * (nb) + (b)) * (nc) + (c))
 
@@ -35,6 +43,19 @@ static double *orc_alloc(size_t n)
 {
     double *p = (double *)calloc(n ? n : 1, sizeof(double));
     return p;
+}
+
+/* Number of threads for the parallel loops (<= 0: the OpenMP default); returns
+ * the count now in effect (1 without OpenMP). */
+int orc_set_threads(int nthreads)
+{
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+    return omp_get_max_threads();
+#else
+    (void)nthreads;
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------------------ */
@@ -95,6 +116,7 @@ void orc_double_layer(int d, int D, const double *K, const double *B, double *a)
 void orc_matmul(int m, int k, int n, const double *A, const double *B, double *C)
 {
     memset(C, 0, sizeof(double) * (size_t)m * n);
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < m; ++i)
         for (int p = 0; p < k; ++p) {
             double aip = A[(size_t)i * k + p];
@@ -102,12 +124,14 @@ void orc_matmul(int m, int k, int n, const double *A, const double *B, double *C
         }
 }
 
-/* C[m x n] = A^T B with A stored k x m, B stored k x n                       */
+/* C[m x n] = A^T B with A stored k x m, B stored k x n.  Each C[i][j] sums its
+ * products over p in ascending order.                                        */
 void orc_matmul_tn(int m, int k, int n, const double *A, const double *B, double *C)
 {
     memset(C, 0, sizeof(double) * (size_t)m * n);
-    for (int p = 0; p < k; ++p)
-        for (int i = 0; i < m; ++i) {
+#pragma omp parallel for schedule(static)
+    for (int i = 0; i < m; ++i)
+        for (int p = 0; p < k; ++p) {
             double api = A[(size_t)p * m + i];
             for (int j = 0; j < n; ++j) C[(size_t)i * n + j] += api * B[(size_t)p * n + j];
         }
@@ -126,6 +150,7 @@ void orc_enlarged_corner(int chi, int D2, const double *C, const double *T,
     double *X = orc_alloc((size_t)chi * D2 * D2 * chi);
     double *Y1 = orc_alloc((size_t)chi * chi * D2);
     orc_matmul((int)n, chi, chi, T, C, W);
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < chi; ++a)
         for (int u = 0; u < D2; ++u)
             for (int l = 0; l < D2; ++l)
@@ -135,6 +160,7 @@ void orc_enlarged_corner(int chi, int D2, const double *C, const double *T,
                         s += W[IDX3(a, u, h, D2, chi)] * T[IDX3(b, l, h, D2, chi)];
                     X[(((size_t)a * D2 + u) * D2 + l) * chi + b] = s;
                 }
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < chi; ++a)
         for (int b = 0; b < chi; ++b)
             for (int z = 0; z < D2; ++z) {
@@ -144,6 +170,7 @@ void orc_enlarged_corner(int chi, int D2, const double *C, const double *T,
                         s += X[(((size_t)a * D2 + u) * D2 + l) * chi + b] * aB[IDX3(u, l, z, D2, D2)];
                 Y1[IDX3(a, b, z, chi, D2)] = s;
             }
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < chi; ++a)
         for (int y = 0; y < D2; ++y)
             for (int b = 0; b < chi; ++b)
@@ -256,6 +283,7 @@ double orc_edge_update(int chi, int D2, const double *T, const double *aB, const
     double *H1 = orc_alloc((size_t)chi * D2 * D2 * chi);
     double *H2 = orc_alloc((size_t)chi * chi * D2);
     double *H3 = orc_alloc((size_t)chi * chi * D2 * D2);
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < chi; ++a)
         for (int u = 0; u < D2; ++u)
             for (int w = 0; w < D2; ++w)
@@ -265,6 +293,7 @@ double orc_edge_update(int chi, int D2, const double *T, const double *aB, const
                         s += T[IDX3(a, u, g, D2, chi)] * Q[((size_t)g * D2 + w) * chi + j];
                     H1[(((size_t)a * D2 + u) * D2 + w) * chi + j] = s;
                 }
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < chi; ++a)
         for (int j = 0; j < chi; ++j)
             for (int z = 0; z < D2; ++z) {
@@ -274,6 +303,7 @@ double orc_edge_update(int chi, int D2, const double *T, const double *aB, const
                         s += H1[(((size_t)a * D2 + u) * D2 + w) * chi + j] * aB[IDX3(u, w, z, D2, D2)];
                 H2[IDX3(a, j, z, chi, D2)] = s;
             }
+#pragma omp parallel for schedule(static)
     for (int a = 0; a < chi; ++a)
         for (int j = 0; j < chi; ++j)
             for (int x = 0; x < D2; ++x)
@@ -282,6 +312,7 @@ double orc_edge_update(int chi, int D2, const double *T, const double *aB, const
                     for (int z = 0; z < D2; ++z) s += H2[IDX3(a, j, z, chi, D2)] * aA[IDX3(z, x, y, D2, D2)];
                     H3[(((size_t)a * chi + j) * D2 + x) * D2 + y] = s;
                 }
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < chi; ++i)
         for (int x = 0; x < D2; ++x)
             for (int j = 0; j < chi; ++j) {

@@ -42,10 +42,15 @@ _lib = None
 
 
 def build_oracle(force: bool = False) -> str:
-    """Compile ctm_oracle.c into a shared library next to it (plain gcc, -O2)."""
+    """Compile ctm_oracle.c into a shared library next to it (plain gcc, -O2, OpenMP
+    where the compiler has it; the results do not depend on the thread count)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"])
+        base = ["gcc", "-O2", "-std=c99", "-fPIC", "-shared", _SRC, "-o", tmp, "-lm"]
+        try:
+            subprocess.check_call(base[:1] + ["-fopenmp"] + base[1:], stderr=subprocess.DEVNULL)
+        except subprocess.CalledProcessError:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -59,6 +64,7 @@ def _load():
             P = ctypes.POINTER(ctypes.c_double)
             I = ctypes.c_int
             sig = {
+                "orc_set_threads": (I, [I]),
                 "orc_c3v_project": (None, [I, I, P, P]),
                 "orc_frobenius": (ctypes.c_double, [ctypes.c_long, P]),
                 "orc_double_layer": (None, [I, I, P, P, P]),
@@ -88,6 +94,11 @@ def _p(x: np.ndarray):
 
 def _c(x) -> np.ndarray:
     return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def set_threads(nthreads: int = 0) -> int:
+    """Threads of the oracle's parallel loops (<= 0: all cores); returns the count in effect."""
+    return int(_load().orc_set_threads(int(nthreads)))
 
 
 # --- single steps (each mirrors one row of the hot path) -------------------
