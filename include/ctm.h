@@ -173,6 +173,15 @@ int ctm_get_intermediate(const ctm_ctx *ctx, int which, double *dst_dev, size_t 
  * without its operand pre-pass). */
 int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
 
+/* Failure-detection test hook (no counterpart in the paper).  With enable != 0
+ * the context's next Householder QR runs with a grid barrier that waits for one
+ * arrival more than the grid provides and gives up after a short bounded spin
+ * (about a millisecond): every CTA raises the context's error flag and returns,
+ * and the step reports CTM_ETIMEOUT, exactly as an expired device wait does.
+ * Nothing faults or hangs.  The environment is undefined afterwards; destroy the
+ * context.  enable = 0 restores normal waits.  Synchronous. */
+int ctm_debug_force_timeout(ctm_ctx *ctx, int enable);
+
 /* Number of kernel launches the library has enqueued since it was loaded
  * (host-side count; a replay of a captured graph adds the kernels it holds). */
 unsigned long long ctm_kernel_launches(void);

@@ -82,6 +82,7 @@ def load(path: str = LIB_PATH):
         "ctm_batch_ctx": (I, [P, I, ctypes.POINTER(P)]),
         "ctm_batch_destroy": (None, [P]),
         "ctm_grad": (I, [P, I, I, P, P, ctypes.c_size_t, dp, P]),
+        "ctm_debug_force_timeout": (I, [P, I]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -279,6 +280,11 @@ class CTM:
         out["spectrum"] = ms[7]       # side stream, overlaps the next step in ctm_step
         out["gemm_kernels"] = ms[8]   # the contraction-engine kernels alone (subset of the phases)
         return out
+
+    def ctm_debug_force_timeout(self, enable=True):
+        st = load().ctm_debug_force_timeout(self._h, 1 if enable else 0)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_debug_force_timeout")
 
     def close(self):
         if getattr(self, "_h", None):

@@ -955,6 +955,21 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
 
 unsigned long long ctm_kernel_launches(void) { return g_ctm_launches; }
 
+int ctm_debug_force_timeout(ctm_ctx *c, int enable)
+{
+    if (!c) return CTM_EINVAL;
+    if (join_side(c) != CTM_OK) return CTM_ECUDA;
+    CK(cudaStreamSynchronize(c->stream));
+    c->force_timeout = enable ? 1 : 0;
+    // captured graphs hold the QR's launch arguments: capture again with the new ones
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    c->graph = nullptr;
+    c->graph1 = nullptr;
+    c->graph_steps = 0;
+    return CTM_OK;
+}
+
 size_t ctm_gemm_workspace_bytes(int M, int N, int K, int precision, int n_split)
 {
     if (M <= 0 || N <= 0 || K <= 0) return 0;

@@ -69,6 +69,7 @@ struct ctm_ctx {
     // kernel timing (ctm_step_profiled): events around each contraction launch
     int prof_on, prof_n;
     int qr_rows_min;          // 1 for a lone instance; larger inside a batch
+    int force_timeout;        // ctm_debug_force_timeout: the QR grid barrier waits for an arrival that never comes
     cudaEvent_t prof_ev[64];
     int steps_done;
 };
@@ -90,6 +91,8 @@ inline QrScratch qr_scratch(ctm_ctx *c)
     q.ta = q.W + k * k;
     q.sk = q.ta + 2 * k + k * k;   // (k*k of slack after ta keeps the scratch 8-byte aligned)
     q.sk_elems = qr_sk_doubles((int)n, (int)k);
+    q.bar_extra = c->force_timeout ? 1u : 0u;
+    q.spin_limit = c->force_timeout ? 20000 : 0;
     return q;
 }
 enum {

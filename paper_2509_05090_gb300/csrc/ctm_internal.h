@@ -43,7 +43,6 @@ int gemm_f64_pick_split(int M, int N, int K);
 struct SplitPlan {
     int NT, mTiles, nTiles, kTiles, chunks_per_split, ksplit;
     size_t a_pack_bytes, b_pack_bytes, partial_bytes;
-    int persist;   // one CTA per SM walking the output tiles (NT 48, K <= 256, no K split)
 };
 struct SplitWork {
     unsigned char *Apk, *Bpk;
@@ -55,8 +54,7 @@ struct SplitWork {
     int *err;
     int autotune;      // time the candidate tile shapes / K-splits of a new shape once (eager only)
 };
-// ks_override: > 0 a K split, 0 automatic, -1 (with nt_override 48) the persistent variant
-// when K fits one exact chunk.
+// ks_override: > 0 a K split, 0 automatic.
 SplitPlan split_plan(int M, int N, int K, int T, int nt_override = 0, int ks_override = 0);
 // Operand reuse: reuse_a = the A operand (same pointer and maps) was packed by the
 // previous split call and is unchanged; b_cache = a constant B operand packed once
@@ -96,6 +94,8 @@ struct QrScratch {
     double *ta;        // 2 x k (tau, alpha)
     double *sk;        // split-K scratch of the V^T V product
     size_t sk_elems;
+    unsigned bar_extra;      // arrivals the grid barrier waits for beyond the grid (0; > 0 only to force a timeout)
+    long long spin_limit;    // polls before a barrier wait gives up (0: the default, about a second)
 };
 size_t qr_wy_doubles(int n, int k);   // V + S + W + ta + split-K scratch
 size_t qr_sk_doubles(int n, int k);   // the split-K scratch part

@@ -778,310 +778,6 @@ __global__ void __launch_bounds__(SpCfg<NT>::THREADS, SpCfg<NT>::MIN_BLOCKS) gem
     if (threadIdx.x == 0 && abort_sh) atomicExch(a.err, 2);
 }
 
-// ---------------------------------------------------------------- persistent variant
-// For contractions whose K fits one exact chunk (K <= 256) and that run without a
-// K split -- the four whose output is n x n -- a CTA's life is short and half of
-// it is its epilogue.  This variant keeps one CTA per SM for the whole launch:
-// it walks the output tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... (N tile
-// fastest, so concurrent CTAs share A tiles in L2), with the tile's T level
-// accumulators in one of two TMEM buffers (2 x 256 columns), so the MMAs and
-// copies of tile i+1 run while the twelve epilogue warps drain, convert and
-// store tile i; the staging area has its own shared memory.  Roles, rings and
-// arithmetic are those of gemm_split_kernel with NT = 48.  Every wait is bounded;
-// after an abort the epilogue warps still pass both named barriers of every
-// remaining tile, so no warp is left waiting on another.
-constexpr int PT_NT = 48;
-constexpr int PT_ASLOTS = 6;
-constexpr int PT_EPI_WARPS = 12;   // three per TMEM sub-partition, 16 columns each
-constexpr int PT_EPI_THREADS = 32 * PT_EPI_WARPS;
-constexpr int PT_THREADS = 64 + PT_EPI_THREADS;
-constexpr int PT_PITCH = PT_NT + 1;
-constexpr size_t pt_stage_bytes() { return (size_t)SP_BM * PT_PITCH * 8 + (size_t)(SP_BM + PT_NT) * 12; }
-size_t split_pt_smem_bytes(int T)
-{
-    return 1024 + (size_t)PT_ASLOTS * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * PT_NT * SP_BK * 2 + pt_stage_bytes();
-}
-
-template <int T>
-__global__ void __launch_bounds__(PT_THREADS, 1) gemm_split_pt_kernel(SplitArgs a)
-{
-    constexpr int NT = PT_NT;
-    constexpr int A_TILE = SP_BM * SP_BK * 2;   // 16 KB
-    constexpr int B_TILE = NT * SP_BK * 2;
-    constexpr int QW = NT / (PT_EPI_WARPS / 4);   // 16 columns per epilogue warp
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t bars[PT_ASLOTS * 2 + SP_BSLOTS * 2 + 5];
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
-
-    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *Asm = sm;
-    unsigned char *Bsm = sm + PT_ASLOTS * A_TILE;
-    unsigned char *Ssm = Bsm + SP_BSLOTS * T * B_TILE;   // output staging
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const uint32_t bar0 = smem_u32(bars);
-    auto A_full = [&](int s) { return bar0 + 8u * s; };
-    auto A_empty = [&](int s) { return bar0 + 8u * (PT_ASLOTS + s); };
-    auto B_full = [&](int s) { return bar0 + 8u * (2 * PT_ASLOTS + s); };
-    auto B_empty = [&](int s) { return bar0 + 8u * (2 * PT_ASLOTS + SP_BSLOTS + s); };
-    const uint32_t ACC_FULL0 = bar0 + 8u * (2 * PT_ASLOTS + 2 * SP_BSLOTS);   // + 8 buf
-    const uint32_t ACC_EMPTY0 = ACC_FULL0 + 16u;                              // + 8 buf
-    const uint32_t DRAIN = ACC_FULL0 + 32u;
-    const int tiles = a.mTiles * a.nTiles;
-    volatile int *abort_flag = &abort_sh;
-
-    if (threadIdx.x == 0) {
-        abort_sh = 0;
-        for (int s = 0; s < PT_ASLOTS; ++s) {
-            mbar_init(A_full(s), 1);
-            mbar_init(A_empty(s), 1);
-        }
-        for (int s = 0; s < SP_BSLOTS; ++s) {
-            mbar_init(B_full(s), 1);
-            mbar_init(B_empty(s), 1);
-        }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(ACC_FULL0 + 8u * b, 1);
-            mbar_init(ACC_EMPTY0 + 8u * b, PT_EPI_WARPS);
-        }
-        mbar_init(DRAIN, 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
-                     "r"(512)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = tmem_base_sh;
-
-    if (warp == 0) {
-        // ------------------------------------------------ producers (as in gemm_split_kernel)
-        if (lane == 0) {
-            int b = 0;
-            for (int t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x) {
-                const int nt = t % a.nTiles;
-                for (int kt = 0; kt < a.kTiles; ++kt, ++b) {
-                    const int sb = b % SP_BSLOTS;
-                    if (!mbar_wait(B_empty(sb), ((b / SP_BSLOTS) & 1) ^ 1, abort_flag)) break;
-                    mbar_expect_tx(B_full(sb), (uint32_t)(T * B_TILE));
-                    for (int j = 0; j < T; ++j) {
-                        const unsigned char *src =
-                            a.Bpk + j * a.b_slice_bytes + ((long long)nt * a.kTiles + kt) * B_TILE;
-                        bulk_g2s(smem_u32(Bsm + (sb * T + j) * B_TILE), src, B_TILE, B_full(sb));
-                    }
-                }
-            }
-        } else if (lane == 1) {
-            int u = 0;
-            for (int t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x) {
-                const int mt = t / a.nTiles;
-                for (int kt = 0; kt < a.kTiles && !*abort_flag; ++kt) {
-                    for (int i = 0; i < T; ++i, ++u) {
-                        const int sa = u % PT_ASLOTS;
-                        if (!mbar_wait(A_empty(sa), ((u / PT_ASLOTS) & 1) ^ 1, abort_flag)) break;
-                        mbar_expect_tx(A_full(sa), (uint32_t)A_TILE);
-                        const unsigned char *src =
-                            a.Apk + i * a.a_slice_bytes + ((long long)mt * a.kTiles + kt) * A_TILE;
-                        bulk_g2s(smem_u32(Asm + sa * A_TILE), src, A_TILE, A_full(sa));
-                    }
-                }
-            }
-        }
-    } else if (warp == 1) {
-        // ------------------------------------------------ MMA issuer (one thread)
-        if (lane == 0) {
-            const uint32_t idesc0 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(SP_BM >> 4) << 24);
-            constexpr int G = 256 / NT;
-            const uint64_t ad0 = sdesc_sw128(smem_u32(Asm)), bd0 = sdesc_sw128(smem_u32(Bsm));
-            int u = 0, b = 0, ti = 0;
-            for (int t = blockIdx.x; t < tiles && !*abort_flag; t += gridDim.x, ++ti) {
-                const int buf = ti & 1;
-                if (!mbar_wait(ACC_EMPTY0 + 8u * buf, ((ti >> 1) & 1) ^ 1, abort_flag)) break;
-                tc_fence_after();
-                const uint32_t tm = tmem + (uint32_t)(buf * 256);
-                for (int kt = 0; kt < a.kTiles; ++kt) {
-                    const int sb = b % SP_BSLOTS;
-                    if (!mbar_wait(B_full(sb), (b / SP_BSLOTS) & 1, abort_flag)) break;
-                    tc_fence_after();
-                    const int kvalid = min(SP_BK, a.K - kt * SP_BK);
-                    const int ksteps = (kvalid + 15) / 16;
-                    const uint32_t acc0 = (kt == 0) ? 0u : 1u;
-                    const uint64_t bdb = bd0 + (uint64_t)((sb * T * B_TILE) >> 4);
-#pragma unroll
-                    for (int i = 0; i < T; ++i) {
-                        const int sa = u % PT_ASLOTS;
-                        if (!mbar_wait(A_full(sa), (u / PT_ASLOTS) & 1, abort_flag)) break;
-                        tc_fence_after();
-                        const uint64_t ad = ad0 + (uint64_t)((sa * A_TILE) >> 4);
-#pragma unroll
-                        for (int j0 = 0; j0 < T - i; j0 += G) {
-                            const int nj = (T - i - j0 < G) ? T - i - j0 : G;
-                            const uint32_t idesc = idesc0 | ((uint32_t)((nj * NT) >> 3) << 17);
-                            const uint32_t d = tm + (uint32_t)((i + j0) * NT);
-                            const uint64_t bd = bdb + (uint64_t)((j0 * B_TILE) >> 4);
-                            for (int kk = 0; kk < ksteps; ++kk)
-                                mma_bf16(d, ad + 2ull * kk, bd + 2ull * kk, idesc, (i == 0 && kk == 0) ? acc0 : 1u);
-                        }
-                        mma_commit(A_empty(sa));
-                        ++u;
-                    }
-                    mma_commit(B_empty(sb));
-                    ++b;
-                    if (*abort_flag) break;
-                }
-                mma_commit(ACC_FULL0 + 8u * buf);
-            }
-            mma_commit(DRAIN);
-            {
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try(DRAIN, 0) && global_ns() - t0 < SP_WAIT_NS) {
-                }
-            }
-        }
-    } else {
-        // ------------------------------------------------ epilogue warps 2..13
-        const int sub = warp & 3, part = (warp - 2) >> 2;
-        const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
-        long long *stage = reinterpret_cast<long long *>(Ssm);
-        long long *row_off = stage + SP_BM * PT_PITCH;
-        long long *col_off = row_off + SP_BM;
-        int *row_sc = reinterpret_cast<int *>(col_off + NT);
-        int *col_sc = row_sc + SP_BM;
-        const int ew = warp - 2, et = threadIdx.x - 64;
-        int ti = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++ti) {
-            const int buf = ti & 1;
-            const int nt = t % a.nTiles, mt = t / a.nTiles;
-            long long acc[QW];
-#pragma unroll
-            for (int q = 0; q < QW; ++q) acc[q] = 0;
-            int ok = 0;
-            if (lane == 0) ok = (!*abort_flag && mbar_wait(ACC_FULL0 + 8u * buf, (ti >> 1) & 1, abort_flag)) ? 1 : 0;
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (ok) {
-                tc_fence_after();
-                for (int lv = 0; lv < T; ++lv) {
-                    const int sh = 8 * (T - 1 - lv);
-                    uint32_t r[QW];
-                    const uint32_t col = (uint32_t)(buf * 256 + lv * NT + part * QW);
-                    tmem_ld8(tmem + lane_base + col, r);
-                    tmem_ld8(tmem + lane_base + col + 8, r + 8);
-                    tmem_wait_ld();
-#pragma unroll
-                    for (int q = 0; q < QW; ++q) acc[q] += (long long)__float2int_rn(__uint_as_float(r[q])) << sh;
-                }
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(ACC_EMPTY0 + 8u * buf);
-            }
-            // every epilogue warp reaches both barriers of every tile, aborted or not
-            asm volatile("bar.sync 1, %0;" ::"n"(PT_EPI_THREADS) : "memory");   // previous tile written out
-            const int m0 = mt * SP_BM, n0 = nt * NT;
-            const int rows = min(SP_BM, a.M - m0), cols = min(NT, a.N - n0);
-            if (!*abort_flag) {
-                const int r = 32 * sub + lane;
-                const int m = m0 + r;
-                if (m < a.M) {
-                    if (part == 0) {
-                        row_off[r] = off2(a.Cm, m);
-                        row_sc[r] = exp_of_word(__ldg(a.eA + m)) - 14 - 8 * (T - 1);
-                    }
-#pragma unroll
-                    for (int q = 0; q < QW; ++q) {
-                        const int c = part * QW + q;
-                        if (n0 + c < a.N) stage[r * PT_PITCH + c] = acc[q];
-                    }
-                }
-                for (int c = et; c < cols; c += PT_EPI_THREADS) {
-                    col_off[c] = off2(a.Cn, n0 + c);
-                    col_sc[c] = exp_of_word(__ldg(a.eB + n0 + c));
-                }
-            }
-            asm volatile("bar.sync 1, %0;" ::"n"(PT_EPI_THREADS) : "memory");   // tile staged
-            if (!*abort_flag) {
-                constexpr int WU = 4;
-                const bool along_n = a.Cn.s2 == 1 || a.Cm.s2 != 1;
-                if (along_n) {
-                    constexpr int NCH = (NT + 31) / 32;
-                    long long co[NCH];
-                    int cs[NCH];
-#pragma unroll
-                    for (int j = 0; j < NCH; ++j) {
-                        const bool in = lane + 32 * j < cols;
-                        co[j] = in ? col_off[lane + 32 * j] : 0;
-                        cs[j] = in ? col_sc[lane + 32 * j] : 0;
-                    }
-                    for (int rb = ew; rb < rows; rb += WU * PT_EPI_WARPS) {
-                        long long ro[WU], v[WU][NCH];
-                        int rsc[WU];
-#pragma unroll
-                        for (int w = 0; w < WU; ++w) {
-                            const int r = rb + w * PT_EPI_WARPS;
-                            ro[w] = r < rows ? row_off[r] : 0;
-                            rsc[w] = r < rows ? row_sc[r] : 0;
-#pragma unroll
-                            for (int j = 0; j < NCH; ++j)
-                                v[w][j] = (r < rows && lane + 32 * j < cols) ? stage[r * PT_PITCH + lane + 32 * j] : 0;
-                        }
-#pragma unroll
-                        for (int w = 0; w < WU; ++w) {
-                            if (rb + w * PT_EPI_WARPS >= rows) break;
-#pragma unroll
-                            for (int j = 0; j < NCH; ++j)
-                                if (lane + 32 * j < cols) a.C[ro[w] + co[j]] = scaled_int_to_double(v[w][j], rsc[w] + cs[j]);
-                        }
-                    }
-                } else {
-                    constexpr int NRC = SP_BM / 32;
-                    long long ro[NRC];
-                    int rsc[NRC];
-#pragma unroll
-                    for (int j = 0; j < NRC; ++j) {
-                        const bool in = lane + 32 * j < rows;
-                        ro[j] = in ? row_off[lane + 32 * j] : 0;
-                        rsc[j] = in ? row_sc[lane + 32 * j] : 0;
-                    }
-                    for (int cb = ew; cb < cols; cb += WU * PT_EPI_WARPS) {
-                        long long co[WU], v[WU][NRC];
-                        int cs[WU];
-#pragma unroll
-                        for (int w = 0; w < WU; ++w) {
-                            const int c = cb + w * PT_EPI_WARPS;
-                            co[w] = c < cols ? col_off[c] : 0;
-                            cs[w] = c < cols ? col_sc[c] : 0;
-#pragma unroll
-                            for (int j = 0; j < NRC; ++j)
-                                v[w][j] = (c < cols && lane + 32 * j < rows) ? stage[(lane + 32 * j) * PT_PITCH + c] : 0;
-                        }
-#pragma unroll
-                        for (int w = 0; w < WU; ++w) {
-                            if (cb + w * PT_EPI_WARPS >= cols) break;
-#pragma unroll
-                            for (int j = 0; j < NRC; ++j)
-                                if (lane + 32 * j < rows) a.C[ro[j] + co[w]] = scaled_int_to_double(v[w][j], rsc[j] + cs[w]);
-                        }
-                    }
-                }
-            }
-        }
-    }
-    tc_fence_before();
-    __syncthreads();
-    if (abort_sh && threadIdx.x == 0)
-        for (int i = 0; i < 2000; ++i) __nanosleep(100);   // let bulk copies still in flight land
-    __syncthreads();
-    if (warp == 0) {
-        __syncwarp();
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
-    }
-    if (threadIdx.x == 0 && abort_sh) atomicExch(a.err, 2);
-}
-
 __global__ void split_finalize_kernel(int M, int N, int T, const unsigned long long *partial, const int *eA,
                                       const int *eB, double *C, Idx2 Cm, Idx2 Cn)
 {
@@ -1130,7 +826,6 @@ SplitPlan split_plan(int M, int N, int K, int T, int nt_override, int ks_overrid
     const long long tiles = (long long)p.mTiles * p.nTiles;
     int ks = 1;
     const int sms = device_sm_count();
-    if (ks_override == -1 && p.NT == PT_NT && chunks == 1) p.persist = 1;
     if (ks_override > 0) {
         ks = ks_override;
     } else if (tiles < sms && chunks > 1) {
@@ -1180,11 +875,6 @@ cudaError_t split_prepare()
     if (e == cudaSuccess) e = split_attr<48, 3>();
     if (e == cudaSuccess) e = split_attr<48, 4>();
     if (e == cudaSuccess) e = split_attr<48, 5>();
-    for (int t = 2; t <= 5 && e == cudaSuccess; ++t) {
-        auto *k = t == 2 ? gemm_split_pt_kernel<2> : t == 3 ? gemm_split_pt_kernel<3>
-                                                            : t == 4 ? gemm_split_pt_kernel<4> : gemm_split_pt_kernel<5>;
-        e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)split_pt_smem_bytes(t));
-    }
     return e;
 }
 
@@ -1429,17 +1119,6 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
     dim3 grid(p.nTiles, p.mTiles, p.ksplit);
     CTM_COUNT_LAUNCH(1);
     if (ev) cudaEventRecord(ev[0], st);
-    if (p.persist) {
-        const int tiles = p.mTiles * p.nTiles, sms = device_sm_count();
-        const dim3 pgrid(tiles < sms ? tiles : sms);
-        if (T == 2) gemm_split_pt_kernel<2><<<pgrid, PT_THREADS, split_pt_smem_bytes(2), st>>>(a);
-        if (T == 3) gemm_split_pt_kernel<3><<<pgrid, PT_THREADS, split_pt_smem_bytes(3), st>>>(a);
-        if (T == 4) gemm_split_pt_kernel<4><<<pgrid, PT_THREADS, split_pt_smem_bytes(4), st>>>(a);
-        if (T == 5) gemm_split_pt_kernel<5><<<pgrid, PT_THREADS, split_pt_smem_bytes(5), st>>>(a);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
-        if (ev) cudaEventRecord(ev[1], st);
-        return cudaSuccess;
-    }
 #define CTM_SPLIT_LAUNCH(nt, t) \
     if (p.NT == nt && T == t)                                                                               \
         gemm_split_kernel<nt, t><<<grid, SpCfg<nt>::THREADS, split_smem_bytes<nt>(t), st>>>(a);
@@ -1518,11 +1197,6 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
         if ((nt == 96 && T * 96 > 512) || (nt == 48 && T * 48 > 256)) continue;
         // auto, none, 2x, 1/2x, and the most splits that still fit one wave of CTAs
         const int one_wave = (int)(device_sm_count() / ((long long)base.mTiles * ((g.N + nt - 1) / nt)));
-        // (the persistent variant, K split -1, is not a candidate: timed alone it wins on
-        // the K <= 256 shapes, but it holds every SM with statically assigned tiles, and
-        // inside the step the concurrent corner update and corner spectrum then delay
-        // its CTAs -- 1054 against 1086 steps/s at D = 6, chi = 72; a plan cache can
-        // still select it)
         for (int ks : {base.ksplit, 1, 2 * base.ksplit, base.ksplit / 2, one_wave}) {
             if (ks < 1 || ks > chunks) continue;
             std::pair<int, int> c{nt, ks};

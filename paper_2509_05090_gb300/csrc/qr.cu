@@ -32,7 +32,10 @@
 //
 // The grid barrier is one monotonic counter in global memory; its spin is
 // bounded (about a second) and on expiry sets an error flag that the host
-// reports as CTM_ETIMEOUT instead of hanging.
+// reports as CTM_ETIMEOUT instead of hanging.  A context's forced-timeout switch
+// (a test of that path) makes the barrier wait for one arrival more than the grid
+// has, with a short spin limit; every CTA then gives up at its first barrier and
+// returns.
 #include <cooperative_groups.h>
 
 #include "ctm_internal.h"
@@ -48,18 +51,19 @@ constexpr long long QR_SPIN_LIMIT = 20000000LL;   // x ~64 ns sleep: ~1.3 s
 // counter with a release reduction (no value returned) and polls the counter
 // with acquire loads until it reaches G * epoch.  No reset, no separate flag;
 // the poll is bounded.
-__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned G, unsigned epoch, int *err)
+__device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned G, unsigned epoch, int *err, unsigned extra,
+                                             long long spin_limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
         asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(count) : "memory");
-        const unsigned target = G * epoch;
+        const unsigned target = G * epoch + extra;
         long long it = 0;
         unsigned f;
         for (;;) {
             asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(f) : "l"(count) : "memory");
             if ((int)(f - target) >= 0) break;
-            if (++it > QR_SPIN_LIMIT) {
+            if (++it > spin_limit) {
                 atomicExch(err, 1);
                 break;
             }
@@ -80,6 +84,8 @@ struct QrArgs {
     double *rowbuf;   // 2 x QB x k published panel rows
     unsigned *bar;
     int *err;
+    unsigned bar_extra;
+    long long spin_limit;
 };
 
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
@@ -189,7 +195,7 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     while (j0 < k) {
         const double *acc = acc_buf(blk);
         const double *pub = pub_buf(blk);
-        if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 1), a.err)) return;
+        if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 1), a.err, a.bar_extra, a.spin_limit)) return;
         for (int t = tid; t < nn0 * (k - j0); t += blockDim.x) {
             const int i = t / (k - j0), kk = j0 + t % (k - j0);
             Gs[i * k + kk] = (kk >= j0 + i) ? ((volatile const double *)acc)[i * k + kk] : 0.0;
@@ -474,7 +480,8 @@ static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y,
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return e;
-    QrArgs a{n, k, G, rows_per, Y, R, s.V, s.ta, s.sbuf, s.rowbuf, s.bar, s.err};
+    QrArgs a{n, k, G, rows_per, Y, R, s.V, s.ta, s.sbuf, s.rowbuf, s.bar, s.err, s.bar_extra,
+             s.spin_limit > 0 ? s.spin_limit : QR_SPIN_LIMIT};
     void *args[] = {&a};
     CTM_COUNT_LAUNCH(1);
     return cudaLaunchCooperativeKernel((void *)qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st);
@@ -491,7 +498,7 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
 {
     int G, rp0;
     qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp0);
-    if (s.rows_min > 1) return rp0;
+    if (s.rows_min > 1 || s.bar_extra) return rp0;
     {
         std::lock_guard<std::mutex> lk(g_qr_mu);
         auto it = g_qr_rows.find({n, k});

@@ -21,6 +21,7 @@ import numpy as np
 __all__ = [
     "random_site_tensor",
     "product_site_tensor",
+    "perturbed_product_site_tensor",
     "ising_site_tensor",
     "spin_matrices",
     "bond_hamiltonians",
@@ -45,6 +46,23 @@ def product_site_tensor(v) -> np.ndarray:
     """D = 1 site tensor A[s, 0, 0, 0] = v[s] (a product state |v> on every site)."""
     v = np.asarray(v, dtype=np.float64)
     return v.reshape(-1, 1, 1, 1).copy()
+
+
+def perturbed_product_site_tensor(v, D: int, eps: float, seed: int) -> np.ndarray:
+    """Product state |v> on every site plus a small seeded perturbation.
+
+    A[s, i, j, k] = v[s] delta_{i0} delta_{j0} delta_{k0} + eps * U[s, i, j, k] with U
+    uniform in [-1, 1] from ``default_rng(seed)``.  Its correlations are short, so
+    the corner spectrum falls off fast: at D = 6 the 72nd unit-norm
+    corner singular value is ~1e-12 at eps = 0.002, and a chi = 72 environment
+    converges to delta < 1e-10 in a few steps (a random tensor at D = 6 has no spectral gap at
+    chi = 72 and does not converge).  Not projected or normalised here.
+    """
+    v = np.asarray(v, dtype=np.float64)
+    rng = np.random.default_rng(seed)
+    A = eps * rng.uniform(-1.0, 1.0, size=(v.size, D, D, D))
+    A[:, 0, 0, 0] += v
+    return A
 
 
 def ising_site_tensor(beta: float) -> np.ndarray:
@@ -119,6 +137,7 @@ class Workload:
     tol: float = 1e-10
     precision: str = "fp64"
     note: str = ""
+    eps: float = 0.0          # > 0: perturbed product state (perturbed_product_site_tensor)
 
     @property
     def D2(self) -> int:
@@ -129,6 +148,9 @@ class Workload:
         return self.chi * self.D * self.D
 
     def site_tensor(self) -> np.ndarray:
+        if self.eps > 0.0:
+            return perturbed_product_site_tensor(_PRODUCT_V[:self.d] / np.linalg.norm(_PRODUCT_V[:self.d]),
+                                                 self.D, self.eps, self.seed)
         return random_site_tensor(self.d, self.D, self.seed)
 
     def hamiltonians(self) -> np.ndarray:
@@ -136,10 +158,12 @@ class Workload:
 
 
 _PHI = 0.3 * math.pi
+_PRODUCT_V = np.array([0.8, 0.6, 0.0])
 
-# The five workloads: Heisenberg D=2/chi=8 (oracle-sized), Kitaev D=4/chi=32,
-# Kitaev-Heisenberg D=6/chi=72 and D=8/chi=128 (phi = 0.3 pi), and a 96-instance
-# ragged batch.  Seeds are 1000 + index (5000 + i for the batch instances).
+# The workloads: Heisenberg D=2/chi=8 (oracle-sized), Kitaev D=4/chi=32,
+# Kitaev-Heisenberg D=6/chi=72 and D=8/chi=128 (phi = 0.3 pi), their converging
+# near-product counterparts, and a 96-instance ragged batch.  Seeds are
+# 1000 + index (5000 + i for the batch instances).
 WORKLOADS = {
     "heis_D2_chi8": Workload("heis_D2_chi8", 2, 2, 8, 0.0, 1.0, 1000, 50,
                              note="Heisenberg J=1, 50 steps or delta<1e-10"),
@@ -149,6 +173,16 @@ WORKLOADS = {
                             note="Kitaev-Heisenberg phi=0.3pi, enlarged corner 2592x2592"),
     "kh_D8_chi128": Workload("kh_D8_chi128", 2, 8, 128, math.cos(_PHI), math.sin(_PHI), 1003, 30,
                              note="Kitaev-Heisenberg phi=0.3pi, enlarged corner 8192x8192"),
+    # converging stand-ins at the same sizes: product state (0.8, 0.6) plus a small
+    # seeded perturbation (short correlations, fast-falling corner spectrum)
+    "kitaev_D4_chi32_conv": Workload("kitaev_D4_chi32_conv", 2, 4, 32, 1.0, 0.0, 1004, 200, eps=0.005,
+                                     note="isotropic Kitaev K=1, near-product state, converges to 1e-10"),
+    "kh_D6_chi72_conv": Workload("kh_D6_chi72_conv", 2, 6, 72, math.cos(_PHI), math.sin(_PHI), 1005, 200,
+                                 eps=0.002,
+                                 note="Kitaev-Heisenberg phi=0.3pi, near-product state, converges to 1e-10"),
+    "kh_D8_chi128_conv": Workload("kh_D8_chi128_conv", 2, 8, 128, math.cos(_PHI), math.sin(_PHI), 1006, 200,
+                                  eps=0.002,
+                                  note="Kitaev-Heisenberg phi=0.3pi, near-product state, D=8, chi=128"),
 }
 
 

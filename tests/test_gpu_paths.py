@@ -51,17 +51,13 @@ _CHILD = textwrap.dedent("""
 
 
 def _plan_line(M, N, K, nt):
-    # "pt": the persistent variant (N tile 48, K split -1) wherever K fits one 256-wide chunk
-    if nt == "pt":
-        return f"split {M} {N} {K} 5 : 48 {-1 if K <= 256 else 1}\n"
     return f"split {M} {N} {K} 5 : {nt} 1\n"
 
 
 @pytest.mark.parametrize("wl,nt", [("kitaev_D4_chi32", 48), ("kitaev_D4_chi32", 64), ("kitaev_D4_chi32", 96),
-                                   ("kitaev_D4_chi32", "pt"), ("kh_D6_chi72", "pt")])
+                                   ("kh_D6_chi72", 48)])
 def test_split_step_each_tile_width(ctm_lib, tmp_path, wl, nt):
-    """One split step with every contraction forced onto one plan family.  At D = 6, chi = 72 the
-    persistent variant walks more output tiles than there are SMs (double-buffered accumulators)."""
+    """One split step with every contraction forced onto one plan family."""
     w = I.WORKLOADS[wl]
     A = w.site_tensor()
     ref = O.OracleCTM(A, w.chi)
@@ -115,3 +111,30 @@ def test_qr_panel_restart_on_nearly_parallel_columns(ctm_lib):
     assert np.max(np.abs(Qn.T @ Qn - np.eye(w.chi))) <= 1e-12
     assert np.max(np.abs(Qn @ R - _np(g.ctm_get_intermediate("Y")))) <= 1e-12 * np.max(np.abs(Y))
     g.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_forced_wait_timeout_is_reported(ctm_lib, precision):
+    """Failure detection without a fault: the context's forced-timeout switch makes the
+    QR grid barrier wait for an arrival that never comes; the bounded wait gives up,
+    the step returns CTM_ETIMEOUT, the context can be destroyed, and a fresh context
+    on the same device then steps like the oracle."""
+    from paper_2509_05090_gb300 import binding
+    w = I.WORKLOADS["heis_D2_chi8"]
+    A = w.site_tensor()
+    g = binding.CTM(A, w.chi, precision=precision, n_split=5)
+    g.ctm_step(2)                      # eager first step, then a captured one
+    g.ctm_debug_force_timeout(True)
+    with pytest.raises(binding.CtmError) as ei:
+        g.ctm_step(1)
+    assert ei.value.status == 6        # CTM_ETIMEOUT
+    g.close()
+    ref = O.OracleCTM(A, w.chi)
+    g2 = binding.CTM(A, w.chi, precision=precision, n_split=5)
+    for _ in range(5):
+        dr = ref.step()
+        dg = g2.ctm_step(1)
+        assert abs(dg - dr) <= 1e-8 * max(1.0, abs(dr))
+    C, T, Q = (_np(x) for x in g2.ctm_get_env())
+    assert _rel(C, ref.C) <= 1e-8
+    g2.close()

@@ -115,6 +115,92 @@ def test_split_step_matches_oracle_d6_chi72(ctm_lib):
     g.close()
 
 
+def test_split_step_outputs_match_oracle_d6_chi72(ctm_lib):
+    """M, Y, Q, R, C' and T' of one split-BF16 step (T = 5) at the benchmark size,
+    element by element against the oracle's step from the same environment (the oracle
+    after one step).  Tolerances (split_bounds): M and Y within the engine's truncation
+    bound carried through their contraction chains; Q and R within the first-order QR
+    perturbation bound of the measured Y difference plus the FP64 Householder backward
+    error; C' and T' within their first-order bounds from the measured M difference,
+    the Q bound and their own chains' truncation.  A factor 2 covers second-order
+    terms.  The step has full column rank here (lead = chi)."""
+    from split_bounds import corner_bound, edge_bound, enlarged_corner_err, gemm_err, qr_bounds
+    w = I.WORKLOADS["kh_D6_chi72"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)
+    ref.step()
+    g = _ctm(A, w.chi, precision="split_bf16", n_split=5)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    C0, T0, Qs = ref.C.copy(), ref.T.copy(), ref.warm_start()
+    ref.step()
+    g.ctm_step(1)
+    last = ref.last
+    dRd = np.abs(np.diag(last["R"]))
+    lead = int(np.sum(dRd / dRd[0] >= 1e-8))
+    assert lead == w.chi
+    eM = enlarged_corner_err(C0, T0, ref.a, 5)
+    M = _np(g.ctm_get_intermediate("M"))
+    assert np.all(np.abs(M - last["M"]) <= 2.0 * eM)
+    eY = gemm_err(last["M"], Qs, 5, eA=eM)
+    Y = _np(g.ctm_get_intermediate("Y"))
+    assert np.all(np.abs(Y - last["Y"]) <= 2.0 * eY)
+    dQ, dR = qr_bounds(float(np.linalg.norm(Y - last["Y"])), last["Y"], last["R"], lead)
+    R = _np(g.ctm_get_intermediate("R"))
+    assert np.all(np.diag(R) >= 0.0) and np.all(np.tril(R, -1) == 0.0)
+    assert np.linalg.norm(R - last["R"]) <= 2.0 * dR
+    C, T, Q = (_np(x) for x in g.ctm_get_env())
+    assert np.linalg.norm(Q - last["Q"]) <= 2.0 * dQ
+    dC = corner_bound(last["M"], last["Q"], float(np.linalg.norm(M - last["M"])), 2.0 * dQ, 5)
+    assert np.linalg.norm(C - last["C"]) <= 2.0 * dC
+    dT = edge_bound(T0, ref.a, last["Q"], 2.0 * dQ, 5)
+    assert np.linalg.norm(T - last["T"]) <= 2.0 * dT
+    # the bounds are not vacuous: far below the entries they bound (the truncation
+    # terms are worst-case, K max|A| max|B|, so the C' and T' bounds are the loosest)
+    for bound, x in ((2.0 * dQ, last["Q"]), (2.0 * dC, last["C"]), (2.0 * dT, last["T"])):
+        assert bound < 1e-4 * np.max(np.abs(x))
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("split_bf16", 1e-9), ("fp64", 1e-12)])
+def test_energy_after_steps_matches_oracle_d6_chi72(ctm_lib, prec, tol):
+    """Benchmark workload: three steps from the initial environment on each side, then
+    the bond energies; split (T = 5) within 1e-9 of the FP64 oracle, FP64 within 1e-12."""
+    w = I.WORKLOADS["kh_D6_chi72"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    O.set_threads(0)
+    ref = O.OracleCTM(A, w.chi)
+    for _ in range(3):
+        ref.step()
+    e_ref, E_ref = ref.energy(h)
+    g = _ctm(A, w.chi, precision=prec, n_split=5)
+    g.ctm_step(3)
+    e, E, rho = g.ctm_energy(h)
+    assert abs(E - E_ref) <= tol
+    assert np.max(np.abs(e - e_ref)) <= tol
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("split_bf16", 1e-9), ("fp64", 1e-12)])
+def test_converged_energy_matches_oracle_d6_chi72(ctm_lib, prec, tol):
+    """Converging workload at the benchmark size (near-product state, D = 6, chi = 72):
+    both sides iterate to delta < 1e-10, then the energies agree within 1e-9 (split) /
+    1e-12 (FP64) -- the mixed-vs-FP64 energy criterion against the oracle itself."""
+    w = I.WORKLOADS["kh_D6_chi72_conv"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    O.set_threads(0)
+    ref = O.OracleCTM(A, w.chi)
+    rsteps, rdelta = ref.converge(w.steps, w.tol)
+    assert rdelta < w.tol
+    e_ref, E_ref = ref.energy(h)
+    g = _ctm(A, w.chi, precision=prec, n_split=5)
+    steps, delta, ok = g.ctm_converge(max_steps=w.steps, tol=w.tol, check_every=1)
+    assert ok and abs(steps - rsteps) <= 2
+    e, E, rho = g.ctm_energy(h)
+    assert abs(E - E_ref) <= tol
+    assert np.max(np.abs(e - e_ref)) <= tol
+    g.close()
+
+
 def test_split_energy_error_below_1e9(ctm_lib):
     """Mixed precision (T = 5 slices) reaches the FP64 oracle's converged energy within 1e-9."""
     w = I.WORKLOADS["heis_D2_chi8"]
