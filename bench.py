@@ -43,11 +43,6 @@ def _peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
 
 
-def fp64_peak_tflops(peaks):
-    # FP64 has no measured figure: measured BF16 burst x nominal FP64/BF16 ratio (1.25 / 2250 TFLOP/s)
-    return peaks["bf16_tflops"] * 1.25 / 2250.0
-
-
 def step_gemm_flops(chi, D2):
     """Algorithmic FP64 flops of the GEMM phases of one step (2 x MACs)."""
     n = chi * D2
@@ -68,19 +63,67 @@ def step_gemm_flops(chi, D2):
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle-reason samples while the timed region runs."""
+    """SM clock and clock-event (throttle) reasons sampled about every millisecond while
+    the timed region runs, read through NVML (the driver's libnvidia-ml, via ctypes);
+    nvidia-smi polling (100 ms) if NVML cannot be opened."""
 
+    # NVML clock-event reason bits
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+               0x80: "hw_power_brake_slowdown"}
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
+        self.samples = []      # (sm_mhz, reason bits)
+        self.max_mhz = None
+        self.source = None
+        self._stop = threading.Event()
         self.proc = None
         self.lines = []
 
+    def _nvml_handle(self):
+        import ctypes
+        lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        h = ctypes.c_void_p()
+        uuid = None
+        try:
+            import torch
+            uuid = "GPU-" + str(torch.cuda.get_device_properties(self.gpu).uuid)
+        except Exception:
+            uuid = None
+        if not uuid or lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(h)) != 0:
+            if lib.nvmlDeviceGetHandleByIndex_v2(ctypes.c_uint(self.gpu), ctypes.byref(h)) != 0:
+                raise RuntimeError("no NVML handle")
+        reasons = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            getattr(lib, "nvmlDeviceGetCurrentClocksThrottleReasons")
+        return lib, h, reasons
+
+    def _nvml_loop(self, lib, h, reasons):
+        import ctypes
+        mhz, mx, bits = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        if lib.nvmlDeviceGetMaxClockInfo(h, 1, ctypes.byref(mx)) == 0:
+            self.max_mhz = float(mx.value)
+        while not self._stop.is_set():
+            if lib.nvmlDeviceGetClockInfo(h, 1, ctypes.byref(mhz)) == 0 and reasons(h, ctypes.byref(bits)) == 0:
+                self.samples.append((float(mhz.value), int(bits.value)))
+            time.sleep(0.0005)
+
     def __enter__(self):
         try:
+            lib, h, reasons = self._nvml_handle()
+            self.source = "nvml ~1 ms"
+            self.t = threading.Thread(target=self._nvml_loop, args=(lib, h, reasons), daemon=True)
+            self.t.start()
+            time.sleep(0.003)   # first samples before the timed work starts
+            return self
+        except Exception:
+            pass
+        try:
+            self.source = "nvidia-smi 100 ms"
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
@@ -95,15 +138,25 @@ class ClockSampler:
             self.lines.append(ln.strip())
 
     def __exit__(self, *a):
+        self._stop.set()
         if self.proc:
             self.proc.terminate()
             try:
                 self.proc.wait(timeout=5)
             except Exception:
                 self.proc.kill()
+        elif getattr(self, "t", None):
+            self.t.join(timeout=2)
 
     def summary(self):
         sm, mx, reasons = [], [], set()
+        if self.samples:
+            for mhz, bits in self.samples:
+                sm.append(mhz)
+                for b, nm in self.REASONS.items():
+                    if bits & b:
+                        reasons.add(nm)
+            mx = [self.max_mhz] if self.max_mhz else [max(sm)]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for ln in self.lines:
             p = [x.strip() for x in ln.split(",")]
@@ -120,7 +173,7 @@ class ClockSampler:
         if not sm:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "source": self.source}
 
 
 def dist_setup():
@@ -130,9 +183,12 @@ def dist_setup():
     return ws, rank, local
 
 
-def cpu_oracle_rate(w, budget_s=20.0, max_steps=None):
-    """The FP64 CPU oracle as it stands, single thread, on bounded steps of the workload."""
+def cpu_oracle_rate(w, budget_s=20.0, max_steps=None, threads=1):
+    """The FP64 CPU oracle as it stands on bounded steps of the workload; threads = 0: all
+    cores (its loops are OpenMP-parallel over output rows).  Returns (steps/s, steps,
+    seconds, init seconds, threads used)."""
     from oracle import oracle as orc
+    used = orc.set_threads(threads if threads > 0 else (os.cpu_count() or 1))
     A = w.site_tensor()
     t0 = time.perf_counter()
     ctm = orc.OracleCTM(A, w.chi)
@@ -144,7 +200,7 @@ def cpu_oracle_rate(w, budget_s=20.0, max_steps=None):
         times.append(time.perf_counter() - t)
         if sum(times) >= budget_s or (max_steps and len(times) >= max_steps):
             break
-    return len(times) / sum(times), len(times), sum(times), init_s
+    return len(times) / sum(times), len(times), sum(times), init_s, used
 
 
 def run_reference(args, w):
@@ -152,38 +208,88 @@ def run_reference(args, w):
     if rank != 0:
         return 0
     budget = min(150.0, max(10.0, 8.0 * args.steps))
-    rate, nsteps, secs, _ = cpu_oracle_rate(w, budget_s=budget, max_steps=args.steps + args.warmup)
+    rate, nsteps, secs, _, used = cpu_oracle_rate(w, budget_s=budget, max_steps=args.steps + args.warmup, threads=0)
     line = {
         "metric": METRIC, "value": rate, "unit": "steps/s", "n_gpus": args.gpus, "steps": nsteps,
         "warmup": 0, "ms_per_step": 1e3 / rate, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": w.name, "d": w.d, "D": w.D, "chi": w.chi, "n": w.n, "precision": "fp64"},
         "impl": "reference",
-        "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": rate, "unit": "steps/s", "cores": used, "host_cores": os.cpu_count(),
+                         "kind": "oracle",
                          "sample": f"{nsteps} plain-C FP64 oracle steps of {w.name} from the initial environment "
-                                   f"({secs:.1f} s, single thread)"},
+                                   f"({secs:.1f} s, {used} OpenMP threads)"},
         "e2e": {"value": rate, "unit": "steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def run_batch(args):
+def batch_record(args, steps):
     """96 independent Kitaev-Heisenberg instances (phi = 2 pi i / 96, D in 3..6, chi in 24..72):
-    aggregate steps/s of the batch (one graph launch per batched step, split-BF16 contractions
-    with autotuned tiles) against one-instance-at-a-time FP64 launches."""
-    import numpy as np
+    aggregate instance-steps/s of the batch (one graph launch per batched step, split-BF16
+    contractions with autotuned tiles) against one-instance-at-a-time FP64 launches."""
     import torch
     from paper_2509_05090_gb300 import binding, inputs
+    wl = inputs.batch_workload()
+    tensors = [w.site_tensor() for w in wl]
+    chis = [w.chi for w in wl]
+    t_init = time.perf_counter()
+    batch = binding.CTMBatch(tensors, chis, precision=args.precision, n_split=args.n_split)
+    l_warm = binding.ctm_kernel_launches()
+    batch.ctm_batch_step(2)   # eager (autotuning) step + capture: each enqueues one batched step
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t_init
+    kernels_per_step = (binding.ctm_kernel_launches() - l_warm) // 2
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(batch.stream)
+        batch.ctm_batch_step(steps)
+        e1.record(batch.stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    value = len(wl) * steps / (ms / 1e3)
+    flops = sum(step_gemm_flops(w.chi, w.D2) for w in wl)
+    T = args.n_split
+    pairs = T * (T + 1) // 2 if args.precision != "fp64" else 1
+    peaks, src = _peaks()
+    achieved = pairs * flops / (ms / steps / 1e3) / 1e12
+    rec = {"value": value, "unit": "instance-steps/s", "instances": len(wl), "steps": steps,
+           "ms_per_batched_step": ms / steps, "setup_s": setup_s,
+           "kernels_per_batched_step": int(kernels_per_step),
+           "launch": "one CUDA graph launch per batched step",
+           "tensor_frac_of_bf16_burst": achieved / peaks["bf16_tflops"] if args.precision != "fp64" else None,
+           "clocks": clk.summary()}
+    batch.close()
+    # baseline: the same instances in FP64, one instance at a time (its own launches, no batching)
+    base_ms = 0.0
+    for A, chi in zip(tensors, chis):
+        c = binding.CTM(A, chi, precision="fp64")
+        c.ctm_step(1, want_delta=False)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(c.stream)
+        for _ in range(steps):   # one launch sequence per instance and step
+            c.ctm_step(1, want_delta=False)
+        b1.record(c.stream)
+        torch.cuda.synchronize()
+        base_ms += b0.elapsed_time(b1)
+        c.close()
+    rec["fp64_one_instance_at_a_time"] = {"value": len(wl) * steps / (base_ms / 1e3), "unit": "instance-steps/s"}
+    return rec
+
+
+def run_batch(args):
+    """The ragged batch as the benchmark's own workload (--workload batch96)."""
+    import torch
+    from paper_2509_05090_gb300 import inputs
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         if rank != 0:
             return 0
         wl = inputs.batch_workload()
-        rates = []
         t_tot, n_tot = 0.0, 0
         for w in wl[:: max(1, len(wl) // 4)]:
-            r, n, secs, _ = cpu_oracle_rate(w, budget_s=8.0, max_steps=2)
+            r, n, secs, _, used = cpu_oracle_rate(w, budget_s=8.0, max_steps=2, threads=0)
             t_tot += secs
             n_tot += n
         rate = n_tot / t_tot
@@ -191,68 +297,103 @@ def run_batch(args):
                           "n_gpus": args.gpus, "steps": n_tot, "warmup": 0, "ms_per_step": 1e3 / rate,
                           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                           "data": "synthetic", "config": {"workload": "batch96"}, "impl": "reference",
-                          "cpu_baseline": {"value": rate, "unit": "instance-steps/s", "cores": 1, "kind": "oracle",
+                          "cpu_baseline": {"value": rate, "unit": "instance-steps/s", "cores": used, "kind": "oracle",
                                            "sample": f"{n_tot} oracle steps on 4 of the 96 instances"},
                           "e2e": {"value": rate, "unit": "instance-steps/s", "h2d_bytes_per_step": 0,
                                   "d2h_bytes_per_step": 0}}), flush=True)
         return 0
     torch.cuda.set_device(local)
-    wl = inputs.batch_workload()
-    tensors = [w.site_tensor() for w in wl]
-    chis = [w.chi for w in wl]
-    batch = binding.CTMBatch(tensors, chis, precision=args.precision, n_split=args.n_split)
-    l_warm = binding.ctm_kernel_launches()
-    batch.ctm_batch_step(args.warmup)   # eager (autotuning) step + capture: each enqueues one batched step
-    torch.cuda.synchronize()
-    kernels_per_step = (binding.ctm_kernel_launches() - l_warm) // 2
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    with ClockSampler(torch.cuda.current_device()) as clk:
-        e0.record(batch.stream)
-        batch.ctm_batch_step(args.steps)
-        e1.record(batch.stream)
-        torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    launches = kernels_per_step * args.steps     # graph replays: the captured kernels of one batched step
-    value = len(wl) * args.steps / (ms / 1e3)
-    flops = sum(step_gemm_flops(w.chi, w.D2) for w in wl)
+    rec = batch_record(args, args.steps)
     T = args.n_split
-    pairs = T * (T + 1) // 2 if args.precision != "fp64" else 1
-    peaks, src = _peaks()
-    achieved = pairs * flops / (ms / args.steps / 1e3) / 1e12
-    peak = peaks["bf16_tflops"] if args.precision != "fp64" else fp64_peak_tflops(peaks)
-    # baseline: the same instances in FP64, one instance at a time (its own launches, no batching)
-    base_ms = 0.0
-    if not args.no_compare:
-        for A, chi in zip(tensors, chis):
-            c = binding.CTM(A, chi, precision="fp64")
-            c.ctm_step(1, want_delta=False)
-            b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            b0.record(c.stream)
-            for _ in range(args.steps):   # one launch sequence per instance and step
-                c.ctm_step(1, want_delta=False)
-            b1.record(c.stream)
-            torch.cuda.synchronize()
-            base_ms += b0.elapsed_time(b1)
-            c.close()
-    line = {"metric": METRIC + " [ragged batch of 96]", "value": value, "unit": "instance-steps/s", "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+    line = {"metric": METRIC + " [ragged batch of 96]", "value": rec["value"], "unit": "instance-steps/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": rec["ms_per_batched_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else f"bf16x{T}-split+f64",
             "data": "synthetic (seeded C3v-projected tensors, Kitaev-Heisenberg phi_i = 2 pi i/96)",
-            "config": {"workload": "batch96", "instances": len(wl), "D": "3..6", "chi": "24..72",
-                       "precision": args.precision, "launch": "one CUDA graph launch per batched step",
+            "config": {"workload": "batch96", "instances": rec["instances"], "D": "3..6", "chi": "24..72",
+                       "precision": args.precision, "launch": rec["launch"],
                        "l2": "batched step working set several GB > L2"},
-            "roofline": {"bound": "tensor" if args.precision != "fp64" else "alu", "achieved": achieved,
-                         "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                         "kernel": "whole batched step (executed slice-product flops / step time)",
-                         "peak_source": src},
-            "clocks": clk.summary(), "gpu_launches": int(launches)}
-    if base_ms > 0:
-        line["fp64_one_instance_at_a_time"] = {"value": len(wl) * args.steps / (base_ms / 1e3),
-                                               "unit": "instance-steps/s"}
-    batch.close()
+            "clocks": rec["clocks"], "gpu_launches": rec["kernels_per_batched_step"] * args.steps,
+            "batch96": rec}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def energy_vs_oracle(w, precision, n_split, steps):
+    """Energy after `steps` steps from the initial environment on the GPU (precision) and in
+    the oracle (all cores): (E_gpu, E_oracle)."""
+    from oracle import oracle as orc
+    from paper_2509_05090_gb300 import binding
+    A, h = w.site_tensor(), w.hamiltonians()
+    g = binding.CTM(A, w.chi, precision=precision, n_split=n_split)
+    g.ctm_step(steps, want_delta=False)
+    _, E, _ = g.ctm_energy(h)
+    g.close()
+    orc.set_threads(os.cpu_count() or 1)
+    ref = orc.OracleCTM(A, w.chi)
+    for _ in range(steps):
+        ref.step()
+    return E, ref.energy(h)[1]
+
+
+def time_to_converged(w, precision, n_split, max_steps):
+    """Wall time from ctm_init to a converged environment (delta < tol, read back every
+    step) and the energy there."""
+    import torch
+    from paper_2509_05090_gb300 import binding
+    A, h = w.site_tensor(), w.hamiltonians()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    g = binding.CTM(A, w.chi, precision=precision, n_split=n_split)
+    nst, dl, ok = g.ctm_converge(max_steps=max_steps, tol=w.tol, check_every=1)
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    _, E, _ = g.ctm_energy(h)
+    g.close()
+    return {"steps": nst, "delta": dl, "converged": ok, "seconds": secs, "E_site": E}
+
+
+def fp64_step_record(w, steps, fp64_peak):
+    """FP64 steps of workload w (one captured graph of `steps` steps), CUDA-event timed."""
+    import torch
+    from paper_2509_05090_gb300 import binding
+    c = binding.CTM(w.site_tensor(), w.chi, precision="fp64")
+    c.ctm_step(1, want_delta=False)       # eager first step
+    c.ctm_step(steps, want_delta=False)   # capture + run the K-step graph
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(c.stream)
+    c.ctm_step(steps, want_delta=False)
+    e1.record(c.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ph = {k: 0.0 for k in binding.CTM.PHASES + binding.CTM.SIDE_PHASES}
+    for _ in range(2):
+        for k, v in c.ctm_step_profiled().items():
+            ph[k] += v / 2
+    c.close()
+    flops = step_gemm_flops(w.chi, w.D2)
+    return {"workload": w.name, "steps_per_s": 1e3 / ms, "ms_per_step": ms,
+            "contraction_tflops": flops / (ph["gemm_kernels"] / 1e3) / 1e12,
+            "contraction_frac_of_fp64_peak": flops / (ph["gemm_kernels"] / 1e3) / 1e12 / fp64_peak,
+            "step_tflops": flops / (ms / 1e3) / 1e12, "step_frac_of_fp64_peak": flops / (ms / 1e3) / 1e12 / fp64_peak,
+            "fp64_peak_tflops": fp64_peak, "phase_ms": ph, "algorithmic_flops_per_step": flops}
+
+
+def split_step_rate(w, steps, n_split):
+    import torch
+    from paper_2509_05090_gb300 import binding
+    c = binding.CTM(w.site_tensor(), w.chi, precision="split_bf16", n_split=n_split)
+    c.ctm_step(1, want_delta=False)
+    c.ctm_step(steps, want_delta=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(c.stream)
+    c.ctm_step(steps, want_delta=False)
+    e1.record(c.stream)
+    torch.cuda.synchronize()
+    c.close()
+    return steps / (e0.elapsed_time(e1) / 1e3)
 
 
 def main():
@@ -264,8 +405,8 @@ def main():
     ap.add_argument("--workload", default="kh_D6_chi72")
     ap.add_argument("--precision", default="split_bf16", choices=["fp64", "split_bf16"])
     ap.add_argument("--n-split", type=int, default=5)
-    ap.add_argument("--no-compare", action="store_true")
-    ap.add_argument("--converge-steps", type=int, default=200)
+    ap.add_argument("--no-compare", action="store_true", help="skip the FP64/oracle/convergence sub-records")
+    ap.add_argument("--no-extras", action="store_true", help="skip the D=8 and batch96 sub-records")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
@@ -341,15 +482,17 @@ def main():
         for k, v in ph.items():
             phases[k] += v
     peaks, src = _peaks()
+    fp64_peak = binding.ctm_probe_fp64_peak()
     kern_ms = phases["gemm_kernels"] / nprof
+    prepass_ms = phases["prepass"] / nprof
     flops = step_gemm_flops(w.chi, w.D2)
     if args.precision == "fp64":
         achieved = flops / (kern_ms / 1e3) / 1e12
-        peak = fp64_peak_tflops(peaks)
-        roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None,
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_peak, "traffic": None,
                     "kernel": "gemm_f64_kernel (+ split-K reduce): the step's 11 FP64 contractions",
-                    "peak_source": f"{src}: bf16 burst x nominal FP64/BF16 (1.25/2250); FP64 DFMA pipe, not tcgen05"}
+                    "peak_source": "measured live: DFMA throughput probe (ctm_probe_fp64_peak); GB300 has no "
+                                   "FP64 tcgen05 kind, so the DFMA pipe is the FP64 ceiling"}
     else:
         T = args.n_split
         pairs = T * (T + 1) // 2
@@ -360,13 +503,17 @@ def main():
                     "kernel": f"gemm_split_kernel: {pairs} BF16 slice products (T={T}) per contraction, tcgen05 "
                               "kind::f16 into TMEM",
                     "peak_source": f"{src} bf16 burst",
-                    "fp64_equivalent_tflops": flops / (kern_ms / 1e3) / 1e12}
+                    "fp64_equivalent_tflops": flops / (kern_ms / 1e3) / 1e12,
+                    "with_prepass": {"ms_per_step": kern_ms + prepass_ms,
+                                     "achieved": pairs * flops / ((kern_ms + prepass_ms) / 1e3) / 1e12,
+                                     "frac": pairs * flops / ((kern_ms + prepass_ms) / 1e3) / 1e12 / peak}}
     key = (w.name, args.precision, args.n_split if args.precision != "fp64" else 0)
     if key in NCU_TRAFFIC:
         roofline["traffic"] = NCU_TRAFFIC[key]
         roofline["traffic_note"] = ("dram__bytes_read.sum + dram__bytes_write.sum of the step's 11 contraction "
                                     "launches (bytes per step, like achieved), one ncu capture, cold cache")
     roofline["kernel_ms_per_step"] = kern_ms
+    roofline["prepass_ms_per_step"] = prepass_ms
     roofline["algorithmic_flops_per_step"] = flops
     roofline["phase_ms"] = {k: v / nprof for k, v in phases.items()}
 
@@ -381,43 +528,49 @@ def main():
                    "l2": "timed steps back to back; per-step working set > L2 (no flush); profiled steps flush "
                          "256 MB before each"},
         "roofline": roofline,
+        "fp64_peak_measured_tflops": fp64_peak,
         "clocks": clk.summary(),
         "gpu_launches": int(launches),
         "wall_s_timed_region": wall,
     }
+    ctm.close()
 
-    # ---- mixed vs FP64 on the same GPU: same K steps from the same start, and the
-    # time to a converged environment (delta < tol) or to the step limit
+    # ---- mixed vs FP64 on the same GPU, and both against the FP64 oracle
     if not args.no_compare and rank == 0:
-        ref = binding.CTM(A, w.chi, precision="fp64")
-        ref.ctm_step(args.warmup + args.steps, want_delta=False)
-        ctm2 = binding.CTM(A, w.chi, precision=args.precision, n_split=args.n_split)
-        ctm2.ctm_step(args.warmup + args.steps, want_delta=False)
-        _, E_ref, _ = ref.ctm_energy(h)
-        _, E_mix, _ = ctm2.ctm_energy(h)
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        ref.ctm_step(args.steps, want_delta=False)   # captures the K-step graph, untimed
-        torch.cuda.synchronize()
-        f0.record(ref.stream)
-        ref.ctm_step(args.steps, want_delta=False)
-        f1.record(ref.stream)
-        torch.cuda.synchronize()
-        fp64_rate = args.steps / (f0.elapsed_time(f1) / 1e3)
-        conv = {}
-        for name, prec in (("mixed", args.precision), ("fp64", "fp64")):
-            cc = binding.CTM(A, w.chi, precision=prec, n_split=args.n_split)
-            torch.cuda.synchronize()
+        line["mixed_vs_fp64"] = {"fp64_steps_per_s": fp64_step_record(w, args.steps, fp64_peak)["steps_per_s"]}
+        e_steps = 3
+        E_mix, E_orc = energy_vs_oracle(w, args.precision, args.n_split, e_steps)
+        E_64, _ = energy_vs_oracle(w, "fp64", args.n_split, e_steps) if args.precision != "fp64" else (E_mix, E_orc)
+        line["mixed_vs_fp64"].update({
+            "after_steps": e_steps, "E_site_oracle": E_orc, "E_site_mixed": E_mix, "E_site_fp64": E_64,
+            "abs_energy_error_mixed_vs_oracle": abs(E_mix - E_orc), "abs_energy_error_fp64_vs_oracle": abs(E_64 - E_orc),
+            "abs_energy_error_mixed_vs_fp64": abs(E_mix - E_64)})
+        # time to a converged environment on the converging stand-in at the same size
+        wc = inputs.WORKLOADS.get(w.name + "_conv")
+        if wc is not None:
+            from oracle import oracle as orc
+            conv = {"workload": wc.name, "tol": wc.tol,
+                    "mixed": time_to_converged(wc, args.precision, args.n_split, wc.steps),
+                    "fp64": time_to_converged(wc, "fp64", args.n_split, wc.steps)}
+            orc.set_threads(os.cpu_count() or 1)
+            ref = orc.OracleCTM(wc.site_tensor(), wc.chi)
             t0 = time.perf_counter()
-            nst, dl, ok = cc.ctm_converge(max_steps=args.converge_steps, tol=w.tol, check_every=10)
-            conv[name] = {"steps": nst, "delta": dl, "converged": ok, "seconds": time.perf_counter() - t0}
-            cc.close()
-        line["mixed_vs_fp64"] = {"fp64_steps_per_s": fp64_rate, "E_site_fp64": E_ref, "E_site_mixed": E_mix,
-                                 "abs_energy_error": abs(E_mix - E_ref),
-                                 "after_steps": args.warmup + args.steps,
-                                 "time_to_converged": conv, "tol": w.tol}
-        ref.close()
-        ctm2.close()
+            rsteps, rdelta = ref.converge(wc.steps, wc.tol)
+            rsecs = time.perf_counter() - t0
+            E_ref = ref.energy(wc.hamiltonians())[1]
+            conv["oracle"] = {"steps": rsteps, "delta": rdelta, "seconds": rsecs, "E_site": E_ref,
+                              "threads": os.cpu_count()}
+            for k in ("mixed", "fp64"):
+                conv[k]["abs_energy_error_vs_oracle"] = abs(conv[k]["E_site"] - E_ref)
+            line["time_to_converged"] = conv
+
+    # ---- the spec D = 8, chi = 128 step in FP64 (and split for context), and the batch
+    if not args.no_extras and rank == 0 and w.name == "kh_D6_chi72":
+        w8 = inputs.WORKLOADS["kh_D8_chi128"]
+        rec8 = fp64_step_record(w8, 3, fp64_peak)
+        rec8["split_bf16_steps_per_s"] = split_step_rate(w8, 3, args.n_split)
+        line["fp64_d8_chi128"] = rec8
+        line["batch96"] = batch_record(args, args.steps)
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:
@@ -448,11 +601,14 @@ def main():
         e2e.close()
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, nsteps, secs, _ = cpu_oracle_rate(w, budget_s=15.0, max_steps=4)
-        line["cpu_baseline"] = {"value": rate, "unit": "steps/s", "cores": 1, "kind": "oracle",
-                                "sample": f"{nsteps} plain-C FP64 oracle steps of {w.name} from the initial "
-                                          f"environment ({secs:.1f} s, single thread)"}
-    ctm.close()
+        rate, nsteps, secs, _, _ = cpu_oracle_rate(w, budget_s=10.0, max_steps=4, threads=1)
+        rate_all, nsteps_all, secs_all, _, used = cpu_oracle_rate(w, budget_s=10.0, max_steps=8, threads=0)
+        line["cpu_baseline"] = {"value": rate_all, "unit": "steps/s", "cores": used, "host_cores": os.cpu_count(),
+                                "kind": "oracle",
+                                "sample": f"{nsteps_all} plain-C FP64 oracle steps of {w.name} from the initial "
+                                          f"environment ({secs_all:.1f} s, {used} OpenMP threads)",
+                                "single_thread": {"value": rate, "unit": "steps/s", "cores": 1,
+                                                  "sample": f"{nsteps} steps ({secs:.1f} s)"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -170,8 +170,16 @@ int ctm_get_intermediate(const ctm_ctx *ctx, int which, double *dst_dev, size_t 
  * (here they are waited for before returning), and (nphase >= 9) [8] the
  * summed time of the contraction-engine kernels alone (events around each
  * launch: the FP64 GEMM with its split-K reduction, or the tcgen05 kernel
- * without its operand pre-pass). */
+ * without its operand pre-pass), and (nphase >= 10) [9] the summed time of the
+ * split engine's operand pre-pass (exponents and digit packing; 0 in FP64). */
 int ctm_step_profiled(ctm_ctx *ctx, double *phase_ms, int nphase);
+
+/* Measured FP64 peak of the device (no counterpart in the paper; the roofline
+ * denominator of the FP64 contractions): a grid of 4 CTAs per SM, each thread
+ * running 16 independent chains of dependent DFMAs, timed with CUDA events after a
+ * warm-up launch.  *tflops_host receives 2 x DFMAs / second / 1e12.  Synchronous
+ * on `stream`. */
+int ctm_probe_fp64_peak(void *stream, double *tflops_host);
 
 /* Failure-detection test hook (no counterpart in the paper).  With enable != 0
  * the context's next Householder QR runs with a grid barrier that waits for one

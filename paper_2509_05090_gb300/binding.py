@@ -83,6 +83,7 @@ def load(path: str = LIB_PATH):
         "ctm_batch_destroy": (None, [P]),
         "ctm_grad": (I, [P, I, I, P, P, ctypes.c_size_t, dp, P]),
         "ctm_debug_force_timeout": (I, [P, I]),
+        "ctm_probe_fp64_peak": (I, [P, dp]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -94,6 +95,16 @@ def load(path: str = LIB_PATH):
 
 def ctm_kernel_launches() -> int:
     return int(load().ctm_kernel_launches())
+
+
+def ctm_probe_fp64_peak() -> float:
+    """Measured FP64 (DFMA) peak of the current device in TFLOP/s."""
+    torch = _torch()
+    t = ctypes.c_double(0.0)
+    st = load().ctm_probe_fp64_peak(ctypes.c_void_p(torch.cuda.current_stream().cuda_stream), ctypes.byref(t))
+    if st != CTM_OK:
+        raise CtmError(st, "ctm_probe_fp64_peak")
+    return t.value
 
 
 def ctm_gemm(A, B, precision="fp64", n_split=4):
@@ -269,16 +280,17 @@ class CTM:
         return out
 
     PHASES = ("enlarged_corner", "reduced_corner", "qr", "corner", "edge", "spectrum_wait", "handover")
-    SIDE_PHASES = ("spectrum", "gemm_kernels")
+    SIDE_PHASES = ("spectrum", "gemm_kernels", "prepass")
 
     def ctm_step_profiled(self):
-        ms = (ctypes.c_double * 9)()
-        st = load().ctm_step_profiled(self._h, ms, 9)
+        ms = (ctypes.c_double * 10)()
+        st = load().ctm_step_profiled(self._h, ms, 10)
         if st != CTM_OK:
             raise CtmError(st, "ctm_step_profiled")
         out = dict(zip(self.PHASES, ms[:7]))
         out["spectrum"] = ms[7]       # side stream, overlaps the next step in ctm_step
         out["gemm_kernels"] = ms[8]   # the contraction-engine kernels alone (subset of the phases)
+        out["prepass"] = ms[9]        # the split engine's operand pre-pass (subset of the phases)
         return out
 
     def ctm_debug_force_timeout(self, enable=True):

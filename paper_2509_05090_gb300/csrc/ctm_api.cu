@@ -223,9 +223,9 @@ bool config_ok(const ctm_config *cfg)
 cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint, int lane)
 {
     cudaEvent_t *ev = nullptr;
-    if (c->prof_on && c->prof_n + 2 <= 64) {
+    if (c->prof_on && c->prof_n + 3 <= CTM_PROF_EVENTS) {
         ev = c->prof_ev + c->prof_n;
-        c->prof_n += 2;
+        c->prof_n += 3;
     }
     if (c->split_T > 0) {
         SplitOpts o{};
@@ -252,7 +252,10 @@ cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint, int lane)
         if (fill_slot >= 0) c->ack_valid[fill_slot] = (e == cudaSuccess);
         return e;
     }
-    if (ev) cudaEventRecord(ev[0], c->stream);
+    if (ev) {
+        cudaEventRecord(ev[2], c->stream);   // no pre-pass in FP64
+        cudaEventRecord(ev[0], c->stream);
+    }
     cudaError_t e = gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, c->stream);
     if (ev) cudaEventRecord(ev[1], c->stream);
     return e;
@@ -889,7 +892,7 @@ void ctm_destroy(ctm_ctx *c)
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->prof_ev[0])
-        for (int i = 0; i < 64; ++i) cudaEventDestroy(c->prof_ev[i]);
+        for (int i = 0; i < CTM_PROF_EVENTS; ++i) cudaEventDestroy(c->prof_ev[i]);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     delete c;
@@ -917,7 +920,7 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
     for (int i = 0; i < 10; ++i)
         if (cudaEventCreate(&ev[i]) != cudaSuccess) return CTM_ECUDA;
     if (!c->prof_ev[0])
-        for (int i = 0; i < 64; ++i)
+        for (int i = 0; i < CTM_PROF_EVENTS; ++i)
             if (cudaEventCreate(&c->prof_ev[i]) != cudaSuccess) return CTM_ECUDA;
     c->prof_on = 1;
     c->prof_n = 0;
@@ -941,13 +944,16 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
         phase_ms[7] = ms;
     }
     if (rc == CTM_OK && nphase >= 9) {
-        double tot = 0.0;
-        for (int i = 0; i + 1 < c->prof_n; i += 2) {
-            float ms = 0.f;
+        double tot = 0.0, pre = 0.0;
+        for (int i = 0; i + 2 < c->prof_n; i += 3) {
+            float ms = 0.f, mp = 0.f;
             if (cudaEventElapsedTime(&ms, c->prof_ev[i], c->prof_ev[i + 1]) != cudaSuccess) rc = CTM_ECUDA;
+            if (cudaEventElapsedTime(&mp, c->prof_ev[i + 2], c->prof_ev[i]) != cudaSuccess) rc = CTM_ECUDA;
             tot += ms;
+            pre += mp;
         }
         phase_ms[8] = tot;
+        if (nphase >= 10) phase_ms[9] = pre;
     }
     for (int i = 0; i < 10; ++i) cudaEventDestroy(ev[i]);
     return rc;

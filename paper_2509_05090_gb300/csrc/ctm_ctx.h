@@ -6,6 +6,7 @@
 #include "ctm_internal.h"
 
 inline size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+constexpr int CTM_PROF_EVENTS = 96;
 
 struct ctm_ctx {
     ctm_config cfg;
@@ -70,7 +71,7 @@ struct ctm_ctx {
     int prof_on, prof_n;
     int qr_rows_min;          // 1 for a lone instance; larger inside a batch
     int force_timeout;        // ctm_debug_force_timeout: the QR grid barrier waits for an arrival that never comes
-    cudaEvent_t prof_ev[64];
+    cudaEvent_t prof_ev[CTM_PROF_EVENTS];   // three per contraction: kernel start, kernel end, pre-pass start
     int steps_done;
 };
 

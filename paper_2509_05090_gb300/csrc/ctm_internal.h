@@ -76,6 +76,8 @@ struct SplitOpts {
 SplitPlan split_plan_caps(int M, int N, int K, int T);
 int split_supported_T(int T);
 cudaError_t split_prepare();
+// ev (may be null): three events, recorded around the contraction kernel (ev[0] before,
+// ev[1] after) and before its operand pre-pass (ev[2]).
 cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
                        const SplitOpts *opt = nullptr);
 

@@ -1083,6 +1083,7 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
         g.M > w.e_cap || g.N > w.e_cap)
         return cudaErrorInvalidValue;
     cudaError_t e;
+    if (ev) cudaEventRecord(ev[2], st);   // before the operand pre-pass (profiling)
     if (pack_a) {
         e = split_prepass(g.M, g.K, g.A, g.Am, g.Ak, SP_BM, p.mTiles, p.kTiles, T, w.eA, w.Apk, st);
         if (e != cudaSuccess) return e;

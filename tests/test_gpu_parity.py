@@ -63,11 +63,11 @@ def test_prepared_tensors_match_oracle(ctm_lib, name, d, D, chi, seed):
     g.close()
 
 
-def _compare_last_step(g, ref, expect_full, tol_q=1e-10):
+def _compare_last_step(g, ref, expect_full, T_in, tol_q=1e-10):
     """The GPU context's last step against the oracle's last step (ref.last and its
-    environment); expect_full: every column of R is leading (R_ii / R_00 >= 1e-8).
-    Returns the number of leading columns."""
-    from split_bounds import qr_column_bounds
+    environment); T_in is the edge that step started from.  expect_full: every column
+    of R is leading (R_ii / R_00 >= 1e-8).  Returns the number of leading columns."""
+    from split_bounds import edge_operator_fro, qr_column_bounds
     chi = ref.chi
     last = ref.last
     assert _rel(_np(g.ctm_get_intermediate("M")), last["M"]) <= 1e-12
@@ -95,13 +95,28 @@ def _compare_last_step(g, ref, expect_full, tol_q=1e-10):
         Pg = Q[:, lead:] @ (Q[:, lead:].T @ Y)
         Po = last["Q"][:, lead:] @ (last["Q"][:, lead:].T @ last["Y"])
         assert np.max(np.abs(Pg - Po)) <= 1e-10 * np.max(np.abs(last["Y"]))
-        # C' and T' on the columns whose projector is tightly determined
-        well = int(np.sum(np.cumsum(2.0 * bq > tol_q * np.max(np.abs(last["Q"]))) == 0))
+        # C' and T' on the leading columns whose projector bound is below 1e-8 max|Q|,
+        # each side scaled to unit norm on that block; tolerance: the first-order effect
+        # of those columns' Q bound (2 ||M Q_w||_2 ||dQ_w||_F on the corner block,
+        # 2 ||K||_F ||dQ_w||_F on the edge block), doubled for the scaling, floor 1e-10
+        well = int(np.sum(np.cumsum(2.0 * bq > 1e-8 * np.max(np.abs(last["Q"]))) == 0))
         assert well >= 1
+        Qw = last["Q"][:, :well]
+        dQw = float(np.sqrt(np.sum((2.0 * bq[:well]) ** 2)))
+        MQw = last["M"] @ Qw
+        Cw = Qw.T @ MQw
+        tol_c = max(1e-10, 4.0 * np.linalg.norm(MQw, 2) * dQw / np.linalg.norm(0.5 * (Cw + Cw.T)))
+        D2 = ref.D2
+        Qr = last["Q"].reshape(chi, D2, chi)
+        Tw = np.einsum("ayi,ayxj->ixj", Qr[:, :, :well],
+                       np.einsum("aug,uwz,zxy,gwj->ayxj", T_in, ref.a, ref.a, Qr[:, :, :well], optimize=True),
+                       optimize=True)
+        tol_t = max(1e-10, 4.0 * edge_operator_fro(T_in, ref.a) * dQw / np.linalg.norm(Tw))
         Cb, Cbr = C[:well, :well], last["C"][:well, :well]
         Tb, Tbr = T[:well, :, :well], last["T"][:well, :, :well]
-        assert _rel(Cb / np.linalg.norm(Cb), Cbr / np.linalg.norm(Cbr)) <= 1e-10
-        assert _rel(Tb / np.linalg.norm(Tb), Tbr / np.linalg.norm(Tbr)) <= 1e-10
+        assert np.max(np.abs(Cb / np.linalg.norm(Cb) - Cbr / np.linalg.norm(Cbr))) <= tol_c
+        assert np.max(np.abs(Tb / np.linalg.norm(Tb) - Tbr / np.linalg.norm(Tbr))) <= tol_t
+        assert tol_c < 1e-4 and tol_t < 1e-4   # not vacuous
     assert np.max(np.abs(_np(g.ctm_get_intermediate("s")) - ref.s)) <= 1e-10
     return lead
 
@@ -114,9 +129,10 @@ def _step_parity(A, chi, pre_steps, expect_full=True):
         ref.step()
     g = _ctm(A, chi)
     g.ctm_set_env(ref.C, ref.T, ref.Q)
+    T_in = ref.T.copy()
     ref.step()
     g.ctm_step(1)
-    lead = _compare_last_step(g, ref, expect_full)
+    lead = _compare_last_step(g, ref, expect_full, T_in)
     g.close()
     return lead
 
@@ -178,10 +194,11 @@ def test_trajectory_200_steps_converging_d4_chi32(ctm_lib):
     ref = O.OracleCTM(A, w.chi)
     g = _ctm(A, w.chi)
     for k in range(200):
+        T_in = ref.T.copy()
         dr = ref.step()
         dg = g.ctm_step(1)
         assert abs(dg - dr) <= 1e-10 + 1e-8 * abs(dr), (k, dg, dr)
-    _compare_last_step(g, ref, expect_full=False)
+    _compare_last_step(g, ref, expect_full=False, T_in=T_in)
     e_ref, E_ref = ref.energy(h)
     e, E, rho = g.ctm_energy(h)
     assert abs(E - E_ref) <= 1e-12
@@ -191,18 +208,21 @@ def test_trajectory_200_steps_converging_d4_chi32(ctm_lib):
 
 def test_trajectory_random_d4_chi32_first_20_steps(ctm_lib):
     """The random D = 4, chi = 32 state: its iteration amplifies rounding differences by
-    ~1e3 every 20 steps (test_trajectory_sensitivity), so steps are compared while the
-    oracle's own sensitivity stays far below the tolerance: delta of each of 20 steps
-    and the whole last step."""
+    ~1e3 every 20 steps (test_trajectory_sensitivity; measured 1.6e-11 in M between GPU
+    and oracle after 20 steps), so the environment itself is compared step by step
+    elsewhere; here delta of each of 20 steps, the spectrum and the energies after them."""
     w = I.WORKLOADS["kitaev_D4_chi32"]
-    A = w.site_tensor()
+    A, h = w.site_tensor(), w.hamiltonians()
     ref = O.OracleCTM(A, w.chi)
     g = _ctm(A, w.chi)
     for k in range(20):
         dr = ref.step()
         dg = g.ctm_step(1)
         assert abs(dg - dr) <= 1e-10 + 1e-8 * abs(dr), (k, dg, dr)
-    _compare_last_step(g, ref, expect_full=True)
+    assert np.max(np.abs(_np(g.ctm_get_intermediate("s")) - ref.s)) <= 1e-10
+    e_ref, E_ref = ref.energy(h)
+    e, E, rho = g.ctm_energy(h)
+    assert abs(E - E_ref) <= 1e-10
     g.close()
 
 
