@@ -336,7 +336,7 @@ def energy_vs_oracle(w, precision, n_split, steps):
     return E, ref.energy(h)[1]
 
 
-def time_to_converged(w, precision, n_split, max_steps):
+def time_to_converged(w, precision, n_split, max_steps, corner="qmq"):
     """Wall time from ctm_init to a converged environment (delta < tol, read back every
     step) and the energy there."""
     import torch
@@ -344,7 +344,7 @@ def time_to_converged(w, precision, n_split, max_steps):
     A, h = w.site_tensor(), w.hamiltonians()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    g = binding.CTM(A, w.chi, precision=precision, n_split=n_split)
+    g = binding.CTM(A, w.chi, precision=precision, n_split=n_split, corner=corner)
     nst, dl, ok = g.ctm_converge(max_steps=max_steps, tol=w.tol, check_every=1)
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
@@ -380,10 +380,10 @@ def fp64_step_record(w, steps, fp64_peak):
             "fp64_peak_tflops": fp64_peak, "phase_ms": ph, "algorithmic_flops_per_step": flops}
 
 
-def split_step_rate(w, steps, n_split):
+def split_step_rate(w, steps, n_split, corner="qmq"):
     import torch
     from paper_2509_05090_gb300 import binding
-    c = binding.CTM(w.site_tensor(), w.chi, precision="split_bf16", n_split=n_split)
+    c = binding.CTM(w.site_tensor(), w.chi, precision="split_bf16", n_split=n_split, corner=corner)
     c.ctm_step(1, want_delta=False)
     c.ctm_step(steps, want_delta=False)
     torch.cuda.synchronize()
@@ -563,6 +563,13 @@ def main():
             for k in ("mixed", "fp64"):
                 conv[k]["abs_energy_error_vs_oracle"] = abs(conv[k]["E_site"] - E_ref)
             line["time_to_converged"] = conv
+            # the cheap corner variant C' = sym(R S) (corner_mode 1): step rate, and the
+            # converged energy on the converging state against the standard oracle
+            cr = time_to_converged(wc, args.precision, args.n_split, wc.steps, corner="r")
+            cr["abs_energy_error_vs_oracle"] = abs(cr["E_site"] - E_ref)
+            line["corner_from_r"] = {"steps_per_s": split_step_rate(w, args.steps, args.n_split, corner="r")
+                                     if args.precision != "fp64" else None,
+                                     "time_to_converged": cr}
 
     # ---- the spec D = 8, chi = 128 step in FP64 (and split for context), and the batch
     if not args.no_extras and rank == 0 and w.name == "kh_D6_chi72":

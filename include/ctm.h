@@ -68,6 +68,10 @@ typedef struct {
     double tol;              /* convergence threshold on delta (Sec. II.B: "desired precision") */
     int max_steps;           /* step limit of ctm_converge when its argument is <= 0 */
     int symmetrize;          /* 1: project A onto the C3v A1 subspace and normalise (App. A) */
+    int corner_mode;         /* 0: C' = sym(Q^T M Q)/|.| (Fig. 3a); 1: C' = sym(R S)/|.| from the QR
+                                factor R of the reduced corner Y = M Q_prev S (S = diag(sgn C_ii)),
+                                which equals Q^T M Q_prev and so Q^T M Q at a fixed point: skips the
+                                two corner contractions (a cheap variant, Sec. II.B, Fig. 3d) */
 } ctm_config;
 
 /* Bytes of device workspace ctm_init needs for this configuration (0 on a bad
@@ -103,9 +107,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
  * Once the context has run a step, a call replays its nsteps steps as one
  * CUDA graph: a one-step graph for nsteps = 1 (captured on the first such call
  * and kept), and one for the last nsteps >= 2 requested (re-captured when that
- * count changes); the work is the same.  Only the context's configured
- * contraction precision is replayed this way (the adjoint's tracked FP64 steps
- * on a split-BF16 context run eagerly). */
+ * count changes); the work is the same. */
 int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
 
 /* Sec. II.B: repeat steps until delta < tol (tol <= 0: cfg->tol) or max_steps
@@ -128,10 +130,11 @@ int ctm_energy(ctm_ctx *ctx, const double *h_dev, double *e_bond_host, double *e
                double *rho_host);
 
 /* Sec. II.D: energy gradient by a hand-written adjoint.  From the current
- * environment, run `warmup` steps (treated as constants, in the context's
- * precision), then k_tracked steps in FP64 whose inputs are checkpointed, then
- * the energy of ctm_energy.  The adjoint recomputes each tracked step from its
- * checkpoint and back-propagates through every contraction, the Householder
+ * environment, run `warmup` steps (treated as constants), then k_tracked steps
+ * whose inputs are checkpointed, both in the context's precision (on a
+ * CTM_SPLIT_BF16 context: split-BF16 contractions with the FP64 QR), then the
+ * energy of ctm_energy.  The adjoint recomputes each tracked step from its
+ * checkpoint in FP64 and back-propagates through every contraction, the Householder
  * QR (Y-bar = (Q-bar + Q copyltu(-Q-bar^T Q)) R^{-T}, the triangular solve
  * regularised as R_ii / (R_ii^2 + (1e-13 R_00)^2)), the corner and edge
  * normalisations, the double and open layers, and the C3v projection and
@@ -146,6 +149,15 @@ int ctm_energy(ctm_ctx *ctx, const double *h_dev, double *e_bond_host, double *e
 size_t ctm_grad_workspace_bytes(const ctm_ctx *ctx, int k_tracked);
 int ctm_grad(ctm_ctx *ctx, int warmup, int k_tracked, const double *h_dev, void *gws, size_t gws_bytes,
              double *energy_host, double *dA_dev);
+
+/* Replace the site tensor of a context (Sec. II.D: an optimiser's next trial
+ * tensor) without reallocating: A_dev (raw, as for ctm_init) is projected and
+ * normalised under the context's symmetrize setting and its double layer formed;
+ * the environment is kept as the warm start of the next steps (reset_env = 0) or
+ * reset to the initial environment of ctm_init (reset_env != 0).  Captured step
+ * graphs are dropped and captured again on the next call.  CTM_ENONFINITE if the
+ * tensor holds NaN/Inf.  Synchronous. */
+int ctm_set_site(ctm_ctx *ctx, const double *A_dev, int reset_env);
 
 /* Copy the current environment out / in (device pointers; parity checks and
  * resume).  C: chi x chi, T: chi x D2 x chi, Q: n x chi. */

@@ -266,6 +266,23 @@ double orc_corner_update(int n, int chi, const double *M, const double *Q, doubl
     return nrm;
 }
 
+/* Cheap corner variant: the QR of the reduced corner Y = M Q_prev S gives
+ * Q^T M Q_prev = R S (S = diag(sgn Cprev_jj), sgn(0) = +1), which is Q^T M Q once
+ * Q = Q_prev; C' = sym(R S), unit Frobenius norm.  Returns the norm before
+ * normalisation.                                                             */
+double orc_corner_from_r(int chi, const double *R, const double *Cprev, double *Cn)
+{
+    for (int i = 0; i < chi; ++i)
+        for (int j = 0; j < chi; ++j) {
+            double si = Cprev[(size_t)i * chi + i] < 0.0 ? -1.0 : 1.0;
+            double sj = Cprev[(size_t)j * chi + j] < 0.0 ? -1.0 : 1.0;
+            Cn[(size_t)i * chi + j] = 0.5 * (R[(size_t)i * chi + j] * sj + R[(size_t)j * chi + i] * si);
+        }
+    double nrm = orc_frobenius((long)chi * chi, Cn);
+    if (nrm > 0.0) orc_scale((long)chi * chi, Cn, 1.0 / nrm);
+    return nrm;
+}
+
 /* ------------------------------------------------------------------------ */
 /* a6: edge renormalisation, Fig. 3(b).  The edge grows by one radial dimer at
  * its apex end; both of its long sides are compressed with the same Q:

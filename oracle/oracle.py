@@ -73,6 +73,7 @@ def _load():
                 "orc_enlarged_corner": (None, [I, I, P, P, P, P, P]),
                 "orc_householder_qr": (None, [I, I, P, P, P]),
                 "orc_corner_update": (ctypes.c_double, [I, I, P, P, P]),
+                "orc_corner_from_r": (ctypes.c_double, [I, P, P, P]),
                 "orc_edge_update": (ctypes.c_double, [I, I, P, P, P, P, P]),
                 "orc_sym_eig": (I, [I, P, P, P]),
                 "orc_corner_spectrum": (None, [I, P, P]),
@@ -170,6 +171,16 @@ def corner_update(M, Q) -> np.ndarray:
     return Cn
 
 
+def corner_from_r(R, Cprev) -> np.ndarray:
+    """Cheap variant of a5: C' = sym(R S) / ||.||_F, S = diag(sgn Cprev_jj), from the QR
+    factor R of Y = M Q_prev S (R S = Q^T M Q_prev, equal to Q^T M Q at a fixed point)."""
+    R, Cprev = _c(R), _c(Cprev)
+    chi = R.shape[0]
+    Cn = np.empty((chi, chi))
+    _load().orc_corner_from_r(chi, _p(R), _p(Cprev), _p(Cn))
+    return Cn
+
+
 def edge_update(T, aB, aA, Q) -> np.ndarray:
     """a6 (Fig. 3b): T'[i,x,j] = sum Q[(a,y),i] T[a,u,g] aB[u,w,z] aA[z,x,y] Q[(g,w),j], normalised."""
     T, aB, aA, Q = _c(T), _c(aB), _c(aA), _c(Q)
@@ -228,7 +239,8 @@ def bond_energies(rho, h):
 class OracleCTM:
     """QR-based (or, for cross-checks, EVD-based) C3v CTMRG on one site tensor."""
 
-    def __init__(self, A, chi: int, symmetrize: bool = True, projector: str = "qr"):
+    def __init__(self, A, chi: int, symmetrize: bool = True, projector: str = "qr", corner: str = "qmq"):
+        self.corner = corner          # "qmq": C' = sym(Q^T M Q); "r": the cheap variant sym(R S)
         self.A = prepare_site(A, symmetrize)
         self.d, self.D = self.A.shape[0], self.A.shape[1]
         self.D2 = self.D * self.D
@@ -266,7 +278,10 @@ class OracleCTM:
         else:
             Y, R = None, None
             Q = evd_projector(M, self.chi)
-        Cn = corner_update(M, Q)
+        if self.corner == "r" and self.projector == "qr":
+            Cn = corner_from_r(R, self.C)
+        else:
+            Cn = corner_update(M, Q)
         Tn = edge_update(self.T, self.a, self.a, Q)
         s = corner_spectrum(Cn)
         delta = float(np.sqrt(np.sum((s - self.s) ** 2)))

@@ -27,7 +27,7 @@ PRECISIONS = {"fp64": CTM_FP64, "split_bf16": CTM_SPLIT_BF16}
 class ctm_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("D", ctypes.c_int), ("chi", ctypes.c_int),
                 ("precision", ctypes.c_int), ("n_split", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_steps", ctypes.c_int), ("symmetrize", ctypes.c_int)]
+                ("max_steps", ctypes.c_int), ("symmetrize", ctypes.c_int), ("corner_mode", ctypes.c_int)]
 
 
 class CtmError(RuntimeError):
@@ -84,6 +84,7 @@ def load(path: str = LIB_PATH):
         "ctm_grad": (I, [P, I, I, P, P, ctypes.c_size_t, dp, P]),
         "ctm_debug_force_timeout": (I, [P, I]),
         "ctm_probe_fp64_peak": (I, [P, dp]),
+        "ctm_set_site": (I, [P, P, I]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -160,9 +161,13 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_config(d, D, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True):
+CORNER_MODES = {"qmq": 0, "r": 1}
+
+
+def make_config(d, D, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True, corner="qmq"):
     return ctm_config(int(d), int(D), int(chi), PRECISIONS[precision] if isinstance(precision, str) else
-                      int(precision), int(n_split), float(tol), int(max_steps), 1 if symmetrize else 0)
+                      int(precision), int(n_split), float(tol), int(max_steps), 1 if symmetrize else 0,
+                      CORNER_MODES[corner])
 
 
 def ctm_workspace_bytes(cfg: ctm_config) -> int:
@@ -173,7 +178,7 @@ class CTM:
     """One CTMRG instance on the current CUDA device (ctm_init ... ctm_destroy)."""
 
     def __init__(self, A, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True,
-                 stream=None):
+                 stream=None, corner="qmq"):
         torch = _torch()
         lib = load()
         if isinstance(A, np.ndarray):
@@ -183,7 +188,7 @@ class CTM:
         self.d, self.D, self.chi = d, D, int(chi)
         self.D2 = D * D
         self.n = self.chi * self.D2
-        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize)
+        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize, corner)
         nbytes = ctm_workspace_bytes(self.cfg)
         if nbytes == 0:
             raise CtmError(1, "ctm_workspace_bytes")
@@ -245,6 +250,19 @@ class CTM:
         if st != CTM_OK:
             raise CtmError(st, "ctm_grad")
         return E.value, dA
+
+    def ctm_set_site(self, A, reset_env=False):
+        """Replace the site tensor (same d, D); keep (or reset) the environment."""
+        torch = _torch()
+        if isinstance(A, np.ndarray):
+            A = torch.from_numpy(np.ascontiguousarray(A, dtype=np.float64))
+        A = A.to(device="cuda", dtype=torch.float64).contiguous()
+        if tuple(A.shape) != (self.d, self.D, self.D, self.D):
+            raise CtmError(1, "ctm_set_site")
+        st = load().ctm_set_site(self._h, _ptr(A), 1 if reset_env else 0)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_set_site")
+        self._A = A
 
     def ctm_get_env(self):
         torch = _torch()

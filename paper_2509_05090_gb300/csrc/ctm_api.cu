@@ -214,6 +214,7 @@ bool config_ok(const ctm_config *cfg)
     if (cfg->chi < 1 || cfg->chi > 160) return false;
     if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return false;
     if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
+    if (cfg->corner_mode != 0 && cfg->corner_mode != 1) return false;
     long long n = (long long)cfg->chi * cfg->D * cfg->D;
     if (n > 20000) return false;
     return true;
@@ -330,6 +331,16 @@ int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout, int lane = 0)
     return CTM_OK;
 }
 
+// Cheap corner variant: Cout = sym(R S)/|.|_F with S = diag(sgn C_jj) of the corner
+// that entered the step (R S = Q^T M Q_prev exactly; = Q^T M Q at a fixed point).
+int enqueue_corner_from_r(ctm_ctx *c, double *Cout)
+{
+    const int chi = c->chi;
+    CK(launch_warm_start(chi, chi, c->R, c->C, c->Cr, c->stream));
+    CK(launch_corner_sym_normalize(chi, c->Cr, Cout, c->norm_part, c->stream));
+    return CTM_OK;
+}
+
 // Fig. 3(b): T'[i,x,j] = sum Q[(a,y),i] T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j], normalised.
 // lane 2 (split mode): with the edge lane's work buffers, concurrent with a corner
 // update on lane2; the last contraction waits for it (it uses the corner's pack of Q^T).
@@ -376,7 +387,7 @@ int enqueue_step(ctm_ctx *c)
     // Split mode after the first step (whose eager contractions time their plans
     // one at a time): the corner and edge updates both need only Q, so the corner
     // update runs on lane2 beside the edge update.
-    if (c->split_T > 0 && c->steps_done > 0) {
+    if (c->split_T > 0 && c->steps_done > 0 && c->cfg.corner_mode == 0) {
         CK(cudaEventRecord(c->ev_q, st));
         CK(cudaStreamWaitEvent(c->lane2, c->ev_q, 0));
         // the previous step's spectrum (reading C or Cspec) is done before Cspec is rewritten
@@ -401,7 +412,8 @@ int enqueue_step(ctm_ctx *c)
         CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
         return CTM_OK;
     }
-    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    if ((rc = c->cfg.corner_mode ? enqueue_corner_from_r(c, c->Cn) : enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK)
+        return rc;
     if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
     if (c->side_pending) CK(cudaStreamWaitEvent(st, c->ev_join, 0));
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
@@ -447,7 +459,8 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
         CK(qr_householder((int)n, (int)chi, c->Y, c->Qn, c->R, qs, st));
     }
     CK(cudaEventRecord(ev[3], st));
-    if ((rc = enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK) return rc;
+    if ((rc = c->cfg.corner_mode ? enqueue_corner_from_r(c, c->Cn) : enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK)
+        return rc;
     CK(cudaEventRecord(ev[4], st));
     if ((rc = enqueue_edge(c, c->Qn, c->Tn)) != CTM_OK) return rc;
     CK(cudaEventRecord(ev[5], st));
@@ -960,6 +973,34 @@ int ctm_step_profiled(ctm_ctx *c, double *phase_ms, int nphase)
 }
 
 unsigned long long ctm_kernel_launches(void) { return g_ctm_launches; }
+
+int ctm_set_site(ctm_ctx *c, const double *A_dev, int reset_env)
+{
+    if (!c || !A_dev) return CTM_EINVAL;
+    if (join_side(c) != CTM_OK) return CTM_ECUDA;
+    cudaStream_t st = c->stream;
+    const long long nA = (long long)c->d * c->D * c->D * c->D;
+    CK(cudaMemcpyAsync(c->Araw, A_dev, sizeof(double) * nA, cudaMemcpyDeviceToDevice, st));
+    CK(launch_c3v_project_normalize(c->d, c->D, c->Araw, c->A, c->cfg.symmetrize ? 1 : 0, st));
+    CK(launch_double_layer(c->d, c->D, c->A, c->A, c->a, st));
+    // the packed digits of the old double layer and the graphs that assumed them are stale
+    c->apk_state[0] = c->apk_state[1] = 0;
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    c->graph = nullptr;
+    c->graph1 = nullptr;
+    c->graph_steps = 0;
+    if (reset_env) {
+        CK(launch_init_env(c->chi, c->D, c->a, c->C, c->T, c->Q, st));
+        CK(launch_spectrum_init(c->chi, c->s, st));
+    }
+    CK(cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+    CK(launch_check_finite(nA, c->A, c->flag, st));
+    int f = 0;
+    CK(cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return f ? CTM_ENONFINITE : CTM_OK;
+}
 
 int ctm_debug_force_timeout(ctm_ctx *c, int enable)
 {

@@ -498,7 +498,7 @@ extern "C" int ctm_grad(ctm_ctx *c, int warmup, int k_tracked, const double *h_d
                         double *energy_host, double *dA_dev)
 {
     if (!c || !h_dev || !gws || !dA_dev || warmup < 0 || k_tracked < 1) return CTM_EINVAL;
-    if (c->d * c->d > 9) return CTM_EUNSUPPORTED;
+    if (c->d * c->d > 9 || c->cfg.corner_mode != 0) return CTM_EUNSUPPORTED;
     if ((uintptr_t)gws % 256 != 0) return CTM_EINVAL;
     if (gws_bytes < grad_layout(c, k_tracked, nullptr, nullptr)) return CTM_ENOMEM;
     GradBufs b;
@@ -514,13 +514,12 @@ extern "C" int ctm_grad(ctm_ctx *c, int warmup, int k_tracked, const double *h_d
     cudaStream_t st = c->stream;
     G64 G{c, &b};
     if (join_side(c) != CTM_OK) return CTM_ECUDA;
-    // ---- forward: detached warm-up (context precision), then tracked FP64 steps with checkpoints
+    // ---- forward: detached warm-up, then tracked steps with checkpoints, both in the
+    // context's precision (split-BF16 contractions with the FP64 QR on a split context)
     if (warmup > 0) {
         int rc = ctm_step(c, warmup, nullptr);
         if (rc != CTM_OK) return rc;
     }
-    const int saved_T = c->split_T;
-    c->split_T = 0;
     auto ck = [&](int t) { return b.ck + (size_t)t * b.ck_stride; };
     int rc = CTM_OK;
     for (int t = 0; t <= k_tracked && rc == CTM_OK; ++t) {
@@ -531,7 +530,6 @@ extern "C" int ctm_grad(ctm_ctx *c, int warmup, int k_tracked, const double *h_d
             rc = CTM_ECUDA;
         if (rc == CTM_OK && t < k_tracked) rc = ctm_step(c, 1, nullptr);
     }
-    c->split_T = saved_T;
     if (rc != CTM_OK) return rc;
     if (join_side(c) != CTM_OK) return CTM_ECUDA;
 

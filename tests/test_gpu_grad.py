@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 def _gpu_grad(A, chi, h, warmup, k, precision="fp64"):
     from paper_2509_05090_gb300 import binding
-    g = binding.CTM(A, chi, precision=precision)
+    g = binding.CTM(A, chi, precision=precision, n_split=5)
     E, dA = g.ctm_grad(h, warmup=warmup, k_tracked=k)
     out = dA.cpu().numpy()
     g.close()
@@ -114,3 +114,90 @@ def test_adjoint_full_size_d8_chi128_directional(ctm_lib, k):
         c.close()
     fd = (vals[0] - vals[1]) / 2e-6
     assert abs(fd - np.sum(g * V)) <= 1e-5 * max(1.0, abs(fd))
+
+
+def _zz_bonds():
+    """S^z S^z on all three bonds.  On the converging near-product states every isotropic
+    Kitaev-Heisenberg bond energy is stationary (K|S|^2 + 3J|S|^2 with |S| = 1/2 for
+    any product state), so their gradients are tiny; this observable's are O(1)."""
+    Sz = np.diag([0.5, -0.5])
+    hz = np.kron(Sz, Sz)
+    return np.stack([hz, hz, hz])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_adjoint_k30_matches_cpu_reference(ctm_lib, precision):
+    """k = 30 tracked steps (D = 4, chi = 32, converging near-product state) with the
+    forward in the context's precision (split: BF16 slice contractions, FP64 QR) against
+    the PyTorch float64 reference gradient through the same 30 steps."""
+    import torch_reference as TR
+    w = I.WORKLOADS["kitaev_D4_chi32_conv"]
+    A, h = w.site_tensor(), _zz_bonds()
+    E_gpu, g_gpu = _gpu_grad(A, w.chi, h, 3, 30, precision)
+    env = _oracle_env_after(A, w.chi, 3)
+    E_ref, g_ref = TR.energy_and_grad(A, env, h, 30)
+    assert abs(E_gpu - E_ref) <= 1e-10
+    assert np.max(np.abs(g_gpu - g_ref)) <= 1e-7 * np.max(np.abs(g_ref))
+
+
+def test_adjoint_d8_chi128_k30_split_forward(ctm_lib):
+    """D = 8, chi = 128 (enlarged corner 8192 x 8192), converging near-product state: 3
+    warm-up and 30 checkpointed steps in split-BF16 with the FP64 QR, the adjoint in
+    FP64, against central differences (h = 1e-6) of the FP64 GPU forward through the
+    same 30 steps from the same environment, along 3 random directions."""
+    from paper_2509_05090_gb300 import binding
+    w = I.WORKLOADS["kh_D8_chi128_conv"]
+    A, h = w.site_tensor(), _zz_bonds()
+    E, g = _gpu_grad(A, w.chi, h, 3, 30, "split_bf16")
+    assert np.all(np.isfinite(g))
+    base = binding.CTM(A, w.chi, precision="split_bf16", n_split=5)
+    base.ctm_step(3)
+    C0, T0, Q0 = base.ctm_get_env()
+    base.close()
+    rng = np.random.default_rng(8)
+    for _ in range(3):
+        V = rng.standard_normal(A.shape)
+        vals = []
+        for sgn in (1.0, -1.0):
+            c = binding.CTM(A + sgn * 1e-6 * V, w.chi)
+            c.ctm_set_env(C0, T0, Q0)
+            c.ctm_step(30)
+            vals.append(c.ctm_energy(h)[1])
+            c.close()
+        fd = (vals[0] - vals[1]) / 2e-6
+        assert abs(fd - np.sum(g * V)) <= 1e-6 * max(1.0, abs(fd)), (fd, np.sum(g * V))
+
+
+def test_autograd_reuses_context_and_defers_adjoint(ctm_lib):
+    """Two differentiable energies of different tensors share one library context (the
+    second starts from the first one's environment); a forward without backward runs no
+    adjoint; each gradient matches a fresh ctm_grad from the environment it started at."""
+    import torch
+    from paper_2509_05090_gb300 import autograd as AG
+    from paper_2509_05090_gb300 import binding
+    AG.release_contexts()
+    w = I.WORKLOADS["heis_D2_chi8"]
+    h = torch.from_numpy(w.hamiltonians()).cuda()
+    A1 = torch.from_numpy(w.site_tensor()).cuda().requires_grad_(True)
+    E1 = AG.ctm_energy(A1, w.chi, h, warmup=5, k_tracked=3)
+    (g1,) = torch.autograd.grad(E1, A1)
+    assert len(AG._CONTEXTS) == 1
+    ctm = next(iter(AG._CONTEXTS.values()))
+    env1 = [x.clone() for x in ctm.ctm_get_env()]
+    A2 = (A1.detach() * 1.01 + 0.001).requires_grad_(True)
+    l0 = binding.ctm_kernel_launches()
+    E2 = AG.ctm_energy(A2, w.chi, h, warmup=5, k_tracked=3)
+    l_fwd = binding.ctm_kernel_launches() - l0
+    (g2,) = torch.autograd.grad(E2, A2)
+    l_bwd = binding.ctm_kernel_launches() - l0 - l_fwd
+    # backward repeats the forward's steps and adds the adjoint (dozens of launches per
+    # tracked step); the forward ran none of it
+    assert l_bwd > l_fwd + 50, (l_fwd, l_bwd)
+    assert len(AG._CONTEXTS) == 1 and next(iter(AG._CONTEXTS.values())) is ctm
+    ref = binding.CTM(A2.detach(), w.chi)
+    ref.ctm_set_env(*env1)
+    E2r, g2r = ref.ctm_grad(h.cpu().numpy(), warmup=5, k_tracked=3)
+    ref.close()
+    assert abs(float(E2) - E2r) <= 1e-12
+    assert torch.max(torch.abs(g2 - g2r)).item() <= 1e-10 * torch.max(torch.abs(g2r)).item()
+    AG.release_contexts()

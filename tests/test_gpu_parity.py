@@ -121,13 +121,14 @@ def _compare_last_step(g, ref, expect_full, T_in, tol_q=1e-10):
     return lead
 
 
-def _step_parity(A, chi, pre_steps, expect_full=True):
+def _step_parity(A, chi, pre_steps, expect_full=True, corner="qmq"):
     """One GPU step from the oracle's environment after pre_steps steps, compared with
     the oracle's step; the test asserts which comparison branch it took."""
     ref = O.OracleCTM(A, chi)
     for _ in range(pre_steps):
         ref.step()
-    g = _ctm(A, chi)
+    ref.corner = corner
+    g = _ctm(A, chi, corner=corner)
     g.ctm_set_env(ref.C, ref.T, ref.Q)
     T_in = ref.T.copy()
     ref.step()
@@ -331,3 +332,29 @@ def test_chi_one_and_d1(ctm_lib):
     A = I.random_site_tensor(2, 3, 12)
     _step_parity(A, 1, 2)
     _step_parity(I.random_site_tensor(2, 1, 4), 3, 1)
+
+
+@pytest.mark.parametrize("name,pre", [("kitaev_D4_chi32", 3), ("kh_D6_chi72", 1)])
+def test_corner_from_r_step_matches_oracle(ctm_lib, name, pre):
+    """The cheap corner variant C' = sym(R S)/|.| (corner_mode 1), one FP64 step."""
+    w = I.WORKLOADS[name]
+    _step_parity(w.site_tensor(), w.chi, pre, corner="r")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("split_bf16", 1e-9)])
+def test_corner_from_r_converged_energy_matches_oracle(ctm_lib, prec, tol):
+    """The variant iterated to convergence on the Ising PEPS (beta = 0.3) in both
+    precisions: delta of every step and the bond energies against the oracle's variant."""
+    A = I.ising_site_tensor(0.3)
+    Sz = np.diag([0.5, -0.5])
+    h = np.stack([np.kron(Sz, Sz)] * 3)
+    ref = O.OracleCTM(A, 8, corner="r")
+    g = _ctm(A, 8, precision=prec, n_split=5, corner="r")
+    for k in range(30):
+        dr = ref.step()
+        dg = g.ctm_step(1)
+        assert abs(dg - dr) <= 1e-10 + 1e-7 * abs(dr), (k, dg, dr)
+    e_ref, E_ref = ref.energy(h)
+    e, E, rho = g.ctm_energy(h)
+    assert abs(E - E_ref) <= tol
+    g.close()

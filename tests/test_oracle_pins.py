@@ -310,3 +310,64 @@ def test_kitaev_variational_bound(seed, K):
     ctm.converge(200, 1e-11)
     _, E = ctm.energy(I.bond_hamiltonians(K, 0.0))
     assert E >= golden * abs(K) - 1e-12
+
+
+def test_corner_from_r_identity_and_fixed_point():
+    """Cheap corner variant C' = sym(R S)/|.|: the QR of Y = M Q_prev S gives
+    R S = Q^T M Q_prev at any step (S^2 = I; a sign factor on the wrong side or a
+    transposed R fails this), so it equals sym(Q^T M Q)/|.| once Q = Q_prev -- at the
+    fixed point of the Ising PEPS (beta = 0.3), whose kept spectrum is well separated."""
+    w = I.WORKLOADS["heis_D2_chi8"]
+    ref = O.OracleCTM(w.site_tensor(), w.chi)
+    for _ in range(3):
+        ref.step()
+    Qs = ref.warm_start()
+    S = np.where(np.diag(ref.C) < 0.0, -1.0, 1.0)
+    M = O.enlarged_corner(ref.C, ref.T, ref.a, ref.a)
+    Q, R = O.householder_qr(O.matmul(M, Qs))
+    assert np.max(np.abs(R * S[None, :] - Q.T @ M @ ref.Q)) <= 1e-13 * np.max(np.abs(R))
+    early = np.max(np.abs(O.corner_from_r(R, ref.C) - O.corner_update(M, Q)))
+    ising = O.OracleCTM(I.ising_site_tensor(0.3), 8)
+    ising.converge(300, 1e-13)
+    M = O.enlarged_corner(ising.C, ising.T, ising.a, ising.a)
+    Q, R = O.householder_qr(O.matmul(M, ising.warm_start()))
+    late = np.max(np.abs(O.corner_from_r(R, ising.C) - O.corner_update(M, Q)))
+    assert late <= 1e-9 and early > 1e3 * late
+
+
+def _zz3():
+    Sz = np.diag([0.5, -0.5])
+    hz = np.kron(Sz, Sz)
+    return np.stack([hz, hz, hz])
+
+
+def test_corner_from_r_iteration_reaches_the_same_fixed_point():
+    """Iterating with the cheap corner variant converges to the environment of the
+    standard QR-CTMRG when the kept spectrum has no near-degeneracy (Ising PEPS,
+    beta = 0.3): the converged energies and corner spectra agree."""
+    A = I.ising_site_tensor(0.3)
+    a = O.OracleCTM(A, 8)
+    b = O.OracleCTM(A, 8, corner="r")
+    na, da = a.converge(400, 1e-13)
+    nb, db = b.converge(400, 1e-13)
+    assert da < 1e-13 and db < 1e-13
+    assert abs(a.energy(_zz3())[1] - b.energy(_zz3())[1]) <= 1e-14
+    assert np.max(np.abs(a.s - b.s)) <= 1e-10
+
+
+def test_corner_from_r_is_inconsistent_while_the_basis_rotates():
+    """The variant's limitation: on the random D = 2, chi = 8 state two kept eigenvalues
+    of M are within 1 % of each other, so the orthogonal iteration turns the basis inside
+    that pair by ~1e-2 per step long after the spectrum (delta < 1e-12) has converged.
+    The standard corner Q^T M Q is covariant under that rotation; R S = Q^T M Q_prev is
+    not, and the variant settles on a different energy."""
+    w = I.WORKLOADS["heis_D2_chi8"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    a = O.OracleCTM(A, w.chi)
+    b = O.OracleCTM(A, w.chi, corner="r")
+    a.converge(400, 1e-12)
+    b.converge(400, 1e-12)
+    Qp = a.Q.copy()
+    a.step()
+    assert np.max(np.abs(a.Q - Qp)) > 1e-3
+    assert abs(a.energy(h)[1] - b.energy(h)[1]) > 1e-6
