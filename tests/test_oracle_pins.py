@@ -371,3 +371,14 @@ def test_corner_from_r_is_inconsistent_while_the_basis_rotates():
     a.step()
     assert np.max(np.abs(a.Q - Qp)) > 1e-3
     assert abs(a.energy(h)[1] - b.energy(h)[1]) > 1e-6
+
+
+def test_pad_site_tensor_embeds_and_is_seeded():
+    from paper_2509_05090_gb300.optimize import pad_site_tensor
+    A = I.random_site_tensor(2, 3, 5)
+    P1, P2 = pad_site_tensor(A, 5, 1e-2, 9), pad_site_tensor(A, 5, 1e-2, 9)
+    assert P1.shape == (2, 5, 5, 5) and np.array_equal(P1, P2)
+    assert np.array_equal(P1[:, :3, :3, :3], A)
+    rest = P1.copy()
+    rest[:, :3, :3, :3] = 0.0
+    assert 0.0 < np.max(np.abs(rest)) <= 1e-2
