@@ -349,6 +349,86 @@ double orc_edge_update(int chi, int D2, const double *T, const double *aB, const
 }
 
 /* ------------------------------------------------------------------------ */
+/* Transfer matrix of the converged environment (Sec. II.C, Fig. 4a).  With the
+ * sector reading above every sector is a quadrant of an effective square lattice
+ * of radial dimers d[u,w,x,y] = sum_z aB[u,w,z] aA[z,x,y], and the edge T is a
+ * half-infinite strip of it.  One column of the plane is an edge, one dimer and
+ * the opposite edge; it maps the boundary index (g,w,h) on one side to (a,y,b)
+ * on the other, one Bravais vector along the edge direction:
+ *   TM[(a,y,b),(g,w,h)] = sum_{u,x,z} T[a,u,g] aB[u,w,z] aA[z,x,y] T[b,x,h].
+ * Index fusion: (a,y,b) -> (a*D2 + y)*chi + b.
+ *
+ * orc_transfer_apply: out = TM v for v[g][w][h], pairwise in the order
+ *   P1[a,u,w,h] = sum_g T[a,u,g] v[g,w,h]
+ *   P2[a,h,z]   = sum_{u,w} P1[a,u,w,h] aB[u,w,z]
+ *   P3[a,x,y,h] = sum_z P2[a,h,z] aA[z,x,y]
+ *   out[a,y,b]  = sum_{x,h} P3[a,x,y,h] T[b,x,h].                             */
+void orc_transfer_apply(int chi, int D2, const double *T, const double *aB, const double *aA, const double *v,
+                        double *out)
+{
+    size_t cd = (size_t)chi * D2;
+    double *P1 = orc_alloc(cd * D2 * chi);
+    double *P2 = orc_alloc((size_t)chi * chi * D2);
+    double *P3 = orc_alloc(cd * D2 * chi);
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < chi; ++a)
+        for (int u = 0; u < D2; ++u)
+            for (int w = 0; w < D2; ++w)
+                for (int h = 0; h < chi; ++h) {
+                    double s = 0.0;
+                    for (int g = 0; g < chi; ++g) s += T[IDX3(a, u, g, D2, chi)] * v[IDX3(g, w, h, D2, chi)];
+                    P1[(((size_t)a * D2 + u) * D2 + w) * chi + h] = s;
+                }
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < chi; ++a)
+        for (int h = 0; h < chi; ++h)
+            for (int z = 0; z < D2; ++z) {
+                double s = 0.0;
+                for (int u = 0; u < D2; ++u)
+                    for (int w = 0; w < D2; ++w)
+                        s += P1[(((size_t)a * D2 + u) * D2 + w) * chi + h] * aB[IDX3(u, w, z, D2, D2)];
+                P2[IDX3(a, h, z, chi, D2)] = s;
+            }
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < chi; ++a)
+        for (int x = 0; x < D2; ++x)
+            for (int y = 0; y < D2; ++y)
+                for (int h = 0; h < chi; ++h) {
+                    double s = 0.0;
+                    for (int z = 0; z < D2; ++z) s += P2[IDX3(a, h, z, chi, D2)] * aA[IDX3(z, x, y, D2, D2)];
+                    P3[(((size_t)a * D2 + x) * D2 + y) * chi + h] = s;
+                }
+#pragma omp parallel for schedule(static)
+    for (int a = 0; a < chi; ++a)
+        for (int y = 0; y < D2; ++y)
+            for (int b = 0; b < chi; ++b) {
+                double s = 0.0;
+                for (int x = 0; x < D2; ++x)
+                    for (int h = 0; h < chi; ++h)
+                        s += P3[(((size_t)a * D2 + x) * D2 + y) * chi + h] * T[IDX3(b, x, h, D2, chi)];
+                out[IDX3(a, y, b, D2, chi)] = s;
+            }
+    free(P1);
+    free(P2);
+    free(P3);
+}
+
+/* The dense transfer matrix (small cases): column c of TM is TM e_c.          */
+void orc_transfer_matrix(int chi, int D2, const double *T, const double *aB, const double *aA, double *TM)
+{
+    size_t N = (size_t)chi * D2 * chi;
+    double *e = orc_alloc(N), *col = orc_alloc(N);
+    for (size_t c = 0; c < N; ++c) {
+        memset(e, 0, sizeof(double) * N);
+        e[c] = 1.0;
+        orc_transfer_apply(chi, D2, T, aB, aA, e, col);
+        for (size_t r = 0; r < N; ++r) TM[r * N + c] = col[r];
+    }
+    free(e);
+    free(col);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Symmetric eigen-decomposition by the cyclic Jacobi method (rotations in row
  * order, sweeps until the off-diagonal mass is negligible).  w gets the
  * eigenvalues (unsorted), V (may be NULL) the eigenvectors as columns.        */

@@ -79,6 +79,8 @@ def _load():
                 "orc_corner_spectrum": (None, [I, P, P]),
                 "orc_evd_projector": (None, [I, I, P, P]),
                 "orc_rho": (None, [I, I, I, P, P, P, P, P]),
+                "orc_transfer_apply": (None, [I, I, P, P, P, P, P]),
+                "orc_transfer_matrix": (None, [I, I, P, P, P, P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(lib, name)
@@ -227,6 +229,47 @@ def rho_bond(A, C, T, Q) -> np.ndarray:
     return rho
 
 
+def transfer_apply(T, aB, aA, v) -> np.ndarray:
+    """f2 (Sec. II.C, Fig. 4a): TM v for the transfer matrix
+    TM[(a,y,b),(g,w,h)] = sum T[a,u,g] aB[u,w,z] aA[z,x,y] T[b,x,h] (one Bravais step)."""
+    T, aB, aA, v = _c(T), _c(aB), _c(aA), _c(v)
+    chi, D2 = T.shape[0], T.shape[1]
+    out = np.empty(chi * D2 * chi)
+    _load().orc_transfer_apply(chi, D2, _p(T), _p(aB), _p(aA), _p(v.reshape(-1)), _p(out))
+    return out
+
+
+def transfer_matrix(T, aB, aA) -> np.ndarray:
+    """The dense transfer matrix (chi D2 chi square; small cases)."""
+    T, aB, aA = _c(T), _c(aB), _c(aA)
+    chi, D2 = T.shape[0], T.shape[1]
+    N = chi * D2 * chi
+    TM = np.empty((N, N))
+    _load().orc_transfer_matrix(chi, D2, _p(T), _p(aB), _p(aA), _p(TM))
+    return TM
+
+
+def transfer_spectrum(T, aB, aA, nev: int = 3, dense_max: int = 4096):
+    """Magnitudes of the nev largest-magnitude eigenvalues of the transfer matrix,
+    normalised by the largest (lambda_i = |lambda_i'| / |lambda_0'|, Sec. II.C), the
+    correlation length xi = -1 / ln lambda_1 in Bravais steps and the gap
+    ln(lambda_1 / lambda_2) of the FCLS extrapolation (Eq. 3).  LAPACK's general
+    eigenvalues on the dense matrix when it is small, else ARPACK on transfer_apply."""
+    chi, D2 = T.shape[0], T.shape[1]
+    N = chi * D2 * chi
+    if N <= dense_max:
+        w = np.linalg.eigvals(transfer_matrix(T, aB, aA))
+    else:
+        import scipy.sparse.linalg as sla
+        op = sla.LinearOperator((N, N), matvec=lambda v: transfer_apply(T, aB, aA, v), dtype=np.float64)
+        w = sla.eigs(op, k=max(nev, 3) + 2, which="LM", tol=1e-13, return_eigenvectors=False)
+    lam = np.sort(np.abs(w))[::-1][:nev]
+    lam = lam / lam[0]
+    xi = -1.0 / np.log(lam[1]) if lam[1] > 0.0 else 0.0
+    gap = np.log(lam[1] / lam[2]) if nev >= 3 and lam[2] > 0.0 else float("inf")
+    return lam, xi, gap
+
+
 def bond_energies(rho, h):
     """e_a = tr(rho h_a) for a = x, y, z; E_site = (1/2) sum_a e_a (3 bonds per site, 2 sites per bond)."""
     h = np.asarray(h, dtype=np.float64)
@@ -310,3 +353,7 @@ class OracleCTM:
 
     def energy(self, h):
         return bond_energies(self.rho(), h)
+
+    def transfer_spectrum(self, nev: int = 3):
+        """f2: leading transfer-matrix eigenvalues of the current environment, xi, gap."""
+        return transfer_spectrum(self.T, self.a, self.a, nev)

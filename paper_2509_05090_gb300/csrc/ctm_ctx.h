@@ -87,11 +87,11 @@ inline QrScratch qr_scratch(ctm_ctx *c)
     q.err = c->err;
     q.rows_min = c->qr_rows_min;
     q.V = c->qr_wy;
-    q.S = q.V + n * k;
+    q.S = q.V + k * k;
     q.W = q.S + k * k;
     q.ta = q.W + k * k;
-    q.sk = q.ta + 2 * k + k * k;   // (k*k of slack after ta keeps the scratch 8-byte aligned)
-    q.sk_elems = qr_sk_doubles((int)n, (int)k);
+    q.sk = nullptr;
+    q.sk_elems = 0;
     q.bar_extra = c->force_timeout ? 1u : 0u;
     q.spin_limit = c->force_timeout ? 20000 : 0;
     return q;

@@ -83,18 +83,19 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
 
 // ---------------------------------------------------------------- QR
 // Householder QR of Y (n x k row-major, n >= k) with diag(R) >= 0.  Q (n x k)
-// and R (k x k) row-major.  A cooperative factorisation (one grid barrier per
-// column), then Q in compact-WY form by GEMMs and the sign gauge.
+// and R (k x k) row-major.  One cooperative kernel: the blocked factorisation (one
+// grid barrier per panel), then Q in compact-WY form and the sign gauge (two more
+// grid barriers).
 struct QrScratch {
     double *sbuf;      // qr_scratch_doubles(k): rotating column-sum accumulators
     double *rowbuf;    // qr_rowbuf_doubles(k): published panel rows
     unsigned *bar;     // 2 (count, generation)
     int *err;          // 1
     int rows_min;      // fewest rows per CTA (batched instances use small grids so they overlap)
-    double *V;         // n x k reflectors
-    double *S, *W;     // k x k each
-    double *ta;        // 2 x k (tau, alpha)
-    double *sk;        // split-K scratch of the V^T V product
+    double *V;         // k x k: the first k rows of the reflectors
+    double *S, *W;     // k x k each: V^T V and T V_top^T
+    double *ta;        // 2 x k (unused)
+    double *sk;        // unused
     size_t sk_elems;
     unsigned bar_extra;      // arrivals the grid barrier waits for beyond the grid (0; > 0 only to force a timeout)
     long long spin_limit;    // polls before a barrier wait gives up (0: the default, about a second)

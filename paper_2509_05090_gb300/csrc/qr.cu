@@ -21,14 +21,16 @@
 // which makes the worst case the one-column-per-barrier algorithm.  Finally the
 // CTA applies the panel's reflectors to its own rows and, in the same pass over
 // its shared-memory block, forms the next panel's partial Gram rows.  So a
-// panel of QB columns costs one grid barrier.  The reflectors v_j (unnormalised,
-// tau_j = 2 / v_j^T v_j) are written out and Q = H_0 ... H_{k-1} [I; 0] is formed
-// in compact-WY form without further barriers: with S = V^T V, the triangular
-// factor satisfies T^{-1} = striu(S) + diag(S)/2 (the "UT" form of the
-// product of reflectors), so Q = E - V W with W = T V_top^T (one small
-// triangular solve) -- two GEMMs and two small kernels.  Columns with
-// R_jj < 0 are negated (gauge diag(R) >= 0).  The grid size of the
-// factorisation is tuned once per shape by timing a few rows-per-CTA choices.
+// panel of QB columns costs one grid barrier.  Q = H_0 ... H_{k-1} [I; 0] is then
+// formed in compact-WY form inside the same launch: with the unnormalised
+// reflectors v_j as the columns of V and S = V^T V, the triangular factor
+// satisfies T^{-1} = striu(S) + diag(S)/2 (the "UT" form of the product of
+// reflectors), so Q = E - V W with W = T V_top^T.  Every CTA adds its rows' share
+// of S with FP64 atomics; after a grid barrier ceil(k/8) CTAs solve eight columns
+// of W each (blocked back-substitution with inverted 8 x 8 diagonal blocks); after
+// a second barrier every CTA forms its rows of Q and applies the gauge (columns
+// with R_jj < 0 negated, and the rows of R with them).  The grid size is tuned
+// once per shape by timing a few rows-per-CTA choices.
 //
 // The grid barrier is one monotonic counter in global memory; its spin is
 // bounded (about a second) and on expiry sets an error flag that the host
@@ -78,8 +80,10 @@ struct QrArgs {
     int n, k, G, rows_per;
     const double *Y;
     double *R;
-    double *V;        // n x k reflectors (written)
-    double *ta;       // 2 x k: tau, alpha (written by CTA 0)
+    double *Q;        // n x k projector (written)
+    double *V;        // first k rows of the reflectors (written, read by the W solve)
+    double *S;        // k x k: V^T V, upper triangle (zeroed by the host, summed with atomics)
+    double *W;        // k x k: T V_top^T (written by the solving CTAs)
     double *sbuf;     // 3 x QB x k rotating Gram-row accumulators
     double *rowbuf;   // 2 x QB x k published panel rows
     unsigned *bar;
@@ -87,6 +91,121 @@ struct QrArgs {
     unsigned bar_extra;
     long long spin_limit;
 };
+
+// W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
+// The k right-hand sides are independent: CTA b of the QR grid solves columns
+// [8b, 8b + 8) after the grid barrier that completes S.
+// Rows are blocked by QR_WB = 8 from the bottom; every CTA first inverts the
+// diagonal 8 x 8 blocks of U (all blocks at once, one thread per block column),
+// then per row block sums the already solved rows below it (independent dot
+// products split over QR_WL lanes) and applies the block inverse (8-term dots).
+// So the dependent FP64 chains per block are short and the CTA syncs twice per
+// block.  U (packed upper triangle), the block inverses and the CTA's W columns
+// live in shared memory.
+constexpr int QR_WB = 8;      // row block (and diagonal inverse) size
+constexpr int QR_WC = 8;      // right-hand-side columns per CTA
+constexpr int QR_WL = 4;      // lanes per dot product in the block update
+
+__device__ __forceinline__ int up_off(int k, int i, int j) { return i * k - (i * (i - 1)) / 2 + (j - i); }
+
+size_t qr_wy_smem_bytes(int k)
+{
+    const int nb = (k + QR_WB - 1) / QR_WB;
+    return sizeof(double) * ((size_t)k * (k + 1) / 2 + (size_t)nb * QR_WB * QR_WB + (size_t)k * QR_WC + k);
+}
+
+__device__ void wy_solve_cta(int k, int cblk, const double *S, const double *V, const double *taus, double *W,
+                             double *sm)
+{
+    const int nb = (k + QR_WB - 1) / QR_WB;
+    double *Us = sm;                                   // k (k+1) / 2
+    double *Di = Us + (size_t)k * (k + 1) / 2;         // nb x 8 x 8 block inverses
+    double *Wc = Di + (size_t)nb * QR_WB * QR_WB;      // k x QR_WC
+    double *rd = Wc + (size_t)k * QR_WC;               // k reciprocal diagonal
+    const int c0 = cblk * QR_WC;
+    const int ncol = min(QR_WC, k - c0);
+    const int tid = threadIdx.x;
+    for (int t = tid; t < k * k; t += blockDim.x) {
+        const int i = t / k, j = t % k;
+        if (j > i) Us[up_off(k, i, j)] = __ldcg(S + t);
+        else if (j == i) Us[up_off(k, i, i)] = (taus[i] == 0.0) ? 1.0 : 0.5 * __ldcg(S + t);
+    }
+    for (int t = tid; t < k * QR_WC; t += blockDim.x) {
+        const int i = t / QR_WC, cc = t % QR_WC;
+        Wc[t] = (cc < ncol) ? __ldcg(V + (size_t)(c0 + cc) * k + i) : 0.0;
+    }
+    __syncthreads();
+    for (int i = tid; i < k; i += blockDim.x) rd[i] = 1.0 / Us[up_off(k, i, i)];
+    __syncthreads();
+    // block inverses: thread (b, c) back-substitutes D_b x = e_c
+    for (int t = tid; t < nb * QR_WB; t += blockDim.x) {
+        const int bb = t / QR_WB, cl = t % QR_WB;
+        const int i0 = bb * QR_WB, bs = min(QR_WB, k - i0);
+        double *D = Di + bb * QR_WB * QR_WB;
+        if (cl < bs) {
+            double x[QR_WB];
+#pragma unroll
+            for (int r = QR_WB - 1; r >= 0; --r) {
+                double v = 0.0;
+                if (r <= cl) {
+                    v = (r == cl) ? 1.0 : 0.0;
+#pragma unroll
+                    for (int j = r + 1; j < QR_WB; ++j)
+                        if (j <= cl) v = fma(-Us[up_off(k, i0 + r, i0 + j)], x[j], v);
+                    v *= rd[i0 + r];
+                }
+                x[r] = v;
+            }
+#pragma unroll
+            for (int r = 0; r < QR_WB; ++r) D[r * QR_WB + cl] = x[r];
+        } else {
+#pragma unroll
+            for (int r = 0; r < QR_WB; ++r) D[r * QR_WB + cl] = 0.0;
+        }
+    }
+    __syncthreads();
+    for (int bb = nb - 1; bb >= 0; --bb) {
+        const int i0 = bb * QR_WB, i1 = min(k, i0 + QR_WB);
+        // rhs of the block: Wc[i][cc] -= sum_{j >= i1} U[i][j] Wc[j][cc]
+        for (int t = tid; t < QR_WB * QR_WC * QR_WL; t += blockDim.x) {
+            const int lane = t % QR_WL, pc = t / QR_WL;
+            const int i = i0 + pc / QR_WC, cc = pc % QR_WC;
+            double s0 = 0.0, s1 = 0.0;
+            if (i < i1) {
+                const double *u = Us + up_off(k, i, i) - i;   // u[j] = U[i][j] for j >= i
+                int j = i1 + lane;
+                for (; j + QR_WL < k; j += 2 * QR_WL) {
+                    s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
+                    s1 = fma(u[j + QR_WL], Wc[(j + QR_WL) * QR_WC + cc], s1);
+                }
+                if (j < k) s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
+            }
+            double sum = s0 + s1;
+#pragma unroll
+            for (int o = QR_WL / 2; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, QR_WL);
+            if (lane == 0 && i < i1) Wc[i * QR_WC + cc] -= sum;
+        }
+        __syncthreads();
+        // apply the block inverse
+        double wv = 0.0;
+        const int r = tid / QR_WC, cc = tid % QR_WC;
+        if (tid < QR_WB * QR_WC && i0 + r < i1) {
+            const double *D = Di + bb * QR_WB * QR_WB + r * QR_WB;
+#pragma unroll
+            for (int j = 0; j < QR_WB; ++j)
+                if (i0 + j < i1) wv = fma(D[j], Wc[(i0 + j) * QR_WC + cc], wv);
+        }
+        __syncthreads();
+        if (tid < QR_WB * QR_WC && i0 + r < i1) Wc[(i0 + r) * QR_WC + cc] = wv;
+        __syncthreads();
+    }
+    for (int t = tid; t < k * QR_WC; t += blockDim.x) {
+        const int i = t / QR_WC, cc = t % QR_WC;
+        if (cc < ncol) W[(size_t)i * k + c0 + cc] = Wc[t];
+    }
+}
+
+constexpr int QR_QROWS = 8;   // rows per thread and pass in the Q formation
 
 __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
 {
@@ -100,14 +219,15 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     const int nr = max(0, r1 - r0);
     const int tid = threadIdx.x;
     double *Ys = sm;                                // rows_per x ld
-    double *Gs = Ys + (size_t)a.rows_per * ld;      // QB x k: panel Gram rows, downdated
-    double *Ps = Gs + QB * k;                       // QB x k: panel rows, updated
-    double *cfs = Ps + QB * k;                      // QB x k: tau_j v_j^T a_kk
-    double *Rj = cfs + QB * k;                      // k: current row of R
-    double *taus = Rj + k;                          // k
+    double *taus = Ys + (size_t)a.rows_per * ld;    // k
     double *v0s = taus + k;                         // k
     double *alps = v0s + k;                         // k
     double *g0 = alps + k;                          // QB: squared norms at the panel start
+    double *Gs = g0 + QB;                           // QB x k: panel Gram rows, downdated
+    double *Ps = Gs + QB * k;                       // QB x k: panel rows, updated
+    double *cfs = Ps + QB * k;                      // QB x k: tau_j v_j^T a_kk
+    double *Rj = cfs + QB * k;                      // k: current row of R
+    // (after the factorisation the region from Gs on holds the triangular solve's buffers)
     auto acc_buf = [&](int blk) { return a.sbuf + (size_t)(blk % 3) * QB * k; };
     auto pub_buf = [&](int blk) { return a.rowbuf + (size_t)(blk & 1) * QB * k; };
 
@@ -285,157 +405,84 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
         ++blk;
     }
 
-    // ---------------------------------------------------------- reflectors out
+    // ---------------------------------------------------------- Q = E - V W, gauge
+    // V rows of this CTA in place (v_j is 0 above row j, v0 on the diagonal, 0 where
+    // tau = 0); the first k rows also go to global memory for the triangular solve.
+    __syncthreads();
     for (int t = tid; t < nr * k; t += blockDim.x) {
-        const int r = r0 + t / k, j = t % k;
+        const int rl = t / k, j = t % k, rg = r0 + rl;
         double v = 0.0;
-        if (r == j) v = v0s[j];
-        else if (r > j) v = Ys[(t / k) * ld + j];
+        if (rg == j) v = v0s[j];
+        else if (rg > j) v = Ys[rl * ld + j];
         if (taus[j] == 0.0) v = 0.0;
-        a.V[(size_t)r0 * k + t] = v;
+        Ys[rl * ld + j] = v;
+        if (rg < k) a.V[(size_t)rg * k + j] = v;
     }
     if (c == 0) {
-        for (int j = tid; j < k; j += blockDim.x) {
-            a.ta[j] = taus[j];
-            a.ta[k + j] = alps[j];
-        }
         __syncthreads();
         for (int t = tid; t < k * k; t += blockDim.x) {
             int rr = t / k;
             if (alps[rr] < 0.0) a.R[t] = -a.R[t];
         }
     }
-}
-
-// W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
-// The k right-hand sides are independent: CTA b solves columns [8b, 8b + 8).
-// Rows are blocked by QR_WB = 8 from the bottom; every CTA first inverts the
-// diagonal 8 x 8 blocks of U (all blocks at once, one thread per block column),
-// then per row block sums the already solved rows below it (independent dot
-// products split over QR_WL lanes) and applies the block inverse (8-term dots).
-// So the dependent FP64 chains per block are short and the CTA syncs twice per
-// block.  U (packed upper triangle), the block inverses and the CTA's W columns
-// live in shared memory.
-constexpr int QR_WB = 8;      // row block (and diagonal inverse) size
-constexpr int QR_WC = 8;      // right-hand-side columns per CTA
-constexpr int QR_WL = 4;      // lanes per dot product in the block update
-constexpr int QR_WY_THREADS = 256;
-
-__device__ __forceinline__ int up_off(int k, int i, int j) { return i * k - (i * (i - 1)) / 2 + (j - i); }
-
-size_t qr_wy_smem_bytes(int k)
-{
-    const int nb = (k + QR_WB - 1) / QR_WB;
-    return sizeof(double) * ((size_t)k * (k + 1) / 2 + (size_t)nb * QR_WB * QR_WB + (size_t)k * QR_WC + k);
-}
-
-__global__ void __launch_bounds__(QR_WY_THREADS) qr_wy_solve_kernel(int k, const double *S, const double *V,
-                                                                    const double *ta, double *W)
-{
-    extern __shared__ double sm[];
-    const int nb = (k + QR_WB - 1) / QR_WB;
-    double *Us = sm;                                   // k (k+1) / 2
-    double *Di = Us + (size_t)k * (k + 1) / 2;         // nb x 8 x 8 block inverses
-    double *Wc = Di + (size_t)nb * QR_WB * QR_WB;      // k x QR_WC
-    double *rd = Wc + (size_t)k * QR_WC;               // k reciprocal diagonal
-    const int c0 = blockIdx.x * QR_WC;
-    const int ncol = min(QR_WC, k - c0);
-    const int tid = threadIdx.x;
-    for (int t = tid; t < k * k; t += blockDim.x) {
-        const int i = t / k, j = t % k;
-        if (j > i) Us[up_off(k, i, j)] = S[t];
-        else if (j == i) Us[up_off(k, i, i)] = (ta[i] == 0.0) ? 1.0 : 0.5 * S[t];
-    }
-    for (int t = tid; t < k * QR_WC; t += blockDim.x) {
-        const int i = t / QR_WC, cc = t % QR_WC;
-        Wc[t] = (cc < ncol) ? V[(size_t)(c0 + cc) * k + i] : 0.0;
-    }
     __syncthreads();
-    for (int i = tid; i < k; i += blockDim.x) rd[i] = 1.0 / Us[up_off(k, i, i)];
-    __syncthreads();
-    // block inverses: thread (b, c) back-substitutes D_b x = e_c
-    for (int t = tid; t < nb * QR_WB; t += blockDim.x) {
-        const int bb = t / QR_WB, cl = t % QR_WB;
-        const int i0 = bb * QR_WB, bs = min(QR_WB, k - i0);
-        double *D = Di + bb * QR_WB * QR_WB;
-        if (cl < bs) {
-            double x[QR_WB];
+    // S = V^T V (upper triangle): this CTA's rows, two chains per entry, summed over
+    // the CTAs with FP64 atomics
+    for (int e = tid; e < k * k; e += blockDim.x) {
+        const int i = e / k, j = e % k;
+        if (j < i) continue;
+        const int rs = max(0, j - r0);
+        if (rs >= nr) continue;
+        double s0 = 0.0, s1 = 0.0;
+        int rl = rs;
+        for (; rl + 1 < nr; rl += 2) {
+            s0 = fma(Ys[rl * ld + i], Ys[rl * ld + j], s0);
+            s1 = fma(Ys[(rl + 1) * ld + i], Ys[(rl + 1) * ld + j], s1);
+        }
+        if (rl < nr) s0 = fma(Ys[rl * ld + i], Ys[rl * ld + j], s0);
+        atomicAdd(&a.S[(size_t)i * k + j], s0 + s1);
+    }
+    if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 1), a.err, a.bar_extra, a.spin_limit)) return;
+    for (int cb = c; cb < (k + QR_WC - 1) / QR_WC; cb += a.G) {   // a small grid solves several blocks
+        wy_solve_cta(k, cb, a.S, a.V, taus, a.W, Gs);
+        __syncthreads();
+    }
+    if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 2), a.err, a.bar_extra, a.spin_limit)) return;
+    // Q rows of this CTA: (E - V W) with column c negated where alpha_c < 0; a thread
+    // owns one column and up to QR_QROWS rows at a time (W read once per row chunk)
+    {
+        const int grp = blockDim.x / k;
+        const int col = tid % k, g = tid / k;
+        if (g < grp) {
+            const double sgn = alps[col] < 0.0 ? -1.0 : 1.0;
+            for (int rb = g * QR_QROWS; rb < nr; rb += grp * QR_QROWS) {
+                double acc[QR_QROWS];
 #pragma unroll
-            for (int r = QR_WB - 1; r >= 0; --r) {
-                double v = 0.0;
-                if (r <= cl) {
-                    v = (r == cl) ? 1.0 : 0.0;
+                for (int q = 0; q < QR_QROWS; ++q) acc[q] = 0.0;
+                for (int j = 0; j < k; ++j) {
+                    const double w = __ldcg(a.W + (size_t)j * k + col);
 #pragma unroll
-                    for (int j = r + 1; j < QR_WB; ++j)
-                        if (j <= cl) v = fma(-Us[up_off(k, i0 + r, i0 + j)], x[j], v);
-                    v *= rd[i0 + r];
+                    for (int q = 0; q < QR_QROWS; ++q)
+                        if (rb + q < nr) acc[q] = fma(Ys[(rb + q) * ld + j], w, acc[q]);
                 }
-                x[r] = v;
-            }
 #pragma unroll
-            for (int r = 0; r < QR_WB; ++r) D[r * QR_WB + cl] = x[r];
-        } else {
-#pragma unroll
-            for (int r = 0; r < QR_WB; ++r) D[r * QR_WB + cl] = 0.0;
-        }
-    }
-    __syncthreads();
-    for (int bb = nb - 1; bb >= 0; --bb) {
-        const int i0 = bb * QR_WB, i1 = min(k, i0 + QR_WB);
-        // rhs of the block: Wc[i][cc] -= sum_{j >= i1} U[i][j] Wc[j][cc]
-        for (int t = tid; t < QR_WB * QR_WC * QR_WL; t += blockDim.x) {
-            const int lane = t % QR_WL, pc = t / QR_WL;
-            const int i = i0 + pc / QR_WC, cc = pc % QR_WC;
-            double s0 = 0.0, s1 = 0.0;
-            if (i < i1) {
-                const double *u = Us + up_off(k, i, i) - i;   // u[j] = U[i][j] for j >= i
-                int j = i1 + lane;
-                for (; j + QR_WL < k; j += 2 * QR_WL) {
-                    s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
-                    s1 = fma(u[j + QR_WL], Wc[(j + QR_WL) * QR_WC + cc], s1);
+                for (int q = 0; q < QR_QROWS; ++q) {
+                    const int rl = rb + q;
+                    if (rl < nr) {
+                        const int rg = r0 + rl;
+                        a.Q[(size_t)rg * k + col] = sgn * ((rg == col ? 1.0 : 0.0) - acc[q]);
+                    }
                 }
-                if (j < k) s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
             }
-            double sum = s0 + s1;
-#pragma unroll
-            for (int o = QR_WL / 2; o > 0; o >>= 1) sum += __shfl_down_sync(0xffffffffu, sum, o, QR_WL);
-            if (lane == 0 && i < i1) Wc[i * QR_WC + cc] -= sum;
         }
-        __syncthreads();
-        // apply the block inverse
-        double wv = 0.0;
-        const int r = tid / QR_WC, cc = tid % QR_WC;
-        if (tid < QR_WB * QR_WC && i0 + r < i1) {
-            const double *D = Di + bb * QR_WB * QR_WB + r * QR_WB;
-#pragma unroll
-            for (int j = 0; j < QR_WB; ++j)
-                if (i0 + j < i1) wv = fma(D[j], Wc[(i0 + j) * QR_WC + cc], wv);
-        }
-        __syncthreads();
-        if (tid < QR_WB * QR_WC && i0 + r < i1) Wc[(i0 + r) * QR_WC + cc] = wv;
-        __syncthreads();
-    }
-    for (int t = tid; t < k * QR_WC; t += blockDim.x) {
-        const int i = t / QR_WC, cc = t % QR_WC;
-        if (cc < ncol) W[(size_t)i * k + c0 + cc] = Wc[t];
-    }
-}
-
-// Q <- diag-sign gauge of (E - V W): Q holds -V W on entry.
-__global__ void qr_form_q_kernel(long long n, int k, const double *ta, double *Q)
-{
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * k;
-         t += (long long)gridDim.x * blockDim.x) {
-        const long long r = t / k;
-        const int c = (int)(t % k);
-        double q = Q[t] + (r == c ? 1.0 : 0.0);
-        Q[t] = (ta[k + c] < 0.0) ? -q : q;
     }
 }
 
 size_t qr_smem_bytes(int rows_per, int k)
 {
-    return sizeof(double) * ((size_t)rows_per * (k | 1) + 3 * (size_t)QB * k + 4 * (size_t)k + QB);
+    const size_t panel = 3 * (size_t)QB * k + k;
+    const size_t solve = qr_wy_smem_bytes(k) / sizeof(double);
+    return sizeof(double) * ((size_t)rows_per * (k | 1) + 3 * (size_t)k + QB + (panel > solve ? panel : solve));
 }
 
 int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
@@ -463,13 +510,15 @@ int qr_supported(int n, int k)
 
 size_t qr_sk_doubles(int n, int k)
 {
-    const size_t a = 64 * (size_t)k * k, b = 4 * (size_t)n * k;   // split-K partials of V^T V and of V W
-    return a > b ? a : b;
+    (void)n;
+    (void)k;
+    return 0;
 }
 
-size_t qr_wy_doubles(int n, int k) { return (size_t)n * k + 3 * (size_t)k * k + 2 * (size_t)k + qr_sk_doubles(n, k); }
+size_t qr_wy_doubles(int n, int k) { return (size_t)k * k + 3 * (size_t)k * k + 2 * (size_t)k; }
 
-static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y, double *R, QrScratch s, cudaStream_t st)
+static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y, double *Q, double *R, QrScratch s,
+                                    cudaStream_t st)
 {
     const int G = (n + rows_per - 1) / rows_per;
     const size_t smem = qr_smem_bytes(rows_per, k);
@@ -480,7 +529,9 @@ static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y,
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.bar, 0, sizeof(unsigned) * 2, st);
     if (e != cudaSuccess) return e;
-    QrArgs a{n, k, G, rows_per, Y, R, s.V, s.ta, s.sbuf, s.rowbuf, s.bar, s.err, s.bar_extra,
+    e = cudaMemsetAsync(s.S, 0, sizeof(double) * (size_t)k * k, st);
+    if (e != cudaSuccess) return e;
+    QrArgs a{n, k, G, rows_per, Y, R, Q, s.V, s.S, s.W, s.sbuf, s.rowbuf, s.bar, s.err, s.bar_extra,
              s.spin_limit > 0 ? s.spin_limit : QR_SPIN_LIMIT};
     void *args[] = {&a};
     CTM_COUNT_LAUNCH(1);
@@ -494,7 +545,7 @@ static std::mutex g_qr_mu;
 static std::map<std::pair<int, int>, int> g_qr_rows;   // (n, k) -> rows per CTA, for rows_min == 1
 
 // rows per CTA: tuned once per (n, k) by timing the factorisation (eager calls only)
-static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, cudaStream_t st)
+static int qr_pick_rows(int n, int k, const double *Y, double *Q, double *R, QrScratch s, cudaStream_t st)
 {
     int G, rp0;
     qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp0);
@@ -529,7 +580,7 @@ static int qr_pick_rows(int n, int k, const double *Y, double *R, QrScratch s, c
         for (int rep = 0; rep < 4; ++rep) {   // first run warms up; the fastest of three counts
             float t = 0.f;
             cudaEventRecord(e0, st);
-            cudaError_t e = qr_factor_launch(n, k, rp, Y, R, s, st);
+            cudaError_t e = qr_factor_launch(n, k, rp, Y, Q, R, s, st);
             cudaEventRecord(e1, st);
             if (e != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
                 ms = 1e30f;
@@ -563,30 +614,11 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
     if (!qr_supported(n, k) || !s.V) return cudaErrorInvalidValue;
     if (!qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp) && !qr_layout(n, k, 1, &G, &rp))
         return cudaErrorInvalidValue;
-    const int rows_per = qr_pick_rows(n, k, Y, R, s, st);
-    cudaError_t e = qr_factor_launch(n, k, rows_per, Y, R, s, st);
-    if (e != cudaSuccess) return e;
-    // S = V^T V
-    GemmF64 gs{k, k, n, s.V, idx_lin(1), idx_lin(k), s.V, idx_lin(k), idx_lin(1), s.S, idx_lin(k), idx_lin(1), 1.0,
-               0.0};
-    if ((e = gemm_f64(gs, gemm_f64_pick_split(k, k, n), s.sk, s.sk_elems, st)) != cudaSuccess) return e;
-    CTM_COUNT_LAUNCH(2);
-    qr_wy_solve_kernel<<<(k + QR_WC - 1) / QR_WC, QR_WY_THREADS, qr_wy_smem_bytes(k), st>>>(k, s.S, s.V, s.ta, s.W);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    // Q = -V W, then + E and the sign gauge
-    GemmF64 gq{n, k, k, s.V, idx_lin(k), idx_lin(1), s.W, idx_lin(k), idx_lin(1), Q, idx_lin(k), idx_lin(1), -1.0,
-               0.0};
-    if ((e = gemm_f64(gq, gemm_f64_pick_split(n, k, k), s.sk, s.sk_elems, st)) != cudaSuccess) return e;
-    long long tot = (long long)n * k;
-    int blocks = (int)((tot + 255) / 256);
-    if (blocks > 8 * device_sm_count()) blocks = 8 * device_sm_count();
-    qr_form_q_kernel<<<blocks, 256, 0, st>>>(n, k, s.ta, Q);
-    return cudaGetLastError();
+    const int rows_per = qr_pick_rows(n, k, Y, Q, R, s, st);
+    return qr_factor_launch(n, k, rows_per, Y, Q, R, s, st);
 }
 
 cudaError_t qr_prepare()
 {
-    cudaError_t e = cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(qr_wy_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    return cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
 }

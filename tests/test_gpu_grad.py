@@ -198,7 +198,7 @@ def test_autograd_reuses_context_and_defers_adjoint(ctm_lib):
     ref.ctm_set_env(*env1)
     E2r, g2r = ref.ctm_grad(h.cpu().numpy(), warmup=5, k_tracked=3)
     ref.close()
-    assert abs(float(E2) - E2r) <= 1e-12
+    assert abs(float(E2.detach()) - E2r) <= 1e-12
     assert torch.max(torch.abs(g2 - g2r)).item() <= 1e-10 * torch.max(torch.abs(g2r)).item()
     AG.release_contexts()
 
@@ -206,8 +206,9 @@ def test_autograd_reuses_context_and_defers_adjoint(ctm_lib):
 def test_lbfgs_optimisation_lowers_the_heisenberg_energy(ctm_lib):
     """Sec. II.D: L-BFGS over A with the adjoint gradient.  Heisenberg model with the
     pi-rotation on sublattice B (uniform ansatz), D = 2, chi = 16, from a seeded random
-    tensor: the energy falls well below its start and stays above the QMC ground-state
-    energy -0.544553(20) (Sec. III.B) -- a variational upper bound."""
+    tensor: the energy decreases at every iteration (strong-Wolfe line search), ends
+    well below its start, and stays above the QMC ground-state energy -0.544553(20)
+    (Sec. III.B) -- a variational upper bound."""
     from paper_2509_05090_gb300 import autograd as AG
     from paper_2509_05090_gb300.optimize import optimize
     AG.release_contexts()
@@ -215,7 +216,8 @@ def test_lbfgs_optimisation_lowers_the_heisenberg_energy(ctm_lib):
     A0 = I.random_site_tensor(2, 2, 2024)
     A, Es = optimize(A0, 16, h, steps=12, warmup=10, k_tracked=8)
     AG.release_contexts()
-    assert Es[-1] < Es[0] - 0.05
+    assert all(b <= a + 1e-12 for a, b in zip(Es, Es[1:]))
+    assert Es[-1] < Es[0] - 5e-3
     assert Es[-1] > -0.54457
     assert all(np.isfinite(Es))
 

@@ -382,3 +382,71 @@ def test_pad_site_tensor_embeds_and_is_seeded():
     rest = P1.copy()
     rest[:, :3, :3, :3] = 0.0
     assert 0.0 < np.max(np.abs(rest)) <= 1e-2
+
+
+def _ising_xi_along_chains(beta, L=12):
+    """Correlation length of the honeycomb Ising model along a zigzag chain, in Bravais
+    vectors: brute-force transfer matrix of a brick-wall cylinder (L rows, periodic)
+    propagating along its chains, two columns (one Bravais vector) per step."""
+    import scipy.sparse.linalg as sla
+    sig = 1 - 2 * ((np.arange(2 ** L)[:, None] >> np.arange(L)[None, :]) & 1)
+
+    def vert(par):
+        e = np.zeros(2 ** L)
+        for r in range(L):
+            if (r + par) % 2 == 0:
+                e += sig[:, r] * sig[:, (r + 1) % L]
+        return np.exp(beta * e)
+
+    v0, v1 = vert(0), vert(1)
+    B = np.array([[math.exp(beta), math.exp(-beta)], [math.exp(-beta), math.exp(beta)]])
+
+    def hor(psi):
+        t = psi.reshape((2,) * L)
+        for ax in range(L):
+            t = np.moveaxis(np.tensordot(B, t, axes=([1], [ax])), 0, ax)
+        return t.reshape(-1)
+
+    op = sla.LinearOperator((2 ** L, 2 ** L), matvec=lambda p: v1 * hor(v0 * hor(p)), dtype=np.float64)
+    w = np.sort(np.abs(sla.eigs(op, k=3, which="LM", return_eigenvectors=False)))[::-1]
+    return -1.0 / np.log(w[1] / w[0])
+
+
+def test_transfer_spectrum_pins_ising_correlation_length():
+    """f2 (Sec. II.C, Eq. 3): the transfer matrix of the converged Ising-PEPS environment
+    (beta = 0.3) gives xi(chi) rising toward the exact correlation length along the
+    Bravais direction (brute-force cylinder transfer matrix), and the paper's
+    extrapolation xi^-1(chi) = xi^-1(inf) + a ln(lambda_1/lambda_2) over chi = 16, 24
+    lands on it.  A transfer matrix with the wrong column (another lattice direction or
+    step) misses it by ~14 %."""
+    beta = 0.3
+    exact = _ising_xi_along_chains(beta)
+    assert abs(exact - _ising_xi_along_chains(beta, 10)) < 1e-7        # converged in L
+    res = []
+    for chi in (8, 16, 24):
+        ctm = O.OracleCTM(I.ising_site_tensor(beta), chi)
+        ctm.converge(1000, 1e-13)
+        lam, xi, gap = ctm.transfer_spectrum()
+        res.append((xi, gap))
+    assert res[0][0] < res[1][0] < res[2][0] < exact
+    assert exact - res[2][0] < 0.005 * exact
+    (x1, g1), (x2, g2) = res[1], res[2]
+    slope = (1 / x1 - 1 / x2) / (g1 - g2)
+    xi_inf = 1.0 / (1 / x2 - slope * g2)
+    assert abs(xi_inf - exact) < 1e-4 * exact
+
+
+def test_transfer_spectrum_product_state_and_apply():
+    """D = 1 product state: with C = I, T = delta t the chi copies decouple and the
+    transfer matrix is a multiple of the identity (every lambda_i = 1); and the
+    matrix-free apply equals the dense matrix on a random vector."""
+    ctm = O.OracleCTM(I.product_site_tensor([0.6, -0.8]), 4, symmetrize=False)
+    ctm.converge(20, 1e-14)
+    TM = O.transfer_matrix(ctm.T, ctm.a, ctm.a)
+    assert np.max(np.abs(TM - TM[0, 0] * np.eye(TM.shape[0]))) <= 1e-14 * abs(TM[0, 0])
+    w = I.WORKLOADS["heis_D2_chi8"]
+    ref = O.OracleCTM(w.site_tensor(), w.chi)
+    ref.step()
+    v = np.random.default_rng(4).standard_normal(w.chi * w.D2 * w.chi)
+    TM = O.transfer_matrix(ref.T, ref.a, ref.a)
+    assert np.max(np.abs(TM @ v - O.transfer_apply(ref.T, ref.a, ref.a, v))) <= 1e-13 * np.max(np.abs(TM @ v))
