@@ -336,7 +336,7 @@ def energy_vs_oracle(w, precision, n_split, steps):
     return E, ref.energy(h)[1]
 
 
-def time_to_converged(w, precision, n_split, max_steps, corner="qmq"):
+def time_to_converged(w, precision, n_split, max_steps, corner="qmq", spectrum=False):
     """Wall time from ctm_init to a converged environment (delta < tol, read back every
     step) and the energy there."""
     import torch
@@ -349,8 +349,17 @@ def time_to_converged(w, precision, n_split, max_steps, corner="qmq"):
     torch.cuda.synchronize()
     secs = time.perf_counter() - t0
     _, E, _ = g.ctm_energy(h)
+    rec = {"steps": nst, "delta": dl, "converged": ok, "seconds": secs, "E_site": E}
+    if spectrum:
+        # transfer-matrix spectrum of the converged environment (Sec. II.C, Eq. 3)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        lam, xi, gap, iters, sok = g.ctm_transfer_spectrum(nev=3, max_iter=1000)
+        rec["transfer_spectrum"] = {"lambda": [float(x) for x in lam], "xi_bravais": xi,
+                                    "ln_lambda1_over_lambda2": gap, "iterations": iters, "converged": sok,
+                                    "seconds": time.perf_counter() - t1}
     g.close()
-    return {"steps": nst, "delta": dl, "converged": ok, "seconds": secs, "E_site": E}
+    return rec
 
 
 def fp64_step_record(w, steps, fp64_peak):
@@ -550,7 +559,7 @@ def main():
         if wc is not None:
             from oracle import oracle as orc
             conv = {"workload": wc.name, "tol": wc.tol,
-                    "mixed": time_to_converged(wc, args.precision, args.n_split, wc.steps),
+                    "mixed": time_to_converged(wc, args.precision, args.n_split, wc.steps, spectrum=True),
                     "fp64": time_to_converged(wc, "fp64", args.n_split, wc.steps)}
             orc.set_threads(os.cpu_count() or 1)
             ref = orc.OracleCTM(wc.site_tensor(), wc.chi)

@@ -150,6 +150,28 @@ size_t ctm_grad_workspace_bytes(const ctm_ctx *ctx, int k_tracked);
 int ctm_grad(ctm_ctx *ctx, int warmup, int k_tracked, const double *h_dev, void *gws, size_t gws_bytes,
              double *energy_host, double *dA_dev);
 
+/* Sec. II.C, Fig. 4a, Eq. 3: leading eigenvalues of the transfer matrix of the
+ * current environment.  With each sector a quadrant of radial dimers
+ * d[u,w,x,y] = sum_z a[u,w,z] a[z,x,y], one column of the plane (an edge, a
+ * dimer, the opposite edge) is
+ *   TM[(a,y,b),(g,w,h)] = sum_{u,x} T[a,u,g] d[u,w,x,y] T[b,x,h],
+ * (chi D2 chi square), which advances one Bravais vector along the edge.  It is
+ * applied matrix-free through the context's contraction engine (FP64 or
+ * split-BF16); nev + 5 vectors (at most 12) are iterated and orthonormalised in
+ * FP64, and the eigenvalues of their Rayleigh quotient are found on the device
+ * every 5 iterations until the nev leading magnitudes, normalised by the largest,
+ * change by less than tol (absolute; <= 0: 1e-12) or max_iter iterations ran
+ * (CTM_ENOTCONVERGED, outputs filled).  lambda_host[0..nev) receives |lambda_i| / |lambda_0| (descending),
+ * xi_host (may be NULL) the correlation length -1 / ln lambda_1 in Bravais
+ * vectors, gap_host (may be NULL) ln(lambda_1 / lambda_2) of the finite
+ * correlation length extrapolation (nev >= 3), iters_out (may be NULL) the
+ * iterations used.  2 <= nev <= 10.  tws: device workspace of
+ * ctm_transfer_workspace_bytes bytes (256-byte aligned).  Overwrites the
+ * step's scratch intermediates (not C, T, Q or M).  Synchronous. */
+size_t ctm_transfer_workspace_bytes(const ctm_ctx *ctx, int nev);
+int ctm_transfer_spectrum(ctm_ctx *ctx, int nev, int max_iter, double tol, void *tws, size_t tws_bytes,
+                          double *lambda_host, double *xi_host, double *gap_host, int *iters_out);
+
 /* Replace the site tensor of a context (Sec. II.D: an optimiser's next trial
  * tensor) without reallocating: A_dev (raw, as for ctm_init) is projected and
  * normalised under the context's symmetrize setting and its double layer formed;

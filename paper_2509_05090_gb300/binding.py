@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
         "ctm_debug_force_timeout": (I, [P, I]),
         "ctm_probe_fp64_peak": (I, [P, dp]),
         "ctm_set_site": (I, [P, P, I]),
+        "ctm_transfer_workspace_bytes": (ctypes.c_size_t, [P, I]),
+        "ctm_transfer_spectrum": (I, [P, I, I, ctypes.c_double, P, ctypes.c_size_t, dp, dp, dp,
+                                      ctypes.POINTER(I)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -250,6 +253,21 @@ class CTM:
         if st != CTM_OK:
             raise CtmError(st, "ctm_grad")
         return E.value, dA
+
+    def ctm_transfer_spectrum(self, nev=3, max_iter=2000, tol=1e-12):
+        """(lambda[0..nev) normalised magnitudes, xi, ln(lambda_1/lambda_2), iterations, converged)."""
+        torch = _torch()
+        nbytes = int(load().ctm_transfer_workspace_bytes(self._h, int(nev)))
+        if nbytes == 0:
+            raise CtmError(1, "ctm_transfer_workspace_bytes")
+        tws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        lam = (ctypes.c_double * nev)()
+        xi, gap, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        st = load().ctm_transfer_spectrum(self._h, int(nev), int(max_iter), float(tol), _ptr(tws), nbytes, lam,
+                                          ctypes.byref(xi), ctypes.byref(gap), ctypes.byref(it))
+        if st not in (CTM_OK, CTM_ENOTCONVERGED):
+            raise CtmError(st, "ctm_transfer_spectrum")
+        return np.array(lam[:]), xi.value, gap.value, it.value, st == CTM_OK
 
     def ctm_set_site(self, A, reset_env=False):
         """Replace the site tensor (same d, D); keep (or reset) the environment."""
