@@ -354,7 +354,7 @@ def time_to_converged(w, precision, n_split, max_steps, corner="qmq", spectrum=F
         # transfer-matrix spectrum of the converged environment (Sec. II.C, Eq. 3)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        lam, xi, gap, iters, sok = g.ctm_transfer_spectrum(nev=3, max_iter=1000)
+        lam, xi, gap, iters, sok = g.ctm_transfer_spectrum(nev=3, max_iter=200)
         rec["transfer_spectrum"] = {"lambda": [float(x) for x in lam], "xi_bravais": xi,
                                     "ln_lambda1_over_lambda2": gap, "iterations": iters, "converged": sok,
                                     "seconds": time.perf_counter() - t1}
