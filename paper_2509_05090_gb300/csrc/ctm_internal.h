@@ -43,6 +43,7 @@ int gemm_f64_pick_split(int M, int N, int K);
 struct SplitPlan {
     int NT, mTiles, nTiles, kTiles, chunks_per_split, ksplit;
     size_t a_pack_bytes, b_pack_bytes, partial_bytes;
+    int deep;      // the 48-wide tile with one CTA per SM and a deep A ring (plan code 148)
 };
 struct SplitWork {
     unsigned char *Apk, *Bpk;
@@ -54,7 +55,8 @@ struct SplitWork {
     int *err;
     int autotune;      // time the candidate tile shapes / K-splits of a new shape once (eager only)
 };
-// ks_override: > 0 a K split, 0 automatic.
+// nt_override: 48, 64, 96, or 148 (the 48-wide tile with a deep A ring); ks_override: > 0 a
+// K split, 0 automatic.
 SplitPlan split_plan(int M, int N, int K, int T, int nt_override = 0, int ks_override = 0);
 // Operand reuse: reuse_a = the A operand (same pointer and maps) was packed by the
 // previous split call and is unchanged; b_cache = a constant B operand packed once

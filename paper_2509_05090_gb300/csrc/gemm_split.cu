@@ -57,6 +57,19 @@ struct SpCfg {
     static constexpr int TMEM_COLS = NT == 48 ? 256 : 512;
     static constexpr int MIN_BLOCKS = NT == 48 ? 2 : 1;
 };
+// The deep-ring variant of the 48-wide tile (plan code SP_DEEP_CODE): one CTA per SM
+// whose A ring takes the shared memory a second CTA would have used, so a K-heavy
+// contraction (the packed n x n operand streamed past a narrow B) keeps 160 KB of A
+// copies in flight per SM instead of 96 KB.
+constexpr int SP_DEEP_CODE = 148;
+constexpr size_t SP_SMEM_MAX = 232448;   // 227 KB of dynamic shared memory per CTA
+template <int T>
+struct SpDeep {
+    static constexpr size_t B_RING = (size_t)2 * T * 48 * 64 * 2;
+    static constexpr int A = (int)((SP_SMEM_MAX - 1024 - B_RING) / (128 * 64 * 2)) < 12
+                                 ? (int)((SP_SMEM_MAX - 1024 - B_RING) / (128 * 64 * 2))
+                                 : 12;
+};
 constexpr unsigned SP_SUSPEND_NS = 2000;        // try_wait suspend-time hint: woken at phase completion
 constexpr unsigned long long SP_WAIT_NS = 1000000000ULL;   // give up a wait after ~1 s
 
@@ -462,13 +475,13 @@ struct SplitArgs {
     int *err;
 };
 
-template <int NT, int T>
-__global__ void __launch_bounds__(SpCfg<NT>::THREADS, SpCfg<NT>::MIN_BLOCKS) gemm_split_kernel(SplitArgs a)
+template <int NT, int T, bool DEEP = false>
+__global__ void __launch_bounds__(SpCfg<NT>::THREADS, DEEP ? 1 : SpCfg<NT>::MIN_BLOCKS) gemm_split_kernel(SplitArgs a)
 {
     constexpr int A_TILE = SP_BM * SP_BK * 2;   // 16 KB
     constexpr int B_TILE = NT * SP_BK * 2;
     constexpr int QW = NT / (SpCfg<NT>::EPI_WARPS / 4);   // columns per epilogue warp
-    constexpr int SP_ASLOTS = SpCfg<NT>::ASLOTS;
+    constexpr int SP_ASLOTS = DEEP ? SpDeep<T>::A : SpCfg<NT>::ASLOTS;
     constexpr int SP_EPI_WARPS = SpCfg<NT>::EPI_WARPS;
     constexpr int SP_EPI_THREADS = SpCfg<NT>::EPI_THREADS;
     constexpr int TMEM_COLS = SpCfg<NT>::TMEM_COLS;
@@ -799,13 +812,15 @@ int pick_nt(int N, int T)
 
 // A one-CTA-per-SM shape asks for at least 120 KB, so a second CTA never shares the SM
 // (it holds all 512 TMEM columns); the NT = 48 shape fits two per SM.
-template <int NT>
+template <int NT, bool DEEP = false>
 size_t split_smem_bytes(int T)
 {
-    size_t b = 1024 + (size_t)SpCfg<NT>::ASLOTS * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
+    const int aslots = DEEP ? (T == 2 ? SpDeep<2>::A : T == 3 ? SpDeep<3>::A : T == 4 ? SpDeep<4>::A : SpDeep<5>::A)
+                            : SpCfg<NT>::ASLOTS;
+    size_t b = 1024 + (size_t)aslots * SP_BM * SP_BK * 2 + (size_t)SP_BSLOTS * T * NT * SP_BK * 2;
     const size_t out_stage = 1024 + (size_t)SP_BM * (NT + 1) * 8 + (size_t)(SP_BM + NT) * 12;   // epilogue reuse
     if (b < out_stage) b = out_stage;
-    if (SpCfg<NT>::MIN_BLOCKS == 1 && b < 120 * 1024) b = 120 * 1024;
+    if ((DEEP || SpCfg<NT>::MIN_BLOCKS == 1) && b < 120 * 1024) b = 120 * 1024;
     return b;
 }
 
@@ -816,6 +831,10 @@ int split_supported_T(int T) { return T >= 2 && T <= 5; }
 SplitPlan split_plan(int M, int N, int K, int T, int nt_override, int ks_override)
 {
     SplitPlan p{};
+    if (nt_override == SP_DEEP_CODE && T * 48 <= 256) {
+        p.deep = 1;
+        nt_override = 48;
+    }
     p.NT = (nt_override == 64 || (nt_override == 96 && T * 96 <= 512) || (nt_override == 48 && T * 48 <= 256))
                ? nt_override
                : pick_nt(N, T);
@@ -853,11 +872,11 @@ SplitPlan split_plan_caps(int M, int N, int K, int T)
     return c;
 }
 
-template <int NT, int T>
+template <int NT, int T, bool DEEP = false>
 static cudaError_t split_attr()
 {
-    return cudaFuncSetAttribute(gemm_split_kernel<NT, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)split_smem_bytes<NT>(T));
+    return cudaFuncSetAttribute(gemm_split_kernel<NT, T, DEEP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)split_smem_bytes<NT, DEEP>(T));
 }
 
 cudaError_t split_prepare()
@@ -875,6 +894,10 @@ cudaError_t split_prepare()
     if (e == cudaSuccess) e = split_attr<48, 3>();
     if (e == cudaSuccess) e = split_attr<48, 4>();
     if (e == cudaSuccess) e = split_attr<48, 5>();
+    if (e == cudaSuccess) e = split_attr<48, 2, true>();
+    if (e == cudaSuccess) e = split_attr<48, 3, true>();
+    if (e == cudaSuccess) e = split_attr<48, 4, true>();
+    if (e == cudaSuccess) e = split_attr<48, 5, true>();
     return e;
 }
 
@@ -994,7 +1017,10 @@ static cudaError_t split_prepass_t(int R, int K, const double *X, Idx2 rmap, Idx
     int CS = 1;
     while (CS * KC < kTiles) CS *= 2;   // <= 8 for kTiles <= 64
     // one launch for transposed operands whose clusters fit in one wave (one CTA
-    // per SM at this register count); wider ones convert faster at full occupancy
+    // per SM at this register count); wider ones convert faster at full occupancy.
+    // (For the n x chi projector operands the clusters cover only a few row groups,
+    // but the two-launch path, fully parallel, measured slower: 0.254 -> 0.274 ms of
+    // pre-pass per step at D = 6, chi = 72.)
     if (rmap.s1 == 0 && rmap.s2 == 1 && kmap.s1 == 0 && kmap.s2 != 1 && kTiles <= 64 &&
         (long long)(rowTiles * rowsT + 31) / 32 * CS <= device_sm_count()) {
         CTM_COUNT_LAUNCH(1);
@@ -1121,8 +1147,10 @@ static cudaError_t gemm_split_run(const GemmF64 &g, int T, SplitWork w, cudaStre
     CTM_COUNT_LAUNCH(1);
     if (ev) cudaEventRecord(ev[0], st);
 #define CTM_SPLIT_LAUNCH(nt, t) \
-    if (p.NT == nt && T == t)                                                                               \
-        gemm_split_kernel<nt, t><<<grid, SpCfg<nt>::THREADS, split_smem_bytes<nt>(t), st>>>(a);
+    if (p.NT == nt && T == t && !p.deep)                                                                    \
+        gemm_split_kernel<nt, t><<<grid, SpCfg<nt>::THREADS, split_smem_bytes<nt>(t), st>>>(a);       \
+    if (p.NT == nt && T == t && p.deep && nt == 48)                                                         \
+        gemm_split_kernel<48, t, true><<<grid, SpCfg<48>::THREADS, split_smem_bytes<48, true>(t), st>>>(a);
     CTM_SPLIT_LAUNCH(64, 2)
     CTM_SPLIT_LAUNCH(64, 3)
     CTM_SPLIT_LAUNCH(64, 4)
@@ -1194,10 +1222,12 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
     SplitPlan base = split_plan(g.M, g.N, g.K, T);
     const int chunks = (base.kTiles + SP_KT_PER_CHUNK - 1) / SP_KT_PER_CHUNK;
     std::vector<std::pair<int, int>> cands;
-    for (int nt : {48, 64, 96}) {
-        if ((nt == 96 && T * 96 > 512) || (nt == 48 && T * 48 > 256)) continue;
+    for (int nt : {48, 64, 96, SP_DEEP_CODE}) {
+        if ((nt == 96 && T * 96 > 512) || ((nt == 48 || nt == SP_DEEP_CODE) && T * 48 > 256)) continue;
+        if (nt == SP_DEEP_CODE && chunks < 2) continue;   // the deep ring pays off only when K streams
         // auto, none, 2x, 1/2x, and the most splits that still fit one wave of CTAs
-        const int one_wave = (int)(device_sm_count() / ((long long)base.mTiles * ((g.N + nt - 1) / nt)));
+        const int ntw = nt == SP_DEEP_CODE ? 48 : nt;   // tile width of the candidate
+        const int one_wave = (int)(device_sm_count() / ((long long)base.mTiles * ((g.N + ntw - 1) / ntw)));
         for (int ks : {base.ksplit, 1, 2 * base.ksplit, base.ksplit / 2, one_wave}) {
             if (ks < 1 || ks > chunks) continue;
             std::pair<int, int> c{nt, ks};
