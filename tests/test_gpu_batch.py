@@ -50,3 +50,28 @@ def test_batch96_runs_and_matches_standalone_instances(ctm_lib):
         assert np.max(np.abs(sb - sa)) <= 1e-9, i
         alone.close()
     batch.close()
+
+
+def test_batch96_largest_instances_match_oracle(ctm_lib):
+    """The 96-instance batch at its own sizes: after 3 batched steps, the three largest
+    instances (n up to 2592) against the oracle run from the same initial environment
+    (split-BF16 T = 5: spectrum 1e-8, energy 1e-9)."""
+    from paper_2509_05090_gb300 import binding
+    O.set_threads(0)
+    wl = I.batch_workload()
+    tensors = [w.site_tensor() for w in wl]
+    batch = binding.CTMBatch(tensors, [w.chi for w in wl], precision="split_bf16", n_split=5)
+    batch.ctm_batch_step(3)
+    order = sorted(range(len(wl)), key=lambda i: -wl[i].n)[:3]
+    for i in order:
+        w = wl[i]
+        ref = O.OracleCTM(tensors[i], w.chi)
+        for _ in range(3):
+            ref.step()
+        g = batch.instance(i)
+        s = g.ctm_get_intermediate("s").cpu().numpy()
+        assert np.max(np.abs(s - ref.s)) <= 1e-8, i
+        h = w.hamiltonians()
+        e, E, rho = g.ctm_energy(h)
+        assert abs(E - ref.energy(h)[1]) <= 1e-9, i
+    batch.close()

@@ -213,3 +213,45 @@ def test_split_energy_error_below_1e9(ctm_lib):
     e, E, rho = g.ctm_energy(h)
     assert abs(E - E_ref) <= 1e-9
     g.close()
+
+
+def test_split_step_outputs_match_oracle_d8_chi128(ctm_lib):
+    """D = 8, chi = 128 (enlarged corner 8192 x 8192) in split-BF16 (T = 5), one step from
+    the oracle's environment after one step: M and Y within the derived chain bounds,
+    Q and R within the first-order QR bound of the measured Y difference, C' and T' within
+    their first-order bounds (as at D = 6, split_bounds)."""
+    from split_bounds import corner_bound, edge_bound, enlarged_corner_err, gemm_err, qr_bounds
+    O.set_threads(0)
+    w = I.WORKLOADS["kh_D8_chi128"]
+    A = w.site_tensor()
+    ref = O.OracleCTM(A, w.chi)
+    ref.step()
+    g = _ctm(A, w.chi, precision="split_bf16", n_split=5)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    C0, T0, Qs = ref.C.copy(), ref.T.copy(), ref.warm_start()
+    ref.step()
+    g.ctm_step(1)
+    last = ref.last
+    dRd = np.abs(np.diag(last["R"]))
+    lead = int(np.sum(dRd / dRd[0] >= 1e-8))
+    assert lead == w.chi
+    eM = enlarged_corner_err(C0, T0, ref.a, 5)
+    M = _np(g.ctm_get_intermediate("M"))
+    assert np.all(np.abs(M - last["M"]) <= 2.0 * eM)
+    eY = gemm_err(last["M"], Qs, 5, eA=eM)
+    del eM
+    Y = _np(g.ctm_get_intermediate("Y"))
+    assert np.all(np.abs(Y - last["Y"]) <= 2.0 * eY)
+    dQ, dR = qr_bounds(float(np.linalg.norm(Y - last["Y"])), last["Y"], last["R"], lead)
+    R = _np(g.ctm_get_intermediate("R"))
+    assert np.linalg.norm(R - last["R"]) <= 2.0 * dR
+    C, T, Q = (_np(x) for x in g.ctm_get_env())
+    assert np.linalg.norm(Q - last["Q"]) <= 2.0 * dQ
+    dC = corner_bound(last["M"], last["Q"], float(np.linalg.norm(M - last["M"])), 2.0 * dQ, 5)
+    assert np.linalg.norm(C - last["C"]) <= 2.0 * dC
+    dT = edge_bound(T0, ref.a, last["Q"], 2.0 * dQ, 5)
+    assert np.linalg.norm(T - last["T"]) <= 2.0 * dT
+    # not vacuous; the worst-case truncation terms K max|A| max|B| grow with K (8192 here)
+    for bound, x in ((2.0 * dQ, last["Q"]), (2.0 * dC, last["C"]), (2.0 * dT, last["T"])):
+        assert bound < 1e-3 * np.max(np.abs(x))
+    g.close()
