@@ -1224,7 +1224,11 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
     std::vector<std::pair<int, int>> cands;
     for (int nt : {48, 64, 96, SP_DEEP_CODE}) {
         if ((nt == 96 && T * 96 > 512) || ((nt == 48 || nt == SP_DEEP_CODE) && T * 48 > 256)) continue;
-        if (nt == SP_DEEP_CODE && chunks < 2) continue;   // the deep ring pays off only when K streams
+        // the deep ring pays off only for long K streams: at K of a few thousand it can win
+        // alone yet slow the step, whose concurrent corner update and corner spectrum
+        // then find every SM held by one 226 KB CTA (measured 1053 against ~1130 steps/s
+        // at D = 6, chi = 72); it was chosen at K = 8192 (D = 8, chi = 128)
+        if (nt == SP_DEEP_CODE && (chunks < 2 || g.K < 4096)) continue;
         // auto, none, 2x, 1/2x, and the most splits that still fit one wave of CTAs
         const int ntw = nt == SP_DEEP_CODE ? 48 : nt;   // tile width of the candidate
         const int one_wave = (int)(device_sm_count() / ((long long)base.mTiles * ((g.N + ntw - 1) / ntw)));
