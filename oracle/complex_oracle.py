@@ -164,9 +164,12 @@ def open_layer(A, s, t, first_leg=0):
 
 
 def enlarged_corner(C, T, aB, aA):
+    """Fig. 3c, one pair at a time: W = T C, X' = W conj(T), Y1 = X' aB, M = Y1 aA."""
     chi, D2 = T.shape[0], T.shape[1]
-    X = np.einsum("aug,gh,blh->aulb", T, C, T.conj())
-    return np.einsum("aulb,ulz,zxy->aybx", X, aB, aA).reshape(chi * D2, chi * D2)
+    W = np.einsum("aug,gh->auh", T, C, optimize=True)
+    X = np.einsum("auh,blh->aulb", W, T.conj(), optimize=True)
+    Y1 = np.einsum("aulb,ulz->abz", X, aB, optimize=True)
+    return np.einsum("abz,zxy->aybx", Y1, aA, optimize=True).reshape(chi * D2, chi * D2)
 
 
 def edge_update(T, aB, aA, Q):
@@ -174,10 +177,10 @@ def edge_update(T, aB, aA, Q):
     contracted one pair at a time."""
     chi, D2 = T.shape[0], T.shape[1]
     Q4 = Q.reshape(chi, D2, -1)
-    H1 = np.einsum("aug,gwj->auwj", T, Q4)
-    H2 = np.einsum("auwj,uwz->ajz", H1, aB)
-    H3 = np.einsum("ajz,zxy->ajxy", H2, aA)
-    Tn = np.einsum("ayi,ajxy->ixj", Q4.conj(), H3)
+    H1 = np.einsum("aug,gwj->auwj", T, Q4, optimize=True)
+    H2 = np.einsum("auwj,uwz->ajz", H1, aB, optimize=True)
+    H3 = np.einsum("ajz,zxy->ajxy", H2, aA, optimize=True)
+    Tn = np.einsum("ayi,ajxy->ixj", Q4.conj(), H3, optimize=True)
     return Tn / np.linalg.norm(Tn)
 
 
