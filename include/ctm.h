@@ -281,6 +281,73 @@ int ctm_batch_step(ctm_batch *batch, int nsteps, double *max_delta_host);
 int ctm_batch_ctx(ctm_batch *batch, int i, ctm_ctx **ctx);
 void ctm_batch_destroy(ctm_batch *batch);
 
+/* ---------------------------------------------------------------------------
+ * Complex tensors (App. A, Sec. III.C): the same step for a complex site tensor
+ * made symmetric under a complex representation of C3v on the physical leg.
+ *
+ *  - Complex arrays are interleaved (re, im) pairs of doubles, row-major in the
+ *    complex elements (a torch.complex128 tensor's storage), on the device.
+ *  - irrep CTM_IRREP_E: the rotation U_C3 = (-1)^(d-1) e^{i 2pi/3}
+ *    exp(i 2pi/3 n.S), n = (1,1,1)/sqrt 3, acts with the leg cycle
+ *    A[s; i, j, k] -> sum_t U[s,t] A[t; k, i, j]; the reflection through the
+ *    plane with spin-space normal m_1 = (1,-1,0)/sqrt 2 acts as the anti-unitary
+ *    K-hat C exp(i pi m_1.S) (K-hat: +1, -1, ... on the anti-diagonal; C: complex
+ *    conjugation of the whole tensor) with the exchange of the x and y legs; the
+ *    other four elements follow by composition.  cfg->symmetrize averages A over
+ *    the six and normalises it.  CTM_IRREP_A1: U = I, no conjugation (then the
+ *    path reproduces the real one).  d = 2 or 3 for E.
+ *  - The double layer a[(ii')][(jj')][(kk')] = sum_s A[s,i,j,k] conj(A[s,i',j',k'])
+ *    obeys a[l][u][z] = conj(a[u][l][z]) under each reflection (Fig. 2b), so with
+ *    a Hermitian corner and the column edge the conjugate of the row edge the
+ *    enlarged corner M[(a,y)][(b,x)] = sum T[a,u,g] C[g,h] conj(T[b,l,h])
+ *    a[u,l,z] a[z,x,y] is Hermitian; a step forms Y = M Q diag(sgn Re C_jj),
+ *    Y = Q R with diag(R) real and >= 0, C' = sym(Q^H M Q)/|.| (Hermitian part),
+ *    T'[i,x,j] = sum conj(Q[(a,y),i]) T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j] /|.|,
+ *    and delta from the eigenvalue magnitudes of C'.
+ *  - Limits: chi <= 64, n = chi D^2 <= 12000, D <= 10, corner_mode 0.
+ *  - The caller owns the workspace (ctm_complex_workspace_bytes), as for ctm_init.
+ *    Errors as for the real calls. */
+typedef struct ctm_complex_ctx ctm_complex_ctx;
+enum { CTM_IRREP_A1 = 0, CTM_IRREP_E = 1 };
+size_t ctm_complex_workspace_bytes(const ctm_config *cfg, int irrep);
+
+/* App. A, Sec. II.A-B: A_dev = raw complex site tensor [s][i][j][k]
+ * (d x D x D x D, interleaved); projection, normalisation, double layer and the
+ * environment C = I, T[a][u][b] = delta_ab t_u, Q = [I; 0] as for ctm_init. */
+int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void *workspace, size_t ws_bytes,
+                     void *stream, ctm_complex_ctx **out);
+
+/* Sec. II.B: nsteps steps; delta_host (may be NULL) as for ctm_step.  Synchronous. */
+int ctm_complex_step(ctm_complex_ctx *ctx, int nsteps, double *delta_host);
+
+/* Sec. II.B: steps until delta < tol, as for ctm_converge. */
+int ctm_complex_converge(ctm_complex_ctx *ctx, int max_steps, double tol, int check_every, int *steps_out,
+                         double *delta_out);
+
+/* Eq. 1: bond energies as for ctm_energy, h_dev = 3 complex d^2 x d^2 bond
+ * operators (interleaved).  The density matrix rho of the apex bond is formed
+ * for the z bond (the apex bond is the z leg of both sites); the x and y bonds
+ * are the z bond of the tensor rotated by the C3 element, so
+ * e_x = Re tr(rho (W^H h_x W)) with W = U^2 (x) U^2, e_y likewise with
+ * W = U (x) U (U = U_C3, or I for A1), e_z = Re tr(rho h_z).  rho_host (may be
+ * NULL): the z-bond rho, d^2 x d^2 complex interleaved. */
+int ctm_complex_energy(ctm_complex_ctx *ctx, const double *h_dev, double *e_bond_host, double *e_site_host,
+                       double *rho_host);
+
+/* C (chi x chi), T (chi x D2 x chi), Q (n x chi), complex interleaved (device).
+ * get: any pointer may be NULL; set: the corner's spectrum becomes the
+ * reference of the next delta.  Synchronous. */
+int ctm_complex_get_env(const ctm_complex_ctx *ctx, double *C_dev, double *T_dev, double *Q_dev);
+int ctm_complex_set_env(ctm_complex_ctx *ctx, const double *C_dev, const double *T_dev, const double *Q_dev);
+
+/* Intermediates of the last step, complex interleaved into dst (device,
+ * count = doubles available): 0 M (n x n), 1 Y (n x chi), 2 R (chi x chi),
+ * 3 Q (n x chi), 4 the corner spectrum s (chi doubles, real), 5 the projected
+ * site tensor, 6 the double layer (D2^3), 7 C, 8 T.  Synchronous. */
+int ctm_complex_get_intermediate(const ctm_complex_ctx *ctx, int which, double *dst_dev, size_t count);
+
+void ctm_complex_destroy(ctm_complex_ctx *ctx);
+
 /* Release the host context (the caller frees the workspace). */
 void ctm_destroy(ctm_ctx *ctx);
 

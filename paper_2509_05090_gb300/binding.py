@@ -85,6 +85,15 @@ def load(path: str = LIB_PATH):
         "ctm_debug_force_timeout": (I, [P, I]),
         "ctm_probe_fp64_peak": (I, [P, dp]),
         "ctm_set_site": (I, [P, P, I]),
+        "ctm_complex_workspace_bytes": (ctypes.c_size_t, [cfgp, I]),
+        "ctm_complex_init": (I, [cfgp, I, P, P, ctypes.c_size_t, P, ctypes.POINTER(P)]),
+        "ctm_complex_step": (I, [P, I, dp]),
+        "ctm_complex_converge": (I, [P, I, ctypes.c_double, I, ctypes.POINTER(I), dp]),
+        "ctm_complex_energy": (I, [P, P, dp, dp, dp]),
+        "ctm_complex_get_env": (I, [P, P, P, P]),
+        "ctm_complex_set_env": (I, [P, P, P, P]),
+        "ctm_complex_get_intermediate": (I, [P, I, P, ctypes.c_size_t]),
+        "ctm_complex_destroy": (None, [P]),
         "ctm_transfer_workspace_bytes": (ctypes.c_size_t, [P, I]),
         "ctm_transfer_spectrum": (I, [P, I, I, ctypes.c_double, P, ctypes.c_size_t, dp, dp, dp,
                                       ctypes.POINTER(I)]),
@@ -338,6 +347,126 @@ class CTM:
         if getattr(self, "_h", None):
             self.stream.synchronize()
             load().ctm_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+IRREPS = {"A1": 0, "E": 1}
+
+
+def _complex_dev(x, torch):
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.complex128))
+    return x.to(device="cuda", dtype=torch.complex128).contiguous()
+
+
+class CTMComplex:
+    """One complex (E- or A1-irrep) CTMRG instance (ctm_complex_init ... ctm_complex_destroy).
+    Complex tensors go in and out as torch.complex128 on the current CUDA device."""
+
+    def __init__(self, A, chi, irrep="E", precision="fp64", n_split=5, tol=1e-10, max_steps=200, symmetrize=True,
+                 stream=None):
+        torch = _torch()
+        lib = load()
+        A = _complex_dev(A, torch)
+        if A.dim() != 4 or not (A.shape[1] == A.shape[2] == A.shape[3]):
+            raise ValueError(f"site tensor must be d x D x D x D, got {tuple(A.shape)}")
+        d, D = int(A.shape[0]), int(A.shape[1])
+        self.d, self.D, self.chi = d, D, int(chi)
+        self.D2 = D * D
+        self.n = self.chi * self.D2
+        self.irrep = IRREPS[irrep] if isinstance(irrep, str) else int(irrep)
+        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize)
+        nbytes = int(lib.ctm_complex_workspace_bytes(ctypes.byref(self.cfg), self.irrep))
+        if nbytes == 0:
+            raise CtmError(1, "ctm_complex_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        self._A = A
+        h = ctypes.c_void_p()
+        st = lib.ctm_complex_init(ctypes.byref(self.cfg), self.irrep, _ptr(A), _ptr(self.workspace), nbytes,
+                                  ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_complex_init")
+        self._h = h
+
+    def ctm_complex_step(self, nsteps=1, want_delta=True):
+        d = ctypes.c_double(float("nan"))
+        st = load().ctm_complex_step(self._h, int(nsteps), ctypes.byref(d) if want_delta else None)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_complex_step")
+        return d.value if want_delta else None
+
+    def ctm_complex_converge(self, max_steps=0, tol=0.0, check_every=1):
+        steps = ctypes.c_int(0)
+        delta = ctypes.c_double(float("nan"))
+        st = load().ctm_complex_converge(self._h, int(max_steps), float(tol), int(check_every), ctypes.byref(steps),
+                                         ctypes.byref(delta))
+        if st not in (CTM_OK, CTM_ENOTCONVERGED):
+            raise CtmError(st, "ctm_complex_converge")
+        return steps.value, delta.value, st == CTM_OK
+
+    def ctm_complex_energy(self, h):
+        """h: three d^2 x d^2 complex bond operators (x, y, z); returns (e_bond, E_site, rho_z)."""
+        torch = _torch()
+        h = _complex_dev(h, torch)
+        dd = self.d * self.d
+        if h.numel() != 3 * dd * dd:
+            raise ValueError(f"need three {dd} x {dd} bond operators, got {tuple(h.shape)}")
+        e = (ctypes.c_double * 3)()
+        es = ctypes.c_double()
+        rho = (ctypes.c_double * (2 * dd * dd))()
+        st = load().ctm_complex_energy(self._h, _ptr(h), e, ctypes.byref(es), rho)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_complex_energy")
+        r = np.array(rho[:])
+        return np.array(e[:]), es.value, (r[0::2] + 1j * r[1::2]).reshape(dd, dd)
+
+    def ctm_complex_get_env(self):
+        torch = _torch()
+        C = torch.empty((self.chi, self.chi), dtype=torch.complex128, device="cuda")
+        T = torch.empty((self.chi, self.D2, self.chi), dtype=torch.complex128, device="cuda")
+        Q = torch.empty((self.n, self.chi), dtype=torch.complex128, device="cuda")
+        st = load().ctm_complex_get_env(self._h, _ptr(C), _ptr(T), _ptr(Q))
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_complex_get_env")
+        return C, T, Q
+
+    def ctm_complex_set_env(self, C, T, Q):
+        torch = _torch()
+        conv = [_complex_dev(x, torch) for x in (C, T, Q)]
+        for x, cnt, name in zip(conv, (self.chi ** 2, self.chi * self.D2 * self.chi, self.n * self.chi), "CTQ"):
+            if x.numel() != cnt:
+                raise ValueError(f"{name} has {x.numel()} elements, expected {cnt}")
+        st = load().ctm_complex_set_env(self._h, *[_ptr(x) for x in conv])
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_complex_set_env")
+
+    _SHAPES = {0: "M", 1: "Y", 2: "R", 3: "Q", 4: "s", 5: "A", 6: "a", 7: "C", 8: "T"}
+
+    def ctm_complex_get_intermediate(self, which):
+        torch = _torch()
+        if isinstance(which, str):
+            which = {v: k for k, v in self._SHAPES.items()}[which]
+        n, chi, D2, D = self.n, self.chi, self.D2, self.D
+        shape = {0: (n, n), 1: (n, chi), 2: (chi, chi), 3: (n, chi), 4: (chi,), 5: (self.d, D, D, D),
+                 6: (D2, D2, D2), 7: (chi, chi), 8: (chi, D2, chi)}[which]
+        out = torch.empty(shape, dtype=torch.float64 if which == 4 else torch.complex128, device="cuda")
+        count = out.numel() * (1 if which == 4 else 2)
+        st = load().ctm_complex_get_intermediate(self._h, int(which), _ptr(out), count)
+        if st != CTM_OK:
+            raise CtmError(st, "ctm_complex_get_intermediate")
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.stream.synchronize()
+            load().ctm_complex_destroy(self._h)
             self._h = None
 
     def __del__(self):

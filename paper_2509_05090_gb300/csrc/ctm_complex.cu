@@ -1,0 +1,1285 @@
+// Complex C3v CTMRG (App. A, Sec. II.B, Sec. III.C): site tensors symmetric under
+// a complex physical representation of C3v (the E irrep of the Kitaev model, or the
+// trivial A1 one), a Hermitian enlarged corner, Householder QR with real diag(R) >= 0,
+// C' = sym(Q^H M Q)/|.|, T' = Q^H (T a a) Q/|.|, and the bond energies.
+//
+// Storage: complex tensors are planar.  A tensor that enters a contraction as the
+// right operand holds four planes [Re, Im, -Im, Re] so that each complex product
+// C = op(A) op(B) is two real products with the inner dimension doubled,
+//   Re C = [Re A | s_A Im A] [Re B ; -s_B Im B],  Im C = [Re A | s_A Im A] [s_B Im B ; Re B]
+// (s = -1 for a conjugated operand), every operand a strided view of one plane pair
+// and both products sharing the packed left operand.  The complex QR is the real
+// Householder QR of the 2 x 2 block embedding [[Re, -Im], [Im, Re]] of the reduced
+// corner, whose unique factors (positive diagonal) are the embeddings of the complex
+// Q and R; the corner spectrum is that of the embedded (real symmetric) corner, each
+// eigenvalue twice.
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <array>
+#include <new>
+#include <vector>
+
+#include "ctm_internal.h"
+
+struct ctm_complex_ctx {
+    ctm_config cfg;
+    int irrep;
+    int d, D, D2, chi;
+    long long n;
+    int split_T;
+    cudaStream_t stream;
+    double U[3][3][2];      // the rotation paired with the leg cycle (energies of the x, y bonds)
+    // planes: P_* is the plane stride of each tensor (elements)
+    double *Ain, *A, *a, *bB, *bA;
+    long long PA, Pa, Pb;
+    double *C, *Cn, *Cr, *T, *Tn, *Q, *Qn, *Qs;
+    long long PC, PT, PQ;
+    double *Y, *W, *MQ, *R;
+    long long PY;
+    double *M, *X, *H;
+    long long PM;
+    double *Y1, *Y1o, *G2;
+    long long PY1, PYo;
+    double *P5a, *P5b;
+    double *Yemb, *Qemb, *Remb, *Cemb;
+    double *s, *s_new, *delta, *spec_work;
+    double *splitk;
+    size_t splitk_elems;
+    double *qr_sbuf, *qr_rowbuf, *qr_wy;
+    unsigned *qr_bar;
+    int *err, *flag;
+    double *norm_part;
+    double *rho_part, *rho_raw, *hrot, *eout;
+    SplitWork sw;
+    int steps_done;
+};
+
+namespace {
+
+constexpr int ZMAX_D = 3;
+constexpr int ZNORM_BLOCKS = 128;
+constexpr int ZRHO_BLOCKS = 128;
+constexpr int ZRHO_MAX_DD = 9;
+
+struct ZGroup {
+    double U[6][ZMAX_D][ZMAX_D][2];
+    int perm[6][3];
+    int anti[6];
+};
+
+// ------------------------------------------------------------------ host: the group
+struct Cx {
+    double re, im;
+};
+static inline Cx cmul(Cx a, Cx b) { return Cx{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+static inline Cx cadd(Cx a, Cx b) { return Cx{a.re + b.re, a.im + b.im}; }
+static inline Cx cconj(Cx a) { return Cx{a.re, -a.im}; }
+
+struct HMat {
+    int d;
+    Cx v[ZMAX_D][ZMAX_D];
+};
+static HMat hm_zero(int d)
+{
+    HMat m;
+    m.d = d;
+    for (int i = 0; i < ZMAX_D; ++i)
+        for (int j = 0; j < ZMAX_D; ++j) m.v[i][j] = Cx{0.0, 0.0};
+    return m;
+}
+static HMat hm_eye(int d)
+{
+    HMat m = hm_zero(d);
+    for (int i = 0; i < d; ++i) m.v[i][i] = Cx{1.0, 0.0};
+    return m;
+}
+static HMat hm_mul(const HMat &a, const HMat &b)
+{
+    HMat m = hm_zero(a.d);
+    for (int i = 0; i < a.d; ++i)
+        for (int j = 0; j < a.d; ++j)
+            for (int k = 0; k < a.d; ++k) m.v[i][j] = cadd(m.v[i][j], cmul(a.v[i][k], b.v[k][j]));
+    return m;
+}
+static HMat hm_conj(const HMat &a)
+{
+    HMat m = a;
+    for (int i = 0; i < a.d; ++i)
+        for (int j = 0; j < a.d; ++j) m.v[i][j] = cconj(a.v[i][j]);
+    return m;
+}
+static HMat hm_scale(const HMat &a, Cx s)
+{
+    HMat m = a;
+    for (int i = 0; i < a.d; ++i)
+        for (int j = 0; j < a.d; ++j) m.v[i][j] = cmul(a.v[i][j], s);
+    return m;
+}
+static double hm_dist(const HMat &a, const HMat &b)
+{
+    double m = 0.0;
+    for (int i = 0; i < a.d; ++i)
+        for (int j = 0; j < a.d; ++j) m = fmax(m, hypot(a.v[i][j].re - b.v[i][j].re, a.v[i][j].im - b.v[i][j].im));
+    return m;
+}
+
+// Spin-S matrices in the S^z basis (m = S, S-1, ..., -S) combined along a unit vector:
+// e.S = e_x S^x + e_y S^y + e_z S^z.
+static HMat spin_along(int d, const double e[3])
+{
+    const double S = 0.5 * (d - 1);
+    HMat m = hm_zero(d);
+    for (int k = 0; k < d; ++k) m.v[k][k] = Cx{e[2] * (S - k), 0.0};
+    for (int k = 1; k < d; ++k) {
+        const double mk = S - k;
+        const double sp = sqrt(S * (S + 1.0) - mk * (mk + 1.0));   // <m_k + 1| S^+ |m_k>
+        // S^x = (S^+ + S^-)/2, S^y = (S^+ - S^-)/(2i)
+        m.v[k - 1][k] = cadd(m.v[k - 1][k], Cx{0.5 * sp * e[0], -0.5 * sp * e[1]});
+        m.v[k][k - 1] = cadd(m.v[k][k - 1], Cx{0.5 * sp * e[0], 0.5 * sp * e[1]});
+    }
+    return m;
+}
+
+// exp(i theta H): Taylor series of the scaled argument, then repeated squaring.
+static HMat expm_i(const HMat &H, double theta)
+{
+    double nrm = 0.0;
+    for (int i = 0; i < H.d; ++i)
+        for (int j = 0; j < H.d; ++j) nrm += hypot(H.v[i][j].re, H.v[i][j].im);
+    nrm *= fabs(theta);
+    int sq = 0;
+    while (nrm > 0.25) {
+        nrm *= 0.5;
+        ++sq;
+    }
+    const HMat X = hm_scale(H, Cx{0.0, theta / (double)(1 << sq)});
+    HMat sum = hm_eye(H.d), term = hm_eye(H.d);
+    for (int k = 1; k <= 24; ++k) {
+        term = hm_scale(hm_mul(term, X), Cx{1.0 / k, 0.0});
+        for (int i = 0; i < H.d; ++i)
+            for (int j = 0; j < H.d; ++j) sum.v[i][j] = cadd(sum.v[i][j], term.v[i][j]);
+    }
+    for (int s = 0; s < sq; ++s) sum = hm_mul(sum, sum);
+    return sum;
+}
+
+struct Elem {
+    HMat U;
+    int perm[3];
+    int anti;
+};
+
+// g after h: U = U_g op(U_h) (op = conj when g is anti-unitary), legs perm[q] = p_h[p_g[q]].
+static Elem compose(const Elem &g, const Elem &h)
+{
+    Elem r;
+    r.U = hm_mul(g.U, g.anti ? hm_conj(h.U) : h.U);
+    for (int q = 0; q < 3; ++q) r.perm[q] = h.perm[g.perm[q]];
+    r.anti = g.anti ^ h.anti;
+    return r;
+}
+static bool same(const Elem &a, const Elem &b)
+{
+    return a.anti == b.anti && a.perm[0] == b.perm[0] && a.perm[1] == b.perm[1] && a.perm[2] == b.perm[2] &&
+           hm_dist(a.U, b.U) < 1e-12;
+}
+
+// App. A: generators of C3v acting on A[s; x, y, z].  The rotation
+// U_C3 = (-1)^(d-1) e^{i 2pi/3} exp(i 2pi/3 n.S), n = (1,1,1)/sqrt 3, with the leg
+// cycle out[s; i, j, k] = U A[s; k, i, j]; the reflection p_1 (normal m_1 = (1,-1,0)/sqrt 2)
+// = K-hat C exp(i pi m_1.S) (anti-unitary; its phase set to 1), with the exchange of
+// the x and y legs.  The other elements come from closure.  A1: U = I, no conjugation.
+static bool make_group(int d, int irrep, ZGroup *grp, HMat *Urot)
+{
+    Elem e, r, p;
+    e.U = hm_eye(d);
+    e.perm[0] = 0, e.perm[1] = 1, e.perm[2] = 2;
+    e.anti = 0;
+    r = e;
+    r.perm[0] = 1, r.perm[1] = 2, r.perm[2] = 0;
+    p = e;
+    p.perm[0] = 1, p.perm[1] = 0, p.perm[2] = 2;
+    if (irrep == 1) {
+        const double PI = 3.14159265358979323846;
+        const double s3 = 1.0 / sqrt(3.0), s2 = 1.0 / sqrt(2.0);
+        const double nvec[3] = {s3, s3, s3}, mvec[3] = {s2, -s2, 0.0};
+        const double sgn = (d - 1) % 2 ? -1.0 : 1.0;
+        r.U = hm_scale(expm_i(spin_along(d, nvec), 2.0 * PI / 3.0),
+                       Cx{sgn * cos(2.0 * PI / 3.0), sgn * sin(2.0 * PI / 3.0)});
+        HMat K = hm_zero(d);
+        for (int q = 0; q < d; ++q) K.v[q][d - 1 - q] = Cx{(q % 2) ? -1.0 : 1.0, 0.0};
+        p.U = hm_mul(K, hm_conj(expm_i(spin_along(d, mvec), PI)));
+        p.anti = 1;
+    }
+    std::vector<Elem> el{e};
+    std::vector<Elem> frontier{r, p};
+    while (!frontier.empty()) {
+        Elem g = frontier.back();
+        frontier.pop_back();
+        bool found = false;
+        for (const Elem &x : el) found = found || same(g, x);
+        if (found) continue;
+        el.push_back(g);
+        if (el.size() > 6) return false;
+        const size_t cur = el.size();
+        for (size_t i = 0; i < cur; ++i) {
+            frontier.push_back(compose(g, el[i]));
+            frontier.push_back(compose(el[i], g));
+        }
+    }
+    if (el.size() != 6) return false;
+    memset(grp, 0, sizeof(*grp));
+    for (int g = 0; g < 6; ++g) {
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) {
+                grp->U[g][i][j][0] = el[g].U.v[i][j].re;
+                grp->U[g][i][j][1] = el[g].U.v[i][j].im;
+            }
+        for (int q = 0; q < 3; ++q) grp->perm[g][q] = el[g].perm[q];
+        grp->anti[g] = el[g].anti;
+    }
+    *Urot = r.U;
+    return true;
+}
+
+// ------------------------------------------------------------------ device kernels
+__device__ __forceinline__ long long zoff2(const Idx2 &x, int i)
+{
+    if (x.s1 == 0) return (long long)i * x.s2;
+    const int hi = i / x.div;
+    return (long long)hi * x.s1 + (long long)(i - hi * x.div) * x.s2;
+}
+
+int zgrid(long long count)
+{
+    long long b = (count + 255) / 256, cap = 8LL * device_sm_count();
+    if (b > cap) b = cap;
+    return b < 1 ? 1 : (int)b;
+}
+
+// interleaved (re, im) -> planar; planes >= 3 also fill -Im and a copy of Re
+__global__ void zc_planar_kernel(long long count, const double *src, double *dst, long long P, int planes)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double re = src[2 * t], im = src[2 * t + 1];
+        dst[t] = re;
+        dst[P + t] = im;
+        if (planes >= 3) dst[2 * P + t] = -im;
+        if (planes >= 4) dst[3 * P + t] = re;
+    }
+}
+
+__global__ void zc_interleave_kernel(long long count, const double *src, long long P, double *dst)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x) {
+        dst[2 * t] = src[t];
+        dst[2 * t + 1] = src[P + t];
+    }
+}
+
+// planes 2 and 3 of a four-plane tensor from planes 0 and 1
+__global__ void zc_complete_kernel(long long count, double *x, long long P)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x) {
+        x[2 * P + t] = -x[P + t];
+        x[3 * P + t] = x[t];
+    }
+}
+
+// App. A: out[s; i0, i1, i2] = (1/6) sum_g sum_t U_g[s, t] X_g[t; legs], X_g = conj(A) for an
+// anti-unitary g, and A's leg perm_g[q] carries i_q.
+__global__ void zc_project_kernel(int d, int D, const double *A, long long P, ZGroup grp, int symmetrize,
+                                  double *out, long long Po)
+{
+    const int D3 = D * D * D;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < d * D3; t += gridDim.x * blockDim.x) {
+        const int s = t / D3, r = t - s * D3;
+        if (!symmetrize) {
+            out[t] = A[t];
+            out[Po + t] = A[P + t];
+            continue;
+        }
+        const int iv[3] = {r / (D * D), (r / D) % D, r % D};
+        double re = 0.0, im = 0.0;
+        for (int g = 0; g < 6; ++g) {
+            int l[3];
+            for (int q = 0; q < 3; ++q) l[grp.perm[g][q]] = iv[q];
+            const int off = (l[0] * D + l[1]) * D + l[2];
+            const double sg = grp.anti[g] ? -1.0 : 1.0;
+            for (int u = 0; u < d; ++u) {
+                const double ar = A[u * D3 + off], ai = sg * A[P + u * D3 + off];
+                const double ur = grp.U[g][s][u][0], ui = grp.U[g][s][u][1];
+                re += ur * ar - ui * ai;
+                im += ur * ai + ui * ar;
+            }
+        }
+        out[t] = re / 6.0;
+        out[Po + t] = im / 6.0;
+    }
+}
+
+// sum of |x|^2 over a planar complex array
+__global__ void zc_sumsq_kernel(long long count, const double *x, long long P, double *partials)
+{
+    __shared__ double red[8];
+    double acc = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        acc += x[t] * x[t] + x[P + t] * x[P + t];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        partials[blockIdx.x] = s;
+    }
+}
+
+// x <- x / sqrt(sum of partials); fills planes 2, 3 when planes == 4
+__global__ void zc_scale_kernel(long long count, double *x, long long P, const double *partials, int nparts,
+                                int planes)
+{
+    __shared__ double inv;
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += partials[b];
+        inv = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    }
+    __syncthreads();
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double re = x[t] * inv, im = x[P + t] * inv;
+        x[t] = re;
+        x[P + t] = im;
+        if (planes == 4) {
+            x[2 * P + t] = -im;
+            x[3 * P + t] = re;
+        }
+    }
+}
+
+// Fig. 1b: a[(ii'),(jj'),(kk')] = sum_s K[s,i,j,k] conj(B[s,i',j',k']) (four planes).
+// rot = 1 cycles the legs of both layers so that the z leg comes first.
+__device__ __forceinline__ void zc_layer_entry(int D, long long t, int rot, int &kidx, int &bidx)
+{
+    const int D2 = D * D;
+    const int u = (int)(t / ((long long)D2 * D2)), l = (int)((t / D2) % D2), z = (int)(t % D2);
+    const int i = u / D, ip = u % D, j = l / D, jp = l % D, k = z / D, kp = z % D;
+    if (!rot) {
+        kidx = (i * D + j) * D + k;
+        bidx = (ip * D + jp) * D + kp;
+    } else {   // legs (z, x, y): the first index is the z leg of A
+        kidx = (j * D + k) * D + i;
+        bidx = (jp * D + kp) * D + ip;
+    }
+}
+
+__global__ void zc_double_layer_kernel(int d, int D, const double *A, long long PA, double *a, long long Pa)
+{
+    const long long D6 = (long long)D * D * D * D * D * D;
+    const int D3 = D * D * D;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < D6;
+         t += (long long)gridDim.x * blockDim.x) {
+        int ki, bi;
+        zc_layer_entry(D, t, 0, ki, bi);
+        double re = 0.0, im = 0.0;
+        for (int s = 0; s < d; ++s) {
+            const double kr = A[s * D3 + ki], kim = A[PA + s * D3 + ki];
+            const double br = A[s * D3 + bi], bim = A[PA + s * D3 + bi];
+            re += kr * br + kim * bim;
+            im += kim * br - kr * bim;
+        }
+        a[t] = re;
+        a[Pa + t] = im;
+        a[2 * Pa + t] = -im;
+        a[3 * Pa + t] = re;
+    }
+}
+
+// open layers b[p = s*d + t][(ii'),(jj'),(kk')] = A[s, ...] conj(A[t, ...]) (four planes)
+__global__ void zc_open_layers_kernel(int d, int D, const double *A, long long PA, int rot, double *b, long long Pb)
+{
+    const long long D6 = (long long)D * D * D * D * D * D;
+    const int D3 = D * D * D;
+    const long long tot = D6 * d * d;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int p = (int)(t / D6);
+        const long long e = t - (long long)p * D6;
+        const int s = p / d, tt = p % d;
+        int ki, bi;
+        zc_layer_entry(D, e, rot, ki, bi);
+        const double kr = A[s * D3 + ki], kim = A[PA + s * D3 + ki];
+        const double br = A[tt * D3 + bi], bim = A[PA + tt * D3 + bi];
+        const double re = kr * br + kim * bim, im = kim * br - kr * bim;
+        b[t] = re;
+        b[Pb + t] = im;
+        b[2 * Pb + t] = -im;
+        b[3 * Pb + t] = re;
+    }
+}
+
+// C = I, T[a][u][b] = delta_ab t_u with t_u = sum_{v,w} a[u][(vv)][(ww)], Q = first chi columns of I
+__global__ void zc_init_env_kernel(int chi, int D, const double *a, long long Pa, double *C, long long PC, double *T,
+                                   long long PT, double *Q, long long PQ)
+{
+    const int D2 = D * D;
+    const long long n = (long long)chi * D2;
+    const long long tot = (long long)chi * D2 * chi;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int al = (int)(t / ((long long)D2 * chi)), u = (int)((t / chi) % D2), be = (int)(t % chi);
+        double re = 0.0, im = 0.0;
+        if (al == be)
+            for (int v = 0; v < D; ++v)
+                for (int w = 0; w < D; ++w) {
+                    const long long o = ((long long)u * D2 + v * D + v) * D2 + w * D + w;
+                    re += a[o];
+                    im += a[Pa + o];
+                }
+        T[t] = re;
+        T[PT + t] = im;
+        T[2 * PT + t] = -im;
+        T[3 * PT + t] = re;
+    }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)chi * chi;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double v = (t / chi == t % chi) ? 1.0 : 0.0;
+        C[t] = v;
+        C[PC + t] = 0.0;
+        C[2 * PC + t] = 0.0;
+        C[3 * PC + t] = v;
+    }
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * chi;
+         t += (long long)gridDim.x * blockDim.x) {
+        const double v = (t / chi == t % chi) ? 1.0 : 0.0;
+        Q[t] = v;
+        Q[PQ + t] = 0.0;
+        Q[2 * PQ + t] = 0.0;
+        Q[3 * PQ + t] = v;
+    }
+}
+
+// Qs = Q diag(sgn Re C_jj) (sgn 0 = +1), four planes
+__global__ void zc_warm_start_kernel(long long n, int chi, const double *Q, long long PQ, const double *C, double *Qs)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * chi;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int j = (int)(t % chi);
+        const double sg = C[(long long)j * chi + j] < 0.0 ? -1.0 : 1.0;
+        for (int p = 0; p < 4; ++p) Qs[p * PQ + t] = sg * Q[p * PQ + t];
+    }
+}
+
+// E[(r,c),(j,c')] = [[Re y, -Im y], [Im y, Re y]][c][c'] (2n x 2k, row-major)
+__global__ void zc_embed_kernel(long long n, int k, const double *Y, long long PY, double *E)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * k;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / k;
+        const int j = (int)(t % k);
+        const double re = Y[t], im = Y[PY + t];
+        const long long ld = 2LL * k;
+        E[(2 * r) * ld + 2 * j] = re;
+        E[(2 * r) * ld + 2 * j + 1] = -im;
+        E[(2 * r + 1) * ld + 2 * j] = im;
+        E[(2 * r + 1) * ld + 2 * j + 1] = re;
+    }
+}
+
+// complex factor from the first column of each 2 x 2 block of an embedding
+__global__ void zc_extract_kernel(long long n, int k, const double *E, double *Z, long long PZ, int planes)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * k;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long r = t / k;
+        const int j = (int)(t % k);
+        const long long ld = 2LL * k;
+        const double re = E[(2 * r) * ld + 2 * j], im = E[(2 * r + 1) * ld + 2 * j];
+        Z[t] = re;
+        Z[PZ + t] = im;
+        if (planes == 4) {
+            Z[2 * PZ + t] = -im;
+            Z[3 * PZ + t] = re;
+        }
+    }
+}
+
+// Fig. 3a: Cn = (Cr + Cr^H)/2 normalised (four planes); one CTA.
+__global__ void zc_herm_normalize_kernel(int chi, const double *Cr, long long PCr, double *Cn, long long PC)
+{
+    __shared__ double red[32];
+    __shared__ double inv;
+    const int nn = chi * chi;
+    double acc = 0.0;
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int i = t / chi, j = t % chi;
+        const double re = 0.5 * (Cr[t] + Cr[j * chi + i]);
+        const double im = 0.5 * (Cr[PCr + t] - Cr[PCr + j * chi + i]);
+        acc += re * re + im * im;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+        inv = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        const int i = t / chi, j = t % chi;
+        const double re = 0.5 * (Cr[t] + Cr[j * chi + i]) * inv;
+        const double im = 0.5 * (Cr[PCr + t] - Cr[PCr + j * chi + i]) * inv;
+        Cn[t] = re;
+        Cn[PC + t] = im;
+        Cn[2 * PC + t] = -im;
+        Cn[3 * PC + t] = re;
+    }
+}
+
+// the real symmetric embedding [[Re C, -Im C], [Im C, Re C]] (2chi x 2chi) of a Hermitian C
+__global__ void zc_embed_herm_kernel(int chi, const double *C, long long PC, double *E)
+{
+    const int m = 2 * chi;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
+        const int I = t / m, J = t % m;
+        const int i = I % chi, j = J % chi, bi = I / chi, bj = J / chi;
+        const double re = C[i * chi + j], im = C[PC + i * chi + j];
+        E[t] = (bi == bj) ? re : (bi == 1 ? im : -im);
+    }
+}
+
+// raw[pA][pB] = sum_{ab, z} Y1o[ab][pB][z] G2[ab][pA][z] (complex, no conjugation)
+__global__ void zc_rho_partial_kernel(long long nab, int dd, int D2, const double *Y1o, const double *G2,
+                                      long long P, double *partials)
+{
+    __shared__ double red[2 * ZRHO_MAX_DD * ZRHO_MAX_DD][8];
+    double acc[2 * ZRHO_MAX_DD * ZRHO_MAX_DD];
+    for (int i = 0; i < 2 * dd * dd; ++i) acc[i] = 0.0;
+    const long long row = (long long)dd * D2;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nab * D2;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long ab = t / D2;
+        const int z = (int)(t - ab * D2);
+        const long long o = ab * row + z;
+        for (int pb = 0; pb < dd; ++pb) {
+            const double yr = Y1o[o + pb * D2], yi = Y1o[P + o + pb * D2];
+            for (int pa = 0; pa < dd; ++pa) {
+                const double gr = G2[o + pa * D2], gi = G2[P + o + pa * D2];
+                acc[2 * (pa * dd + pb)] += yr * gr - yi * gi;
+                acc[2 * (pa * dd + pb) + 1] += yr * gi + yi * gr;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = 0; i < 2 * dd * dd; ++i) {
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[i][warp] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 2 * dd * dd) {
+        double s = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
+        partials[(size_t)blockIdx.x * 2 * dd * dd + threadIdx.x] = s;
+    }
+}
+
+// Eq. 1: rho[(sA sB)][(tA tB)] = raw[(sA tA)][(sB tB)] / tr; e_a = Re tr(rho h'_a) with the
+// rotated bond operators h'_a; out = e_x, e_y, e_z, E_site, then rho (complex, interleaved).
+__global__ void zc_energy_kernel(int d, int nparts, const double *partials, const double *hrot, double *out)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const int dd = d * d;
+    double raw[2 * ZRHO_MAX_DD * ZRHO_MAX_DD];
+    for (int i = 0; i < 2 * dd * dd; ++i) {
+        double s = 0.0;
+        for (int b = 0; b < nparts; ++b) s += partials[(size_t)b * 2 * dd * dd + i];
+        raw[i] = s;
+    }
+    double zr = 0.0, zi = 0.0;
+    for (int sA = 0; sA < d; ++sA)
+        for (int sB = 0; sB < d; ++sB) {
+            const int o = 2 * ((sA * d + sA) * dd + sB * d + sB);
+            zr += raw[o];
+            zi += raw[o + 1];
+        }
+    const double zz = zr * zr + zi * zi;
+    double *rho = out + 4;
+    for (int sA = 0; sA < d; ++sA)
+        for (int sB = 0; sB < d; ++sB)
+            for (int tA = 0; tA < d; ++tA)
+                for (int tB = 0; tB < d; ++tB) {
+                    const int o = 2 * ((sA * d + tA) * dd + sB * d + tB);
+                    const int r = 2 * ((sA * d + sB) * dd + tA * d + tB);
+                    rho[r] = (raw[o] * zr + raw[o + 1] * zi) / zz;
+                    rho[r + 1] = (raw[o + 1] * zr - raw[o] * zi) / zz;
+                }
+    double es = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e = 0.0;
+        for (int r = 0; r < dd; ++r)
+            for (int c = 0; c < dd; ++c) {
+                const double *h = hrot + 2 * ((size_t)a * dd * dd + c * dd + r);
+                e += rho[2 * (r * dd + c)] * h[0] - rho[2 * (r * dd + c) + 1] * h[1];
+            }
+        out[a] = e;
+        es += e;
+    }
+    out[3] = 0.5 * es;
+}
+
+__global__ void zc_check_finite_kernel(long long count, const double *x, int *flag)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        if (!isfinite(x[t])) *flag = 1;
+}
+
+// ------------------------------------------------------------------ host helpers
+#define ZK(expr)                                          \
+    do {                                                  \
+        cudaError_t _e = (expr);                          \
+        if (_e != cudaSuccess) return CTM_ECUDA;          \
+    } while (0)
+
+#define ZLAUNCH(kernel, grid, block, ...)                          \
+    do {                                                           \
+        CTM_COUNT_LAUNCH(1);                                       \
+        kernel<<<(grid), (block), 0, c->stream>>>(__VA_ARGS__);    \
+        ZK(cudaGetLastError());                                    \
+    } while (0)
+
+// A complex contraction C(m,n) = sum_k op(A)(m,k) op(B)(k,n) of planar tensors; the left
+// operand's k map is a plain stride (the plane index is stacked on it), B has four planes.
+struct ZGemm {
+    int M, N, K;
+    const double *A;
+    long long PA;
+    Idx2 Am, Ak;
+    int conjA;
+    const double *B;
+    long long PB;
+    Idx2 Bk, Bn;
+    int conjB;
+    double *C;
+    long long PC;
+    Idx2 Cm, Cn;
+};
+
+int real_gemm(ctm_complex_ctx *c, const GemmF64 &g, int reuse_a)
+{
+    if (c->split_T > 0) {
+        SplitOpts o{};
+        o.reuse_a = reuse_a;
+        return gemm_split(g, c->split_T, c->sw, c->stream, nullptr, &o) == cudaSuccess ? CTM_OK : CTM_ECUDA;
+    }
+    return gemm_f64(g, gemm_f64_pick_split(g.M, g.N, g.K), c->splitk, c->splitk_elems, c->stream) == cudaSuccess
+               ? CTM_OK
+               : CTM_ECUDA;
+}
+
+int zgemm(ctm_complex_ctx *c, const ZGemm &z)
+{
+    if (z.Ak.s1 != 0 || z.Bk.s1 != 0) return CTM_EINVAL;
+    const Idx2 Ak2{z.K, (z.conjA ? 2 : 1) * z.PA, z.Ak.s2};
+    // Re C: [Re B ; -s_B Im B] = planes (0, 2) (s_B = +1) or (0, 1) (conjugated B)
+    const Idx2 Bkr{z.K, (z.conjB ? 1 : 2) * z.PB, z.Bk.s2};
+    // Im C: [s_B Im B ; Re B] = planes (1, 3) or (2, 3)
+    const double *Bi = z.B + (z.conjB ? 2 : 1) * z.PB;
+    const Idx2 Bki{z.K, (z.conjB ? 1 : 2) * z.PB, z.Bk.s2};
+    GemmF64 gr{z.M, z.N, 2 * z.K, z.A, z.Am, Ak2, z.B, Bkr, z.Bn, z.C, z.Cm, z.Cn, 1.0, 0.0};
+    GemmF64 gi{z.M, z.N, 2 * z.K, z.A, z.Am, Ak2, Bi, Bki, z.Bn, z.C + z.PC, z.Cm, z.Cn, 1.0, 0.0};
+    int rc = real_gemm(c, gr, 0);
+    if (rc != CTM_OK) return rc;
+    return real_gemm(c, gi, 1);
+}
+
+int znormalize(ctm_complex_ctx *c, long long count, double *x, long long P, int planes)
+{
+    int nb = zgrid(count);
+    if (nb > ZNORM_BLOCKS) nb = ZNORM_BLOCKS;
+    ZLAUNCH(zc_sumsq_kernel, nb, 256, count, x, P, c->norm_part);
+    ZLAUNCH(zc_scale_kernel, zgrid(count), 256, count, x, P, c->norm_part, nb, planes);
+    return CTM_OK;
+}
+
+QrScratch zqr_scratch(ctm_complex_ctx *c)
+{
+    const long long k = 2LL * c->chi;
+    QrScratch q;
+    memset(&q, 0, sizeof(q));
+    q.sbuf = c->qr_sbuf;
+    q.rowbuf = c->qr_rowbuf;
+    q.bar = c->qr_bar;
+    q.err = c->err;
+    q.rows_min = 1;
+    q.V = c->qr_wy;
+    q.S = q.V + k * k;
+    q.W = q.S + k * k;
+    q.ta = q.W + k * k;
+    return q;
+}
+
+// (M, N, K) of the real products (K doubled) of the step and the energy
+std::vector<std::array<int, 3>> zshapes(const ctm_complex_ctx *c)
+{
+    const int chi = c->chi, D2 = c->D2, n = (int)c->n, dd = c->d * c->d;
+    return {{n, chi, 2 * chi},          {n, n, 2 * chi},          {chi * chi, D2, 2 * D2 * D2},
+            {chi * chi, D2 * D2, 2 * D2}, {n, chi, 2 * n},          {chi, chi, 2 * n},
+            {n, chi, 2 * chi},          {chi, chi, 2 * chi},      {chi * chi, dd * D2, 2 * D2 * D2}};
+}
+
+size_t zlayout(ctm_complex_ctx *c, char *base)
+{
+    const long long chi = c->chi, D2 = c->D2, n = c->n, d = c->d, D = c->D;
+    const long long D3 = D2 * D2 * D2, dd = d * d, k2 = 2 * chi;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    auto td = [&](long long count) -> double * { return (double *)take(sizeof(double) * (size_t)count); };
+    c->PA = d * D * D * D;
+    c->Ain = td(2 * c->PA);
+    c->A = td(2 * c->PA);
+    c->Pa = D3;
+    c->a = td(4 * D3);
+    c->Pb = dd * D3;
+    c->bB = td(4 * c->Pb);
+    c->bA = td(4 * c->Pb);
+    c->PC = chi * chi;
+    c->C = td(4 * c->PC);
+    c->Cn = td(4 * c->PC);
+    c->Cr = td(2 * c->PC);
+    c->R = td(2 * c->PC);
+    c->P5a = td(2 * c->PC);
+    c->P5b = td(4 * c->PC);
+    c->PT = chi * D2 * chi;
+    c->T = td(4 * c->PT);
+    c->Tn = td(4 * c->PT);
+    c->PQ = n * chi;
+    c->Q = td(4 * c->PQ);
+    c->Qn = td(4 * c->PQ);
+    c->Qs = td(4 * c->PQ);
+    c->PY = n * chi;
+    c->Y = td(2 * c->PY);
+    c->W = td(2 * c->PY);
+    c->MQ = td(2 * c->PY);
+    c->PM = n * n;
+    c->M = td(2 * c->PM);
+    c->X = td(2 * c->PM);
+    c->H = td(2 * c->PM);
+    c->PY1 = chi * chi * D2;
+    c->Y1 = td(2 * c->PY1);
+    c->PYo = chi * chi * dd * D2;
+    c->Y1o = td(2 * c->PYo);
+    c->G2 = td(2 * c->PYo);
+    c->Yemb = td(2 * n * k2);
+    c->Qemb = td(2 * n * k2);
+    c->Remb = td(k2 * k2);
+    c->Cemb = td(k2 * k2);
+    c->s = td(k2);
+    c->s_new = td(k2);
+    c->delta = td(8);
+    c->spec_work = td((long long)spectrum_work_doubles((int)k2));
+    size_t sk = 0;
+    for (const auto &sh : zshapes(c)) {
+        int s = gemm_f64_pick_split(sh[0], sh[1], sh[2]);
+        if (s > 1 && (size_t)s * sh[0] * sh[1] > sk) sk = (size_t)s * sh[0] * sh[1];
+    }
+    c->splitk_elems = sk;
+    c->splitk = td((long long)sk + 1);
+    c->qr_sbuf = td((long long)qr_scratch_doubles((int)k2));
+    c->qr_rowbuf = td((long long)qr_rowbuf_doubles((int)k2));
+    c->qr_wy = td((long long)qr_wy_doubles((int)(2 * n), (int)k2));
+    c->qr_bar = (unsigned *)take(64);
+    c->err = (int *)take(64);
+    c->flag = (int *)take(64);
+    c->norm_part = td(ZNORM_BLOCKS);
+    c->rho_part = td((long long)ZRHO_BLOCKS * 2 * dd * dd);
+    c->rho_raw = td(2 * dd * dd);
+    c->hrot = td(3 * 2 * dd * dd);
+    c->eout = td(4 + 2 * dd * dd);
+    if (c->split_T > 0) {
+        size_t ap = 0, bp = 0, pp = 0;
+        long long ecap = 0;
+        for (const auto &sh : zshapes(c)) {
+            SplitPlan pl = split_plan_caps(sh[0], sh[1], sh[2], c->split_T);
+            if (pl.a_pack_bytes > ap) ap = pl.a_pack_bytes;
+            if (pl.b_pack_bytes > bp) bp = pl.b_pack_bytes;
+            if (pl.partial_bytes > pp) pp = pl.partial_bytes;
+            if (sh[0] > ecap) ecap = sh[0];
+            if (sh[1] > ecap) ecap = sh[1];
+        }
+        c->sw.Apk = (unsigned char *)take(ap);
+        c->sw.a_pack_cap = ap;
+        c->sw.Bpk = (unsigned char *)take(bp);
+        c->sw.b_pack_cap = bp;
+        c->sw.eA = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw.eB = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw.e_cap = (int)ecap;
+        c->sw.partial = (void *)take(pp + 8);
+        c->sw.partial_cap = pp;
+        c->sw.err = c->err;
+        c->sw.autotune = 1;
+    }
+    return off;
+}
+
+bool zconfig_ok(const ctm_config *cfg, int irrep)
+{
+    if (!cfg) return false;
+    if (irrep != CTM_IRREP_A1 && irrep != CTM_IRREP_E) return false;
+    if (cfg->d < 1 || cfg->d > ZMAX_D) return false;
+    if (irrep == CTM_IRREP_E && cfg->d < 2) return false;
+    if (cfg->D < 1 || cfg->D > 10) return false;
+    if (cfg->chi < 1 || cfg->chi > 80) return false;
+    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return false;
+    if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
+    if (cfg->corner_mode != 0) return false;
+    const long long n = (long long)cfg->chi * cfg->D * cfg->D;
+    if (n > 12000) return false;
+    return qr_supported((int)(2 * n), 2 * cfg->chi) != 0;
+}
+
+int zread_status(ctm_complex_ctx *c)
+{
+    int err = 0;
+    ZK(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    ZK(cudaStreamSynchronize(c->stream));
+    return err ? CTM_ETIMEOUT : CTM_OK;
+}
+
+// ------------------------------------------------------------------ the step
+// Fig. 3c: W = T C; X'[a][b][u][l] = sum_h W[(a,u),h] conj(T[(b,l),h]);
+// Y1[(a,b)][z] = sum_{u,l} X' a[u,l,z]; M[(a,y)][(b,x)] = sum_z Y1 a[z,x,y]
+int zenlarged_corner(ctm_complex_ctx *c)
+{
+    const int chi = c->chi, D2 = c->D2;
+    const long long n = c->n;
+    int rc;
+    ZGemm z{(int)n, chi, chi, c->T, c->PT, idx_lin(chi), idx_lin(1), 0, c->C, c->PC, idx_lin(chi), idx_lin(1), 0,
+            c->W, c->PY, idx_lin(chi), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    z = ZGemm{(int)n, (int)n, chi, c->W, c->PY, idx_lin(chi), idx_lin(1), 0, c->T, c->PT, idx_lin(1), idx_lin(chi), 1,
+              c->X, c->PM, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    z = ZGemm{chi * chi, D2, D2 * D2, c->X, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->a, c->Pa,
+              idx_lin(D2), idx_lin(1), 0, c->Y1, c->PY1, idx_lin(D2), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, c->PY1, idx_lin(D2), idx_lin(1), 0, c->a, c->Pa,
+              idx_lin((long long)D2 * D2), idx_split(D2, 1, D2), 0, c->M, c->PM,
+              idx_split(chi, (long long)D2 * n, D2), idx_split(D2, n, 1)};
+    return zgemm(c, z);
+}
+
+// Fig. 3d: Y = M Q diag(sgn Re C_jj); Y = Q R through the real QR of the embedding
+int zprojector(ctm_complex_ctx *c)
+{
+    const int chi = c->chi;
+    const long long n = c->n;
+    int rc;
+    ZLAUNCH(zc_warm_start_kernel, zgrid(n * chi), 256, n, chi, c->Q, c->PQ, c->C, c->Qs);
+    ZGemm z{(int)n, chi, (int)n, c->M, c->PM, idx_lin(n), idx_lin(1), 0, c->Qs, c->PQ, idx_lin(chi), idx_lin(1), 0,
+            c->Y, c->PY, idx_lin(chi), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    ZLAUNCH(zc_embed_kernel, zgrid(n * chi), 256, n, chi, c->Y, c->PY, c->Yemb);
+    ZK(qr_householder((int)(2 * n), 2 * chi, c->Yemb, c->Qemb, c->Remb, zqr_scratch(c), c->stream));
+    ZLAUNCH(zc_extract_kernel, zgrid(n * chi), 256, n, chi, c->Qemb, c->Qn, c->PQ, 4);
+    ZLAUNCH(zc_extract_kernel, zgrid((long long)chi * chi), 256, (long long)chi, chi, c->Remb, c->R, c->PC, 2);
+    return CTM_OK;
+}
+
+// Fig. 3a: Cn = sym(Qn^H M Qn)/|.|, through Cr[i][j] = sum_r MQ[r][j] conj(Qn[r][i])
+int zcorner(ctm_complex_ctx *c, double *Cout)
+{
+    const int chi = c->chi;
+    const long long n = c->n;
+    int rc;
+    ZGemm z{(int)n, chi, (int)n, c->M, c->PM, idx_lin(n), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 0,
+            c->MQ, c->PY, idx_lin(chi), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    z = ZGemm{chi, chi, (int)n, c->MQ, c->PY, idx_lin(1), idx_lin(chi), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 1,
+              c->Cr, c->PC, idx_lin(1), idx_lin(chi)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    ZLAUNCH(zc_herm_normalize_kernel, 1, 1024, chi, c->Cr, c->PC, Cout, c->PC);
+    return CTM_OK;
+}
+
+// Fig. 3b: T'[i,x,j] = sum conj(Q[(a,y),i]) T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j], normalised
+int zedge(ctm_complex_ctx *c)
+{
+    const int chi = c->chi, D2 = c->D2;
+    const long long n = c->n;
+    int rc;
+    // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]
+    ZGemm z{(int)n, (int)n, chi, c->T, c->PT, idx_lin(chi), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(n),
+            idx_split(D2, 1, chi), 0, c->X, c->PM, idx_split(D2, (long long)chi * D2 * D2, D2),
+            idx_split(D2, (long long)D2 * D2, 1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
+    z = ZGemm{chi * chi, D2, D2 * D2, c->X, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->a, c->Pa,
+              idx_lin(D2), idx_lin(1), 0, c->Y1, c->PY1, idx_lin(D2), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // H3'[a][y][x][j] = H2[(a,j),z] a[z,x,y]
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, c->PY1, idx_lin(D2), idx_lin(1), 0, c->a, c->Pa,
+              idx_lin((long long)D2 * D2), idx_split(D2, 1, D2), 0, c->H, c->PM,
+              idx_split(chi, (long long)D2 * D2 * chi, 1), idx_split(D2, (long long)D2 * chi, chi)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // T'[i][(x,j)] = sum_{(a,y)} H3'[(a,y),(x,j)] conj(Q[(a,y),i])
+    z = ZGemm{(int)n, chi, (int)n, c->H, c->PM, idx_lin(1), idx_lin(n), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 1,
+              c->Tn, c->PT, idx_lin(1), idx_lin(n)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    return znormalize(c, (long long)chi * D2 * chi, c->Tn, c->PT, 4);
+}
+
+int zspectrum(ctm_complex_ctx *c, const double *Cin)
+{
+    const int k2 = 2 * c->chi;
+    ZLAUNCH(zc_embed_herm_kernel, (k2 * k2 + 255) / 256, 256, c->chi, Cin, c->PC, c->Cemb);
+    ZK(launch_spectrum(k2, c->Cemb, c->s_new, c->s, c->delta, c->spec_work, c->stream));
+    ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * k2, cudaMemcpyDeviceToDevice, c->stream));
+    return CTM_OK;
+}
+
+int zstep(ctm_complex_ctx *c)
+{
+    int rc;
+    if ((rc = zenlarged_corner(c)) != CTM_OK) return rc;
+    if ((rc = zprojector(c)) != CTM_OK) return rc;
+    if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
+    if ((rc = zedge(c)) != CTM_OK) return rc;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    cudaStream_t st = c->stream;
+    ZK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * 4 * chi * chi, cudaMemcpyDeviceToDevice, st));
+    ZK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * 4 * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
+    ZK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * 4 * n * chi, cudaMemcpyDeviceToDevice, st));
+    if ((rc = zspectrum(c, c->C)) != CTM_OK) return rc;
+    c->steps_done++;
+    return CTM_OK;
+}
+
+int zcheck_env_finite(ctm_complex_ctx *c)
+{
+    cudaStream_t st = c->stream;
+    ZK(cudaMemsetAsync(c->flag, 0, sizeof(int), st));
+    ZLAUNCH(zc_check_finite_kernel, zgrid(2 * c->PC), 256, 2 * c->PC, c->C, c->flag);
+    ZLAUNCH(zc_check_finite_kernel, zgrid(2 * c->PT), 256, 2 * c->PT, c->T, c->flag);
+    int f = 0;
+    ZK(cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    ZK(cudaStreamSynchronize(st));
+    return f ? CTM_ENONFINITE : CTM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ctm_complex_workspace_bytes(const ctm_config *cfg, int irrep)
+{
+    if (!zconfig_ok(cfg, irrep)) return 0;
+    ctm_complex_ctx c;
+    memset(&c, 0, sizeof(c));
+    c.cfg = *cfg;
+    c.d = cfg->d;
+    c.D = cfg->D;
+    c.D2 = cfg->D * cfg->D;
+    c.chi = cfg->chi;
+    c.n = (long long)c.chi * c.D2;
+    c.split_T = cfg->precision == CTM_SPLIT_BF16 ? cfg->n_split : 0;
+    return zlayout(&c, nullptr);
+}
+
+int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void *workspace, size_t ws_bytes,
+                     void *stream, ctm_complex_ctx **out)
+{
+    if (!out) return CTM_EINVAL;
+    *out = nullptr;
+    if (!cfg || !A_dev || !workspace) return CTM_EINVAL;
+    if (!zconfig_ok(cfg, irrep)) return CTM_EINVAL;
+    if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
+    ctm_complex_ctx *c = new (std::nothrow) ctm_complex_ctx;
+    if (!c) return CTM_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->cfg = *cfg;
+    c->irrep = irrep;
+    c->d = cfg->d;
+    c->D = cfg->D;
+    c->D2 = cfg->D * cfg->D;
+    c->chi = cfg->chi;
+    c->n = (long long)c->chi * c->D2;
+    c->split_T = cfg->precision == CTM_SPLIT_BF16 ? cfg->n_split : 0;
+    c->stream = (cudaStream_t)stream;
+    if (ws_bytes < zlayout(c, nullptr)) {
+        delete c;
+        return CTM_ENOMEM;
+    }
+    zlayout(c, (char *)workspace);
+    ZGroup grp;
+    HMat Ur;
+    if (!make_group(c->d, irrep, &grp, &Ur)) {
+        delete c;
+        return CTM_EUNSUPPORTED;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            c->U[i][j][0] = (i < c->d && j < c->d) ? Ur.v[i][j].re : 0.0;
+            c->U[i][j][1] = (i < c->d && j < c->d) ? Ur.v[i][j].im : 0.0;
+        }
+    int rc = CTM_OK;
+    do {
+        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
+        const long long cnt = c->PA;
+        if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        CTM_COUNT_LAUNCH(4);
+        zc_planar_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(cnt, A_dev, c->Ain, cnt, 2);
+        zc_project_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(c->d, c->D, c->Ain, cnt, grp, cfg->symmetrize ? 1 : 0,
+                                                             c->A, cnt);
+        if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if ((rc = znormalize(c, cnt, c->A, cnt, 2)) != CTM_OK) break;
+        const long long D6 = c->Pa;
+        zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, c->a, c->Pa);
+        zc_init_env_kernel<<<zgrid(c->PT), 256, 0, c->stream>>>(c->chi, c->D, c->a, c->Pa, c->C, c->PC, c->T,
+                                                                c->PT, c->Q, c->PQ);
+        if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (launch_spectrum_init(2 * c->chi, c->s, c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        CTM_COUNT_LAUNCH(1);
+        zc_check_finite_kernel<<<zgrid(2 * cnt), 256, 0, c->stream>>>(2 * cnt, c->A, c->flag);
+        int f = 0;
+        if (cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
+        if (f) rc = CTM_ENONFINITE;
+    } while (0);
+    if (rc != CTM_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return CTM_OK;
+}
+
+int ctm_complex_step(ctm_complex_ctx *c, int nsteps, double *delta_host)
+{
+    if (!c || nsteps < 1) return CTM_EINVAL;
+    int rc;
+    for (int k = 0; k < nsteps; ++k)
+        if ((rc = zstep(c)) != CTM_OK) return rc;
+    if ((rc = zread_status(c)) != CTM_OK) return rc;
+    if (delta_host) {
+        ZK(cudaMemcpyAsync(delta_host, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+        ZK(cudaStreamSynchronize(c->stream));
+        if (!isfinite(*delta_host)) return CTM_ENONFINITE;
+        return zcheck_env_finite(c);
+    }
+    return CTM_OK;
+}
+
+int ctm_complex_converge(ctm_complex_ctx *c, int max_steps, double tol, int check_every, int *steps_out,
+                         double *delta_out)
+{
+    if (!c) return CTM_EINVAL;
+    if (max_steps <= 0) max_steps = c->cfg.max_steps;
+    if (tol <= 0.0) tol = c->cfg.tol;
+    if (check_every < 1) check_every = 1;
+    if (max_steps <= 0) return CTM_EINVAL;
+    int done = 0, rc;
+    double delta = INFINITY;
+    while (done < max_steps) {
+        const int k = (max_steps - done) < check_every ? (max_steps - done) : check_every;
+        if ((rc = ctm_complex_step(c, k, &delta)) != CTM_OK && rc != CTM_ENONFINITE) return rc;
+        done += k;
+        if (rc == CTM_ENONFINITE) return rc;
+        if (delta < tol) break;
+    }
+    if (steps_out) *steps_out = done;
+    if (delta_out) *delta_out = delta;
+    return delta < tol ? CTM_OK : CTM_ENOTCONVERGED;
+}
+
+int ctm_complex_energy(ctm_complex_ctx *c, const double *h_dev, double *e_bond_host, double *e_site_host,
+                       double *rho_host)
+{
+    if (!c || !h_dev) return CTM_EINVAL;
+    const int chi = c->chi, D2 = c->D2, d = c->d, dd = d * d;
+    const long long n = c->n, D3 = (long long)D2 * D2 * D2;
+    int rc;
+    if (dd > ZRHO_MAX_DD) return CTM_EUNSUPPORTED;
+    // the rotated bond operators h'_a = W_a^H h_a W_a, W_x = U^2 (x) U^2, W_y = U (x) U, W_z = I:
+    // the x and y bonds are the z bond of the rotated tensor (App. A, the C3 symmetry)
+    double hh[3 * 2 * ZRHO_MAX_DD * ZRHO_MAX_DD];
+    ZK(cudaMemcpyAsync(hh, h_dev, sizeof(double) * 3 * 2 * dd * dd, cudaMemcpyDeviceToHost, c->stream));
+    ZK(cudaStreamSynchronize(c->stream));
+    {
+        HMat U = hm_zero(d);
+        for (int i = 0; i < d; ++i)
+            for (int j = 0; j < d; ++j) U.v[i][j] = Cx{c->U[i][j][0], c->U[i][j][1]};
+        const HMat U2 = hm_mul(U, U);
+        double hr[3 * 2 * ZRHO_MAX_DD * ZRHO_MAX_DD];
+        for (int a = 0; a < 3; ++a) {
+            const HMat &V = a == 0 ? U2 : U;
+            auto Wel = [&](int r, int q) -> Cx {   // (V (x) V)[r][q], r = (s, t)
+                if (a == 2) return Cx{r == q ? 1.0 : 0.0, 0.0};
+                return cmul(V.v[r / d][q / d], V.v[r % d][q % d]);
+            };
+            for (int r = 0; r < dd; ++r)
+                for (int q = 0; q < dd; ++q) {
+                    Cx acc{0.0, 0.0};
+                    for (int i = 0; i < dd; ++i)
+                        for (int j = 0; j < dd; ++j) {
+                            const double *hv = hh + 2 * ((size_t)a * dd * dd + i * dd + j);
+                            acc = cadd(acc, cmul(cmul(cconj(Wel(i, r)), Cx{hv[0], hv[1]}), Wel(j, q)));
+                        }
+                    hr[2 * ((size_t)a * dd * dd + r * dd + q)] = acc.re;
+                    hr[2 * ((size_t)a * dd * dd + r * dd + q) + 1] = acc.im;
+                }
+        }
+        ZK(cudaMemcpyAsync(c->hrot, hr, sizeof(double) * 3 * 2 * dd * dd, cudaMemcpyHostToDevice, c->stream));
+        ZK(cudaStreamSynchronize(c->stream));
+    }
+    // projector of one more step and Ch = sym(Q^H M Q)/|.|
+    if ((rc = zenlarged_corner(c)) != CTM_OK) return rc;
+    if ((rc = zprojector(c)) != CTM_OK) return rc;
+    if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
+    // P5 = Ch^5
+    const double *src = c->Cn;
+    double *bufs[2] = {c->P5a, c->P5b};
+    for (int p = 0; p < 4; ++p) {
+        double *dst = bufs[p & 1];
+        ZGemm z{chi, chi, chi, src, c->PC, idx_lin(chi), idx_lin(1), 0, c->Cn, c->PC, idx_lin(chi), idx_lin(1), 0,
+                dst, c->PC, idx_lin(chi), idx_lin(1)};
+        if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+        src = dst;
+    }
+    ZLAUNCH(zc_complete_kernel, zgrid((long long)chi * chi), 256, (long long)chi * chi, c->P5b, c->PC);
+    // F = Q P5 (n x chi) into W; E'[(a,b)][(x,y)] = E[(b,x),(a,y)], E = F Q^H, into H
+    ZGemm z{(int)n, chi, chi, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 0, c->P5b, c->PC, idx_lin(chi), idx_lin(1), 0,
+            c->W, c->PY, idx_lin(chi), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    z = ZGemm{(int)n, (int)n, chi, c->W, c->PY, idx_lin(chi), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(1), idx_lin(chi), 1,
+              c->H, c->PM, idx_split(D2, (long long)D2 * D2, D2), idx_split(D2, (long long)chi * D2 * D2, 1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // open layers: the outer site B with its legs as they are, the apex site A with z first
+    CTM_COUNT_LAUNCH(2);
+    zc_open_layers_kernel<<<zgrid(D3 * dd), 256, 0, c->stream>>>(d, c->D, c->A, c->PA, 0, c->bB, c->Pb);
+    zc_open_layers_kernel<<<zgrid(D3 * dd), 256, 0, c->stream>>>(d, c->D, c->A, c->PA, 1, c->bA, c->Pb);
+    ZK(cudaGetLastError());
+    // Y1o[(a,b)][(pB,z)] = sum_{u,l} X'[(a,b),(u,l)] bB[pB][u][l][z]
+    z = ZGemm{chi * chi, dd * D2, D2 * D2, c->X, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->bB, c->Pb,
+              idx_lin(D2), idx_split(D2, D3, 1), 0, c->Y1o, c->PYo, idx_lin((long long)dd * D2), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // G2[(a,b)][(pA,z)] = sum_{x,y} E'[(a,b),(x,y)] bA[pA][z][x][y]
+    z = ZGemm{chi * chi, dd * D2, D2 * D2, c->H, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->bA, c->Pb,
+              idx_lin(1), idx_split(D2, D3, (long long)D2 * D2), 0, c->G2, c->PYo, idx_lin((long long)dd * D2),
+              idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    ZLAUNCH(zc_rho_partial_kernel, ZRHO_BLOCKS, 256, (long long)chi * chi, dd, D2, c->Y1o, c->G2, c->PYo,
+            c->rho_part);
+    ZLAUNCH(zc_energy_kernel, 1, 32, d, ZRHO_BLOCKS, c->rho_part, c->hrot, c->eout);
+    double host[4 + 2 * ZRHO_MAX_DD * ZRHO_MAX_DD];
+    ZK(cudaMemcpyAsync(host, c->eout, sizeof(double) * (4 + 2 * dd * dd), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = zread_status(c)) != CTM_OK) return rc;
+    for (int i = 0; i < 4 + 2 * dd * dd; ++i)
+        if (!isfinite(host[i])) return CTM_ENONFINITE;
+    if (e_bond_host)
+        for (int i = 0; i < 3; ++i) e_bond_host[i] = host[i];
+    if (e_site_host) *e_site_host = host[3];
+    if (rho_host)
+        for (int i = 0; i < 2 * dd * dd; ++i) rho_host[i] = host[4 + i];
+    return CTM_OK;
+}
+
+int ctm_complex_get_env(const ctm_complex_ctx *c, double *C_dev, double *T_dev, double *Q_dev)
+{
+    if (!c) return CTM_EINVAL;
+    cudaStream_t st = c->stream;
+    auto out = [&](const double *src, long long cnt, long long P, double *dst) -> bool {
+        CTM_COUNT_LAUNCH(1);
+        zc_interleave_kernel<<<zgrid(cnt), 256, 0, st>>>(cnt, src, P, dst);
+        return cudaGetLastError() == cudaSuccess;
+    };
+    if (C_dev && !out(c->C, c->PC, c->PC, C_dev)) return CTM_ECUDA;
+    if (T_dev && !out(c->T, c->PT, c->PT, T_dev)) return CTM_ECUDA;
+    if (Q_dev && !out(c->Q, c->PQ, c->PQ, Q_dev)) return CTM_ECUDA;
+    ZK(cudaStreamSynchronize(st));
+    return CTM_OK;
+}
+
+int ctm_complex_set_env(ctm_complex_ctx *c, const double *C_dev, const double *T_dev, const double *Q_dev)
+{
+    if (!c || !C_dev || !T_dev || !Q_dev) return CTM_EINVAL;
+    cudaStream_t st = c->stream;
+    CTM_COUNT_LAUNCH(3);
+    zc_planar_kernel<<<zgrid(c->PC), 256, 0, st>>>(c->PC, C_dev, c->C, c->PC, 4);
+    zc_planar_kernel<<<zgrid(c->PT), 256, 0, st>>>(c->PT, T_dev, c->T, c->PT, 4);
+    zc_planar_kernel<<<zgrid(c->PQ), 256, 0, st>>>(c->PQ, Q_dev, c->Q, c->PQ, 4);
+    ZK(cudaGetLastError());
+    // the spectrum of the new corner becomes the reference for the next delta
+    const int k2 = 2 * c->chi;
+    CTM_COUNT_LAUNCH(1);
+    zc_embed_herm_kernel<<<(k2 * k2 + 255) / 256, 256, 0, st>>>(c->chi, c->C, c->PC, c->Cemb);
+    ZK(launch_spectrum(k2, c->Cemb, c->s, c->s, c->delta, c->spec_work, st));
+    ZK(cudaStreamSynchronize(st));
+    return CTM_OK;
+}
+
+int ctm_complex_get_intermediate(const ctm_complex_ctx *c, int which, double *dst, size_t count)
+{
+    if (!c || !dst) return CTM_EINVAL;
+    const long long chi = c->chi, D2 = c->D2, n = c->n;
+    cudaStream_t st = c->stream;
+    const double *src = nullptr;
+    long long cnt = 0, P = 0;
+    switch (which) {
+    case 0: src = c->M; cnt = n * n; P = c->PM; break;
+    case 1: src = c->Y; cnt = n * chi; P = c->PY; break;
+    case 2: src = c->R; cnt = chi * chi; P = c->PC; break;
+    case 3: src = c->Q; cnt = n * chi; P = c->PQ; break;
+    case 4: {   // the corner spectrum: every other value of the embedded one, times sqrt 2
+        if (count < (size_t)chi) return CTM_EINVAL;
+        std::vector<double> s2((size_t)(2 * chi));
+        ZK(cudaMemcpyAsync(s2.data(), c->s, sizeof(double) * 2 * chi, cudaMemcpyDeviceToHost, st));
+        ZK(cudaStreamSynchronize(st));
+        std::vector<double> s((size_t)chi);
+        for (long long i = 0; i < chi; ++i) s[i] = (s2[2 * i] + s2[2 * i + 1]) * sqrt(0.5);
+        ZK(cudaMemcpyAsync(dst, s.data(), sizeof(double) * chi, cudaMemcpyHostToDevice, st));
+        ZK(cudaStreamSynchronize(st));
+        return CTM_OK;
+    }
+    case 5: src = c->A; cnt = c->PA; P = c->PA; break;
+    case 6: src = c->a; cnt = D2 * D2 * D2; P = c->Pa; break;
+    case 7: src = c->C; cnt = chi * chi; P = c->PC; break;
+    case 8: src = c->T; cnt = chi * D2 * chi; P = c->PT; break;
+    default: return CTM_EINVAL;
+    }
+    if (count < (size_t)(2 * cnt)) return CTM_EINVAL;
+    CTM_COUNT_LAUNCH(1);
+    zc_interleave_kernel<<<zgrid(cnt), 256, 0, st>>>(cnt, src, P, dst);
+    ZK(cudaGetLastError());
+    ZK(cudaStreamSynchronize(st));
+    return CTM_OK;
+}
+
+void ctm_complex_destroy(ctm_complex_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    delete c;
+}
+
+}  // extern "C"

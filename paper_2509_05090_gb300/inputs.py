@@ -65,6 +65,38 @@ def perturbed_product_site_tensor(v, D: int, eps: float, seed: int) -> np.ndarra
     return A
 
 
+def coherent_state(d: int, direction) -> np.ndarray:
+    """Spin-S coherent state |S, m = S> along a unit vector (theta, phi), in the S^z basis
+    m = S, S-1, ..., -S: c_m = sqrt(binom(2S, S-m)) cos(theta/2)^(S+m) sin(theta/2)^(S-m)
+    e^{i (S-m) phi}.  The spin-1/2 state along (1,1,1)/sqrt 3 is the one the three-fold
+    spin rotation about that axis leaves unchanged (the seed of the complex workloads)."""
+    x, y, z = (float(c) for c in direction)
+    r = math.sqrt(x * x + y * y + z * z)
+    theta, phi = math.acos(z / r), math.atan2(y, x)
+    twoS = d - 1
+    c = np.zeros(d, dtype=np.complex128)
+    for k in range(d):                     # k = S - m
+        c[k] = (math.sqrt(math.comb(twoS, k)) * math.cos(theta / 2) ** (twoS - k) * math.sin(theta / 2) ** k
+                * np.exp(1j * k * phi))
+    return c
+
+
+def complex_perturbed_product_site_tensor(v, D: int, eps: float, seed: int) -> np.ndarray:
+    """Complex counterpart of perturbed_product_site_tensor: A = v (x) e_000 + eps (U + i V),
+    U and V uniform in [-1, 1] from ``default_rng(seed)``.  Not projected or normalised."""
+    v = np.asarray(v, dtype=np.complex128)
+    rng = np.random.default_rng(seed)
+    A = eps * (rng.uniform(-1.0, 1.0, size=(v.size, D, D, D)) + 1j * rng.uniform(-1.0, 1.0, size=(v.size, D, D, D)))
+    A[:, 0, 0, 0] += v
+    return A
+
+
+def random_complex_site_tensor(d: int, D: int, seed: int) -> np.ndarray:
+    """A[s, i, j, k] = U + i V, U and V uniform in [-1, 1] from ``default_rng(seed)``."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-1.0, 1.0, size=(d, D, D, D)) + 1j * rng.uniform(-1.0, 1.0, size=(d, D, D, D))
+
+
 def ising_site_tensor(beta: float) -> np.ndarray:
     """Site tensor whose norm network is the classical Ising model on the honeycomb lattice.
 
@@ -138,6 +170,7 @@ class Workload:
     precision: str = "fp64"
     note: str = ""
     eps: float = 0.0          # > 0: perturbed product state (perturbed_product_site_tensor)
+    irrep: str = "A1"         # "E": complex tensor for the complex representation of C3v
 
     @property
     def D2(self) -> int:
@@ -148,6 +181,11 @@ class Workload:
         return self.chi * self.D * self.D
 
     def site_tensor(self) -> np.ndarray:
+        if self.irrep == "E":
+            if self.eps > 0.0:
+                return complex_perturbed_product_site_tensor(coherent_state(self.d, (1.0, 1.0, 1.0)), self.D,
+                                                             self.eps, self.seed)
+            return random_complex_site_tensor(self.d, self.D, self.seed)
         if self.eps > 0.0:
             return perturbed_product_site_tensor(_PRODUCT_V[:self.d] / np.linalg.norm(_PRODUCT_V[:self.d]),
                                                  self.D, self.eps, self.seed)
@@ -183,6 +221,16 @@ WORKLOADS = {
     "kh_D8_chi128_conv": Workload("kh_D8_chi128_conv", 2, 8, 128, math.cos(_PHI), math.sin(_PHI), 1006, 200,
                                   eps=0.002,
                                   note="Kitaev-Heisenberg phi=0.3pi, near-product state, D=8, chi=128"),
+    # complex tensors for the E irrep of C3v (the Kitaev model's representation, ferromagnetic
+    # K = -1 as in Sec. III.C): the spin-1/2 state along (1,1,1) plus a small complex
+    # perturbation (converging), and random complex tensors (step parity)
+    "kitaev_E_D4_chi32_conv": Workload("kitaev_E_D4_chi32_conv", 2, 4, 32, -1.0, 0.0, 1007, 200, eps=0.005,
+                                       irrep="E", note="Kitaev K=-1, complex E-irrep tensor, near-product"),
+    "kitaev_E_D6_chi64_conv": Workload("kitaev_E_D6_chi64_conv", 2, 6, 64, -1.0, 0.0, 1008, 200, eps=0.002,
+                                       irrep="E", note="Kitaev K=-1, complex E-irrep tensor, near-product, "
+                                                       "enlarged corner 2304x2304 complex"),
+    "kitaev_E_D6_chi64": Workload("kitaev_E_D6_chi64", 2, 6, 64, -1.0, 0.0, 1009, 30, irrep="E",
+                                  note="Kitaev K=-1, random complex E-irrep tensor"),
 }
 
 

@@ -1,0 +1,227 @@
+"""Parity of the complex (E-irrep) CUDA path with the complex oracle (App. A, Sec. II.B-C).
+
+FP64: the contractions differ from the oracle only in rounding order, so the
+enlarged corner agrees to a few ulps of its largest entry; Q and R are unique
+(diag(R) real > 0), and a column j of Q can move by about n u (R_00 / R_jj), which
+sets the per-column tolerance.  Split BF16 (T = 5 slices): every real product with
+inner dimension K' has error below (T+1) 2^(-8T) K' max|a| max|b| per entry
+(about 6e-12 K' relative), propagated the same way.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import complex_oracle as Z
+from oracle import oracle as O
+from paper_2509_05090_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+U64 = 2.0 ** -52
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _kh(d, K, J):
+    S = Z.spin_ops(d)
+    heis = sum(np.kron(s, s) for s in S)
+    return np.stack([K * np.kron(S[a], S[a]) + J * heis for a in range(3)])
+
+
+def _ctm(A, chi, irrep="E", precision="fp64"):
+    from paper_2509_05090_gb300 import binding
+    return binding.CTMComplex(A, chi, irrep=irrep, precision=precision, n_split=5)
+
+
+def _col_tol(R, n, scale):
+    """First-order tolerance of each column of Q: scale * n u R_00 / R_jj."""
+    dg = np.abs(np.diag(R))
+    return scale * n * U64 * dg[0] / np.maximum(dg, 1e-300)
+
+
+def _compare_step(g, z, label, mscale=64.0, qscale=64.0):
+    """One step's outputs of the GPU context g against the oracle z (same inputs)."""
+    M = _np(g.ctm_complex_get_intermediate("M"))
+    Mz = z.last["M"]
+    errM = np.abs(M - Mz).max() / np.abs(Mz).max()
+    assert errM < mscale * U64 * math.sqrt(Mz.shape[0]), (label, "M", errM)
+    R = _np(g.ctm_complex_get_intermediate("R"))
+    Rz = z.last["R"]
+    assert np.abs(np.diag(R).imag).max() < 1e-13 * abs(Rz[0, 0]), (label, "diag R imag")
+    assert np.diag(R).real.min() >= 0.0
+    Q = _np(g.ctm_complex_get_intermediate("Q"))
+    Qz = z.last["Q"]
+    tol = _col_tol(Rz, Qz.shape[0], qscale)
+    errQ = np.abs(Q - Qz).max(axis=0)
+    well = tol < 1e-4
+    assert well.sum() >= 1
+    assert np.all(errQ[well] < tol[well]), (label, "Q", errQ[well].max(), tol[well].min())
+    return errM, errQ[well].max()
+
+
+@pytest.mark.parametrize("d,D", [(2, 3), (3, 2)])
+def test_complex_projection_and_double_layer(ctm_lib, d, D):
+    A = I.random_complex_site_tensor(d, D, 41 + d)
+    g = _ctm(A, chi=4)
+    P = Z.project(A, "E")
+    assert np.abs(_np(g.ctm_complex_get_intermediate("A")) - P).max() < 1e-14
+    assert np.abs(_np(g.ctm_complex_get_intermediate("a")) - Z.double_layer(P)).max() < 1e-14
+    g.close()
+
+
+@pytest.mark.parametrize("D,chi,seed", [(2, 8, 51), (3, 12, 52)])
+def test_complex_steps_fp64(ctm_lib, D, chi, seed):
+    """Random E-irrep tensors, ten steps in lockstep, each step from the oracle's environment."""
+    A = I.random_complex_site_tensor(2, D, seed)
+    g = _ctm(A, chi)
+    z = Z.ComplexCTM(A, chi)
+    for k in range(10):
+        C, T, Q = z.C, z.T, z.Q
+        if k > 0:
+            g.ctm_complex_set_env(C, T, Q)
+        dg = g.ctm_complex_step()
+        dz = z.step()
+        _compare_step(g, z, f"step {k}")
+        Cg = _np(g.ctm_complex_get_intermediate("C"))
+        assert np.abs(Cg - Cg.conj().T).max() == 0.0
+        # C' and T' inherit the error of the well-determined part of Q
+        assert np.abs(Cg - z.C).max() < 1e-9, (k, np.abs(Cg - z.C).max())
+        assert abs(dg - dz) < 1e-9
+
+
+def test_complex_a1_matches_real_oracle(ctm_lib):
+    A = I.random_site_tensor(2, 3, 61)
+    g = _ctm(A.astype(np.complex128), 9, irrep="A1")
+    r = O.OracleCTM(A, chi=9)
+    for _ in range(6):
+        g.ctm_complex_step()
+        r.step()
+    C = _np(g.ctm_complex_get_intermediate("C"))
+    T = _np(g.ctm_complex_get_intermediate("T"))
+    assert np.abs(C.imag).max() < 1e-14 and np.abs(T.imag).max() < 1e-14
+    assert np.abs(C.real - r.C).max() < 1e-10
+    assert np.abs(T.real - r.T).max() < 1e-10
+    h = I.bond_hamiltonians(-0.6, 0.8)
+    e, E, _ = g.ctm_complex_energy(h.astype(np.complex128))
+    er, Er = r.energy(h)
+    assert np.abs(e - er).max() < 1e-11 and abs(E - Er) < 1e-11
+
+
+def test_complex_gauge_covariance_against_real_oracle(ctm_lib):
+    """A real environment in a diagonal phase gauge stays that environment in that gauge."""
+    rng = np.random.default_rng(71)
+    D, chi = 2, 6
+    A = I.random_site_tensor(2, D, 72)
+    r = O.OracleCTM(A, chi=chi)
+    for _ in range(4):
+        r.step()
+    W = np.exp(1j * rng.uniform(0, 2 * math.pi, chi))
+    Wn = np.repeat(W, D * D)
+
+    def gauge(C, T, Q):
+        return (W.conj()[:, None] * C * W[None, :], W.conj()[:, None, None] * T * W[None, None, :],
+                Wn.conj()[:, None] * Q * W[None, :])
+
+    g = _ctm(A.astype(np.complex128), chi, irrep="A1")
+    g.ctm_complex_set_env(*gauge(r.C, r.T, r.Q))
+    for _ in range(4):
+        r.step()
+        g.ctm_complex_step()
+        Cg, Tg, Qg = gauge(r.C, r.T, r.Q)
+        C, T, Q = (_np(x) for x in g.ctm_complex_get_env())
+        assert np.abs(C - Cg).max() < 1e-11
+        assert np.abs(T - Tg).max() < 1e-11
+        assert np.abs(Q - Qg).max() < 1e-10
+
+
+@pytest.mark.parametrize("d,D,chi", [(2, 2, 8), (3, 2, 8)])
+def test_complex_energy_fp64(ctm_lib, d, D, chi):
+    v = I.coherent_state(d, (1.0, 1.0, 1.0) if d == 2 else (-1.0, -1.0, -1.0))
+    A = I.complex_perturbed_product_site_tensor(v, D, 0.2, 81 + d)
+    g = _ctm(A, chi)
+    z = Z.ComplexCTM(A, chi)
+    steps, delta, ok = g.ctm_complex_converge(60, 1e-10)
+    z.converge(60, 1e-10)
+    assert ok
+    Cg = _np(g.ctm_complex_get_intermediate("C"))
+    assert np.abs(np.sort(np.abs(np.linalg.eigvalsh(Cg)))[::-1] / np.linalg.norm(np.linalg.eigvalsh(Cg))
+                  - z.s).max() < 1e-8
+    for K, J in [(-1.0, 0.0), (-1.0, 0.4)]:
+        h = _kh(d, K, J)
+        e, E, rho = g.ctm_complex_energy(h)
+        ez, Ez = z.energy(list(h))
+        assert np.abs(e - ez).max() < 1e-9, (e, ez)
+        assert abs(E - Ez) < 1e-9
+        assert np.abs(e - e[2]).max() < 1e-9          # C3 covariance
+        assert np.abs(rho - z.rho(bond_leg=2)).max() < 1e-9
+
+
+def test_complex_split_steps_and_energy(ctm_lib):
+    """Split BF16 (T = 5): step outputs against the oracle and the converged energy."""
+    v = I.coherent_state(2, (1.0, 1.0, 1.0))
+    A = I.complex_perturbed_product_site_tensor(v, 3, 0.05, 91)
+    chi = 18
+    g = _ctm(A, chi, precision="split_bf16")
+    z = Z.ComplexCTM(A, chi)
+    for k in range(3):
+        if k > 0:
+            g.ctm_complex_set_env(z.C, z.T, z.Q)
+        g.ctm_complex_step()
+        z.step()
+        # split error of each real product: 6 * 2^-40 K' max|a| max|b| (K' <= 2 n); the
+        # chained contractions of M add a few such terms
+        n = z.n
+        M = _np(g.ctm_complex_get_intermediate("M"))
+        errM = np.abs(M - z.last["M"]).max() / np.abs(z.last["M"]).max()
+        assert errM < 4 * 6 * 2.0 ** -40 * 2 * n, (k, errM)
+    g.ctm_complex_set_env(z.C, z.T, z.Q)
+    g.ctm_complex_converge(60, 1e-10)
+    z.converge(60, 1e-10)
+    h = _kh(2, -1.0, 0.3)
+    e, E, _ = g.ctm_complex_energy(h)
+    _, Ez = z.energy(list(h))
+    assert abs(E - Ez) < 1e-9, (E, Ez)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_complex_d6_chi64_workload(ctm_lib, precision):
+    """The D = 6, chi = 64 complex workload: three steps of the random tensor against the
+    oracle (M, and Q on its well-determined columns), then the converging tensor's
+    energy."""
+    w = I.WORKLOADS["kitaev_E_D6_chi64"]
+    A = w.site_tensor()
+    g = _ctm(A, w.chi, precision=precision)
+    z = Z.ComplexCTM(A, w.chi)
+    scale = 64.0 if precision == "fp64" else 4 * 6 * 2.0 ** -40 / U64
+    for k in range(3):
+        if k > 0:
+            g.ctm_complex_set_env(z.C, z.T, z.Q)
+        g.ctm_complex_step()
+        z.step()
+        _compare_step(g, z, f"{precision} step {k}", mscale=scale * (1 if precision == "fp64" else 2 * math.sqrt(z.n)),
+                      qscale=scale)
+    g.close()
+    w = I.WORKLOADS["kitaev_E_D6_chi64_conv"]
+    A = w.site_tensor()
+    g = _ctm(A, w.chi, precision=precision)
+    z = Z.ComplexCTM(A, w.chi)
+    _, _, ok = g.ctm_complex_converge(40, 1e-10)
+    assert ok
+    z.converge(40, 1e-10)
+    h = I.bond_hamiltonians(w.K, w.J, w.d).astype(np.complex128)
+    e, E, _ = g.ctm_complex_energy(h)
+    ez, Ez = z.energy(list(h))
+    assert np.abs(e - ez).max() < 1e-9 and abs(E - Ez) < 1e-9, (e, ez)
+    g.close()
+
+
+def test_complex_rejects_bad_config(ctm_lib):
+    from paper_2509_05090_gb300 import binding
+    A = I.random_complex_site_tensor(2, 2, 3)
+    with pytest.raises(binding.CtmError):
+        binding.CTMComplex(A, 65)                       # chi above the embedded QR's limit
+    with pytest.raises(binding.CtmError):
+        binding.CTMComplex(A[:1], 4)                    # d = 1 has no E irrep
