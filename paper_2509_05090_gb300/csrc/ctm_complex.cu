@@ -54,6 +54,15 @@ struct ctm_complex_ctx {
     double *rho_part, *rho_raw, *hrot, *eout;
     SplitWork sw;
     int steps_done;
+    // steps after the first (eager, autotuning) one replay a captured one-step graph
+    cudaStream_t own;
+    cudaEvent_t ev_in, ev_out;
+    // the corner spectrum runs on a side stream beside the edge update
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_join;
+    cudaGraphExec_t graph1;
+    unsigned long long graph1_kernels;
+    int graph_failed;
 };
 
 namespace {
@@ -259,35 +268,69 @@ int zgrid(long long count)
     return b < 1 ? 1 : (int)b;
 }
 
-// interleaved (re, im) -> planar; planes >= 3 also fill -Im and a copy of Re
-__global__ void zc_planar_kernel(long long count, const double *src, double *dst, long long P, int planes)
+// Layout of a planar complex tensor: element t (row-major in the complex index) sits at
+// base(t) = (t / row_len) * row_stride + t % row_len, plane p at base(t) + p * P.  Two
+// planes hold [Re, Im]; five hold [Re, -Im, Re, Im, Re], so that every pair a real product
+// needs -- [Re ; -Im], [Im ; Re], [Re ; Im], [-Im ; Re] -- is two adjacent planes.
+// "Plane-stacked": one row (row_len = count), P = count.  "Row-blocked": the planes of
+// one row follow each other, P = row_len, row_stride = planes * row_len.
+struct ZLay {
+    long long row_len, row_stride, P;
+    int planes;
+};
+__host__ __device__ inline ZLay zlay_stacked(long long count, int planes) { return ZLay{count, 0, count, planes}; }
+__host__ __device__ inline ZLay zlay_rows(long long row_len, int planes)
 {
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
-         t += (long long)gridDim.x * blockDim.x) {
-        const double re = src[2 * t], im = src[2 * t + 1];
-        dst[t] = re;
-        dst[P + t] = im;
-        if (planes >= 3) dst[2 * P + t] = -im;
-        if (planes >= 4) dst[3 * P + t] = re;
+    return ZLay{row_len, planes * row_len, row_len, planes};
+}
+__host__ __device__ inline long long zbase(const ZLay &L, long long t)
+{
+    return L.row_stride ? (t / L.row_len) * L.row_stride + t % L.row_len : t;
+}
+__host__ __device__ inline int zim_plane(const ZLay &L) { return L.planes == 5 ? 3 : 1; }
+
+__device__ __forceinline__ void zstore(double *x, const ZLay &L, long long t, double re, double im)
+{
+    const long long b = zbase(L, t);
+    if (L.planes == 5) {
+        x[b] = re;
+        x[b + L.P] = -im;
+        x[b + 2 * L.P] = re;
+        x[b + 3 * L.P] = im;
+        x[b + 4 * L.P] = re;
+    } else {
+        x[b] = re;
+        x[b + L.P] = im;
     }
 }
 
-__global__ void zc_interleave_kernel(long long count, const double *src, long long P, double *dst)
+// interleaved (re, im) -> the layout L
+__global__ void zc_load_kernel(long long count, const double *src, double *dst, ZLay L)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
+         t += (long long)gridDim.x * blockDim.x)
+        zstore(dst, L, t, src[2 * t], src[2 * t + 1]);
+}
+
+// the layout L -> interleaved
+__global__ void zc_interleave_kernel(long long count, const double *src, ZLay L, double *dst)
+{
+    const int ip = zim_plane(L);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
          t += (long long)gridDim.x * blockDim.x) {
-        dst[2 * t] = src[t];
-        dst[2 * t + 1] = src[P + t];
+        const long long b = zbase(L, t);
+        dst[2 * t] = src[b];
+        dst[2 * t + 1] = src[b + ip * L.P];
     }
 }
 
-// planes 2 and 3 of a four-plane tensor from planes 0 and 1
-__global__ void zc_complete_kernel(long long count, double *x, long long P)
+// the other planes of a five-plane tensor from its Re (0) and Im (3) planes
+__global__ void zc_complete_kernel(long long count, double *x, ZLay L)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
          t += (long long)gridDim.x * blockDim.x) {
-        x[2 * P + t] = -x[P + t];
-        x[3 * P + t] = x[t];
+        const long long b = zbase(L, t);
+        zstore(x, L, t, x[b], x[b + 3 * L.P]);
     }
 }
 
@@ -323,14 +366,17 @@ __global__ void zc_project_kernel(int d, int D, const double *A, long long P, ZG
     }
 }
 
-// sum of |x|^2 over a planar complex array
-__global__ void zc_sumsq_kernel(long long count, const double *x, long long P, double *partials)
+// sum of |x|^2 over a complex tensor of layout L
+__global__ void zc_sumsq_kernel(long long count, const double *x, ZLay L, double *partials)
 {
     __shared__ double red[8];
+    const int ip = zim_plane(L);
     double acc = 0.0;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
-         t += (long long)gridDim.x * blockDim.x)
-        acc += x[t] * x[t] + x[P + t] * x[P + t];
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long b = zbase(L, t);
+        acc += x[b] * x[b] + x[b + ip * L.P] * x[b + ip * L.P];
+    }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
     __syncthreads();
@@ -341,9 +387,8 @@ __global__ void zc_sumsq_kernel(long long count, const double *x, long long P, d
     }
 }
 
-// x <- x / sqrt(sum of partials); fills planes 2, 3 when planes == 4
-__global__ void zc_scale_kernel(long long count, double *x, long long P, const double *partials, int nparts,
-                                int planes)
+// x <- x / sqrt(sum of partials), every plane of layout L
+__global__ void zc_scale_kernel(long long count, double *x, ZLay L, const double *partials, int nparts)
 {
     __shared__ double inv;
     if (threadIdx.x == 0) {
@@ -352,19 +397,15 @@ __global__ void zc_scale_kernel(long long count, double *x, long long P, const d
         inv = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
     }
     __syncthreads();
+    const int ip = zim_plane(L);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < count;
          t += (long long)gridDim.x * blockDim.x) {
-        const double re = x[t] * inv, im = x[P + t] * inv;
-        x[t] = re;
-        x[P + t] = im;
-        if (planes == 4) {
-            x[2 * P + t] = -im;
-            x[3 * P + t] = re;
-        }
+        const long long b = zbase(L, t);
+        zstore(x, L, t, x[b] * inv, x[b + ip * L.P] * inv);
     }
 }
 
-// Fig. 1b: a[(ii'),(jj'),(kk')] = sum_s K[s,i,j,k] conj(B[s,i',j',k']) (four planes).
+// Fig. 1b: a[(ii'),(jj'),(kk')] = sum_s K[s,i,j,k] conj(B[s,i',j',k']) (five planes, stacked).
 // rot = 1 cycles the legs of both layers so that the z leg comes first.
 __device__ __forceinline__ void zc_layer_entry(int D, long long t, int rot, int &kidx, int &bidx)
 {
@@ -380,7 +421,7 @@ __device__ __forceinline__ void zc_layer_entry(int D, long long t, int rot, int 
     }
 }
 
-__global__ void zc_double_layer_kernel(int d, int D, const double *A, long long PA, double *a, long long Pa)
+__global__ void zc_double_layer_kernel(int d, int D, const double *A, long long PA, double *a)
 {
     const long long D6 = (long long)D * D * D * D * D * D;
     const int D3 = D * D * D;
@@ -395,15 +436,12 @@ __global__ void zc_double_layer_kernel(int d, int D, const double *A, long long 
             re += kr * br + kim * bim;
             im += kim * br - kr * bim;
         }
-        a[t] = re;
-        a[Pa + t] = im;
-        a[2 * Pa + t] = -im;
-        a[3 * Pa + t] = re;
+        zstore(a, zlay_stacked(D6, 5), t, re, im);
     }
 }
 
-// open layers b[p = s*d + t][(ii'),(jj'),(kk')] = A[s, ...] conj(A[t, ...]) (four planes)
-__global__ void zc_open_layers_kernel(int d, int D, const double *A, long long PA, int rot, double *b, long long Pb)
+// open layers b[p = s*d + t][(ii'),(jj'),(kk')] = A[s, ...] conj(A[t, ...]) (five planes, stacked)
+__global__ void zc_open_layers_kernel(int d, int D, const double *A, long long PA, int rot, double *b)
 {
     const long long D6 = (long long)D * D * D * D * D * D;
     const int D3 = D * D * D;
@@ -417,21 +455,18 @@ __global__ void zc_open_layers_kernel(int d, int D, const double *A, long long P
         zc_layer_entry(D, e, rot, ki, bi);
         const double kr = A[s * D3 + ki], kim = A[PA + s * D3 + ki];
         const double br = A[tt * D3 + bi], bim = A[PA + tt * D3 + bi];
-        const double re = kr * br + kim * bim, im = kim * br - kr * bim;
-        b[t] = re;
-        b[Pb + t] = im;
-        b[2 * Pb + t] = -im;
-        b[3 * Pb + t] = re;
+        zstore(b, zlay_stacked(tot, 5), t, kr * br + kim * bim, kim * br - kr * bim);
     }
 }
 
 // C = I, T[a][u][b] = delta_ab t_u with t_u = sum_{v,w} a[u][(vv)][(ww)], Q = first chi columns of I
-__global__ void zc_init_env_kernel(int chi, int D, const double *a, long long Pa, double *C, long long PC, double *T,
-                                   long long PT, double *Q, long long PQ)
+// (C, Q: five planes stacked; T: five planes row-blocked by its rows (a, u))
+__global__ void zc_init_env_kernel(int chi, int D, const double *a, long long Pa, double *C, double *T, double *Q)
 {
     const int D2 = D * D;
     const long long n = (long long)chi * D2;
     const long long tot = (long long)chi * D2 * chi;
+    const int ip = 3;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
          t += (long long)gridDim.x * blockDim.x) {
         const int al = (int)(t / ((long long)D2 * chi)), u = (int)((t / chi) % D2), be = (int)(t % chi);
@@ -441,39 +476,26 @@ __global__ void zc_init_env_kernel(int chi, int D, const double *a, long long Pa
                 for (int w = 0; w < D; ++w) {
                     const long long o = ((long long)u * D2 + v * D + v) * D2 + w * D + w;
                     re += a[o];
-                    im += a[Pa + o];
+                    im += a[ip * Pa + o];
                 }
-        T[t] = re;
-        T[PT + t] = im;
-        T[2 * PT + t] = -im;
-        T[3 * PT + t] = re;
+        zstore(T, zlay_rows(chi, 5), t, re, im);
     }
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)chi * chi;
-         t += (long long)gridDim.x * blockDim.x) {
-        const double v = (t / chi == t % chi) ? 1.0 : 0.0;
-        C[t] = v;
-        C[PC + t] = 0.0;
-        C[2 * PC + t] = 0.0;
-        C[3 * PC + t] = v;
-    }
+         t += (long long)gridDim.x * blockDim.x)
+        zstore(C, zlay_stacked((long long)chi * chi, 5), t, (t / chi == t % chi) ? 1.0 : 0.0, 0.0);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * chi;
-         t += (long long)gridDim.x * blockDim.x) {
-        const double v = (t / chi == t % chi) ? 1.0 : 0.0;
-        Q[t] = v;
-        Q[PQ + t] = 0.0;
-        Q[2 * PQ + t] = 0.0;
-        Q[3 * PQ + t] = v;
-    }
+         t += (long long)gridDim.x * blockDim.x)
+        zstore(Q, zlay_stacked(n * chi, 5), t, (t / chi == t % chi) ? 1.0 : 0.0, 0.0);
 }
 
-// Qs = Q diag(sgn Re C_jj) (sgn 0 = +1), four planes
+// Qs = Q diag(sgn Re C_jj) (sgn 0 = +1), every plane of the five (stacked)
 __global__ void zc_warm_start_kernel(long long n, int chi, const double *Q, long long PQ, const double *C, double *Qs)
 {
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n * chi;
          t += (long long)gridDim.x * blockDim.x) {
         const int j = (int)(t % chi);
         const double sg = C[(long long)j * chi + j] < 0.0 ? -1.0 : 1.0;
-        for (int p = 0; p < 4; ++p) Qs[p * PQ + t] = sg * Q[p * PQ + t];
+        for (int p = 0; p < 5; ++p) Qs[p * PQ + t] = sg * Q[p * PQ + t];
     }
 }
 
@@ -501,17 +523,11 @@ __global__ void zc_extract_kernel(long long n, int k, const double *E, double *Z
         const long long r = t / k;
         const int j = (int)(t % k);
         const long long ld = 2LL * k;
-        const double re = E[(2 * r) * ld + 2 * j], im = E[(2 * r + 1) * ld + 2 * j];
-        Z[t] = re;
-        Z[PZ + t] = im;
-        if (planes == 4) {
-            Z[2 * PZ + t] = -im;
-            Z[3 * PZ + t] = re;
-        }
+        zstore(Z, zlay_stacked(PZ, planes), t, E[(2 * r) * ld + 2 * j], E[(2 * r + 1) * ld + 2 * j]);
     }
 }
 
-// Fig. 3a: Cn = (Cr + Cr^H)/2 normalised (four planes); one CTA.
+// Fig. 3a: Cn = (Cr + Cr^H)/2 normalised (five planes, stacked); one CTA.
 __global__ void zc_herm_normalize_kernel(int chi, const double *Cr, long long PCr, double *Cn, long long PC)
 {
     __shared__ double red[32];
@@ -537,10 +553,7 @@ __global__ void zc_herm_normalize_kernel(int chi, const double *Cr, long long PC
         const int i = t / chi, j = t % chi;
         const double re = 0.5 * (Cr[t] + Cr[j * chi + i]) * inv;
         const double im = 0.5 * (Cr[PCr + t] - Cr[PCr + j * chi + i]) * inv;
-        Cn[t] = re;
-        Cn[PC + t] = im;
-        Cn[2 * PC + t] = -im;
-        Cn[3 * PC + t] = re;
+        zstore(Cn, zlay_stacked(PC, 5), t, re, im);
     }
 }
 
@@ -551,7 +564,7 @@ __global__ void zc_embed_herm_kernel(int chi, const double *C, long long PC, dou
     for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
         const int I = t / m, J = t % m;
         const int i = I % chi, j = J % chi, bi = I / chi, bj = J / chi;
-        const double re = C[i * chi + j], im = C[PC + i * chi + j];
+        const double re = C[i * chi + j], im = C[3 * PC + i * chi + j];
         E[t] = (bi == bj) ? re : (bi == 1 ? im : -im);
     }
 }
@@ -657,12 +670,16 @@ __global__ void zc_check_finite_kernel(long long count, const double *x, int *fl
         ZK(cudaGetLastError());                                    \
     } while (0)
 
-// A complex contraction C(m,n) = sum_k op(A)(m,k) op(B)(k,n) of planar tensors; the left
-// operand's k map is a plain stride (the plane index is stacked on it), B has four planes.
+// A complex contraction C(m,n) = sum_k op(A)(m,k) op(B)(k,n) of planar tensors.  Each
+// operand's k map is a plain stride; the plane index is stacked on it (k' = (plane, k)),
+// which is again a plain stride when the planes are K strides apart.  A has two planes
+// [Re, Im] (a5 = 0) or five (a5 = 1); B has five; C receives Re in plane 0 and Im in
+// plane 1 (c5 = 0) or 3 (c5 = 1, the caller completes the other planes).
 struct ZGemm {
     int M, N, K;
     const double *A;
     long long PA;
+    int a5;
     Idx2 Am, Ak;
     int conjA;
     const double *B;
@@ -671,6 +688,7 @@ struct ZGemm {
     int conjB;
     double *C;
     long long PC;
+    int c5;
     Idx2 Cm, Cn;
 };
 
@@ -686,28 +704,39 @@ int real_gemm(ctm_complex_ctx *c, const GemmF64 &g, int reuse_a)
                : CTM_ECUDA;
 }
 
-int zgemm(ctm_complex_ctx *c, const ZGemm &z)
+static Idx2 zkmap(int K, long long P, long long s2)
+{
+    if (P == (long long)K * s2) return idx_lin(s2);   // the two planes are one strided run
+    return Idx2{K, P, s2};
+}
+
+// reuse_a: the left operand is that of the previous zgemm call, unchanged since (its
+// packed slices are still in the split engine's work buffers)
+int zgemm(ctm_complex_ctx *c, const ZGemm &z, int reuse_a = 0)
 {
     if (z.Ak.s1 != 0 || z.Bk.s1 != 0) return CTM_EINVAL;
-    const Idx2 Ak2{z.K, (z.conjA ? 2 : 1) * z.PA, z.Ak.s2};
-    // Re C: [Re B ; -s_B Im B] = planes (0, 2) (s_B = +1) or (0, 1) (conjugated B)
-    const Idx2 Bkr{z.K, (z.conjB ? 1 : 2) * z.PB, z.Bk.s2};
-    // Im C: [s_B Im B ; Re B] = planes (1, 3) or (2, 3)
-    const double *Bi = z.B + (z.conjB ? 2 : 1) * z.PB;
-    const Idx2 Bki{z.K, (z.conjB ? 1 : 2) * z.PB, z.Bk.s2};
-    GemmF64 gr{z.M, z.N, 2 * z.K, z.A, z.Am, Ak2, z.B, Bkr, z.Bn, z.C, z.Cm, z.Cn, 1.0, 0.0};
-    GemmF64 gi{z.M, z.N, 2 * z.K, z.A, z.Am, Ak2, Bi, Bki, z.Bn, z.C + z.PC, z.Cm, z.Cn, 1.0, 0.0};
-    int rc = real_gemm(c, gr, 0);
+    if (z.conjA && !z.a5) return CTM_EINVAL;
+    // A' = [Re A | s_A Im A]: planes (2, 3) of five, (0, 1) conjugated, or (0, 1) of two
+    const double *Ap = z.A + ((z.a5 && !z.conjA) ? 2 * z.PA : 0);
+    const Idx2 Ak2 = zkmap(z.K, z.PA, z.Ak.s2);
+    // B planes [Re, -Im, Re, Im, Re]: Re C takes [Re ; -s_B Im] = planes (0, 1), or (2, 3)
+    // conjugated; Im C takes [s_B Im ; Re] = planes (3, 4), or (1, 2) conjugated
+    const double *Br = z.B + (z.conjB ? 2 : 0) * z.PB;
+    const double *Bi = z.B + (z.conjB ? 1 : 3) * z.PB;
+    const Idx2 Bk2 = zkmap(z.K, z.PB, z.Bk.s2);
+    GemmF64 gr{z.M, z.N, 2 * z.K, Ap, z.Am, Ak2, Br, Bk2, z.Bn, z.C, z.Cm, z.Cn, 1.0, 0.0};
+    GemmF64 gi{z.M, z.N, 2 * z.K, Ap, z.Am, Ak2, Bi, Bk2, z.Bn, z.C + (z.c5 ? 3 : 1) * z.PC, z.Cm, z.Cn, 1.0, 0.0};
+    int rc = real_gemm(c, gr, reuse_a);
     if (rc != CTM_OK) return rc;
     return real_gemm(c, gi, 1);
 }
 
-int znormalize(ctm_complex_ctx *c, long long count, double *x, long long P, int planes)
+int znormalize(ctm_complex_ctx *c, long long count, double *x, ZLay L)
 {
     int nb = zgrid(count);
     if (nb > ZNORM_BLOCKS) nb = ZNORM_BLOCKS;
-    ZLAUNCH(zc_sumsq_kernel, nb, 256, count, x, P, c->norm_part);
-    ZLAUNCH(zc_scale_kernel, zgrid(count), 256, count, x, P, c->norm_part, nb, planes);
+    ZLAUNCH(zc_sumsq_kernel, nb, 256, count, x, L, c->norm_part);
+    ZLAUNCH(zc_scale_kernel, zgrid(count), 256, count, x, L, c->norm_part, nb);
     return CTM_OK;
 }
 
@@ -752,24 +781,24 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->Ain = td(2 * c->PA);
     c->A = td(2 * c->PA);
     c->Pa = D3;
-    c->a = td(4 * D3);
+    c->a = td(5 * D3);
     c->Pb = dd * D3;
-    c->bB = td(4 * c->Pb);
-    c->bA = td(4 * c->Pb);
+    c->bB = td(5 * c->Pb);
+    c->bA = td(5 * c->Pb);
     c->PC = chi * chi;
-    c->C = td(4 * c->PC);
-    c->Cn = td(4 * c->PC);
+    c->C = td(5 * c->PC);
+    c->Cn = td(5 * c->PC);
     c->Cr = td(2 * c->PC);
     c->R = td(2 * c->PC);
     c->P5a = td(2 * c->PC);
-    c->P5b = td(4 * c->PC);
+    c->P5b = td(5 * c->PC);
     c->PT = chi * D2 * chi;
-    c->T = td(4 * c->PT);
-    c->Tn = td(4 * c->PT);
+    c->T = td(5 * c->PT);
+    c->Tn = td(5 * c->PT);
     c->PQ = n * chi;
-    c->Q = td(4 * c->PQ);
-    c->Qn = td(4 * c->PQ);
-    c->Qs = td(4 * c->PQ);
+    c->Q = td(5 * c->PQ);
+    c->Qn = td(5 * c->PQ);
+    c->Qs = td(5 * c->PQ);
     c->PY = n * chi;
     c->Y = td(2 * c->PY);
     c->W = td(2 * c->PY);
@@ -860,25 +889,30 @@ int zread_status(ctm_complex_ctx *c)
 }
 
 // ------------------------------------------------------------------ the step
+// Layouts of the step's tensors (ZLay): a, C, Q, Qs five planes stacked; T five planes
+// row-blocked by its rows (a, u); W [(a,u)][2][h], X [(a,b)][2][(u,l)], Y1 [(a,b)][2][z] and
+// M [(a,y)][2][(b,x)] two planes row-blocked (k contiguous for the next contraction); Y, MQ,
+// Cr and H two planes stacked (k slowest for the next contraction).
+ZLay lay_T(const ctm_complex_ctx *c) { return zlay_rows(c->chi, 5); }
+
 // Fig. 3c: W = T C; X'[a][b][u][l] = sum_h W[(a,u),h] conj(T[(b,l),h]);
 // Y1[(a,b)][z] = sum_{u,l} X' a[u,l,z]; M[(a,y)][(b,x)] = sum_z Y1 a[z,x,y]
 int zenlarged_corner(ctm_complex_ctx *c)
 {
     const int chi = c->chi, D2 = c->D2;
-    const long long n = c->n;
+    const long long n = c->n, DD = (long long)D2 * D2;
     int rc;
-    ZGemm z{(int)n, chi, chi, c->T, c->PT, idx_lin(chi), idx_lin(1), 0, c->C, c->PC, idx_lin(chi), idx_lin(1), 0,
-            c->W, c->PY, idx_lin(chi), idx_lin(1)};
+    ZGemm z{(int)n, chi, chi, c->T, chi, 1, idx_lin(5LL * chi), idx_lin(1), 0, c->C, c->PC, idx_lin(chi), idx_lin(1),
+            0, c->W, chi, 0, idx_lin(2LL * chi), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    z = ZGemm{(int)n, (int)n, chi, c->W, c->PY, idx_lin(chi), idx_lin(1), 0, c->T, c->PT, idx_lin(1), idx_lin(chi), 1,
-              c->X, c->PM, idx_split(D2, (long long)chi * D2 * D2, D2), idx_split(D2, (long long)D2 * D2, 1)};
+    z = ZGemm{(int)n, (int)n, chi, c->W, chi, 0, idx_lin(2LL * chi), idx_lin(1), 0, c->T, chi, idx_lin(1),
+              idx_lin(5LL * chi), 1, c->X, DD, 0, idx_split(D2, (long long)chi * 2 * DD, D2), idx_split(D2, 2 * DD, 1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    z = ZGemm{chi * chi, D2, D2 * D2, c->X, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->a, c->Pa,
-              idx_lin(D2), idx_lin(1), 0, c->Y1, c->PY1, idx_lin(D2), idx_lin(1)};
+    z = ZGemm{chi * chi, D2, D2 * D2, c->X, DD, 0, idx_lin(2 * DD), idx_lin(1), 0, c->a, c->Pa, idx_lin(D2),
+              idx_lin(1), 0, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, c->PY1, idx_lin(D2), idx_lin(1), 0, c->a, c->Pa,
-              idx_lin((long long)D2 * D2), idx_split(D2, 1, D2), 0, c->M, c->PM,
-              idx_split(chi, (long long)D2 * n, D2), idx_split(D2, n, 1)};
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->a, c->Pa, idx_lin(DD),
+              idx_split(D2, 1, D2), 0, c->M, n, 0, idx_split(chi, 2LL * D2 * n, D2), idx_split(D2, 2 * n, 1)};
     return zgemm(c, z);
 }
 
@@ -889,12 +923,12 @@ int zprojector(ctm_complex_ctx *c)
     const long long n = c->n;
     int rc;
     ZLAUNCH(zc_warm_start_kernel, zgrid(n * chi), 256, n, chi, c->Q, c->PQ, c->C, c->Qs);
-    ZGemm z{(int)n, chi, (int)n, c->M, c->PM, idx_lin(n), idx_lin(1), 0, c->Qs, c->PQ, idx_lin(chi), idx_lin(1), 0,
-            c->Y, c->PY, idx_lin(chi), idx_lin(1)};
+    ZGemm z{(int)n, chi, (int)n, c->M, n, 0, idx_lin(2 * n), idx_lin(1), 0, c->Qs, c->PQ, idx_lin(chi), idx_lin(1), 0,
+            c->Y, c->PY, 0, idx_lin(chi), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     ZLAUNCH(zc_embed_kernel, zgrid(n * chi), 256, n, chi, c->Y, c->PY, c->Yemb);
     ZK(qr_householder((int)(2 * n), 2 * chi, c->Yemb, c->Qemb, c->Remb, zqr_scratch(c), c->stream));
-    ZLAUNCH(zc_extract_kernel, zgrid(n * chi), 256, n, chi, c->Qemb, c->Qn, c->PQ, 4);
+    ZLAUNCH(zc_extract_kernel, zgrid(n * chi), 256, n, chi, c->Qemb, c->Qn, c->PQ, 5);
     ZLAUNCH(zc_extract_kernel, zgrid((long long)chi * chi), 256, (long long)chi, chi, c->Remb, c->R, c->PC, 2);
     return CTM_OK;
 }
@@ -905,11 +939,12 @@ int zcorner(ctm_complex_ctx *c, double *Cout)
     const int chi = c->chi;
     const long long n = c->n;
     int rc;
-    ZGemm z{(int)n, chi, (int)n, c->M, c->PM, idx_lin(n), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 0,
-            c->MQ, c->PY, idx_lin(chi), idx_lin(1)};
-    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    z = ZGemm{chi, chi, (int)n, c->MQ, c->PY, idx_lin(1), idx_lin(chi), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 1,
-              c->Cr, c->PC, idx_lin(1), idx_lin(chi)};
+    // the previous contraction was Y = M Qs (only the QR in between): M is packed already
+    ZGemm z{(int)n, chi, (int)n, c->M, n, 0, idx_lin(2 * n), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 0,
+            c->MQ, c->PY, 0, idx_lin(chi), idx_lin(1)};
+    if ((rc = zgemm(c, z, 1)) != CTM_OK) return rc;
+    z = ZGemm{chi, chi, (int)n, c->MQ, c->PY, 0, idx_lin(1), idx_lin(chi), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 1,
+              c->Cr, c->PC, 0, idx_lin(1), idx_lin(chi)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     ZLAUNCH(zc_herm_normalize_kernel, 1, 1024, chi, c->Cr, c->PC, Cout, c->PC);
     return CTM_OK;
@@ -919,35 +954,43 @@ int zcorner(ctm_complex_ctx *c, double *Cout)
 int zedge(ctm_complex_ctx *c)
 {
     const int chi = c->chi, D2 = c->D2;
-    const long long n = c->n;
+    const long long n = c->n, DD = (long long)D2 * D2;
     int rc;
-    // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]
-    ZGemm z{(int)n, (int)n, chi, c->T, c->PT, idx_lin(chi), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(n),
-            idx_split(D2, 1, chi), 0, c->X, c->PM, idx_split(D2, (long long)chi * D2 * D2, D2),
-            idx_split(D2, (long long)D2 * D2, 1)};
+    // H1'[a][j][u][w] = sum_g T[(a,u),g] Q[(g,w),j]   (into X, laid out as X')
+    ZGemm z{(int)n, (int)n, chi, c->T, chi, 1, idx_lin(5LL * chi), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(n),
+            idx_split(D2, 1, chi), 0, c->X, DD, 0, idx_split(D2, (long long)chi * 2 * DD, D2),
+            idx_split(D2, 2 * DD, 1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     // H2[(a,j)][z] = H1'[(a,j),(u,w)] a[(u,w),z]
-    z = ZGemm{chi * chi, D2, D2 * D2, c->X, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->a, c->Pa,
-              idx_lin(D2), idx_lin(1), 0, c->Y1, c->PY1, idx_lin(D2), idx_lin(1)};
+    z = ZGemm{chi * chi, D2, D2 * D2, c->X, DD, 0, idx_lin(2 * DD), idx_lin(1), 0, c->a, c->Pa, idx_lin(D2),
+              idx_lin(1), 0, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     // H3'[a][y][x][j] = H2[(a,j),z] a[z,x,y]
-    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, c->PY1, idx_lin(D2), idx_lin(1), 0, c->a, c->Pa,
-              idx_lin((long long)D2 * D2), idx_split(D2, 1, D2), 0, c->H, c->PM,
-              idx_split(chi, (long long)D2 * D2 * chi, 1), idx_split(D2, (long long)D2 * chi, chi)};
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->a, c->Pa, idx_lin(DD),
+              idx_split(D2, 1, D2), 0, c->H, c->PM, 0, idx_split(chi, DD * chi, 1),
+              idx_split(D2, (long long)D2 * chi, chi)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    // T'[i][(x,j)] = sum_{(a,y)} H3'[(a,y),(x,j)] conj(Q[(a,y),i])
-    z = ZGemm{(int)n, chi, (int)n, c->H, c->PM, idx_lin(1), idx_lin(n), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 1,
-              c->Tn, c->PT, idx_lin(1), idx_lin(n)};
+    // T'[i][(x,j)] = sum_{(a,y)} H3'[(a,y),(x,j)] conj(Q[(a,y),i]), into T's row-blocked layout
+    z = ZGemm{(int)n, chi, (int)n, c->H, c->PM, 0, idx_lin(1), idx_lin(n), 0, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 1,
+              c->Tn, chi, 1, idx_split(chi, 5LL * chi, 1), idx_lin(5 * n)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    return znormalize(c, (long long)chi * D2 * chi, c->Tn, c->PT, 4);
+    return znormalize(c, (long long)chi * D2 * chi, c->Tn, lay_T(c));
 }
 
-int zspectrum(ctm_complex_ctx *c, const double *Cin)
+// the corner spectrum of C (five planes): delta against the previous one, on `st`
+int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st)
 {
     const int k2 = 2 * c->chi;
-    ZLAUNCH(zc_embed_herm_kernel, (k2 * k2 + 255) / 256, 256, c->chi, Cin, c->PC, c->Cemb);
-    ZK(launch_spectrum(k2, c->Cemb, c->s_new, c->s, c->delta, c->spec_work, c->stream));
-    ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * k2, cudaMemcpyDeviceToDevice, c->stream));
+    CTM_COUNT_LAUNCH(1);
+    zc_embed_herm_kernel<<<(k2 * k2 + 255) / 256, 256, 0, c->stream>>>(c->chi, Cin, c->PC, c->Cemb);
+    ZK(cudaGetLastError());
+    if (st != c->stream) {
+        ZK(cudaEventRecord(c->ev_fork, c->stream));
+        ZK(cudaStreamWaitEvent(st, c->ev_fork, 0));
+    }
+    ZK(launch_spectrum(k2, c->Cemb, c->s_new, c->s, c->delta, c->spec_work, st));
+    ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * k2, cudaMemcpyDeviceToDevice, st));
+    if (st != c->stream) ZK(cudaEventRecord(c->ev_join, st));
     return CTM_OK;
 }
 
@@ -957,13 +1000,15 @@ int zstep(ctm_complex_ctx *c)
     if ((rc = zenlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = zprojector(c)) != CTM_OK) return rc;
     if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
+    // the spectrum of C' (from its private embedding) beside the edge update
+    if ((rc = zspectrum(c, c->Cn, c->side)) != CTM_OK) return rc;
     if ((rc = zedge(c)) != CTM_OK) return rc;
     const long long chi = c->chi, D2 = c->D2, n = c->n;
     cudaStream_t st = c->stream;
-    ZK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * 4 * chi * chi, cudaMemcpyDeviceToDevice, st));
-    ZK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * 4 * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
-    ZK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * 4 * n * chi, cudaMemcpyDeviceToDevice, st));
-    if ((rc = zspectrum(c, c->C)) != CTM_OK) return rc;
+    ZK(cudaStreamWaitEvent(st, c->ev_join, 0));
+    ZK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * 5 * chi * chi, cudaMemcpyDeviceToDevice, st));
+    ZK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * 5 * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
+    ZK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * 5 * n * chi, cudaMemcpyDeviceToDevice, st));
     c->steps_done++;
     return CTM_OK;
 }
@@ -972,8 +1017,8 @@ int zcheck_env_finite(ctm_complex_ctx *c)
 {
     cudaStream_t st = c->stream;
     ZK(cudaMemsetAsync(c->flag, 0, sizeof(int), st));
-    ZLAUNCH(zc_check_finite_kernel, zgrid(2 * c->PC), 256, 2 * c->PC, c->C, c->flag);
-    ZLAUNCH(zc_check_finite_kernel, zgrid(2 * c->PT), 256, 2 * c->PT, c->T, c->flag);
+    ZLAUNCH(zc_check_finite_kernel, zgrid(5 * c->PC), 256, 5 * c->PC, c->C, c->flag);
+    ZLAUNCH(zc_check_finite_kernel, zgrid(5 * c->PT), 256, 5 * c->PT, c->T, c->flag);
     int f = 0;
     ZK(cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, st));
     ZK(cudaStreamSynchronize(st));
@@ -1041,18 +1086,28 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
             rc = CTM_ECUDA;
             break;
         }
+        int prio_least = 0, prio_greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
+        if (cudaStreamCreateWithFlags(&c->own, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&c->side, cudaStreamNonBlocking, prio_least) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            rc = CTM_ECUDA;
+            break;
+        }
         const long long cnt = c->PA;
         if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
         CTM_COUNT_LAUNCH(4);
-        zc_planar_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(cnt, A_dev, c->Ain, cnt, 2);
+        zc_load_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(cnt, A_dev, c->Ain, zlay_stacked(cnt, 2));
         zc_project_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(c->d, c->D, c->Ain, cnt, grp, cfg->symmetrize ? 1 : 0,
                                                              c->A, cnt);
         if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
-        if ((rc = znormalize(c, cnt, c->A, cnt, 2)) != CTM_OK) break;
+        if ((rc = znormalize(c, cnt, c->A, zlay_stacked(cnt, 2))) != CTM_OK) break;
         const long long D6 = c->Pa;
-        zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, c->a, c->Pa);
-        zc_init_env_kernel<<<zgrid(c->PT), 256, 0, c->stream>>>(c->chi, c->D, c->a, c->Pa, c->C, c->PC, c->T,
-                                                                c->PT, c->Q, c->PQ);
+        zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, c->a);
+        zc_init_env_kernel<<<zgrid(c->PT), 256, 0, c->stream>>>(c->chi, c->D, c->a, c->Pa, c->C, c->T, c->Q);
         if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
         if (launch_spectrum_init(2 * c->chi, c->s, c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
         if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
@@ -1067,10 +1122,35 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         if (f) rc = CTM_ENONFINITE;
     } while (0);
     if (rc != CTM_OK) {
-        delete c;
+        ctm_complex_destroy(c);
         return rc;
     }
     *out = c;
+    return CTM_OK;
+}
+
+// Capture one step on the private stream into graph1; a launch that cannot be captured
+// leaves graph_failed set and the context runs eagerly.
+static int zcapture(ctm_complex_ctx *c)
+{
+    if (c->graph1 || c->graph_failed) return CTM_OK;
+    cudaGraph_t g = nullptr;
+    const unsigned long long l0 = g_ctm_launches;
+    ZK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+    const int steps0 = c->steps_done;
+    int rc = zstep(c);
+    c->steps_done = steps0;
+    cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+    if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph1, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (rc != CTM_OK || e != cudaSuccess || !c->graph1) {
+        cudaGetLastError();
+        c->graph1 = nullptr;
+        c->graph_failed = 1;
+    } else {
+        c->graph1_kernels = g_ctm_launches - l0;
+    }
+    g_ctm_launches = l0;
     return CTM_OK;
 }
 
@@ -1078,7 +1158,24 @@ int ctm_complex_step(ctm_complex_ctx *c, int nsteps, double *delta_host)
 {
     if (!c || nsteps < 1) return CTM_EINVAL;
     int rc;
-    for (int k = 0; k < nsteps; ++k)
+    int done = 0;
+    if (c->steps_done > 0 && !c->graph_failed) {
+        cudaStream_t user = c->stream;
+        ZK(cudaEventRecord(c->ev_in, user));
+        ZK(cudaStreamWaitEvent(c->own, c->ev_in, 0));
+        c->stream = c->own;
+        rc = zcapture(c);
+        for (; rc == CTM_OK && c->graph1 && done < nsteps; ++done) {
+            if (cudaGraphLaunch(c->graph1, c->stream) != cudaSuccess) rc = CTM_ECUDA;
+            CTM_COUNT_LAUNCH(c->graph1_kernels);
+        }
+        c->steps_done += done;
+        c->stream = user;
+        ZK(cudaEventRecord(c->ev_out, c->own));
+        ZK(cudaStreamWaitEvent(user, c->ev_out, 0));
+        if (rc != CTM_OK) return rc;
+    }
+    for (; done < nsteps; ++done)
         if ((rc = zstep(c)) != CTM_OK) return rc;
     if ((rc = zread_status(c)) != CTM_OK) return rc;
     if (delta_host) {
@@ -1156,37 +1253,38 @@ int ctm_complex_energy(ctm_complex_ctx *c, const double *h_dev, double *e_bond_h
     if ((rc = zenlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = zprojector(c)) != CTM_OK) return rc;
     if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
-    // P5 = Ch^5
+    // P5 = Ch^5 (the last product into P5b's five planes)
     const double *src = c->Cn;
     double *bufs[2] = {c->P5a, c->P5b};
+    const long long DD = (long long)D2 * D2;
     for (int p = 0; p < 4; ++p) {
         double *dst = bufs[p & 1];
-        ZGemm z{chi, chi, chi, src, c->PC, idx_lin(chi), idx_lin(1), 0, c->Cn, c->PC, idx_lin(chi), idx_lin(1), 0,
-                dst, c->PC, idx_lin(chi), idx_lin(1)};
+        ZGemm z{chi, chi, chi, src, c->PC, p == 0, idx_lin(chi), idx_lin(1), 0, c->Cn, c->PC, idx_lin(chi), idx_lin(1),
+                0, dst, c->PC, p == 3, idx_lin(chi), idx_lin(1)};
         if ((rc = zgemm(c, z)) != CTM_OK) return rc;
         src = dst;
     }
-    ZLAUNCH(zc_complete_kernel, zgrid((long long)chi * chi), 256, (long long)chi * chi, c->P5b, c->PC);
+    ZLAUNCH(zc_complete_kernel, zgrid((long long)chi * chi), 256, (long long)chi * chi, c->P5b,
+            zlay_stacked((long long)chi * chi, 5));
     // F = Q P5 (n x chi) into W; E'[(a,b)][(x,y)] = E[(b,x),(a,y)], E = F Q^H, into H
-    ZGemm z{(int)n, chi, chi, c->Qn, c->PQ, idx_lin(chi), idx_lin(1), 0, c->P5b, c->PC, idx_lin(chi), idx_lin(1), 0,
-            c->W, c->PY, idx_lin(chi), idx_lin(1)};
+    ZGemm z{(int)n, chi, chi, c->Qn, c->PQ, 1, idx_lin(chi), idx_lin(1), 0, c->P5b, c->PC, idx_lin(chi), idx_lin(1), 0,
+            c->W, chi, 0, idx_lin(2LL * chi), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    z = ZGemm{(int)n, (int)n, chi, c->W, c->PY, idx_lin(chi), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(1), idx_lin(chi), 1,
-              c->H, c->PM, idx_split(D2, (long long)D2 * D2, D2), idx_split(D2, (long long)chi * D2 * D2, 1)};
+    z = ZGemm{(int)n, (int)n, chi, c->W, chi, 0, idx_lin(2LL * chi), idx_lin(1), 0, c->Qn, c->PQ, idx_lin(1),
+              idx_lin(chi), 1, c->H, c->PM, 0, idx_split(D2, DD, D2), idx_split(D2, (long long)chi * DD, 1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     // open layers: the outer site B with its legs as they are, the apex site A with z first
     CTM_COUNT_LAUNCH(2);
-    zc_open_layers_kernel<<<zgrid(D3 * dd), 256, 0, c->stream>>>(d, c->D, c->A, c->PA, 0, c->bB, c->Pb);
-    zc_open_layers_kernel<<<zgrid(D3 * dd), 256, 0, c->stream>>>(d, c->D, c->A, c->PA, 1, c->bA, c->Pb);
+    zc_open_layers_kernel<<<zgrid(D3 * dd), 256, 0, c->stream>>>(d, c->D, c->A, c->PA, 0, c->bB);
+    zc_open_layers_kernel<<<zgrid(D3 * dd), 256, 0, c->stream>>>(d, c->D, c->A, c->PA, 1, c->bA);
     ZK(cudaGetLastError());
     // Y1o[(a,b)][(pB,z)] = sum_{u,l} X'[(a,b),(u,l)] bB[pB][u][l][z]
-    z = ZGemm{chi * chi, dd * D2, D2 * D2, c->X, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->bB, c->Pb,
-              idx_lin(D2), idx_split(D2, D3, 1), 0, c->Y1o, c->PYo, idx_lin((long long)dd * D2), idx_lin(1)};
+    z = ZGemm{chi * chi, dd * D2, D2 * D2, c->X, DD, 0, idx_lin(2 * DD), idx_lin(1), 0, c->bB, c->Pb, idx_lin(D2),
+              idx_split(D2, D3, 1), 0, c->Y1o, c->PYo, 0, idx_lin((long long)dd * D2), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     // G2[(a,b)][(pA,z)] = sum_{x,y} E'[(a,b),(x,y)] bA[pA][z][x][y]
-    z = ZGemm{chi * chi, dd * D2, D2 * D2, c->H, c->PM, idx_lin((long long)D2 * D2), idx_lin(1), 0, c->bA, c->Pb,
-              idx_lin(1), idx_split(D2, D3, (long long)D2 * D2), 0, c->G2, c->PYo, idx_lin((long long)dd * D2),
-              idx_lin(1)};
+    z = ZGemm{chi * chi, dd * D2, D2 * D2, c->H, c->PM, 0, idx_lin(DD), idx_lin(1), 0, c->bA, c->Pb, idx_lin(1),
+              idx_split(D2, D3, DD), 0, c->G2, c->PYo, 0, idx_lin((long long)dd * D2), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     ZLAUNCH(zc_rho_partial_kernel, ZRHO_BLOCKS, 256, (long long)chi * chi, dd, D2, c->Y1o, c->G2, c->PYo,
             c->rho_part);
@@ -1208,14 +1306,14 @@ int ctm_complex_get_env(const ctm_complex_ctx *c, double *C_dev, double *T_dev, 
 {
     if (!c) return CTM_EINVAL;
     cudaStream_t st = c->stream;
-    auto out = [&](const double *src, long long cnt, long long P, double *dst) -> bool {
+    auto out = [&](const double *src, long long cnt, ZLay L, double *dst) -> bool {
         CTM_COUNT_LAUNCH(1);
-        zc_interleave_kernel<<<zgrid(cnt), 256, 0, st>>>(cnt, src, P, dst);
+        zc_interleave_kernel<<<zgrid(cnt), 256, 0, st>>>(cnt, src, L, dst);
         return cudaGetLastError() == cudaSuccess;
     };
-    if (C_dev && !out(c->C, c->PC, c->PC, C_dev)) return CTM_ECUDA;
-    if (T_dev && !out(c->T, c->PT, c->PT, T_dev)) return CTM_ECUDA;
-    if (Q_dev && !out(c->Q, c->PQ, c->PQ, Q_dev)) return CTM_ECUDA;
+    if (C_dev && !out(c->C, c->PC, zlay_stacked(c->PC, 5), C_dev)) return CTM_ECUDA;
+    if (T_dev && !out(c->T, c->PT, lay_T(c), T_dev)) return CTM_ECUDA;
+    if (Q_dev && !out(c->Q, c->PQ, zlay_stacked(c->PQ, 5), Q_dev)) return CTM_ECUDA;
     ZK(cudaStreamSynchronize(st));
     return CTM_OK;
 }
@@ -1225,9 +1323,9 @@ int ctm_complex_set_env(ctm_complex_ctx *c, const double *C_dev, const double *T
     if (!c || !C_dev || !T_dev || !Q_dev) return CTM_EINVAL;
     cudaStream_t st = c->stream;
     CTM_COUNT_LAUNCH(3);
-    zc_planar_kernel<<<zgrid(c->PC), 256, 0, st>>>(c->PC, C_dev, c->C, c->PC, 4);
-    zc_planar_kernel<<<zgrid(c->PT), 256, 0, st>>>(c->PT, T_dev, c->T, c->PT, 4);
-    zc_planar_kernel<<<zgrid(c->PQ), 256, 0, st>>>(c->PQ, Q_dev, c->Q, c->PQ, 4);
+    zc_load_kernel<<<zgrid(c->PC), 256, 0, st>>>(c->PC, C_dev, c->C, zlay_stacked(c->PC, 5));
+    zc_load_kernel<<<zgrid(c->PT), 256, 0, st>>>(c->PT, T_dev, c->T, lay_T(c));
+    zc_load_kernel<<<zgrid(c->PQ), 256, 0, st>>>(c->PQ, Q_dev, c->Q, zlay_stacked(c->PQ, 5));
     ZK(cudaGetLastError());
     // the spectrum of the new corner becomes the reference for the next delta
     const int k2 = 2 * c->chi;
@@ -1244,12 +1342,13 @@ int ctm_complex_get_intermediate(const ctm_complex_ctx *c, int which, double *ds
     const long long chi = c->chi, D2 = c->D2, n = c->n;
     cudaStream_t st = c->stream;
     const double *src = nullptr;
-    long long cnt = 0, P = 0;
+    long long cnt = 0;
+    ZLay L;
     switch (which) {
-    case 0: src = c->M; cnt = n * n; P = c->PM; break;
-    case 1: src = c->Y; cnt = n * chi; P = c->PY; break;
-    case 2: src = c->R; cnt = chi * chi; P = c->PC; break;
-    case 3: src = c->Q; cnt = n * chi; P = c->PQ; break;
+    case 0: src = c->M; cnt = n * n; L = zlay_rows(n, 2); break;
+    case 1: src = c->Y; cnt = n * chi; L = zlay_stacked(c->PY, 2); break;
+    case 2: src = c->R; cnt = chi * chi; L = zlay_stacked(c->PC, 2); break;
+    case 3: src = c->Q; cnt = n * chi; L = zlay_stacked(c->PQ, 5); break;
     case 4: {   // the corner spectrum: every other value of the embedded one, times sqrt 2
         if (count < (size_t)chi) return CTM_EINVAL;
         std::vector<double> s2((size_t)(2 * chi));
@@ -1261,15 +1360,15 @@ int ctm_complex_get_intermediate(const ctm_complex_ctx *c, int which, double *ds
         ZK(cudaStreamSynchronize(st));
         return CTM_OK;
     }
-    case 5: src = c->A; cnt = c->PA; P = c->PA; break;
-    case 6: src = c->a; cnt = D2 * D2 * D2; P = c->Pa; break;
-    case 7: src = c->C; cnt = chi * chi; P = c->PC; break;
-    case 8: src = c->T; cnt = chi * D2 * chi; P = c->PT; break;
+    case 5: src = c->A; cnt = c->PA; L = zlay_stacked(c->PA, 2); break;
+    case 6: src = c->a; cnt = D2 * D2 * D2; L = zlay_stacked(c->Pa, 5); break;
+    case 7: src = c->C; cnt = chi * chi; L = zlay_stacked(c->PC, 5); break;
+    case 8: src = c->T; cnt = chi * D2 * chi; L = lay_T(c); break;
     default: return CTM_EINVAL;
     }
     if (count < (size_t)(2 * cnt)) return CTM_EINVAL;
     CTM_COUNT_LAUNCH(1);
-    zc_interleave_kernel<<<zgrid(cnt), 256, 0, st>>>(cnt, src, P, dst);
+    zc_interleave_kernel<<<zgrid(cnt), 256, 0, st>>>(cnt, src, L, dst);
     ZK(cudaGetLastError());
     ZK(cudaStreamSynchronize(st));
     return CTM_OK;
@@ -1279,6 +1378,19 @@ void ctm_complex_destroy(ctm_complex_ctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->stream);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    if (c->own) {
+        cudaStreamSynchronize(c->own);
+        cudaStreamDestroy(c->own);
+    }
+    if (c->side) {
+        cudaStreamSynchronize(c->side);
+        cudaStreamDestroy(c->side);
+    }
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 
