@@ -389,6 +389,68 @@ def fp64_step_record(w, steps, fp64_peak):
             "fp64_peak_tflops": fp64_peak, "phase_ms": ph, "algorithmic_flops_per_step": flops}
 
 
+def complex_record(steps, n_split, fp64_peak, bf16_peak, with_oracle=True):
+    """The complex (E-irrep) path, Kitaev K = -1 at D = 6, chi = 72 (complex enlarged corner
+    2592 x 2592, the size of the real benchmark workload): steps/s in split BF16 and FP64 on the random tensor (CUDA events over one
+    replayed one-step graph per step, after warm-up), then the converging tensor's time to
+    delta < 1e-10 and its energy against the complex oracle."""
+    import numpy as np
+    import torch
+    from paper_2509_05090_gb300 import binding, inputs
+    w = inputs.WORKLOADS["kitaev_E_D6_chi72"]
+    flops = 4.0 * step_gemm_flops(w.chi, w.D2)     # a complex product is four real ones
+    rec = {"workload": w.name, "d": w.d, "D": w.D, "chi": w.chi, "n": w.n, "algorithmic_flops_per_step": flops}
+    for prec in ("split_bf16", "fp64"):
+        g = binding.CTMComplex(w.site_tensor(), w.chi, precision=prec, n_split=n_split)
+        for _ in range(3):
+            g.ctm_complex_step(1, want_delta=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = binding.ctm_kernel_launches()
+        e0.record(g.stream)
+        g.ctm_complex_step(steps, want_delta=False)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        launches = (binding.ctm_kernel_launches() - l0) / steps
+        g.close()
+        r = {"steps_per_s": 1e3 / ms, "ms_per_step": ms, "kernels_per_step": launches,
+             "fp64_equivalent_tflops_step": flops / (ms / 1e3) / 1e12}
+        if prec == "fp64":
+            r["step_frac_of_fp64_peak"] = r["fp64_equivalent_tflops_step"] / fp64_peak
+        else:
+            pairs = n_split * (n_split + 1) // 2
+            r["tensor_tflops_step"] = pairs * flops / (ms / 1e3) / 1e12
+            r["step_frac_of_bf16_burst"] = r["tensor_tflops_step"] / bf16_peak
+        rec[prec] = r
+    wc = inputs.WORKLOADS["kitaev_E_D6_chi72_conv"]
+    h = inputs.bond_hamiltonians(wc.K, wc.J, wc.d).astype(np.complex128)
+    conv = {}
+    for prec in ("split_bf16", "fp64"):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g = binding.CTMComplex(wc.site_tensor(), wc.chi, precision=prec, n_split=n_split)
+        nst, dl, ok = g.ctm_complex_converge(wc.steps, wc.tol, 1)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        eb, E, _ = g.ctm_complex_energy(h)
+        g.close()
+        conv[prec] = {"steps": nst, "delta": dl, "converged": ok, "seconds": secs, "E_site": E,
+                      "e_bond": [float(x) for x in eb]}
+    if with_oracle:
+        from oracle import complex_oracle as zorc
+        t0 = time.perf_counter()
+        ref = zorc.ComplexCTM(wc.site_tensor(), wc.chi)
+        nst, _ = ref.converge(wc.steps, wc.tol)
+        _, Ez = ref.energy(list(h))
+        conv["oracle"] = {"steps": nst, "E_site": Ez, "seconds": time.perf_counter() - t0,
+                          "what": "numpy complex128 oracle (oracle/complex_oracle.py), all host cores via BLAS"}
+        for prec in ("split_bf16", "fp64"):
+            conv[prec]["abs_err_vs_oracle"] = abs(conv[prec]["E_site"] - Ez)
+    rec["converge_" + wc.name] = conv
+    return rec
+
+
 def split_step_rate(w, steps, n_split, corner="qmq"):
     import torch
     from paper_2509_05090_gb300 import binding
@@ -587,6 +649,8 @@ def main():
         rec8["split_bf16_steps_per_s"] = split_step_rate(w8, 3, args.n_split)
         line["fp64_d8_chi128"] = rec8
         line["batch96"] = batch_record(args, args.steps)
+        line["complex_E_D6_chi72"] = complex_record(args.steps, args.n_split, fp64_peak, peaks["bf16_tflops"],
+                                                    with_oracle=not args.no_compare)
 
     # end to end through the public API from pinned host memory
     if not args.no_e2e:

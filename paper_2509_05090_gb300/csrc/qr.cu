@@ -505,7 +505,7 @@ size_t qr_rowbuf_doubles(int k) { return (size_t)2 * QB * k; }
 int qr_supported(int n, int k)
 {
     int G, rp;
-    return n >= k && k >= 1 && k <= 128 && qr_layout(n, k, 1, &G, &rp);
+    return n >= k && k >= 1 && k <= 160 && qr_layout(n, k, 1, &G, &rp);
 }
 
 size_t qr_sk_doubles(int n, int k)

@@ -231,6 +231,11 @@ WORKLOADS = {
                                                        "enlarged corner 2304x2304 complex"),
     "kitaev_E_D6_chi64": Workload("kitaev_E_D6_chi64", 2, 6, 64, -1.0, 0.0, 1009, 30, irrep="E",
                                   note="Kitaev K=-1, random complex E-irrep tensor"),
+    "kitaev_E_D6_chi72_conv": Workload("kitaev_E_D6_chi72_conv", 2, 6, 72, -1.0, 0.0, 1010, 200, eps=0.002,
+                                       irrep="E", note="Kitaev K=-1, complex E-irrep tensor, near-product, "
+                                                       "enlarged corner 2592x2592 complex"),
+    "kitaev_E_D6_chi72": Workload("kitaev_E_D6_chi72", 2, 6, 72, -1.0, 0.0, 1011, 30, irrep="E",
+                                  note="Kitaev K=-1, random complex E-irrep tensor, the size of kh_D6_chi72"),
 }
 
 

@@ -186,12 +186,13 @@ def test_complex_split_steps_and_energy(ctm_lib):
     assert abs(E - Ez) < 1e-9, (E, Ez)
 
 
+@pytest.mark.parametrize("chi", [64, 72])
 @pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
-def test_complex_d6_chi64_workload(ctm_lib, precision):
-    """The D = 6, chi = 64 complex workload: three steps of the random tensor against the
-    oracle (M, and Q on its well-determined columns), then the converging tensor's
-    energy."""
-    w = I.WORKLOADS["kitaev_E_D6_chi64"]
+def test_complex_d6_workload(ctm_lib, precision, chi):
+    """The D = 6 complex workloads (chi = 64, and 72 whose embedded QR has 144 columns):
+    three steps of the random tensor against the oracle (M, and Q on its well-determined
+    columns), then the converging tensor's energy."""
+    w = I.WORKLOADS[f"kitaev_E_D6_chi{chi}"]
     A = w.site_tensor()
     g = _ctm(A, w.chi, precision=precision)
     z = Z.ComplexCTM(A, w.chi)
@@ -204,7 +205,7 @@ def test_complex_d6_chi64_workload(ctm_lib, precision):
         _compare_step(g, z, f"{precision} step {k}", mscale=scale * (1 if precision == "fp64" else 2 * math.sqrt(z.n)),
                       qscale=scale)
     g.close()
-    w = I.WORKLOADS["kitaev_E_D6_chi64_conv"]
+    w = I.WORKLOADS[f"kitaev_E_D6_chi{chi}_conv"]
     A = w.site_tensor()
     g = _ctm(A, w.chi, precision=precision)
     z = Z.ComplexCTM(A, w.chi)
@@ -222,6 +223,6 @@ def test_complex_rejects_bad_config(ctm_lib):
     from paper_2509_05090_gb300 import binding
     A = I.random_complex_site_tensor(2, 2, 3)
     with pytest.raises(binding.CtmError):
-        binding.CTMComplex(A, 65)                       # chi above the embedded QR's limit
+        binding.CTMComplex(A, 81)                       # chi above the embedded QR's limit
     with pytest.raises(binding.CtmError):
         binding.CTMComplex(A[:1], 4)                    # d = 1 has no E irrep

@@ -151,6 +151,11 @@ def test_single_step_matches_oracle_d6_chi72(ctm_lib):
     _step_parity(w.site_tensor(), w.chi, 1)
 
 
+def test_single_step_matches_oracle_chi144(ctm_lib):
+    """chi = 144 (a QR of 144 columns) at D = 3 (n = 1296), from a non-trivial environment."""
+    _step_parity(I.random_site_tensor(2, 3, 77), 144, 2)
+
+
 @pytest.mark.parametrize("name,pre", [("kh_D6_chi72_conv", 1), ("kitaev_D4_chi32_conv", 3)])
 def test_single_step_matches_oracle_rank_deficient(ctm_lib, name, pre):
     """Converging near-product states: R falls below 1e-8 R_00 after ~16 / 37 columns, so
