@@ -451,6 +451,83 @@ def complex_record(steps, n_split, fp64_peak, bf16_peak, with_oracle=True):
     return rec
 
 
+def run_complex(args, w):
+    """A complex (E-irrep) workload as the benchmark's own line: K steps of the complex path
+    (one replayed one-step graph each) timed with CUDA events after warm-up, 1 GPU."""
+    import numpy as np
+    import torch
+    from paper_2509_05090_gb300 import binding
+    torch.cuda.set_device(0)
+    A = w.site_tensor()
+    g = binding.CTMComplex(A, w.chi, precision=args.precision, n_split=args.n_split)
+    for _ in range(args.warmup):
+        g.ctm_complex_step(1, want_delta=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0 = binding.ctm_kernel_launches()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        e0.record(g.stream)
+        g.ctm_complex_step(args.steps, want_delta=False)
+        e1.record(g.stream)
+        torch.cuda.synchronize()
+    launches = binding.ctm_kernel_launches() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    g.close()
+    peaks, src = _peaks()
+    flops = 4.0 * step_gemm_flops(w.chi, w.D2)
+    if args.precision == "fp64":
+        fp64_peak = binding.ctm_probe_fp64_peak()
+        ach = flops / (ms / 1e3) / 1e12
+        roofline = {"bound": "alu", "achieved": ach, "peak": fp64_peak, "unit": "TFLOP/s", "frac": ach / fp64_peak,
+                    "traffic": None, "peak_source": "measured live: DFMA throughput probe",
+                    "scope": "whole step (contractions, embedded QR, corner spectrum) against the FP64 pipe"}
+    else:
+        pairs = args.n_split * (args.n_split + 1) // 2
+        ach = pairs * flops / (ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                    "frac": ach / peaks["bf16_tflops"], "traffic": None, "peak_source": f"{src} bf16 burst",
+                    "scope": "whole step time (a lower bound on the contraction kernels' rate)"}
+    line = {"metric": METRIC, "value": 1e3 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128" if args.precision == "fp64" else f"bf16x{args.n_split}-split+c128",
+            "data": "synthetic (seeded complex site tensor, E-irrep projected)",
+            "config": {"workload": w.name, "d": w.d, "D": w.D, "chi": w.chi, "n": w.n, "irrep": "E",
+                       "precision": args.precision, "parallelism": "single",
+                       "l2": "timed steps back to back; per-step working set > L2"},
+            "roofline": roofline, "algorithmic_flops_per_step": flops, "clocks": clk.summary(),
+            "gpu_launches": int(launches)}
+    if not args.no_e2e:
+        A_host = torch.from_numpy(np.ascontiguousarray(A)).pin_memory()
+        h_host = torch.from_numpy(np.ascontiguousarray(w.hamiltonians().astype(np.complex128))).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        gz = binding.CTMComplex(A_host.to("cuda", non_blocking=True), w.chi, precision=args.precision,
+                                n_split=args.n_split)
+        for _ in range(args.steps):
+            gz.ctm_complex_step(1, want_delta=True)
+        _, es, rho = gz.ctm_complex_energy(h_host.to("cuda", non_blocking=True))
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        gz.close()
+        line["e2e"] = {"value": args.steps / t, "unit": "steps/s",
+                       "h2d_bytes_per_step": (A_host.numel() + h_host.numel()) * 16 / args.steps,
+                       "d2h_bytes_per_step": 8 + (4 + 2 * rho.size) * 8 / args.steps, "E_site": es}
+    if not args.no_cpu_baseline:
+        from oracle import complex_oracle as zorc
+        ref = zorc.ComplexCTM(A, w.chi)
+        t0 = time.perf_counter()
+        nst = 0
+        while nst < 4 and time.perf_counter() - t0 < 10.0:
+            ref.step()
+            nst += 1
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": nst / secs, "unit": "steps/s", "cores": os.cpu_count(), "kind": "oracle",
+                                "sample": f"{nst} numpy complex128 oracle steps of {w.name} ({secs:.1f} s, BLAS "
+                                          "threads on all host cores)"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def split_step_rate(w, steps, n_split, corner="qmq"):
     import torch
     from paper_2509_05090_gb300 import binding
@@ -487,6 +564,8 @@ def main():
     if args.workload == "batch96":
         return run_batch(args)
     w = inputs.WORKLOADS[args.workload]
+    if w.irrep == "E" and args.impl != "reference":
+        return run_complex(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
 

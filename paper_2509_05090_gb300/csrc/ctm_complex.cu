@@ -11,8 +11,8 @@
 // and both products sharing the packed left operand.  The complex QR is the real
 // Householder QR of the 2 x 2 block embedding [[Re, -Im], [Im, Re]] of the reduced
 // corner, whose unique factors (positive diagonal) are the embeddings of the complex
-// Q and R; the corner spectrum is that of the embedded (real symmetric) corner, each
-// eigenvalue twice.
+// Q and R; the corner spectrum comes from a Householder reduction of the Hermitian
+// corner to a tridiagonal matrix and the bisection of the real path.
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -43,7 +43,7 @@ struct ctm_complex_ctx {
     double *Y1, *Y1o, *G2;
     long long PY1, PYo;
     double *P5a, *P5b;
-    double *Yemb, *Qemb, *Remb, *Cemb;
+    double *Yemb, *Qemb, *Remb;
     double *s, *s_new, *delta, *spec_work;
     double *splitk;
     size_t splitk_elems;
@@ -60,9 +60,11 @@ struct ctm_complex_ctx {
     // the corner spectrum runs on a side stream beside the edge update
     cudaStream_t side;
     cudaEvent_t ev_fork, ev_join;
-    cudaGraphExec_t graph1;
-    unsigned long long graph1_kernels;
+    cudaGraphExec_t graph1, graphK;
+    unsigned long long graph1_kernels, graphK_kernels;
+    int graphK_steps;
     int graph_failed;
+    int side_pending;   // a corner spectrum on the side stream not yet joined into the main stream
 };
 
 namespace {
@@ -557,15 +559,134 @@ __global__ void zc_herm_normalize_kernel(int chi, const double *Cr, long long PC
     }
 }
 
-// the real symmetric embedding [[Re C, -Im C], [Im C, Re C]] (2chi x 2chi) of a Hermitian C
-__global__ void zc_embed_herm_kernel(int chi, const double *C, long long PC, double *E)
+// Sum over the CTA of one value per thread (blockDim a multiple of 32, <= 1024).
+__device__ double zblock_sum(double v, double *red)
 {
-    const int m = 2 * chi;
-    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < m * m; t += gridDim.x * blockDim.x) {
-        const int I = t / m, J = t % m;
-        const int i = I % chi, j = J % chi, bi = I / chi, bj = J / chi;
-        const double re = C[i * chi + j], im = C[3 * PC + i * chi + j];
-        E[t] = (bi == bj) ? re : (bi == 1 ? im : -im);
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < nw; ++i) s += red[i];
+        red[32] = s;
+    }
+    __syncthreads();
+    return red[32];
+}
+
+// The corner spectrum, step one: Householder reduction of the Hermitian corner (Re in plane
+// 0, Im in plane 3 of its five planes) to tridiagonal form in one CTA's shared memory.  For
+// column k with x the part below the diagonal, x_0 = |x_0| e^{i theta}: alpha =
+// -e^{i theta} |x|, v = x - alpha e_0, beta = 2 / |v|^2 = 1 / (|x| (|x| + |x_0|)); with
+// p = beta A v, K = (beta/2) Re(v^H p) and w = p - K v the update is
+// A <- A - v w^H - w v^H.  The result is a Hermitian tridiagonal matrix whose eigenvalues
+// are those of the real symmetric one with off-diagonal |e_i|: work receives its diagonal
+// and |e_i|^2, which the bisection of the real spectrum takes as they are.
+constexpr int ZTRI_THREADS = 256;
+size_t ztridiag_smem_bytes(int chi) { return sizeof(double) * ((size_t)2 * chi * (chi | 1) + 4 * (size_t)chi); }
+
+__global__ void __launch_bounds__(ZTRI_THREADS) zc_tridiag_kernel(int chi, const double *C, long long PC, double *work)
+{
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh_beta, sh_ar, sh_ai;
+    const int ld = chi | 1;
+    double *Ar = sm, *Ai = Ar + (size_t)chi * ld;
+    double *vr = Ai + (size_t)chi * ld, *vi = vr + chi, *pr = vi + chi, *pim = pr + chi;
+    const int tid = threadIdx.x;
+    const double *Ci = C + 3 * PC;
+    for (int t = tid; t < chi * chi; t += blockDim.x) {
+        const int i = t / chi, j = t % chi;
+        Ar[i * ld + j] = 0.5 * (C[t] + C[j * chi + i]);
+        Ai[i * ld + j] = 0.5 * (Ci[t] - Ci[j * chi + i]);
+    }
+    __syncthreads();
+    for (int kc = 0; kc + 2 < chi; ++kc) {
+        const int b0 = kc + 1, m = chi - b0;
+        double part = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) {
+            const double xr = Ar[(b0 + i) * ld + kc], xi = Ai[(b0 + i) * ld + kc];
+            vr[i] = xr;
+            vi[i] = xi;
+            if (i > 0) part += xr * xr + xi * xi;
+        }
+        const double tail = zblock_sum(part, red);   // its barriers also publish v
+        if (tail == 0.0) continue;                   // already tridiagonal in this column
+        const double x0r = vr[0], x0i = vi[0];
+        if (tid == (int)blockDim.x - 1) {
+            const double a0 = sqrt(x0r * x0r + x0i * x0i);
+            const double nrm = sqrt(tail + a0 * a0);
+            const double cr = a0 > 0.0 ? x0r / a0 : 1.0, ci = a0 > 0.0 ? x0i / a0 : 0.0;
+            sh_ar = -cr * nrm;
+            sh_ai = -ci * nrm;
+            sh_beta = 1.0 / (nrm * (nrm + a0));
+        }
+        // y = A x over the trailing block (v still holds x)
+        for (int i = tid; i < m; i += blockDim.x) {
+            const double *rr = Ar + (b0 + i) * ld + b0, *ri = Ai + (b0 + i) * ld + b0;
+            double sr0 = 0.0, si0 = 0.0, sr1 = 0.0, si1 = 0.0;
+            int j = 0;
+            for (; j + 1 < m; j += 2) {
+                sr0 = fma(rr[j], vr[j], fma(-ri[j], vi[j], sr0));
+                si0 = fma(rr[j], vi[j], fma(ri[j], vr[j], si0));
+                sr1 = fma(rr[j + 1], vr[j + 1], fma(-ri[j + 1], vi[j + 1], sr1));
+                si1 = fma(rr[j + 1], vi[j + 1], fma(ri[j + 1], vr[j + 1], si1));
+            }
+            if (j < m) {
+                sr0 = fma(rr[j], vr[j], fma(-ri[j], vi[j], sr0));
+                si0 = fma(rr[j], vi[j], fma(ri[j], vr[j], si0));
+            }
+            pr[i] = sr0 + sr1;
+            pim[i] = si0 + si1;
+        }
+        __syncthreads();
+        const double beta = sh_beta, ar = sh_ar, ai = sh_ai;
+        // p = beta (A x - alpha A e_0), then v_0 = x_0 - alpha
+        for (int i = tid; i < m; i += blockDim.x) {
+            const double er = Ar[(b0 + i) * ld + b0], ei = Ai[(b0 + i) * ld + b0];
+            pr[i] = beta * (pr[i] - (ar * er - ai * ei));
+            pim[i] = beta * (pim[i] - (ar * ei + ai * er));
+        }
+        if (tid == 0) {
+            vr[0] = x0r - ar;
+            vi[0] = x0i - ai;
+        }
+        __syncthreads();
+        double pv = 0.0;   // Re(v^H p)
+        for (int i = tid; i < m; i += blockDim.x) pv += vr[i] * pr[i] + vi[i] * pim[i];
+        pv = zblock_sum(pv, red);
+        const double Kf = 0.5 * beta * pv;
+        for (int i = tid; i < m; i += blockDim.x) {   // p <- w
+            pr[i] -= Kf * vr[i];
+            pim[i] -= Kf * vi[i];
+        }
+        __syncthreads();
+        for (int t = tid; t < m * m; t += blockDim.x) {
+            const int i = t / m, j = t % m;
+            // v_i conj(w_j) + w_i conj(v_j)
+            const double re = vr[i] * pr[j] + vi[i] * pim[j] + pr[i] * vr[j] + pim[i] * vi[j];
+            const double im = vi[i] * pr[j] - vr[i] * pim[j] + pim[i] * vr[j] - pr[i] * vi[j];
+            Ar[(b0 + i) * ld + b0 + j] -= re;
+            Ai[(b0 + i) * ld + b0 + j] -= im;
+        }
+        if (tid == 0) {
+            Ar[b0 * ld + kc] = ar;
+            Ai[b0 * ld + kc] = ai;
+            Ar[kc * ld + b0] = ar;
+            Ai[kc * ld + b0] = -ai;
+        }
+        __syncthreads();
+    }
+    for (int i = tid; i < chi; i += blockDim.x) {
+        work[i] = Ar[i * ld + i];
+        double e2 = 0.0;
+        if (i + 1 < chi) {
+            const double er = Ar[(i + 1) * ld + i], ei = Ai[(i + 1) * ld + i];
+            e2 = er * er + ei * ei;
+        }
+        work[chi + i] = e2;
     }
 }
 
@@ -815,11 +936,10 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->Yemb = td(2 * n * k2);
     c->Qemb = td(2 * n * k2);
     c->Remb = td(k2 * k2);
-    c->Cemb = td(k2 * k2);
-    c->s = td(k2);
-    c->s_new = td(k2);
+    c->s = td(chi);
+    c->s_new = td(chi);
     c->delta = td(8);
-    c->spec_work = td((long long)spectrum_work_doubles((int)k2));
+    c->spec_work = td((long long)spectrum_work_doubles((int)chi));
     size_t sk = 0;
     for (const auto &sh : zshapes(c)) {
         int s = gemm_f64_pick_split(sh[0], sh[1], sh[2]);
@@ -980,32 +1100,41 @@ int zedge(ctm_complex_ctx *c)
 // the corner spectrum of C (five planes): delta against the previous one, on `st`
 int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st)
 {
-    const int k2 = 2 * c->chi;
-    CTM_COUNT_LAUNCH(1);
-    zc_embed_herm_kernel<<<(k2 * k2 + 255) / 256, 256, 0, c->stream>>>(c->chi, Cin, c->PC, c->Cemb);
-    ZK(cudaGetLastError());
+    const int chi = c->chi;
     if (st != c->stream) {
         ZK(cudaEventRecord(c->ev_fork, c->stream));
         ZK(cudaStreamWaitEvent(st, c->ev_fork, 0));
     }
-    ZK(launch_spectrum(k2, c->Cemb, c->s_new, c->s, c->delta, c->spec_work, st));
-    ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * k2, cudaMemcpyDeviceToDevice, st));
+    CTM_COUNT_LAUNCH(1);
+    zc_tridiag_kernel<<<1, ZTRI_THREADS, ztridiag_smem_bytes(chi), st>>>(chi, Cin, c->PC, c->spec_work);
+    ZK(cudaGetLastError());
+    ZK(launch_spectrum_from_tridiag(chi, c->spec_work, c->s_new, c->s, c->delta, st));
+    ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
     if (st != c->stream) ZK(cudaEventRecord(c->ev_join, st));
     return CTM_OK;
 }
 
-int zstep(ctm_complex_ctx *c)
+// One step.  The spectrum of C' runs on the side stream from the corner update on; it is
+// joined before the next step's corner update rewrites C', or at the end when join_now.
+int zstep(ctm_complex_ctx *c, int join_now)
 {
     int rc;
     if ((rc = zenlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = zprojector(c)) != CTM_OK) return rc;
+    if (c->side_pending) {
+        ZK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        c->side_pending = 0;
+    }
     if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
-    // the spectrum of C' (from its private embedding) beside the edge update
     if ((rc = zspectrum(c, c->Cn, c->side)) != CTM_OK) return rc;
+    c->side_pending = 1;
     if ((rc = zedge(c)) != CTM_OK) return rc;
     const long long chi = c->chi, D2 = c->D2, n = c->n;
     cudaStream_t st = c->stream;
-    ZK(cudaStreamWaitEvent(st, c->ev_join, 0));
+    if (join_now) {
+        ZK(cudaStreamWaitEvent(st, c->ev_join, 0));
+        c->side_pending = 0;
+    }
     ZK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * 5 * chi * chi, cudaMemcpyDeviceToDevice, st));
     ZK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * 5 * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
     ZK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * 5 * n * chi, cudaMemcpyDeviceToDevice, st));
@@ -1082,7 +1211,9 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         }
     int rc = CTM_OK;
     do {
-        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess) {
+        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess ||
+            cudaFuncSetAttribute(zc_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)ztridiag_smem_bytes(80)) != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
         }
@@ -1109,7 +1240,7 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, c->a);
         zc_init_env_kernel<<<zgrid(c->PT), 256, 0, c->stream>>>(c->chi, c->D, c->a, c->Pa, c->C, c->T, c->Q);
         if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
-        if (launch_spectrum_init(2 * c->chi, c->s, c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
+        if (launch_spectrum_init(c->chi, c->s, c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
         if (cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
         CTM_COUNT_LAUNCH(1);
         zc_check_finite_kernel<<<zgrid(2 * cnt), 256, 0, c->stream>>>(2 * cnt, c->A, c->flag);
@@ -1129,26 +1260,39 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
     return CTM_OK;
 }
 
-// Capture one step on the private stream into graph1; a launch that cannot be captured
-// leaves graph_failed set and the context runs eagerly.
-static int zcapture(ctm_complex_ctx *c)
+// Capture nsteps steps on the private stream into graph1 (one step) or graphK (the last
+// multi-step count asked for); a launch that cannot be captured leaves graph_failed set
+// and the context runs eagerly.  Inside a multi-step graph each step's spectrum overlaps
+// the next step up to its corner update; the graph ends joined.
+static int zcapture(ctm_complex_ctx *c, int nsteps)
 {
-    if (c->graph1 || c->graph_failed) return CTM_OK;
+    cudaGraphExec_t *exec = nsteps == 1 ? &c->graph1 : &c->graphK;
+    if (c->graph_failed) return CTM_OK;
+    if (nsteps == 1 ? c->graph1 != nullptr : (c->graphK && c->graphK_steps == nsteps)) return CTM_OK;
+    if (*exec) {
+        cudaGraphExecDestroy(*exec);
+        *exec = nullptr;
+    }
     cudaGraph_t g = nullptr;
     const unsigned long long l0 = g_ctm_launches;
     ZK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     const int steps0 = c->steps_done;
-    int rc = zstep(c);
+    int rc = CTM_OK;
+    for (int i = 0; i < nsteps && rc == CTM_OK; ++i) rc = zstep(c, i == nsteps - 1);
     c->steps_done = steps0;
+    c->side_pending = 0;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
-    if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->graph1, g, 0);
+    if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);
-    if (rc != CTM_OK || e != cudaSuccess || !c->graph1) {
+    if (rc != CTM_OK || e != cudaSuccess || !*exec) {
         cudaGetLastError();
-        c->graph1 = nullptr;
+        *exec = nullptr;
         c->graph_failed = 1;
-    } else {
+    } else if (nsteps == 1) {
         c->graph1_kernels = g_ctm_launches - l0;
+    } else {
+        c->graphK_kernels = g_ctm_launches - l0;
+        c->graphK_steps = nsteps;
     }
     g_ctm_launches = l0;
     return CTM_OK;
@@ -1158,25 +1302,29 @@ int ctm_complex_step(ctm_complex_ctx *c, int nsteps, double *delta_host)
 {
     if (!c || nsteps < 1) return CTM_EINVAL;
     int rc;
-    int done = 0;
+    bool done = false;
     if (c->steps_done > 0 && !c->graph_failed) {
+        // steps after the first (eager, autotuning) one: one captured graph of nsteps steps,
+        // ordered after the caller's stream
         cudaStream_t user = c->stream;
         ZK(cudaEventRecord(c->ev_in, user));
         ZK(cudaStreamWaitEvent(c->own, c->ev_in, 0));
         c->stream = c->own;
-        rc = zcapture(c);
-        for (; rc == CTM_OK && c->graph1 && done < nsteps; ++done) {
-            if (cudaGraphLaunch(c->graph1, c->stream) != cudaSuccess) rc = CTM_ECUDA;
-            CTM_COUNT_LAUNCH(c->graph1_kernels);
+        rc = zcapture(c, nsteps);
+        cudaGraphExec_t ge = nsteps == 1 ? c->graph1 : c->graphK;
+        if (rc == CTM_OK && ge) {
+            if (cudaGraphLaunch(ge, c->stream) != cudaSuccess) rc = CTM_ECUDA;
+            CTM_COUNT_LAUNCH(nsteps == 1 ? c->graph1_kernels : c->graphK_kernels);
+            done = (rc == CTM_OK);
+            if (done) c->steps_done += nsteps;
         }
-        c->steps_done += done;
         c->stream = user;
         ZK(cudaEventRecord(c->ev_out, c->own));
         ZK(cudaStreamWaitEvent(user, c->ev_out, 0));
         if (rc != CTM_OK) return rc;
     }
-    for (; done < nsteps; ++done)
-        if ((rc = zstep(c)) != CTM_OK) return rc;
+    for (int i = 0; i < nsteps && !done; ++i)
+        if ((rc = zstep(c, i == nsteps - 1)) != CTM_OK) return rc;
     if ((rc = zread_status(c)) != CTM_OK) return rc;
     if (delta_host) {
         ZK(cudaMemcpyAsync(delta_host, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -1328,10 +1476,7 @@ int ctm_complex_set_env(ctm_complex_ctx *c, const double *C_dev, const double *T
     zc_load_kernel<<<zgrid(c->PQ), 256, 0, st>>>(c->PQ, Q_dev, c->Q, zlay_stacked(c->PQ, 5));
     ZK(cudaGetLastError());
     // the spectrum of the new corner becomes the reference for the next delta
-    const int k2 = 2 * c->chi;
-    CTM_COUNT_LAUNCH(1);
-    zc_embed_herm_kernel<<<(k2 * k2 + 255) / 256, 256, 0, st>>>(c->chi, c->C, c->PC, c->Cemb);
-    ZK(launch_spectrum(k2, c->Cemb, c->s, c->s, c->delta, c->spec_work, st));
+    if (zspectrum(c, c->C, st) != CTM_OK) return CTM_ECUDA;
     ZK(cudaStreamSynchronize(st));
     return CTM_OK;
 }
@@ -1349,14 +1494,9 @@ int ctm_complex_get_intermediate(const ctm_complex_ctx *c, int which, double *ds
     case 1: src = c->Y; cnt = n * chi; L = zlay_stacked(c->PY, 2); break;
     case 2: src = c->R; cnt = chi * chi; L = zlay_stacked(c->PC, 2); break;
     case 3: src = c->Q; cnt = n * chi; L = zlay_stacked(c->PQ, 5); break;
-    case 4: {   // the corner spectrum: every other value of the embedded one, times sqrt 2
+    case 4: {   // the corner spectrum (real)
         if (count < (size_t)chi) return CTM_EINVAL;
-        std::vector<double> s2((size_t)(2 * chi));
-        ZK(cudaMemcpyAsync(s2.data(), c->s, sizeof(double) * 2 * chi, cudaMemcpyDeviceToHost, st));
-        ZK(cudaStreamSynchronize(st));
-        std::vector<double> s((size_t)chi);
-        for (long long i = 0; i < chi; ++i) s[i] = (s2[2 * i] + s2[2 * i + 1]) * sqrt(0.5);
-        ZK(cudaMemcpyAsync(dst, s.data(), sizeof(double) * chi, cudaMemcpyHostToDevice, st));
+        ZK(cudaMemcpyAsync(dst, c->s, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
         ZK(cudaStreamSynchronize(st));
         return CTM_OK;
     }
@@ -1379,6 +1519,7 @@ void ctm_complex_destroy(ctm_complex_ctx *c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    if (c->graphK) cudaGraphExecDestroy(c->graphK);
     if (c->own) {
         cudaStreamSynchronize(c->own);
         cudaStreamDestroy(c->own);

@@ -123,6 +123,10 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
                             double *work, cudaStream_t st);
 cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st);
+// The last two phases of launch_spectrum for a real symmetric tridiagonal matrix already in
+// `work` (diagonal d in work[0, chi), squared off-diagonal e^2 in work[chi, 2 chi)).
+cudaError_t launch_spectrum_from_tridiag(int chi, double *work, double *s_new, const double *s_old, double *delta,
+                                        cudaStream_t st);
 cudaError_t launch_bond_energy(int d, const double *rho_raw, const double *h, double *out, cudaStream_t st);
 cudaError_t launch_open_layers(int d, int D, const double *A, double *b, cudaStream_t st);
 cudaError_t launch_check_finite(long long count, const double *x, int *flag, cudaStream_t st);

@@ -505,6 +505,18 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
     return cudaGetLastError();
 }
 
+cudaError_t launch_spectrum_from_tridiag(int chi, double *work, double *s_new, const double *s_old, double *delta,
+                                        cudaStream_t st)
+{
+    if (chi > 160 || !work) return cudaErrorInvalidValue;
+    CTM_COUNT_LAUNCH(2);
+    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, work + 2 * chi, s_new, s_old, delta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st)
 {
     CTM_COUNT_LAUNCH(1);

@@ -90,6 +90,9 @@ def test_complex_steps_fp64(ctm_lib, D, chi, seed):
         # C' and T' inherit the error of the well-determined part of Q
         assert np.abs(Cg - z.C).max() < 1e-9, (k, np.abs(Cg - z.C).max())
         assert abs(dg - dz) < 1e-9
+        # the corner spectrum from the Hermitian tridiagonal reduction and bisection
+        sg = _np(g.ctm_complex_get_intermediate("s"))
+        assert np.abs(sg - z.s).max() < 1e-12, (k, np.abs(sg - z.s).max())
 
 
 def test_complex_a1_matches_real_oracle(ctm_lib):
