@@ -528,10 +528,10 @@ def run_complex(args, w):
     return 0
 
 
-def split_step_rate(w, steps, n_split, corner="qmq"):
+def split_step_rate(w, steps, n_split, corner="qmq", precision="split_bf16"):
     import torch
     from paper_2509_05090_gb300 import binding
-    c = binding.CTM(w.site_tensor(), w.chi, precision="split_bf16", n_split=n_split, corner=corner)
+    c = binding.CTM(w.site_tensor(), w.chi, precision=precision, n_split=n_split, corner=corner)
     c.ctm_step(1, want_delta=False)
     c.ctm_step(steps, want_delta=False)
     torch.cuda.synchronize()
@@ -727,6 +727,13 @@ def main():
         rec8 = fp64_step_record(w8, 3, fp64_peak)
         rec8["split_bf16_steps_per_s"] = split_step_rate(w8, 3, args.n_split)
         line["fp64_d8_chi128"] = rec8
+        # the TF32 tensor-core modes: steps/s and the energy after 3 steps against the oracle
+        tf = {}
+        for prec in ("split_tf32", "fp32_tf32"):
+            E_t, E_o = energy_vs_oracle(w, prec, args.n_split, 3)
+            tf[prec] = {"steps_per_s": split_step_rate(w, args.steps, args.n_split, precision=prec),
+                        "E_site_after_3_steps": E_t, "abs_err_vs_oracle": abs(E_t - E_o)}
+        line["tf32_modes"] = tf
         line["batch96"] = batch_record(args, args.steps)
         line["complex_E_D6_chi72"] = complex_record(args.steps, args.n_split, fp64_peak, peaks["bf16_tflops"],
                                                     with_oracle=not args.no_compare)

@@ -56,9 +56,14 @@ typedef enum {
 
 typedef enum {
     CTM_FP64 = 0,            /* every contraction in FP64 */
-    CTM_SPLIT_BF16 = 1       /* contractions as split-BF16 tcgen05 products (FP32 accumulate,
+    CTM_SPLIT_BF16 = 1,      /* contractions as split-BF16 tcgen05 products (FP32 accumulate,
                                 FP64 recombination); QR, normalisation and the
                                 convergence test stay FP64 */
+    CTM_SPLIT_TF32 = 2,      /* contractions as A_hi B_hi + A_hi B_lo + A_lo B_hi of TF32 hi/lo
+                                slices on tcgen05 (kind::tf32), FP32 accumulation: about FP32
+                                accuracy (n_split ignored); QR etc. FP64 */
+    CTM_FP32_TF32 = 3        /* contractions as one TF32 product A_hi B_hi (FP32 inputs rounded
+                                to TF32), FP32 accumulation; QR etc. FP64 */
 } ctm_precision;
 
 typedef struct {

@@ -21,7 +21,9 @@ CTM_OK = 0
 CTM_ENOTCONVERGED = 4
 CTM_FP64 = 0
 CTM_SPLIT_BF16 = 1
-PRECISIONS = {"fp64": CTM_FP64, "split_bf16": CTM_SPLIT_BF16}
+CTM_SPLIT_TF32 = 2
+CTM_FP32_TF32 = 3
+PRECISIONS = {"fp64": CTM_FP64, "split_bf16": CTM_SPLIT_BF16, "split_tf32": CTM_SPLIT_TF32, "fp32_tf32": CTM_FP32_TF32}
 
 
 class ctm_config(ctypes.Structure):

@@ -149,6 +149,36 @@ size_t layout(ctm_ctx *c, char *base)
     c->rho_raw = td(d * d * d * d);
     c->eout = td(4 + d * d * d * d);
     c->h = td(3 * d * d * d * d);
+    if (c->tf32_T > 0) {
+        // packed TF32 slices, exponents and the split-K FP64 accumulator for the largest
+        // operand of the step's, the energy's and the transfer spectrum's contractions
+        size_t ap = 0, bp = 0, pp = 0;
+        long long ecap = 0;
+        std::vector<Shape> shapes = step_shapes(c);
+        shapes.push_back({(int)n, (int)n, (int)chi});
+        shapes.push_back({(int)(chi * chi), (int)(d * d * D2), (int)(D2 * D2)});
+        for (const auto &sh : shapes) {
+            SplitPlan pl = tf32_plan_caps(sh.M, sh.N, sh.K, c->tf32_T);
+            if (pl.a_pack_bytes > ap) ap = pl.a_pack_bytes;
+            if (pl.b_pack_bytes > bp) bp = pl.b_pack_bytes;
+            if (pl.partial_bytes > pp) pp = pl.partial_bytes;
+            if (sh.M > ecap) ecap = sh.M;
+            if (sh.N > ecap) ecap = sh.N;
+        }
+        c->sw.Apk = (unsigned char *)take(ap);
+        c->sw.a_pack_cap = ap;
+        c->sw.Bpk = (unsigned char *)take(bp);
+        c->sw.b_pack_cap = bp;
+        c->sw.eA = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw.eB = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw.e_cap = (int)ecap;
+        c->sw.partial = (void *)take(pp + 8);
+        c->sw.partial_cap = pp;
+        c->sw.err = c->err;
+        c->sw.autotune = 0;
+        c->sw_c = c->sw;
+        c->sw_e = c->sw;
+    }
     if (c->split_T > 0) {
         // packed digit slices, exponents and the split-K integer accumulator for the
         // largest operand of the step's contractions
@@ -206,13 +236,20 @@ size_t layout(ctm_ctx *c, char *base)
     return off;
 }
 
+int tf32_slices(int precision)
+{
+    return precision == CTM_SPLIT_TF32 ? 2 : (precision == CTM_FP32_TF32 ? 1 : 0);
+}
+
 bool config_ok(const ctm_config *cfg)
 {
     if (!cfg) return false;
     if (cfg->d < 1 || cfg->d > 3) return false;
     if (cfg->D < 1 || cfg->D > 12) return false;
     if (cfg->chi < 1 || cfg->chi > 160) return false;
-    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return false;
+    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16 && cfg->precision != CTM_SPLIT_TF32 &&
+        cfg->precision != CTM_FP32_TF32)
+        return false;
     if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
     if (cfg->corner_mode != 0 && cfg->corner_mode != 1) return false;
     long long n = (long long)cfg->chi * cfg->D * cfg->D;
@@ -227,6 +264,10 @@ cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint, int lane)
     if (c->prof_on && c->prof_n + 3 <= CTM_PROF_EVENTS) {
         ev = c->prof_ev + c->prof_n;
         c->prof_n += 3;
+    }
+    if (c->tf32_T > 0) {
+        cudaError_t e = gemm_tf32(g, c->tf32_T, c->sw, c->stream, ev);
+        return e;
     }
     if (c->split_T > 0) {
         SplitOpts o{};
@@ -617,6 +658,7 @@ size_t ctm_workspace_bytes(const ctm_config *cfg)
     c.chi = cfg->chi;
     c.n = (long long)c.chi * c.D2;
     c.split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
+    c.tf32_T = tf32_slices(cfg->precision);
     return layout(&c, nullptr);
 }
 
@@ -626,7 +668,6 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     if (!out) return CTM_EINVAL;
     *out = nullptr;
     if (!cfg || !A_dev || !workspace) return CTM_EINVAL;
-    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return CTM_EUNSUPPORTED;
     if (!config_ok(cfg)) return CTM_EINVAL;
     if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
     ctm_ctx *c = new (std::nothrow) ctm_ctx;
@@ -639,6 +680,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     c->chi = cfg->chi;
     c->n = (long long)c->chi * c->D2;
     c->split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
+    c->tf32_T = tf32_slices(cfg->precision);
     c->qr_rows_min = 1;
     c->stream = (cudaStream_t)stream;
     if (!qr_supported((int)c->n, c->chi)) {
@@ -654,7 +696,8 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     cudaStream_t st = c->stream;
     int rc = CTM_OK;
     do {
-        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess) {
+        if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess ||
+            tf32_prepare() != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
         }
@@ -1024,6 +1067,12 @@ size_t ctm_gemm_workspace_bytes(int M, int N, int K, int precision, int n_split)
         int s = gemm_f64_pick_split(M, N, K);
         return align_up(64) + align_up(sizeof(double) * (size_t)(s > 1 ? s : 0) * M * N + 8);
     }
+    if (tf32_slices(precision) > 0) {
+        SplitPlan p = tf32_plan_caps(M, N, K, tf32_slices(precision));
+        int ec = M > N ? M : N;
+        return align_up(64) + align_up(p.a_pack_bytes) + align_up(p.b_pack_bytes) + 2 * align_up(sizeof(int) * ec) +
+               align_up(p.partial_bytes + 8);
+    }
     if (precision != CTM_SPLIT_BF16 || !split_supported_T(n_split)) return 0;
     SplitPlan p = split_plan(M, N, K, n_split);
     int ec = M > N ? M : N;
@@ -1048,8 +1097,9 @@ int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, i
     if (precision == CTM_FP64) {
         CK(gemm_f64(g, gemm_f64_pick_split(M, N, K), (double *)(base + off), (ws_bytes - off) / sizeof(double), st));
     } else {
-        if (split_prepare() != cudaSuccess) return CTM_ECUDA;
-        SplitPlan p = split_plan(M, N, K, n_split);
+        if (split_prepare() != cudaSuccess || tf32_prepare() != cudaSuccess) return CTM_ECUDA;
+        const int tT = tf32_slices(precision);
+        SplitPlan p = tT > 0 ? tf32_plan_caps(M, N, K, tT) : split_plan(M, N, K, n_split);
         int ec = M > N ? M : N;
         SplitWork w;
         w.Apk = (unsigned char *)(base + off);
@@ -1067,7 +1117,8 @@ int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, i
         w.partial_cap = p.partial_bytes;
         w.err = err;
         w.autotune = 0;
-        CK(gemm_split(g, n_split, w, st, nullptr));
+        if (tT > 0) CK(gemm_tf32(g, tT, w, st, nullptr));
+        else CK(gemm_split(g, n_split, w, st, nullptr));
     }
     int e = 0;
     CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -1075,6 +1126,6 @@ int ctm_gemm(int M, int N, int K, const double *A, const double *B, double *C, i
     return e ? CTM_ETIMEOUT : CTM_OK;
 }
 
-const char *ctm_version(void) { return "libctm sm_103a fp64+bf16split"; }
+const char *ctm_version(void) { return "libctm sm_103a fp64+bf16split+tf32split"; }
 
 }  // extern "C"

@@ -35,6 +35,7 @@ struct ctm_ctx {
     double *splitk;
     size_t splitk_elems;
     int split_T;              // 0: FP64 contractions; 2..5: split-BF16 slices per operand
+    int tf32_T;               // 1, 2: TF32 slices per operand (FP32_TF32, SPLIT_TF32); 0 otherwise
     SplitWork sw;
     SplitWork sw_c;           // corner lane: M's pack read from sw; own B pack, exponents, split-K buffer
     SplitWork sw_e;           // edge lane: own A pack and exponents; B pack and split-K buffer of sw

@@ -83,6 +83,15 @@ cudaError_t split_prepare();
 cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev,
                        const SplitOpts *opt = nullptr);
 
+// ---------------------------------------------------------------- split-TF32 engine
+// C = A B from TF32 hi/lo slices (T = 2: A_hi B_hi + A_hi B_lo + A_lo B_hi; T = 1: A_hi B_hi)
+// on tcgen05.mma.kind::tf32 with FP32 accumulation (gemm_split.cu); the same work buffers
+// as the BF16 engine, sized by tf32_plan_caps.  ev as for gemm_split.
+SplitPlan tf32_plan_caps(int M, int N, int K, int T);
+int tf32_supported_T(int T);
+cudaError_t tf32_prepare();
+cudaError_t gemm_tf32(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev);
+
 // ---------------------------------------------------------------- QR
 // Householder QR of Y (n x k row-major, n >= k) with diag(R) >= 0.  Q (n x k)
 // and R (k x k) row-major.  One cooperative kernel: the blocked factorisation (one

@@ -1288,3 +1288,456 @@ cudaError_t gemm_split(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cu
 }
 
 int split_autotuned_shapes() { return (int)g_tune.size(); }
+
+// ---------------------------------------------------------------- split TF32
+// C = A B with A = A_hi + A_lo and B = B_hi + B_lo (TF32 values in FP32 containers, after
+// the exact power-of-two scaling of each row of A and column of B by 2^-E, E from the
+// exponent pre-pass above), the products A_hi B_hi + A_hi B_lo + A_lo B_hi (T = 2) or
+// A_hi B_hi alone (T = 1) by tcgen05.mma.kind::tf32 into FP32 accumulators in TMEM, so
+// the result has about FP32 accuracy.  A K tile is 32 wide: 128-byte rows of four-byte
+// elements, so tiles, rings, bulk copies, the 128-byte swizzle and the 32-byte advance of
+// the operand descriptors per MMA (K = 8) are those of the BF16 path, byte for byte.  The
+// CTA accumulates its whole K range in TMEM (two levels: A_hi [B_hi | B_lo] as one MMA of
+// N = 2 NT, then A_lo B_hi into the second level) and drains it once; the epilogue adds the
+// levels in FP32 and builds the FP64 result and its scale on the exponent field with integer
+// arithmetic.  Split-K partial results meet in an FP64 buffer through atomics.
+namespace {
+
+constexpr int TF_BK = 32;            // K per packed tile
+constexpr int TF_NT = 64;            // tile N
+constexpr int TF_ASLOTS = 4;         // A ring (16 KB slots)
+constexpr int TF_EPI_WARPS = 8;      // two per TMEM sub-partition, NT / 2 columns each
+constexpr int TF_THREADS = 64 + 32 * TF_EPI_WARPS;
+constexpr int TF_KT_PER_CHUNK = 4;   // split-K granularity: 128 K
+
+// byte offset of element (r, k) in a packed (rows x 32) four-byte tile, K-major 128B swizzle
+__device__ __forceinline__ int sw128_off32(int r, int k)
+{
+    return (r >> 3) * 1024 + (r & 7) * 128 + ((((k >> 2) ^ (r & 7))) << 4) + ((k & 3) << 2);
+}
+
+// x 2^-E (exact, on the exponent field; |x| < 2^E) rounded to FP32, then hi = that value
+// rounded to TF32 (10 fraction bits, ties away from zero) and lo = the exact remainder
+// rounded to TF32.  Values more than 2^-1022 below the row's scale become zero.
+__device__ __forceinline__ void tf32_split(double x, int E, uint32_t &hi, uint32_t &lo)
+{
+    const int hw = __double2hiint(x), lw = __double2loint(x);
+    const int ex = (hw >> 20) & 0x7FF;
+    hi = 0u;
+    lo = 0u;
+    if (ex == 0 || ex == 0x7FF || ex - E <= 0) return;
+    const double xs = __hiloint2double(hw - (E << 20), lw);
+    const float f = __double2float_rn(xs);
+    const uint32_t hb = (__float_as_uint(f) + 0x1000u) & 0xFFFFE000u;
+    const float r = f - __uint_as_float(hb);
+    hi = hb;
+    lo = (__float_as_uint(r) + 0x1000u) & 0xFFFFE000u;
+}
+
+// the FP32 value with bits b times 2^scale, as a double, by integer arithmetic (subnormal
+// FP32 values, far below the scales of the row and the column, become zero)
+__device__ __forceinline__ double scaled_f32_to_double(uint32_t b, int scale)
+{
+    const uint32_t mag = b & 0x7FFFFFFFu;
+    const int ef = (int)(mag >> 23);
+    if (ef == 0) return 0.0;
+    const int be = ef - 127 + 1023 + scale;
+    if (be <= 0) return 0.0;
+    const uint32_t sgn = b & 0x80000000u;
+    if (be >= 2047) return __hiloint2double((int)(sgn | 0x7FF00000u), 0);
+    const uint32_t m = mag & 0x7FFFFFu;
+    return __hiloint2double((int)(sgn | ((uint32_t)be << 20) | (m >> 3)), (int)(m << 29));
+}
+
+// Operand pre-pass: one thread per element of the padded tile grid (rows x kTiles*32),
+// along the rows when they are the contiguous index, else along K.
+template <int T>
+__global__ void tf32_pack_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles, const double *X, Idx2 rmap,
+                                 Idx2 kmap, const int *e, int rfast, unsigned char *out, long long slice_bytes)
+{
+    const long long KT = (long long)kTiles * TF_BK;
+    const long long total = (long long)rowsTotal * KT;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        int gr, gk;
+        if (rfast) {
+            gr = (int)(t % rowsTotal);
+            gk = (int)(t / rowsTotal);
+        } else {
+            gk = (int)(t % KT);
+            gr = (int)(t / KT);
+        }
+        uint32_t hi = 0u, lo = 0u;
+        if (gr < R && gk < K) tf32_split(X[off2(rmap, gr) + off2(kmap, gk)], exp_of_word(e[gr]), hi, lo);
+        const long long tile = (long long)(gr / rowsT) * kTiles + gk / TF_BK;
+        unsigned char *dst = out + tile * ((long long)rowsT * TF_BK * 4) + sw128_off32(gr % rowsT, gk % TF_BK);
+        *(uint32_t *)dst = hi;
+        if (T == 2) *(uint32_t *)(dst + slice_bytes) = lo;
+    }
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+size_t tf32_smem_bytes(int T)
+{
+    size_t b = 1024 + (size_t)TF_ASLOTS * SP_BM * TF_BK * 4 + (size_t)SP_BSLOTS * T * TF_NT * TF_BK * 4;
+    const size_t stage = 1024 + (size_t)SP_BM * (TF_NT + 1) * 4 + (size_t)(SP_BM + TF_NT) * 12;
+    return b > stage ? b : stage;
+}
+
+template <int T>
+__global__ void __launch_bounds__(TF_THREADS, 2) gemm_tf32_kernel(SplitArgs a)
+{
+    constexpr int NT = TF_NT;
+    constexpr int A_TILE = SP_BM * TF_BK * 4;   // 16 KB
+    constexpr int B_TILE = NT * TF_BK * 4;      // 8 KB
+    constexpr int QW = NT / (TF_EPI_WARPS / 4);  // columns per epilogue thread
+    constexpr int TMEM_COLS = T == 1 ? 64 : 128;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t bars[TF_ASLOTS * 2 + SP_BSLOTS * 2 + 2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+
+    unsigned char *sm = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *Asm = sm;
+    unsigned char *Bsm = sm + TF_ASLOTS * A_TILE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t bar0 = smem_u32(bars);
+    auto A_full = [&](int s) { return bar0 + 8u * s; };
+    auto A_empty = [&](int s) { return bar0 + 8u * (TF_ASLOTS + s); };
+    auto B_full = [&](int s) { return bar0 + 8u * (2 * TF_ASLOTS + s); };
+    auto B_empty = [&](int s) { return bar0 + 8u * (2 * TF_ASLOTS + SP_BSLOTS + s); };
+    const uint32_t ACC_FULL = bar0 + 8u * (2 * TF_ASLOTS + 2 * SP_BSLOTS);
+    const uint32_t DRAIN = ACC_FULL + 8u;
+
+    const int nt = blockIdx.x, mt = blockIdx.y, ks = blockIdx.z;
+    const int kt_beg = ks * a.chunks_per_split * TF_KT_PER_CHUNK;
+    const int kt_end = min(a.kTiles, kt_beg + a.chunks_per_split * TF_KT_PER_CHUNK);
+    volatile int *abort_flag = &abort_sh;
+
+    if (threadIdx.x == 0) {
+        abort_sh = 0;
+        for (int s = 0; s < TF_ASLOTS; ++s) {
+            mbar_init(A_full(s), 1);
+            mbar_init(A_empty(s), 1);
+        }
+        for (int s = 0; s < SP_BSLOTS; ++s) {
+            mbar_init(B_full(s), 1);
+            mbar_init(B_empty(s), 1);
+        }
+        mbar_init(ACC_FULL, 1);
+        mbar_init(DRAIN, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_base_sh)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base_sh;
+
+    if (warp == 0) {
+        // ------------------------------------------------ producers: bulk copies
+        if (lane == 0) {
+            int b = 0;
+            for (int kt = kt_beg; kt < kt_end && !*abort_flag; ++kt, ++b) {
+                const int sb = b % SP_BSLOTS;
+                if (!mbar_wait(B_empty(sb), ((b / SP_BSLOTS) & 1) ^ 1, abort_flag)) break;
+                mbar_expect_tx(B_full(sb), (uint32_t)(T * B_TILE));
+                for (int j = 0; j < T; ++j) {
+                    const unsigned char *src = a.Bpk + j * a.b_slice_bytes + ((long long)nt * a.kTiles + kt) * B_TILE;
+                    bulk_g2s(smem_u32(Bsm + (sb * T + j) * B_TILE), src, B_TILE, B_full(sb));
+                }
+            }
+        } else if (lane == 1) {
+            int u = 0;
+            for (int kt = kt_beg; kt < kt_end && !*abort_flag; ++kt) {
+                for (int i = 0; i < T; ++i, ++u) {
+                    const int sa = u % TF_ASLOTS;
+                    if (!mbar_wait(A_empty(sa), ((u / TF_ASLOTS) & 1) ^ 1, abort_flag)) break;
+                    mbar_expect_tx(A_full(sa), (uint32_t)A_TILE);
+                    const unsigned char *src = a.Apk + i * a.a_slice_bytes + ((long long)mt * a.kTiles + kt) * A_TILE;
+                    bulk_g2s(smem_u32(Asm + sa * A_TILE), src, A_TILE, A_full(sa));
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ------------------------------------------------ MMA issuer (one thread)
+        if (lane == 0) {
+            // kind::tf32: D = F32 (bits 4-5 = 1), A = B = TF32 (bits 7-9, 10-12 = 2), both
+            // K-major, N >> 3 at bit 17, M >> 4 at bit 24
+            const uint32_t idesc0 = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(SP_BM >> 4) << 24);
+            const uint64_t ad0 = sdesc_sw128(smem_u32(Asm)), bd0 = sdesc_sw128(smem_u32(Bsm));
+            int u = 0, b = 0;
+            for (int kt = kt_beg; kt < kt_end && !*abort_flag; ++kt, ++b) {
+                const int sb = b % SP_BSLOTS;
+                if (!mbar_wait(B_full(sb), (b / SP_BSLOTS) & 1, abort_flag)) break;
+                tc_fence_after();
+                const uint64_t bdb = bd0 + (uint64_t)((sb * T * B_TILE) >> 4);
+#pragma unroll
+                for (int i = 0; i < T; ++i, ++u) {
+                    const int sa = u % TF_ASLOTS;
+                    if (!mbar_wait(A_full(sa), (u / TF_ASLOTS) & 1, abort_flag)) break;
+                    tc_fence_after();
+                    const uint64_t ad = ad0 + (uint64_t)((sa * A_TILE) >> 4);
+                    // A_hi times [B_hi | B_lo] into levels 0 .. T-1; A_lo times B_hi into level 1
+                    const int n = (i == 0) ? T * NT : NT;
+                    const uint32_t idesc = idesc0 | ((uint32_t)(n >> 3) << 17);
+                    const uint32_t d = tmem + (uint32_t)(i * NT);
+#pragma unroll
+                    for (int kk = 0; kk < TF_BK / 8; ++kk)
+                        mma_tf32(d, ad + 2ull * kk, bdb + 2ull * kk, idesc, (kt == kt_beg && kk == 0 && i == 0) ? 0u : 1u);
+                    mma_commit(A_empty(sa));
+                }
+                mma_commit(B_empty(sb));
+            }
+            mma_commit(ACC_FULL);
+            mma_commit(DRAIN);
+            {
+                const unsigned long long t0 = global_ns();
+                while (!mbar_try(DRAIN, 0) && global_ns() - t0 < SP_WAIT_NS) {
+                }
+            }
+        }
+    } else {
+        // ------------------------------------------------ epilogue warps
+        const int sub = warp & 3;
+        const int part = (warp - 2) >> 2;
+        const uint32_t lane_base = (uint32_t)(32 * sub) << 16;
+        uint32_t v[QW];
+        int ok = 0;
+        if (lane == 0) ok = mbar_wait(ACC_FULL, 0, abort_flag) ? 1 : 0;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok) {
+            tc_fence_after();
+#pragma unroll
+            for (int g = 0; g < QW / 8; ++g) tmem_ld8(tmem + lane_base + (uint32_t)(part * QW + 8 * g), v + 8 * g);
+            tmem_wait_ld();
+            if (T == 2) {
+                uint32_t w[QW];
+#pragma unroll
+                for (int g = 0; g < QW / 8; ++g)
+                    tmem_ld8(tmem + lane_base + (uint32_t)(NT + part * QW + 8 * g), w + 8 * g);
+                tmem_wait_ld();
+#pragma unroll
+                for (int q = 0; q < QW; ++q) v[q] = __float_as_uint(__uint_as_float(v[q]) + __uint_as_float(w[q]));
+            }
+            tc_fence_before();
+        }
+        // stage the FP32 sums in the (now idle) operand ring, then write them out along the
+        // contiguous output index
+        constexpr int PITCH = NT + 1;
+        uint32_t *stage = reinterpret_cast<uint32_t *>(sm);
+        long long *row_off = reinterpret_cast<long long *>(sm + (((size_t)SP_BM * PITCH * 4 + 15) & ~(size_t)15));
+        long long *col_off = row_off + SP_BM;
+        int *row_sc = reinterpret_cast<int *>(col_off + NT);
+        int *col_sc = row_sc + SP_BM;
+        const int et = threadIdx.x - 64, ew = warp - 2;
+        const int m0 = mt * SP_BM, n0 = nt * NT;
+        const int rows = min(SP_BM, a.M - m0), cols = min(NT, a.N - n0);
+        const bool fin = a.ksplit == 1;
+        if (!*abort_flag) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const int r = 32 * sub + lane;
+            if (m0 + r < a.M) {
+                if (part == 0) {
+                    row_off[r] = fin ? off2(a.Cm, m0 + r) : (long long)(m0 + r) * a.N;
+                    row_sc[r] = exp_of_word(__ldg(a.eA + m0 + r));
+                }
+#pragma unroll
+                for (int q = 0; q < QW; ++q) {
+                    const int c = part * QW + q;
+                    if (n0 + c < a.N) stage[r * PITCH + c] = v[q];
+                }
+            }
+            for (int c = et; c < cols; c += 32 * TF_EPI_WARPS) {
+                col_off[c] = fin ? off2(a.Cn, n0 + c) : (long long)(n0 + c);
+                col_sc[c] = exp_of_word(__ldg(a.eB + n0 + c));
+            }
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * TF_EPI_WARPS) : "memory");
+        if (!*abort_flag) {
+            double *part_buf = reinterpret_cast<double *>(a.partial);
+            const bool along_n = !fin || a.Cn.s2 == 1 || a.Cm.s2 != 1;
+            if (along_n) {
+                for (int r = ew; r < rows; r += TF_EPI_WARPS) {
+                    const long long ro = row_off[r];
+                    const int rs = row_sc[r];
+                    for (int c = lane; c < cols; c += 32) {
+                        const double x = scaled_f32_to_double(stage[r * PITCH + c], rs + col_sc[c]);
+                        if (fin) a.C[ro + col_off[c]] = x;
+                        else atomicAdd(part_buf + ro + col_off[c], x);
+                    }
+                }
+            } else {
+                for (int c = ew; c < cols; c += TF_EPI_WARPS) {
+                    const long long co = col_off[c];
+                    const int cs = col_sc[c];
+                    for (int r = lane; r < rows; r += 32)
+                        a.C[row_off[r] + co] = scaled_f32_to_double(stage[r * PITCH + c], row_sc[r] + cs);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (abort_sh && threadIdx.x == 0)
+        for (int i = 0; i < 2000; ++i) __nanosleep(100);   // let bulk copies still in flight land
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+    if (threadIdx.x == 0 && abort_sh) atomicExch(a.err, 2);
+}
+
+// split-K: the FP64 partial sums (already scaled) to the output maps
+__global__ void tf32_finalize_kernel(int M, int N, const double *partial, double *C, Idx2 Cm, Idx2 Cn)
+{
+    const long long total = (long long)M * N;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int m = (int)(t / N), n = (int)(t - (long long)m * N);
+        C[off2(Cm, m) + off2(Cn, n)] = partial[t];
+    }
+}
+
+}  // namespace
+
+SplitPlan tf32_plan(int M, int N, int K, int T)
+{
+    SplitPlan p{};
+    p.NT = TF_NT;
+    p.deep = 0;
+    p.mTiles = (M + SP_BM - 1) / SP_BM;
+    p.nTiles = (N + TF_NT - 1) / TF_NT;
+    p.kTiles = (K + TF_BK - 1) / TF_BK;
+    const int chunks = (p.kTiles + TF_KT_PER_CHUNK - 1) / TF_KT_PER_CHUNK;
+    const long long tiles = (long long)p.mTiles * p.nTiles;
+    const int slots = 2 * device_sm_count();   // two CTAs per SM
+    int ks = 1;
+    if (tiles < slots && chunks > 1) ks = (int)((slots + tiles - 1) / tiles);
+    if (ks > chunks) ks = chunks;
+    p.chunks_per_split = (chunks + ks - 1) / ks;
+    p.ksplit = (chunks + p.chunks_per_split - 1) / p.chunks_per_split;
+    p.a_pack_bytes = (size_t)T * p.mTiles * p.kTiles * SP_BM * TF_BK * 4;
+    p.b_pack_bytes = (size_t)T * p.nTiles * p.kTiles * TF_NT * TF_BK * 4;
+    p.partial_bytes = p.ksplit > 1 ? (size_t)M * N * 8 : 0;
+    return p;
+}
+
+SplitPlan tf32_plan_caps(int M, int N, int K, int T) { return tf32_plan(M, N, K, T); }
+
+int tf32_supported_T(int T) { return T == 1 || T == 2; }
+
+cudaError_t tf32_prepare()
+{
+    cudaError_t e = cudaFuncSetAttribute(gemm_tf32_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tf32_smem_bytes(1));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(gemm_tf32_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tf32_smem_bytes(2));
+    return e;
+}
+
+// exponents of the rows of X(r, k) (the largest high word of |X| along k)
+static cudaError_t tf32_exponents(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int *e, cudaStream_t st)
+{
+    if (rmap.s1 == 0 && rmap.s2 == 1 && kmap.s1 == 0 && kmap.s2 != 1) {
+        cudaError_t e0 = cudaMemsetAsync(e, 0, sizeof(int) * (size_t)R, st);
+        if (e0 != cudaSuccess) return e0;
+        CTM_COUNT_LAUNCH(1);
+        split_colexp_kernel<<<dim3((R + 127) / 128, (K + SP_COLEXP_K - 1) / SP_COLEXP_K), 128, 0, st>>>(R, K, X,
+                                                                                                       kmap.s2, e);
+        return cudaGetLastError();
+    }
+    CTM_COUNT_LAUNCH(1);
+    split_rowexp_kernel<<<(R * 32 + 255) / 256, 256, 0, st>>>(R, K, X, rmap, kmap, e);
+    return cudaGetLastError();
+}
+
+static cudaError_t tf32_pack(int R, int K, const double *X, Idx2 rmap, Idx2 kmap, int rowsT, int rowTiles, int kTiles,
+                             int T, const int *e, unsigned char *out, cudaStream_t st)
+{
+    const int rowsTotal = rowTiles * rowsT;
+    const long long slice_bytes = (long long)rowsTotal * kTiles * TF_BK * 4;
+    const long long total = (long long)rowsTotal * kTiles * TF_BK;
+    long long blocks = (total + 255) / 256, cap = 32LL * device_sm_count();
+    if (blocks > cap) blocks = cap;
+    const int rfast = (rmap.s1 == 0 && rmap.s2 == 1 && !(kmap.s1 == 0 && kmap.s2 == 1)) ? 1 : 0;
+    CTM_COUNT_LAUNCH(1);
+    if (T == 1)
+        tf32_pack_kernel<1><<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowsTotal, kTiles, X, rmap, kmap, e, rfast, out,
+                                                         slice_bytes);
+    else
+        tf32_pack_kernel<2><<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowsTotal, kTiles, X, rmap, kmap, e, rfast, out,
+                                                         slice_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t gemm_tf32(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cudaEvent_t *ev)
+{
+    if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+    if (!tf32_supported_T(T) || g.alpha != 1.0 || g.beta != 0.0) return cudaErrorInvalidValue;
+    const SplitPlan p = tf32_plan(g.M, g.N, g.K, T);
+    if (p.a_pack_bytes > w.a_pack_cap || p.b_pack_bytes > w.b_pack_cap || p.partial_bytes > w.partial_cap ||
+        g.M > w.e_cap || g.N > w.e_cap)
+        return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (ev) cudaEventRecord(ev[2], st);
+    if ((e = tf32_exponents(g.M, g.K, g.A, g.Am, g.Ak, w.eA, st)) != cudaSuccess) return e;
+    if ((e = tf32_pack(g.M, g.K, g.A, g.Am, g.Ak, SP_BM, p.mTiles, p.kTiles, T, w.eA, w.Apk, st)) != cudaSuccess)
+        return e;
+    if ((e = tf32_exponents(g.N, g.K, g.B, g.Bn, g.Bk, w.eB, st)) != cudaSuccess) return e;
+    if ((e = tf32_pack(g.N, g.K, g.B, g.Bn, g.Bk, TF_NT, p.nTiles, p.kTiles, T, w.eB, w.Bpk, st)) != cudaSuccess)
+        return e;
+    if (p.ksplit > 1 && (e = cudaMemsetAsync(w.partial, 0, p.partial_bytes, st)) != cudaSuccess) return e;
+    SplitArgs a{g.M,
+                g.N,
+                g.K,
+                T,
+                p.mTiles,
+                p.nTiles,
+                p.kTiles,
+                p.chunks_per_split,
+                p.ksplit,
+                w.Apk,
+                w.Bpk,
+                (long long)p.mTiles * p.kTiles * SP_BM * TF_BK * 4,
+                (long long)p.nTiles * p.kTiles * TF_NT * TF_BK * 4,
+                w.eA,
+                w.eB,
+                g.C,
+                g.Cm,
+                g.Cn,
+                (unsigned long long *)w.partial,
+                w.err};
+    dim3 grid(p.nTiles, p.mTiles, p.ksplit);
+    if (ev) cudaEventRecord(ev[0], st);
+    CTM_COUNT_LAUNCH(1);
+    if (T == 1) gemm_tf32_kernel<1><<<grid, TF_THREADS, tf32_smem_bytes(1), st>>>(a);
+    else gemm_tf32_kernel<2><<<grid, TF_THREADS, tf32_smem_bytes(2), st>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[1], st);
+    if (p.ksplit > 1) {
+        const long long total = (long long)g.M * g.N;
+        long long blocks = (total + 255) / 256, cap = 16LL * device_sm_count();
+        if (blocks > cap) blocks = cap;
+        CTM_COUNT_LAUNCH(1);
+        tf32_finalize_kernel<<<(int)blocks, 256, 0, st>>>(g.M, g.N, (const double *)w.partial, g.C, g.Cm, g.Cn);
+        e = cudaGetLastError();
+    }
+    return e;
+}
