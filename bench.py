@@ -551,7 +551,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="kh_D6_chi72")
-    ap.add_argument("--precision", default="split_bf16", choices=["fp64", "split_bf16"])
+    ap.add_argument("--precision", default="split_bf16", choices=["fp64", "split_bf16", "split_tf32", "fp32_tf32"])
     ap.add_argument("--n-split", type=int, default=5)
     ap.add_argument("--no-compare", action="store_true", help="skip the FP64/oracle/convergence sub-records")
     ap.add_argument("--no-extras", action="store_true", help="skip the D=8 and batch96 sub-records")
@@ -643,6 +643,21 @@ def main():
                     "kernel": "gemm_f64_kernel (+ split-K reduce): the step's 11 FP64 contractions",
                     "peak_source": "measured live: DFMA throughput probe (ctm_probe_fp64_peak); GB300 has no "
                                    "FP64 tcgen05 kind, so the DFMA pipe is the FP64 ceiling"}
+    elif args.precision in ("split_tf32", "fp32_tf32"):
+        # TF32 products on the tensor pipe: 3 (A_hi B_hi + A_hi B_lo + A_lo B_hi) or 1 per
+        # contraction; the TF32 peak is the measured BF16 burst times the nominal dense ratio
+        # 1.1 / 2.25 PFLOP/s
+        prods = 3 if args.precision == "split_tf32" else 1
+        peak = peaks["bf16_tflops"] * 1.1 / 2.25
+        achieved = prods * flops / (kern_ms / 1e3) / 1e12
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                    "traffic": None,
+                    "kernel": f"gemm_tf32_kernel: {prods} TF32 products per contraction, tcgen05 kind::tf32 into TMEM",
+                    "peak_source": f"{src} bf16 burst x 1.1/2.25 (nominal TF32/BF16 dense ratio)",
+                    "fp64_equivalent_tflops": flops / (kern_ms / 1e3) / 1e12,
+                    "with_prepass": {"ms_per_step": kern_ms + prepass_ms,
+                                     "achieved": prods * flops / ((kern_ms + prepass_ms) / 1e3) / 1e12,
+                                     "frac": prods * flops / ((kern_ms + prepass_ms) / 1e3) / 1e12 / peak}}
     else:
         T = args.n_split
         pairs = T * (T + 1) // 2
@@ -670,7 +685,9 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": "steps/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else f"bf16x{args.n_split}-split+f64",
+        "vs_baseline": None,
+        "dtype": {"fp64": "f64", "split_tf32": "tf32x3-split+f64", "fp32_tf32": "tf32+f64"}.get(
+            args.precision, f"bf16x{args.n_split}-split+f64"),
         "data": "synthetic (seeded uniform[-1,1] site tensor, C3v-projected)",
         "config": {"workload": w.name, "d": w.d, "D": w.D, "chi": w.chi, "n": w.n,
                    "precision": args.precision, "n_split": args.n_split if args.precision != "fp64" else None,

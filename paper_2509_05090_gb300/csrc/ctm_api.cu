@@ -176,8 +176,16 @@ size_t layout(ctm_ctx *c, char *base)
         c->sw.partial_cap = pp;
         c->sw.err = c->err;
         c->sw.autotune = 0;
+        // the corner update (lane2) and the edge update run concurrently after the first
+        // step: the corner lane gets its own B pack, exponents and split-K buffer, the
+        // edge lane its own A pack and exponents
         c->sw_c = c->sw;
+        c->sw_c.Bpk = (unsigned char *)take(bp);
+        c->sw_c.eB = (int *)take(sizeof(int) * (size_t)ecap);
+        c->sw_c.partial = (void *)take(pp + 8);
         c->sw_e = c->sw;
+        c->sw_e.Apk = (unsigned char *)take(ap);
+        c->sw_e.eA = (int *)take(sizeof(int) * (size_t)ecap);
     }
     if (c->split_T > 0) {
         // packed digit slices, exponents and the split-K integer accumulator for the
@@ -266,8 +274,8 @@ cudaError_t run_gemm(ctm_ctx *c, const GemmF64 &g, int hint, int lane)
         c->prof_n += 3;
     }
     if (c->tf32_T > 0) {
-        cudaError_t e = gemm_tf32(g, c->tf32_T, c->sw, c->stream, ev);
-        return e;
+        const SplitWork &w = lane == 1 ? c->sw_c : (lane == 2 ? c->sw_e : c->sw);
+        return gemm_tf32(g, c->tf32_T, w, lane == 1 ? c->lane2 : c->stream, ev);
     }
     if (c->split_T > 0) {
         SplitOpts o{};
@@ -428,7 +436,7 @@ int enqueue_step(ctm_ctx *c)
     // Split mode after the first step (whose eager contractions time their plans
     // one at a time): the corner and edge updates both need only Q, so the corner
     // update runs on lane2 beside the edge update.
-    if (c->split_T > 0 && c->steps_done > 0 && c->cfg.corner_mode == 0) {
+    if ((c->split_T > 0 || c->tf32_T > 0) && c->steps_done > 0 && c->cfg.corner_mode == 0) {
         CK(cudaEventRecord(c->ev_q, st));
         CK(cudaStreamWaitEvent(c->lane2, c->ev_q, 0));
         // the previous step's spectrum (reading C or Cspec) is done before Cspec is rewritten

@@ -1349,30 +1349,39 @@ __device__ __forceinline__ double scaled_f32_to_double(uint32_t b, int scale)
     return __hiloint2double((int)(sgn | ((uint32_t)be << 20) | (m >> 3)), (int)(m << 29));
 }
 
-// Operand pre-pass: one thread per element of the padded tile grid (rows x kTiles*32),
-// along the rows when they are the contiguous index, else along K.
+// Operand pre-pass: one block per 32 rows x one 32-wide K tile.  The loads run along
+// whichever index of X is contiguous (rfast: the rows), the hi/lo words are staged in
+// shared memory, and one warp stores each row's 128 bytes (its 16-byte chunks permuted
+// within the row as the swizzle asks).  Rows from R up to the padded tile grid get zeros.
 template <int T>
-__global__ void tf32_pack_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles, const double *X, Idx2 rmap,
-                                 Idx2 kmap, const int *e, int rfast, unsigned char *out, long long slice_bytes)
+__global__ void __launch_bounds__(256) tf32_pack_kernel(int R, int K, int rowsT, int rowsTotal, int kTiles,
+                                                        const double *X, Idx2 rmap, Idx2 kmap, const int *e, int rfast,
+                                                        unsigned char *out, long long slice_bytes)
 {
-    const long long KT = (long long)kTiles * TF_BK;
-    const long long total = (long long)rowsTotal * KT;
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
-        int gr, gk;
-        if (rfast) {
-            gr = (int)(t % rowsTotal);
-            gk = (int)(t / rowsTotal);
-        } else {
-            gk = (int)(t % KT);
-            gr = (int)(t / KT);
-        }
+    __shared__ uint32_t Hs[32][33], Ls[32][33];
+    __shared__ int Es[32];
+    const int r0 = blockIdx.x * 32, kt = blockIdx.y;
+    const int tid = threadIdx.x;
+    if (tid < 32) Es[tid] = (r0 + tid < R) ? exp_of_word(e[r0 + tid]) : 0;
+    __syncthreads();
+    for (int q = tid; q < 32 * TF_BK; q += 256) {
+        const int i = rfast ? (q & 31) : (q >> 5);
+        const int j = rfast ? (q >> 5) : (q & 31);
+        const int gr = r0 + i, gk = kt * TF_BK + j;
         uint32_t hi = 0u, lo = 0u;
-        if (gr < R && gk < K) tf32_split(X[off2(rmap, gr) + off2(kmap, gk)], exp_of_word(e[gr]), hi, lo);
-        const long long tile = (long long)(gr / rowsT) * kTiles + gk / TF_BK;
-        unsigned char *dst = out + tile * ((long long)rowsT * TF_BK * 4) + sw128_off32(gr % rowsT, gk % TF_BK);
-        *(uint32_t *)dst = hi;
-        if (T == 2) *(uint32_t *)(dst + slice_bytes) = lo;
+        if (gr < R && gk < K) tf32_split(X[off2(rmap, gr) + off2(kmap, gk)], Es[i], hi, lo);
+        Hs[i][j] = hi;
+        Ls[i][j] = lo;
+    }
+    __syncthreads();
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int i = warp; i < 32; i += 8) {
+        const int gr = r0 + i;
+        if (gr >= rowsTotal) break;
+        const long long tile = (long long)(gr / rowsT) * kTiles + kt;
+        unsigned char *dst = out + tile * ((long long)rowsT * TF_BK * 4) + sw128_off32(gr % rowsT, lane);
+        *(uint32_t *)dst = Hs[i][lane];
+        if (T == 2) *(uint32_t *)(dst + slice_bytes) = Ls[i][lane];
     }
 }
 
@@ -1673,17 +1682,15 @@ static cudaError_t tf32_pack(int R, int K, const double *X, Idx2 rmap, Idx2 kmap
 {
     const int rowsTotal = rowTiles * rowsT;
     const long long slice_bytes = (long long)rowsTotal * kTiles * TF_BK * 4;
-    const long long total = (long long)rowsTotal * kTiles * TF_BK;
-    long long blocks = (total + 255) / 256, cap = 32LL * device_sm_count();
-    if (blocks > cap) blocks = cap;
     const int rfast = (rmap.s1 == 0 && rmap.s2 == 1 && !(kmap.s1 == 0 && kmap.s2 == 1)) ? 1 : 0;
+    const dim3 grid((rowsTotal + 31) / 32, kTiles);
     CTM_COUNT_LAUNCH(1);
     if (T == 1)
-        tf32_pack_kernel<1><<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowsTotal, kTiles, X, rmap, kmap, e, rfast, out,
-                                                         slice_bytes);
+        tf32_pack_kernel<1><<<grid, 256, 0, st>>>(R, K, rowsT, rowsTotal, kTiles, X, rmap, kmap, e, rfast, out,
+                                                  slice_bytes);
     else
-        tf32_pack_kernel<2><<<(int)blocks, 256, 0, st>>>(R, K, rowsT, rowsTotal, kTiles, X, rmap, kmap, e, rfast, out,
-                                                         slice_bytes);
+        tf32_pack_kernel<2><<<grid, 256, 0, st>>>(R, K, rowsT, rowsTotal, kTiles, X, rmap, kmap, e, rfast, out,
+                                                  slice_bytes);
     return cudaGetLastError();
 }
 
