@@ -29,10 +29,11 @@ struct ctm_complex_ctx {
     int d, D, D2, chi;
     long long n;
     int split_T;
+    int tf32_T;   // 1, 2: TF32 products (CTM_FP32_TF32, CTM_SPLIT_TF32)
     cudaStream_t stream;
     double U[3][3][2];      // the rotation paired with the leg cycle (energies of the x, y bonds)
     // planes: P_* is the plane stride of each tensor (elements)
-    double *Ain, *A, *a, *bB, *bA;
+    double *Ain, *A, *a, *aA, *bB, *bA;   // a: the outer site's layer; aA: the apex site's (z leg first)
     long long PA, Pa, Pb;
     double *C, *Cn, *Cr, *T, *Tn, *Q, *Qn, *Qs;
     long long PC, PT, PQ;
@@ -423,14 +424,14 @@ __device__ __forceinline__ void zc_layer_entry(int D, long long t, int rot, int 
     }
 }
 
-__global__ void zc_double_layer_kernel(int d, int D, const double *A, long long PA, double *a)
+__global__ void zc_double_layer_kernel(int d, int D, const double *A, long long PA, int rot, double *a)
 {
     const long long D6 = (long long)D * D * D * D * D * D;
     const int D3 = D * D * D;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < D6;
          t += (long long)gridDim.x * blockDim.x) {
         int ki, bi;
-        zc_layer_entry(D, t, 0, ki, bi);
+        zc_layer_entry(D, t, rot, ki, bi);
         double re = 0.0, im = 0.0;
         for (int s = 0; s < d; ++s) {
             const double kr = A[s * D3 + ki], kim = A[PA + s * D3 + ki];
@@ -815,6 +816,7 @@ struct ZGemm {
 
 int real_gemm(ctm_complex_ctx *c, const GemmF64 &g, int reuse_a)
 {
+    if (c->tf32_T > 0) return gemm_tf32(g, c->tf32_T, c->sw, c->stream, nullptr) == cudaSuccess ? CTM_OK : CTM_ECUDA;
     if (c->split_T > 0) {
         SplitOpts o{};
         o.reuse_a = reuse_a;
@@ -903,6 +905,7 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->A = td(2 * c->PA);
     c->Pa = D3;
     c->a = td(5 * D3);
+    c->aA = td(5 * D3);
     c->Pb = dd * D3;
     c->bB = td(5 * c->Pb);
     c->bA = td(5 * c->Pb);
@@ -958,11 +961,12 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->rho_raw = td(2 * dd * dd);
     c->hrot = td(3 * 2 * dd * dd);
     c->eout = td(4 + 2 * dd * dd);
-    if (c->split_T > 0) {
+    if (c->split_T > 0 || c->tf32_T > 0) {
         size_t ap = 0, bp = 0, pp = 0;
         long long ecap = 0;
         for (const auto &sh : zshapes(c)) {
-            SplitPlan pl = split_plan_caps(sh[0], sh[1], sh[2], c->split_T);
+            SplitPlan pl = c->tf32_T > 0 ? tf32_plan_caps(sh[0], sh[1], sh[2], c->tf32_T)
+                                         : split_plan_caps(sh[0], sh[1], sh[2], c->split_T);
             if (pl.a_pack_bytes > ap) ap = pl.a_pack_bytes;
             if (pl.b_pack_bytes > bp) bp = pl.b_pack_bytes;
             if (pl.partial_bytes > pp) pp = pl.partial_bytes;
@@ -992,7 +996,9 @@ bool zconfig_ok(const ctm_config *cfg, int irrep)
     if (irrep == CTM_IRREP_E && cfg->d < 2) return false;
     if (cfg->D < 1 || cfg->D > 10) return false;
     if (cfg->chi < 1 || cfg->chi > 80) return false;
-    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16) return false;
+    if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16 && cfg->precision != CTM_SPLIT_TF32 &&
+        cfg->precision != CTM_FP32_TF32)
+        return false;
     if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
     if (cfg->corner_mode != 0) return false;
     const long long n = (long long)cfg->chi * cfg->D * cfg->D;
@@ -1009,14 +1015,15 @@ int zread_status(ctm_complex_ctx *c)
 }
 
 // ------------------------------------------------------------------ the step
-// Layouts of the step's tensors (ZLay): a, C, Q, Qs five planes stacked; T five planes
+// Layouts of the step's tensors (ZLay): a, aA, C, Q, Qs five planes stacked; T five planes
 // row-blocked by its rows (a, u); W [(a,u)][2][h], X [(a,b)][2][(u,l)], Y1 [(a,b)][2][z] and
 // M [(a,y)][2][(b,x)] two planes row-blocked (k contiguous for the next contraction); Y, MQ,
 // Cr and H two planes stacked (k slowest for the next contraction).
 ZLay lay_T(const ctm_complex_ctx *c) { return zlay_rows(c->chi, 5); }
 
 // Fig. 3c: W = T C; X'[a][b][u][l] = sum_h W[(a,u),h] conj(T[(b,l),h]);
-// Y1[(a,b)][z] = sum_{u,l} X' a[u,l,z]; M[(a,y)][(b,x)] = sum_z Y1 a[z,x,y]
+// Y1[(a,b)][z] = sum_{u,l} X' a[u,l,z]; M[(a,y)][(b,x)] = sum_z Y1 aA[z,x,y], with aA the double
+// layer of the apex site (z leg first; equal to a for a C3-symmetric tensor)
 int zenlarged_corner(ctm_complex_ctx *c)
 {
     const int chi = c->chi, D2 = c->D2;
@@ -1031,7 +1038,7 @@ int zenlarged_corner(ctm_complex_ctx *c)
     z = ZGemm{chi * chi, D2, D2 * D2, c->X, DD, 0, idx_lin(2 * DD), idx_lin(1), 0, c->a, c->Pa, idx_lin(D2),
               idx_lin(1), 0, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
-    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->a, c->Pa, idx_lin(DD),
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->aA, c->Pa, idx_lin(DD),
               idx_split(D2, 1, D2), 0, c->M, n, 0, idx_split(chi, 2LL * D2 * n, D2), idx_split(D2, 2 * n, 1)};
     return zgemm(c, z);
 }
@@ -1070,7 +1077,7 @@ int zcorner(ctm_complex_ctx *c, double *Cout)
     return CTM_OK;
 }
 
-// Fig. 3b: T'[i,x,j] = sum conj(Q[(a,y),i]) T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j], normalised
+// Fig. 3b: T'[i,x,j] = sum conj(Q[(a,y),i]) T[a,u,g] a[u,w,z] aA[z,x,y] Q[(g,w),j], normalised
 int zedge(ctm_complex_ctx *c)
 {
     const int chi = c->chi, D2 = c->D2;
@@ -1086,7 +1093,7 @@ int zedge(ctm_complex_ctx *c)
               idx_lin(1), 0, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
     // H3'[a][y][x][j] = H2[(a,j),z] a[z,x,y]
-    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->a, c->Pa, idx_lin(DD),
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->aA, c->Pa, idx_lin(DD),
               idx_split(D2, 1, D2), 0, c->H, c->PM, 0, idx_split(chi, DD * chi, 1),
               idx_split(D2, (long long)D2 * chi, chi)};
     if ((rc = zgemm(c, z)) != CTM_OK) return rc;
@@ -1170,6 +1177,7 @@ size_t ctm_complex_workspace_bytes(const ctm_config *cfg, int irrep)
     c.chi = cfg->chi;
     c.n = (long long)c.chi * c.D2;
     c.split_T = cfg->precision == CTM_SPLIT_BF16 ? cfg->n_split : 0;
+    c.tf32_T = cfg->precision == CTM_SPLIT_TF32 ? 2 : (cfg->precision == CTM_FP32_TF32 ? 1 : 0);
     return zlayout(&c, nullptr);
 }
 
@@ -1192,6 +1200,7 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
     c->chi = cfg->chi;
     c->n = (long long)c->chi * c->D2;
     c->split_T = cfg->precision == CTM_SPLIT_BF16 ? cfg->n_split : 0;
+    c->tf32_T = cfg->precision == CTM_SPLIT_TF32 ? 2 : (cfg->precision == CTM_FP32_TF32 ? 1 : 0);
     c->stream = (cudaStream_t)stream;
     if (ws_bytes < zlayout(c, nullptr)) {
         delete c;
@@ -1212,6 +1221,7 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
     int rc = CTM_OK;
     do {
         if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess ||
+            tf32_prepare() != cudaSuccess ||
             cudaFuncSetAttribute(zc_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)ztridiag_smem_bytes(80)) != cudaSuccess) {
             rc = CTM_ECUDA;
@@ -1230,14 +1240,15 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         }
         const long long cnt = c->PA;
         if (cudaMemsetAsync(c->err, 0, sizeof(int), c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }
-        CTM_COUNT_LAUNCH(4);
+        CTM_COUNT_LAUNCH(5);
         zc_load_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(cnt, A_dev, c->Ain, zlay_stacked(cnt, 2));
         zc_project_kernel<<<zgrid(cnt), 256, 0, c->stream>>>(c->d, c->D, c->Ain, cnt, grp, cfg->symmetrize ? 1 : 0,
                                                              c->A, cnt);
         if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
         if ((rc = znormalize(c, cnt, c->A, zlay_stacked(cnt, 2))) != CTM_OK) break;
         const long long D6 = c->Pa;
-        zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, c->a);
+        zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, 0, c->a);
+        zc_double_layer_kernel<<<zgrid(D6), 256, 0, c->stream>>>(c->d, c->D, c->A, cnt, 1, c->aA);
         zc_init_env_kernel<<<zgrid(c->PT), 256, 0, c->stream>>>(c->chi, c->D, c->a, c->Pa, c->C, c->T, c->Q);
         if (cudaGetLastError() != cudaSuccess) { rc = CTM_ECUDA; break; }
         if (launch_spectrum_init(c->chi, c->s, c->stream) != cudaSuccess) { rc = CTM_ECUDA; break; }

@@ -229,3 +229,65 @@ def test_complex_rejects_bad_config(ctm_lib):
         binding.CTMComplex(A, 81)                       # chi above the embedded QR's limit
     with pytest.raises(binding.CtmError):
         binding.CTMComplex(A[:1], 4)                    # d = 1 has no E irrep
+
+
+def test_complex_graph_replay_equals_eager(ctm_lib):
+    """Steps replayed from captured graphs (one-step and multi-step) follow the eager steps;
+    the QR's FP64 atomics leave differences at rounding level only."""
+    A = I.random_complex_site_tensor(2, 3, 101)
+    g1, g2 = _ctm(A, 12), _ctm(A, 12)
+    for _ in range(7):
+        g1.ctm_complex_step(1)          # eager first, then the one-step graph
+    g2.ctm_complex_step(1)
+    g2.ctm_complex_step(6)              # one six-step graph
+    for x, y in zip(g1.ctm_complex_get_env(), g2.ctm_complex_get_env()):
+        assert np.abs(_np(x) - _np(y)).max() < 1e-11
+    z = Z.ComplexCTM(A, 12)
+    for _ in range(7):
+        z.step()
+    assert np.abs(_np(g1.ctm_complex_get_intermediate("C")) - z.C).max() < 1e-9
+
+
+def test_complex_env_round_trip(ctm_lib):
+    A = I.random_complex_site_tensor(2, 2, 102)
+    g = _ctm(A, 8)
+    g.ctm_complex_step(3)
+    C, T, Q = g.ctm_complex_get_env()
+    g.ctm_complex_set_env(C, T, Q)
+    C2, T2, Q2 = g.ctm_complex_get_env()
+    for x, y in ((C, C2), (T, T2), (Q, Q2)):
+        assert np.array_equal(_np(x), _np(y))
+
+
+def test_complex_unsymmetrised_tensor_follows_oracle(ctm_lib):
+    """Without the projection M is not Hermitian; the step is the same formula on both sides."""
+    from paper_2509_05090_gb300 import binding
+    A = I.random_complex_site_tensor(2, 2, 103)
+    g = binding.CTMComplex(A, 8, precision="fp64", symmetrize=False)
+    z = Z.ComplexCTM(A, 8, symmetrize=False)
+    assert np.abs(_np(g.ctm_complex_get_intermediate("A")) - z.A).max() < 1e-15
+    for k in range(3):
+        if k > 0:
+            g.ctm_complex_set_env(z.C, z.T, z.Q)
+        g.ctm_complex_step()
+        z.step()
+        M = _np(g.ctm_complex_get_intermediate("M"))
+        assert np.abs(M - z.last["M"]).max() < 1e-13 * np.abs(z.last["M"]).max()
+    g.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("split_tf32", 2e-6), ("fp32_tf32", 2e-4)])
+def test_complex_tf32_energy(ctm_lib, prec, tol):
+    """The TF32 engines under the complex path (their accuracy as in test_gpu_tf32.py)."""
+    v = I.coherent_state(2, (1.0, 1.0, 1.0))
+    A = I.complex_perturbed_product_site_tensor(v, 2, 0.2, 83)
+    g = _ctm(A, 8, precision=prec)
+    z = Z.ComplexCTM(A, 8)
+    g.ctm_complex_converge(60, 1e-6 if prec == "split_tf32" else 1e-3)
+    z.converge(60, 1e-10)
+    h = _kh(2, -1.0, 0.3)
+    _, E, _ = g.ctm_complex_energy(h)
+    _, Ez = z.energy(list(h))
+    print(prec, E, Ez, abs(E - Ez))
+    assert abs(E - Ez) < tol, (E, Ez)
+    g.close()
