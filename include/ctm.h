@@ -309,6 +309,8 @@ void ctm_batch_destroy(ctm_batch *batch);
  *    Y = Q R with diag(R) real and >= 0, C' = sym(Q^H M Q)/|.| (Hermitian part),
  *    T'[i,x,j] = sum conj(Q[(a,y),i]) T[a,u,g] a[u,w,z] a[z,x,y] Q[(g,w),j] /|.|,
  *    and delta from the eigenvalue magnitudes of C'.
+ *  - Precisions as for ctm_init (FP64, split BF16, split TF32, one TF32 product):
+ *    every real product of a complex contraction runs on the chosen engine.
  *  - Limits: chi <= 80, n = chi D^2 <= 12000, D <= 10, corner_mode 0.
  *  - The caller owns the workspace (ctm_complex_workspace_bytes), as for ctm_init.
  *    Errors as for the real calls. */
