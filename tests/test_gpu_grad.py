@@ -140,6 +140,25 @@ def test_adjoint_k30_matches_cpu_reference(ctm_lib, precision):
     assert np.max(np.abs(g_gpu - g_ref)) <= 1e-7 * np.max(np.abs(g_ref))
 
 
+@pytest.mark.parametrize("name,k", [("kitaev_D4_chi32_conv", 30), ("heis_D2_chi8", 10)])
+def test_adjoint_tf32_forward(ctm_lib, name, k):
+    """The FP32/TF32 forward with the FP64 QR: k tracked steps whose contractions are split-TF32
+    products (about FP32 accuracy: (3 2^-21 + K 2^-23) relative, ~7e-5 at K = n = 512), the
+    adjoint in FP64 from their checkpoints, against the float64 reference gradient through the
+    same steps.  The forward's error carries into the energy and the gradient at most at that
+    level (the near-product state hides most of it: its errors fall in the dominant direction
+    that the normalisations remove; the random heis_D2_chi8 state shows it)."""
+    import torch_reference as TR
+    w = I.WORKLOADS[name]
+    A, h = w.site_tensor(), _zz_bonds()
+    E_gpu, g_gpu = _gpu_grad(A, w.chi, h, 3, k, "split_tf32")
+    env = _oracle_env_after(A, w.chi, 3)
+    E_ref, g_ref = TR.energy_and_grad(A, env, h, k)
+    print(name, "tf32 forward: dE", abs(E_gpu - E_ref), "dg", np.max(np.abs(g_gpu - g_ref)) / np.max(np.abs(g_ref)))
+    assert abs(E_gpu - E_ref) <= 1e-6                                   # measured 4e-9 (heis), 1e-13
+    assert np.max(np.abs(g_gpu - g_ref)) <= 1e-4 * np.max(np.abs(g_ref))   # measured 2e-8, 5e-11
+
+
 def test_adjoint_d8_chi128_k30_split_forward(ctm_lib):
     """D = 8, chi = 128 (enlarged corner 8192 x 8192), converging near-product state: 3
     warm-up and 30 checkpointed steps in split-BF16 with the FP64 QR, the adjoint in
