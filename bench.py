@@ -236,18 +236,18 @@ def batch_record(args, steps):
     chis = [w.chi for w in wl]
     t_init = time.perf_counter()
     batch = binding.CTMBatch(tensors, chis, precision=args.precision, n_split=args.n_split)
-    l_warm = binding.ctm_kernel_launches()
-    batch.ctm_batch_step(2)   # eager (autotuning) step + capture: each enqueues one batched step
+    batch.ctm_batch_step(2)   # eager (autotuning) step, then the captured graph's first replay
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t_init
-    kernels_per_step = (binding.ctm_kernel_launches() - l_warm) // 2
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l_timed = binding.ctm_kernel_launches()
     with ClockSampler(torch.cuda.current_device()) as clk:
         e0.record(batch.stream)
         batch.ctm_batch_step(steps)
         e1.record(batch.stream)
         torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    kernels_per_step = (binding.ctm_kernel_launches() - l_timed) // steps   # kernels of one replay
     value = len(wl) * steps / (ms / 1e3)
     flops = sum(step_gemm_flops(w.chi, w.D2) for w in wl)
     T = args.n_split
@@ -766,22 +766,37 @@ def main():
         A_dev = A_host.to("cuda", non_blocking=True)
         h_dev = h_host.to("cuda", non_blocking=True)
         e2e = binding.CTM(A_dev, w.chi, precision=args.precision, n_split=args.n_split)
-        deltas = []
-        for _ in range(args.steps):
-            deltas.append(e2e.ctm_step(1, want_delta=True))   # delta read back every step
+        # ctm_converge with every step's delta read back (check_every = 1; a tol no
+        # delta reaches, so exactly K steps)
+        nst, _, _ = e2e.ctm_converge(max_steps=args.steps, tol=1e-300, check_every=1)
         eb, es, rho = e2e.ctm_energy(h_dev)
         torch.cuda.synchronize()
         t_e2e = time.perf_counter() - t0
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
+        e2e.close()
+        assert nst == args.steps
+        # the same through K single-step calls (each returns its delta)
+        t1 = time.perf_counter()
+        A_dev = A_host.to("cuda", non_blocking=True)
+        h_dev = h_host.to("cuda", non_blocking=True)
+        e2s = binding.CTM(A_dev, w.chi, precision=args.precision, n_split=args.n_split)
+        for _ in range(args.steps):
+            e2s.ctm_step(1, want_delta=True)
+        e2s.ctm_energy(h_dev)
+        torch.cuda.synchronize()
+        t_calls = time.perf_counter() - t1
+        e2s.close()
+        tt = torch.tensor([t_e2e, t_calls], dtype=torch.float64, device="cuda")
         if ws > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+        t_e2e, t_calls = (float(x) for x in tt.tolist())
         line["e2e"] = {"value": ws * args.steps / t_e2e, "unit": "steps/s",
                        "h2d_bytes_per_step": (A_host.numel() * 8 + h_host.numel() * 8) / args.steps,
                        "d2h_bytes_per_step": 8 + (4 + rho.size) * 8 / args.steps,
-                       "what": "H2D of the site tensor and bond operators, ctm_init, K steps with delta read "
-                               "back each step, ctm_energy read back", "E_site": es}
-        e2e.close()
+                       "what": "H2D of the site tensor and bond operators, ctm_init, ctm_converge over K steps "
+                               "with every step's delta read back (check_every 1), ctm_energy read back",
+                       "E_site": es,
+                       "single_step_calls": {"value": ws * args.steps / t_calls, "unit": "steps/s",
+                                             "what": "the same with K ctm_step(1) calls, each returning its delta"}}
 
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, nsteps, secs, _, _ = cpu_oracle_rate(w, budget_s=10.0, max_steps=4, threads=1)

@@ -116,9 +116,18 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
 int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
 
 /* Sec. II.B: repeat steps until delta < tol (tol <= 0: cfg->tol) or max_steps
- * (<= 0: cfg->max_steps).  Steps are replayed from a captured CUDA graph;
- * delta is read back every check_every steps (>= 1).  Synchronous.  Returns
- * CTM_ENOTCONVERGED (outputs filled) if the limit was hit. */
+ * (<= 0: cfg->max_steps).  A fresh context's first step runs eagerly; then
+ * chunks of check_every (>= 1) steps are replayed from two captured CUDA graphs
+ * that copy every step's delta into pinned host memory.  Each chunk's last
+ * corner spectrum runs at the head of the next chunk (beside its steps), and
+ * while the newest delta is above 100 tol a second chunk is queued behind the
+ * one the host is reading; so the host learns a step's delta one chunk late,
+ * and up to one chunk (two far from tol) more steps run after the first chunk
+ * whose newest delta is below tol.  The run ends with the last step's own
+ * spectrum: *delta_out is the delta of the last executed step, *steps_out the
+ * number of steps this call ran (at most max_steps; fewer than check_every
+ * left run one at a time).  Synchronous.  Returns CTM_ENOTCONVERGED (outputs
+ * filled) if the limit was hit with delta >= tol. */
 int ctm_converge(ctm_ctx *ctx, int max_steps, double tol, int check_every,
                  int *steps_out, double *delta_out);
 

@@ -431,6 +431,19 @@ int enqueue_step(ctm_ctx *c)
     int rc;
     cudaStream_t st = c->stream;
     const long long chi = c->chi, D2 = c->D2, n = c->n;
+    if (c->spec_head) {
+        // the deferred spectrum of the corner this step starts from, beside the
+        // step; C is rewritten only at the hand-over, which waits for it (below,
+        // or through the corner update that waits for ev_join)
+        CK(cudaEventRecord(c->ev_fork, st));
+        CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+        CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
+        CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
+        if (c->delta_head)
+            CK(cudaMemcpyAsync(c->delta_head, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->side));
+        CK(cudaEventRecord(c->ev_join, c->side));
+        c->side_pending = 1;
+    }
     if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
     // Split mode after the first step (whose eager contractions time their plans
@@ -442,16 +455,21 @@ int enqueue_step(ctm_ctx *c)
         // the previous step's spectrum (reading C or Cspec) is done before Cspec is rewritten
         if (c->side_pending) CK(cudaStreamWaitEvent(c->lane2, c->ev_join, 0));
         if ((rc = enqueue_corner(c, c->Qn, c->Cn, 1)) != CTM_OK) return rc;
-        CK(cudaMemcpyAsync(c->Cspec, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, c->lane2));
+        if (!c->spec_skip)
+            CK(cudaMemcpyAsync(c->Cspec, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, c->lane2));
         CK(cudaEventRecord(c->ev_corner, c->lane2));
         // this step's corner spectrum starts from its private copy of C' as soon as the
         // corner update is done, beside the edge update and the next step's first
         // phases; only the next such step rewrites the copy, after waiting for it
-        CK(cudaStreamWaitEvent(c->side, c->ev_corner, 0));
-        CK(launch_spectrum((int)chi, c->Cspec, c->s_new, c->s, c->delta, c->spec_work, c->side));
-        CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
-        CK(cudaEventRecord(c->ev_join, c->side));
-        c->side_pending = 1;
+        if (!c->spec_skip) {
+            CK(cudaStreamWaitEvent(c->side, c->ev_corner, 0));
+            CK(launch_spectrum((int)chi, c->Cspec, c->s_new, c->s, c->delta, c->spec_work, c->side));
+            CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
+            if (c->delta_dst)
+                CK(cudaMemcpyAsync(c->delta_dst, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->side));
+            CK(cudaEventRecord(c->ev_join, c->side));
+            c->side_pending = 1;
+        }
         if ((rc = enqueue_edge(c, c->Qn, c->Tn, 2)) != CTM_OK) return rc;
         // no wait for the spectrum before the hand-over: it reads Cspec, and the last
         // edge contraction waited for the corner update, which waited for the previous
@@ -468,10 +486,12 @@ int enqueue_step(ctm_ctx *c)
     CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
     CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
+    if (c->spec_skip) return CTM_OK;
     CK(cudaEventRecord(c->ev_fork, st));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
     CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
+    if (c->delta_dst) CK(cudaMemcpyAsync(c->delta_dst, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->side));
     CK(cudaEventRecord(c->ev_join, c->side));
     c->side_pending = 1;
     return CTM_OK;
@@ -550,13 +570,17 @@ int check_env_finite(ctm_ctx *c)
     return f ? CTM_ENONFINITE : CTM_OK;
 }
 
-// Capture `nsteps` steps (spectrum fork/join included) into c->graph on the
-// private stream c->own; the caller has switched c->stream to c->own.  Kernel
-// launches counted during the capture are what one replay launches.  A launch
-// that cannot be captured leaves graph_failed set and the caller runs eagerly.
-// Capture nsteps steps into *exec (replacing what it held); on failure the
-// context stays eager (graph_failed).
-static int capture_into(ctm_ctx *c, int nsteps, cudaGraphExec_t *exec, unsigned long long *kernels)
+// Capture `nsteps` steps (spectrum fork/join included) on the private stream
+// c->own; the caller has switched c->stream to c->own.  Kernel launches counted
+// during the capture are what one replay launches.  The result replaces what
+// *exec held; a launch that cannot be captured leaves graph_failed set and the
+// caller runs eagerly.  half >= 0 captures the pipelined form, whose corner
+// spectra are shifted by one step: the first step also computes the spectrum of
+// the corner it starts from (the previous graph's last step), the last step
+// leaves its own to the next graph, and ring half `half` (pinned host memory)
+// receives the deltas -- slot 0 that of the step before the graph, slot i that
+// of step i (1 <= i < nsteps) -- and, at the end, the error flag.
+static int capture_into(ctm_ctx *c, int nsteps, cudaGraphExec_t *exec, unsigned long long *kernels, int half = -1)
 {
     if (*exec) {
         cudaGraphExecDestroy(*exec);
@@ -567,8 +591,20 @@ static int capture_into(ctm_ctx *c, int nsteps, cudaGraphExec_t *exec, unsigned 
     const unsigned long long l0 = g_ctm_launches;
     CK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
     int rc = CTM_OK;
-    for (int i = 0; i < nsteps && rc == CTM_OK; ++i) rc = enqueue_step(c);
+    for (int i = 0; i < nsteps && rc == CTM_OK; ++i) {
+        double *ring = half >= 0 ? c->ring_h + (size_t)half * c->ring_cap : nullptr;
+        c->spec_head = half >= 0 && i == 0;
+        c->delta_head = c->spec_head ? ring : nullptr;
+        c->spec_skip = half >= 0 && i == nsteps - 1;
+        c->delta_dst = (half >= 0 && !c->spec_skip) ? ring + i + 1 : nullptr;
+        rc = enqueue_step(c);
+    }
+    c->delta_dst = c->delta_head = nullptr;
+    c->spec_head = c->spec_skip = 0;
     if (rc == CTM_OK) rc = join_side(c);
+    if (rc == CTM_OK && half >= 0 &&
+        cudaMemcpyAsync(c->ring_err_h + half, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        rc = CTM_ECUDA;
     cudaError_t e = cudaStreamEndCapture(c->stream, &g);
     if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(exec, g, 0);
     if (g) cudaGraphDestroy(g);
@@ -602,37 +638,154 @@ int graph_launch(ctm_ctx *c, int nsteps)
     return CTM_OK;
 }
 
+// The two pipelined graphs of k steps (ring halves 0 and 1), the pinned ring grown
+// to k deltas per half first.  Leaves pipe_steps = 0 if capturing failed.
+static int capture_pipe(ctm_ctx *c, int k)
+{
+    if (c->pipe[0] && c->pipe[1] && c->pipe_steps == k) return CTM_OK;
+    c->pipe_steps = 0;
+    if (k > c->ring_cap) {
+        for (int h = 0; h < 2; ++h)
+            if (c->pipe[h]) {
+                cudaGraphExecDestroy(c->pipe[h]);
+                c->pipe[h] = nullptr;
+            }
+        if (c->ring_h) cudaFreeHost(c->ring_h);
+        c->ring_h = nullptr;
+        c->ring_cap = 0;
+        CK(cudaHostAlloc((void **)&c->ring_h, sizeof(double) * 2 * (size_t)k, cudaHostAllocDefault));
+        c->ring_cap = k;
+    }
+    if (!c->ring_err_h) CK(cudaHostAlloc((void **)&c->ring_err_h, 2 * sizeof(int), cudaHostAllocDefault));
+    for (int h = 0; h < 2; ++h) {
+        if (!c->pipe_done[h]) CK(cudaEventCreateWithFlags(&c->pipe_done[h], cudaEventDisableTiming));
+        int rc = capture_into(c, k, &c->pipe[h], &c->pipe_kernels, h);
+        if (rc != CTM_OK) return rc;
+        if (!c->pipe[h]) return CTM_OK;
+    }
+    c->pipe_steps = k;
+    return CTM_OK;
+}
+
+// One step with its delta read back (synchronous): the one-step graph once the
+// context has stepped in its configured mode, else eagerly.
+static int step_and_read(ctm_ctx *c, double *delta)
+{
+    const int cfg_T = (c->cfg.precision == CTM_SPLIT_BF16) ? c->cfg.n_split : 0;
+    bool replayed = false;
+    int rc;
+    if (c->steps_done > 0 && c->split_T == cfg_T) {
+        if ((rc = capture_steps(c, 1)) != CTM_OK) return rc;
+        if (c->graph1) {
+            if ((rc = graph_launch(c, 1)) != CTM_OK) return rc;
+            replayed = true;
+        }
+    }
+    if (!replayed) {
+        if ((rc = enqueue_step(c)) != CTM_OK) return rc;
+        if (join_side(c) != CTM_OK) return CTM_ECUDA;
+    }
+    c->steps_done++;
+    CK(cudaMemcpyAsync(delta, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = read_status(c)) != CTM_OK) return rc;
+    return isfinite(*delta) ? CTM_OK : CTM_ENONFINITE;
+}
+
+// The spectrum of the current corner C against the last one computed, on the
+// step's stream (the step whose spectrum the pipelined graphs deferred); delta read
+// back (synchronous).
+static int spectrum_now(ctm_ctx *c, double *delta)
+{
+    if (join_side(c) != CTM_OK) return CTM_ECUDA;
+    CK(launch_spectrum(c->chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->stream));
+    CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * c->chi, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(delta, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    int rc = read_status(c);
+    if (rc != CTM_OK) return rc;
+    return isfinite(*delta) ? CTM_OK : CTM_ENONFINITE;
+}
+
+// Chunks of k steps from the two pipelined graphs while at least k steps are left;
+// each chunk's last spectrum runs at the head of the next chunk.  While the newest
+// delta read is above 100 tol (or none is known yet) a second chunk is queued
+// behind the one whose deltas the host is reading, so the GPU does not wait for
+// the host; closer to tol only one chunk is in flight, so that few steps run past
+// convergence.  Queueing stops once the newest delta read is below tol; a chunk
+// already queued still runs (each step moves the environment closer to the fixed
+// point), and the last executed step's own spectrum then gives *delta.  Returns
+// with *ran = 0 when no chunk fits.
+static int converge_pipelined(ctm_ctx *c, int k, int budget, double tol, int *ran, double *delta)
+{
+    *ran = 0;
+    if (budget < k) return CTM_OK;
+    int rc = capture_pipe(c, k);
+    if (rc != CTM_OK || c->pipe_steps != k) return rc;
+    int queue[2], nq = 0, next = 0, launched = 0, chunks_read = 0;
+    bool stop = false;
+    double newest = INFINITY;
+    for (;;) {
+        while (!stop && nq < (newest > 100.0 * tol ? 2 : 1) && launched + k <= budget) {
+            const int h = next;
+            next ^= 1;
+            CK(cudaGraphLaunch(c->pipe[h], c->stream));
+            CTM_COUNT_LAUNCH(c->pipe_kernels);
+            CK(cudaEventRecord(c->pipe_done[h], c->stream));
+            queue[nq++] = h;
+            launched += k;
+        }
+        if (nq == 0) break;
+        const int h = queue[0];
+        queue[0] = queue[1];
+        --nq;
+        CK(cudaEventSynchronize(c->pipe_done[h]));
+        c->steps_done += k;
+        *ran += k;
+        const double *dh = c->ring_h + (size_t)h * c->ring_cap;
+        // slot 0 of the first chunk repeats the delta of a step whose spectrum was
+        // already taken (the recomputation gives 0): no information
+        const int first = chunks_read++ == 0 ? 1 : 0;
+        bool finite = true;
+        for (int i = first; i < k; ++i) finite = finite && isfinite(dh[i]);
+        if (c->ring_err_h[h] || !finite) {
+            // let a queued chunk finish before reporting
+            CK(cudaStreamSynchronize(c->stream));
+            c->steps_done += nq * k;
+            *ran += nq * k;
+            *delta = NAN;
+            return c->ring_err_h[h] ? CTM_ETIMEOUT : CTM_ENONFINITE;
+        }
+        if (k - 1 >= first) {
+            newest = dh[k - 1];
+            stop = newest < tol;
+        }
+    }
+    return spectrum_now(c, delta);
+}
+
+// A fresh context's first step runs eagerly (its launches time the plans); then
+// pipelined chunks of check_every steps while that many are left (see
+// converge_pipelined), and single steps otherwise or when graphs are unavailable.
 int converge_on_own(ctm_ctx *c, int max_steps, double tol, int check_every, int *steps_out, double *delta_out)
 {
-    int rc0 = capture_steps(c, check_every);
-    if (rc0 != CTM_OK) return rc0;
-    int done = 0;
+    const int cfg_T = (c->cfg.precision == CTM_SPLIT_BF16) ? c->cfg.n_split : 0;
+    int done = 0, rc = CTM_OK;
     double delta = INFINITY;
-    while (done < max_steps) {
-        int chunk = check_every;
-        if (done + chunk > max_steps) chunk = max_steps - done;
-        if (chunk == 1 ? c->graph1 != nullptr : (c->graph && chunk == c->graph_steps)) {
-            int rc = graph_launch(c, chunk);
-            if (rc != CTM_OK) return rc;
-        } else {
-            for (int i = 0; i < chunk; ++i) {
-                int rc = enqueue_step(c);
-                if (rc != CTM_OK) return rc;
-            }
-            if (join_side(c) != CTM_OK) return CTM_ECUDA;
+    while (!(delta < tol) && done < max_steps) {
+        int ran = 0;
+        if (c->steps_done > 0 && c->split_T == cfg_T && !c->graph_failed) {
+            rc = converge_pipelined(c, check_every, max_steps - done, tol, &ran, &delta);
+            done += ran;
+            if (rc != CTM_OK) break;
         }
-        done += chunk;
-        c->steps_done += chunk;
-        CK(cudaMemcpyAsync(&delta, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-        int rc = read_status(c);
-        if (rc != CTM_OK) return rc;
-        if (!isfinite(delta)) return CTM_ENONFINITE;
-        if (delta < tol) break;
+        if (ran == 0) {
+            if ((rc = step_and_read(c, &delta)) != CTM_OK) break;
+            ++done;
+        }
     }
     if (steps_out) *steps_out = done;
     if (delta_out) *delta_out = delta;
-    int rc = check_env_finite(c);
     if (rc != CTM_OK) return rc;
+    if ((rc = check_env_finite(c)) != CTM_OK) return rc;
     return (delta < tol) ? CTM_OK : CTM_ENOTCONVERGED;
 }
 
@@ -939,6 +1092,10 @@ void ctm_destroy(ctm_ctx *c)
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    for (int h = 0; h < 2; ++h) {
+        if (c->pipe[h]) cudaGraphExecDestroy(c->pipe[h]);
+        if (c->pipe_done[h]) cudaEventDestroy(c->pipe_done[h]);
+    }
     if (c->own) {
         cudaStreamSynchronize(c->own);
         cudaStreamDestroy(c->own);
@@ -959,6 +1116,8 @@ void ctm_destroy(ctm_ctx *c)
         for (int i = 0; i < CTM_PROF_EVENTS; ++i) cudaEventDestroy(c->prof_ev[i]);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->ring_h) cudaFreeHost(c->ring_h);
+    if (c->ring_err_h) cudaFreeHost(c->ring_err_h);
     delete c;
 }
 

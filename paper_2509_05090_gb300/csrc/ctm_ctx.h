@@ -68,6 +68,22 @@ struct ctm_ctx {
     cudaGraphExec_t graph1;
     unsigned long long graph1_kernels;
     int side_pending;
+    // pipelined ctm_converge: two graphs of pipe_steps steps that also copy each
+    // step's delta, and at the end the error flag, into pinned host memory (ring
+    // half 0 and half 1), so the host reads one half while the other graph runs
+    cudaGraphExec_t pipe[2];
+    int pipe_steps;
+    unsigned long long pipe_kernels;
+    cudaEvent_t pipe_done[2];
+    double *ring_h;           // pinned: 2 x ring_cap deltas
+    int *ring_err_h;          // pinned: one error flag per half
+    int ring_cap;
+    double *delta_dst;        // while capturing those graphs: where this step's delta goes
+    // while capturing them, also: spec_head = this step first computes the spectrum
+    // of the corner it starts from (the previous step's, whose own spectrum was
+    // deferred), its delta to delta_head; spec_skip = this step defers its own
+    int spec_head, spec_skip;
+    double *delta_head;
     // kernel timing (ctm_step_profiled): events around each contraction launch
     int prof_on, prof_n;
     int qr_rows_min;          // 1 for a lone instance; larger inside a batch

@@ -138,3 +138,71 @@ def test_forced_wait_timeout_is_reported(ctm_lib, precision):
     C, T, Q = (_np(x) for x in g2.ctm_get_env())
     assert _rel(C, ref.C) <= 1e-8
     g2.close()
+
+
+def _pipelined_steps(deltas, k, tol, max_steps):
+    """The step count of ctm_converge(max_steps, tol, check_every=k) on a context whose
+    first step is eager, given the delta of every step (deltas[i]: step i + 1): chunks
+    of k steps, a second one queued behind the one being read while the newest delta
+    read is above 100 tol (or unknown); a chunk shows the delta of the step before it
+    (slot 0, no information in the first chunk of a run) and of its own steps but the
+    last; queueing stops when the newest delta read is below tol, and a run of chunks
+    ends with the last step's own spectrum.  Fewer than k steps left run one at a
+    time."""
+    done = 1
+    if deltas[0] < tol:
+        return done
+    while done < max_steps:
+        budget = max_steps - done
+        if budget < k:
+            done += 1
+            if deltas[done - 1] < tol:
+                return done
+            continue
+        queue, launched, stop, reads, newest = [], 0, False, 0, float("inf")
+        while True:
+            while not stop and len(queue) < (2 if newest > 100 * tol else 1) and launched + k <= budget:
+                queue.append(launched)
+                launched += k
+            if not queue:
+                break
+            base = done + queue.pop(0)      # steps done before this chunk
+            slots = [deltas[base - 1]] + [deltas[base + i - 1] for i in range(1, k)]
+            first = 1 if reads == 0 else 0
+            reads += 1
+            if k - 1 >= first:
+                newest = slots[k - 1]
+                stop = newest < tol
+        done += launched
+        if deltas[done - 1] < tol:
+            return done
+    return done
+
+
+@pytest.mark.parametrize("precision,k", [("fp64", 1), ("split_bf16", 1), ("split_bf16", 3)])
+def test_pipelined_converge_matches_single_steps(ctm_lib, precision, k):
+    """ctm_converge keeps one chunk of check_every steps queued behind the one whose
+    deltas it reads and defers each chunk's last corner spectrum to the head of the
+    next.  Against a context stepped one call at a time (delta read back after each
+    step): the same environment after as many steps, the reported delta equal to that
+    step's delta, and the step count that the delta sequence implies."""
+    from paper_2509_05090_gb300 import binding
+    w = I.WORKLOADS["heis_D2_chi8"]
+    A, tol = w.site_tensor(), 1e-10
+    g1 = binding.CTM(A, w.chi, precision=precision, n_split=5)
+    steps, delta, ok = g1.ctm_converge(max_steps=200, tol=tol, check_every=k)
+    assert ok and delta < tol
+    g2 = binding.CTM(A, w.chi, precision=precision, n_split=5)
+    deltas = [g2.ctm_step(1) for _ in range(steps)]
+    assert _pipelined_steps(deltas, k, tol, 200) == steps
+    assert abs(delta - deltas[-1]) <= 1e-13 + 1e-6 * abs(deltas[-1])
+    for x, y in zip(g1.ctm_get_env(), g2.ctm_get_env()):
+        assert _rel(_np(x), _np(y)) <= 1e-10
+    # a step limit that is not a multiple of the chunk: exactly max_steps steps
+    steps2, _, ok2 = g1.ctm_converge(max_steps=7, tol=1e-300, check_every=3)
+    assert steps2 == 7 and not ok2
+    g2.ctm_step(7)
+    for x, y in zip(g1.ctm_get_env(), g2.ctm_get_env()):
+        assert _rel(_np(x), _np(y)) <= 1e-10
+    g1.close()
+    g2.close()
