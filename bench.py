@@ -503,15 +503,28 @@ def run_complex(args, w):
         t0 = time.perf_counter()
         gz = binding.CTMComplex(A_host.to("cuda", non_blocking=True), w.chi, precision=args.precision,
                                 n_split=args.n_split)
-        for _ in range(args.steps):
-            gz.ctm_complex_step(1, want_delta=True)
+        # every step's delta read back (check_every 1; a tol no delta reaches)
+        nst, _, _ = gz.ctm_complex_converge(args.steps, 1e-300, 1)
         _, es, rho = gz.ctm_complex_energy(h_host.to("cuda", non_blocking=True))
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         gz.close()
+        assert nst == args.steps
+        t1 = time.perf_counter()
+        gs = binding.CTMComplex(A_host.to("cuda", non_blocking=True), w.chi, precision=args.precision,
+                                n_split=args.n_split)
+        for _ in range(args.steps):
+            gs.ctm_complex_step(1, want_delta=True)
+        gs.ctm_complex_energy(h_host.to("cuda", non_blocking=True))
+        torch.cuda.synchronize()
+        t_calls = time.perf_counter() - t1
+        gs.close()
         line["e2e"] = {"value": args.steps / t, "unit": "steps/s",
                        "h2d_bytes_per_step": (A_host.numel() + h_host.numel()) * 16 / args.steps,
-                       "d2h_bytes_per_step": 8 + (4 + 2 * rho.size) * 8 / args.steps, "E_site": es}
+                       "d2h_bytes_per_step": 8 + (4 + 2 * rho.size) * 8 / args.steps, "E_site": es,
+                       "what": "H2D of the tensor and bond operators, init, ctm_complex_converge over K steps "
+                               "with every step's delta read back, energy read back",
+                       "single_step_calls": {"value": args.steps / t_calls, "unit": "steps/s"}}
     if not args.no_cpu_baseline:
         from oracle import complex_oracle as zorc
         ref = zorc.ComplexCTM(A, w.chi)

@@ -66,6 +66,18 @@ struct ctm_complex_ctx {
     int graphK_steps;
     int graph_failed;
     int side_pending;   // a corner spectrum on the side stream not yet joined into the main stream
+    // pipelined converge (as in the real path): two graphs of pipe_steps steps whose
+    // corner spectra are shifted by one step and whose deltas (and final error flag)
+    // go to pinned host memory, ring half 0 and half 1
+    cudaGraphExec_t pipe[2];
+    int pipe_steps;
+    unsigned long long pipe_kernels;
+    cudaEvent_t pipe_done[2];
+    double *ring_h;
+    int *ring_err_h;
+    int ring_cap;
+    int spec_head, spec_skip;           // while capturing them: see zstep
+    double *delta_head, *delta_dst;
 };
 
 namespace {
@@ -1104,8 +1116,9 @@ int zedge(ctm_complex_ctx *c)
     return znormalize(c, (long long)chi * D2 * chi, c->Tn, lay_T(c));
 }
 
-// the corner spectrum of C (five planes): delta against the previous one, on `st`
-int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st)
+// the corner spectrum of C (five planes): delta against the previous one, on `st`;
+// with dst, the delta is also copied there (pinned host memory)
+int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st, double *dst = nullptr)
 {
     const int chi = c->chi;
     if (st != c->stream) {
@@ -1117,15 +1130,24 @@ int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st)
     ZK(cudaGetLastError());
     ZK(launch_spectrum_from_tridiag(chi, c->spec_work, c->s_new, c->s, c->delta, st));
     ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
+    if (dst) ZK(cudaMemcpyAsync(dst, c->delta, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (st != c->stream) ZK(cudaEventRecord(c->ev_join, st));
     return CTM_OK;
 }
 
 // One step.  The spectrum of C' runs on the side stream from the corner update on; it is
 // joined before the next step's corner update rewrites C', or at the end when join_now.
+// In the pipelined graphs (spec_head / spec_skip set while capturing) the first step
+// also computes, beside itself, the spectrum of the corner C it starts from (the
+// previous graph's last step, whose own spectrum was skipped); C is rewritten only at
+// the hand-over, after the corner update that waits for it.
 int zstep(ctm_complex_ctx *c, int join_now)
 {
     int rc;
+    if (c->spec_head) {
+        if ((rc = zspectrum(c, c->C, c->side, c->delta_head)) != CTM_OK) return rc;
+        c->side_pending = 1;
+    }
     if ((rc = zenlarged_corner(c)) != CTM_OK) return rc;
     if ((rc = zprojector(c)) != CTM_OK) return rc;
     if (c->side_pending) {
@@ -1133,12 +1155,14 @@ int zstep(ctm_complex_ctx *c, int join_now)
         c->side_pending = 0;
     }
     if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
-    if ((rc = zspectrum(c, c->Cn, c->side)) != CTM_OK) return rc;
-    c->side_pending = 1;
+    if (!c->spec_skip) {
+        if ((rc = zspectrum(c, c->Cn, c->side, c->delta_dst)) != CTM_OK) return rc;
+        c->side_pending = 1;
+    }
     if ((rc = zedge(c)) != CTM_OK) return rc;
     const long long chi = c->chi, D2 = c->D2, n = c->n;
     cudaStream_t st = c->stream;
-    if (join_now) {
+    if (join_now && c->side_pending) {
         ZK(cudaStreamWaitEvent(st, c->ev_join, 0));
         c->side_pending = 0;
     }
@@ -1309,6 +1333,70 @@ static int zcapture(ctm_complex_ctx *c, int nsteps)
     return CTM_OK;
 }
 
+// The two pipelined graphs of k steps (ring halves 0 and 1): slot 0 of a half gets the
+// delta of the step before the graph, slot i that of step i (1 <= i < k), and the graph
+// ends by copying the error flag.  Leaves pipe_steps = 0 if capturing failed.
+static int zcapture_pipe(ctm_complex_ctx *c, int k)
+{
+    if (c->pipe[0] && c->pipe[1] && c->pipe_steps == k) return CTM_OK;
+    c->pipe_steps = 0;
+    if (k > c->ring_cap) {
+        for (int h = 0; h < 2; ++h)
+            if (c->pipe[h]) {
+                cudaGraphExecDestroy(c->pipe[h]);
+                c->pipe[h] = nullptr;
+            }
+        if (c->ring_h) cudaFreeHost(c->ring_h);
+        c->ring_h = nullptr;
+        c->ring_cap = 0;
+        ZK(cudaHostAlloc((void **)&c->ring_h, sizeof(double) * 2 * (size_t)k, cudaHostAllocDefault));
+        c->ring_cap = k;
+    }
+    if (!c->ring_err_h) ZK(cudaHostAlloc((void **)&c->ring_err_h, 2 * sizeof(int), cudaHostAllocDefault));
+    for (int h = 0; h < 2; ++h) {
+        if (!c->pipe_done[h]) ZK(cudaEventCreateWithFlags(&c->pipe_done[h], cudaEventDisableTiming));
+        if (c->pipe[h]) {
+            cudaGraphExecDestroy(c->pipe[h]);
+            c->pipe[h] = nullptr;
+        }
+        if (c->graph_failed) return CTM_OK;
+        double *ring = c->ring_h + (size_t)h * c->ring_cap;
+        cudaGraph_t g = nullptr;
+        const unsigned long long l0 = g_ctm_launches;
+        ZK(cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal));
+        const int steps0 = c->steps_done;
+        int rc = CTM_OK;
+        for (int i = 0; i < k && rc == CTM_OK; ++i) {
+            c->spec_head = i == 0;
+            c->delta_head = c->spec_head ? ring : nullptr;
+            c->spec_skip = i == k - 1;
+            c->delta_dst = c->spec_skip ? nullptr : ring + i + 1;
+            rc = zstep(c, i == k - 1);
+        }
+        c->spec_head = c->spec_skip = 0;
+        c->delta_head = c->delta_dst = nullptr;
+        if (rc == CTM_OK &&
+            cudaMemcpyAsync(c->ring_err_h + h, c->err, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+            rc = CTM_ECUDA;
+        c->steps_done = steps0;
+        c->side_pending = 0;
+        cudaError_t e = cudaStreamEndCapture(c->stream, &g);
+        if (rc == CTM_OK && e == cudaSuccess && g) e = cudaGraphInstantiate(&c->pipe[h], g, 0);
+        if (g) cudaGraphDestroy(g);
+        const unsigned long long captured = g_ctm_launches - l0;
+        g_ctm_launches = l0;   // nothing ran yet: replays add the captured kernel count
+        if (rc != CTM_OK || e != cudaSuccess || !c->pipe[h]) {
+            cudaGetLastError();
+            c->pipe[h] = nullptr;
+            c->graph_failed = 1;
+            return CTM_OK;
+        }
+        c->pipe_kernels = captured;
+    }
+    c->pipe_steps = k;
+    return CTM_OK;
+}
+
 int ctm_complex_step(ctm_complex_ctx *c, int nsteps, double *delta_host)
 {
     if (!c || nsteps < 1) return CTM_EINVAL;
@@ -1346,6 +1434,60 @@ int ctm_complex_step(ctm_complex_ctx *c, int nsteps, double *delta_host)
     return CTM_OK;
 }
 
+// Chunks of k steps from the two pipelined graphs on the private stream, as in the real
+// path: a second chunk queued while the newest delta read is above 100 tol, queueing
+// stopped once it is below tol, and the last executed step's own spectrum at the end.
+static int zconverge_pipelined(ctm_complex_ctx *c, int k, int budget, double tol, int *ran, double *delta)
+{
+    *ran = 0;
+    if (budget < k) return CTM_OK;
+    int rc = zcapture_pipe(c, k);
+    if (rc != CTM_OK || c->pipe_steps != k) return rc;
+    int queue[2], nq = 0, next = 0, launched = 0, chunks_read = 0;
+    bool stop = false;
+    double newest = INFINITY;
+    for (;;) {
+        while (!stop && nq < (newest > 100.0 * tol ? 2 : 1) && launched + k <= budget) {
+            const int h = next;
+            next ^= 1;
+            ZK(cudaGraphLaunch(c->pipe[h], c->stream));
+            CTM_COUNT_LAUNCH(c->pipe_kernels);
+            ZK(cudaEventRecord(c->pipe_done[h], c->stream));
+            queue[nq++] = h;
+            launched += k;
+        }
+        if (nq == 0) break;
+        const int h = queue[0];
+        queue[0] = queue[1];
+        --nq;
+        ZK(cudaEventSynchronize(c->pipe_done[h]));
+        c->steps_done += k;
+        *ran += k;
+        const double *dh = c->ring_h + (size_t)h * c->ring_cap;
+        const int first = chunks_read++ == 0 ? 1 : 0;   // slot 0 of the first chunk: no information
+        bool finite = true;
+        for (int i = first; i < k; ++i) finite = finite && isfinite(dh[i]);
+        if (c->ring_err_h[h] || !finite) {
+            ZK(cudaStreamSynchronize(c->stream));
+            c->steps_done += nq * k;
+            *ran += nq * k;
+            *delta = NAN;
+            return c->ring_err_h[h] ? CTM_ETIMEOUT : CTM_ENONFINITE;
+        }
+        if (k - 1 >= first) {
+            newest = dh[k - 1];
+            stop = newest < tol;
+        }
+    }
+    // the last step's own spectrum
+    if ((rc = zspectrum(c, c->C, c->stream)) != CTM_OK) return rc;
+    ZK(cudaMemcpyAsync(delta, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    if ((rc = zread_status(c)) != CTM_OK) return rc;
+    return isfinite(*delta) ? CTM_OK : CTM_ENONFINITE;
+}
+
+// A fresh context's first step runs eagerly; then pipelined chunks of check_every steps
+// while that many are left, single steps otherwise (see ctm_converge).
 int ctm_complex_converge(ctm_complex_ctx *c, int max_steps, double tol, int check_every, int *steps_out,
                          double *delta_out)
 {
@@ -1354,17 +1496,32 @@ int ctm_complex_converge(ctm_complex_ctx *c, int max_steps, double tol, int chec
     if (tol <= 0.0) tol = c->cfg.tol;
     if (check_every < 1) check_every = 1;
     if (max_steps <= 0) return CTM_EINVAL;
-    int done = 0, rc;
+    int done = 0, rc = CTM_OK;
     double delta = INFINITY;
-    while (done < max_steps) {
-        const int k = (max_steps - done) < check_every ? (max_steps - done) : check_every;
-        if ((rc = ctm_complex_step(c, k, &delta)) != CTM_OK && rc != CTM_ENONFINITE) return rc;
-        done += k;
-        if (rc == CTM_ENONFINITE) return rc;
-        if (delta < tol) break;
+    while (!(delta < tol) && done < max_steps) {
+        int ran = 0;
+        if (c->steps_done > 0 && !c->graph_failed) {
+            cudaStream_t user = c->stream;
+            ZK(cudaEventRecord(c->ev_in, user));
+            ZK(cudaStreamWaitEvent(c->own, c->ev_in, 0));
+            c->stream = c->own;
+            rc = zconverge_pipelined(c, check_every, max_steps - done, tol, &ran, &delta);
+            c->stream = user;
+            ZK(cudaEventRecord(c->ev_out, c->own));
+            ZK(cudaStreamWaitEvent(user, c->ev_out, 0));
+            done += ran;
+            if (rc != CTM_OK) break;
+        }
+        if (ran == 0) {
+            rc = ctm_complex_step(c, 1, &delta);
+            ++done;
+            if (rc != CTM_OK) break;
+        }
     }
     if (steps_out) *steps_out = done;
     if (delta_out) *delta_out = delta;
+    if (rc != CTM_OK) return rc;
+    if ((rc = zcheck_env_finite(c)) != CTM_OK) return rc;
     return delta < tol ? CTM_OK : CTM_ENOTCONVERGED;
 }
 
@@ -1543,6 +1700,12 @@ void ctm_complex_destroy(ctm_complex_ctx *c)
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int h = 0; h < 2; ++h) {
+        if (c->pipe[h]) cudaGraphExecDestroy(c->pipe[h]);
+        if (c->pipe_done[h]) cudaEventDestroy(c->pipe_done[h]);
+    }
+    if (c->ring_h) cudaFreeHost(c->ring_h);
+    if (c->ring_err_h) cudaFreeHost(c->ring_err_h);
     delete c;
 }
 

@@ -291,3 +291,26 @@ def test_complex_tf32_energy(ctm_lib, prec, tol):
     print(prec, E, Ez, abs(E - Ez))
     assert abs(E - Ez) < tol, (E, Ez)
     g.close()
+
+
+@pytest.mark.parametrize("precision,k", [("fp64", 1), ("split_bf16", 1), ("split_bf16", 3)])
+def test_complex_pipelined_converge_matches_single_steps(ctm_lib, precision, k):
+    """ctm_complex_converge's pipelined chunks (shifted corner spectra, deltas through
+    pinned memory) against single-step calls: the step count the delta sequence
+    implies, the last step's delta, and the same environment."""
+    from test_gpu_paths import _pipelined_steps
+    v = I.coherent_state(2, (1.0, 1.0, 1.0))
+    A = I.complex_perturbed_product_site_tensor(v, 2, 0.2, 7)
+    tol = 1e-10
+    g1 = _ctm(A, 8, precision=precision)
+    steps, delta, ok = g1.ctm_complex_converge(60, tol, k)
+    assert ok and delta < tol
+    g2 = _ctm(A, 8, precision=precision)
+    deltas = [g2.ctm_complex_step(1) for _ in range(steps)]
+    assert _pipelined_steps(deltas, k, tol, 60) == steps
+    assert abs(delta - deltas[-1]) <= 1e-13 + 1e-6 * abs(deltas[-1])
+    for x, y in zip(g1.ctm_complex_get_env(), g2.ctm_complex_get_env()):
+        x, y = _np(x), _np(y)
+        assert np.abs(x - y).max() <= 1e-10 * np.abs(y).max()
+    g1.close()
+    g2.close()
