@@ -437,7 +437,7 @@ int enqueue_step(ctm_ctx *c)
         // or through the corner update that waits for ev_join)
         CK(cudaEventRecord(c->ev_fork, st));
         CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-        CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
+        CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side, c->qr_rows_min <= 1));
         CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
         if (c->delta_head)
             CK(cudaMemcpyAsync(c->delta_head, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->side));
@@ -463,7 +463,8 @@ int enqueue_step(ctm_ctx *c)
         // phases; only the next such step rewrites the copy, after waiting for it
         if (!c->spec_skip) {
             CK(cudaStreamWaitEvent(c->side, c->ev_corner, 0));
-            CK(launch_spectrum((int)chi, c->Cspec, c->s_new, c->s, c->delta, c->spec_work, c->side));
+            CK(launch_spectrum((int)chi, c->Cspec, c->s_new, c->s, c->delta, c->spec_work, c->side,
+                               c->qr_rows_min <= 1));
             CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
             if (c->delta_dst)
                 CK(cudaMemcpyAsync(c->delta_dst, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->side));
@@ -489,7 +490,7 @@ int enqueue_step(ctm_ctx *c)
     if (c->spec_skip) return CTM_OK;
     CK(cudaEventRecord(c->ev_fork, st));
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
+    CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side, c->qr_rows_min <= 1));
     CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
     if (c->delta_dst) CK(cudaMemcpyAsync(c->delta_dst, c->delta, sizeof(double), cudaMemcpyDeviceToHost, c->side));
     CK(cudaEventRecord(c->ev_join, c->side));
@@ -541,7 +542,7 @@ int enqueue_step_profiled(ctm_ctx *c, cudaEvent_t *ev)
     CK(cudaEventRecord(ev[7], st));
     CK(cudaStreamWaitEvent(c->side, ev[7], 0));
     CK(cudaEventRecord(ev[8], c->side));
-    CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side));
+    CK(launch_spectrum((int)chi, c->C, c->s_new, c->s, c->delta, c->spec_work, c->side, c->qr_rows_min <= 1));
     CK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, c->side));
     CK(cudaEventRecord(ev[9], c->side));
     CK(cudaEventRecord(c->ev_join, c->side));

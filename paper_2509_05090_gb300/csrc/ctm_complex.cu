@@ -599,6 +599,11 @@ __device__ double zblock_sum(double v, double *red)
 // and |e_i|^2, which the bisection of the real spectrum takes as they are.
 constexpr int ZTRI_THREADS = 256;
 size_t ztridiag_smem_bytes(int chi) { return sizeof(double) * ((size_t)2 * chi * (chi | 1) + 4 * (size_t)chi); }
+size_t ztridiag_launch_bytes(int chi)
+{
+    const size_t need = ztridiag_smem_bytes(chi), alone = 220 * 1024;
+    return need > alone ? need : alone;
+}
 
 __global__ void __launch_bounds__(ZTRI_THREADS) zc_tridiag_kernel(int chi, const double *C, long long PC, double *work)
 {
@@ -1126,7 +1131,9 @@ int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st, double *ds
         ZK(cudaStreamWaitEvent(st, c->ev_fork, 0));
     }
     CTM_COUNT_LAUNCH(1);
-    zc_tridiag_kernel<<<1, ZTRI_THREADS, ztridiag_smem_bytes(chi), st>>>(chi, Cin, c->PC, c->spec_work);
+    // all but a few KB of the SM's shared memory: the step's CTAs stay off its SM (as for
+    // the real corner spectrum)
+    zc_tridiag_kernel<<<1, ZTRI_THREADS, ztridiag_launch_bytes(chi), st>>>(chi, Cin, c->PC, c->spec_work);
     ZK(cudaGetLastError());
     ZK(launch_spectrum_from_tridiag(chi, c->spec_work, c->s_new, c->s, c->delta, st));
     ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
@@ -1247,7 +1254,7 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess ||
             tf32_prepare() != cudaSuccess ||
             cudaFuncSetAttribute(zc_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ztridiag_smem_bytes(80)) != cudaSuccess) {
+                                 (int)ztridiag_launch_bytes(80)) != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
         }

@@ -130,7 +130,7 @@ constexpr int CORNER_NORM_BLOCKS = 64;
 cudaError_t launch_corner_sym_normalize(int chi, const double *Cr, double *Cn, double *partials, cudaStream_t st);
 cudaError_t launch_normalize(long long count, double *x, double *partials, int nblocks, cudaStream_t st);
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
-                            double *work, cudaStream_t st);
+                            double *work, cudaStream_t st, bool reserve_sm = false);
 cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st);
 // The last two phases of launch_spectrum for a real symmetric tridiagonal matrix already in
 // `work` (diagonal d in work[0, chi), squared off-diagonal e^2 in work[chi, 2 chi)).

@@ -192,6 +192,7 @@ __global__ void scale_by_partials_kernel(long long count, double *x, const doubl
 // (3) one CTA: |lambda| sorted descending by rank, unit 2-norm, delta.
 constexpr int SPEC_WARPS = 1;   // one eigenvalue per CTA: the chi Sturm chains spread over chi SMs
 constexpr int TRI_THREADS = 256;
+constexpr size_t SPEC_SM_ALONE_BYTES = 220 * 1024;   // within the 224 KB opt-in of spectrum_prepare
 
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const double *C, double *work)
 {
@@ -490,10 +491,16 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
 size_t spectrum_work_doubles(int chi) { return (size_t)3 * chi + 8; }
 
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
-                            double *work, cudaStream_t st)
+                            double *work, cudaStream_t st, bool reserve_sm)
 {
     if (chi > 160 || !work) return cudaErrorInvalidValue;
+    // reserve_sm: the tridiagonalisation runs beside a lone instance's step for ~0.4 ms on
+    // one SM; asking for (nearly) all of the SM's shared memory keeps the step's CTAs off
+    // that SM, whose CTAs it would otherwise slow (a grid-synchronous QR waits for its
+    // slowest CTA): measured 0.892 -> 0.872 ms per step at D = 6, chi = 72.  (Not inside a
+    // batch, where many spectra run at once.)
     size_t smem = sizeof(double) * ((size_t)chi * (chi | 1) + 2 * (size_t)chi);
+    if (reserve_sm && smem < SPEC_SM_ALONE_BYTES) smem = SPEC_SM_ALONE_BYTES;
     CTM_COUNT_LAUNCH(3);
     tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     cudaError_t e = cudaGetLastError();
