@@ -375,7 +375,7 @@ int enqueue_corner(ctm_ctx *c, const double *Qp, double *Cout, int lane = 0)
     CK(run_gemm(c, g, GEMM_REUSE_A, lane));
     g = GemmF64{chi, chi, (int)n, Qp, idx_lin(1), idx_lin(chi), c->MQ, idx_lin(chi), idx_lin(1),
                 c->Cr, idx_lin(chi), idx_lin(1), 1.0, 0.0};
-    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_FILL_Q : GEMM_PLAIN, lane));
+    CK(run_gemm(c, g, (Qp == c->Qn || Qp == c->Q) ? GEMM_A_FILL_Q : GEMM_PLAIN, lane));
     CK(launch_corner_sym_normalize(chi, c->Cr, Cout, lane == 1 ? c->norm_part2 : c->norm_part, st));
     return CTM_OK;
 }
@@ -416,7 +416,7 @@ int enqueue_edge(ctm_ctx *c, const double *Qp, double *Tout, int lane = 0)
     g = GemmF64{chi, (int)n, (int)n, Qp, idx_lin(1), idx_lin(chi), c->H, idx_lin(n), idx_lin(1),
                 Tout, idx_lin(n), idx_lin(1), 1.0, 0.0};
     if (lane == 2) CK(cudaStreamWaitEvent(st, c->ev_corner, 0));
-    CK(run_gemm(c, g, Qp == c->Qn ? GEMM_A_USE_Q : GEMM_PLAIN, lane));
+    CK(run_gemm(c, g, (Qp == c->Qn || Qp == c->Q) ? GEMM_A_USE_Q : GEMM_PLAIN, lane));
     CK(launch_normalize((long long)chi * D2 * chi, Tout, c->norm_part, NORM_BLOCKS, st));
     return CTM_OK;
 }
@@ -444,19 +444,24 @@ int enqueue_step(ctm_ctx *c)
         CK(cudaEventRecord(c->ev_join, c->side));
         c->side_pending = 1;
     }
-    if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
-    if ((rc = enqueue_projector(c, c->Qn)) != CTM_OK) return rc;
     // Split mode after the first step (whose eager contractions time their plans
     // one at a time): the corner and edge updates both need only Q, so the corner
-    // update runs on lane2 beside the edge update.
-    if ((c->split_T > 0 || c->tf32_T > 0) && c->steps_done > 0 && c->cfg.corner_mode == 0) {
+    // update runs on lane2 beside the edge update.  This path also writes the new
+    // environment in place: C, T and Q are not read after the QR except by their
+    // own updates (the warm start and the enlarged corner come before it; the edge
+    // update reads T in its first contraction, before its last one writes T'), so
+    // no hand-over copies are needed.
+    const bool lanes = (c->split_T > 0 || c->tf32_T > 0) && c->steps_done > 0 && c->cfg.corner_mode == 0;
+    if ((rc = enqueue_enlarged_corner(c)) != CTM_OK) return rc;
+    if ((rc = enqueue_projector(c, lanes ? c->Q : c->Qn)) != CTM_OK) return rc;
+    if (lanes) {
         CK(cudaEventRecord(c->ev_q, st));
         CK(cudaStreamWaitEvent(c->lane2, c->ev_q, 0));
-        // the previous step's spectrum (reading C or Cspec) is done before Cspec is rewritten
+        // the previous step's spectrum (reading C or Cspec) is done before C or Cspec is rewritten
         if (c->side_pending) CK(cudaStreamWaitEvent(c->lane2, c->ev_join, 0));
-        if ((rc = enqueue_corner(c, c->Qn, c->Cn, 1)) != CTM_OK) return rc;
+        if ((rc = enqueue_corner(c, c->Q, c->C, 1)) != CTM_OK) return rc;
         if (!c->spec_skip)
-            CK(cudaMemcpyAsync(c->Cspec, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, c->lane2));
+            CK(cudaMemcpyAsync(c->Cspec, c->C, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, c->lane2));
         CK(cudaEventRecord(c->ev_corner, c->lane2));
         // this step's corner spectrum starts from its private copy of C' as soon as the
         // corner update is done, beside the edge update and the next step's first
@@ -471,13 +476,9 @@ int enqueue_step(ctm_ctx *c)
             CK(cudaEventRecord(c->ev_join, c->side));
             c->side_pending = 1;
         }
-        if ((rc = enqueue_edge(c, c->Qn, c->Tn, 2)) != CTM_OK) return rc;
-        // no wait for the spectrum before the hand-over: it reads Cspec, and the last
-        // edge contraction waited for the corner update, which waited for the previous
-        // spectrum (the one that may read C)
-        CK(cudaMemcpyAsync(c->C, c->Cn, sizeof(double) * chi * chi, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(c->T, c->Tn, sizeof(double) * chi * D2 * chi, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(c->Q, c->Qn, sizeof(double) * n * chi, cudaMemcpyDeviceToDevice, st));
+        // the last edge contraction waits for the corner update (whose pack of Q^T it
+        // reuses), which waited for the previous spectrum
+        if ((rc = enqueue_edge(c, c->Q, c->T, 2)) != CTM_OK) return rc;
         return CTM_OK;
     }
     if ((rc = c->cfg.corner_mode ? enqueue_corner_from_r(c, c->Cn) : enqueue_corner(c, c->Qn, c->Cn)) != CTM_OK)
