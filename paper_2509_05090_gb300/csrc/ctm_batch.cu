@@ -26,6 +26,7 @@ struct ctm_batch {
     cudaStream_t user, root;
     cudaEvent_t ev_root, ev_user, ev_back;
     cudaGraphExec_t graph;
+    unsigned long long graph_kernels;   // kernels one replay launches (counted at capture)
     long long steps;
 };
 
@@ -144,17 +145,22 @@ int ctm_batch_step(ctm_batch *b, int nsteps, double *max_delta_host)
             if ((rc = read_status(c)) != CTM_OK) return rc;
         ++done;
         cudaGraph_t g = nullptr;
+        const unsigned long long l0 = g_ctm_launches;
         if (cudaStreamBeginCapture(b->root, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CTM_ECUDA;
         rc = enqueue_batched_step(b);
         cudaError_t e = cudaStreamEndCapture(b->root, &g);
+        b->graph_kernels = g_ctm_launches - l0;
+        g_ctm_launches = l0;   // nothing ran yet: replays add the captured kernel count
         if (rc != CTM_OK) return rc;
         if (e != cudaSuccess || !g) return CTM_ECUDA;
         e = cudaGraphInstantiate(&b->graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return CTM_ECUDA;
     }
-    for (; done < nsteps; ++done)
+    for (; done < nsteps; ++done) {
         if (cudaGraphLaunch(b->graph, b->root) != cudaSuccess) return CTM_ECUDA;
+        CTM_COUNT_LAUNCH(b->graph_kernels);
+    }
     b->steps += nsteps;
     for (auto *c : b->ctx) c->steps_done += 0;
     if (cudaEventRecord(b->ev_back, b->root) != cudaSuccess) return CTM_ECUDA;
