@@ -389,6 +389,64 @@ def fp64_step_record(w, steps, fp64_peak):
             "fp64_peak_tflops": fp64_peak, "phase_ms": ph, "algorithmic_flops_per_step": flops}
 
 
+def grad_record(fp64_peak, warmup=3, k_tracked=30):
+    """The differentiation configuration: D = 8, chi = 128 (enlarged corner 8192 x 8192), the
+    FP32/TF32 forward (split TF32 contractions, FP64 QR) over `warmup` + `k_tracked`
+    checkpointed steps of the converging Kitaev-Heisenberg state, the energy, and the
+    hand-written FP64 adjoint (ctm_grad).  The forward alone (same steps, energy) is timed on
+    a second context so that the adjoint's share can be stated; the adjoint recomputes each
+    tracked step in FP64 and runs two FP64 products per contraction, so its algorithmic work
+    is 3 k_tracked step GEMMs."""
+    import torch
+    from paper_2509_05090_gb300 import binding, inputs
+    w = inputs.WORKLOADS["kh_D8_chi128_conv"]
+    A, h = w.site_tensor(), w.hamiltonians()
+    c = binding.CTM(A, w.chi, precision="split_tf32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, dA = c.ctm_grad(h, warmup=warmup, k_tracked=k_tracked)
+    torch.cuda.synchronize()
+    t_grad = time.perf_counter() - t0
+    c.close()
+    f = binding.CTM(A, w.chi, precision="split_tf32")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f.ctm_step(warmup + k_tracked, want_delta=False)
+    E_f = f.ctm_energy(h)[1]
+    torch.cuda.synchronize()
+    t_fwd = time.perf_counter() - t0
+    f.close()
+    t_adj = max(t_grad - t_fwd, 1e-9)
+    adj_flops = 3.0 * k_tracked * step_gemm_flops(w.chi, w.D2)
+    return {"workload": w.name, "precision": "split_tf32 forward, FP64 QR and adjoint", "warmup": warmup,
+            "k_tracked": k_tracked, "seconds": t_grad, "forward_seconds": t_fwd, "adjoint_seconds": t_adj,
+            "E_site": E, "E_site_forward_only": E_f, "grad_norm": float(dA.norm().item()),
+            "adjoint_fp64_tflops": adj_flops / t_adj / 1e12,
+            "adjoint_frac_of_fp64_peak": adj_flops / t_adj / 1e12 / fp64_peak,
+            "note": "adjoint time = ctm_grad wall time minus the forward's; frac over the whole adjoint phase"}
+
+
+def optimize_record(iters=8, D=3, chi=27):
+    """The variational loop (Sec. II.D): L-BFGS over the site tensor with the adjoint gradient
+    (split-BF16 forward, 10 warm-up + 10 tracked steps per evaluation, each evaluation
+    warm-started from the previous environment), for the Heisenberg model with the pi
+    rotation on sublattice B from a seeded random D = 3 tensor at chi = 27: the energy per
+    outer iteration (a variational upper bound of the QMC -0.544553) and the wall time."""
+    import torch
+    from paper_2509_05090_gb300 import autograd, inputs, optimize
+    h = inputs.bond_hamiltonians(0.0, 1.0, rotate_b=True)
+    A0 = inputs.random_site_tensor(2, D, 2024)
+    autograd.release_contexts()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, energies = optimize.optimize(A0, chi, h, steps=iters, warmup=10, k_tracked=10, precision="split_bf16")
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    autograd.release_contexts()
+    return {"model": "Heisenberg, B sublattice rotated", "d": 2, "D": D, "chi": chi, "seed": 2024,
+            "outer_iterations": iters, "energies": energies, "seconds": secs, "seconds_per_iteration": secs / iters}
+
+
 def complex_record(steps, n_split, fp64_peak, bf16_peak, with_oracle=True):
     """The complex (E-irrep) path, Kitaev K = -1 at D = 6, chi = 72 (complex enlarged corner
     2592 x 2592, the size of the real benchmark workload): steps/s in split BF16 and FP64 on the random tensor (CUDA events over one
@@ -764,6 +822,8 @@ def main():
             tf[prec] = {"steps_per_s": split_step_rate(w, args.steps, args.n_split, precision=prec),
                         "E_site_after_3_steps": E_t, "abs_err_vs_oracle": abs(E_t - E_o)}
         line["tf32_modes"] = tf
+        line["grad_d8_chi128"] = grad_record(fp64_peak)
+        line["optimize_heisenberg_D3"] = optimize_record()
         line["batch96"] = batch_record(args, args.steps)
         line["complex_E_D6_chi72"] = complex_record(args.steps, args.n_split, fp64_peak, peaks["bf16_tflops"],
                                                     with_oracle=not args.no_compare)
