@@ -126,8 +126,11 @@ int ctm_step(ctm_ctx *ctx, int nsteps, double *delta_host);
  * whose newest delta is below tol.  The run ends with the last step's own
  * spectrum: *delta_out is the delta of the last executed step, *steps_out the
  * number of steps this call ran (at most max_steps; fewer than check_every
- * left run one at a time).  Synchronous.  Returns CTM_ENOTCONVERGED (outputs
- * filled) if the limit was hit with delta >= tol. */
+ * left run one at a time).  Synchronous.  The ring of deltas is pinned host
+ * memory the context allocates on first use (2 x check_every doubles plus two
+ * flags; cudaHostAlloc) and frees in ctm_destroy; no device memory is allocated.
+ * Returns CTM_ENOTCONVERGED (outputs filled) if the limit was hit with
+ * delta >= tol. */
 int ctm_converge(ctm_ctx *ctx, int max_steps, double tol, int check_every,
                  int *steps_out, double *delta_out);
 
