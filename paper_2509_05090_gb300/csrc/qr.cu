@@ -491,6 +491,8 @@ int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
     int rows_per = (n + sms - 1) / sms;
     if (rows_per < rows_min) rows_per = rows_min;
     if (rows_per < 1) rows_per = 1;
+    // a floor that would not fit shared memory gives way (more CTAs)
+    while (rows_per > 1 && qr_smem_bytes(rows_per, k) > 200 * 1024) rows_per = (rows_per * 3) / 4;
     int G = (n + rows_per - 1) / rows_per;
     *G_out = G;
     *rows_out = rows_per;
