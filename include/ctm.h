@@ -77,6 +77,11 @@ typedef struct {
                                 factor R of the reduced corner Y = M Q_prev S (S = diag(sgn C_ii)),
                                 which equals Q^T M Q_prev and so Q^T M Q at a fixed point: skips the
                                 two corner contractions (a cheap variant, Sec. II.B, Fig. 3d) */
+    int deterministic;       /* 1: the QR's cross-CTA sums (Gram rows, V^T V) are written per CTA and
+                                added in CTA order instead of with FP64 atomics, so with FP64 or
+                                split-BF16 contractions a replayed step gives the same bits every
+                                time (the split-K partials of the TF32 modes still meet through
+                                FP64 atomics); costs some workspace and a few % of QR time */
 } ctm_config;
 
 /* Bytes of device workspace ctm_init needs for this configuration (0 on a bad

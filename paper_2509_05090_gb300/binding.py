@@ -29,7 +29,8 @@ PRECISIONS = {"fp64": CTM_FP64, "split_bf16": CTM_SPLIT_BF16, "split_tf32": CTM_
 class ctm_config(ctypes.Structure):
     _fields_ = [("d", ctypes.c_int), ("D", ctypes.c_int), ("chi", ctypes.c_int),
                 ("precision", ctypes.c_int), ("n_split", ctypes.c_int), ("tol", ctypes.c_double),
-                ("max_steps", ctypes.c_int), ("symmetrize", ctypes.c_int), ("corner_mode", ctypes.c_int)]
+                ("max_steps", ctypes.c_int), ("symmetrize", ctypes.c_int), ("corner_mode", ctypes.c_int),
+                ("deterministic", ctypes.c_int)]
 
 
 class CtmError(RuntimeError):
@@ -178,10 +179,11 @@ def _ptr(t):
 CORNER_MODES = {"qmq": 0, "r": 1}
 
 
-def make_config(d, D, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True, corner="qmq"):
+def make_config(d, D, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True, corner="qmq",
+                deterministic=False):
     return ctm_config(int(d), int(D), int(chi), PRECISIONS[precision] if isinstance(precision, str) else
                       int(precision), int(n_split), float(tol), int(max_steps), 1 if symmetrize else 0,
-                      CORNER_MODES[corner])
+                      CORNER_MODES[corner], 1 if deterministic else 0)
 
 
 def ctm_workspace_bytes(cfg: ctm_config) -> int:
@@ -192,7 +194,7 @@ class CTM:
     """One CTMRG instance on the current CUDA device (ctm_init ... ctm_destroy)."""
 
     def __init__(self, A, chi, precision="fp64", n_split=3, tol=1e-10, max_steps=200, symmetrize=True,
-                 stream=None, corner="qmq"):
+                 stream=None, corner="qmq", deterministic=False):
         torch = _torch()
         lib = load()
         if isinstance(A, np.ndarray):
@@ -202,7 +204,7 @@ class CTM:
         self.d, self.D, self.chi = d, D, int(chi)
         self.D2 = D * D
         self.n = self.chi * self.D2
-        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize, corner)
+        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize, corner, deterministic)
         nbytes = ctm_workspace_bytes(self.cfg)
         if nbytes == 0:
             raise CtmError(1, "ctm_workspace_bytes")
@@ -372,7 +374,7 @@ class CTMComplex:
     Complex tensors go in and out as torch.complex128 on the current CUDA device."""
 
     def __init__(self, A, chi, irrep="E", precision="fp64", n_split=5, tol=1e-10, max_steps=200, symmetrize=True,
-                 stream=None):
+                 stream=None, deterministic=False):
         torch = _torch()
         lib = load()
         A = _complex_dev(A, torch)
@@ -383,7 +385,7 @@ class CTMComplex:
         self.D2 = D * D
         self.n = self.chi * self.D2
         self.irrep = IRREPS[irrep] if isinstance(irrep, str) else int(irrep)
-        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize)
+        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize, deterministic=deterministic)
         nbytes = int(lib.ctm_complex_workspace_bytes(ctypes.byref(self.cfg), self.irrep))
         if nbytes == 0:
             raise CtmError(1, "ctm_complex_workspace_bytes")

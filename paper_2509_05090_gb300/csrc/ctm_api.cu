@@ -135,6 +135,11 @@ size_t layout(ctm_ctx *c, char *base)
     c->qr_sbuf = td((long long)qr_scratch_doubles((int)chi));
     c->qr_rowbuf = td((long long)qr_rowbuf_doubles((int)chi));
     c->qr_wy = td((long long)qr_wy_doubles((int)n, (int)chi));
+    if (c->cfg.deterministic) {
+        c->qr_gmax = qr_det_gmax((int)n);
+        c->qr_gpart = td((long long)qr_det_gram_doubles((int)chi, c->qr_gmax));
+        c->qr_spart = td((long long)qr_det_s_doubles((int)chi, c->qr_gmax));
+    }
     c->qr_bar = (unsigned *)take(64);
     c->err = (int *)take(64);
     c->flag = (int *)take(64);
@@ -260,6 +265,7 @@ bool config_ok(const ctm_config *cfg)
         return false;
     if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
     if (cfg->corner_mode != 0 && cfg->corner_mode != 1) return false;
+    if (cfg->deterministic != 0 && cfg->deterministic != 1) return false;
     long long n = (long long)cfg->chi * cfg->D * cfg->D;
     if (n > 20000) return false;
     return true;

@@ -49,6 +49,8 @@ struct ctm_complex_ctx {
     double *splitk;
     size_t splitk_elems;
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
+    double *qr_gpart, *qr_spart;   // deterministic mode: per-CTA partial sums of the embedded QR
+    int qr_gmax;
     unsigned *qr_bar;
     int *err, *flag;
     double *norm_part;
@@ -894,6 +896,9 @@ QrScratch zqr_scratch(ctm_complex_ctx *c)
     q.S = q.V + k * k;
     q.W = q.S + k * k;
     q.ta = q.W + k * k;
+    q.gpart = c->qr_gpart;
+    q.spart = c->qr_spart;
+    q.gmax = c->qr_gmax;
     return q;
 }
 
@@ -970,6 +975,11 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->qr_sbuf = td((long long)qr_scratch_doubles((int)k2));
     c->qr_rowbuf = td((long long)qr_rowbuf_doubles((int)k2));
     c->qr_wy = td((long long)qr_wy_doubles((int)(2 * n), (int)k2));
+    if (c->cfg.deterministic) {
+        c->qr_gmax = qr_det_gmax((int)(2 * n));
+        c->qr_gpart = td((long long)qr_det_gram_doubles((int)k2, c->qr_gmax));
+        c->qr_spart = td((long long)qr_det_s_doubles((int)k2, c->qr_gmax));
+    }
     c->qr_bar = (unsigned *)take(64);
     c->err = (int *)take(64);
     c->flag = (int *)take(64);
@@ -1018,6 +1028,7 @@ bool zconfig_ok(const ctm_config *cfg, int irrep)
         return false;
     if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
     if (cfg->corner_mode != 0) return false;
+    if (cfg->deterministic != 0 && cfg->deterministic != 1) return false;
     const long long n = (long long)cfg->chi * cfg->D * cfg->D;
     if (n > 12000) return false;
     return qr_supported((int)(2 * n), 2 * cfg->chi) != 0;

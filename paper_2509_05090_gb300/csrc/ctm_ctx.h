@@ -53,6 +53,8 @@ struct ctm_ctx {
     size_t ack_cap[2];
     int ack_valid[2];
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
+    double *qr_gpart, *qr_spart;   // deterministic mode: per-CTA partial sums (else null)
+    int qr_gmax;
     unsigned *qr_bar;
     int *err, *flag;
     double *norm_part, *norm_part2;
@@ -111,6 +113,9 @@ inline QrScratch qr_scratch(ctm_ctx *c)
     q.sk_elems = 0;
     q.bar_extra = c->force_timeout ? 1u : 0u;
     q.spin_limit = c->force_timeout ? 20000 : 0;
+    q.gpart = c->qr_gpart;
+    q.spart = c->qr_spart;
+    q.gmax = c->qr_gmax;
     return q;
 }
 enum {

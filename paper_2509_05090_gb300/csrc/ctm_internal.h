@@ -110,10 +110,18 @@ struct QrScratch {
     size_t sk_elems;
     unsigned bar_extra;      // arrivals the grid barrier waits for beyond the grid (0; > 0 only to force a timeout)
     long long spin_limit;    // polls before a barrier wait gives up (0: the default, about a second)
+    // deterministic mode (null: FP64 atomics): per-CTA partial-sum slots for up to gmax CTAs
+    double *gpart;           // qr_det_gram_doubles(k, gmax)
+    double *spart;           // qr_det_s_doubles(k, gmax)
+    int gmax;
 };
 size_t qr_wy_doubles(int n, int k);   // V + S + W + ta + split-K scratch
 size_t qr_sk_doubles(int n, int k);   // the split-K scratch part
 size_t qr_scratch_doubles(int k);
+// deterministic QR: slots of partial sums for up to qr_det_gmax(n) CTAs
+size_t qr_det_gram_doubles(int k, int gmax);
+size_t qr_det_s_doubles(int k, int gmax);
+int qr_det_gmax(int n);
 size_t qr_rowbuf_doubles(int k);
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,
                            cudaStream_t st);

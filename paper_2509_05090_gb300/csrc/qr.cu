@@ -45,6 +45,7 @@
 namespace {
 
 constexpr int QR_THREADS = 512;
+constexpr int QR_DET_GMAX = 320;   // deterministic mode: partial-sum slots (CTAs) provided for
 constexpr int QB = 8;                     // panel width (columns per grid barrier)
 constexpr double QR_DOWNDATE_MIN = 1.0 / 16.0;   // smallest kept ratio of downdated / fresh norm^2
 constexpr long long QR_SPIN_LIMIT = 20000000LL;   // x ~64 ns sleep: ~1.3 s
@@ -76,6 +77,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned *count, unsigned G, unsign
     return *((volatile int *)err) == 0;
 }
 
+// sum_{c < G} p[c * stride] by a group of DET_LANES consecutive lanes: lane `part`
+// adds c = part, part + DET_LANES, ... (independent loads, one round of L2 latency), and
+// an xor butterfly adds the lanes' sums (every lane gets the same bits; the assignment
+// is fixed, so the result is the same on every run): the deterministic mode's
+// cross-CTA reduction.  All lanes of the group must call it.
+constexpr int DET_LANES = 16;
+__device__ __forceinline__ double det_sum(const double *p, size_t stride, int G, int part)
+{
+    double s = 0.0;
+    for (int c = part; c < G; c += DET_LANES) s += __ldcg(p + (size_t)c * stride);
+#pragma unroll
+    for (int o = DET_LANES / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o, DET_LANES);
+    return s;
+}
+
 struct QrArgs {
     int n, k, G, rows_per;
     const double *Y;
@@ -90,6 +106,10 @@ struct QrArgs {
     int *err;
     unsigned bar_extra;
     long long spin_limit;
+    // deterministic mode (non-null): each CTA writes its partial sums to its own slot
+    // and every reader adds the G slots in CTA order, instead of FP64 atomics
+    double *gpart;    // 2 x G x QB x k: partial Gram rows, by panel parity
+    double *spart;    // G x k x k: partial V^T V
 };
 
 // W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
@@ -228,7 +248,11 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     double *cfs = Ps + QB * k;                      // QB x k: tau_j v_j^T a_kk
     double *Rj = cfs + QB * k;                      // k: current row of R
     // (after the factorisation the region from Gs on holds the triangular solve's buffers)
-    auto acc_buf = [&](int blk) { return a.sbuf + (size_t)(blk % 3) * QB * k; };
+    const bool det = a.gpart != nullptr;
+    // atomics: three rotating accumulators; deterministic: this CTA's slot of panel parity blk
+    auto acc_buf = [&](int blk) {
+        return det ? a.gpart + ((size_t)(blk & 1) * a.G + c) * QB * k : a.sbuf + (size_t)(blk % 3) * QB * k;
+    };
     auto pub_buf = [&](int blk) { return a.rowbuf + (size_t)(blk & 1) * QB * k; };
 
     for (int t = tid; t < nr * k; t += blockDim.x) Ys[(t / k) * ld + t % k] = a.Y[(size_t)r0 * k + t];
@@ -289,7 +313,13 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             for (int i = 0; i < QB; ++i) {
                 double v = g[i];
                 for (int o = P >> 1; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o, P);
-                if (t < ncols * P && part == 0 && nrow > 0 && i < nn && j1 + i <= kk) atomicAdd(&acc[i * k + kk], v);
+                if (det) {
+                    // this CTA's slot: every entry of the panel's rows written, zero where
+                    // the CTA has no rows below the panel
+                    if (t < ncols * P && part == 0 && i < nn) acc[i * k + kk] = (nrow > 0 && j1 + i <= kk) ? v : 0.0;
+                } else if (t < ncols * P && part == 0 && nrow > 0 && i < nn && j1 + i <= kk) {
+                    atomicAdd(&acc[i * k + kk], v);
+                }
             }
         }
     };
@@ -311,17 +341,35 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     };
 
     int j0 = 0, nn0 = min(QB, k), blk = 0;
+    unsigned ep = 0;   // grid barriers passed
     gram_pass(0, 0, 0, nn0, acc_buf(0), pub_buf(0));
     while (j0 < k) {
         const double *acc = acc_buf(blk);
         const double *pub = pub_buf(blk);
-        if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 1), a.err, a.bar_extra, a.spin_limit)) return;
+        if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
+        if (det) {
+            // the G partial sums of each entry added in a fixed order, the entries shared
+            // out over the CTAs, into a.sbuf; one more barrier publishes them
+            const double *slots = a.gpart + (size_t)(blk & 1) * a.G * QB * k;
+            const int ne = nn0 * (k - j0), lane = tid & 31, part = tid % DET_LANES;
+            // entries by groups of lanes; whole warps iterate together (the groups shuffle)
+            for (int wb = c * blockDim.x + tid - lane; wb < ne * DET_LANES; wb += a.G * blockDim.x) {
+                const int u = wb + lane;
+                const int t = min(u / DET_LANES, ne - 1);
+                const int i = t / (k - j0), kk = j0 + t % (k - j0);
+                const double v = det_sum(slots + i * k + kk, (size_t)QB * k, a.G, part);
+                if (part == 0 && u / DET_LANES < ne && kk >= j0 + i) a.sbuf[i * k + kk] = v;
+            }
+            if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
+        }
         for (int t = tid; t < nn0 * (k - j0); t += blockDim.x) {
             const int i = t / (k - j0), kk = j0 + t % (k - j0);
-            Gs[i * k + kk] = (kk >= j0 + i) ? ((volatile const double *)acc)[i * k + kk] : 0.0;
+            double gv = 0.0;
+            if (kk >= j0 + i) gv = det ? __ldcg(a.sbuf + i * k + kk) : ((volatile const double *)acc)[i * k + kk];
+            Gs[i * k + kk] = gv;
             Ps[i * k + kk] = ((volatile const double *)pub)[i * k + kk];
         }
-        if (c == 0) {
+        if (c == 0 && !det) {
             double *z = a.sbuf + (size_t)((blk + 2) % 3) * QB * k;
             for (int t = tid; t < QB * k; t += blockDim.x) z[t] = 0.0;
         }
@@ -440,14 +488,31 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
             s1 = fma(Ys[(rl + 1) * ld + i], Ys[(rl + 1) * ld + j], s1);
         }
         if (rl < nr) s0 = fma(Ys[rl * ld + i], Ys[rl * ld + j], s0);
-        atomicAdd(&a.S[(size_t)i * k + j], s0 + s1);
+        if (det) a.spart[(size_t)c * k * k + e] = s0 + s1;
+        else atomicAdd(&a.S[(size_t)i * k + j], s0 + s1);
     }
-    if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 1), a.err, a.bar_extra, a.spin_limit)) return;
+    if (det) {
+        // slots of CTAs without rows at or below column j hold no entry: zero them
+        for (int e = tid; e < k * k; e += blockDim.x) {
+            const int i = e / k, j = e % k;
+            if (j >= i && max(0, j - r0) >= nr) a.spart[(size_t)c * k * k + e] = 0.0;
+        }
+        if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
+        // S = the G partials in a fixed order, each CTA a share of the entries
+        const int lane = tid & 31, part = tid % DET_LANES;
+        for (int wb = c * blockDim.x + tid - lane; wb < k * k * DET_LANES; wb += a.G * blockDim.x) {
+            const int u = wb + lane;
+            const int e = min(u / DET_LANES, k * k - 1);
+            const double v = det_sum(a.spart + e, (size_t)k * k, a.G, part);
+            if (part == 0 && u / DET_LANES < k * k && e % k >= e / k) a.S[e] = v;
+        }
+    }
+    if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
     for (int cb = c; cb < (k + QR_WC - 1) / QR_WC; cb += a.G) {   // a small grid solves several blocks
         wy_solve_cta(k, cb, a.S, a.V, taus, a.W, Gs);
         __syncthreads();
     }
-    if (!grid_barrier(a.bar, a.G, (unsigned)(blk + 2), a.err, a.bar_extra, a.spin_limit)) return;
+    if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
     // Q rows of this CTA: (E - V W) with column c negated where alpha_c < 0; a thread
     // owns one column and up to QR_QROWS rows at a time (W read once per row chunk)
     {
@@ -502,6 +567,9 @@ int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
 }  // namespace
 
 size_t qr_scratch_doubles(int k) { return (size_t)3 * QB * k + 8; }
+size_t qr_det_gram_doubles(int k, int gmax) { return (size_t)2 * gmax * QB * k; }
+size_t qr_det_s_doubles(int k, int gmax) { return (size_t)gmax * k * k; }
+int qr_det_gmax(int n) { return n < QR_DET_GMAX ? n : QR_DET_GMAX; }
 size_t qr_rowbuf_doubles(int k) { return (size_t)2 * QB * k; }
 
 int qr_supported(int n, int k)
@@ -533,8 +601,9 @@ static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y,
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(s.S, 0, sizeof(double) * (size_t)k * k, st);
     if (e != cudaSuccess) return e;
+    if (s.gpart && (!s.spart || G > s.gmax)) return cudaErrorInvalidValue;
     QrArgs a{n, k, G, rows_per, Y, R, Q, s.V, s.S, s.W, s.sbuf, s.rowbuf, s.bar, s.err, s.bar_extra,
-             s.spin_limit > 0 ? s.spin_limit : QR_SPIN_LIMIT};
+             s.spin_limit > 0 ? s.spin_limit : QR_SPIN_LIMIT, s.gpart, s.spart};
     void *args[] = {&a};
     CTM_COUNT_LAUNCH(1);
     return cudaLaunchCooperativeKernel((void *)qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st);

@@ -206,3 +206,38 @@ def test_pipelined_converge_matches_single_steps(ctm_lib, precision, k):
         assert _rel(_np(x), _np(y)) <= 1e-10
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_deterministic_mode_gives_bitwise_equal_replays(ctm_lib, precision):
+    """With cfg.deterministic the QR's cross-CTA sums are per-CTA partials added in CTA
+    order (no FP64 atomics): a context stepped one call at a time and another replaying a
+    captured multi-step graph reach bit-identical environments, and one step from the
+    oracle's environment still matches the oracle's factorisation."""
+    from paper_2509_05090_gb300 import binding
+    w = I.WORKLOADS["kitaev_D4_chi32"]
+    A = w.site_tensor()
+    g1 = binding.CTM(A, w.chi, precision=precision, n_split=5, deterministic=True)
+    g2 = binding.CTM(A, w.chi, precision=precision, n_split=5, deterministic=True)
+    for _ in range(12):
+        g1.ctm_step(1)
+    g2.ctm_step(1)
+    g2.ctm_step(11)
+    for x, y in zip(g1.ctm_get_env(), g2.ctm_get_env()):
+        assert np.array_equal(_np(x), _np(y))
+    g1.close()
+    g2.close()
+    ref = O.OracleCTM(A, w.chi)
+    ref.step()
+    ref.step()
+    g = binding.CTM(A, w.chi, precision="fp64", deterministic=True)
+    g.ctm_set_env(ref.C, ref.T, ref.Q)
+    g.ctm_step(1)
+    ref.step()
+    R_ref = ref.last["R"]
+    dR = np.abs(np.diag(R_ref))
+    lead = int(np.sum(dR / dR[0] >= 1e-8))
+    assert lead >= w.chi // 2
+    R = _np(g.ctm_get_intermediate("R"))
+    assert np.max(np.abs(R[:lead, :lead] - R_ref[:lead, :lead])) <= 1e-10 * dR[0]
+    g.close()
