@@ -314,3 +314,23 @@ def test_complex_pipelined_converge_matches_single_steps(ctm_lib, precision, k):
         assert np.abs(x - y).max() <= 1e-10 * np.abs(y).max()
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split_bf16"])
+def test_complex_deterministic_mode_bitwise_replays(ctm_lib, precision):
+    """cfg.deterministic on the complex path (its embedded real QR sums per-CTA partials in a
+    fixed order): eager single steps and a replayed multi-step graph give bit-identical
+    environments."""
+    from paper_2509_05090_gb300 import binding
+    v = I.coherent_state(2, (1.0, 1.0, 1.0))
+    A = I.complex_perturbed_product_site_tensor(v, 3, 0.2, 17)
+    g1 = binding.CTMComplex(A, 18, irrep="E", precision=precision, n_split=5, deterministic=True)
+    g2 = binding.CTMComplex(A, 18, irrep="E", precision=precision, n_split=5, deterministic=True)
+    for _ in range(8):
+        g1.ctm_complex_step(1)
+    g2.ctm_complex_step(1)
+    g2.ctm_complex_step(7)
+    for x, y in zip(g1.ctm_complex_get_env(), g2.ctm_complex_get_env()):
+        assert np.array_equal(_np(x), _np(y))
+    g1.close()
+    g2.close()
