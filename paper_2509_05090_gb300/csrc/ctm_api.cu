@@ -1232,6 +1232,11 @@ int ctm_debug_force_timeout(ctm_ctx *c, int enable)
     c->graph = nullptr;
     c->graph1 = nullptr;
     c->graph_steps = 0;
+    for (int h = 0; h < 2; ++h) {
+        if (c->pipe[h]) cudaGraphExecDestroy(c->pipe[h]);
+        c->pipe[h] = nullptr;
+    }
+    c->pipe_steps = 0;
     return CTM_OK;
 }
 

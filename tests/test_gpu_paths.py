@@ -129,6 +129,15 @@ def test_forced_wait_timeout_is_reported(ctm_lib, precision):
         g.ctm_step(1)
     assert ei.value.status == 6        # CTM_ETIMEOUT
     g.close()
+    # the same through ctm_converge's pipelined graphs (the error flag comes back with a
+    # chunk's deltas; a chunk already queued is drained before the call returns)
+    g = binding.CTM(A, w.chi, precision=precision, n_split=5)
+    g.ctm_step(2)
+    g.ctm_debug_force_timeout(True)
+    with pytest.raises(binding.CtmError) as ei:
+        g.ctm_converge(max_steps=20, tol=1e-300, check_every=2)
+    assert ei.value.status == 6
+    g.close()
     ref = O.OracleCTM(A, w.chi)
     g2 = binding.CTM(A, w.chi, precision=precision, n_split=5)
     for _ in range(5):
