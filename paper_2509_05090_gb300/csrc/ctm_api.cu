@@ -646,6 +646,22 @@ int graph_launch(ctm_ctx *c, int nsteps)
     return CTM_OK;
 }
 
+// Forget every captured graph (they hold launch arguments and the packed operand
+// state of the moment they were captured); the next calls capture again.
+void drop_graphs(ctm_ctx *c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph1) cudaGraphExecDestroy(c->graph1);
+    c->graph = nullptr;
+    c->graph1 = nullptr;
+    c->graph_steps = 0;
+    for (int h = 0; h < 2; ++h) {
+        if (c->pipe[h]) cudaGraphExecDestroy(c->pipe[h]);
+        c->pipe[h] = nullptr;
+    }
+    c->pipe_steps = 0;
+}
+
 // The two pipelined graphs of k steps (ring halves 0 and 1), the pinned ring grown
 // to k deltas per half first.  Leaves pipe_steps = 0 if capturing failed.
 static int capture_pipe(ctm_ctx *c, int k)
@@ -1203,11 +1219,7 @@ int ctm_set_site(ctm_ctx *c, const double *A_dev, int reset_env)
     CK(launch_double_layer(c->d, c->D, c->A, c->A, c->a, st));
     // the packed digits of the old double layer and the graphs that assumed them are stale
     c->apk_state[0] = c->apk_state[1] = 0;
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    if (c->graph1) cudaGraphExecDestroy(c->graph1);
-    c->graph = nullptr;
-    c->graph1 = nullptr;
-    c->graph_steps = 0;
+    drop_graphs(c);
     if (reset_env) {
         CK(launch_init_env(c->chi, c->D, c->a, c->C, c->T, c->Q, st));
         CK(launch_spectrum_init(c->chi, c->s, st));
@@ -1227,16 +1239,7 @@ int ctm_debug_force_timeout(ctm_ctx *c, int enable)
     CK(cudaStreamSynchronize(c->stream));
     c->force_timeout = enable ? 1 : 0;
     // captured graphs hold the QR's launch arguments: capture again with the new ones
-    if (c->graph) cudaGraphExecDestroy(c->graph);
-    if (c->graph1) cudaGraphExecDestroy(c->graph1);
-    c->graph = nullptr;
-    c->graph1 = nullptr;
-    c->graph_steps = 0;
-    for (int h = 0; h < 2; ++h) {
-        if (c->pipe[h]) cudaGraphExecDestroy(c->pipe[h]);
-        c->pipe[h] = nullptr;
-    }
-    c->pipe_steps = 0;
+    drop_graphs(c);
     return CTM_OK;
 }
 

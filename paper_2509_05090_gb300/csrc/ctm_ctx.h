@@ -134,5 +134,6 @@ int enqueue_enlarged_corner(ctm_ctx *c);
 int enqueue_step(ctm_ctx *c);
 int join_side(ctm_ctx *c);
 int read_status(ctm_ctx *c);
+void drop_graphs(ctm_ctx *c);   // forget captured graphs (launch arguments or packed state changed)
 cudaError_t rho_reduce(ctm_ctx *c);   // raw[pB][pA] = sum Y1o G2 (energy contraction)
 }  // namespace ctmi

@@ -250,3 +250,26 @@ def test_deterministic_mode_gives_bitwise_equal_replays(ctm_lib, precision):
     R = _np(g.ctm_get_intermediate("R"))
     assert np.max(np.abs(R[:lead, :lead] - R_ref[:lead, :lead])) <= 1e-10 * dR[0]
     g.close()
+
+
+def test_converge_after_set_site_uses_the_new_tensor(ctm_lib):
+    """ctm_set_site drops every captured graph (they assumed the old double layer's packed
+    digits): ctm_converge after swapping in a new tensor reaches the energy of a fresh
+    context on that tensor."""
+    from paper_2509_05090_gb300 import binding
+    w = I.WORKLOADS["heis_D2_chi8"]
+    h = w.hamiltonians()
+    A1 = w.site_tensor()
+    A2 = I.random_site_tensor(2, 2, 4242)
+    g = binding.CTM(A1, w.chi, precision="split_bf16", n_split=5)
+    g.ctm_converge(max_steps=200, tol=1e-11, check_every=1)
+    g.ctm_set_site(A2, reset_env=True)
+    _, _, ok = g.ctm_converge(max_steps=300, tol=1e-11, check_every=1)
+    E = g.ctm_energy(h)[1]
+    f = binding.CTM(A2, w.chi, precision="split_bf16", n_split=5)
+    _, _, okf = f.ctm_converge(max_steps=300, tol=1e-11, check_every=1)
+    Ef = f.ctm_energy(h)[1]
+    assert ok == okf
+    assert abs(E - Ef) <= 1e-9
+    g.close()
+    f.close()
