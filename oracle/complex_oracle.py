@@ -40,7 +40,11 @@ text; each is pinned by tests/test_complex_oracle.py):
     (A[s; z, x, y] = A[s; x, y, z]), so the apex bond is a z bond for both ends and
     E_site = (3/2) Re tr(rho h_z) (C3 symmetry makes the x, y, z bonds equal);
   * for the real A1 representation (U_g = I, no conjugation) every step reduces to
-    the real oracle.
+    the real oracle;
+  * transfer matrix (f2): the real path's column (edge, radial dimer, opposite edge,
+    one Bravais vector along the edge) with the opposite edge conj(T), the mirror
+    image of T as for the enlarged corner's column edge; then the spectrum is closed
+    under complex conjugation (the reflections' anti-unitarity).
 """
 from __future__ import annotations
 
@@ -198,6 +202,50 @@ def corner_spectrum(C):
     return w / np.linalg.norm(w)
 
 
+def transfer_apply(T, aB, aA, v):
+    """f2 for complex environments (Sec. II.C, Fig. 4a): TM v for the column transfer
+    matrix TM[(a,y,b),(g,w,h)] = sum T[a,u,g] aB[u,w,z] aA[z,x,y] conj(T[b,x,h]): one
+    edge, one radial dimer and the opposite edge, advancing one Bravais vector along
+    the edge (the real path's reading).  The opposite edge is the mirror image of T,
+    conj(T), as the column edge of the enlarged corner is.  Contracted one pair at a
+    time, v[g, w, h] in, out[a, y, b] out."""
+    chi, D2 = T.shape[0], T.shape[1]
+    V = np.asarray(v, dtype=np.complex128).reshape(chi, D2, chi)
+    P1 = np.einsum("aug,gwh->auwh", T, V, optimize=True)
+    P2 = np.einsum("auwh,uwz->ahz", P1, aB, optimize=True)
+    P3 = np.einsum("ahz,zxy->axyh", P2, aA, optimize=True)
+    return np.einsum("axyh,bxh->ayb", P3, T.conj(), optimize=True).reshape(-1)
+
+
+def transfer_matrix(T, aB, aA):
+    """The dense complex transfer matrix (chi D2 chi square; small cases)."""
+    chi, D2 = T.shape[0], T.shape[1]
+    N = chi * D2 * chi
+    TM = np.einsum("aug,uwz,zxy,bxh->aybgwh", T, aB, aA, T.conj(), optimize=True)
+    return TM.reshape(N, N)
+
+
+def transfer_spectrum(T, aB, aA, nev: int = 3, dense_max: int = 4096):
+    """The nev largest eigenvalue magnitudes of the transfer matrix normalised by the
+    largest (lambda_i = |lambda_i'| / |lambda_0'|), xi = -1 / ln lambda_1 (Bravais
+    steps) and the gap ln(lambda_1 / lambda_2) of the FCLS extrapolation (Eq. 3).
+    LAPACK's general eigenvalues on the dense matrix when it is small, else ARPACK on
+    transfer_apply."""
+    chi, D2 = T.shape[0], T.shape[1]
+    N = chi * D2 * chi
+    if N <= dense_max:
+        w = np.linalg.eigvals(transfer_matrix(T, aB, aA))
+    else:
+        import scipy.sparse.linalg as sla
+        op = sla.LinearOperator((N, N), matvec=lambda v: transfer_apply(T, aB, aA, v), dtype=np.complex128)
+        w = sla.eigs(op, k=max(nev, 3) + 2, which="LM", tol=1e-13, return_eigenvectors=False)
+    lam = np.sort(np.abs(w))[::-1][:nev]
+    lam = lam / lam[0]
+    xi = -1.0 / np.log(lam[1]) if lam[1] > 0.0 else 0.0
+    gap = np.log(lam[1] / lam[2]) if nev >= 3 and lam[2] > 0.0 else float("inf")
+    return lam, xi, gap
+
+
 class ComplexCTM:
     """QR-CTMRG of a complex C3v-symmetric tensor (irrep "E"; "A1" is the real case)."""
 
@@ -285,6 +333,10 @@ class ComplexCTM:
             Moo = enlarged_corner(self.C, self.T, bB, bA)
             raw[sA * d + sB, tA * d + tB] = np.trace(P5 @ (Q.conj().T @ Moo @ Q))
         return raw / np.trace(raw)
+
+    def transfer_spectrum(self, nev: int = 3):
+        """f2: leading transfer-matrix eigenvalue magnitudes of the current environment, xi, gap."""
+        return transfer_spectrum(self.T, self.aB, self.aA, nev)
 
     def energy(self, h):
         """(e_x, e_y, e_z, E_site): e_a = Re tr(rho_a h_a) on an a bond, E = (1/2) sum_a e_a."""

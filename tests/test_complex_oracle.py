@@ -13,7 +13,12 @@
   complex conjugate in the corner or the edge update breaks this;
 * C3 covariance of the bond energies of the Kitaev-Heisenberg model (e_x = e_y = e_z),
   which fixes the pairing of the rotation with the leg cycle;
-* QR and EVD projectors reach the same fixed point.
+* QR and EVD projectors reach the same fixed point;
+* the column transfer matrix (f2): a real A1 tensor gives the real oracle's matrix,
+  the matrix-free application equals the dense matrix, the spectrum is closed under
+  complex conjugation with a real leading eigenvalue (which fixes the conjugated
+  opposite edge; T on both sides breaks it), and a unitary change of the bond basis
+  leaves the spectrum unchanged.
 """
 import math
 
@@ -248,3 +253,72 @@ def test_qr_and_evd_reach_the_same_fixed_point():
     assert np.abs(qr.s - ev.s).max() < 1e-10
     h = _kh(2, -1.0, 0.3)
     assert abs(qr.energy(h)[1] - ev.energy(h)[1]) < 1e-10
+
+
+# ----------------------------------------------------------- transfer matrix (f2)
+def _random_e_env(seed, D=2, chi=6, steps=60):
+    from paper_2509_05090_gb300 import inputs as I
+    z = Z.ComplexCTM(I.random_complex_site_tensor(2, D, seed), chi)
+    z.converge(steps, 1e-11)
+    return z
+
+
+def test_transfer_a1_reduces_to_real_oracle():
+    """A real A1 tensor: the complex transfer matrix is the real oracle's (pinned there by
+    the exact Ising correlation length), entry by entry, with the same spectrum."""
+    rng = np.random.default_rng(23)
+    A = rng.standard_normal((2, 2, 2, 2))
+    real = O.OracleCTM(A, chi=6)
+    cplx = Z.ComplexCTM(A.astype(np.complex128), chi=6, irrep="A1")
+    for _ in range(6):
+        real.step()
+        cplx.step()
+    TMr = O.transfer_matrix(real.T, real.a, real.a)
+    TMc = Z.transfer_matrix(cplx.T, cplx.aB, cplx.aA)
+    assert np.abs(TMc.imag).max() < 1e-14
+    assert np.abs(TMc.real - TMr).max() < 1e-12 * np.abs(TMr).max()
+    lr, xr, gr = O.transfer_spectrum(real.T, real.a, real.a)
+    lc, xc, gc = cplx.transfer_spectrum()
+    assert np.abs(lr - lc).max() < 1e-10 and abs(xr - xc) < 1e-10
+
+
+def test_transfer_apply_is_the_dense_matrix():
+    z = _random_e_env(5)
+    rng = np.random.default_rng(2)
+    N = z.chi * z.D2 * z.chi
+    v = rng.standard_normal(N) + 1j * rng.standard_normal(N)
+    TM = Z.transfer_matrix(z.T, z.aB, z.aA)
+    assert np.abs(Z.transfer_apply(z.T, z.aB, z.aA, v) - TM @ v).max() < 1e-13 * np.abs(TM).max() * N
+
+
+@pytest.mark.parametrize("seed", [3, 9])
+def test_transfer_spectrum_closed_under_conjugation(seed):
+    """The reflections of the E-irrep state (anti-unitary) make the column transfer matrix
+    equal to its complex conjugate in the basis with the two edges exchanged, so its
+    spectrum is closed under conjugation and the leading eigenvalue is real.  That
+    holds only with the opposite edge conjugated: the same column with T on both sides
+    (a mistake planted here, in the oracle) loses it."""
+    z = _random_e_env(seed)
+    w = np.linalg.eigvals(Z.transfer_matrix(z.T, z.aB, z.aA))
+    w = w[np.argsort(-np.abs(w))]
+    scale = abs(w[0])
+    assert max(np.min(np.abs(w - np.conj(x))) for x in w[:12]) < 1e-12 * scale
+    assert abs(w[0].imag) < 1e-12 * scale and w[0].real > 0.0
+    chi, D2 = z.chi, z.D2
+    wrong = np.einsum("aug,uwz,zxy,bxh->aybgwh", z.T, z.aB, z.aA, z.T, optimize=True)
+    ww = np.linalg.eigvals(wrong.reshape(chi * D2 * chi, -1))
+    ww = ww[np.argsort(-np.abs(ww))]
+    assert max(np.min(np.abs(ww - np.conj(x))) for x in ww[:12]) > 1e-6 * abs(ww[0])
+
+
+def test_transfer_spectrum_gauge_invariant():
+    """A unitary change of the environment's bond basis, T -> U T U^H (and C, Q with it),
+    is a similarity of the transfer matrix: the same spectrum."""
+    z = _random_e_env(4)
+    rng = np.random.default_rng(12)
+    X = rng.standard_normal((z.chi, z.chi)) + 1j * rng.standard_normal((z.chi, z.chi))
+    U, _ = np.linalg.qr(X)
+    T2 = np.einsum("ab,bug,hg->auh", U, z.T, U.conj(), optimize=True)
+    l1, x1, g1 = Z.transfer_spectrum(z.T, z.aB, z.aA)
+    l2, x2, g2 = Z.transfer_spectrum(T2, z.aB, z.aA)
+    assert np.abs(l1 - l2).max() < 1e-12 and abs(x1 - x2) < 1e-10 and abs(g1 - g2) < 1e-8
