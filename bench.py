@@ -494,9 +494,17 @@ def complex_record(steps, n_split, fp64_peak, bf16_peak, with_oracle=True):
         torch.cuda.synchronize()
         secs = time.perf_counter() - t0
         eb, E, _ = g.ctm_complex_energy(h)
-        g.close()
         conv[prec] = {"steps": nst, "delta": dl, "converged": ok, "seconds": secs, "E_site": E,
                       "e_bond": [float(x) for x in eb]}
+        if prec == "split_bf16":
+            # the transfer-matrix spectrum of the converged complex environment (Sec. II.C)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            lam, xi, gap, iters, sok = g.ctm_complex_transfer_spectrum(nev=3, max_iter=200, tol=1e-9)
+            conv[prec]["transfer_spectrum"] = {"tol": 1e-9, "lambda": [float(x) for x in lam], "xi_bravais": xi,
+                                               "ln_lambda1_over_lambda2": gap, "iterations": iters,
+                                               "converged": sok, "seconds": time.perf_counter() - t1}
+        g.close()
     if with_oracle:
         from oracle import complex_oracle as zorc
         t0 = time.perf_counter()

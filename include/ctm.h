@@ -370,6 +370,20 @@ int ctm_complex_set_env(ctm_complex_ctx *ctx, const double *C_dev, const double 
  * site tensor, 6 the double layer (D2^3), 7 C, 8 T.  Synchronous. */
 int ctm_complex_get_intermediate(const ctm_complex_ctx *ctx, int which, double *dst_dev, size_t count);
 
+/* Sec. II.C for complex environments: the leading eigenvalue magnitudes of the column
+ * transfer matrix TM[(a,y,b),(g,w,h)] = sum T[a,u,g] aB[u,w,z] aA[z,x,y] conj(T[b,x,h])
+ * (the opposite edge is the mirror image of T), normalised by the largest, with
+ * xi = -1/ln lambda_1 and ln(lambda_1/lambda_2) as for ctm_transfer_spectrum.  The
+ * subspace iteration of the real path runs on the operator's real form (vectors
+ * [Re v | Im v]); the spectrum is closed under conjugation, so each magnitude appears
+ * twice there and every second one is kept.  nev: 2 or 3.  tws: device workspace of
+ * ctm_complex_transfer_workspace_bytes bytes (256-byte aligned).  Overwrites the
+ * step's scratch intermediates.  Synchronous. */
+size_t ctm_complex_transfer_workspace_bytes(const ctm_complex_ctx *ctx, int nev);
+int ctm_complex_transfer_spectrum(ctm_complex_ctx *ctx, int nev, int max_iter, double tol, void *tws,
+                                  size_t tws_bytes, double *lambda_host, double *xi_host, double *gap_host,
+                                  int *iters_out);
+
 void ctm_complex_destroy(ctm_complex_ctx *ctx);
 
 /* Release the host context (the caller frees the workspace). */

@@ -100,6 +100,9 @@ def load(path: str = LIB_PATH):
         "ctm_transfer_workspace_bytes": (ctypes.c_size_t, [P, I]),
         "ctm_transfer_spectrum": (I, [P, I, I, ctypes.c_double, P, ctypes.c_size_t, dp, dp, dp,
                                       ctypes.POINTER(I)]),
+        "ctm_complex_transfer_workspace_bytes": (ctypes.c_size_t, [P, I]),
+        "ctm_complex_transfer_spectrum": (I, [P, I, I, ctypes.c_double, P, ctypes.c_size_t, dp, dp, dp,
+                                              ctypes.POINTER(I)]),
     }
     for name, (res, args) in sigs.items():
         f = getattr(lib, name)
@@ -430,6 +433,22 @@ class CTMComplex:
             raise CtmError(st, "ctm_complex_energy")
         r = np.array(rho[:])
         return np.array(e[:]), es.value, (r[0::2] + 1j * r[1::2]).reshape(dd, dd)
+
+    def ctm_complex_transfer_spectrum(self, nev=3, max_iter=2000, tol=1e-12):
+        """(lambda[0..nev) normalised magnitudes, xi, ln(lambda_1/lambda_2), iterations, converged)
+        of the complex environment's column transfer matrix."""
+        torch = _torch()
+        nbytes = int(load().ctm_complex_transfer_workspace_bytes(self._h, int(nev)))
+        if nbytes == 0:
+            raise CtmError(1, "ctm_complex_transfer_workspace_bytes")
+        tws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        lam = (ctypes.c_double * nev)()
+        xi, gap, it = ctypes.c_double(), ctypes.c_double(), ctypes.c_int()
+        st = load().ctm_complex_transfer_spectrum(self._h, int(nev), int(max_iter), float(tol), _ptr(tws), nbytes,
+                                                  lam, ctypes.byref(xi), ctypes.byref(gap), ctypes.byref(it))
+        if st not in (CTM_OK, CTM_ENOTCONVERGED):
+            raise CtmError(st, "ctm_complex_transfer_spectrum")
+        return np.array(lam[:]), xi.value, gap.value, it.value, st == CTM_OK
 
     def ctm_complex_get_env(self):
         torch = _torch()

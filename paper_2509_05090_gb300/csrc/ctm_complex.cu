@@ -1203,6 +1203,79 @@ int zcheck_env_finite(ctm_complex_ctx *c)
     return f ? CTM_ENONFINITE : CTM_OK;
 }
 
+// ------------------------------------------------------------------ transfer spectrum (f2)
+// The column transfer matrix of the complex environment (Sec. II.C),
+//   TM[(a,y,b),(g,w,h)] = sum T[a,u,g] aB[u,w,z] aA[z,x,y] conj(T[b,x,h])
+// (the opposite edge is the mirror image of T), is applied as the edge update's first
+// three contractions with v in place of Q, then a contraction with conj(T) over
+// (x, h).  The real path's subspace iteration runs on its real form (vectors
+// [Re v | Im v]), whose spectrum holds each magnitude of the complex one twice.
+
+// [Re v | Im v] (N each) -> five planes [Re, -Im, Re, Im, Re] of stride N
+__global__ void zc_tr_expand_kernel(long long N, const double *v2, double *v5)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < N; t += (long long)gridDim.x * blockDim.x) {
+        const double re = v2[t], im = v2[N + t];
+        v5[t] = re;
+        v5[N + t] = -im;
+        v5[2 * N + t] = re;
+        v5[3 * N + t] = im;
+        v5[4 * N + t] = re;
+    }
+}
+
+// T's row-blocked five planes (row r = (b,x) holds 5 chi values) -> plain planes of stride N
+__global__ void zc_tr_unblock_kernel(long long N, int chi, const double *T, double *Tp)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < 5 * N;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long p = t / N, e = t - p * N, r = e / chi, h = e - r * chi;
+        Tp[t] = T[r * 5 * chi + p * chi + h];
+    }
+}
+
+size_t ztransfer_layout(const ctm_complex_ctx *c, int m, char *base, double **Vq, double **Tp, void **sub)
+{
+    const long long N = (long long)c->chi * c->D2 * c->chi;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    *sub = take(subspace_workspace_bytes(2 * N, m));
+    *Vq = (double *)take(sizeof(double) * 5 * (size_t)N);
+    *Tp = (double *)take(sizeof(double) * 5 * (size_t)N);
+    return off;
+}
+
+// out2 = TM v2 for vectors [Re | Im] of length N each
+int ztransfer_apply(ctm_complex_ctx *c, const double *v2, double *out2, double *Vq, const double *Tp)
+{
+    const int chi = c->chi, D2 = c->D2;
+    const long long n = c->n, N = n * chi, DD = (long long)D2 * D2;
+    int rc;
+    ZLAUNCH(zc_tr_expand_kernel, zgrid(N), 256, N, v2, Vq);
+    // P1[a][h][u][w] = sum_g T[(a,u),g] v[(g,w),h]   (into X, as H1' of the edge update)
+    ZGemm z{(int)n, (int)n, chi, c->T, chi, 1, idx_lin(5LL * chi), idx_lin(1), 0, Vq, N, idx_lin(n),
+            idx_split(D2, 1, chi), 0, c->X, DD, 0, idx_split(D2, (long long)chi * 2 * DD, D2),
+            idx_split(D2, 2 * DD, 1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // P2[(a,h)][z] = P1[(a,h),(u,w)] aB[(u,w),z]
+    z = ZGemm{chi * chi, D2, D2 * D2, c->X, DD, 0, idx_lin(2 * DD), idx_lin(1), 0, c->a, c->Pa, idx_lin(D2),
+              idx_lin(1), 0, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // P3[a][y][x][h] = P2[(a,h),z] aA[z,x,y]
+    z = ZGemm{chi * chi, D2 * D2, D2, c->Y1, D2, 0, idx_lin(2LL * D2), idx_lin(1), 0, c->aA, c->Pa, idx_lin(DD),
+              idx_split(D2, 1, D2), 0, c->H, c->PM, 0, idx_split(chi, DD * chi, 1),
+              idx_split(D2, (long long)D2 * chi, chi)};
+    if ((rc = zgemm(c, z)) != CTM_OK) return rc;
+    // out[(a,y)][b] = sum_{(x,h)} P3[(a,y),(x,h)] conj(T[b,(x,h)])
+    z = ZGemm{(int)n, chi, (int)n, c->H, c->PM, 0, idx_lin(n), idx_lin(1), 0, Tp, N, idx_lin(1), idx_lin(n), 1,
+              out2, N, 0, idx_lin(chi), idx_lin(1)};
+    return zgemm(c, z);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1725,6 +1798,44 @@ void ctm_complex_destroy(ctm_complex_ctx *c)
     if (c->ring_h) cudaFreeHost(c->ring_h);
     if (c->ring_err_h) cudaFreeHost(c->ring_err_h);
     delete c;
+}
+
+size_t ctm_complex_transfer_workspace_bytes(const ctm_complex_ctx *c, int nev)
+{
+    if (!c || nev < 2 || 2 * nev + 5 > SUBSPACE_MAXV) return 0;
+    double *Vq, *Tp;
+    void *sub;
+    return ztransfer_layout(c, 2 * nev + 5, nullptr, &Vq, &Tp, &sub);
+}
+
+int ctm_complex_transfer_spectrum(ctm_complex_ctx *c, int nev, int max_iter, double tol, void *tws, size_t tws_bytes,
+                                  double *lambda_host, double *xi_host, double *gap_host, int *iters_out)
+{
+    if (!c || !tws || !lambda_host || nev < 2 || 2 * nev + 5 > SUBSPACE_MAXV || max_iter < 1) return CTM_EINVAL;
+    if ((uintptr_t)tws % 256 != 0) return CTM_EINVAL;
+    if (tws_bytes < ctm_complex_transfer_workspace_bytes(c, nev)) return CTM_ENOMEM;
+    if (tol <= 0.0) tol = 1e-12;
+    if (c->side_pending) {
+        ZK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
+        c->side_pending = 0;
+    }
+    const int m = 2 * nev + 5;
+    const long long N = (long long)c->chi * c->D2 * c->chi;
+    double *Vq, *Tp;
+    void *sub;
+    ztransfer_layout(c, m, (char *)tws, &Vq, &Tp, &sub);
+    ZLAUNCH(zc_tr_unblock_kernel, zgrid(5 * N), 256, N, c->chi, c->T, Tp);
+    SubspaceWork sw{c->stream, c->splitk, c->splitk_elems, c->err};
+    int rc = subspace_spectrum(
+        sw, 2 * N, m, nev, 2, max_iter, tol, sub,
+        [c, Vq, Tp](const double *v, double *out) {
+            return ztransfer_apply(c, v, out, Vq, Tp) == CTM_OK ? cudaSuccess : cudaErrorUnknown;
+        },
+        lambda_host, iters_out);
+    if (rc != CTM_OK && rc != CTM_ENOTCONVERGED) return rc;
+    if (xi_host) *xi_host = lambda_host[1] > 0.0 ? -1.0 / log(lambda_host[1]) : 0.0;
+    if (gap_host) *gap_host = (nev >= 3 && lambda_host[2] > 0.0) ? log(lambda_host[1] / lambda_host[2]) : INFINITY;
+    return rc;
 }
 
 }  // extern "C"

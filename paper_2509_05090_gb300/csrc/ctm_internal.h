@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <functional>
+
 #include "../../include/ctm.h"
 
 // Two-level index map: off(i) = (i / div) * s1 + (i % div) * s2.  A plain
@@ -97,6 +99,27 @@ cudaError_t gemm_tf32(const GemmF64 &g, int T, SplitWork w, cudaStream_t st, cud
 // and R (k x k) row-major.  One cooperative kernel: the blocked factorisation (one
 // grid barrier per panel), then Q in compact-WY form and the sign gauge (two more
 // grid barriers).
+// Subspace iteration for the leading eigenvalue magnitudes of a matrix-free real operator
+// (transfer.cu; the transfer-matrix spectra of the real and the complex path): the
+// stream, the FP64 GEMM's split-K scratch and a device error flag read at each check.
+struct SubspaceWork {
+    cudaStream_t stream;
+    double *splitk;
+    size_t splitk_elems;
+    const int *err;
+};
+constexpr int SUBSPACE_MAXV = 12;   // vectors in the subspace
+size_t subspace_workspace_bytes(long long N, int m);
+// apply(v, out): out = Op v for device vectors of length N, enqueued on s.stream.  pairs
+// = 1: the magnitudes as they come; 2: Op is the real form of a complex operator whose
+// spectrum is closed under conjugation, so every magnitude appears twice and every
+// second one is kept.  mags (host, nev) gets the leading magnitudes over the largest;
+// returns CTM_OK when they moved by less than tol between checks (else
+// CTM_ENOTCONVERGED with the last estimates).
+int subspace_spectrum(const SubspaceWork &s, long long N, int m, int nev, int pairs, int max_iter, double tol,
+                      void *tws, const std::function<cudaError_t(const double *, double *)> &apply, double *mags,
+                      int *iters_out);
+
 struct QrScratch {
     double *sbuf;      // qr_scratch_doubles(k): rotating column-sum accumulators
     double *rowbuf;    // qr_rowbuf_doubles(k): published panel rows

@@ -32,7 +32,7 @@
 
 namespace {
 
-constexpr int TR_MAXV = 12;   // vectors in the subspace
+constexpr int TR_MAXV = SUBSPACE_MAXV;
 
 struct cplx {
     double re, im;
@@ -251,18 +251,17 @@ static cudaError_t transfer_apply(ctm_ctx *c, const double *v, double *out)
     return run_gemm(c, g);
 }
 
-static size_t transfer_layout(const ctm_ctx *c, int m, char *base, double **V, double **W, double **G, double **Rinv,
+static size_t subspace_layout(long long N, int m, char *base, double **V, double **W, double **G, double **Rinv,
                               double **H, double **lam, int **flag)
 {
-    const size_t N = (size_t)c->chi * c->D2 * c->chi;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
         char *p = base ? base + off : nullptr;
         off += align_up(bytes);
         return p;
     };
-    *V = (double *)take(sizeof(double) * N * m);
-    *W = (double *)take(sizeof(double) * N * m);
+    *V = (double *)take(sizeof(double) * (size_t)N * m);
+    *W = (double *)take(sizeof(double) * (size_t)N * m);
     *G = (double *)take(sizeof(double) * m * m);
     *Rinv = (double *)take(sizeof(double) * m * m);
     *H = (double *)take(sizeof(double) * m * m);
@@ -272,16 +271,16 @@ static size_t transfer_layout(const ctm_ctx *c, int m, char *base, double **V, d
 }
 
 // V <- orthonormal basis of span(W) (Cholesky QR twice), W used as scratch.
-static cudaError_t orthonormalise(ctm_ctx *c, int m, long long N, double *W, double *V, double *G, double *Rinv,
-                                  int *flag)
+static cudaError_t orthonormalise(const SubspaceWork &s, int m, long long N, double *W, double *V, double *G,
+                                  double *Rinv, int *flag)
 {
-    cudaStream_t st = c->stream;
+    cudaStream_t st = s.stream;
     double *src = W, *dst = V;
     for (int pass = 0; pass < 2; ++pass) {
         // G = src^T src (m x m over N), vectors stored one after another
         GemmF64 g{m, m, (int)N, src, idx_lin(N), idx_lin(1), src, idx_lin(1), idx_lin(N), G, idx_lin(m), idx_lin(1),
                   1.0, 0.0};
-        cudaError_t e = gemm_f64(g, gemm_f64_pick_split(m, m, (int)N), c->splitk, c->splitk_elems, st);
+        cudaError_t e = gemm_f64(g, gemm_f64_pick_split(m, m, (int)N), s.splitk, s.splitk_elems, st);
         if (e != cudaSuccess) return e;
         CTM_COUNT_LAUNCH(1);
         tr_chol_kernel<<<1, 32, 0, st>>>(m, G, Rinv, flag);
@@ -289,7 +288,7 @@ static cudaError_t orthonormalise(ctm_ctx *c, int m, long long N, double *W, dou
         // dst = src Rinv: row r of the (N x m) matrix whose column j is vector j
         g = GemmF64{(int)N, m, m, src, idx_lin(1), idx_lin(N), Rinv, idx_lin(m), idx_lin(1), dst, idx_lin(1),
                     idx_lin(N), 1.0, 0.0};
-        if ((e = gemm_f64(g, 1, c->splitk, c->splitk_elems, st)) != cudaSuccess) return e;
+        if ((e = gemm_f64(g, 1, s.splitk, s.splitk_elems, st)) != cudaSuccess) return e;
         double *t = src;
         src = dst;
         dst = t;
@@ -302,14 +301,74 @@ static cudaError_t orthonormalise(ctm_ctx *c, int m, long long N, double *W, dou
 
 using namespace ctmi;
 
+size_t subspace_workspace_bytes(long long N, int m)
+{
+    double *V, *W, *G, *Rinv, *H, *lam;
+    int *flag;
+    return subspace_layout(N, m, nullptr, &V, &W, &G, &Rinv, &H, &lam, &flag);
+}
+
+int subspace_spectrum(const SubspaceWork &s, long long N, int m, int nev, int pairs, int max_iter, double tol,
+                      void *tws, const std::function<cudaError_t(const double *, double *)> &apply, double *mags,
+                      int *iters_out)
+{
+    if (m < 2 || m > TR_MAXV || nev < 1 || pairs * (nev - 1) >= m || max_iter < 1) return CTM_EINVAL;
+    double *V, *W, *G, *Rinv, *H, *lam;
+    int *flag;
+    subspace_layout(N, m, (char *)tws, &V, &W, &G, &Rinv, &H, &lam, &flag);
+    cudaStream_t st = s.stream;
+    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    CTM_COUNT_LAUNCH(1);
+    tr_init_kernel<<<256, 256, 0, st>>>(N * m, W);
+    CK(cudaGetLastError());
+    CK(orthonormalise(s, m, N, W, V, G, Rinv, flag));
+    double prev[TR_MAXV], cur[TR_MAXV];
+    for (int i = 0; i < m; ++i) prev[i] = -1.0;
+    const int check = 5;
+    int it = 0;
+    bool done = false;
+    while (it < max_iter && !done) {
+        for (int j = 0; j < m; ++j) CK(apply(V + (size_t)j * N, W + (size_t)j * N));
+        ++it;
+        if (it % check == 0 || it == max_iter) {
+            // Rayleigh quotient H = V^T (Op V) and its eigenvalue magnitudes
+            GemmF64 g{m, m, (int)N, V, idx_lin(N), idx_lin(1), W, idx_lin(1), idx_lin(N), H, idx_lin(m), idx_lin(1),
+                      1.0, 0.0};
+            CK(gemm_f64(g, gemm_f64_pick_split(m, m, (int)N), s.splitk, s.splitk_elems, st));
+            CTM_COUNT_LAUNCH(1);
+            tr_eig_kernel<<<1, 32, 0, st>>>(m, H, lam, flag);
+            CK(cudaGetLastError());
+            CK(cudaMemcpyAsync(cur, lam, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+            int err = 0;
+            if (s.err) CK(cudaMemcpyAsync(&err, s.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (err) return CTM_ETIMEOUT;
+            // converged when every kept magnitude, normalised by the largest, moved by less
+            // than tol (absolute: magnitudes far below lambda_0 carry FP64 noise of order
+            // 1e-16 lambda_0)
+            done = true;
+            for (int i = 0; i < nev; ++i) {
+                const int k = i * pairs;
+                if (!isfinite(cur[k])) return CTM_ENONFINITE;
+                const double a = cur[k] / cur[0], b = prev[k] / (prev[0] > 0.0 ? prev[0] : 1.0);
+                if (!(fabs(a - b) <= tol)) done = false;
+            }
+            for (int i = 0; i < m; ++i) prev[i] = cur[i];
+        }
+        if (!done) CK(orthonormalise(s, m, N, W, V, G, Rinv, flag));
+    }
+    if (!(cur[0] > 0.0)) return CTM_ENONFINITE;
+    for (int i = 0; i < nev; ++i) mags[i] = cur[i * pairs] / cur[0];
+    if (iters_out) *iters_out = it;
+    return done ? CTM_OK : CTM_ENOTCONVERGED;
+}
+
 static int transfer_vectors(int nev) { return nev + 5 < TR_MAXV ? nev + 5 : TR_MAXV; }
 
 extern "C" size_t ctm_transfer_workspace_bytes(const ctm_ctx *c, int nev)
 {
     if (!c || nev < 2 || nev > TR_MAXV - 2) return 0;
-    double *V, *W, *G, *Rinv, *H, *lam;
-    int *flag;
-    return transfer_layout(c, transfer_vectors(nev), nullptr, &V, &W, &G, &Rinv, &H, &lam, &flag);
+    return subspace_workspace_bytes((long long)c->chi * c->D2 * c->chi, transfer_vectors(nev));
 }
 
 extern "C" int ctm_transfer_spectrum(ctm_ctx *c, int nev, int max_iter, double tol, void *tws, size_t tws_bytes,
@@ -319,53 +378,14 @@ extern "C" int ctm_transfer_spectrum(ctm_ctx *c, int nev, int max_iter, double t
     if ((uintptr_t)tws % 256 != 0) return CTM_EINVAL;
     if (tws_bytes < ctm_transfer_workspace_bytes(c, nev)) return CTM_ENOMEM;
     if (tol <= 0.0) tol = 1e-12;
-    const int m = transfer_vectors(nev);
-    const long long N = (long long)c->chi * c->D2 * c->chi;
-    double *V, *W, *G, *Rinv, *H, *lam;
-    int *flag;
-    transfer_layout(c, m, (char *)tws, &V, &W, &G, &Rinv, &H, &lam, &flag);
     if (join_side(c) != CTM_OK) return CTM_ECUDA;
-    cudaStream_t st = c->stream;
-    CK(cudaMemsetAsync(flag, 0, sizeof(int), st));
-    CTM_COUNT_LAUNCH(1);
-    tr_init_kernel<<<256, 256, 0, st>>>(N * m, W);
-    CK(cudaGetLastError());
-    CK(orthonormalise(c, m, N, W, V, G, Rinv, flag));
-    double prev[TR_MAXV], cur[TR_MAXV];
-    for (int i = 0; i < m; ++i) prev[i] = -1.0;
-    const int check = 5;
-    int it = 0;
-    bool done = false;
-    while (it < max_iter && !done) {
-        for (int j = 0; j < m; ++j) CK(transfer_apply(c, V + (size_t)j * N, W + (size_t)j * N));
-        ++it;
-        if (it % check == 0 || it == max_iter) {
-            // Rayleigh quotient H = V^T (TM V) and its eigenvalue magnitudes
-            GemmF64 g{m, m, (int)N, V, idx_lin(N), idx_lin(1), W, idx_lin(1), idx_lin(N), H, idx_lin(m), idx_lin(1),
-                      1.0, 0.0};
-            CK(gemm_f64(g, gemm_f64_pick_split(m, m, (int)N), c->splitk, c->splitk_elems, st));
-            CTM_COUNT_LAUNCH(1);
-            tr_eig_kernel<<<1, 32, 0, st>>>(m, H, lam, flag);
-            CK(cudaGetLastError());
-            CK(cudaMemcpyAsync(cur, lam, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
-            int rc = read_status(c);
-            if (rc != CTM_OK) return rc;
-            // converged when every normalised magnitude moved by less than tol (absolute:
-            // magnitudes far below lambda_0 carry FP64 noise of order 1e-16 lambda_0)
-            done = true;
-            for (int i = 0; i < nev; ++i) {
-                if (!isfinite(cur[i])) return CTM_ENONFINITE;
-                const double a = cur[i] / cur[0], b = prev[i] / (prev[0] > 0.0 ? prev[0] : 1.0);
-                if (!(fabs(a - b) <= tol)) done = false;
-            }
-            for (int i = 0; i < m; ++i) prev[i] = cur[i];
-        }
-        if (!done) CK(orthonormalise(c, m, N, W, V, G, Rinv, flag));
-    }
-    if (!(cur[0] > 0.0)) return CTM_ENONFINITE;
-    for (int i = 0; i < nev; ++i) lambda_host[i] = cur[i] / cur[0];
+    const long long N = (long long)c->chi * c->D2 * c->chi;
+    SubspaceWork sw{c->stream, c->splitk, c->splitk_elems, c->err};
+    int rc = subspace_spectrum(sw, N, transfer_vectors(nev), nev, 1, max_iter, tol, tws,
+                               [c](const double *v, double *out) { return transfer_apply(c, v, out); }, lambda_host,
+                               iters_out);
+    if (rc != CTM_OK && rc != CTM_ENOTCONVERGED) return rc;
     if (xi_host) *xi_host = lambda_host[1] > 0.0 ? -1.0 / log(lambda_host[1]) : 0.0;
     if (gap_host) *gap_host = (nev >= 3 && lambda_host[2] > 0.0) ? log(lambda_host[1] / lambda_host[2]) : INFINITY;
-    if (iters_out) *iters_out = it;
-    return done ? CTM_OK : CTM_ENOTCONVERGED;
+    return rc;
 }

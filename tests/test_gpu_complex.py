@@ -334,3 +334,22 @@ def test_complex_deterministic_mode_bitwise_replays(ctm_lib, precision):
         assert np.array_equal(_np(x), _np(y))
     g1.close()
     g2.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("split_bf16", 1e-8)])
+def test_complex_transfer_spectrum_matches_oracle(ctm_lib, precision, tol):
+    """f2 on the E irrep (Sec. II.C): the leading transfer-matrix magnitudes, xi and the
+    FCLS gap of a converged complex environment against the complex oracle (dense
+    eigenvalues), from the same environment."""
+    A = I.random_complex_site_tensor(2, 2, 9)
+    z = Z.ComplexCTM(A, 8)
+    z.converge(80, 1e-11)
+    lam_ref, xi_ref, gap_ref = z.transfer_spectrum(3)
+    g = _ctm(A, 8, precision=precision)
+    g.ctm_complex_set_env(z.C, z.T, z.Q)
+    lam, xi, gap, iters, ok = g.ctm_complex_transfer_spectrum(nev=3, max_iter=2000, tol=1e-12)
+    assert ok
+    assert np.abs(lam - lam_ref).max() < tol
+    assert abs(xi - xi_ref) < tol * 100 * max(1.0, xi_ref)
+    assert abs(gap - gap_ref) < 1e-4 * max(1.0, abs(gap_ref))
+    g.close()
