@@ -183,6 +183,24 @@ def dist_setup():
     return ws, rank, local
 
 
+def max_over_ranks(values, ws, device="cuda"):
+    """Each value's maximum over the ranks of the process group (the replicas' timings:
+    the job is as slow as its slowest rank); identity for one rank."""
+    if ws <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
+
+
+def replica_throughput(total_ms_max, steps, ws):
+    """Whole-job steps/s of ws independent replicas that each ran `steps` steps, timed by
+    the slowest rank's total_ms_max; and the ms per step."""
+    return ws * steps / (total_ms_max / 1e3), total_ms_max / steps
+
+
 def cpu_oracle_rate(w, budget_s=20.0, max_steps=None, threads=1):
     """The FP64 CPU oracle as it stands on bounded steps of the workload; threads = 0: all
     cores (its loops are OpenMP-parallel over output rows).  Returns (steps/s, steps,
@@ -693,13 +711,8 @@ def main():
     if ws > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    total_ms = e0.elapsed_time(e1)
-    t_max = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    total_ms = float(t_max.item())
-    ms_per_step = total_ms / args.steps
-    value = ws * args.steps / (total_ms / 1e3)
+    total_ms, = max_over_ranks([e0.elapsed_time(e1)], ws)
+    value, ms_per_step = replica_throughput(total_ms, args.steps, ws)
 
     # ---- profiled steps (same kernels, events between phases and around every
     # contraction launch; L2 flushed before each) for the roofline of the
@@ -868,10 +881,7 @@ def main():
         torch.cuda.synchronize()
         t_calls = time.perf_counter() - t1
         e2s.close()
-        tt = torch.tensor([t_e2e, t_calls], dtype=torch.float64, device="cuda")
-        if ws > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e, t_calls = (float(x) for x in tt.tolist())
+        t_e2e, t_calls = max_over_ranks([t_e2e, t_calls], ws)
         line["e2e"] = {"value": ws * args.steps / t_e2e, "unit": "steps/s",
                        "h2d_bytes_per_step": (A_host.numel() * 8 + h_host.numel() * 8) / args.steps,
                        "d2h_bytes_per_step": 8 + (4 + rho.size) * 8 / args.steps,
