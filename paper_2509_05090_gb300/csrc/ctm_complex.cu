@@ -85,6 +85,9 @@ struct ctm_complex_ctx {
 namespace {
 
 constexpr int ZMAX_D = 3;
+// the Hermitian corner of the spectrum kernel (two planes) fits one SM's shared memory up
+// to chi = 112; the QR of the 2n x 2chi embedding takes up to 256 columns
+constexpr int ZMAX_CHI = 112;
 constexpr int ZNORM_BLOCKS = 128;
 constexpr int ZRHO_BLOCKS = 128;
 constexpr int ZRHO_MAX_DD = 9;
@@ -1022,7 +1025,7 @@ bool zconfig_ok(const ctm_config *cfg, int irrep)
     if (cfg->d < 1 || cfg->d > ZMAX_D) return false;
     if (irrep == CTM_IRREP_E && cfg->d < 2) return false;
     if (cfg->D < 1 || cfg->D > 10) return false;
-    if (cfg->chi < 1 || cfg->chi > 80) return false;
+    if (cfg->chi < 1 || cfg->chi > ZMAX_CHI) return false;
     if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16 && cfg->precision != CTM_SPLIT_TF32 &&
         cfg->precision != CTM_FP32_TF32)
         return false;
@@ -1338,7 +1341,7 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess ||
             tf32_prepare() != cudaSuccess ||
             cudaFuncSetAttribute(zc_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ztridiag_launch_bytes(80)) != cudaSuccess) {
+                                 (int)ztridiag_launch_bytes(ZMAX_CHI)) != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
         }

@@ -128,34 +128,50 @@ constexpr int QR_WL = 4;      // lanes per dot product in the block update
 
 __device__ __forceinline__ int up_off(int k, int i, int j) { return i * k - (i * (i - 1)) / 2 + (j - i); }
 
+// Up to QR_WY_PACKED_MAX columns U is copied into shared memory (packed upper triangle);
+// beyond, the solve reads it from S in global memory (L2) and shared memory holds only
+// the block inverses and the CTA's W columns.
+constexpr int QR_WY_PACKED_MAX = 160;
+constexpr int QR_MAX_COLS = 256;   // the Q formation gives each column at least two threads
+__host__ __device__ inline bool wy_packed(int k) { return k <= QR_WY_PACKED_MAX; }
+
 size_t qr_wy_smem_bytes(int k)
 {
     const int nb = (k + QR_WB - 1) / QR_WB;
-    return sizeof(double) * ((size_t)k * (k + 1) / 2 + (size_t)nb * QR_WB * QR_WB + (size_t)k * QR_WC + k);
+    const size_t packed = wy_packed(k) ? (size_t)k * (k + 1) / 2 : 0;
+    return sizeof(double) * (packed + (size_t)nb * QR_WB * QR_WB + (size_t)k * QR_WC + k);
 }
 
+template <bool PACKED>
 __device__ void wy_solve_cta(int k, int cblk, const double *S, const double *V, const double *taus, double *W,
                              double *sm)
 {
     const int nb = (k + QR_WB - 1) / QR_WB;
-    double *Us = sm;                                   // k (k+1) / 2
-    double *Di = Us + (size_t)k * (k + 1) / 2;         // nb x 8 x 8 block inverses
-    double *Wc = Di + (size_t)nb * QR_WB * QR_WB;      // k x QR_WC
-    double *rd = Wc + (size_t)k * QR_WC;               // k reciprocal diagonal
+    double *Us = sm;                                               // PACKED: k (k+1) / 2
+    double *Di = Us + (PACKED ? (size_t)k * (k + 1) / 2 : 0);      // nb x 8 x 8 block inverses
+    double *Wc = Di + (size_t)nb * QR_WB * QR_WB;                  // k x QR_WC
+    double *rd = Wc + (size_t)k * QR_WC;                           // k reciprocal diagonal
     const int c0 = cblk * QR_WC;
     const int ncol = min(QR_WC, k - c0);
     const int tid = threadIdx.x;
-    for (int t = tid; t < k * k; t += blockDim.x) {
-        const int i = t / k, j = t % k;
-        if (j > i) Us[up_off(k, i, j)] = __ldcg(S + t);
-        else if (j == i) Us[up_off(k, i, i)] = (taus[i] == 0.0) ? 1.0 : 0.5 * __ldcg(S + t);
-    }
+    // U[i][j] (j >= i): striu(S) + diag(S)/2, a unit diagonal where tau = 0
+    auto uval = [&](int i, int j) -> double {
+        if (PACKED) return Us[up_off(k, i, j)];
+        if (j > i) return __ldcg(S + (size_t)i * k + j);
+        return (taus[i] == 0.0) ? 1.0 : 0.5 * __ldcg(S + (size_t)i * k + i);
+    };
+    if (PACKED)
+        for (int t = tid; t < k * k; t += blockDim.x) {
+            const int i = t / k, j = t % k;
+            if (j > i) Us[up_off(k, i, j)] = __ldcg(S + t);
+            else if (j == i) Us[up_off(k, i, i)] = (taus[i] == 0.0) ? 1.0 : 0.5 * __ldcg(S + t);
+        }
     for (int t = tid; t < k * QR_WC; t += blockDim.x) {
         const int i = t / QR_WC, cc = t % QR_WC;
         Wc[t] = (cc < ncol) ? __ldcg(V + (size_t)(c0 + cc) * k + i) : 0.0;
     }
     __syncthreads();
-    for (int i = tid; i < k; i += blockDim.x) rd[i] = 1.0 / Us[up_off(k, i, i)];
+    for (int i = tid; i < k; i += blockDim.x) rd[i] = 1.0 / uval(i, i);
     __syncthreads();
     // block inverses: thread (b, c) back-substitutes D_b x = e_c
     for (int t = tid; t < nb * QR_WB; t += blockDim.x) {
@@ -171,7 +187,7 @@ __device__ void wy_solve_cta(int k, int cblk, const double *S, const double *V, 
                     v = (r == cl) ? 1.0 : 0.0;
 #pragma unroll
                     for (int j = r + 1; j < QR_WB; ++j)
-                        if (j <= cl) v = fma(-Us[up_off(k, i0 + r, i0 + j)], x[j], v);
+                        if (j <= cl) v = fma(-uval(i0 + r, i0 + j), x[j], v);
                     v *= rd[i0 + r];
                 }
                 x[r] = v;
@@ -192,13 +208,14 @@ __device__ void wy_solve_cta(int k, int cblk, const double *S, const double *V, 
             const int i = i0 + pc / QR_WC, cc = pc % QR_WC;
             double s0 = 0.0, s1 = 0.0;
             if (i < i1) {
-                const double *u = Us + up_off(k, i, i) - i;   // u[j] = U[i][j] for j >= i
+                // u[j] = U[i][j] for j >= i (j > i here: the rows below the block)
+                const double *u = PACKED ? Us + up_off(k, i, i) - i : S + (size_t)i * k;
                 int j = i1 + lane;
                 for (; j + QR_WL < k; j += 2 * QR_WL) {
-                    s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
-                    s1 = fma(u[j + QR_WL], Wc[(j + QR_WL) * QR_WC + cc], s1);
+                    s0 = fma(PACKED ? u[j] : __ldcg(u + j), Wc[j * QR_WC + cc], s0);
+                    s1 = fma(PACKED ? u[j + QR_WL] : __ldcg(u + j + QR_WL), Wc[(j + QR_WL) * QR_WC + cc], s1);
                 }
-                if (j < k) s0 = fma(u[j], Wc[j * QR_WC + cc], s0);
+                if (j < k) s0 = fma(PACKED ? u[j] : __ldcg(u + j), Wc[j * QR_WC + cc], s0);
             }
             double sum = s0 + s1;
 #pragma unroll
@@ -509,7 +526,8 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     }
     if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
     for (int cb = c; cb < (k + QR_WC - 1) / QR_WC; cb += a.G) {   // a small grid solves several blocks
-        wy_solve_cta(k, cb, a.S, a.V, taus, a.W, Gs);
+        if (wy_packed(k)) wy_solve_cta<true>(k, cb, a.S, a.V, taus, a.W, Gs);
+        else wy_solve_cta<false>(k, cb, a.S, a.V, taus, a.W, Gs);
         __syncthreads();
     }
     if (!grid_barrier(a.bar, a.G, ++ep, a.err, a.bar_extra, a.spin_limit)) return;
@@ -575,7 +593,7 @@ size_t qr_rowbuf_doubles(int k) { return (size_t)2 * QB * k; }
 int qr_supported(int n, int k)
 {
     int G, rp;
-    return n >= k && k >= 1 && k <= 160 && qr_layout(n, k, 1, &G, &rp);
+    return n >= k && k >= 1 && k <= QR_MAX_COLS && qr_layout(n, k, 1, &G, &rp);
 }
 
 size_t qr_sk_doubles(int n, int k)

@@ -72,9 +72,11 @@ def test_complex_projection_and_double_layer(ctm_lib, d, D):
     g.close()
 
 
-@pytest.mark.parametrize("D,chi,seed", [(2, 8, 51), (3, 12, 52)])
+@pytest.mark.parametrize("D,chi,seed", [(2, 8, 51), (3, 12, 52), (2, 112, 53)])
 def test_complex_steps_fp64(ctm_lib, D, chi, seed):
-    """Random E-irrep tensors, ten steps in lockstep, each step from the oracle's environment."""
+    """Random E-irrep tensors, ten steps in lockstep, each step from the oracle's environment
+    (chi = 112: the embedded QR has 224 columns, beyond which U of its compact-WY solve no
+    longer fits shared memory and is read from L2)."""
     A = I.random_complex_site_tensor(2, D, seed)
     g = _ctm(A, chi)
     z = Z.ComplexCTM(A, chi)
@@ -226,7 +228,7 @@ def test_complex_rejects_bad_config(ctm_lib):
     from paper_2509_05090_gb300 import binding
     A = I.random_complex_site_tensor(2, 2, 3)
     with pytest.raises(binding.CtmError):
-        binding.CTMComplex(A, 81)                       # chi above the embedded QR's limit
+        binding.CTMComplex(A, 113)                      # chi above the spectrum kernel's limit
     with pytest.raises(binding.CtmError):
         binding.CTMComplex(A[:1], 4)                    # d = 1 has no E irrep
 
