@@ -86,8 +86,9 @@ typedef struct {
 } ctm_config;
 
 /* Bytes of device workspace ctm_init needs for this configuration (0 on a bad
- * config: d <= 3, D <= 12, chi <= 160, n = chi D^2 <= 20000, n_split 2..5 for
- * CTM_SPLIT_BF16).  Dominated by two n x n FP64 intermediates (enlarged corner and
+ * config: d <= 3, D <= 12, chi <= 224, n = chi D^2 <= 20000, n_split 2..5 for
+ * CTM_SPLIT_BF16; ctm_init also returns CTM_EUNSUPPORTED when the QR's row blocks
+ * would not fit shared memory on the device).  Dominated by two n x n FP64 intermediates (enlarged corner and
  * edge-chain buffers). */
 size_t ctm_workspace_bytes(const ctm_config *cfg);
 

@@ -259,7 +259,7 @@ bool config_ok(const ctm_config *cfg)
     if (!cfg) return false;
     if (cfg->d < 1 || cfg->d > 3) return false;
     if (cfg->D < 1 || cfg->D > 12) return false;
-    if (cfg->chi < 1 || cfg->chi > 160) return false;
+    if (cfg->chi < 1 || cfg->chi > 224) return false;   // the corner spectrum's limit
     if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16 && cfg->precision != CTM_SPLIT_TF32 &&
         cfg->precision != CTM_FP32_TF32)
         return false;
@@ -855,6 +855,8 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     if (!cfg || !A_dev || !workspace) return CTM_EINVAL;
     if (!config_ok(cfg)) return CTM_EINVAL;
     if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
+    // the QR's row blocks must fit shared memory on this device's SM count
+    if (!qr_supported(cfg->chi * cfg->D * cfg->D, cfg->chi)) return CTM_EUNSUPPORTED;
     ctm_ctx *c = new (std::nothrow) ctm_ctx;
     if (!c) return CTM_ENOMEM;
     memset(c, 0, sizeof(*c));

@@ -193,6 +193,8 @@ __global__ void scale_by_partials_kernel(long long count, double *x, const doubl
 constexpr int SPEC_WARPS = 1;   // one eigenvalue per CTA: the chi Sturm chains spread over chi SMs
 constexpr int TRI_THREADS = 256;
 constexpr size_t SPEC_SM_ALONE_BYTES = 220 * 1024;   // within the 224 KB opt-in of spectrum_prepare
+constexpr int TRI_FULL_MAX = 160;   // the full corner in shared memory up to here, its lower triangle beyond
+constexpr int SPEC_MAX_CHI = 224;   // the lower triangle of a 224 x 224 corner: 197 KB
 
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const double *C, double *work)
 {
@@ -271,6 +273,80 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const dou
     }
 }
 
+// The same reduction with only the lower triangle in shared memory (packed rows; the
+// mat-vec reads the upper part through the symmetry), for corners too large for the
+// full matrix: chi > TRI_FULL_MAX.
+__device__ __forceinline__ int lo_off(int i, int j) { return i * (i + 1) / 2 + j; }   // i >= j
+
+__global__ void __launch_bounds__(TRI_THREADS) tridiag_packed_kernel(int chi, const double *C, double *work)
+{
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    __shared__ double sh_beta, sh_alpha;
+    double *A = sm;                                    // chi (chi + 1) / 2
+    double *v = A + (size_t)chi * (chi + 1) / 2;       // chi
+    double *p = v + chi;                               // chi
+    const int tid = threadIdx.x;
+    for (int t = tid; t < chi * chi; t += blockDim.x) {
+        const int i = t / chi, j = t % chi;
+        if (j <= i) A[lo_off(i, j)] = 0.5 * (C[t] + C[(size_t)j * chi + i]);
+    }
+    __syncthreads();
+    for (int kc = 0; kc + 2 < chi; ++kc) {
+        const int b0 = kc + 1, m = chi - b0;
+        double part = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) {
+            const double x = A[lo_off(b0 + i, kc)];
+            v[i] = x;
+            if (i > 0) part += x * x;
+        }
+        const double tail = block_sum(part, red);
+        if (tail == 0.0) continue;
+        const double x0 = v[0];
+        if (tid == (int)blockDim.x - 1) {
+            const double nrm = sqrt(tail + x0 * x0);
+            const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+            sh_alpha = alpha;
+            sh_beta = 1.0 / (nrm * (nrm + fabs(x0)));
+        }
+        for (int i = tid; i < m; i += blockDim.x) {
+            const int r = b0 + i;
+            const double *row = A + lo_off(r, b0);   // A[r][b0 + j] for j <= i
+            double s0 = 0.0, s1 = 0.0;
+            int j = 0;
+            for (; j + 1 <= i; j += 2) {
+                s0 = fma(row[j], v[j], s0);
+                s1 = fma(row[j + 1], v[j + 1], s1);
+            }
+            if (j <= i) s0 = fma(row[j], v[j], s0);
+            for (j = i + 1; j < m; ++j) s1 = fma(A[lo_off(b0 + j, r)], v[j], s1);   // A[r][b0+j] = A[b0+j][r]
+            p[i] = s0 + s1;
+        }
+        __syncthreads();
+        const double beta = sh_beta, alpha = sh_alpha;
+        for (int i = tid; i < m; i += blockDim.x) p[i] = beta * fma(-alpha, A[lo_off(b0 + i, b0)], p[i]);
+        if (tid == 0) v[0] = x0 - alpha;
+        __syncthreads();
+        double pv = 0.0;
+        for (int i = tid; i < m; i += blockDim.x) pv += p[i] * v[i];
+        pv = block_sum(pv, red);
+        const double Kf = 0.5 * beta * pv;
+        for (int i = tid; i < m; i += blockDim.x) p[i] -= Kf * v[i];   // p <- w
+        __syncthreads();
+        for (int t = tid; t < m * m; t += blockDim.x) {
+            const int i = t / m, j = t % m;
+            if (j <= i) A[lo_off(b0 + i, b0 + j)] -= v[i] * p[j] + p[i] * v[j];
+        }
+        if (tid == 0) A[lo_off(b0, kc)] = alpha;
+        __syncthreads();
+    }
+    for (int i = tid; i < chi; i += blockDim.x) {
+        work[i] = A[lo_off(i, i)];
+        double e = (i + 1 < chi) ? A[lo_off(i + 1, i)] : 0.0;
+        work[chi + i] = e * e;
+    }
+}
+
 // Number of eigenvalues of the tridiagonal (d, e2) below x: the sign changes of
 // p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}.  Only the recurrence itself is FP64
 // arithmetic (three operations per step -- GB300's FP64 pipe is narrow); the zero
@@ -309,7 +385,7 @@ __device__ __forceinline__ int sturm_count(int chi, const double *d, const doubl
 
 __global__ void bisect_kernel(int chi, const double *work, double *lam)
 {
-    __shared__ double d[160], e2[160];
+    __shared__ double d[SPEC_MAX_CHI], e2[SPEC_MAX_CHI];
     for (int i = threadIdx.x; i < chi; i += blockDim.x) {
         d[i] = work[i];
         e2[i] = work[chi + i];
@@ -346,7 +422,7 @@ __global__ void spectrum_finish_kernel(int chi, const double *lam_in, double *s_
                                        double *delta)
 {
     __shared__ double red[33];
-    __shared__ double lam[160], srt[160];
+    __shared__ double lam[SPEC_MAX_CHI], srt[SPEC_MAX_CHI];
     const int tid = threadIdx.x;
     for (int i = tid; i < chi; i += blockDim.x) lam[i] = fabs(lam_in[i]);
     __syncthreads();
@@ -493,16 +569,18 @@ size_t spectrum_work_doubles(int chi) { return (size_t)3 * chi + 8; }
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
                             double *work, cudaStream_t st, bool reserve_sm)
 {
-    if (chi > 160 || !work) return cudaErrorInvalidValue;
+    if (chi > SPEC_MAX_CHI || !work) return cudaErrorInvalidValue;
     // reserve_sm: the tridiagonalisation runs beside a lone instance's step for ~0.4 ms on
     // one SM; asking for (nearly) all of the SM's shared memory keeps the step's CTAs off
     // that SM, whose CTAs it would otherwise slow (a grid-synchronous QR waits for its
     // slowest CTA): measured 0.892 -> 0.872 ms per step at D = 6, chi = 72.  (Not inside a
     // batch, where many spectra run at once.)
-    size_t smem = sizeof(double) * ((size_t)chi * (chi | 1) + 2 * (size_t)chi);
+    const bool full = chi <= TRI_FULL_MAX;
+    size_t smem = sizeof(double) * ((full ? (size_t)chi * (chi | 1) : (size_t)chi * (chi + 1) / 2) + 2 * (size_t)chi);
     if (reserve_sm && smem < SPEC_SM_ALONE_BYTES) smem = SPEC_SM_ALONE_BYTES;
     CTM_COUNT_LAUNCH(3);
-    tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
+    if (full) tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
+    else tridiag_packed_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
@@ -515,7 +593,7 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
 cudaError_t launch_spectrum_from_tridiag(int chi, double *work, double *s_new, const double *s_old, double *delta,
                                         cudaStream_t st)
 {
-    if (chi > 160 || !work) return cudaErrorInvalidValue;
+    if (chi > SPEC_MAX_CHI || !work) return cudaErrorInvalidValue;
     CTM_COUNT_LAUNCH(2);
     bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
     cudaError_t e = cudaGetLastError();
@@ -547,5 +625,7 @@ cudaError_t launch_check_finite(long long count, const double *x, int *flag, cud
 
 cudaError_t spectrum_prepare()
 {
-    return cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tridiag_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
 }

@@ -156,6 +156,14 @@ def test_single_step_matches_oracle_chi144(ctm_lib):
     _step_parity(I.random_site_tensor(2, 3, 77), 144, 2)
 
 
+@pytest.mark.parametrize("chi", [192, 224])
+def test_single_step_matches_oracle_wide(ctm_lib, chi):
+    """chi = 192 and 224 at D = 3: the QR's compact-WY solve reads U from L2 (more than 160
+    columns) and the corner spectrum keeps only C's lower triangle in shared memory."""
+    O.set_threads(0)
+    _step_parity(I.random_site_tensor(2, 3, 78), chi, 2)
+
+
 @pytest.mark.parametrize("name,pre", [("kh_D6_chi72_conv", 1), ("kitaev_D4_chi32_conv", 3)])
 def test_single_step_matches_oracle_rank_deficient(ctm_lib, name, pre):
     """Converging near-product states: R falls below 1e-8 R_00 after ~16 / 37 columns, so
