@@ -249,9 +249,11 @@ def transfer_spectrum(T, aB, aA, nev: int = 3, dense_max: int = 4096):
 class ComplexCTM:
     """QR-CTMRG of a complex C3v-symmetric tensor (irrep "E"; "A1" is the real case)."""
 
-    def __init__(self, A, chi: int, irrep: str = "E", symmetrize: bool = True, projector: str = "qr"):
+    def __init__(self, A, chi: int, irrep: str = "E", symmetrize: bool = True, projector: str = "qr",
+                 corner: str = "qmq"):
         A = np.asarray(A, dtype=np.complex128)
         self.projector = projector      # "qr" (Sec. II.B) or "evd" (the conventional Fig. 3c projector)
+        self.corner = corner            # "qmq" (Fig. 3a) or "r": the cheap variant from R
         self.A = project(A, irrep) if symmetrize else A / np.linalg.norm(A)
         self.irrep = irrep
         self.d, self.D = self.A.shape[0], self.A.shape[1]
@@ -293,8 +295,14 @@ class ComplexCTM:
 
     def step(self):
         M = enlarged_corner(self.C, self.T, self.aB, self.aA)
+        S = np.where(np.real(np.diag(self.C)) < 0.0, -1.0, 1.0)
         Y, Q, R = self._projector(M)
-        Cr = Q.conj().T @ M @ Q
+        if self.corner == "r":
+            # the cheap variant (Sec. II.B, Fig. 3d): R S = Q^H M Q_prev, which is Q^H M Q once
+            # Q = Q_prev; S = diag(sgn C_jj) of the corner that entered the step
+            Cr = R * S[None, :]
+        else:
+            Cr = Q.conj().T @ M @ Q
         Cn = 0.5 * (Cr + Cr.conj().T)
         Cn = Cn / np.linalg.norm(Cn)
         chi, D2 = self.chi, self.D2

@@ -377,7 +377,7 @@ class CTMComplex:
     Complex tensors go in and out as torch.complex128 on the current CUDA device."""
 
     def __init__(self, A, chi, irrep="E", precision="fp64", n_split=5, tol=1e-10, max_steps=200, symmetrize=True,
-                 stream=None, deterministic=False):
+                 stream=None, deterministic=False, corner="qmq"):
         torch = _torch()
         lib = load()
         A = _complex_dev(A, torch)
@@ -388,7 +388,7 @@ class CTMComplex:
         self.D2 = D * D
         self.n = self.chi * self.D2
         self.irrep = IRREPS[irrep] if isinstance(irrep, str) else int(irrep)
-        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize, deterministic=deterministic)
+        self.cfg = make_config(d, D, chi, precision, n_split, tol, max_steps, symmetrize, corner, deterministic)
         nbytes = int(lib.ctm_complex_workspace_bytes(ctypes.byref(self.cfg), self.irrep))
         if nbytes == 0:
             raise CtmError(1, "ctm_complex_workspace_bytes")

@@ -519,6 +519,18 @@ __global__ void zc_warm_start_kernel(long long n, int chi, const double *Q, long
     }
 }
 
+// The cheap corner variant: Cr = R S with S = diag(sgn Re C_jj) of the corner that entered the
+// step (two planes each)
+__global__ void zc_rs_kernel(int chi, const double *R, long long PR, const double *C, double *Cr, long long PCr)
+{
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < chi * chi; t += gridDim.x * blockDim.x) {
+        const int j = t % chi;
+        const double sg = C[(long long)j * chi + j] < 0.0 ? -1.0 : 1.0;
+        Cr[t] = sg * R[t];
+        Cr[PCr + t] = sg * R[PR + t];
+    }
+}
+
 // E[(r,c),(j,c')] = [[Re y, -Im y], [Im y, Re y]][c][c'] (2n x 2k, row-major)
 __global__ void zc_embed_kernel(long long n, int k, const double *Y, long long PY, double *E)
 {
@@ -1030,7 +1042,7 @@ bool zconfig_ok(const ctm_config *cfg, int irrep)
         cfg->precision != CTM_FP32_TF32)
         return false;
     if (cfg->precision == CTM_SPLIT_BF16 && !split_supported_T(cfg->n_split)) return false;
-    if (cfg->corner_mode != 0) return false;
+    if (cfg->corner_mode != 0 && cfg->corner_mode != 1) return false;
     if (cfg->deterministic != 0 && cfg->deterministic != 1) return false;
     const long long n = (long long)cfg->chi * cfg->D * cfg->D;
     if (n > 12000) return false;
@@ -1108,6 +1120,16 @@ int zcorner(ctm_complex_ctx *c, double *Cout)
     return CTM_OK;
 }
 
+// Cheap corner variant (Sec. II.B, Fig. 3d): Cn = sym(R S)/|.|; R S = Qn^H M Q_prev exactly,
+// which is Qn^H M Qn at a fixed point
+int zcorner_from_r(ctm_complex_ctx *c, double *Cout)
+{
+    const int chi = c->chi;
+    ZLAUNCH(zc_rs_kernel, zgrid((long long)chi * chi), 256, chi, c->R, c->PC, c->C, c->Cr, c->PC);
+    ZLAUNCH(zc_herm_normalize_kernel, 1, 1024, chi, c->Cr, c->PC, Cout, c->PC);
+    return CTM_OK;
+}
+
 // Fig. 3b: T'[i,x,j] = sum conj(Q[(a,y),i]) T[a,u,g] a[u,w,z] aA[z,x,y] Q[(g,w),j], normalised
 int zedge(ctm_complex_ctx *c)
 {
@@ -1175,7 +1197,7 @@ int zstep(ctm_complex_ctx *c, int join_now)
         ZK(cudaStreamWaitEvent(c->stream, c->ev_join, 0));
         c->side_pending = 0;
     }
-    if ((rc = zcorner(c, c->Cn)) != CTM_OK) return rc;
+    if ((rc = c->cfg.corner_mode ? zcorner_from_r(c, c->Cn) : zcorner(c, c->Cn)) != CTM_OK) return rc;
     if (!c->spec_skip) {
         if ((rc = zspectrum(c, c->Cn, c->side, c->delta_dst)) != CTM_OK) return rc;
         c->side_pending = 1;

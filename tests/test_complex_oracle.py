@@ -322,3 +322,28 @@ def test_transfer_spectrum_gauge_invariant():
     l1, x1, g1 = Z.transfer_spectrum(z.T, z.aB, z.aA)
     l2, x2, g2 = Z.transfer_spectrum(T2, z.aB, z.aA)
     assert np.abs(l1 - l2).max() < 1e-12 and abs(x1 - x2) < 1e-10 and abs(g1 - g2) < 1e-8
+
+
+# ----------------------------------------------------- cheap corner variant (f4)
+def test_corner_from_r_identity_and_fixed_point():
+    """C' = sym(R S)/|.| (S = diag(sgn Re C_jj)): R S = Q^H M Q_prev at every step (the QR of
+    Y = M Q_prev S), and at a fixed point of the standard iteration whose Q is stationary
+    one step of the variant gives the standard corner."""
+    from paper_2509_05090_gb300 import inputs as I
+    z = Z.ComplexCTM(I.random_complex_site_tensor(2, 2, 5), 8, corner="r")
+    for _ in range(5):
+        Qp, Cp = z.Q.copy(), z.C.copy()
+        z.step()
+        M, Q, R = z.last["M"], z.last["Q"], z.last["R"]
+        S = np.where(np.real(np.diag(Cp)) < 0.0, -1.0, 1.0)
+        assert np.abs(R * S[None, :] - Q.conj().T @ M @ Qp).max() < 1e-13 * np.abs(M).max()
+    A = I.complex_perturbed_product_site_tensor(I.coherent_state(2, (1.0, 1.0, 1.0)), 2, 0.3, 7)
+    zs = Z.ComplexCTM(A, 6)
+    zs.converge(400, 1e-13)
+    std = Z.ComplexCTM(A, 6)
+    var = Z.ComplexCTM(A, 6, corner="r")
+    for x in (std, var):
+        x.set_env(zs.C, zs.T, zs.Q)
+        x.step()
+    assert np.abs(std.Q - zs.Q).max() < 1e-4          # Q stationary at this fixed point
+    assert np.abs(var.C - std.C).max() < 1e-11

@@ -379,3 +379,21 @@ def test_complex_transfer_spectrum_full_size(ctm_lib):
     assert np.abs(lam[1:] / lam_ref[1:] - 1.0).max() < 2e-2, (lam, lam_ref)
     assert abs(xi - xi_ref) < 1e-3 * xi_ref, (xi, xi_ref)
     g.close()
+
+
+def test_complex_corner_from_r_matches_oracle(ctm_lib):
+    """The cheap corner variant on the complex path (corner_mode 1): five FP64 steps, each
+    from the oracle's environment, against the oracle's variant."""
+    from paper_2509_05090_gb300 import binding
+    A = I.random_complex_site_tensor(2, 2, 61)
+    g = binding.CTMComplex(A, 8, irrep="E", precision="fp64", corner="r")
+    z = Z.ComplexCTM(A, 8, corner="r")
+    for k in range(5):
+        if k > 0:
+            g.ctm_complex_set_env(z.C, z.T, z.Q)
+        dg = g.ctm_complex_step()
+        dz = z.step()
+        Cg = _np(g.ctm_complex_get_intermediate("C"))
+        assert np.abs(Cg - z.C).max() < 1e-9, (k, np.abs(Cg - z.C).max())
+        assert abs(dg - dz) < 1e-9
+    g.close()
