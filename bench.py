@@ -627,6 +627,36 @@ def run_complex(args, w):
     return 0
 
 
+def chi_sweep_record(n_split, steps=3):
+    """Heisenberg D = 5 at chi = 120 ... 480 in split BF16 (the sweep of the paper's
+    per-iteration runtime figure): ms per step from a replayed graph of `steps` steps, the
+    profiled phases (QR on the main stream, corner spectrum on the side stream) and the
+    FP64-equivalent rate of the step.  chi > 224 runs the spectrum from global memory and,
+    where one SM's share of the rows does not fit shared memory, the QR from the slab."""
+    import torch
+    from paper_2509_05090_gb300 import binding, inputs
+    out = []
+    for chi in (120, 240, 360, 480):
+        w = inputs.WORKLOADS[f"heis_D5_chi{chi}"]
+        c = binding.CTM(w.site_tensor(), w.chi, precision="split_bf16", n_split=n_split)
+        c.ctm_step(1, want_delta=False)       # eager first step (autotuning)
+        c.ctm_step(steps, want_delta=False)   # capture + run the graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(c.stream)
+        c.ctm_step(steps, want_delta=False)
+        e1.record(c.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        ph = c.ctm_step_profiled()
+        c.close()
+        flops = step_gemm_flops(w.chi, w.D2)
+        out.append({"workload": w.name, "chi": chi, "n": w.n, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+                    "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12,
+                    "qr_ms": ph["qr"], "spectrum_ms": ph["spectrum"], "contractions_ms": ph["gemm_kernels"]})
+    return out
+
+
 def split_step_rate(w, steps, n_split, corner="qmq", precision="split_bf16"):
     import torch
     from paper_2509_05090_gb300 import binding
@@ -847,6 +877,7 @@ def main():
         line["tf32_modes"] = tf
         line["grad_d8_chi128"] = grad_record(fp64_peak)
         line["optimize_heisenberg_D3"] = optimize_record()
+        line["chi_sweep_heisenberg_D5"] = chi_sweep_record(args.n_split)
         line["batch96"] = batch_record(args, args.steps)
         line["complex_E_D6_chi72"] = complex_record(args.steps, args.n_split, fp64_peak, peaks["bf16_tflops"],
                                                     with_oracle=not args.no_compare)

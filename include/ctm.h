@@ -86,10 +86,13 @@ typedef struct {
 } ctm_config;
 
 /* Bytes of device workspace ctm_init needs for this configuration (0 on a bad
- * config: d <= 3, D <= 12, chi <= 224, n = chi D^2 <= 20000, n_split 2..5 for
- * CTM_SPLIT_BF16; ctm_init also returns CTM_EUNSUPPORTED when the QR's row blocks
- * would not fit shared memory on the device).  Dominated by two n x n FP64 intermediates (enlarged corner and
- * edge-chain buffers). */
+ * config: d <= 3, D <= 12, chi <= 512, n = chi D^2 <= 20000, n_split 2..5 for
+ * CTM_SPLIT_BF16; ctm_init also returns CTM_EUNSUPPORTED when the QR's per-CTA
+ * scratch would not fit shared memory on the device).  Where one SM's share of the
+ * QR's rows does not fit shared memory, the row blocks go to a slab of about
+ * n (chi + 1) doubles in this workspace; for chi > 224 the corner spectrum keeps
+ * C's lower triangle in it too.  Dominated by the n x n FP64 intermediates
+ * (enlarged corner and edge-chain buffers). */
 size_t ctm_workspace_bytes(const ctm_config *cfg);
 
 /* Sec. II.A-B: set up one instance.  A_dev: raw site tensor [s][i][j][k]

@@ -135,6 +135,8 @@ size_t layout(ctm_ctx *c, char *base)
     c->qr_sbuf = td((long long)qr_scratch_doubles((int)chi));
     c->qr_rowbuf = td((long long)qr_rowbuf_doubles((int)chi));
     c->qr_wy = td((long long)qr_wy_doubles((int)n, (int)chi));
+    c->qr_slab_elems = qr_slab_doubles((int)n, (int)chi, c->qr_force_slab);
+    c->qr_slab = c->qr_slab_elems ? td((long long)c->qr_slab_elems) : nullptr;
     if (c->cfg.deterministic) {
         c->qr_gmax = qr_det_gmax((int)n);
         c->qr_gpart = td((long long)qr_det_gram_doubles((int)chi, c->qr_gmax));
@@ -259,7 +261,7 @@ bool config_ok(const ctm_config *cfg)
     if (!cfg) return false;
     if (cfg->d < 1 || cfg->d > 3) return false;
     if (cfg->D < 1 || cfg->D > 12) return false;
-    if (cfg->chi < 1 || cfg->chi > 224) return false;   // the corner spectrum's limit
+    if (cfg->chi < 1 || cfg->chi > 512) return false;   // the QR's and the corner spectrum's limit
     if (cfg->precision != CTM_FP64 && cfg->precision != CTM_SPLIT_BF16 && cfg->precision != CTM_SPLIT_TF32 &&
         cfg->precision != CTM_FP32_TF32)
         return false;
@@ -844,6 +846,7 @@ size_t ctm_workspace_bytes(const ctm_config *cfg)
     c.n = (long long)c.chi * c.D2;
     c.split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
     c.tf32_T = tf32_slices(cfg->precision);
+    c.qr_force_slab = qr_force_slab_from_env();
     return layout(&c, nullptr);
 }
 
@@ -855,7 +858,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     if (!cfg || !A_dev || !workspace) return CTM_EINVAL;
     if (!config_ok(cfg)) return CTM_EINVAL;
     if ((uintptr_t)workspace % 256 != 0) return CTM_EINVAL;
-    // the QR's row blocks must fit shared memory on this device's SM count
+    // the QR's per-CTA scratch must fit shared memory (its row blocks may go to the slab)
     if (!qr_supported(cfg->chi * cfg->D * cfg->D, cfg->chi)) return CTM_EUNSUPPORTED;
     ctm_ctx *c = new (std::nothrow) ctm_ctx;
     if (!c) return CTM_ENOMEM;
@@ -869,6 +872,7 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
     c->split_T = (cfg->precision == CTM_SPLIT_BF16) ? cfg->n_split : 0;
     c->tf32_T = tf32_slices(cfg->precision);
     c->qr_rows_min = 1;
+    c->qr_force_slab = qr_force_slab_from_env();
     c->stream = (cudaStream_t)stream;
     if (!qr_supported((int)c->n, c->chi)) {
         delete c;

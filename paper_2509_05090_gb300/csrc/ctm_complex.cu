@@ -50,6 +50,8 @@ struct ctm_complex_ctx {
     size_t splitk_elems;
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
     double *qr_gpart, *qr_spart;   // deterministic mode: per-CTA partial sums of the embedded QR
+    double *qr_slab;               // the embedded QR's row blocks where they do not fit shared memory
+    size_t qr_slab_elems;
     int qr_gmax;
     unsigned *qr_bar;
     int *err, *flag;
@@ -914,6 +916,9 @@ QrScratch zqr_scratch(ctm_complex_ctx *c)
     q.gpart = c->qr_gpart;
     q.spart = c->qr_spart;
     q.gmax = c->qr_gmax;
+    q.yslab = c->qr_slab;
+    q.yslab_elems = c->qr_slab_elems;
+    q.force_slab = false;
     return q;
 }
 
@@ -990,6 +995,8 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->qr_sbuf = td((long long)qr_scratch_doubles((int)k2));
     c->qr_rowbuf = td((long long)qr_rowbuf_doubles((int)k2));
     c->qr_wy = td((long long)qr_wy_doubles((int)(2 * n), (int)k2));
+    c->qr_slab_elems = qr_slab_doubles((int)(2 * n), (int)k2);
+    c->qr_slab = c->qr_slab_elems ? td((long long)c->qr_slab_elems) : nullptr;
     if (c->cfg.deterministic) {
         c->qr_gmax = qr_det_gmax((int)(2 * n));
         c->qr_gpart = td((long long)qr_det_gram_doubles((int)k2, c->qr_gmax));

@@ -54,6 +54,9 @@ struct ctm_ctx {
     int ack_valid[2];
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
     double *qr_gpart, *qr_spart;   // deterministic mode: per-CTA partial sums (else null)
+    double *qr_slab;               // the QR's row blocks where they do not fit shared memory (else null)
+    size_t qr_slab_elems;
+    bool qr_force_slab;            // CTM_QR_SLAB=1 when the context was created
     int qr_gmax;
     unsigned *qr_bar;
     int *err, *flag;
@@ -116,6 +119,9 @@ inline QrScratch qr_scratch(ctm_ctx *c)
     q.gpart = c->qr_gpart;
     q.spart = c->qr_spart;
     q.gmax = c->qr_gmax;
+    q.yslab = c->qr_slab;
+    q.yslab_elems = c->qr_slab_elems;
+    q.force_slab = c->qr_force_slab;
     return q;
 }
 enum {

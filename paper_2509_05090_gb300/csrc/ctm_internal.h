@@ -137,6 +137,10 @@ struct QrScratch {
     double *gpart;           // qr_det_gram_doubles(k, gmax)
     double *spart;           // qr_det_s_doubles(k, gmax)
     int gmax;
+    // row blocks too tall for shared memory (qr_slab_doubles(n, k) > 0): a global slab
+    double *yslab;
+    size_t yslab_elems;
+    bool force_slab;   // the slab for every shape (CTM_QR_SLAB=1 at init: a check of that path)
 };
 size_t qr_wy_doubles(int n, int k);   // V + S + W + ta + split-K scratch
 size_t qr_sk_doubles(int n, int k);   // the split-K scratch part
@@ -146,6 +150,12 @@ size_t qr_det_gram_doubles(int k, int gmax);
 size_t qr_det_s_doubles(int k, int gmax);
 int qr_det_gmax(int n);
 size_t qr_rowbuf_doubles(int k);
+// doubles of the global slab that holds the QR's row blocks where one SM's share of the
+// rows does not fit shared memory (0 where it does)
+size_t qr_slab_doubles(int n, int k, bool force = false);
+// CTM_QR_SLAB=1 in the environment: contexts created from then on keep the QR's row blocks
+// in the slab for every shape (the same factorisation; a check of that path at small sizes)
+bool qr_force_slab_from_env();
 cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, QrScratch s,
                            cudaStream_t st);
 int qr_supported(int n, int k);

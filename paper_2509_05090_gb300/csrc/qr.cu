@@ -39,6 +39,7 @@
 // has, with a short spin limit; every CTA then gives up at its first barrier and
 // returns.
 #include <cooperative_groups.h>
+#include <cstdlib>
 
 #include "ctm_internal.h"
 
@@ -110,6 +111,8 @@ struct QrArgs {
     // and every reader adds the G slots in CTA order, instead of FP64 atomics
     double *gpart;    // 2 x G x QB x k: partial Gram rows, by panel parity
     double *spart;    // G x k x k: partial V^T V
+    // row blocks too tall for shared memory: CTA c's block at yslab + c * rows_per * (k | 1)
+    double *yslab;
 };
 
 // W = U^{-1} V_top^T with U = striu(S) + diag(S)/2 (unit diagonal where tau = 0).
@@ -132,7 +135,8 @@ __device__ __forceinline__ int up_off(int k, int i, int j) { return i * k - (i *
 // beyond, the solve reads it from S in global memory (L2) and shared memory holds only
 // the block inverses and the CTA's W columns.
 constexpr int QR_WY_PACKED_MAX = 160;
-constexpr int QR_MAX_COLS = 256;   // the Q formation gives each column at least two threads
+constexpr int QR_MAX_COLS = 512;   // the Q formation gives each column at least one thread
+constexpr size_t QR_SMEM_MAX = 200 * 1024;
 __host__ __device__ inline bool wy_packed(int k) { return k <= QR_WY_PACKED_MAX; }
 
 size_t qr_wy_smem_bytes(int k)
@@ -244,7 +248,10 @@ __device__ void wy_solve_cta(int k, int cblk, const double *S, const double *V, 
 
 constexpr int QR_QROWS = 8;   // rows per thread and pass in the Q formation
 
-__global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
+// GY: the CTA's row block lives in a global slab (L2) instead of shared memory, for
+// blocks too tall for it (large k or n); the algorithm and the access order are the same.
+template <bool GY>
+__global__ void __launch_bounds__(QR_THREADS, 1) qr_kernel(QrArgs a)
 {
     extern __shared__ double sm[];
     __shared__ int stop_sh[2];
@@ -255,8 +262,8 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     const int r1 = min(a.n, r0 + a.rows_per);
     const int nr = max(0, r1 - r0);
     const int tid = threadIdx.x;
-    double *Ys = sm;                                // rows_per x ld
-    double *taus = Ys + (size_t)a.rows_per * ld;    // k
+    double *Ys = GY ? a.yslab + (size_t)c * a.rows_per * ld : sm;   // rows_per x ld
+    double *taus = GY ? sm : Ys + (size_t)a.rows_per * ld;          // k
     double *v0s = taus + k;                         // k
     double *alps = v0s + k;                         // k
     double *g0 = alps + k;                          // QB: squared norms at the panel start
@@ -561,25 +568,38 @@ __global__ void __launch_bounds__(QR_THREADS) qr_kernel(QrArgs a)
     }
 }
 
-size_t qr_smem_bytes(int rows_per, int k)
+size_t qr_smem_bytes(int rows_per, int k, bool slab)
 {
     const size_t panel = 3 * (size_t)QB * k + k;
     const size_t solve = qr_wy_smem_bytes(k) / sizeof(double);
-    return sizeof(double) * ((size_t)rows_per * (k | 1) + 3 * (size_t)k + QB + (panel > solve ? panel : solve));
+    return sizeof(double) * ((slab ? 0 : (size_t)rows_per * (k | 1)) + 3 * (size_t)k + QB +
+                             (panel > solve ? panel : solve));
 }
 
-int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out)
+// Rows per CTA and the grid.  The kernel holds one CTA per SM (512 threads at ~100
+// registers), so the grid never exceeds the SM count: a floor rows_min above
+// ceil(n / #SM) that would not fit shared memory gives way down to ceil(n / #SM), and
+// where even that block does not fit, the row blocks go to a global slab (*slab_out).
+// A slab grid leaves two SMs free: the corner spectrum of the previous step, which
+// runs for milliseconds at such sizes and holds an SM, must not keep a CTA of the
+// grid-synchronous factorisation waiting.  Returns 0 when the kernel's other shared
+// memory does not fit either.
+int qr_layout(int n, int k, int rows_min, int *G_out, int *rows_out, bool *slab_out = nullptr, bool force_slab = false)
 {
-    int sms = device_sm_count();
-    int rows_per = (n + sms - 1) / sms;
-    if (rows_per < rows_min) rows_per = rows_min;
-    if (rows_per < 1) rows_per = 1;
-    // a floor that would not fit shared memory gives way (more CTAs)
-    while (rows_per > 1 && qr_smem_bytes(rows_per, k) > 200 * 1024) rows_per = (rows_per * 3) / 4;
-    int G = (n + rows_per - 1) / rows_per;
-    *G_out = G;
+    const int sms = device_sm_count();
+    int base = (n + sms - 1) / sms;
+    if (base < 1) base = 1;
+    int rows_per = rows_min > base ? rows_min : base;
+    while (rows_per > base && qr_smem_bytes(rows_per, k, false) > QR_SMEM_MAX) {
+        rows_per = (rows_per * 3) / 4;
+        if (rows_per < base) rows_per = base;
+    }
+    const bool slab = force_slab || qr_smem_bytes(rows_per, k, false) > QR_SMEM_MAX;
+    if (slab && sms > 4) rows_per = (n + sms - 3) / (sms - 2);
+    *G_out = (n + rows_per - 1) / rows_per;
     *rows_out = rows_per;
-    return qr_smem_bytes(rows_per, k) <= 200 * 1024;
+    if (slab_out) *slab_out = slab;
+    return qr_smem_bytes(rows_per, k, slab) <= QR_SMEM_MAX;
 }
 
 }  // namespace
@@ -589,6 +609,20 @@ size_t qr_det_gram_doubles(int k, int gmax) { return (size_t)2 * gmax * QB * k; 
 size_t qr_det_s_doubles(int k, int gmax) { return (size_t)gmax * k * k; }
 int qr_det_gmax(int n) { return n < QR_DET_GMAX ? n : QR_DET_GMAX; }
 size_t qr_rowbuf_doubles(int k) { return (size_t)2 * QB * k; }
+
+size_t qr_slab_doubles(int n, int k, bool force)
+{
+    int G, rp;
+    bool slab = false;
+    if (n < k || k < 1 || k > QR_MAX_COLS || !qr_layout(n, k, 1, &G, &rp, &slab, force) || !slab) return 0;
+    return (size_t)G * rp * (k | 1);
+}
+
+bool qr_force_slab_from_env()
+{
+    const char *e = getenv("CTM_QR_SLAB");
+    return e && e[0] == '1';
+}
 
 int qr_supported(int n, int k)
 {
@@ -609,9 +643,13 @@ static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y,
                                     cudaStream_t st)
 {
     const int G = (n + rows_per - 1) / rows_per;
-    const size_t smem = qr_smem_bytes(rows_per, k);
+    const bool slab = s.force_slab || qr_smem_bytes(rows_per, k, false) > QR_SMEM_MAX;
+    if (slab && (!s.yslab || s.yslab_elems < (size_t)G * rows_per * (k | 1))) return cudaErrorInvalidValue;
+    const size_t smem = qr_smem_bytes(rows_per, k, slab);
+    if (smem > QR_SMEM_MAX) return cudaErrorInvalidValue;
+    void (*kern)(QrArgs) = slab ? qr_kernel<true> : qr_kernel<false>;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel, QR_THREADS, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, QR_THREADS, smem);
     if (per_sm * device_sm_count() < G) return cudaErrorCooperativeLaunchTooLarge;
     cudaError_t e = cudaMemsetAsync(s.sbuf, 0, sizeof(double) * 3 * QB * k, st);
     if (e != cudaSuccess) return e;
@@ -621,10 +659,10 @@ static cudaError_t qr_factor_launch(int n, int k, int rows_per, const double *Y,
     if (e != cudaSuccess) return e;
     if (s.gpart && (!s.spart || G > s.gmax)) return cudaErrorInvalidValue;
     QrArgs a{n, k, G, rows_per, Y, R, Q, s.V, s.S, s.W, s.sbuf, s.rowbuf, s.bar, s.err, s.bar_extra,
-             s.spin_limit > 0 ? s.spin_limit : QR_SPIN_LIMIT, s.gpart, s.spart};
+             s.spin_limit > 0 ? s.spin_limit : QR_SPIN_LIMIT, s.gpart, s.spart, slab ? s.yslab : nullptr};
     void *args[] = {&a};
     CTM_COUNT_LAUNCH(1);
-    return cudaLaunchCooperativeKernel((void *)qr_kernel, dim3(G), dim3(QR_THREADS), args, smem, st);
+    return cudaLaunchCooperativeKernel((void *)kern, dim3(G), dim3(QR_THREADS), args, smem, st);
 }
 
 #include <map>
@@ -638,8 +676,9 @@ static std::map<std::pair<int, int>, int> g_qr_rows;   // (n, k) -> rows per CTA
 static int qr_pick_rows(int n, int k, const double *Y, double *Q, double *R, QrScratch s, cudaStream_t st)
 {
     int G, rp0;
-    qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp0);
-    if (s.rows_min > 1 || s.bar_extra) return rp0;
+    bool slab = false;
+    qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp0, &slab, s.force_slab);
+    if (s.rows_min > 1 || s.bar_extra || slab) return rp0;   // slab: one block per SM, nothing to tune
     {
         std::lock_guard<std::mutex> lk(g_qr_mu);
         auto it = g_qr_rows.find({n, k});
@@ -648,9 +687,9 @@ static int qr_pick_rows(int n, int k, const double *Y, double *Q, double *R, QrS
     const int tkey[2] = {n, k};
     int tval = 0;
     int per_sm = 0;
-    if (tune_cache_lookup("qr", tkey, 2, &tval, 1) && tval >= 1 && qr_smem_bytes(tval, k) <= 200 * 1024 &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel, QR_THREADS, qr_smem_bytes(tval, k)) ==
-            cudaSuccess &&
+    if (tune_cache_lookup("qr", tkey, 2, &tval, 1) && tval >= 1 && qr_smem_bytes(tval, k, false) <= QR_SMEM_MAX &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_kernel<false>, QR_THREADS,
+                                                      qr_smem_bytes(tval, k, false)) == cudaSuccess &&
         (long long)per_sm * device_sm_count() >= (n + tval - 1) / tval) {
         std::lock_guard<std::mutex> lk(g_qr_mu);
         g_qr_rows[{n, k}] = tval;
@@ -666,7 +705,8 @@ static int qr_pick_rows(int n, int k, const double *Y, double *Q, double *R, QrS
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return rp0;
     // fewer rows than rp0 puts several CTAs on an SM (the launch checks they all fit)
     for (int rp : {rp0, 8, 12, 16, 24, 32, 48, 64, 96, 128}) {
-        if ((rp < rp0 && rp * 2 < rp0) || (rp != rp0 && rp < 8) || qr_smem_bytes(rp, k) > 200 * 1024) continue;
+        if ((rp < rp0 && rp * 2 < rp0) || (rp != rp0 && rp < 8) || qr_smem_bytes(rp, k, false) > QR_SMEM_MAX)
+            continue;
         float ms = 1e30f;
         for (int rep = 0; rep < 4; ++rep) {   // first run warms up; the fastest of three counts
             float t = 0.f;
@@ -709,7 +749,8 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
 {
     int G, rp;
     if (!qr_supported(n, k) || !s.V) return cudaErrorInvalidValue;
-    if (!qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp) && !qr_layout(n, k, 1, &G, &rp))
+    if (!qr_layout(n, k, s.rows_min > 0 ? s.rows_min : 1, &G, &rp, nullptr, s.force_slab) &&
+        !qr_layout(n, k, 1, &G, &rp, nullptr, s.force_slab))
         return cudaErrorInvalidValue;
     const int rows_per = qr_pick_rows(n, k, Y, Q, R, s, st);
     return qr_factor_launch(n, k, rows_per, Y, Q, R, s, st);
@@ -717,5 +758,7 @@ cudaError_t qr_householder(int n, int k, const double *Y, double *Q, double *R, 
 
 cudaError_t qr_prepare()
 {
-    return cudaFuncSetAttribute(qr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaError_t e = cudaFuncSetAttribute(qr_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_MAX);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(qr_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, QR_SMEM_MAX);
 }

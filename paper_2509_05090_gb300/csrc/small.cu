@@ -194,7 +194,12 @@ constexpr int SPEC_WARPS = 1;   // one eigenvalue per CTA: the chi Sturm chains 
 constexpr int TRI_THREADS = 256;
 constexpr size_t SPEC_SM_ALONE_BYTES = 220 * 1024;   // within the 224 KB opt-in of spectrum_prepare
 constexpr int TRI_FULL_MAX = 160;   // the full corner in shared memory up to here, its lower triangle beyond
-constexpr int SPEC_MAX_CHI = 224;   // the lower triangle of a 224 x 224 corner: 197 KB
+constexpr int TRI_SMEM_MAX = 224;   // the lower triangle of a 224 x 224 corner: 197 KB of shared memory
+constexpr int SPEC_MAX_CHI = 512;   // beyond TRI_SMEM_MAX the lower triangle lives in the work buffer (L2)
+
+// offset (doubles) of the global lower triangle in the spectrum's work buffer, after
+// d, e^2 (2 chi) and the eigenvalues (chi)
+__host__ __device__ inline size_t tri_global_off(int chi) { return (size_t)3 * chi + 8; }
 
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const double *C, double *work)
 {
@@ -273,19 +278,23 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_kernel(int chi, const dou
     }
 }
 
-// The same reduction with only the lower triangle in shared memory (packed rows; the
-// mat-vec reads the upper part through the symmetry), for corners too large for the
-// full matrix: chi > TRI_FULL_MAX.
+// The same reduction with only the lower triangle stored (packed rows; the mat-vec reads
+// the upper part through the symmetry), for corners too large for the full matrix:
+// chi > TRI_FULL_MAX.  GA: the triangle lives in the work buffer (global memory, L2
+// resident: 1 MB at chi = 512) instead of shared memory, for chi > TRI_SMEM_MAX; the
+// steps are the same, and __syncthreads orders the block's global accesses as it does
+// its shared ones.
 __device__ __forceinline__ int lo_off(int i, int j) { return i * (i + 1) / 2 + j; }   // i >= j
 
+template <bool GA>
 __global__ void __launch_bounds__(TRI_THREADS) tridiag_packed_kernel(int chi, const double *C, double *work)
 {
     extern __shared__ double sm[];
     __shared__ double red[33];
     __shared__ double sh_beta, sh_alpha;
-    double *A = sm;                                    // chi (chi + 1) / 2
-    double *v = A + (size_t)chi * (chi + 1) / 2;       // chi
-    double *p = v + chi;                               // chi
+    double *A = GA ? work + tri_global_off(chi) : sm;         // chi (chi + 1) / 2
+    double *v = GA ? sm : A + (size_t)chi * (chi + 1) / 2;    // chi
+    double *p = v + chi;                                      // chi
     const int tid = threadIdx.x;
     for (int t = tid; t < chi * chi; t += blockDim.x) {
         const int i = t / chi, j = t % chi;
@@ -385,7 +394,8 @@ __device__ __forceinline__ int sturm_count(int chi, const double *d, const doubl
 
 __global__ void bisect_kernel(int chi, const double *work, double *lam)
 {
-    __shared__ double d[SPEC_MAX_CHI], e2[SPEC_MAX_CHI];
+    extern __shared__ double sm[];
+    double *d = sm, *e2 = sm + chi;   // 2 chi
     for (int i = threadIdx.x; i < chi; i += blockDim.x) {
         d[i] = work[i];
         e2[i] = work[chi + i];
@@ -564,7 +574,10 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
     return cudaGetLastError();
 }
 
-size_t spectrum_work_doubles(int chi) { return (size_t)3 * chi + 8; }
+size_t spectrum_work_doubles(int chi)
+{
+    return tri_global_off(chi) + (chi > TRI_SMEM_MAX ? (size_t)chi * (chi + 1) / 2 : 0);
+}
 
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
                             double *work, cudaStream_t st, bool reserve_sm)
@@ -575,15 +588,18 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
     // that SM, whose CTAs it would otherwise slow (a grid-synchronous QR waits for its
     // slowest CTA): measured 0.892 -> 0.872 ms per step at D = 6, chi = 72.  (Not inside a
     // batch, where many spectra run at once.)
-    const bool full = chi <= TRI_FULL_MAX;
-    size_t smem = sizeof(double) * ((full ? (size_t)chi * (chi | 1) : (size_t)chi * (chi + 1) / 2) + 2 * (size_t)chi);
+    const bool full = chi <= TRI_FULL_MAX, global = chi > TRI_SMEM_MAX;
+    size_t smem = sizeof(double) * ((full ? (size_t)chi * (chi | 1) : global ? 0 : (size_t)chi * (chi + 1) / 2) +
+                                    2 * (size_t)chi);
     if (reserve_sm && smem < SPEC_SM_ALONE_BYTES) smem = SPEC_SM_ALONE_BYTES;
     CTM_COUNT_LAUNCH(3);
     if (full) tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
-    else tridiag_packed_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
+    else if (!global) tridiag_packed_kernel<false><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
+    else tridiag_packed_kernel<true><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
+    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 2 * sizeof(double) * chi, st>>>(
+        chi, work, work + 2 * chi);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, work + 2 * chi, s_new, s_old, delta);
@@ -595,7 +611,8 @@ cudaError_t launch_spectrum_from_tridiag(int chi, double *work, double *s_new, c
 {
     if (chi > SPEC_MAX_CHI || !work) return cudaErrorInvalidValue;
     CTM_COUNT_LAUNCH(2);
-    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 0, st>>>(chi, work, work + 2 * chi);
+    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 2 * sizeof(double) * chi, st>>>(
+        chi, work, work + 2 * chi);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, work + 2 * chi, s_new, s_old, delta);
@@ -627,5 +644,7 @@ cudaError_t spectrum_prepare()
 {
     cudaError_t e = cudaFuncSetAttribute(tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tridiag_packed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    e = cudaFuncSetAttribute(tridiag_packed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(tridiag_packed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
 }

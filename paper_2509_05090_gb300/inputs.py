@@ -237,6 +237,11 @@ WORKLOADS = {
     "kitaev_E_D6_chi72": Workload("kitaev_E_D6_chi72", 2, 6, 72, -1.0, 0.0, 1011, 30, irrep="E",
                                   note="Kitaev K=-1, random complex E-irrep tensor, the size of kh_D6_chi72"),
 }
+# Heisenberg D = 5 at growing chi, the sweep of the paper's per-iteration runtime figure
+# (Sec. III.B, Fig. 4c: D = 5, chi from 120 up): seeds 1012 + index
+for _i, _chi in enumerate((120, 240, 360, 480)):
+    WORKLOADS[f"heis_D5_chi{_chi}"] = Workload(f"heis_D5_chi{_chi}", 2, 5, _chi, 0.0, 1.0, 1012 + _i, 3,
+                                               note=f"Heisenberg J=1, D=5, chi={_chi}, n={25 * _chi}")
 
 
 def batch_workload(n_inst: int = 96, seed0: int = 5000):

@@ -26,7 +26,8 @@ def _split_gemm(A, B, T):
 
 SHAPES = [(128, 64, 64), (200, 72, 72), (130, 100, 40), (64, 300, 520), (300, 130, 1000), (1024, 96, 4096),
           (96, 40, 5000),    # K > 4096: the two-launch transposed-operand pre-pass
-          (64, 5000, 520)]   # 5000 transposed rows: clusters beyond one wave, the two-launch pre-pass
+          (64, 5000, 520),   # 5000 transposed rows: clusters beyond one wave, the two-launch pre-pass
+          (40, 48, 12000)]   # K > 8192 (the enlarged corner's n at D = 5, chi = 480): the generic row pack
 
 
 @pytest.mark.parametrize("M,N,K", SHAPES)
