@@ -6,6 +6,9 @@
 // All FP64.
 #include <math.h>
 
+#include <cooperative_groups.h>
+#include <mutex>
+
 #include "ctm_internal.h"
 
 namespace {
@@ -356,6 +359,120 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_packed_kernel(int chi, co
     }
 }
 
+// The reduction spread over a thread-block cluster, for chi > TRI_SMEM_MAX: the
+// symmetric corner is distributed by rows (row i, all chi entries, on CTA i % CS), so
+// each CTA's mat-vec and rank-2 update touch only its own shared memory.  Per column kc
+// the CTA owning row kc (= column kc) stores d_kc = A[kc][kc] and writes the row's
+// trailing part x into every CTA's column buffer (distributed shared memory); after a
+// cluster barrier every CTA derives the same reflector from the same bits (alpha =
+// -sign(x_0)|x|, v = x - alpha e_0, beta = 1/(|x|(|x| + |x_0|))), forms p_i = beta (A v)_i
+// for its rows and writes p_i into every CTA's p buffer; after a second barrier every
+// CTA forms w = p - (beta/2)(p^T v) v and updates its rows, A_ij -= v_i w_j + w_i v_j.
+// e_kc = alpha.  The two buffers alternate by column parity, so a broadcast never
+// overwrites one still being read (every CTA passes the next column's first barrier
+// only after finishing the current column).  Cluster barriers are hardware barriers:
+// nothing spins.
+constexpr int TRI_CL_THREADS = 512;
+constexpr int TRI_CL_SMEM_MAX = 226 * 1024;   // dynamic, below the 227 KB opt-in less the static part
+
+__host__ __device__ inline size_t tri_cluster_smem_bytes(int chi, int cs)
+{
+    return sizeof(double) * ((size_t)((chi + cs - 1) / cs) * chi + 5 * (size_t)chi);
+}
+
+template <int CS>
+__global__ void __launch_bounds__(TRI_CL_THREADS, 1) tridiag_cluster_kernel(int chi, const double *C, double *work)
+{
+    namespace cg = cooperative_groups;
+    cg::cluster_group cl = cg::this_cluster();
+    extern __shared__ double sm[];
+    __shared__ double red[33];
+    const int rank = (int)cl.block_rank();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
+    const int nloc = (chi - rank + CS - 1) / CS;   // rows rank, rank + CS, ...
+    const int nmax = (chi + CS - 1) / CS;
+    double *A = sm;                           // nmax x chi, full rows
+    double *vb = A + (size_t)nmax * chi;      // 2 x chi: the pivot row's trailing part, by parity
+    double *pb = vb + 2 * (size_t)chi;        // 2 x chi: p, by parity
+    double *w = pb + 2 * (size_t)chi;         // chi
+    for (int t = tid; t < nloc * chi; t += blockDim.x) {
+        const int l = t / chi, j = t % chi, i = rank + CS * l;
+        A[t] = 0.5 * (C[(size_t)i * chi + j] + C[(size_t)j * chi + i]);
+    }
+    cl.sync();   // every CTA of the cluster is running before the first remote store
+    for (int kc = 0; kc + 2 < chi; ++kc) {
+        const int b0 = kc + 1, m = chi - b0;
+        double *v = vb + (size_t)(kc & 1) * chi;
+        double *p = pb + (size_t)(kc & 1) * chi;
+        if (kc % CS == rank) {
+            const double *row = A + (size_t)(kc / CS) * chi;
+            if (tid == 0) work[kc] = row[kc];
+            for (int t = tid; t < m * CS; t += blockDim.x) {
+                const int r = t / m, j = t % m;
+                double *dst = cl.map_shared_rank(v, r);
+                dst[j] = row[b0 + j];
+            }
+        }
+        cl.sync();
+        double part = 0.0;
+        for (int i = 1 + tid; i < m; i += blockDim.x) part += v[i] * v[i];
+        const double tail = block_sum(part, red);
+        const double x0 = v[0];
+        if (tail == 0.0) {   // already reduced in this column (the same decision in every CTA)
+            if (rank == 0 && tid == 0) work[chi + kc] = x0 * x0;
+            continue;
+        }
+        const double nrm = sqrt(tail + x0 * x0);
+        const double alpha = (x0 >= 0.0) ? -nrm : nrm;
+        const double beta = 1.0 / (nrm * (nrm + fabs(x0)));
+        const double v0 = x0 - alpha;
+        if (rank == 0 && tid == 0) work[chi + kc] = alpha * alpha;
+        int lf = b0 - rank;                    // first local row with i >= b0
+        lf = lf > 0 ? (lf + CS - 1) / CS : 0;
+        for (int l = lf + warp; l < nloc; l += nwarps) {
+            const int i = rank + CS * l;
+            const double *row = A + (size_t)l * chi + b0;
+            double s0 = 0.0, s1 = 0.0;
+            for (int j = lane; j < m; j += 64) {
+                s0 = fma(row[j], j == 0 ? v0 : v[j], s0);
+                if (j + 32 < m) s1 = fma(row[j + 32], v[j + 32], s1);
+            }
+            double sum = s0 + s1;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            if (lane < CS) {
+                double *dst = cl.map_shared_rank(p, lane);
+                dst[i - b0] = beta * sum;
+            }
+        }
+        cl.sync();
+        double pv = 0.0;
+        for (int j = tid; j < m; j += blockDim.x) pv += p[j] * (j == 0 ? v0 : v[j]);
+        pv = block_sum(pv, red);
+        const double Kf = 0.5 * beta * pv;
+        for (int j = tid; j < m; j += blockDim.x) w[j] = p[j] - Kf * (j == 0 ? v0 : v[j]);
+        __syncthreads();
+        for (int l = lf + warp; l < nloc; l += nwarps) {
+            const int ii = rank + CS * l - b0;
+            const double vi = ii == 0 ? v0 : v[ii], wi = w[ii];
+            double *row = A + (size_t)l * chi + b0;
+            for (int j = lane; j < m; j += 32) row[j] -= vi * w[j] + wi * (j == 0 ? v0 : v[j]);
+        }
+        __syncthreads();   // this CTA's rows are final for the column before its next broadcast
+    }
+    // the last 2 x 2 block (chi > TRI_SMEM_MAX here): d_{chi-2}, d_{chi-1}, e_{chi-2}
+    for (int i = chi - 2; i < chi; ++i)
+        if (i % CS == rank && tid == 0) {
+            const double *row = A + (size_t)(i / CS) * chi;
+            work[i] = row[i];
+            if (i == chi - 1) {
+                work[2 * chi - 2] = row[chi - 2] * row[chi - 2];
+                work[2 * chi - 1] = 0.0;
+            }
+        }
+    cl.sync();   // no CTA leaves while another may still write into its shared memory
+}
+
 // Number of eigenvalues of the tridiagonal (d, e2) below x: the sign changes of
 // p_i = (d_i - x) p_{i-1} - e2_{i-1} p_{i-2}.  Only the recurrence itself is FP64
 // arithmetic (three operations per step -- GB300's FP64 pipe is narrow); the zero
@@ -574,6 +691,63 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
     return cudaGetLastError();
 }
 
+// Cluster size for the distributed reduction of a chi x chi corner (chi > TRI_SMEM_MAX):
+// 16 CTAs where the device schedules such clusters with this shared memory, else 8,
+// else 0 (the single-CTA reduction from global memory).  Decided once per chi.
+static std::mutex g_tri_mu;
+static signed char g_tri_cs[SPEC_MAX_CHI + 1];   // 0: not decided, -1: none, else the size
+static bool g_tri_cluster_ok = false;             // the cluster kernels' attributes were accepted
+
+template <int CS>
+static int tri_cluster_fits(int chi)
+{
+    const size_t smem = tri_cluster_smem_bytes(chi, CS);
+    if (smem > TRI_CL_SMEM_MAX) return 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(CS, 1, 1);
+    cfg.blockDim = dim3(TRI_CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CS;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, tridiag_cluster_kernel<CS>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc > 0;
+}
+
+static int tri_cluster_size(int chi)
+{
+    if (chi <= TRI_SMEM_MAX || chi > SPEC_MAX_CHI || !g_tri_cluster_ok) return 0;
+    std::lock_guard<std::mutex> lk(g_tri_mu);
+    if (!g_tri_cs[chi]) g_tri_cs[chi] = tri_cluster_fits<16>(chi) ? 16 : tri_cluster_fits<8>(chi) ? 8 : -1;
+    return g_tri_cs[chi] > 0 ? g_tri_cs[chi] : 0;
+}
+
+static cudaError_t launch_tridiag_cluster(int cs, int chi, const double *C, double *work, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(cs, 1, 1);
+    cfg.blockDim = dim3(TRI_CL_THREADS, 1, 1);
+    cfg.dynamicSmemBytes = tri_cluster_smem_bytes(chi, cs);
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = cs;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cs == 16 ? cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel<16>, chi, C, work)
+                    : cudaLaunchKernelEx(&cfg, tridiag_cluster_kernel<8>, chi, C, work);
+}
+
 size_t spectrum_work_doubles(int chi)
 {
     return tri_global_off(chi) + (chi > TRI_SMEM_MAX ? (size_t)chi * (chi + 1) / 2 : 0);
@@ -593,10 +767,14 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
                                     2 * (size_t)chi);
     if (reserve_sm && smem < SPEC_SM_ALONE_BYTES) smem = SPEC_SM_ALONE_BYTES;
     CTM_COUNT_LAUNCH(3);
+    cudaError_t e = cudaSuccess;
+    const int cs = global ? tri_cluster_size(chi) : 0;
     if (full) tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     else if (!global) tridiag_packed_kernel<false><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
+    else if (cs) e = launch_tridiag_cluster(cs, chi, C, work, st);
     else tridiag_packed_kernel<true><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
-    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 2 * sizeof(double) * chi, st>>>(
         chi, work, work + 2 * chi);
@@ -646,5 +824,17 @@ cudaError_t spectrum_prepare()
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(tridiag_packed_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(tridiag_packed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    e = cudaFuncSetAttribute(tridiag_packed_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 224 * 1024);
+    if (e != cudaSuccess) return e;
+    // the cluster reduction is optional: where the device refuses these attributes the
+    // single-CTA reduction from global memory serves
+    const bool ok = cudaFuncSetAttribute(tridiag_cluster_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TRI_CL_SMEM_MAX) == cudaSuccess &&
+                    cudaFuncSetAttribute(tridiag_cluster_kernel<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         TRI_CL_SMEM_MAX) == cudaSuccess &&
+                    cudaFuncSetAttribute(tridiag_cluster_kernel<16>, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                         1) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+    g_tri_cluster_ok = ok;
+    return cudaSuccess;
 }
