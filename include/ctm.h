@@ -334,7 +334,9 @@ void ctm_batch_destroy(ctm_batch *batch);
  *    and delta from the eigenvalue magnitudes of C'.
  *  - Precisions as for ctm_init (FP64, split BF16, split TF32, one TF32 product):
  *    every real product of a complex contraction runs on the chosen engine.
- *  - Limits: chi <= 112, n = chi D^2 <= 12000, D <= 10.  corner_mode 1 gives the cheap
+ *  - Limits: chi <= 256 (beyond 112 the corner spectrum runs on the real 2chi x 2chi
+ *    embedding [[Re, -Im], [Im, Re]] of the Hermitian corner), n = chi D^2 <= 12000,
+ *    D <= 10.  corner_mode 1 gives the cheap
  *    variant C' = sym(R S)/|.| with S = diag(sgn Re C_jj) (R S = Q^H M Q_prev).
  *  - The caller owns the workspace (ctm_complex_workspace_bytes), as for ctm_init.
  *    Errors as for the real calls. */

@@ -46,6 +46,7 @@ struct ctm_complex_ctx {
     double *P5a, *P5b;
     double *Yemb, *Qemb, *Remb;
     double *s, *s_new, *delta, *spec_work;
+    double *spec_emb;   // chi > ZSMEM_CHI: the real 2chi x 2chi embedding of the corner
     double *splitk;
     size_t splitk_elems;
     double *qr_sbuf, *qr_rowbuf, *qr_wy;
@@ -87,9 +88,12 @@ struct ctm_complex_ctx {
 namespace {
 
 constexpr int ZMAX_D = 3;
-// the Hermitian corner of the spectrum kernel (two planes) fits one SM's shared memory up
-// to chi = 112; the QR of the 2n x 2chi embedding takes up to 256 columns
-constexpr int ZMAX_CHI = 112;
+// the Hermitian corner of the one-CTA spectrum kernel (two planes) fits one SM's shared
+// memory up to chi = 112; beyond, the spectrum runs on the real 2chi x 2chi embedding
+// through the real path's reduction (a thread-block cluster), up to chi = 256, where the
+// QR of the 2n x 2chi embedding reaches its 512 columns
+constexpr int ZSMEM_CHI = 112;
+constexpr int ZMAX_CHI = 256;
 constexpr int ZNORM_BLOCKS = 128;
 constexpr int ZRHO_BLOCKS = 128;
 constexpr int ZRHO_MAX_DD = 9;
@@ -984,7 +988,8 @@ size_t zlayout(ctm_complex_ctx *c, char *base)
     c->s = td(chi);
     c->s_new = td(chi);
     c->delta = td(8);
-    c->spec_work = td((long long)spectrum_work_doubles((int)chi));
+    c->spec_work = td((long long)spectrum_work_doubles(chi > ZSMEM_CHI ? 2 * (int)chi : (int)chi));
+    c->spec_emb = chi > ZSMEM_CHI ? td(4 * chi * chi) : nullptr;
     size_t sk = 0;
     for (const auto &sh : zshapes(c)) {
         int s = gemm_f64_pick_split(sh[0], sh[1], sh[2]);
@@ -1164,6 +1169,27 @@ int zedge(ctm_complex_ctx *c)
     return znormalize(c, (long long)chi * D2 * chi, c->Tn, lay_T(c));
 }
 
+// The real symmetric embedding of the Hermitian part H = Ar + i Ai of the corner (Re in
+// plane 0, Im in plane 3): E = [[Ar, -Ai], [Ai, Ar]] (2chi x 2chi), whose eigenvalues are
+// H's, each twice.
+__global__ void zc_embed_kernel(int chi, const double *C, long long PC, double *E)
+{
+    const long long N = 2LL * chi, total = N * N;
+    const double *Ci = C + 3 * PC;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(t / N), q = (int)(t % N);
+        const int i = r % chi, j = q % chi, br = r / chi, bq = q / chi;
+        double v;
+        if (br == bq) v = 0.5 * (C[(size_t)i * chi + j] + C[(size_t)j * chi + i]);
+        else {
+            const double ai = 0.5 * (Ci[(size_t)i * chi + j] - Ci[(size_t)j * chi + i]);
+            v = (br == 0) ? -ai : ai;
+        }
+        E[t] = v;
+    }
+}
+
 // the corner spectrum of C (five planes): delta against the previous one, on `st`;
 // with dst, the delta is also copied there (pinned host memory)
 int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st, double *dst = nullptr)
@@ -1173,12 +1199,20 @@ int zspectrum(ctm_complex_ctx *c, const double *Cin, cudaStream_t st, double *ds
         ZK(cudaEventRecord(c->ev_fork, c->stream));
         ZK(cudaStreamWaitEvent(st, c->ev_fork, 0));
     }
-    CTM_COUNT_LAUNCH(1);
-    // all but a few KB of the SM's shared memory: the step's CTAs stay off its SM (as for
-    // the real corner spectrum)
-    zc_tridiag_kernel<<<1, ZTRI_THREADS, ztridiag_launch_bytes(chi), st>>>(chi, Cin, c->PC, c->spec_work);
-    ZK(cudaGetLastError());
-    ZK(launch_spectrum_from_tridiag(chi, c->spec_work, c->s_new, c->s, c->delta, st));
+    if (chi > ZSMEM_CHI) {
+        const long long n2 = 4LL * chi * chi;
+        CTM_COUNT_LAUNCH(1);
+        zc_embed_kernel<<<zgrid(n2), 256, 0, st>>>(chi, Cin, c->PC, c->spec_emb);
+        ZK(cudaGetLastError());
+        ZK(launch_spectrum_pairs(chi, c->spec_emb, c->s_new, c->s, c->delta, c->spec_work, st));
+    } else {
+        CTM_COUNT_LAUNCH(1);
+        // all but a few KB of the SM's shared memory: the step's CTAs stay off its SM (as for
+        // the real corner spectrum)
+        zc_tridiag_kernel<<<1, ZTRI_THREADS, ztridiag_launch_bytes(chi), st>>>(chi, Cin, c->PC, c->spec_work);
+        ZK(cudaGetLastError());
+        ZK(launch_spectrum_from_tridiag(chi, c->spec_work, c->s_new, c->s, c->delta, st));
+    }
     ZK(cudaMemcpyAsync(c->s, c->s_new, sizeof(double) * chi, cudaMemcpyDeviceToDevice, st));
     if (dst) ZK(cudaMemcpyAsync(dst, c->delta, sizeof(double), cudaMemcpyDeviceToHost, st));
     if (st != c->stream) ZK(cudaEventRecord(c->ev_join, st));
@@ -1370,7 +1404,7 @@ int ctm_complex_init(const ctm_config *cfg, int irrep, const double *A_dev, void
         if (qr_prepare() != cudaSuccess || spectrum_prepare() != cudaSuccess || split_prepare() != cudaSuccess ||
             tf32_prepare() != cudaSuccess ||
             cudaFuncSetAttribute(zc_tridiag_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)ztridiag_launch_bytes(ZMAX_CHI)) != cudaSuccess) {
+                                 (int)ztridiag_launch_bytes(ZSMEM_CHI)) != cudaSuccess) {
             rc = CTM_ECUDA;
             break;
         }

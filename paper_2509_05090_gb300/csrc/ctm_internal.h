@@ -177,6 +177,11 @@ cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st);
 // `work` (diagonal d in work[0, chi), squared off-diagonal e^2 in work[chi, 2 chi)).
 cudaError_t launch_spectrum_from_tridiag(int chi, double *work, double *s_new, const double *s_old, double *delta,
                                         cudaStream_t st);
+// The spectrum of a Hermitian chi x chi corner through its real symmetric 2chi x 2chi
+// embedding E = [[Re, -Im], [Im, Re]] (every eigenvalue twice): the real reduction and
+// bisection on E, then every second sorted magnitude.  work: spectrum_work_doubles(2 chi).
+cudaError_t launch_spectrum_pairs(int chi, const double *E, double *s_new, const double *s_old, double *delta,
+                                  double *work, cudaStream_t st);
 cudaError_t launch_bond_energy(int d, const double *rho_raw, const double *h, double *out, cudaStream_t st);
 cudaError_t launch_open_layers(int d, int D, const double *A, double *b, cudaStream_t st);
 cudaError_t launch_check_finite(long long count, const double *x, int *flag, cudaStream_t st);

@@ -545,27 +545,33 @@ __global__ void bisect_kernel(int chi, const double *work, double *lam)
     if (lane == 0) lam[ei] = 0.5 * (lo + hi);
 }
 
-__global__ void spectrum_finish_kernel(int chi, const double *lam_in, double *s_new, const double *s_old,
+// stride 2: the chi x stride eigenvalues come in equal pairs (a Hermitian corner through
+// its real embedding); every second one of the sorted magnitudes is kept.
+__global__ void spectrum_finish_kernel(int chi, int stride, const double *lam_in, double *s_new, const double *s_old,
                                        double *delta)
 {
     __shared__ double red[33];
     __shared__ double lam[SPEC_MAX_CHI], srt[SPEC_MAX_CHI];
-    const int tid = threadIdx.x;
-    for (int i = tid; i < chi; i += blockDim.x) lam[i] = fabs(lam_in[i]);
+    const int tid = threadIdx.x, nall = chi * stride;
+    for (int i = tid; i < nall; i += blockDim.x) lam[i] = fabs(lam_in[i]);
     __syncthreads();
-    double ss = 0.0;
-    for (int i = tid; i < chi; i += blockDim.x) ss += lam[i] * lam[i];
-    ss = block_sum(ss, red);
-    const double f = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
-    for (int i = tid; i < chi; i += blockDim.x) {
+    for (int i = tid; i < nall; i += blockDim.x) {
         double ai = lam[i];
         int rank = 0;
-        for (int j = 0; j < chi; ++j) {
+        for (int j = 0; j < nall; ++j) {
             double aj = lam[j];
             rank += (aj > ai) || (aj == ai && j < i);
         }
-        srt[rank] = ai * f;
+        srt[rank] = ai;
     }
+    __syncthreads();
+    double ss = 0.0;
+    for (int i = tid; i < chi; i += blockDim.x) ss += srt[i * stride] * srt[i * stride];
+    ss = block_sum(ss, red);
+    const double f = ss > 0.0 ? 1.0 / sqrt(ss) : 0.0;
+    for (int i = tid; i < chi; i += blockDim.x) lam[i] = srt[i * stride] * f;
+    __syncthreads();
+    for (int i = tid; i < chi; i += blockDim.x) srt[i] = lam[i];
     __syncthreads();
     double dd = 0.0;
     for (int i = tid; i < chi; i += blockDim.x) {
@@ -753,10 +759,44 @@ size_t spectrum_work_doubles(int chi)
     return tri_global_off(chi) + (chi > TRI_SMEM_MAX ? (size_t)chi * (chi + 1) / 2 : 0);
 }
 
+// bisection of the tridiagonal in work (n = chi x stride eigenvalues), then the sorted,
+// normalised magnitudes (every stride-th) and delta
+static cudaError_t spectrum_tail(int chi, int stride, double *work, double *s_new, const double *s_old, double *delta,
+                                 cudaStream_t st)
+{
+    const int n = chi * stride;
+    CTM_COUNT_LAUNCH(2);
+    bisect_kernel<<<(n + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 2 * sizeof(double) * n, st>>>(n, work,
+                                                                                                      work + 2 * n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, stride, work + 2 * n, s_new, s_old, delta);
+    return cudaGetLastError();
+}
+
+static cudaError_t launch_tridiag(int chi, const double *C, double *work, cudaStream_t st, bool reserve_sm);
+
+cudaError_t launch_spectrum_pairs(int chi, const double *E, double *s_new, const double *s_old, double *delta,
+                                  double *work, cudaStream_t st)
+{
+    if (2 * chi > SPEC_MAX_CHI || !work) return cudaErrorInvalidValue;
+    cudaError_t e = launch_tridiag(2 * chi, E, work, st, false);
+    if (e != cudaSuccess) return e;
+    return spectrum_tail(chi, 2, work, s_new, s_old, delta, st);
+}
+
 cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const double *s_old, double *delta,
                             double *work, cudaStream_t st, bool reserve_sm)
 {
     if (chi > SPEC_MAX_CHI || !work) return cudaErrorInvalidValue;
+    cudaError_t e = launch_tridiag(chi, C, work, st, reserve_sm);
+    if (e != cudaSuccess) return e;
+    return spectrum_tail(chi, 1, work, s_new, s_old, delta, st);
+}
+
+// step one of the spectrum: the tridiagonal (d, e^2) of the symmetric chi x chi matrix C in work
+static cudaError_t launch_tridiag(int chi, const double *C, double *work, cudaStream_t st, bool reserve_sm)
+{
     // reserve_sm: the tridiagonalisation runs beside a lone instance's step for ~0.4 ms on
     // one SM; asking for (nearly) all of the SM's shared memory keeps the step's CTAs off
     // that SM, whose CTAs it would otherwise slow (a grid-synchronous QR waits for its
@@ -766,7 +806,7 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
     size_t smem = sizeof(double) * ((full ? (size_t)chi * (chi | 1) : global ? 0 : (size_t)chi * (chi + 1) / 2) +
                                     2 * (size_t)chi);
     if (reserve_sm && smem < SPEC_SM_ALONE_BYTES) smem = SPEC_SM_ALONE_BYTES;
-    CTM_COUNT_LAUNCH(3);
+    CTM_COUNT_LAUNCH(1);
     cudaError_t e = cudaSuccess;
     const int cs = global ? tri_cluster_size(chi) : 0;
     if (full) tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
@@ -774,13 +814,6 @@ cudaError_t launch_spectrum(int chi, const double *C, double *s_new, const doubl
     else if (cs) e = launch_tridiag_cluster(cs, chi, C, work, st);
     else tridiag_packed_kernel<true><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     if (e != cudaSuccess) return e;
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 2 * sizeof(double) * chi, st>>>(
-        chi, work, work + 2 * chi);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, work + 2 * chi, s_new, s_old, delta);
     return cudaGetLastError();
 }
 
@@ -788,13 +821,7 @@ cudaError_t launch_spectrum_from_tridiag(int chi, double *work, double *s_new, c
                                         cudaStream_t st)
 {
     if (chi > SPEC_MAX_CHI || !work) return cudaErrorInvalidValue;
-    CTM_COUNT_LAUNCH(2);
-    bisect_kernel<<<(chi + SPEC_WARPS - 1) / SPEC_WARPS, 32 * SPEC_WARPS, 2 * sizeof(double) * chi, st>>>(
-        chi, work, work + 2 * chi);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    spectrum_finish_kernel<<<1, 256, 0, st>>>(chi, work + 2 * chi, s_new, s_old, delta);
-    return cudaGetLastError();
+    return spectrum_tail(chi, 1, work, s_new, s_old, delta, st);
 }
 
 cudaError_t launch_spectrum_init(int chi, double *s, cudaStream_t st)

@@ -72,11 +72,13 @@ def test_complex_projection_and_double_layer(ctm_lib, d, D):
     g.close()
 
 
-@pytest.mark.parametrize("D,chi,seed", [(2, 8, 51), (3, 12, 52), (2, 112, 53)])
+@pytest.mark.parametrize("D,chi,seed", [(2, 8, 51), (3, 12, 52), (2, 112, 53), (2, 160, 54), (2, 256, 55)])
 def test_complex_steps_fp64(ctm_lib, D, chi, seed):
     """Random E-irrep tensors, ten steps in lockstep, each step from the oracle's environment
     (chi = 112: the embedded QR has 224 columns, beyond which U of its compact-WY solve no
-    longer fits shared memory and is read from L2)."""
+    longer fits shared memory and is read from L2; chi = 160 and 256: the corner spectrum
+    through the real 2chi x 2chi embedding on a thread-block cluster, and at 256 an embedded
+    QR of 512 columns)."""
     A = I.random_complex_site_tensor(2, D, seed)
     g = _ctm(A, chi)
     z = Z.ComplexCTM(A, chi)
@@ -228,7 +230,7 @@ def test_complex_rejects_bad_config(ctm_lib):
     from paper_2509_05090_gb300 import binding
     A = I.random_complex_site_tensor(2, 2, 3)
     with pytest.raises(binding.CtmError):
-        binding.CTMComplex(A, 113)                      # chi above the spectrum kernel's limit
+        binding.CTMComplex(A, 257)                      # chi above the embedded QR's 512 columns
     with pytest.raises(binding.CtmError):
         binding.CTMComplex(A[:1], 4)                    # d = 1 has no E irrep
 
