@@ -627,7 +627,7 @@ def run_complex(args, w):
     return 0
 
 
-def chi_sweep_record(n_split, steps=3):
+def chi_sweep_record(n_split, steps=3, chis=(120, 240, 360, 480)):
     """Heisenberg D = 5 at chi = 120 ... 480 in split BF16 (the sweep of the paper's
     per-iteration runtime figure): ms per step from a replayed graph of `steps` steps, the
     profiled phases (QR on the main stream, corner spectrum on the side stream) and the
@@ -636,7 +636,7 @@ def chi_sweep_record(n_split, steps=3):
     import torch
     from paper_2509_05090_gb300 import binding, inputs
     out = []
-    for chi in (120, 240, 360, 480):
+    for chi in chis:
         w = inputs.WORKLOADS[f"heis_D5_chi{chi}"]
         c = binding.CTM(w.site_tensor(), w.chi, precision="split_bf16", n_split=n_split)
         c.ctm_step(1, want_delta=False)       # eager first step (autotuning)
