@@ -627,7 +627,7 @@ def run_complex(args, w):
     return 0
 
 
-def chi_sweep_record(n_split, steps=3, chis=(120, 240, 360, 480)):
+def chi_sweep_record(n_split, steps=3, chis=(120, 240, 360, 480), bf16_peak=None):
     """Heisenberg D = 5 at chi = 120 ... 480 in split BF16 (the sweep of the paper's
     per-iteration runtime figure): ms per step from a replayed graph of `steps` steps, the
     profiled phases (QR on the main stream, corner spectrum on the side stream) and the
@@ -651,9 +651,15 @@ def chi_sweep_record(n_split, steps=3, chis=(120, 240, 360, 480)):
         ph = c.ctm_step_profiled()
         c.close()
         flops = step_gemm_flops(w.chi, w.D2)
-        out.append({"workload": w.name, "chi": chi, "n": w.n, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
-                    "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12,
-                    "qr_ms": ph["qr"], "spectrum_ms": ph["spectrum"], "contractions_ms": ph["gemm_kernels"]})
+        rec = {"workload": w.name, "chi": chi, "n": w.n, "ms_per_step": ms, "steps_per_s": 1e3 / ms,
+               "fp64_equivalent_tflops": flops / (ms / 1e3) / 1e12,
+               "qr_ms": ph["qr"], "spectrum_ms": ph["spectrum"], "contractions_ms": ph["gemm_kernels"]}
+        # the contraction kernels' BF16 slice products (T (T + 1) / 2 per algorithmic product)
+        slice_tflops = n_split * (n_split + 1) / 2 * flops / (ph["gemm_kernels"] / 1e3) / 1e12
+        rec["contraction_slice_tflops"] = slice_tflops
+        if bf16_peak:
+            rec["contraction_frac_of_bf16_burst"] = slice_tflops / bf16_peak
+        out.append(rec)
     return out
 
 
@@ -877,7 +883,7 @@ def main():
         line["tf32_modes"] = tf
         line["grad_d8_chi128"] = grad_record(fp64_peak)
         line["optimize_heisenberg_D3"] = optimize_record()
-        line["chi_sweep_heisenberg_D5"] = chi_sweep_record(args.n_split)
+        line["chi_sweep_heisenberg_D5"] = chi_sweep_record(args.n_split, bf16_peak=peaks["bf16_tflops"])
         line["batch96"] = batch_record(args, args.steps)
         line["complex_E_D6_chi72"] = complex_record(args.steps, args.n_split, fp64_peak, peaks["bf16_tflops"],
                                                     with_oracle=not args.no_compare)
