@@ -199,6 +199,10 @@ constexpr size_t SPEC_SM_ALONE_BYTES = 220 * 1024;   // within the 224 KB opt-in
 constexpr int TRI_FULL_MAX = 160;   // the full corner in shared memory up to here, its lower triangle beyond
 constexpr int TRI_SMEM_MAX = 224;   // the lower triangle of a 224 x 224 corner: 197 KB of shared memory
 constexpr int SPEC_MAX_CHI = 512;   // beyond TRI_SMEM_MAX the lower triangle lives in the work buffer (L2)
+// From here up the reduction runs over a thread-block cluster where the device schedules one
+// (its per-column cost hardly depends on chi, so it overtakes the one-CTA kernels early;
+// the benchmark's chi = 72 and the batch's instances keep the one-CTA kernel)
+constexpr int TRI_CLUSTER_MIN = 97;
 
 // offset (doubles) of the global lower triangle in the spectrum's work buffer, after
 // d, e^2 (2 chi) and the eigenvalues (chi)
@@ -359,7 +363,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_packed_kernel(int chi, co
     }
 }
 
-// The reduction spread over a thread-block cluster, for chi > TRI_SMEM_MAX: the
+// The reduction spread over a thread-block cluster, for chi >= TRI_CLUSTER_MIN: the
 // symmetric corner is distributed by rows (row i, all chi entries, on CTA i % CS), so
 // each CTA's mat-vec and rank-2 update touch only its own shared memory.  Per column kc
 // the CTA owning row kc (= column kc) stores d_kc = A[kc][kc] and writes the row's
@@ -460,7 +464,7 @@ __global__ void __launch_bounds__(TRI_CL_THREADS, 1) tridiag_cluster_kernel(int 
         }
         __syncthreads();   // this CTA's rows are final for the column before its next broadcast
     }
-    // the last 2 x 2 block (chi > TRI_SMEM_MAX here): d_{chi-2}, d_{chi-1}, e_{chi-2}
+    // the last 2 x 2 block (chi >= TRI_CLUSTER_MIN here): d_{chi-2}, d_{chi-1}, e_{chi-2}
     for (int i = chi - 2; i < chi; ++i)
         if (i % CS == rank && tid == 0) {
             const double *row = A + (size_t)(i / CS) * chi;
@@ -697,7 +701,7 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
     return cudaGetLastError();
 }
 
-// Cluster size for the distributed reduction of a chi x chi corner (chi > TRI_SMEM_MAX):
+// Cluster size for the distributed reduction of a chi x chi corner (chi >= TRI_CLUSTER_MIN):
 // 16 CTAs where the device schedules such clusters with this shared memory, else 8,
 // else 0 (the single-CTA reduction from global memory).  Decided once per chi.
 static std::mutex g_tri_mu;
@@ -730,7 +734,7 @@ static int tri_cluster_fits(int chi)
 
 static int tri_cluster_size(int chi)
 {
-    if (chi <= TRI_SMEM_MAX || chi > SPEC_MAX_CHI || !g_tri_cluster_ok) return 0;
+    if (chi < TRI_CLUSTER_MIN || chi > SPEC_MAX_CHI || !g_tri_cluster_ok) return 0;
     std::lock_guard<std::mutex> lk(g_tri_mu);
     if (!g_tri_cs[chi]) g_tri_cs[chi] = tri_cluster_fits<16>(chi) ? 16 : tri_cluster_fits<8>(chi) ? 8 : -1;
     return g_tri_cs[chi] > 0 ? g_tri_cs[chi] : 0;
@@ -808,10 +812,10 @@ static cudaError_t launch_tridiag(int chi, const double *C, double *work, cudaSt
     if (reserve_sm && smem < SPEC_SM_ALONE_BYTES) smem = SPEC_SM_ALONE_BYTES;
     CTM_COUNT_LAUNCH(1);
     cudaError_t e = cudaSuccess;
-    const int cs = global ? tri_cluster_size(chi) : 0;
-    if (full) tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
+    const int cs = tri_cluster_size(chi);
+    if (cs) e = launch_tridiag_cluster(cs, chi, C, work, st);
+    else if (full) tridiag_kernel<<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     else if (!global) tridiag_packed_kernel<false><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
-    else if (cs) e = launch_tridiag_cluster(cs, chi, C, work, st);
     else tridiag_packed_kernel<true><<<1, TRI_THREADS, smem, st>>>(chi, C, work);
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
