@@ -376,8 +376,15 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_packed_kernel(int chi, co
 // overwrites one still being read (every CTA passes the next column's first barrier
 // only after finishing the current column).  Cluster barriers are hardware barriers:
 // nothing spins.
-constexpr int TRI_CL_THREADS = 512;
+constexpr int TRI_CL_THREADS = 512;   // at most (tri_cluster_threads)
 constexpr int TRI_CL_SMEM_MAX = 226 * 1024;   // dynamic, below the 227 KB opt-in less the static part
+
+// one warp per local row (4 to 16 warps): fewer threads make the per-column barriers cheaper
+__host__ __device__ inline int tri_cluster_threads(int chi, int cs)
+{
+    const int w = (chi + cs - 1) / cs;
+    return 32 * (w < 4 ? 4 : w > 16 ? 16 : w);
+}
 
 __host__ __device__ inline size_t tri_cluster_smem_bytes(int chi, int cs)
 {
@@ -418,9 +425,16 @@ __global__ void __launch_bounds__(TRI_CL_THREADS, 1) tridiag_cluster_kernel(int 
             }
         }
         cl.sync();
-        double part = 0.0;
-        for (int i = 1 + tid; i < m; i += blockDim.x) part += v[i] * v[i];
-        const double tail = block_sum(part, red);
+        // |x|^2 below the pivot by warp 0 in a fixed order (the same bits in every CTA)
+        if (warp == 0) {
+            double t = 0.0;
+            for (int i = 1 + lane; i < m; i += 32) t = fma(v[i], v[i], t);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[32] = t;
+        }
+        __syncthreads();
+        const double tail = red[32];
         const double x0 = v[0];
         if (tail == 0.0) {   // already reduced in this column (the same decision in every CTA)
             if (rank == 0 && tid == 0) work[chi + kc] = x0 * x0;
@@ -450,10 +464,15 @@ __global__ void __launch_bounds__(TRI_CL_THREADS, 1) tridiag_cluster_kernel(int 
             }
         }
         cl.sync();
-        double pv = 0.0;
-        for (int j = tid; j < m; j += blockDim.x) pv += p[j] * (j == 0 ? v0 : v[j]);
-        pv = block_sum(pv, red);
-        const double Kf = 0.5 * beta * pv;
+        if (warp == 0) {
+            double t = 0.0;
+            for (int j = lane; j < m; j += 32) t = fma(p[j], j == 0 ? v0 : v[j], t);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[32] = t;
+        }
+        __syncthreads();
+        const double Kf = 0.5 * beta * red[32];
         for (int j = tid; j < m; j += blockDim.x) w[j] = p[j] - Kf * (j == 0 ? v0 : v[j]);
         __syncthreads();
         for (int l = lf + warp; l < nloc; l += nwarps) {
@@ -715,7 +734,7 @@ static int tri_cluster_fits(int chi)
     if (smem > TRI_CL_SMEM_MAX) return 0;
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(CS, 1, 1);
-    cfg.blockDim = dim3(TRI_CL_THREADS, 1, 1);
+    cfg.blockDim = dim3(tri_cluster_threads(chi, CS), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute at[1];
     at[0].id = cudaLaunchAttributeClusterDimension;
@@ -744,7 +763,7 @@ static cudaError_t launch_tridiag_cluster(int cs, int chi, const double *C, doub
 {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(cs, 1, 1);
-    cfg.blockDim = dim3(TRI_CL_THREADS, 1, 1);
+    cfg.blockDim = dim3(tri_cluster_threads(chi, cs), 1, 1);
     cfg.dynamicSmemBytes = tri_cluster_smem_bytes(chi, cs);
     cfg.stream = st;
     cudaLaunchAttribute at[1];
