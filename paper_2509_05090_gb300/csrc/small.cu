@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(TRI_THREADS) tridiag_packed_kernel(int chi, co
 // overwrites one still being read (every CTA passes the next column's first barrier
 // only after finishing the current column).  Cluster barriers are hardware barriers:
 // nothing spins.
-constexpr int TRI_CL_THREADS = 512;   // at most (tri_cluster_threads)
+constexpr int TRI_CL_THREADS = 512;   // the largest block tri_cluster_threads gives
 constexpr int TRI_CL_SMEM_MAX = 226 * 1024;   // dynamic, below the 227 KB opt-in less the static part
 
 // one warp per local row (4 to 16 warps): fewer threads make the per-column barriers cheaper
