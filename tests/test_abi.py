@@ -42,3 +42,19 @@ def test_workspace_grows_with_chi(lib):
     # two n x n FP64 intermediates at least
     n = 72 * 36
     assert big >= 2 * 8 * n * n
+
+
+def test_configuration_limits(lib):
+    """The size limits include/ctm.h states, checked by the host-side workspace query (no
+    device work): real chi <= 512 with n = chi D^2 <= 20000, complex chi <= 256 with
+    n <= 12000."""
+    ws = binding.ctm_workspace_bytes
+    assert ws(binding.make_config(2, 3, 512)) > 0
+    assert ws(binding.make_config(2, 3, 513)) == 0
+    assert ws(binding.make_config(2, 6, 512)) > 0          # n = 18432
+    assert ws(binding.make_config(2, 7, 409)) == 0         # n = 20041
+    zws = lib.ctm_complex_workspace_bytes
+    E = 1
+    assert zws(ctypes.byref(binding.make_config(2, 2, 256)), E) > 0
+    assert zws(ctypes.byref(binding.make_config(2, 2, 257)), E) == 0
+    assert zws(ctypes.byref(binding.make_config(2, 7, 245)), E) == 0   # n = 12005
