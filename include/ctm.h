@@ -111,7 +111,11 @@ int ctm_init(const ctm_config *cfg, const double *A_dev, void *workspace, size_t
  * contraction shape in split mode times its candidate tile plans, and the first
  * QR of each shape its grid size; the choices are kept for the process.  With
  * the environment variable CTM_AUTOTUNE_CACHE=<file> they are also read from and
- * appended to that text file, so another process runs the same plans. */
+ * appended to that text file, so another process runs the same plans.
+ * CTM_QR_SLAB=1 in the environment when ctm_init (and ctm_workspace_bytes) run
+ * keeps the QR's row blocks in the global slab for every shape, the layout taken
+ * where one SM's share of the rows does not fit shared memory: the same
+ * factorisation, a check of that path at small sizes. */
 
 /* Sec. II.B, Fig. 3: run nsteps CTMRG steps.  One step builds the enlarged
  * corner M from (C, T, a), the reduced corner Y = M Q diag(sgn C_ii),
