@@ -2,7 +2,7 @@
 
 Heisenberg D = 5, chi = 480 (n = 12000): one SM's share of the QR's rows (79 rows of
 481 doubles) does not fit shared memory, so the row blocks live in the global slab,
-and the corner spectrum keeps C's lower triangle in global memory.  The oracle's
+and the corner spectrum runs over a 16-CTA thread-block cluster (30 rows of C per CTA).  The oracle's
 step at this size takes minutes, so the checks are properties that hold at any size
 (Sec. II.B: Y = Q R with Q orthonormal and diag(R) >= 0; the corner spectrum is the
 normalised |eigenvalues| of the symmetric corner), plus the split-BF16 step against
@@ -65,9 +65,9 @@ def test_large_chi_step_properties_and_split_vs_fp64(ctm_lib):
 
 
 def test_large_chi_converge_pipelined(ctm_lib):
-    """ctm_converge at chi = 360 (the spectrum in global memory, ~10 ms on one SM, runs on
-    the side stream across the pipelined graphs): the deltas it reports match those of
-    single steps from the same start."""
+    """ctm_converge at chi = 360 (the cluster spectrum, ~5 ms, runs on the side stream across
+    the pipelined graphs): the deltas it reports match those of single steps from the same
+    start."""
     from paper_2509_05090_gb300 import binding
     w = I.WORKLOADS["heis_D5_chi360"]
     A = w.site_tensor()

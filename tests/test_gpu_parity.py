@@ -160,14 +160,14 @@ def test_single_step_matches_oracle_chi144(ctm_lib):
 @pytest.mark.parametrize("chi", [192, 224])
 def test_single_step_matches_oracle_wide(ctm_lib, chi):
     """chi = 192 and 224 at D = 3: the QR's compact-WY solve reads U from L2 (more than 160
-    columns) and the corner spectrum keeps only C's lower triangle in shared memory."""
+    columns); the corner spectrum runs on the thread-block cluster (chi >= 97)."""
     O.set_threads(0)
     _step_parity(I.random_site_tensor(2, 3, 78), chi, 2)
 
 
 def test_single_step_matches_oracle_chi320(ctm_lib):
-    """chi = 320 at D = 3 (n = 2880): the corner spectrum keeps C's lower triangle in global
-    memory (chi > 224) and the QR takes 320 columns.  Either comparison branch may apply."""
+    """chi = 320 at D = 3 (n = 2880): the corner spectrum over the 16-CTA cluster (20 rows of
+    C per CTA) and a QR of 320 columns.  Either comparison branch may apply."""
     O.set_threads(0)
     _step_parity(I.random_site_tensor(2, 3, 79), 320, 1, expect_full=None)
 
