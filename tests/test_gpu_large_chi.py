@@ -2,8 +2,9 @@
 
 Heisenberg D = 5, chi = 480 (n = 12000): one SM's share of the QR's rows (79 rows of
 481 doubles) does not fit shared memory, so the row blocks live in the global slab,
-and the corner spectrum runs over a 16-CTA thread-block cluster (30 rows of C per CTA).  The oracle's
-step at this size takes minutes, so the checks are properties that hold at any size
+and the corner spectrum runs over a 16-CTA thread-block cluster (30 rows of C per
+CTA).  The oracle's step at this size takes minutes, so the checks are properties
+that hold at any size
 (Sec. II.B: Y = Q R with Q orthonormal and diag(R) >= 0; the corner spectrum is the
 normalised |eigenvalues| of the symmetric corner), plus the split-BF16 step against
 the library's FP64 step from the same environment.  The same kernels are compared
