@@ -214,6 +214,9 @@ void orc_householder_qr(int n, int k, const double *Y, double *Q, double *R)
             vtv += v * v;
         }
         tau[j] = 2.0 / vtv;
+        /* each column is updated by one thread in the written order (bit-identical for any
+         * thread count) */
+#pragma omp parallel for schedule(static)
         for (int c = j; c < k; ++c) {
             double w = 0.0;
             for (int r = j; r < n; ++r) w += V[(size_t)r * k + j] * A[(size_t)r * k + c];
@@ -228,6 +231,7 @@ void orc_householder_qr(int n, int k, const double *Y, double *Q, double *R)
     for (int j = 0; j < k; ++j) Q[(size_t)j * k + j] = 1.0;
     for (int j = k - 1; j >= 0; --j) {
         if (tau[j] == 0.0) continue;
+#pragma omp parallel for schedule(static)
         for (int c = 0; c < k; ++c) {
             double w = 0.0;
             for (int r = j; r < n; ++r) w += V[(size_t)r * k + j] * Q[(size_t)r * k + c];
