@@ -67,3 +67,21 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with contextlib.redirect_stdout(out):
         rc = bench.run_reference(args, inputs.WORKLOADS["kh_D6_chi72"])
     assert rc == 0 and out.getvalue() == ""
+
+
+def test_reference_arm_line_times_k_steps_after_w(monkeypatch):
+    """Alone (rank 0 of 1) the reference arm prints one JSON line: the oracle timed over
+    exactly K steps after W untimed ones, with the keys the contract asks of that arm."""
+    import json
+    from paper_2509_05090_gb300 import inputs
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    monkeypatch.delenv("RANK", raising=False)
+    args = argparse.Namespace(gpus=1, steps=2, warmup=3)
+    out = io.StringIO()
+    with contextlib.redirect_stdout(out):
+        rc = bench.run_reference(args, inputs.WORKLOADS["heis_D2_chi8"])
+    line = json.loads(out.getvalue().strip().splitlines()[-1])
+    assert rc == 0 and line["impl"] == "reference"
+    assert line["steps"] == 2 and line["warmup"] == 3
+    assert line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["value"] == line["value"]
