@@ -3,7 +3,10 @@
 // fixed so that diag(R) >= 0.  Always FP64.
 //
 // One cooperative launch over G <= #SM CTAs.  CTA c keeps its block of rows of
-// Y (and later of the reflectors) in shared memory for the whole factorisation.
+// Y (and later of the reflectors) in shared memory for the whole factorisation, or,
+// where one SM's share of the rows does not fit there beside the panel scratch (large
+// k or n), in its part of a global slab that stays in L2 (qr_kernel<true>: the same
+// steps on the same layout, on a grid that leaves two SMs free).
 // Columns are taken in panels of up to QB (8).  For a panel starting at column j0
 // every CTA forms, over its rows >= j0, the partial Gram rows
 // G[i][kk] = a_{j0+i}^T a_kk (i < QB, kk >= j0+i) and the owners publish the
