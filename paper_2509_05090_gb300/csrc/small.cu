@@ -185,8 +185,9 @@ __global__ void scale_by_partials_kernel(long long count, double *x, const doubl
 }
 
 // a7: corner spectrum and delta, in three launches.
-// (1) one CTA: Householder tridiagonalisation of the symmetric corner in shared
-//     memory -> diagonal d and squared off-diagonal e^2 (global work buffer);
+// (1) Householder tridiagonalisation of the symmetric corner -> diagonal d and squared
+//     off-diagonal e^2 (global work buffer): one CTA with the corner in shared memory
+//     below TRI_CLUSTER_MIN, a thread-block cluster holding it by rows from there;
 // (2) one warp per eigenvalue: multisection on [-|C|_F, |C|_F], each
 //     lane evaluating the Sturm count at one of 32 points per round
 //     (5 bits per round instead of 1).  The count is the number of sign
