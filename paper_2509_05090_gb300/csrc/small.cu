@@ -6,6 +6,7 @@
 // All FP64.
 #include <math.h>
 
+#include <atomic>
 #include <cooperative_groups.h>
 #include <mutex>
 
@@ -726,7 +727,7 @@ cudaError_t launch_normalize(long long count, double *x, double *partials, int n
 // else 0 (the single-CTA reduction from global memory).  Decided once per chi.
 static std::mutex g_tri_mu;
 static signed char g_tri_cs[SPEC_MAX_CHI + 1];   // 0: not decided, -1: none, else the size
-static bool g_tri_cluster_ok = false;             // the cluster kernels' attributes were accepted
+static std::atomic<bool> g_tri_cluster_ok{false}; // the cluster kernels' attributes were accepted
 
 template <int CS>
 static int tri_cluster_fits(int chi)
